@@ -1,0 +1,26 @@
+"""Plain FP64 CPU oracle for the MLMC multigrid hot path.
+
+TEST INFRASTRUCTURE ONLY. Only tests/, the smoke check and the CPU-baseline leg of
+bench.py may import this package. It shares no code with the CUDA library
+(paper_1607_03252_gb300) and never imports it.
+
+Contents:
+  mlmc_oracle.c  the solver, field and sample pipeline in plain C (FP64), each
+                 function citing the passage of Gmeiner et al. it follows;
+  core.py        ctypes wrapper around it;
+  stats.py       MLMC estimator statistics (Sec. 2: Eqs. 6, 8, 10, 11, 14, 15) from
+                 their plain definitions with exactly rounded sums.
+
+Parity status (each item's pin lives in tests/test_oracle_*.py):
+  Philox4x32-10 words  round structure pinned through the 64-bit variant against
+                       numpy's Philox4x64-10; the 32-bit constants are pinned only by
+                       statistical tests (no published test vector is available offline);
+  field                pinned by its mean, variance and covariance closed forms;
+  operator, smoother,  pinned by the exact discrete eigenfunction, the O(h^2)
+  transfer, V-cycle    manufactured-solution rate, a dense direct solve, the transfer
+                       adjoint and exactness identities, and h-independent convergence;
+  QoI                  pinned by trapezoid exactness on multilinear functions;
+  statistics           pinned by math.fsum and a hand-evaluated Eq. 11 case.
+"""
+from .core import *  # noqa: F401,F403
+from . import stats  # noqa: F401

@@ -1,0 +1,582 @@
+/*
+ * mlmc_oracle.c -- plain, slow FP64 CPU oracle for the MLMC multigrid hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark are the only code that may load this library. It shares no source,
+ * header or helper with the CUDA library, and neither includes the other.
+ *
+ * What it computes, following Gmeiner, Drzisga, Ruede, Scheichl, Wohlmuth,
+ * "Scheduling massively parallel multigrid for multilevel Monte Carlo methods":
+ *   - one sample Y_l = Q_l - Q_{l-1} of the MLMC level difference, both solves on the
+ *     same random coefficient sample (Sec. 2.2, Eq. 8 and Algorithm 1, steps 1.a.i-ii);
+ *   - the model problem -div(k grad u) = f on D = (0,1)^3 with homogeneous Dirichlet
+ *     data (Sec. 3, Eq. 16), with a lognormal coefficient k = exp(Z) (Sec. 3.2);
+ *   - the deterministic solve by geometric multigrid (Sec. 7.1 names the cycle family).
+ *
+ * The concrete discretisation, field model, cycle and quantity of interest are the
+ * readings fixed for this library (the paper uses P1 finite elements, an SPDE field
+ * sampler and an FMG cycle instead):
+ *   grid      nodes x_ijk = (i h, j h, k h), i,j,k in 0..n-1, n = 2^p + 1, h = 1/(n-1);
+ *             u = 0 on boundary nodes, unknowns are the interior nodes;
+ *   operator  (A u)_p = h^-2 sum_{q in N(p)} k_pq (u_p - u_q), the vertex-centred
+ *             7-point finite-volume form with harmonic-mean face coefficients
+ *             k_pq = 2 k_p k_q / (k_p + k_q) of the nodal k (boundary nodes included);
+ *   field     log k(x) = sigma sqrt(2/M) sum_m cos(w_m . x + b_m),
+ *             w_m ~ N(0, I/ell^2), b_m ~ U[0, 2 pi), drawn by Philox4x32-10;
+ *   cycle     V(nu1, nu2) with red-black Gauss-Seidel, full weighting, trilinear
+ *             prolongation, rediscretised coarse operators (k injected), exact dense
+ *             Cholesky solve on the 5^3 grid; cycles repeat until ||f-Au||/||f|| <= rtol;
+ *   QoI       Q = mean of u over [0.25, 0.75]^3 by the tensor trapezoid rule.
+ *
+ * Every loop below follows those definitions directly; nothing is blocked, fused or
+ * reordered. Compile with -ffp-contract=off so that no multiply-add is contracted.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_ERR_INVALID (-1)
+#define ORC_ERR_OOM (-2)
+#define ORC_ERR_NOT_CONVERGED (-3)
+
+static const double ORC_PI = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------------------------
+ * Philox4x32-10 and Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11). One round maps the counter (c0,c1,c2,c3) with
+ * key (k0,k1) to (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0));
+ * the key advances by the Weyl constants (W0, W1) between rounds; ten rounds.
+ * The 64-bit variant is kept only so that the round structure can be checked against
+ * an independent library implementation of Philox4x64-10.
+ * ---------------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  uint32_t k[2] = {key_in[0], key_in[1]};
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k[0] += W0;
+      k[1] += W1;
+    }
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c[0];
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    uint32_t n3 = lo0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+  }
+  out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+  /* schoolbook 32x32 partial products, no compiler extensions */
+  uint64_t a0 = a & 0xFFFFFFFFu, a1 = a >> 32, b0 = b & 0xFFFFFFFFu, b1 = b >> 32;
+  uint64_t p00 = a0 * b0, p01 = a0 * b1, p10 = a1 * b0, p11 = a1 * b1;
+  uint64_t mid = (p00 >> 32) + (p01 & 0xFFFFFFFFu) + (p10 & 0xFFFFFFFFu);
+  *lo = (mid << 32) | (p00 & 0xFFFFFFFFu);
+  *hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+}
+
+void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+  uint64_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  uint64_t k[2] = {key_in[0], key_in[1]};
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k[0] += W0;
+      k[1] += W1;
+    }
+    uint64_t hi0, lo0, hi1, lo1;
+    mulhilo64(M0, c[0], &hi0, &lo0);
+    mulhilo64(M1, c[2], &hi1, &lo1);
+    uint64_t n0 = hi1 ^ c[1] ^ k[0];
+    uint64_t n1 = lo1;
+    uint64_t n2 = hi0 ^ c[3] ^ k[1];
+    uint64_t n3 = lo0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+  }
+  out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* 53-bit uniform in the open interval (0,1) from two 32-bit words. */
+static double uniform53(uint32_t a, uint32_t b) {
+  double hi = (double)(a >> 5);  /* 27 bits */
+  double lo = (double)(b >> 6);  /* 26 bits */
+  return (hi * 67108864.0 + lo + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+/* ------------------------------------------------------------------------------------
+ * Random features of one sample (the realisation omega of Algorithm 1, step 1.a.i).
+ * Philox key = (run_seed low word, run_seed high word); for feature m and block
+ * c = 0,1,2 the counter is (id low word, id high word, m, c). The 12 words give six
+ * uniforms U1..U6 from consecutive word pairs; Box-Muller turns (U1,U2) and (U3,U4)
+ * into three standard normals g1, g2, g3; w_m = (g1, g2, g3) / ell and b_m = 2 pi U5.
+ * ---------------------------------------------------------------------------------- */
+void orc_uniforms(uint64_t run_seed, uint64_t sample_id, int m, double U[6]) {
+  uint32_t key[2] = {(uint32_t)run_seed, (uint32_t)(run_seed >> 32)};
+  uint32_t words[12];
+  for (int c = 0; c < 3; ++c) {
+    uint32_t ctr[4] = {(uint32_t)sample_id, (uint32_t)(sample_id >> 32), (uint32_t)m, (uint32_t)c};
+    orc_philox4x32_10(ctr, key, &words[4 * c]);
+  }
+  for (int i = 0; i < 6; ++i) U[i] = uniform53(words[2 * i], words[2 * i + 1]);
+}
+
+void orc_features(uint64_t run_seed, uint64_t sample_id, int M, double ell, double* w, double* b) {
+  for (int m = 0; m < M; ++m) {
+    double U[6];
+    orc_uniforms(run_seed, sample_id, m, U);
+    double r1 = sqrt(-2.0 * log(U[0]));
+    double r2 = sqrt(-2.0 * log(U[2]));
+    double g1 = r1 * cos(2.0 * ORC_PI * U[1]);
+    double g2 = r1 * sin(2.0 * ORC_PI * U[1]);
+    double g3 = r2 * cos(2.0 * ORC_PI * U[3]);
+    w[3 * m + 0] = g1 / ell;
+    w[3 * m + 1] = g2 / ell;
+    w[3 * m + 2] = g3 / ell;
+    b[m] = 2.0 * ORC_PI * U[4];
+  }
+}
+
+/* log k at one point: sigma sqrt(2/M) sum_m cos(w_m . x + b_m), features in order. */
+double orc_logk_point(const double* w, const double* b, int M, double sigma, double x, double y, double z) {
+  double s = 0.0;
+  for (int m = 0; m < M; ++m) s += cos(w[3 * m] * x + w[3 * m + 1] * y + w[3 * m + 2] * z + b[m]);
+  return sigma * sqrt(2.0 / (double)M) * s;
+}
+
+/* Nodal coefficient k = exp(log k) at all n^3 nodes (x fastest). */
+int orc_field(uint64_t run_seed, uint64_t sample_id, int M, double sigma, double ell, int n, double* k) {
+  if (M <= 0 || n < 2) return ORC_ERR_INVALID;
+  double* w = (double*)malloc(sizeof(double) * 3 * (size_t)M);
+  double* b = (double*)malloc(sizeof(double) * (size_t)M);
+  if (!w || !b) { free(w); free(b); return ORC_ERR_OOM; }
+  orc_features(run_seed, sample_id, M, ell, w, b);
+  double h = 1.0 / (double)(n - 1);
+  for (int kz = 0; kz < n; ++kz)
+    for (int jy = 0; jy < n; ++jy)
+      for (int ix = 0; ix < n; ++ix)
+        k[((size_t)kz * n + jy) * n + ix] = exp(orc_logk_point(w, b, M, sigma, ix * h, jy * h, kz * h));
+  free(w);
+  free(b);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Grid operator. Face coefficients are harmonic means of nodal k. In "mixed" mode the
+ * nodal values are first rounded to FP32 and the harmonic mean is evaluated in FP32
+ * arithmetic (product, sum, quotient, each rounded); the operator is then applied in
+ * FP64 with those FP32-valued faces. That is the operator the FP32-smoother /
+ * FP64-refinement solver converges to.
+ * ---------------------------------------------------------------------------------- */
+static double kface(double a, double b, int mixed) {
+  if (mixed) {
+    float a32 = (float)a, b32 = (float)b;
+    float num = 2.0f * a32 * b32;
+    float den = a32 + b32;
+    float q = num / den;
+    return (double)q;
+  }
+  return 2.0 * a * b / (a + b);
+}
+
+#define IDX(n, i, j, k) (((size_t)(k) * (size_t)(n) + (size_t)(j)) * (size_t)(n) + (size_t)(i))
+
+static int is_interior(int n, int i, int j, int k) {
+  return i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1;
+}
+
+/* (A u)_p for an interior node p; boundary u is taken as zero. */
+static double apply_at(int n, const double* kn, const double* u, int i, int j, int k, int mixed) {
+  static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  double h = 1.0 / (double)(n - 1);
+  size_t p = IDX(n, i, j, k);
+  double up = u[p];
+  double s = 0.0;
+  for (int d = 0; d < 6; ++d) {
+    int qi = i + off[d][0], qj = j + off[d][1], qk = k + off[d][2];
+    size_t q = IDX(n, qi, qj, qk);
+    double uq = is_interior(n, qi, qj, qk) ? u[q] : 0.0;
+    s += kface(kn[p], kn[q], mixed) * (up - uq);
+  }
+  return s / (h * h);
+}
+
+/* A u on all interior nodes; boundary entries of Au are set to zero. */
+void orc_apply(int n, const double* kn, const double* u, double* Au, int mixed) {
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i)
+        Au[IDX(n, i, j, k)] = is_interior(n, i, j, k) ? apply_at(n, kn, u, i, j, k, mixed) : 0.0;
+}
+
+/* r = f - A u on interior nodes, zero on the boundary. f == NULL means f = 1. */
+void orc_residual(int n, const double* kn, const double* f, const double* u, double* r, int mixed) {
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        size_t p = IDX(n, i, j, k);
+        if (!is_interior(n, i, j, k)) { r[p] = 0.0; continue; }
+        double fp = f ? f[p] : 1.0;
+        r[p] = fp - apply_at(n, kn, u, i, j, k, mixed);
+      }
+}
+
+/* One red-black Gauss-Seidel sweep: red nodes ((i+j+k) even) first, then black.
+ * u_p <- (h^2 f_p + sum_q k_pq u_q) / sum_q k_pq with boundary u_q = 0. */
+void orc_rbgs_sweep(int n, const double* kn, const double* f, double* u, int mixed) {
+  static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  double h = 1.0 / (double)(n - 1);
+  for (int colour = 0; colour < 2; ++colour)
+    for (int k = 1; k < n - 1; ++k)
+      for (int j = 1; j < n - 1; ++j)
+        for (int i = 1; i < n - 1; ++i) {
+          if (((i + j + k) & 1) != colour) continue;
+          size_t p = IDX(n, i, j, k);
+          double num = h * h * (f ? f[p] : 1.0), den = 0.0;
+          for (int d = 0; d < 6; ++d) {
+            int qi = i + off[d][0], qj = j + off[d][1], qk = k + off[d][2];
+            size_t q = IDX(n, qi, qj, qk);
+            double kf = kface(kn[p], kn[q], mixed);
+            num += kf * (is_interior(n, qi, qj, qk) ? u[q] : 0.0);
+            den += kf;
+          }
+          u[p] = num / den;
+        }
+}
+
+/* Full weighting: coarse value at interior coarse node I is
+ * sum over offsets d in {-1,0,1}^3 of (1/64) prod_a (2 - |d_a|) * r(2I + d).
+ * Coarse boundary values are zero. */
+void orc_restrict_fw(int nf, const double* r, double* rc) {
+  int nc = (nf + 1) / 2;
+  for (int K = 0; K < nc; ++K)
+    for (int J = 0; J < nc; ++J)
+      for (int I = 0; I < nc; ++I) {
+        size_t P = IDX(nc, I, J, K);
+        if (!is_interior(nc, I, J, K)) { rc[P] = 0.0; continue; }
+        double s = 0.0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              double wgt = (double)((2 - abs(dx)) * (2 - abs(dy)) * (2 - abs(dz))) / 64.0;
+              s += wgt * r[IDX(nf, 2 * I + dx, 2 * J + dy, 2 * K + dz)];
+            }
+        rc[P] = s;
+      }
+}
+
+/* Trilinear interpolation of the coarse correction, added on interior fine nodes:
+ * the fine node (i,j,k) lies between coarse nodes floor(i/2)..ceil(i/2) per axis,
+ * with weight 1 on a coincident axis and 1/2 on each neighbour otherwise. */
+void orc_prolong_add(int nf, const double* ec, double* u) {
+  int nc = (nf + 1) / 2;
+  for (int k = 1; k < nf - 1; ++k)
+    for (int j = 1; j < nf - 1; ++j)
+      for (int i = 1; i < nf - 1; ++i) {
+        int ia[2] = {i / 2, (i + 1) / 2}, ja[2] = {j / 2, (j + 1) / 2}, ka[2] = {k / 2, (k + 1) / 2};
+        double s = 0.0;
+        for (int c = 0; c < 8; ++c) {
+          int I = ia[c & 1], J = ja[(c >> 1) & 1], K = ka[(c >> 2) & 1];
+          s += 0.125 * ec[IDX(nc, I, J, K)];
+        }
+        u[IDX(nf, i, j, k)] += s;
+      }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Exact coarsest-grid solve: assemble the dense matrix of A on the interior nodes
+ * (column by column, by applying A to unit vectors), factor A = L L^T by Cholesky,
+ * and solve by forward and backward substitution.
+ * ---------------------------------------------------------------------------------- */
+int orc_coarse_solve(int n, const double* kn, const double* f, double* u, int mixed) {
+  int m = n - 2, N = m * m * m;
+  size_t n3 = (size_t)n * n * n;
+  double* A = (double*)calloc((size_t)N * N, sizeof(double));
+  double* e = (double*)calloc(n3, sizeof(double));
+  double* Ae = (double*)calloc(n3, sizeof(double));
+  double* y = (double*)calloc((size_t)N, sizeof(double));
+  int status = ORC_OK;
+  if (!A || !e || !Ae || !y) { status = ORC_ERR_OOM; goto done; }
+  for (int c = 0; c < N; ++c) {
+    int ci = 1 + c % m, cj = 1 + (c / m) % m, ck = 1 + c / (m * m);
+    memset(e, 0, n3 * sizeof(double));
+    e[IDX(n, ci, cj, ck)] = 1.0;
+    orc_apply(n, kn, e, Ae, mixed);
+    for (int r = 0; r < N; ++r) {
+      int ri = 1 + r % m, rj = 1 + (r / m) % m, rk = 1 + r / (m * m);
+      A[(size_t)r * N + c] = Ae[IDX(n, ri, rj, rk)];
+    }
+  }
+  /* Cholesky, lower triangle in place */
+  for (int j = 0; j < N; ++j) {
+    double d = A[(size_t)j * N + j];
+    for (int p = 0; p < j; ++p) d -= A[(size_t)j * N + p] * A[(size_t)j * N + p];
+    if (!(d > 0.0)) { status = ORC_ERR_INVALID; goto done; }
+    double ljj = sqrt(d);
+    A[(size_t)j * N + j] = ljj;
+    for (int i = j + 1; i < N; ++i) {
+      double s = A[(size_t)i * N + j];
+      for (int p = 0; p < j; ++p) s -= A[(size_t)i * N + p] * A[(size_t)j * N + p];
+      A[(size_t)i * N + j] = s / ljj;
+    }
+  }
+  /* L y = f */
+  for (int i = 0; i < N; ++i) {
+    int ii = 1 + i % m, ij = 1 + (i / m) % m, ik = 1 + i / (m * m);
+    double s = f ? f[IDX(n, ii, ij, ik)] : 1.0;
+    for (int p = 0; p < i; ++p) s -= A[(size_t)i * N + p] * y[p];
+    y[i] = s / A[(size_t)i * N + i];
+  }
+  /* L^T x = y, written into the interior of u */
+  for (int i = N - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int p = i + 1; p < N; ++p) s -= A[(size_t)p * N + i] * y[p];
+    y[i] = s / A[(size_t)i * N + i];
+  }
+  memset(u, 0, n3 * sizeof(double));
+  for (int i = 0; i < N; ++i) {
+    int ii = 1 + i % m, ij = 1 + (i / m) % m, ik = 1 + i / (m * m);
+    u[IDX(n, ii, ij, ik)] = y[i];
+  }
+done:
+  free(A); free(e); free(Ae); free(y);
+  return status;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Multigrid hierarchy and V-cycle.
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+  int levels;      /* number of grids, finest first */
+  int n[32];
+  double* k[32];   /* nodal coefficient per grid: injection of the finest k */
+  double* f[32];   /* right-hand side per grid (grid 0: the caller's f or NULL) */
+  double* u[32];   /* iterate / correction per grid */
+  double* r[32];   /* residual scratch per grid */
+} orc_hierarchy;
+
+static void hier_free(orc_hierarchy* H) {
+  for (int l = 0; l < H->levels; ++l) {
+    if (l > 0) { free(H->k[l]); free(H->f[l]); free(H->u[l]); }
+    free(H->r[l]);
+  }
+}
+
+/* Injection: coarse node I is fine node 2I. */
+static void inject(int nf, const double* kf, double* kc) {
+  int nc = (nf + 1) / 2;
+  for (int K = 0; K < nc; ++K)
+    for (int J = 0; J < nc; ++J)
+      for (int I = 0; I < nc; ++I) kc[IDX(nc, I, J, K)] = kf[IDX(nf, 2 * I, 2 * J, 2 * K)];
+}
+
+static int valid_n(int n) {
+  if (n < 5) return 0;
+  int m = n - 1;
+  return (m & (m - 1)) == 0;
+}
+
+static int hier_build(orc_hierarchy* H, int n, const double* k, const double* f, double* u) {
+  memset(H, 0, sizeof(*H));
+  int nl = n, l = 0;
+  while (1) {
+    H->n[l] = nl;
+    if (nl == 5) break;
+    nl = (nl + 1) / 2;
+    ++l;
+  }
+  H->levels = l + 1;
+  H->k[0] = (double*)k;
+  H->f[0] = (double*)f;
+  H->u[0] = u;
+  for (l = 0; l < H->levels; ++l) {
+    size_t n3 = (size_t)H->n[l] * H->n[l] * H->n[l];
+    if (l > 0) {
+      H->k[l] = (double*)malloc(n3 * sizeof(double));
+      H->f[l] = (double*)calloc(n3, sizeof(double));
+      H->u[l] = (double*)calloc(n3, sizeof(double));
+      if (!H->k[l] || !H->f[l] || !H->u[l]) { H->levels = l + 1; return ORC_ERR_OOM; }
+      inject(H->n[l - 1], H->k[l - 1], H->k[l]);
+    }
+    H->r[l] = (double*)calloc(n3, sizeof(double));
+    if (!H->r[l]) { H->levels = l + 1; return ORC_ERR_OOM; }
+  }
+  return ORC_OK;
+}
+
+/* One V(nu1, nu2) cycle on grid l of the hierarchy (u[l] is updated in place). */
+static int vcycle(orc_hierarchy* H, int l, int nu1, int nu2, int mixed) {
+  int n = H->n[l];
+  if (l == H->levels - 1) return orc_coarse_solve(n, H->k[l], H->f[l], H->u[l], mixed);
+  for (int s = 0; s < nu1; ++s) orc_rbgs_sweep(n, H->k[l], H->f[l], H->u[l], mixed);
+  orc_residual(n, H->k[l], H->f[l], H->u[l], H->r[l], mixed);
+  orc_restrict_fw(n, H->r[l], H->f[l + 1]);
+  size_t nc3 = (size_t)H->n[l + 1] * H->n[l + 1] * H->n[l + 1];
+  memset(H->u[l + 1], 0, nc3 * sizeof(double));
+  int st = vcycle(H, l + 1, nu1, nu2, mixed);
+  if (st != ORC_OK) return st;
+  orc_prolong_add(n, H->u[l + 1], H->u[l]);
+  for (int s = 0; s < nu2; ++s) orc_rbgs_sweep(n, H->k[l], H->f[l], H->u[l], mixed);
+  return ORC_OK;
+}
+
+/* Discrete l2 norm over interior nodes. */
+static double interior_norm(int n, const double* v) {
+  double s = 0.0;
+  for (int k = 1; k < n - 1; ++k)
+    for (int j = 1; j < n - 1; ++j)
+      for (int i = 1; i < n - 1; ++i) s += v[IDX(n, i, j, k)] * v[IDX(n, i, j, k)];
+  return sqrt(s);
+}
+
+/*
+ * Solve A u = f by V(nu1, nu2) cycles from the caller's initial guess in u (boundary
+ * entries are forced to zero). After each cycle the relative residual
+ * ||f - A u||_2 / ||f||_2 over interior nodes is recorded in res_hist[c] (if not
+ * NULL); cycling stops when it is <= rtol or after max_cycles cycles, which returns
+ * ORC_ERR_NOT_CONVERGED (u still holds the last iterate). rtol <= 0 runs exactly
+ * max_cycles cycles and returns ORC_OK.
+ */
+int orc_mg_solve(int n, const double* k, const double* f, double* u, int nu1, int nu2, double rtol,
+                 int max_cycles, int mixed, int* cycles_out, double* relres_out, double* res_hist) {
+  if (!valid_n(n) || nu1 < 0 || nu2 < 0 || max_cycles < 0) return ORC_ERR_INVALID;
+  size_t n3 = (size_t)n * n * n;
+  for (int kz = 0; kz < n; ++kz)
+    for (int jy = 0; jy < n; ++jy)
+      for (int ix = 0; ix < n; ++ix)
+        if (!is_interior(n, ix, jy, kz)) u[IDX(n, ix, jy, kz)] = 0.0;
+  orc_hierarchy H;
+  int st = hier_build(&H, n, k, f, u);
+  if (st != ORC_OK) { hier_free(&H); return st; }
+  double* fone = NULL;
+  if (!f) {
+    fone = (double*)malloc(n3 * sizeof(double));
+    if (!fone) { hier_free(&H); return ORC_ERR_OOM; }
+    for (size_t p = 0; p < n3; ++p) fone[p] = 1.0;
+  }
+  const double* fe = f ? f : fone;
+  double fnorm = interior_norm(n, fe);
+  double relres = 0.0;
+  orc_residual(n, k, f, u, H.r[0], mixed);
+  relres = interior_norm(n, H.r[0]) / fnorm;
+  int c = 0;
+  int status = ORC_OK;
+  if (rtol > 0.0 && relres <= rtol) goto finish;
+  for (c = 0; c < max_cycles;) {
+    st = vcycle(&H, 0, nu1, nu2, mixed);
+    if (st != ORC_OK) { status = st; goto finish; }
+    ++c;
+    orc_residual(n, k, f, u, H.r[0], mixed);
+    relres = interior_norm(n, H.r[0]) / fnorm;
+    if (res_hist) res_hist[c - 1] = relres;
+    if (rtol > 0.0 && relres <= rtol) break;
+  }
+  if (rtol > 0.0 && relres > rtol) status = ORC_ERR_NOT_CONVERGED;
+finish:
+  if (cycles_out) *cycles_out = c;
+  if (relres_out) *relres_out = relres;
+  free(fone);
+  hier_free(&H);
+  return status;
+}
+
+/* Q = mean of u over [0.25,0.75]^3 = 8 * h^3 * sum_S w_i w_j w_k u_ijk, with S the
+ * nodes (n-1)/4 .. 3(n-1)/4 per axis and trapezoid weights 1/2 at both ends. */
+double orc_qoi(int n, const double* u) {
+  int lo = (n - 1) / 4, hi = 3 * (n - 1) / 4;
+  double h = 1.0 / (double)(n - 1);
+  double s = 0.0;
+  for (int k = lo; k <= hi; ++k)
+    for (int j = lo; j <= hi; ++j)
+      for (int i = lo; i <= hi; ++i) {
+        double wi = (i == lo || i == hi) ? 0.5 : 1.0;
+        double wj = (j == lo || j == hi) ? 0.5 : 1.0;
+        double wk = (k == lo || k == hi) ? 0.5 : 1.0;
+        s += wi * wj * wk * u[IDX(n, i, j, k)];
+      }
+  return 8.0 * h * h * h * s;
+}
+
+/* ------------------------------------------------------------------------------------
+ * One MLMC sample (Algorithm 1, steps 1.a.i-ii): set up the coefficient of the
+ * realisation `sample_id` on the fine grid n_fine and (if n_coarse > 0) on the
+ * coarse grid n_coarse, solve both with f = 1, and return Q on each grid.
+ * Each grid evaluates the field at its own nodes.
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+  uint64_t run_seed;
+  double sigma2;
+  double ell;
+  int M;
+  int nu1, nu2;
+  double rtol;
+  int max_cycles;
+  int mixed;
+} orc_cfg;
+
+static int solve_q(const orc_cfg* c, uint64_t sample_id, int n, double* Q, int* cycles) {
+  size_t n3 = (size_t)n * n * n;
+  double* k = (double*)malloc(n3 * sizeof(double));
+  double* u = (double*)calloc(n3, sizeof(double));
+  if (!k || !u) { free(k); free(u); return ORC_ERR_OOM; }
+  int st = orc_field(c->run_seed, sample_id, c->M, sqrt(c->sigma2), c->ell, n, k);
+  if (st == ORC_OK) {
+    double relres;
+    st = orc_mg_solve(n, k, NULL, u, c->nu1, c->nu2, c->rtol, c->max_cycles, c->mixed, cycles, &relres, NULL);
+    *Q = orc_qoi(n, u);
+  }
+  free(k);
+  free(u);
+  return st;
+}
+
+int orc_sample(const orc_cfg* c, int n_fine, int n_coarse, uint64_t sample_id, double* Qf, double* Qc,
+               int* cycles_f, int* cycles_c) {
+  int st = solve_q(c, sample_id, n_fine, Qf, cycles_f);
+  if (st != ORC_OK) return st;
+  *Qc = 0.0;
+  *cycles_c = 0;
+  if (n_coarse > 0) st = solve_q(c, sample_id, n_coarse, Qc, cycles_c);
+  return st;
+}
+
+/* A batch of independent samples, OpenMP over samples only (no other parallelism).
+ * Y[i] = Qf[i] - Qc[i] (Qc = 0 for level 0). Returns the first non-OK status. */
+int orc_level_batch(const orc_cfg* c, int n_fine, int n_coarse, const uint64_t* ids, int N, double* Y,
+                    double* Qf, double* Qc, int* cycles_f, int* cycles_c, int nthreads) {
+  int status = ORC_OK;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < N; ++i) {
+    int st = orc_sample(c, n_fine, n_coarse, ids[i], &Qf[i], &Qc[i], &cycles_f[i], &cycles_c[i]);
+    Y[i] = Qf[i] - Qc[i];
+    if (st != ORC_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+      if (status == ORC_OK) status = st;
+    }
+  }
+  return status;
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
