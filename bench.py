@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark of the MLMC multigrid hot path on one GB300 (or N, one process per GPU).
+
+One step = one full MLMC estimate of the configured workload: for every level l the
+N_l samples Y_l = Q_l - Q_{l-1} (field evaluation, fine and coarse multigrid solves on
+the same realisation, QoI, level statistics), all in the CUDA library.
+
+Default workload (--config c2): 4-level FP64 MLMC, levels 17^3, 33^3, 65^3, 129^3
+(fine grids), N_l = 4096, 1024, 256, 64, sigma^2 = 1, ell = 0.3, M = 256, V(2,2) to
+relative residual 1e-10, f = 1, QoI = mean of u over [0.25, 0.75]^3.
+
+Reported (one JSON line on rank 0):
+  value          MLMC samples/s over all levels (sum_l N_l per step x ranks / time),
+                 ids already in HBM, outputs left in HBM (device-resident C-ABI call);
+  per_level      samples/s per level;
+  e2e            the same through the host-buffer C-ABI call (ids built on the host,
+                 results copied back into pinned host memory every step);
+  roofline       the dominant kernel class: algorithmic work / its event-timed device
+                 time against the binding peak;
+  cpu_baseline   the FP64 CPU oracle on a bounded sample of the same ids, host cores.
+With --impl reference the oracle itself is timed on the same workload (bounded sample
+per step) and reported as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1607_03252_gb300.workloads import CONFIGS, RUN_SEED, level_n, sample_ids  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="own", choices=["own", "reference"])
+    p.add_argument("--config", default="c2", choices=["c1", "c2"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def workload(cfg_name):
+    c = CONFIGS[cfg_name]
+    levels = c["levels"]
+    N = c["N"]
+    single = c.get("single_level", False)
+    return c, levels, N, single
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# --------------------------------------------------------------------------------------
+def oracle_level_rates(cfg, levels, single, counts):
+    """samples/s of the oracle per level on the given sample counts (OpenMP over samples)."""
+    import oracle
+
+    ocfg = oracle.make_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], cfg["nu1"], cfg["nu2"], cfg["rtol"], 100)
+    rates, secs = {}, {}
+    for l, cnt in zip(levels, counts):
+        ids = sample_ids(l, 0, cnt)
+        nc = 0 if (single or l == 0) else level_n(l - 1)
+        t = time.perf_counter()
+        oracle.level_batch(ocfg, level_n(l), nc, ids)
+        dt = time.perf_counter() - t
+        rates[l] = cnt / dt
+        secs[l] = dt
+    return rates, secs
+
+
+def oracle_counts(levels, threads):
+    base = {0: max(16, 4 * threads), 1: max(8, threads), 2: max(4, threads // 2), 3: max(1, threads // 2),
+            4: 1, 5: 1}
+    return [base[l] for l in levels]
+
+
+def extrapolated_rate(levels, N, rates):
+    t = sum(n / rates[l] for l, n in zip(levels, N))
+    return sum(N) / t
+
+
+# --------------------------------------------------------------------------------------
+# Reference arm: the oracle
+# --------------------------------------------------------------------------------------
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    cfg, levels, N, single = workload(args.config)
+    threads = oracle.max_threads()
+    counts = [max(1, c // 4) for c in oracle_counts(levels, threads)]
+    step_times, all_rates = [], []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        rates, _ = oracle_level_rates(cfg, levels, single, counts)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            step_times.append(dt)
+            all_rates.append(rates)
+    mean_rates = {l: statistics.mean(r[l] for r in all_rates) for l in levels}
+    value = extrapolated_rate(levels, N, mean_rates)
+    sample = "per step: %s samples on levels %s (ids of the benchmark workload), OpenMP over samples; " \
+             "samples/s per level extrapolated to N=%s" % (counts, levels, N)
+    line = {
+        "impl": "reference", "metric": "MLMC samples/s (all levels, %s)" % cfg["name"], "value": value,
+        "unit": "samples/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(step_times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox realisations)",
+        "config": {"workload": cfg["name"], "levels": levels, "N": N, "fine_n": [level_n(l) for l in levels],
+                   "sigma2": cfg["sigma2"], "ell": cfg["ell"], "M": cfg["M"], "rtol": cfg["rtol"]},
+        "per_level": {str(l): mean_rates[l] for l in levels},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------------------
+# Own arm
+# --------------------------------------------------------------------------------------
+def own_arm(args):
+    import torch
+
+    import paper_1607_03252_gb300 as mg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cfg, levels, N, single = workload(args.config)
+    prec = mg.MLMC_PREC_F64 if cfg["precision"] == "f64" else mg.MLMC_PREC_MIXED
+    stream = torch.cuda.Stream()
+    dev = torch.device("cuda", local)
+    # inputs resident in HBM: each rank its own realisations (weak scaling)
+    ids = {l: torch.from_numpy(sample_ids(l, rank * n, n).view("int64")).to(dev) for l, n in zip(levels, N)}
+    Y = {l: torch.empty(n, dtype=torch.float64, device=dev) for l, n in zip(levels, N)}
+    mcfg = {}
+    for l, n in zip(levels, N):
+        n0 = level_n(l) if single else 17
+        lvl = 0 if single else l
+        mcfg[l] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=cfg["nu1"],
+                                    nu2=cfg["nu2"], rtol=cfg["rtol"], precision=prec, max_batch=n, stream=stream), lvl)
+    lev_ev = {l: [] for l in levels}
+    stats = {}
+
+    def step(record):
+        for l in levels:
+            c, lvl = mcfg[l]
+            if record:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            stats[l] = mg.mlmc_level_run(c, lvl, ids[l], Y_dev=Y[l])
+            if record:
+                b.record(stream)
+                lev_ev[l].append((a, b))
+        if world > 1:
+            import torch.distributed as dist
+
+            rec = torch.tensor([[stats[l].N, stats[l].mean, stats[l].M2] for l in levels], dtype=torch.float64,
+                               device=dev)
+            parts = [torch.empty_like(rec) for _ in range(world)]
+            dist.all_gather(parts, rec)
+            merged = merge_records([p.cpu().numpy() for p in parts])
+            stats["merged"] = merged
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    mg.profile_reset()
+    mg.profile_enable(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t_host = time.perf_counter() - t_host0
+    clk = clocks.stop()
+    mg.profile_enable(False)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    prof = mg.profile_read()
+    launches = mg.profile_total_launches()
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_samples = sum(N) * world * args.steps
+    value = total_samples / (elapsed_ms / 1e3)
+    per_level = {}
+    for l, n in zip(levels, N):
+        ms = sum(a.elapsed_time(b) for a, b in lev_ev[l])
+        per_level[str(l)] = n * world * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel class
+    peaks = measured_peaks()
+    roof = roofline(prof, peaks)
+
+    # end to end through the host-buffer C-ABI call
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(cfg, levels, N, single)
+        line = {
+            "metric": "MLMC samples/s (all levels, %s)" % cfg["name"], "value": value, "unit": "samples/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == mg.MLMC_PREC_F64 else "f32+f64",
+            "data": "synthetic (seeded Philox realisations, run_seed %d)" % RUN_SEED,
+            "config": {"workload": cfg["name"], "levels": levels, "N_per_gpu": N,
+                       "fine_n": [level_n(l) for l in levels], "sigma2": cfg["sigma2"], "ell": cfg["ell"],
+                       "M": cfg["M"], "cycle": "V(%d,%d)" % (cfg["nu1"], cfg["nu2"]), "rtol": cfg["rtol"],
+                       "parallelism": "replicas x%d (samples sharded by rank, no data-path collective)" % world,
+                       "l2": "every level's batch working set exceeds the 129 MB L2 (no flush needed)"},
+            "per_level": per_level,
+            "time_per_estimate_s": elapsed_ms / 1e3 / args.steps,
+            "level_stats": {str(l): {"mean": stats[l].mean, "var": stats[l].var_unbiased,
+                                     "cycles_fine": stats[l].mean_cycles_fine,
+                                     "cycles_coarse": stats[l].mean_cycles_coarse} for l in levels},
+            "roofline": roof, "gpu_launches": launches, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu,
+            "host_wall_s": t_host,
+            "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
+                               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def merge_records(parts):
+    """Chan's merge of per-rank (N, mean, M2) rows per level."""
+    import numpy as np
+
+    out = []
+    for l in range(parts[0].shape[0]):
+        n, mean, m2 = 0.0, 0.0, 0.0
+        for p in parts:
+            nb, mb, m2b = p[l]
+            if nb == 0:
+                continue
+            tot = n + nb
+            d = mb - mean
+            mean = mean + d * nb / tot
+            m2 = m2 + m2b + d * d * n * nb / tot
+            n = tot
+        out.append((n, mean, m2))
+    return np.array(out)
+
+
+def roofline(prof, peaks):
+    if not prof:
+        return None
+    name, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    timed = max(rec["timed"], 1)
+    avg_s = rec["ms"] / 1e3 / timed
+    per_launch_bytes = rec["bytes"] / max(rec["launches"], 1)
+    per_launch_flops = rec["flops"] / max(rec["launches"], 1)
+    hbm_peak = peaks.get("hbm_gbs")
+    fp64 = name.endswith("f64") or name in ("residual_mixed", "update_mixed", "coarse_setup", "norm")
+    if fp64:
+        achieved = per_launch_flops / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"],
+                "hbm_achieved_gbs": per_launch_bytes / avg_s / 1e9,
+                "hbm_frac_of_measured": (per_launch_bytes / avg_s / 1e9) / hbm_peak if hbm_peak else None}
+    achieved = per_launch_bytes / avg_s / 1e9
+    peak = hbm_peak if hbm_peak else 6800.0
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": "measured" if hbm_peak else "fallback", "traffic": None,
+            "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"]}
+
+
+def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream):
+    """Same workload through mlmc_level_estimate: ids built on the host and copied in,
+    Y/Qf/Qc copied back into pinned host buffers, every step."""
+    import ctypes
+
+    import numpy as np
+
+    bufs = {l: [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(3)] for l, n in zip(levels, N)}
+    cfgs = {}
+    for l, n in zip(levels, N):
+        n0 = level_n(l) if single else 17
+        cfgs[l] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=cfg["nu1"],
+                                    nu2=cfg["nu2"], rtol=cfg["rtol"], precision=prec, max_batch=n, stream=stream),
+                   0 if single else l)
+    L = mg.lib()
+    dp = ctypes.POINTER(ctypes.c_double)
+
+    def step():
+        for l, n in zip(levels, N):
+            c, lvl = cfgs[l]
+            first = int(sample_ids(l, rank * n, 1)[0])
+            out = mg.LevelStats()
+            y, qf, qc = (ctypes.cast(b.data_ptr(), dp) for b in bufs[l])
+            st = L.mlmc_level_estimate(ctypes.byref(c), lvl, first, n, y, qf, qc, ctypes.byref(out))
+            if st < 0:
+                raise mg.MlmcError(st, "mlmc_level_estimate", L.mlmc_last_error_string().decode())
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([dt], dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt = float(t.item())
+    return {"value": sum(N) * world * args.steps / dt, "unit": "samples/s",
+            "h2d_bytes_per_step": int(8 * sum(N)), "d2h_bytes_per_step": int(24 * sum(N)),
+            "api": "mlmc_level_estimate (host ids in, Y/Qf/Qc to pinned host memory)"}
+
+
+def cpu_baseline(cfg, levels, N, single):
+    import oracle
+
+    threads = oracle.max_threads()
+    counts = oracle_counts(levels, threads)
+    rates, secs = oracle_level_rates(cfg, levels, single, counts)
+    value = extrapolated_rate(levels, N, rates)
+    return {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
+            "sample": "levels %s: %s samples (same ids as the GPU run), %.1f s of CPU time; per-level samples/s "
+                      "extrapolated to N=%s" % (levels, counts, sum(secs.values()), N),
+            "per_level": {str(l): rates[l] for l in levels}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return own_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

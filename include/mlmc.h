@@ -1,0 +1,204 @@
+/*
+ * mlmc.h -- C ABI of the GB300 (sm_103a) multilevel Monte Carlo multigrid library.
+ *
+ * The library computes the data-parallel hot path of the multilevel Monte Carlo
+ * method of Gmeiner, Drzisga, Ruede, Scheichl and Wohlmuth, "Scheduling massively
+ * parallel multigrid for multilevel Monte Carlo methods": samples
+ * Y_l = Q_l - Q_{l-1} of the level differences (Sec. 2.2, Eq. 8, Algorithm 1), where
+ * both Q's of one sample come from solves of the model problem -div(k grad u) = f on
+ * D = (0,1)^3 with homogeneous Dirichlet data (Sec. 3, Eq. 16) on the SAME
+ * realisation of a lognormal coefficient k = exp(Z) (Sec. 3.2), by geometric
+ * multigrid on structured grids.
+ *
+ * Discretisation (fixed by this library; the paper's P1 finite elements and SPDE
+ * field sampler are replaced):
+ *   grid     nodes (i h, j h, k h), i,j,k = 0..n-1, n = 2^p + 1 (p >= 2), h = 1/(n-1);
+ *            u = 0 on boundary nodes;
+ *   operator (A u)_p = h^-2 sum_{q in N(p)} k_pq (u_p - u_q), 7-point, harmonic-mean
+ *            faces k_pq = 2 k_p k_q / (k_p + k_q) of the nodal coefficient;
+ *   field    log k(x) = sigma sqrt(2/M) sum_m cos(w_m . x + b_m), w_m ~ N(0, I/ell^2),
+ *            b_m ~ U[0, 2 pi), drawn by Philox4x32-10 keyed by (run_seed, sample_id):
+ *            key = (seed low, seed high), counter = (id low, id high, m, c), c = 0,1,2;
+ *            the 12 words give six 53-bit uniforms U = ((a>>5) 2^26 + (b>>6) + 1/2) 2^-53
+ *            from consecutive word pairs; Box-Muller on (U1,U2), (U3,U4) gives
+ *            g1, g2 (cos, sin of the first pair) and g3 (cos of the second);
+ *            w_m = (g1, g2, g3) / ell, b_m = 2 pi U5;
+ *   solver   V(nu1, nu2) cycles: red ((i+j+k) even) then black Gauss-Seidel sweeps,
+ *            full weighting (1/64)(1,2,1)^3, trilinear prolongation, rediscretised
+ *            coarse operators (k injected), exact solve on the 5^3 grid; cycles repeat
+ *            until ||f - A u||_2 / ||f||_2 over interior nodes <= rtol;
+ *   QoI      Q = mean of u over [0.25, 0.75]^3 by the tensor trapezoid rule.
+ *
+ * Memory layout of every grid array: batch-outermost, then z, y, x with x fastest:
+ *   element (s, z, y, x) at offset ((s * n + z) * n + y) * n + x, n^3 per sample,
+ *   boundary nodes included.
+ *
+ * Conventions:
+ *   - Every call returns an int status: MLMC_OK (0) or a negative MLMC_ERR_* code;
+ *     mlmc_last_error_string() then describes the failure (thread-local).
+ *   - Device buffers passed in are owned by the caller and must stay valid until the
+ *     stream work of the call has completed; the library never frees them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Calls that say "blocking" synchronise `stream` before returning; the others only
+ *     enqueue work, except where host-side outputs are requested.
+ *   - Only one GPU is used: the device current on the calling thread.
+ *   - There is no CPU fallback: without a usable CUDA device every compute call
+ *     returns MLMC_ERR_CUDA.
+ */
+#ifndef MLMC_GB300_H
+#define MLMC_GB300_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define MLMC_OK 0
+#define MLMC_PENDING 1
+#define MLMC_ERR_INVALID (-1)
+#define MLMC_ERR_OOM (-2)
+#define MLMC_ERR_NOT_CONVERGED (-3)
+#define MLMC_ERR_TIMEOUT (-4)
+#define MLMC_ERR_CUDA (-5)
+#define MLMC_ERR_BUSY (-6)
+#define MLMC_ERR_NOT_FOUND (-7)
+
+/* ---- element types of grid buffers ---- */
+#define MLMC_F64 0
+#define MLMC_F32 1
+
+/* ---- solver precision ---- */
+#define MLMC_PREC_F64 0   /* every step in FP64 */
+#define MLMC_PREC_MIXED 1 /* FP32 faces, FP32 V-cycle as correction; FP64 residual and update */
+
+/* Parameters of the lognormal random field (Sec. 3.2; Fourier-feature form above). */
+typedef struct {
+  uint64_t run_seed; /* Philox key */
+  double sigma2;     /* variance of log k, >= 0 */
+  double ell;        /* correlation length, > 0 */
+  int M;             /* number of Fourier features, >= 1 */
+} mlmc_field_cfg;
+
+/* Multigrid parameters. */
+typedef struct {
+  int nu1;        /* pre-smoothing red-black sweeps, 0..8 */
+  int nu2;        /* post-smoothing red-black sweeps, 0..8 */
+  double rtol;    /* stop when ||f - A u|| / ||f|| <= rtol; rtol <= 0 runs exactly max_cycles */
+  int max_cycles; /* 1..1000 */
+  int precision;  /* MLMC_PREC_F64 or MLMC_PREC_MIXED */
+} mg_cfg;
+
+/* Per-sample solve statistics. */
+typedef struct {
+  int cycles;     /* V-cycles performed (mixed: outer refinement steps, one V-cycle each) */
+  double rel_res; /* final ||f - A u||_2 / ||f||_2 over interior nodes (FP64) */
+} mg_stats;
+
+/*
+ * mlmc_field_eval -- the coefficient of the realisations `sample_ids_host[0..batch)`
+ * (Algorithm 1, step 1.a.i: "set up the problem for omega^i") at the n^3 nodes of
+ * one grid. Writes k = exp(log k) into k_out (device, batch * n^3 elements of type
+ * `dtype`: MLMC_F64, or MLMC_F32 = the FP64 value rounded to FP32). The phase is
+ * always evaluated in FP64. sample_ids_host is host memory, read before return.
+ * Errors: MLMC_ERR_INVALID for n not 2^p+1 (5 <= n <= 4097), batch < 1, M < 1,
+ * ell <= 0, sigma2 < 0, unknown dtype or NULL pointers; MLMC_ERR_OOM / _CUDA.
+ * Enqueued on `stream`; the library's scratch is released stream-ordered.
+ */
+int mlmc_field_eval(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n, int dtype,
+                    void* k_out, void* stream);
+
+/*
+ * mg_solve_batch -- solve A u = f for `batch` independent samples on one grid size n
+ * (the deterministic solve of Algorithm 1, step 1.a.ii) by V(nu1,nu2) cycles.
+ *   k  device, FP64, batch * n^3: nodal coefficient (all nodes used, k > 0);
+ *   f  device, FP64, batch * n^3: right-hand side at interior nodes, or NULL for f = 1;
+ *   u  device, FP64, batch * n^3: initial guess in, solution out (boundary set to 0);
+ *   stats_host  host array of `batch` entries, or NULL.
+ * Each sample stops independently when its relative residual reaches cfg->rtol, so a
+ * sample's result does not depend on the other samples of the batch.
+ * Blocking: synchronises `stream`. Returns MLMC_ERR_NOT_CONVERGED if any sample
+ * reached max_cycles without meeting rtol (u is still written); MLMC_ERR_INVALID for
+ * bad sizes / parameters / NULL k or u; MLMC_ERR_OOM; MLMC_ERR_CUDA.
+ */
+int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const double* f, double* u,
+                   mg_stats* stats_host, void* stream);
+
+/* Configuration of an MLMC level computation. */
+typedef struct {
+  mlmc_field_cfg field;
+  mg_cfg mg;
+  int n0;        /* nodes per axis of MLMC level 0 (17 gives 17, 33, 65, ... for levels 0, 1, 2, ...) */
+  int max_batch; /* samples per device batch, 0 = choose from free HBM */
+  void* stream;  /* cudaStream_t, NULL = default */
+} mlmc_cfg;
+
+/* Statistics of one MLMC level (Sec. 2.3: Y-hat_l, s_l^2, C_l). */
+typedef struct {
+  int64_t N;               /* samples */
+  double mean;             /* Y-hat_l = (1/N) sum Y */
+  double var_biased;       /* s_l^2 with 1/N (Sec. 2.3) */
+  double var_unbiased;     /* with 1/(N-1) (0 for N < 2) */
+  double sum;              /* Kahan-compensated sum of Y */
+  double sum_comp;         /* its compensation term */
+  double M2;               /* sum (Y - mean)^2 (Welford / Chan) */
+  double mean_cycles_fine; /* mean V-cycles of the fine solve */
+  double mean_cycles_coarse;
+  int max_cycles_seen;
+  double seconds;          /* wall time of the call */
+  double cost_per_sample;  /* seconds / N, the C_l estimate of Eq. 15 */
+} mlmc_level_stats;
+
+/*
+ * mlmc_level_estimate -- N samples of Y_level with realisation ids first_id ..
+ * first_id + N - 1 (Algorithm 1, step 1.a for one level; step 1.b for `out`).
+ * For level 0, Y = Q_0 on grid n0; for level l >= 1 the fine grid has
+ * n_l = (n0 - 1) 2^l + 1 nodes and the coarse grid n_{l-1}, both solved on the field
+ * of the same id. Y_host, Qf_host, Qc_host: host arrays of N doubles or NULL
+ * (Qc = 0 for level 0). Blocking. Errors as mg_solve_batch; MLMC_ERR_NOT_CONVERGED
+ * if any solve missed rtol (the outputs are still written).
+ */
+int mlmc_level_estimate(const mlmc_cfg* cfg, int level, uint64_t first_id, int N, double* Y_host, double* Qf_host,
+                        double* Qc_host, mlmc_level_stats* out);
+
+/*
+ * mlmc_level_run -- the device-resident form of mlmc_level_estimate: the N realisation
+ * ids are read from DEVICE memory (ids_dev) and the per-sample results are written to
+ * DEVICE arrays of N doubles (Y_dev, Qf_dev, Qc_dev; each may be NULL). `out` (host,
+ * may be NULL) receives the level statistics; they are accumulated on the device in
+ * id order, so they are identical to mlmc_level_estimate's for the same ids. Blocking
+ * (the cycle loop synchronises cfg->stream once per V-cycle to test convergence).
+ * Errors as mlmc_level_estimate; MLMC_ERR_INVALID for ids_dev == NULL.
+ */
+int mlmc_level_run(const mlmc_cfg* cfg, int level, const uint64_t* ids_dev, int N, double* Y_dev, double* Qf_dev,
+                   double* Qc_dev, mlmc_level_stats* out);
+
+/*
+ * Launch accounting (no counterpart in the paper; measurement support). The library
+ * counts every kernel launch per kernel class with the algorithmic bytes and flops of
+ * that launch. After mlmc_profile_enable(1) it also records a CUDA event pair around
+ * each launch on the launching stream. mlmc_profile_get(i, ...) synchronises on the
+ * recorded events and returns class i's name, launches, launches with timing, total
+ * device milliseconds, algorithmic bytes and flops. mlmc_profile_reset() clears all
+ * classes. mlmc_profile_total_launches() counts launches since the last reset.
+ */
+int mlmc_profile_enable(int on);
+int mlmc_profile_reset(void);
+int mlmc_profile_count(void);
+int64_t mlmc_profile_total_launches(void);
+int mlmc_profile_get(int index, char* name, int name_len, int64_t* launches, int64_t* timed_launches, double* ms,
+                     double* bytes, double* flops);
+
+/* Text of the last error on the calling thread ("" if none). Never NULL. */
+const char* mlmc_last_error_string(void);
+
+/* Library version string. */
+const char* mlmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLMC_GB300_H */

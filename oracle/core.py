@@ -10,7 +10,7 @@ import threading
 
 import numpy as np
 
-from .build import build
+from .build import build as _build_oracle
 
 ORC_OK = 0
 ORC_ERR_INVALID = -1
@@ -44,7 +44,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            L = ctypes.CDLL(_build_oracle())
             L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
             L.orc_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
             L.orc_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _dp]

@@ -1,0 +1,19 @@
+"""GB300-native (sm_103a) multilevel Monte Carlo multigrid library.
+
+The hot path -- Philox-seeded lognormal field, batched geometric multigrid solves of
+-div(k grad u) = 1 on the unit cube, and coupled fine/coarse solves on one realisation
+giving Y_l = Q_l - Q_{l-1} (Gmeiner et al., Sec. 2.2, Eq. 8, Algorithm 1) -- runs in
+hand-written CUDA behind the C ABI of include/mlmc.h (libmlmc_gb300.so). This package
+is a thin ctypes binding with the same names; PyTorch provides device memory and
+streams only.
+
+The library is loaded lazily on first use, so that `workloads` (seeded inputs) can be
+imported on machines without a GPU.
+"""
+from ._capi import (  # noqa: F401
+    MLMC_ERR_BUSY, MLMC_ERR_CUDA, MLMC_ERR_INVALID, MLMC_ERR_NOT_CONVERGED, MLMC_ERR_NOT_FOUND, MLMC_ERR_OOM,
+    MLMC_ERR_TIMEOUT, MLMC_F32, MLMC_F64, MLMC_OK, MLMC_PENDING, MLMC_PREC_F64, MLMC_PREC_MIXED, SIGNATURES,
+    FieldCfg, LevelStats, MgCfg, MgStats, MlmcCfg, MlmcError, field_cfg, lib, library_path, make_mlmc_cfg, mg_cfg,
+    mg_solve_batch, mlmc_field_eval, mlmc_level_estimate, mlmc_level_run, profile_enable, profile_read,
+    profile_reset, profile_total_launches,
+)

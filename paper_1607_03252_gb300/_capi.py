@@ -1,0 +1,270 @@
+"""ctypes binding of include/mlmc.h (argument marshalling only).
+
+Every computation runs in libmlmc_gb300.so. Grid arrays are torch CUDA tensors of
+shape (B, n, n, n) (x fastest), passed by data_ptr; streams are torch.cuda.Stream
+objects or None (the current torch stream). There is no CPU fallback: a missing
+library or CUDA device raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MLMC_OK = 0
+MLMC_PENDING = 1
+MLMC_ERR_INVALID = -1
+MLMC_ERR_OOM = -2
+MLMC_ERR_NOT_CONVERGED = -3
+MLMC_ERR_TIMEOUT = -4
+MLMC_ERR_CUDA = -5
+MLMC_ERR_BUSY = -6
+MLMC_ERR_NOT_FOUND = -7
+
+MLMC_F64 = 0
+MLMC_F32 = 1
+MLMC_PREC_F64 = 0
+MLMC_PREC_MIXED = 1
+
+_STATUS_NAMES = {
+    MLMC_ERR_INVALID: "MLMC_ERR_INVALID",
+    MLMC_ERR_OOM: "MLMC_ERR_OOM",
+    MLMC_ERR_NOT_CONVERGED: "MLMC_ERR_NOT_CONVERGED",
+    MLMC_ERR_TIMEOUT: "MLMC_ERR_TIMEOUT",
+    MLMC_ERR_CUDA: "MLMC_ERR_CUDA",
+    MLMC_ERR_BUSY: "MLMC_ERR_BUSY",
+    MLMC_ERR_NOT_FOUND: "MLMC_ERR_NOT_FOUND",
+}
+
+
+class MlmcError(RuntimeError):
+    def __init__(self, status, func, msg):
+        super().__init__("%s returned %s: %s" % (func, _STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class FieldCfg(ctypes.Structure):
+    _fields_ = [("run_seed", ctypes.c_uint64), ("sigma2", ctypes.c_double), ("ell", ctypes.c_double),
+                ("M", ctypes.c_int)]
+
+
+class MgCfg(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("max_cycles", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class MgStats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("rel_res", ctypes.c_double)]
+
+
+class MlmcCfg(ctypes.Structure):
+    _fields_ = [("field", FieldCfg), ("mg", MgCfg), ("n0", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class LevelStats(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("mean", ctypes.c_double), ("var_biased", ctypes.c_double),
+                ("var_unbiased", ctypes.c_double), ("sum", ctypes.c_double), ("sum_comp", ctypes.c_double),
+                ("M2", ctypes.c_double), ("mean_cycles_fine", ctypes.c_double),
+                ("mean_cycles_coarse", ctypes.c_double), ("max_cycles_seen", ctypes.c_int),
+                ("seconds", ctypes.c_double), ("cost_per_sample", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+# name -> (restype, argtypes); the exported symbols of include/mlmc.h
+SIGNATURES = {
+    "mlmc_field_eval": (ctypes.c_int, [ctypes.POINTER(FieldCfg), _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       _vp, _vp]),
+    "mg_solve_batch": (ctypes.c_int, [ctypes.POINTER(MgCfg), ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
+                                      ctypes.POINTER(MgStats), _vp]),
+    "mlmc_level_estimate": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                           _dp, _dp, _dp, ctypes.POINTER(LevelStats)]),
+    "mlmc_level_run": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
+                                      ctypes.POINTER(LevelStats)]),
+    "mlmc_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "mlmc_profile_reset": (ctypes.c_int, []),
+    "mlmc_profile_count": (ctypes.c_int, []),
+    "mlmc_profile_total_launches": (ctypes.c_int64, []),
+    "mlmc_profile_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp]),
+    "mlmc_last_error_string": (ctypes.c_char_p, []),
+    "mlmc_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libmlmc_gb300.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError("libmlmc_gb300.so not built (%s); run paper_1607_03252_gb300/build.py" % path)
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status, func):
+    if status < 0:
+        raise MlmcError(status, func, lib().mlmc_last_error_string().decode())
+    return status
+
+
+def _stream_ptr(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _grid_tensor(t, dtype, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or not t.is_contiguous() or t.dim() != 4 or not (t.shape[1] == t.shape[2] == t.shape[3]):
+        raise ValueError("%s must be a contiguous %s tensor of shape (B, n, n, n)" % (name, dtype))
+    return t
+
+
+def field_cfg(run_seed, sigma2, ell, M):
+    return FieldCfg(int(run_seed), float(sigma2), float(ell), int(M))
+
+
+def mg_cfg(nu1=2, nu2=2, rtol=1e-10, max_cycles=100, precision=MLMC_PREC_F64):
+    return MgCfg(int(nu1), int(nu2), float(rtol), int(max_cycles), int(precision))
+
+
+def mlmc_field_eval(cfg: FieldCfg, sample_ids, k_out, stream=None):
+    """k_out (B, n, n, n) float64 or float32 CUDA tensor <- k of the given sample ids."""
+    import torch
+
+    ids = np.ascontiguousarray(np.asarray(sample_ids, dtype=np.uint64))
+    if k_out.dtype == torch.float64:
+        dt = MLMC_F64
+    elif k_out.dtype == torch.float32:
+        dt = MLMC_F32
+    else:
+        raise ValueError("k_out must be float64 or float32")
+    _grid_tensor(k_out, k_out.dtype, "k_out")
+    if k_out.shape[0] != len(ids):
+        raise ValueError("k_out batch %d != %d ids" % (k_out.shape[0], len(ids)))
+    st = lib().mlmc_field_eval(ctypes.byref(cfg), ids.ctypes.data_as(_u64p), len(ids), k_out.shape[1], dt,
+                               ctypes.c_void_p(k_out.data_ptr()), _stream_ptr(stream))
+    _check(st, "mlmc_field_eval")
+
+
+def mg_solve_batch(cfg: MgCfg, k, u, f=None, stream=None, allow_not_converged=False):
+    """Solve in place into u; returns (cycles int array, rel_res float array, status)."""
+    import torch
+
+    _grid_tensor(k, torch.float64, "k")
+    _grid_tensor(u, torch.float64, "u")
+    if f is not None:
+        _grid_tensor(f, torch.float64, "f")
+    if k.shape != u.shape or (f is not None and f.shape != k.shape):
+        raise ValueError("k, u (and f) must have the same shape")
+    B, n = k.shape[0], k.shape[1]
+    stats = (MgStats * B)()
+    st = lib().mg_solve_batch(ctypes.byref(cfg), B, n, ctypes.c_void_p(k.data_ptr()),
+                              ctypes.c_void_p(f.data_ptr() if f is not None else 0), ctypes.c_void_p(u.data_ptr()),
+                              stats, _stream_ptr(stream))
+    if not (allow_not_converged and st == MLMC_ERR_NOT_CONVERGED):
+        _check(st, "mg_solve_batch")
+    cyc = np.array([s.cycles for s in stats], dtype=np.int32)
+    rel = np.array([s.rel_res for s in stats], dtype=np.float64)
+    return cyc, rel, st
+
+
+def mlmc_level_estimate(cfg: MlmcCfg, level: int, first_id: int, N: int, want_samples=True,
+                        allow_not_converged=False):
+    """Returns (LevelStats, Y, Qf, Qc) with numpy arrays (or None when want_samples is False)."""
+    Y = np.zeros(N) if want_samples else None
+    Qf = np.zeros(N) if want_samples else None
+    Qc = np.zeros(N) if want_samples else None
+    out = LevelStats()
+
+    def p(a):
+        return a.ctypes.data_as(_dp) if a is not None else None
+
+    st = lib().mlmc_level_estimate(ctypes.byref(cfg), int(level), int(first_id), int(N), p(Y), p(Qf), p(Qc),
+                                   ctypes.byref(out))
+    if not (allow_not_converged and st == MLMC_ERR_NOT_CONVERGED):
+        _check(st, "mlmc_level_estimate")
+    return out, Y, Qf, Qc
+
+
+def mlmc_level_run(cfg: MlmcCfg, level: int, ids_dev, Y_dev=None, Qf_dev=None, Qc_dev=None,
+                   allow_not_converged=False):
+    """Device-resident level run: ids_dev is a uint64-compatible CUDA tensor (int64 dtype);
+    outputs are optional float64 CUDA tensors of N entries. Returns LevelStats."""
+    N = int(ids_dev.numel())
+    out = LevelStats()
+
+    def p(t):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+    st = lib().mlmc_level_run(ctypes.byref(cfg), int(level), p(ids_dev), N, p(Y_dev), p(Qf_dev), p(Qc_dev),
+                              ctypes.byref(out))
+    if not (allow_not_converged and st == MLMC_ERR_NOT_CONVERGED):
+        _check(st, "mlmc_level_run")
+    return out
+
+
+def profile_enable(on=True):
+    lib().mlmc_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    lib().mlmc_profile_reset()
+
+
+def profile_total_launches():
+    return int(lib().mlmc_profile_total_launches())
+
+
+def profile_read():
+    """{class: dict(launches, timed, ms, bytes, flops)} (synchronises on recorded events)."""
+    L = lib()
+    res = {}
+    for i in range(L.mlmc_profile_count()):
+        name = ctypes.create_string_buffer(128)
+        la, ti = ctypes.c_int64(), ctypes.c_int64()
+        ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(L.mlmc_profile_get(i, name, 128, ctypes.byref(la), ctypes.byref(ti), ctypes.byref(ms), ctypes.byref(by),
+                                  ctypes.byref(fl)), "mlmc_profile_get")
+        res[name.value.decode()] = dict(launches=la.value, timed=ti.value, ms=ms.value, bytes=by.value,
+                                        flops=fl.value)
+    return res
+
+
+def make_mlmc_cfg(run_seed, sigma2, ell, M, n0=17, nu1=2, nu2=2, rtol=1e-10, max_cycles=100,
+                  precision=MLMC_PREC_F64, max_batch=0, stream=None):
+    sp = ctypes.c_void_p(0)
+    if stream is not None:
+        sp = ctypes.c_void_p(stream.cuda_stream)
+    return MlmcCfg(field_cfg(run_seed, sigma2, ell, M), mg_cfg(nu1, nu2, rtol, max_cycles, precision), int(n0),
+                   int(max_batch), sp)

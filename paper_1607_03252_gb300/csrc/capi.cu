@@ -1,0 +1,431 @@
+// extern "C" entry points of include/mlmc.h, the batched MLMC level pipeline, and
+// error reporting.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "common.cuh"
+#include "field.cuh"
+#include "mg.cuh"
+#include "prof.cuh"
+
+namespace mlmc {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+const char* last_error() { return g_err; }
+
+int DevBuf::alloc(size_t bytes, cudaStream_t st) {
+  release();
+  st_ = st;
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMallocAsync(&p_, bytes, st);
+  if (e != cudaSuccess) {
+    p_ = nullptr;
+    set_error("cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MLMC_ERR_OOM : MLMC_ERR_CUDA;
+  }
+  return MLMC_OK;
+}
+
+void DevBuf::release() {
+  if (p_) cudaFreeAsync(p_, st_);
+  p_ = nullptr;
+}
+
+static int check_mg(const mg_cfg* c) {
+  if (!c) {
+    set_error("mg_cfg is NULL");
+    return MLMC_ERR_INVALID;
+  }
+  if (c->nu1 < 0 || c->nu1 > 8 || c->nu2 < 0 || c->nu2 > 8 || c->nu1 + c->nu2 < 1) {
+    set_error("nu1=%d nu2=%d out of range (0..8 each, at least one sweep)", c->nu1, c->nu2);
+    return MLMC_ERR_INVALID;
+  }
+  if (c->max_cycles < 1 || c->max_cycles > 1000) {
+    set_error("max_cycles=%d out of range 1..1000", c->max_cycles);
+    return MLMC_ERR_INVALID;
+  }
+  if (!(c->rtol < 1.0) || isnan(c->rtol)) {
+    set_error("rtol=%g must be < 1", c->rtol);
+    return MLMC_ERR_INVALID;
+  }
+  if (c->precision != MLMC_PREC_F64 && c->precision != MLMC_PREC_MIXED) {
+    set_error("unknown precision %d", c->precision);
+    return MLMC_ERR_INVALID;
+  }
+  return MLMC_OK;
+}
+
+static int check_field(const mlmc_field_cfg* c) {
+  if (!c) {
+    set_error("mlmc_field_cfg is NULL");
+    return MLMC_ERR_INVALID;
+  }
+  if (c->M < 1 || c->M > 65536 || !(c->ell > 0.0) || !(c->sigma2 >= 0.0) || isinf(c->sigma2) || isinf(c->ell)) {
+    set_error("field cfg invalid: M=%d ell=%g sigma2=%g", c->M, c->ell, c->sigma2);
+    return MLMC_ERR_INVALID;
+  }
+  return MLMC_OK;
+}
+
+static int check_grid(int n, int batch) {
+  if (!valid_grid(n)) {
+    set_error("n=%d is not 2^p+1 with 5 <= n <= 1025", n);
+    return MLMC_ERR_INVALID;
+  }
+  if (batch < 1 || batch > 65535) {
+    set_error("batch=%d out of range 1..65535", batch);
+    return MLMC_ERR_INVALID;
+  }
+  return MLMC_OK;
+}
+
+static int device_ready() {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error("no usable CUDA device: %s", cudaGetErrorString(e));
+    return MLMC_ERR_CUDA;
+  }
+  return MLMC_OK;
+}
+
+// Running statistics of one MLMC level in device memory (Algorithm 1, step 1.b):
+// Kahan-compensated sum and Welford mean / M2 of Y, accumulated sequentially in
+// sample-id order, so the record does not depend on how the samples were batched.
+struct LevelRecord {
+  double N, sum, comp, mean, M2, cyc_f, cyc_c, max_cyc;
+};
+
+// Y = Qf - Qc (Qc NULL: level 0) for b samples, folded into *rec in order.
+__global__ void k_level_stats(const double* __restrict__ Qf, const double* __restrict__ Qc,
+                              const int* __restrict__ cf, const int* __restrict__ cc, int b, double* __restrict__ Y,
+                              LevelRecord* __restrict__ rec) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  LevelRecord r = *rec;
+  for (int i = 0; i < b; ++i) {
+    const double y = Qc ? Qf[i] - Qc[i] : Qf[i];
+    if (Y) Y[i] = y;
+    const double yk = y - r.comp;
+    const double tk = r.sum + yk;
+    r.comp = (tk - r.sum) - yk;
+    r.sum = tk;
+    r.N += 1.0;
+    const double d = y - r.mean;
+    r.mean += d / r.N;
+    r.M2 += d * (y - r.mean);
+    r.cyc_f += cf[i];
+    r.max_cyc = fmax(r.max_cyc, (double)cf[i]);
+    if (cc) {
+      r.cyc_c += cc[i];
+      r.max_cyc = fmax(r.max_cyc, (double)cc[i]);
+    }
+  }
+  *rec = r;
+}
+
+// One batch of an MLMC level: field on the fine grid, fine solve, coarse solve on the
+// same field (injection: the coarse grid's nodes are every other fine node), QoI of both.
+struct LevelBatch {
+  int nf = 0, nc = 0, B = 0, M = 0, prec = 0;
+  DevBuf ids, k0, uf, uc, Q, cyc, rec, scratch;
+  size_t scratch_bytes = 0;
+
+  static size_t scratch_for(int B, int nf, int nc, int M, int prec) {
+    size_t s = field_scratch_bytes(B, M, nf);
+    size_t m = mg_workspace_bytes(B, nf, prec);
+    if (m > s) s = m;
+    if (nc) {
+      m = mg_workspace_bytes(B, nc, prec);
+      if (m > s) s = m;
+    }
+    m = qoi_scratch_bytes(B, nf);
+    if (m > s) s = m;
+    return s;
+  }
+
+  static size_t bytes_for(int B, int nf, int nc, int M, int prec) {
+    return scratch_for(B, nf, nc, M, prec) + (size_t)B * (cube(nf) * 16 + (nc ? cube(nc) * 8 : 0) + 64);
+  }
+
+  int init(int B_, int nf_, int nc_, int M_, int prec_, cudaStream_t st) {
+    B = B_;
+    nf = nf_;
+    nc = nc_;
+    M = M_;
+    prec = prec_;
+    scratch_bytes = scratch_for(B, nf, nc, M, prec);
+    MLMC_TRY(ids.alloc((size_t)B * sizeof(uint64_t), st));
+    MLMC_TRY(k0.alloc((size_t)B * cube(nf) * sizeof(double), st));
+    MLMC_TRY(uf.alloc((size_t)B * cube(nf) * sizeof(double), st));
+    if (nc) MLMC_TRY(uc.alloc((size_t)B * cube(nc) * sizeof(double), st));
+    MLMC_TRY(Q.alloc((size_t)3 * B * sizeof(double), st));
+    MLMC_TRY(cyc.alloc((size_t)2 * B * sizeof(int), st));
+    MLMC_TRY(rec.alloc(sizeof(LevelRecord), st));
+    MLMC_CUDA_TRY(cudaMemsetAsync(rec.get(), 0, sizeof(LevelRecord), st));
+    MLMC_TRY(scratch.alloc(scratch_bytes, st));
+    return MLMC_OK;
+  }
+
+  // b <= B samples with device ids; Qf/Qc/Y: device outputs of b entries (Qc, Y may be
+  // NULL). Folds the batch into the level record.
+  int run(const mlmc_field_cfg& fc, const mg_cfg& mc, const uint64_t* ids_dev, int b, double* Qf, double* Qc,
+          double* Y, int* n_unconv, cudaStream_t st) {
+    MLMC_TRY(field_eval_dev(fc, ids_dev, b, nf, MLMC_F64, k0.get(), scratch.get(), st));
+    MLMC_CUDA_TRY(cudaMemsetAsync(uf.get(), 0, (size_t)b * cube(nf) * sizeof(double), st));
+    MGSolveArgs a;
+    a.k0 = k0.as<double>();
+    a.n_k0 = nf;
+    a.st0 = 1;
+    a.f = nullptr;
+    a.u = uf.as<double>();
+    a.n = nf;
+    a.B = b;
+    a.cfg = mc;
+    int bad = 0;
+    int* cf = cyc.as<int>();
+    int* cc = cyc.as<int>() + B;
+    MLMC_TRY(mg_solve_dev(a, scratch.get(), st, nullptr, nullptr, &bad, cf, nullptr));
+    *n_unconv += bad;
+    MLMC_TRY(qoi_dev(uf.as<double>(), nf, b, Qf, scratch.get(), st));
+    if (nc) {
+      double* qc = Qc ? Qc : Q.as<double>() + B;
+      MLMC_CUDA_TRY(cudaMemsetAsync(uc.get(), 0, (size_t)b * cube(nc) * sizeof(double), st));
+      a.st0 = 2;
+      a.u = uc.as<double>();
+      a.n = nc;
+      bad = 0;
+      MLMC_TRY(mg_solve_dev(a, scratch.get(), st, nullptr, nullptr, &bad, cc, nullptr));
+      *n_unconv += bad;
+      MLMC_TRY(qoi_dev(uc.as<double>(), nc, b, qc, scratch.get(), st));
+      MLMC_LAUNCH("level_stats", b * 24.0, b * 10.0, st,
+                  (k_level_stats<<<1, 32, 0, st>>>(Qf, qc, cf, cc, b, Y, rec.as<LevelRecord>())));
+    } else {
+      if (Qc) MLMC_CUDA_TRY(cudaMemsetAsync(Qc, 0, (size_t)b * sizeof(double), st));
+      MLMC_LAUNCH("level_stats", b * 16.0, b * 10.0, st,
+                  (k_level_stats<<<1, 32, 0, st>>>(Qf, nullptr, cf, nullptr, b, Y, rec.as<LevelRecord>())));
+    }
+    MLMC_CUDA_TRY(cudaGetLastError());
+    return MLMC_OK;
+  }
+
+  int read_record(LevelRecord* r, cudaStream_t st) {
+    MLMC_CUDA_TRY(cudaMemcpyAsync(r, rec.get(), sizeof(LevelRecord), cudaMemcpyDeviceToHost, st));
+    MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+    return MLMC_OK;
+  }
+};
+
+static void fill_stats(const LevelRecord& r, double secs, mlmc_level_stats* out) {
+  if (!out) return;
+  const double N = r.N > 0 ? r.N : 1.0;
+  out->N = (int64_t)r.N;
+  out->mean = r.mean;
+  out->var_biased = r.M2 / N;
+  out->var_unbiased = r.N > 1 ? r.M2 / (r.N - 1.0) : 0.0;
+  out->sum = r.sum;
+  out->sum_comp = r.comp;
+  out->M2 = r.M2;
+  out->mean_cycles_fine = r.cyc_f / N;
+  out->mean_cycles_coarse = r.cyc_c / N;
+  out->max_cycles_seen = (int)r.max_cyc;
+  out->seconds = secs;
+  out->cost_per_sample = secs / N;
+}
+
+static int check_level(const mlmc_cfg* cfg, int level, int N, int* nf, int* nc) {
+  if (!cfg) {
+    set_error("mlmc_cfg is NULL");
+    return MLMC_ERR_INVALID;
+  }
+  MLMC_TRY(check_field(&cfg->field));
+  MLMC_TRY(check_mg(&cfg->mg));
+  if (level < 0 || level > 8 || N < 1 || !valid_grid(cfg->n0) || cfg->max_batch < 0) {
+    set_error("level=%d N=%d n0=%d max_batch=%d invalid", level, N, cfg->n0, cfg->max_batch);
+    return MLMC_ERR_INVALID;
+  }
+  const long long nfl = (long long)(cfg->n0 - 1) * (1LL << level) + 1;
+  if (nfl > 1025 || !valid_grid((int)nfl)) {
+    set_error("level %d gives n=%lld beyond 1025", level, nfl);
+    return MLMC_ERR_INVALID;
+  }
+  *nf = (int)nfl;
+  *nc = level > 0 ? (cfg->n0 - 1) * (1 << (level - 1)) + 1 : 0;
+  return MLMC_OK;
+}
+
+static int choose_batch(const mlmc_cfg* cfg, int N, int nf, int nc, int* B) {
+  int b = cfg->max_batch;
+  if (b == 0) {
+    size_t fr = 0, tot = 0;
+    MLMC_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    const size_t per = LevelBatch::bytes_for(1, nf, nc, cfg->field.M, cfg->mg.precision);
+    size_t fit = (size_t)(0.6 * (double)fr) / (per + 1);
+    if (fit < 1) fit = 1;
+    b = (int)(fit < (size_t)N ? fit : (size_t)N);
+  }
+  if (b > N) b = N;
+  if (b > 65535) b = 65535;
+  *B = b;
+  return MLMC_OK;
+}
+
+}  // namespace mlmc
+
+using namespace mlmc;
+
+extern "C" {
+
+const char* mlmc_last_error_string(void) { return last_error(); }
+
+const char* mlmc_version(void) { return "mlmc-gb300 0.1 (sm_103a)"; }
+
+int mlmc_field_eval(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n, int dtype,
+                    void* k_out, void* stream) {
+  MLMC_TRY(check_field(cfg));
+  MLMC_TRY(check_grid(n, batch));
+  if (!sample_ids_host || !k_out || (dtype != MLMC_F64 && dtype != MLMC_F32)) {
+    set_error("mlmc_field_eval: NULL pointer or unknown dtype %d", dtype);
+    return MLMC_ERR_INVALID;
+  }
+  MLMC_TRY(device_ready());
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf ids, scratch;
+  MLMC_TRY(ids.alloc((size_t)batch * sizeof(uint64_t), st));
+  MLMC_TRY(scratch.alloc(field_scratch_bytes(batch, cfg->M, n), st));
+  MLMC_CUDA_TRY(
+      cudaMemcpyAsync(ids.get(), sample_ids_host, (size_t)batch * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  MLMC_TRY(field_eval_dev(*cfg, ids.as<uint64_t>(), batch, n, dtype, k_out, scratch.get(), st));
+  // the host ids may be reused by the caller as soon as this returns
+  MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+  return MLMC_OK;
+}
+
+int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const double* f, double* u,
+                   mg_stats* stats_host, void* stream) {
+  MLMC_TRY(check_mg(cfg));
+  MLMC_TRY(check_grid(n, batch));
+  if (!k || !u) {
+    set_error("mg_solve_batch: k and u must be device pointers");
+    return MLMC_ERR_INVALID;
+  }
+  MLMC_TRY(device_ready());
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf ws;
+  MLMC_TRY(ws.alloc(mg_workspace_bytes(batch, n, cfg->precision), st));
+  MGSolveArgs a;
+  a.k0 = k;
+  a.n_k0 = n;
+  a.st0 = 1;
+  a.f = f;
+  a.u = u;
+  a.n = n;
+  a.B = batch;
+  a.cfg = *cfg;
+  std::vector<int> cyc(batch);
+  std::vector<double> rel(batch);
+  int bad = 0;
+  MLMC_TRY(mg_solve_dev(a, ws.get(), st, cyc.data(), rel.data(), &bad));
+  if (stats_host)
+    for (int s = 0; s < batch; ++s) {
+      stats_host[s].cycles = cyc[s];
+      stats_host[s].rel_res = rel[s];
+    }
+  ws.release();
+  MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (bad) {
+    set_error("%d of %d samples did not reach rtol=%g in %d cycles", bad, batch, cfg->rtol, cfg->max_cycles);
+    return MLMC_ERR_NOT_CONVERGED;
+  }
+  return MLMC_OK;
+}
+
+int mlmc_level_estimate(const mlmc_cfg* cfg, int level, uint64_t first_id, int N, double* Y_host, double* Qf_host,
+                        double* Qc_host, mlmc_level_stats* out) {
+  int nf = 0, nc = 0;
+  MLMC_TRY(check_level(cfg, level, N, &nf, &nc));
+  MLMC_TRY(device_ready());
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)cfg->stream;
+  int B = 0;
+  MLMC_TRY(choose_batch(cfg, N, nf, nc, &B));
+  LevelBatch lb;
+  MLMC_TRY(lb.init(B, nf, nc, cfg->field.M, cfg->mg.precision, st));
+  std::vector<uint64_t> ids(B);
+  int unconv = 0;
+  double* Qf = lb.Q.as<double>();
+  double* Qc = nc ? lb.Q.as<double>() + B : nullptr;
+  double* Y = lb.Q.as<double>() + 2 * B;
+  for (int s0 = 0; s0 < N; s0 += B) {
+    const int b = (N - s0) < B ? (N - s0) : B;
+    for (int i = 0; i < b; ++i) ids[i] = first_id + (uint64_t)(s0 + i);
+    MLMC_CUDA_TRY(cudaMemcpyAsync(lb.ids.get(), ids.data(), (size_t)b * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    MLMC_TRY(lb.run(cfg->field, cfg->mg, lb.ids.as<uint64_t>(), b, Qf, Qc, Y, &unconv, st));
+    if (Y_host) MLMC_CUDA_TRY(cudaMemcpyAsync(Y_host + s0, Y, b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (Qf_host) MLMC_CUDA_TRY(cudaMemcpyAsync(Qf_host + s0, Qf, b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (Qc_host) {
+      if (Qc)
+        MLMC_CUDA_TRY(cudaMemcpyAsync(Qc_host + s0, Qc, b * sizeof(double), cudaMemcpyDeviceToHost, st));
+      else
+        memset(Qc_host + s0, 0, b * sizeof(double));
+    }
+    MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  LevelRecord r;
+  MLMC_TRY(lb.read_record(&r, st));
+  fill_stats(r, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), out);
+  if (unconv) {
+    set_error("%d solves of level %d did not reach rtol=%g", unconv, level, cfg->mg.rtol);
+    return MLMC_ERR_NOT_CONVERGED;
+  }
+  return MLMC_OK;
+}
+
+int mlmc_level_run(const mlmc_cfg* cfg, int level, const uint64_t* ids_dev, int N, double* Y_dev, double* Qf_dev,
+                   double* Qc_dev, mlmc_level_stats* out) {
+  int nf = 0, nc = 0;
+  MLMC_TRY(check_level(cfg, level, N, &nf, &nc));
+  if (!ids_dev) {
+    set_error("mlmc_level_run: ids_dev is NULL");
+    return MLMC_ERR_INVALID;
+  }
+  MLMC_TRY(device_ready());
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)cfg->stream;
+  int B = 0;
+  MLMC_TRY(choose_batch(cfg, N, nf, nc, &B));
+  LevelBatch lb;
+  MLMC_TRY(lb.init(B, nf, nc, cfg->field.M, cfg->mg.precision, st));
+  int unconv = 0;
+  for (int s0 = 0; s0 < N; s0 += B) {
+    const int b = (N - s0) < B ? (N - s0) : B;
+    double* Qf = Qf_dev ? Qf_dev + s0 : lb.Q.as<double>();
+    double* Qc = Qc_dev ? Qc_dev + s0 : nullptr;
+    double* Y = Y_dev ? Y_dev + s0 : nullptr;
+    MLMC_TRY(lb.run(cfg->field, cfg->mg, ids_dev + s0, b, Qf, Qc, Y, &unconv, st));
+  }
+  if (out) {
+    LevelRecord r;
+    MLMC_TRY(lb.read_record(&r, st));
+    fill_stats(r, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), out);
+  }
+  if (unconv) {
+    set_error("%d solves of level %d did not reach rtol=%g", unconv, level, cfg->mg.rtol);
+    return MLMC_ERR_NOT_CONVERGED;
+  }
+  return MLMC_OK;
+}
+
+}  // extern "C"

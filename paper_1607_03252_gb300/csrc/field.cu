@@ -1,0 +1,204 @@
+// Lognormal random-field evaluation (K1 feature draw, K2 field evaluation).
+//
+// The coefficient of one realisation omega (Algorithm 1, step 1.a.i; lognormal k =
+// exp(Z) of Sec. 3.2) is log k(x) = sigma sqrt(2/M) sum_m cos(w_m . x + b_m).
+// On the structured grid every node is x = (i h, j h, k h), so each term factorises:
+//   cos(w.x + b) = Re( e^{i(w_1 x_i + b)} e^{i w_2 y_j} e^{i w_3 z_k} ).
+// The kernels tabulate the three per-axis phasors once per (sample, feature, index)
+// and evaluate the sum as Re(A_m[i] * Q_m[j,k]) with Q_m[j,k] = B_m[j] C_m[k]:
+// two FP64 FMAs per node and feature instead of one FP64 cos (about 20x fewer FP64
+// instructions; FP64 throughput is the binding resource of this kernel on GB300).
+#include <math.h>
+
+#include "common.cuh"
+#include "field.cuh"
+#include "prof.cuh"
+
+namespace mlmc {
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the two-multiplier S-box with a
+// Weyl key schedule.
+__device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3, uint32_t k0,
+                                         uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t t0 = hi1 ^ c1 ^ k0, t2 = hi0 ^ c3 ^ k1;
+    c0 = t0;
+    c1 = lo1;
+    c2 = t2;
+    c3 = lo0;
+  }
+}
+
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
+  return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+// One thread per (sample, feature): w (B x M x 3), b (B x M).
+__global__ void k_features(const uint64_t* __restrict__ ids, int B, int M, uint64_t seed, double inv_ell,
+                           double* __restrict__ w, double* __restrict__ bph) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)B * M) return;
+  const int s = (int)(t / M), m = (int)(t - (size_t)s * M);
+  const uint64_t id = ids[s];
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  uint32_t wd[12];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    uint32_t c0 = (uint32_t)id, c1 = (uint32_t)(id >> 32), c2 = (uint32_t)m, c3 = (uint32_t)c;
+    philox10(c0, c1, c2, c3, k0, k1);
+    wd[4 * c + 0] = c0;
+    wd[4 * c + 1] = c1;
+    wd[4 * c + 2] = c2;
+    wd[4 * c + 3] = c3;
+  }
+  const double U1 = u53(wd[0], wd[1]), U2 = u53(wd[2], wd[3]);
+  const double U3 = u53(wd[4], wd[5]), U4 = u53(wd[6], wd[7]);
+  const double U5 = u53(wd[8], wd[9]);
+  const double two_pi = 6.283185307179586476925286766559;
+  const double r1 = sqrt(-2.0 * log(U1)), r2 = sqrt(-2.0 * log(U3));
+  const double g1 = r1 * cos(two_pi * U2);
+  const double g2 = r1 * sin(two_pi * U2);
+  const double g3 = r2 * cos(two_pi * U4);
+  w[3 * t + 0] = g1 * inv_ell;
+  w[3 * t + 1] = g2 * inv_ell;
+  w[3 * t + 2] = g3 * inv_ell;
+  bph[t] = two_pi * U5;
+}
+
+// Phasor tables tab[s][axis][m][i] = (cos, sin) of (w_axis x_i (+ b_m on axis 0)).
+__global__ void k_phasors(const double* __restrict__ w, const double* __restrict__ bph, int B, int M, int n,
+                          double h, double2* __restrict__ tab) {
+  const size_t total = (size_t)B * 3 * M * n;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n);
+    const size_t r = t / n;
+    const int m = (int)(r % M);
+    const size_t r2 = r / M;
+    const int axis = (int)(r2 % 3);
+    const int s = (int)(r2 / 3);
+    const size_t f = (size_t)s * M + m;
+    double ph = w[3 * f + axis] * ((double)i * h);
+    if (axis == 0) ph += bph[f];
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    tab[t] = make_double2(cs, sn);
+  }
+}
+
+constexpr int kFieldThreads = 256;
+constexpr int kFieldOut = 8;  // outputs per thread
+
+// One block: sample blockIdx.y, lines [L0, L0 + LT) of the flattened (z, y) index,
+// all n x-values: LT * n <= 2048 outputs. Features are staged MC at a time in shared
+// memory: the x-phasors A[m][0..n) and the line factors Q[m][l] = B[m][y] C[m][z].
+template <typename TOut>
+__global__ void __launch_bounds__(kFieldThreads) k_field(const double2* __restrict__ tab, int M, int n, int LT, int MC,
+                                                          double scale, TOut* __restrict__ kout) {
+  extern __shared__ double2 sm[];
+  double2* sA = sm;
+  double2* sQ = sm + (size_t)MC * n;
+  const int s = blockIdx.y;
+  const size_t n2 = (size_t)n * n;
+  const size_t L0 = (size_t)blockIdx.x * LT;
+  const int nl = (int)((n2 - L0) < (size_t)LT ? (n2 - L0) : (size_t)LT);
+  const int nout = nl * n;
+  const double2* Tx = tab + (size_t)s * 3 * M * n;
+  const double2* Ty = Tx + (size_t)M * n;
+  const double2* Tz = Ty + (size_t)M * n;
+  int xo[kFieldOut], lo[kFieldOut];
+  double acc[kFieldOut];
+#pragma unroll
+  for (int q = 0; q < kFieldOut; ++q) {
+    const int o = threadIdx.x + q * kFieldThreads;
+    lo[q] = o < nout ? o / n : -1;
+    xo[q] = o < nout ? o - lo[q] * n : 0;
+    acc[q] = 0.0;
+  }
+  for (int m0 = 0; m0 < M; m0 += MC) {
+    const int mc = min(MC, M - m0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < mc * n; t += kFieldThreads) sA[t] = Tx[(size_t)m0 * n + t];
+    for (int t = threadIdx.x; t < mc * nl; t += kFieldThreads) {
+      const int mm = t / nl, l = t - mm * nl;
+      const size_t line = L0 + l;
+      const int y = (int)(line % n), z = (int)(line / n);
+      const double2 b = Ty[(size_t)(m0 + mm) * n + y], c = Tz[(size_t)(m0 + mm) * n + z];
+      sQ[mm * LT + l] = make_double2(b.x * c.x - b.y * c.y, b.x * c.y + b.y * c.x);
+    }
+    __syncthreads();
+    for (int mm = 0; mm < mc; ++mm) {
+#pragma unroll
+      for (int q = 0; q < kFieldOut; ++q) {
+        if (lo[q] >= 0) {
+          const double2 a = sA[mm * n + xo[q]];
+          const double2 qq = sQ[mm * LT + lo[q]];
+          acc[q] = fma(a.x, qq.x, fma(-a.y, qq.y, acc[q]));
+        }
+      }
+    }
+  }
+  TOut* out = kout + (size_t)s * n2 * n + L0 * n;
+#pragma unroll
+  for (int q = 0; q < kFieldOut; ++q) {
+    const int o = threadIdx.x + q * kFieldThreads;
+    if (o < nout) out[o] = (TOut)exp(scale * acc[q]);
+  }
+}
+
+static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t field_scratch_bytes(int B, int M, int n) {
+  return a256((size_t)B * M * 3 * sizeof(double)) + a256((size_t)B * M * sizeof(double)) +
+         a256((size_t)B * 3 * M * n * sizeof(double2));
+}
+
+int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, int n, int dtype, void* kout,
+                   void* scratch, cudaStream_t st) {
+  char* p = (char*)scratch;
+  auto carve = [&](size_t bytes) {
+    void* r = p;
+    p += a256(bytes);
+    return r;
+  };
+  double* w = (double*)carve((size_t)B * cfg.M * 3 * sizeof(double));
+  double* bph = (double*)carve((size_t)B * cfg.M * sizeof(double));
+  double2* tab = (double2*)carve((size_t)B * 3 * cfg.M * n * sizeof(double2));
+  const size_t nf = (size_t)B * cfg.M;
+  MLMC_LAUNCH("features", nf * 40.0, nf * 200.0, st,
+              (k_features<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(ids_dev, B, cfg.M, cfg.run_seed,
+                                                                          1.0 / cfg.ell, w, bph)));
+  const double h = 1.0 / (double)(n - 1);
+  const size_t nt = (size_t)B * 3 * cfg.M * n;
+  MLMC_LAUNCH("phasors", nt * 16.0, nt * 40.0, st,
+              (k_phasors<<<blocks_for(nt, 256), 256, 0, st>>>(w, bph, B, cfg.M, n, h, tab)));
+  int LT = 2048 / n;
+  if (LT < 1) LT = 1;
+  if ((size_t)LT > (size_t)n * n) LT = n * n;
+  int MC = 3072 / (n + LT);
+  if (MC > 32) MC = 32;
+  if (MC < 1) MC = 1;
+  const size_t smem = (size_t)MC * (n + LT) * sizeof(double2);
+  dim3 grid((unsigned)(((size_t)n * n + LT - 1) / LT), (unsigned)B);
+  const double scale = sqrt(cfg.sigma2) * sqrt(2.0 / (double)cfg.M);
+  // algorithmic work: 2 FMA (4 flops) per node and feature, plus one complex product
+  // (6 flops) per line and feature; bytes: the tables once and the output once
+  const double flops = (double)B * cube(n) * cfg.M * 4.0 + (double)B * n * n * cfg.M * 6.0;
+  const double bytes = (double)B * cube(n) * (dtype == MLMC_F64 ? 8.0 : 4.0) + (double)nt * 16.0;
+  if (dtype == MLMC_F64)
+    MLMC_LAUNCH("field_f64", bytes, flops, st,
+                (k_field<double><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (double*)kout)));
+  else
+    MLMC_LAUNCH("field_f64", bytes, flops, st,
+                (k_field<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (float*)kout)));
+  MLMC_CUDA_TRY(cudaGetLastError());
+  return MLMC_OK;
+}
+
+}  // namespace mlmc

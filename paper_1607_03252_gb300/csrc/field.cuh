@@ -1,0 +1,18 @@
+// Random-field evaluation on the device (feature draw + separable phasor sum).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mlmc.h"
+
+namespace mlmc {
+
+// Bytes of device scratch field_eval_dev needs for B samples, M features, n nodes per axis.
+size_t field_scratch_bytes(int B, int M, int n);
+
+// k_out[s][z][y][x] = exp(log k) at the n^3 nodes for the B ids in ids_dev (device).
+// dtype MLMC_F64 or MLMC_F32. scratch: field_scratch_bytes(B, M, n) bytes, 256-aligned.
+int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, int n, int dtype, void* k_out,
+                   void* scratch, cudaStream_t st);
+
+}  // namespace mlmc

@@ -1,0 +1,687 @@
+// Batched geometric multigrid: V(nu1, nu2) cycles with red-black Gauss-Seidel, full
+// weighting, trilinear prolongation, rediscretised coarse operators and an exact 5^3
+// solve (the deterministic solver of Algorithm 1, step 1.a.ii, for the model problem
+// of Sec. 3, Eq. 16; the cycle family of Sec. 7.1).
+//
+// Scaled form. With faces K_pq = 2 k_p k_q / (k_p + k_q) and D_p = sum_q K_pq, every
+// grid stores the h^2-scaled operator (A~ u)_p = D_p u_p - sum_q K_pq u_q and the
+// scaled right-hand side g = h^2 f, so
+//   smoothing     u_p <- (g_p + sum_q K_pq u_q) * (1 / D_p)      (6 FMA + 1 MUL)
+//   residual      r~_p = g_p - D_p u_p + sum_q K_pq u_q = h^2 r_p  (7 FMA)
+//   restriction   g_c = h_c^2 FW(r) = 4 FW(r~)
+//   norms         ||r|| / ||f|| = ||r~|| / ||g||.
+// No division runs inside a cycle; faces, D and 1/D are computed once per solve.
+//
+// Precision MLMC_PREC_MIXED: faces are the FP32 harmonic means of the FP32-rounded
+// nodal k, the V-cycle runs entirely in FP32 as a correction solve, and the outer
+// residual g - A~ u (with the FP32 faces read as FP64 values) and the update u += e run
+// in FP64 (iterative refinement): the fixed point is the FP64 solution of the
+// FP32-faced operator.
+//
+// Every kernel skips samples whose `active` flag is 0, so each sample stops at its own
+// cycle count; every per-sample sum is a fixed tree that depends only on n. A sample's
+// result therefore does not depend on the batch it is solved in.
+#include <math.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "mg.cuh"
+#include "prof.cuh"
+
+namespace mlmc {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxLevels = 12;
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Carves 256-byte aligned pieces; with base == nullptr it only measures.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <typename T>
+  T* take(size_t count) {
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += a256(count * sizeof(T));
+    return p;
+  }
+};
+
+__device__ __forceinline__ double harm(double a, double b, double) {
+  return __ddiv_rn(__dmul_rn(2.0 * a, b), __dadd_rn(a, b));
+}
+__device__ __forceinline__ float harm(double a, double b, float) {
+  const float a32 = __double2float_rn(a), b32 = __double2float_rn(b);
+  return __fdiv_rn(__fmul_rn(2.0f * a32, b32), __fadd_rn(a32, b32));
+}
+
+// ---------------------------------------------------------------------------------
+// Operator set-up
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_faces(const double* __restrict__ k0, int n0, int st0, int n, int B, T* __restrict__ Kx,
+                        T* __restrict__ Ky, T* __restrict__ Kz) {
+  const size_t n3 = (size_t)n * n * n, n03 = (size_t)n0 * n0 * n0;
+  const size_t total = (size_t)B * n3;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t s = t / n3, r = t - s * n3;
+    const int z = (int)(r / ((size_t)n * n)), y = (int)((r / n) % n), x = (int)(r % n);
+    const double* kb = k0 + s * n03;
+    const size_t p0 = ((size_t)(st0 * z) * n0 + (size_t)(st0 * y)) * n0 + (size_t)(st0 * x);
+    const double a = kb[p0];
+    Kx[t] = x < n - 1 ? harm(a, kb[p0 + st0], T()) : T(0);
+    Ky[t] = y < n - 1 ? harm(a, kb[p0 + (size_t)st0 * n0], T()) : T(0);
+    Kz[t] = z < n - 1 ? harm(a, kb[p0 + (size_t)st0 * n0 * n0], T()) : T(0);
+  }
+}
+
+// D = sum of the six faces at interior nodes (fixed order), Dinv = 1 / D; 0 on the boundary.
+template <typename T, typename TD>
+__global__ void k_diag(int n, int B, const T* __restrict__ Kx, const T* __restrict__ Ky, const T* __restrict__ Kz,
+                       TD* __restrict__ D, TD* __restrict__ Dinv) {
+  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
+  const size_t total = (size_t)B * n3;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = t % n3;
+    const int z = (int)(r / n2), y = (int)((r / n) % n), x = (int)(r % n);
+    const bool in = x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1;
+    TD d = 0;
+    if (in) {
+      d = (TD)Kx[t - 1];
+      d += (TD)Kx[t];
+      d += (TD)Ky[t - n];
+      d += (TD)Ky[t];
+      d += (TD)Kz[t - n2];
+      d += (TD)Kz[t];
+    }
+    if (D) D[t] = d;
+    if (Dinv) Dinv[t] = in ? (TD)1 / d : (TD)0;
+  }
+}
+
+// Dense 27x27 scaled operator of the 5^3 grid, Cholesky factor, and its inverse
+// (one thread per sample; L is scratch of 27*27 doubles per sample).
+template <typename T>
+__global__ void k_coarse_setup(int B, const T* __restrict__ Kx, const T* __restrict__ Ky, const T* __restrict__ Kz,
+                               double* __restrict__ Lws, double* __restrict__ Ainv) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  const int n = 5, N = 27;
+  const size_t base = (size_t)s * 125;
+  double* A = Lws + (size_t)s * N * N;
+  double* X = Ainv + (size_t)s * N * N;
+  for (int i = 0; i < N * N; ++i) A[i] = 0.0;
+  for (int i = 0; i < N; ++i) {
+    const int x = 1 + i % 3, y = 1 + (i / 3) % 3, z = 1 + i / 9;
+    const size_t p = base + (size_t)(z * n + y) * n + x;
+    const double f[6] = {(double)Kx[p - 1], (double)Kx[p], (double)Ky[p - n], (double)Ky[p], (double)Kz[p - 25],
+                         (double)Kz[p]};
+    const int nb[6] = {x > 1 ? i - 1 : -1, x < 3 ? i + 1 : -1, y > 1 ? i - 3 : -1,
+                       y < 3 ? i + 3 : -1, z > 1 ? i - 9 : -1, z < 3 ? i + 9 : -1};
+    double d = 0.0;
+    for (int q = 0; q < 6; ++q) {
+      d += f[q];
+      if (nb[q] >= 0) A[i * N + nb[q]] = -f[q];
+    }
+    A[i * N + i] = d;
+  }
+  // Cholesky A = L L^T, lower triangle in place
+  for (int j = 0; j < N; ++j) {
+    double d = A[j * N + j];
+    for (int p = 0; p < j; ++p) d -= A[j * N + p] * A[j * N + p];
+    const double ljj = sqrt(d);
+    A[j * N + j] = ljj;
+    for (int i = j + 1; i < N; ++i) {
+      double v = A[i * N + j];
+      for (int p = 0; p < j; ++p) v -= A[i * N + p] * A[j * N + p];
+      A[i * N + j] = v / ljj;
+    }
+  }
+  // columns of the inverse: solve L L^T x = e_c
+  for (int c = 0; c < N; ++c) {
+    double y[27];
+    for (int i = 0; i < N; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int p = 0; p < i; ++p) v -= A[i * N + p] * y[p];
+      y[i] = v / A[i * N + i];
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      double v = y[i];
+      for (int p = i + 1; p < N; ++p) v -= A[p * N + i] * y[p];
+      y[i] = v / A[i * N + i];
+    }
+    for (int i = 0; i < N; ++i) X[i * N + c] = y[i];
+  }
+}
+
+// u = A~^-1 g on the 5^3 grid (interior nodes; boundary untouched).
+template <typename T>
+__global__ void k_coarse_apply(int B, const double* __restrict__ Ainv, const T* __restrict__ g, T* __restrict__ u,
+                               const int* __restrict__ active) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * 27) return;
+  const int s = t / 27, i = t - s * 27;
+  if (active && !active[s]) return;
+  const double* X = Ainv + (size_t)s * 729 + (size_t)i * 27;
+  const size_t base = (size_t)s * 125;
+  double v = 0.0;
+  for (int j = 0; j < 27; ++j) {
+    const int x = 1 + j % 3, y = 1 + (j / 3) % 3, z = 1 + j / 9;
+    v = fma(X[j], (double)g[base + (z * 5 + y) * 5 + x], v);
+  }
+  const int x = 1 + i % 3, y = 1 + (i / 3) % 3, z = 1 + i / 9;
+  u[base + (z * 5 + y) * 5 + x] = (T)v;
+}
+
+// ---------------------------------------------------------------------------------
+// Cycle kernels
+// ---------------------------------------------------------------------------------
+
+// One colour of a red-black sweep: threads enumerate only the nodes of that colour.
+template <typename T>
+__global__ void k_rbgs(int colour, int n, int B, const T* __restrict__ Kx, const T* __restrict__ Ky,
+                       const T* __restrict__ Kz, const T* __restrict__ Dinv, const T* __restrict__ g, T* __restrict__ u,
+                       const int* __restrict__ active) {
+  const int m = n - 2, half = (n - 1) / 2;
+  const size_t rows = (size_t)m * m, n3 = (size_t)n * n * n, n2 = (size_t)n * n;
+  const size_t total = (size_t)B * rows * half;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int xi = (int)(t % half);
+    const size_t rr = t / half;
+    const size_t row = rr % rows, s = rr / rows;
+    if (active && !active[s]) continue;
+    const int y = 1 + (int)(row % m), z = 1 + (int)(row / m);
+    const int x = (((1 + y + z) & 1) == colour ? 1 : 2) + 2 * xi;
+    if (x > n - 2) continue;
+    const size_t p = s * n3 + (size_t)z * n2 + (size_t)y * n + x;
+    T acc = g[p];
+    acc = fma(Kx[p - 1], u[p - 1], acc);
+    acc = fma(Kx[p], u[p + 1], acc);
+    acc = fma(Ky[p - n], u[p - n], acc);
+    acc = fma(Ky[p], u[p + n], acc);
+    acc = fma(Kz[p - n2], u[p - n2], acc);
+    acc = fma(Kz[p], u[p + n2], acc);
+    u[p] = acc * Dinv[p];
+  }
+}
+
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_part[THREADS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) warp_part[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = lane < THREADS / 32 ? warp_part[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+// Blocks per sample of the deterministic reductions (a function of n only).
+inline int reduce_blocks(size_t work) {
+  size_t nb = (work + 4095) / 4096;
+  if (nb < 1) nb = 1;
+  if (nb > 64) nb = 64;
+  return (int)nb;
+}
+
+// r~ = g - D u + sum K u_q on interior nodes (0 on the boundary); optional store of r~
+// (type TR) and per-block partial sums of r~^2. Grid (NB, B).
+template <typename T, typename TD, typename TU, typename TR>
+__global__ void __launch_bounds__(kThreads)
+    k_residual(int n, const T* __restrict__ Kx, const T* __restrict__ Ky, const T* __restrict__ Kz,
+               const TD* __restrict__ D, const TD* __restrict__ g, const TU* __restrict__ u, TR* __restrict__ r,
+               double* __restrict__ partial, const int* __restrict__ active) {
+  const int s = blockIdx.y;
+  if (active && !active[s]) return;
+  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
+  const size_t chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  double sq = 0.0;
+  for (size_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+    const int z = (int)(i / n2), y = (int)((i / n) % n), x = (int)(i % n);
+    const size_t p = (size_t)s * n3 + i;
+    TD rr = 0;
+    if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
+      rr = fma(-D[p], (TD)u[p], g[p]);
+      rr = fma((TD)Kx[p - 1], (TD)u[p - 1], rr);
+      rr = fma((TD)Kx[p], (TD)u[p + 1], rr);
+      rr = fma((TD)Ky[p - n], (TD)u[p - n], rr);
+      rr = fma((TD)Ky[p], (TD)u[p + n], rr);
+      rr = fma((TD)Kz[p - n2], (TD)u[p - n2], rr);
+      rr = fma((TD)Kz[p], (TD)u[p + n2], rr);
+    }
+    if (r) r[p] = (TR)rr;
+    sq += (double)rr * (double)rr;
+  }
+  if (partial) {
+    const double b = block_sum<kThreads>(sq);
+    if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = b;
+  }
+}
+
+// Sum of squares over interior nodes of an FP64 array (initial ||g||). Grid (NB, B).
+__global__ void __launch_bounds__(kThreads) k_sumsq(int n, const double* __restrict__ v, double* __restrict__ partial) {
+  const int s = blockIdx.y;
+  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
+  const size_t chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  double sq = 0.0;
+  for (size_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+    const int z = (int)(i / n2), y = (int)((i / n) % n), x = (int)(i % n);
+    if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
+      const double a = v[(size_t)s * n3 + i];
+      sq += a * a;
+    }
+  }
+  const double b = block_sum<kThreads>(sq);
+  if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = b;
+}
+
+// Per sample: total of the NB partials (fixed order). mode 0: store ||g||^2.
+// mode 1: relative residual, cycle count and active flag after `inc` cycles.
+__global__ void k_norm_update(int B, int NB, const double* __restrict__ partial, double* __restrict__ g2,
+                              double* __restrict__ relres, int* __restrict__ cycles, int* __restrict__ active,
+                              int mode, int inc, double rtol, int max_cycles, int* __restrict__ n_active) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  if (mode == 1 && !active[s]) return;
+  double t = 0.0;
+  for (int b = 0; b < NB; ++b) t += partial[(size_t)s * NB + b];
+  if (mode == 0) {
+    g2[s] = t;
+    return;
+  }
+  const double rel = g2[s] > 0.0 ? sqrt(t / g2[s]) : 0.0;
+  relres[s] = rel;
+  cycles[s] += inc;
+  const int c = cycles[s];
+  const int still = (rtol > 0.0) ? (rel > rtol && c < max_cycles) : (c < max_cycles);
+  active[s] = still;
+  if (still) atomicAdd(n_active, 1);
+}
+
+// g_c = 4 FW(r~) at interior coarse nodes, 0 on the coarse boundary.
+template <typename T>
+__global__ void k_restrict(int nf, int B, const T* __restrict__ r, T* __restrict__ gc, const int* __restrict__ active) {
+  const int nc = (nf + 1) / 2;
+  const size_t nc3 = (size_t)nc * nc * nc, nf3 = (size_t)nf * nf * nf, nf2 = (size_t)nf * nf;
+  const size_t total = (size_t)B * nc3;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t s = t / nc3, q = t - s * nc3;
+    if (active && !active[s]) continue;
+    const int Z = (int)(q / ((size_t)nc * nc)), Y = (int)((q / nc) % nc), X = (int)(q % nc);
+    T v = 0;
+    if (X > 0 && Y > 0 && Z > 0 && X < nc - 1 && Y < nc - 1 && Z < nc - 1) {
+      const T* rb = r + s * nf3 + (size_t)(2 * Z) * nf2 + (size_t)(2 * Y) * nf + 2 * X;
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const T wgt = (T)((2 - abs(dx)) * (2 - abs(dy)) * (2 - abs(dz))) * (T)(1.0 / 16.0);
+            v = fma(wgt, rb[(ptrdiff_t)dz * (ptrdiff_t)nf2 + (ptrdiff_t)dy * nf + dx], v);
+          }
+    }
+    gc[t] = v;
+  }
+}
+
+// u_f += trilinear interpolation of e_c at interior fine nodes.
+template <typename T>
+__global__ void k_prolong(int nf, int B, const T* __restrict__ ec, T* __restrict__ u, const int* __restrict__ active) {
+  const int nc = (nf + 1) / 2;
+  const size_t nc3 = (size_t)nc * nc * nc, nf3 = (size_t)nf * nf * nf, nf2 = (size_t)nf * nf;
+  const size_t total = (size_t)B * nf3;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t s = t / nf3, q = t - s * nf3;
+    if (active && !active[s]) continue;
+    const int z = (int)(q / nf2), y = (int)((q / nf) % nf), x = (int)(q % nf);
+    if (!(x > 0 && y > 0 && z > 0 && x < nf - 1 && y < nf - 1 && z < nf - 1)) continue;
+    const int xa[2] = {x >> 1, (x + 1) >> 1}, ya[2] = {y >> 1, (y + 1) >> 1}, za[2] = {z >> 1, (z + 1) >> 1};
+    const T* eb = ec + s * nc3;
+    T v = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      v += eb[((size_t)za[(c >> 2) & 1] * nc + ya[(c >> 1) & 1]) * nc + xa[c & 1]];
+    u[t] += (T)0.125 * v;
+  }
+}
+
+// g = h^2 f (f == NULL: h^2) on interior nodes, 0 on the boundary; u boundary := 0.
+__global__ void k_prepare(int n, int B, double h2, const double* __restrict__ f, double* __restrict__ g,
+                          double* __restrict__ u) {
+  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
+  const size_t total = (size_t)B * n3;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = t % n3;
+    const int z = (int)(r / n2), y = (int)((r / n) % n), x = (int)(r % n);
+    const bool in = x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1;
+    g[t] = in ? h2 * (f ? f[t] : 1.0) : 0.0;
+    if (!in) u[t] = 0.0;
+  }
+}
+
+// Mixed refinement update u64 += e32 at interior nodes of active samples.
+__global__ void k_update_mixed(int n, int B, const float* __restrict__ e, double* __restrict__ u,
+                               const int* __restrict__ active) {
+  const size_t n3 = (size_t)n * n * n;
+  const size_t total = (size_t)B * n3;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t s = t / n3;
+    if (!active[s]) continue;
+    u[t] += (double)e[t];  // e is zero on the boundary
+  }
+}
+
+// QoI partial sums (trapezoid weights, Kahan in each thread). Grid (NB, B).
+__global__ void __launch_bounds__(kThreads) k_qoi(int n, const double* __restrict__ u, double* __restrict__ partial) {
+  const int s = blockIdx.y;
+  const int lo = (n - 1) / 4, S = (n - 1) / 2 + 1;
+  const size_t S3 = (size_t)S * S * S, n3 = (size_t)n * n * n;
+  const size_t chunk = (S3 + gridDim.x - 1) / gridDim.x;
+  const size_t a = (size_t)blockIdx.x * chunk, b = a + chunk < S3 ? a + chunk : S3;
+  double sum = 0.0, comp = 0.0;
+  for (size_t i = a + threadIdx.x; i < b; i += kThreads) {
+    const int cz = (int)(i / ((size_t)S * S)), cy = (int)((i / S) % S), cx = (int)(i % S);
+    const double w = (cx == 0 || cx == S - 1 ? 0.5 : 1.0) * (cy == 0 || cy == S - 1 ? 0.5 : 1.0) *
+                     (cz == 0 || cz == S - 1 ? 0.5 : 1.0);
+    const double v = w * u[(size_t)s * n3 + ((size_t)(lo + cz) * n + (lo + cy)) * n + (lo + cx)];
+    const double yk = v - comp;
+    const double tk = sum + yk;
+    comp = (tk - sum) - yk;
+    sum = tk;
+  }
+  const double tot = block_sum<kThreads>(sum);
+  if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = tot;
+}
+
+__global__ void k_qoi_final(int B, int NB, double scale, const double* __restrict__ partial, double* __restrict__ Q) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  double t = 0.0;
+  for (int b = 0; b < NB; ++b) t += partial[(size_t)s * NB + b];
+  Q[s] = scale * t;
+}
+
+// ---------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------
+template <typename T>
+struct Level {
+  int n = 0;
+  size_t n3 = 0;
+  T *Kx = nullptr, *Ky = nullptr, *Kz = nullptr, *D = nullptr, *Dinv = nullptr;
+  T *u = nullptr, *g = nullptr, *r = nullptr;
+};
+
+template <typename T>
+struct Hier {
+  int L = 0, B = 0;
+  Level<T> lv[kMaxLevels];
+  double* Ainv = nullptr;
+  double* Lws = nullptr;
+  // level-0 FP64 state
+  double* g64 = nullptr;   // h^2 f
+  double* D64 = nullptr;   // mixed: FP64 diagonal of the FP32 faces
+  double* partial = nullptr;
+  double* g2 = nullptr;
+  double* relres = nullptr;
+  int* cycles = nullptr;
+  int* active = nullptr;
+  int* n_active = nullptr;
+  int NB = 1;
+};
+
+// Lays out the workspace. Level-0 u of FP64 solves is the caller's array (not carved).
+template <typename T>
+void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed) {
+  H.B = B;
+  H.L = hierarchy_depth(n);
+  int nl = n;
+  for (int j = 0; j < H.L; ++j) {
+    Level<T>& v = H.lv[j];
+    v.n = nl;
+    v.n3 = cube(nl);
+    const size_t e = (size_t)B * v.n3;
+    v.Kx = c.template take<T>(e);
+    v.Ky = c.template take<T>(e);
+    v.Kz = c.template take<T>(e);
+    v.D = c.template take<T>(e);
+    v.Dinv = c.template take<T>(e);
+    if (j > 0 || mixed) {
+      v.u = c.template take<T>(e);
+      v.g = c.template take<T>(e);
+    }
+    if (j < H.L - 1) v.r = c.template take<T>(e);
+    nl = (nl + 1) / 2;
+  }
+  const size_t e0 = (size_t)B * cube(n);
+  H.g64 = c.template take<double>(e0);
+  if (mixed) H.D64 = c.template take<double>(e0);
+  H.Ainv = c.template take<double>((size_t)B * 729);
+  H.Lws = c.template take<double>((size_t)B * 729);
+  H.NB = reduce_blocks(cube(n));
+  H.partial = c.template take<double>((size_t)B * H.NB);
+  H.g2 = c.template take<double>(B);
+  H.relres = c.template take<double>(B);
+  H.cycles = c.template take<int>(B);
+  H.active = c.template take<int>(B);
+  H.n_active = c.template take<int>(1);
+}
+
+template <typename T>
+struct Names;
+template <>
+struct Names<double> {
+  static constexpr const char* rbgs = "rbgs_f64";
+  static constexpr const char* residual = "residual_f64";
+  static constexpr const char* restrict_ = "restrict_f64";
+  static constexpr const char* prolong = "prolong_f64";
+  static constexpr const char* faces = "faces_f64";
+  static constexpr const char* diag = "diag_f64";
+  static constexpr const char* coarse = "coarse_apply_f64";
+};
+template <>
+struct Names<float> {
+  static constexpr const char* rbgs = "rbgs_f32";
+  static constexpr const char* residual = "residual_f32";
+  static constexpr const char* restrict_ = "restrict_f32";
+  static constexpr const char* prolong = "prolong_f32";
+  static constexpr const char* faces = "faces_f32";
+  static constexpr const char* diag = "diag_f32";
+  static constexpr const char* coarse = "coarse_apply_f32";
+};
+
+inline double interior(int n) { return (double)(n - 2) * (n - 2) * (n - 2); }
+
+template <typename T>
+void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
+  Level<T>& v = H.lv[j];
+  const int* act = H.active;
+  const int B = H.B;
+  const double W = (double)sizeof(T);
+  if (j == H.L - 1) {
+    MLMC_LAUNCH(Names<T>::coarse, B * (729.0 * 8 + 54 * W), B * 27 * 54.0, st,
+                (k_coarse_apply<T><<<(B * 27 + 127) / 128, 128, 0, st>>>(B, H.Ainv, v.g, v.u, act)));
+    return;
+  }
+  const size_t nsweep = (size_t)B * (v.n - 2) * (v.n - 2) * ((v.n - 1) / 2);
+  const unsigned gs = blocks_for(nsweep, kThreads);
+  // one colour: half of the 7 words per node of a full sweep; 13 flops per updated node
+  const double sweep_bytes = B * interior(v.n) * 3.5 * W, sweep_flops = B * interior(v.n) * 0.5 * 13.0;
+  for (int s = 0; s < nu1; ++s)
+    for (int c = 0; c < 2; ++c)
+      MLMC_LAUNCH(Names<T>::rbgs, sweep_bytes, sweep_flops, st,
+                  (k_rbgs<T><<<gs, kThreads, 0, st>>>(c, v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, act)));
+  dim3 rg(reduce_blocks(v.n3), B);
+  MLMC_LAUNCH(Names<T>::residual, B * interior(v.n) * 7.0 * W, B * interior(v.n) * 14.0, st,
+              (k_residual<T, T, T, T><<<rg, kThreads, 0, st>>>(v.n, v.Kx, v.Ky, v.Kz, v.D, v.g, v.u, v.r, nullptr,
+                                                              act)));
+  Level<T>& w = H.lv[j + 1];
+  MLMC_LAUNCH(Names<T>::restrict_, B * ((double)v.n3 + (double)w.n3) * W, B * interior(w.n) * 54.0, st,
+              (k_restrict<T><<<blocks_for((size_t)B * w.n3, kThreads), kThreads, 0, st>>>(v.n, B, v.r, w.g, act)));
+  cudaMemsetAsync(w.u, 0, (size_t)B * w.n3 * sizeof(T), st);
+  vcycle(H, j + 1, nu1, nu2, st);
+  MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 10.0, st,
+              (k_prolong<T><<<blocks_for((size_t)B * v.n3, kThreads), kThreads, 0, st>>>(v.n, B, w.u, v.u, act)));
+  for (int s = 0; s < nu2; ++s)
+    for (int c = 0; c < 2; ++c)
+      MLMC_LAUNCH(Names<T>::rbgs, sweep_bytes, sweep_flops, st,
+                  (k_rbgs<T><<<gs, kThreads, 0, st>>>(c, v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, act)));
+}
+
+template <typename T>
+int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host, double* relres_host,
+               int* n_unconv, int* cycles_dev, double* relres_dev) {
+  const bool mixed = a.cfg.precision == MLMC_PREC_MIXED;
+  Hier<T> H;
+  Carver c(ws);
+  layout<T>(H, c, a.B, a.n, mixed);
+  const int B = a.B;
+  const double W = (double)sizeof(T);
+  // operators of every level (k injected from k0)
+  int stride = a.st0;
+  for (int j = 0; j < H.L; ++j) {
+    Level<T>& v = H.lv[j];
+    const unsigned gb = blocks_for((size_t)B * v.n3, kThreads);
+    MLMC_LAUNCH(Names<T>::faces, B * (double)v.n3 * (8.0 + 3 * W), B * (double)v.n3 * 12.0, st,
+                (k_faces<T><<<gb, kThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, v.Kx, v.Ky, v.Kz)));
+    MLMC_LAUNCH(Names<T>::diag, B * (double)v.n3 * 5 * W, B * (double)v.n3 * 6.0, st,
+                (k_diag<T, T><<<gb, kThreads, 0, st>>>(v.n, B, v.Kx, v.Ky, v.Kz, v.D, v.Dinv)));
+    stride *= 2;
+  }
+  Level<T>& l0 = H.lv[0];
+  const unsigned g0 = blocks_for((size_t)B * l0.n3, kThreads);
+  if (mixed) {
+    MLMC_LAUNCH("diag64_mixed", B * (double)l0.n3 * (3 * W + 8), B * (double)l0.n3 * 5.0, st,
+                (k_diag<T, double><<<g0, kThreads, 0, st>>>(l0.n, B, l0.Kx, l0.Ky, l0.Kz, H.D64, nullptr)));
+  }
+  Level<T>& lc = H.lv[H.L - 1];
+  MLMC_LAUNCH("coarse_setup", B * 2 * 729.0 * 8, B * 40000.0, st,
+              (k_coarse_setup<T><<<(B + 63) / 64, 64, 0, st>>>(B, lc.Kx, lc.Ky, lc.Kz, H.Lws, H.Ainv)));
+  const double h = 1.0 / (double)(a.n - 1);
+  MLMC_LAUNCH("prepare", B * (double)l0.n3 * (a.f ? 16.0 : 8.0), B * (double)l0.n3, st,
+              (k_prepare<<<g0, kThreads, 0, st>>>(a.n, B, h * h, a.f, H.g64, a.u)));
+  if (!mixed) {
+    l0.u = (T*)a.u;
+    l0.g = (T*)H.g64;
+  }
+  dim3 rg(H.NB, B);
+  const unsigned sb = (B + 127) / 128;
+  MLMC_LAUNCH("norm", B * (double)l0.n3 * 8, B * (double)l0.n3 * 2, st,
+              (k_sumsq<<<rg, kThreads, 0, st>>>(a.n, H.g64, H.partial)));
+  MLMC_LAUNCH("norm_update", B * H.NB * 8.0, B * H.NB * 1.0, st,
+              (k_norm_update<<<sb, 128, 0, st>>>(B, H.NB, H.partial, H.g2, nullptr, nullptr, nullptr, 0, 0, 0.0, 0,
+                                                 nullptr)));
+  MLMC_CUDA_TRY(cudaMemsetAsync(H.cycles, 0, B * sizeof(int), st));
+  {
+    // every sample starts active; the first residual decides
+    std::vector<int> ones(B, 1);
+    MLMC_CUDA_TRY(cudaMemcpyAsync(H.active, ones.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  const double rtol = a.cfg.rtol;
+  const int maxc = a.cfg.max_cycles;
+  auto residual_check = [&](int inc) -> int {
+    MLMC_CUDA_TRY(cudaMemsetAsync(H.n_active, 0, sizeof(int), st));
+    if (mixed) {
+      MLMC_LAUNCH("residual_mixed", B * interior(a.n) * (3 * W + 8 * 3 + W), B * interior(a.n) * 16.0, st,
+                  (k_residual<T, double, double, T><<<rg, kThreads, 0, st>>>(a.n, l0.Kx, l0.Ky, l0.Kz, H.D64, H.g64,
+                                                                             a.u, l0.g, H.partial, H.active)));
+    } else {
+      MLMC_LAUNCH("residual_norm_f64", B * interior(a.n) * 6.0 * 8, B * interior(a.n) * 16.0, st,
+                  (k_residual<T, T, T, T><<<rg, kThreads, 0, st>>>(a.n, l0.Kx, l0.Ky, l0.Kz, l0.D, l0.g, l0.u,
+                                                                  nullptr, H.partial, H.active)));
+    }
+    MLMC_LAUNCH("norm_update", B * H.NB * 8.0, B * H.NB * 1.0, st,
+                (k_norm_update<<<sb, 128, 0, st>>>(B, H.NB, H.partial, H.g2, H.relres, H.cycles, H.active, 1, inc,
+                                                   rtol, maxc, H.n_active)));
+    int na = 0;
+    MLMC_CUDA_TRY(cudaMemcpyAsync(&na, H.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+    return na;
+  };
+  int na = residual_check(0);
+  if (na < 0) return na;
+  while (na > 0) {
+    if (mixed) {
+      MLMC_CUDA_TRY(cudaMemsetAsync(l0.u, 0, (size_t)B * l0.n3 * sizeof(T), st));
+      vcycle<T>(H, 0, a.cfg.nu1, a.cfg.nu2, st);
+      MLMC_LAUNCH("update_mixed", B * (double)l0.n3 * (W + 16), B * (double)l0.n3, st,
+                  (k_update_mixed<<<g0, kThreads, 0, st>>>(a.n, B, (const float*)l0.u, a.u, H.active)));
+    } else {
+      vcycle<T>(H, 0, a.cfg.nu1, a.cfg.nu2, st);
+    }
+    na = residual_check(1);
+    if (na < 0) return na;
+  }
+  MLMC_CUDA_TRY(cudaGetLastError());
+  if (cycles_dev)
+    MLMC_CUDA_TRY(cudaMemcpyAsync(cycles_dev, H.cycles, B * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  if (relres_dev)
+    MLMC_CUDA_TRY(cudaMemcpyAsync(relres_dev, H.relres, B * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  std::vector<int> cyc(B);
+  std::vector<double> rel(B);
+  MLMC_CUDA_TRY(cudaMemcpyAsync(cyc.data(), H.cycles, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+  MLMC_CUDA_TRY(cudaMemcpyAsync(rel.data(), H.relres, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+  MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+  int bad = 0;
+  for (int s = 0; s < B; ++s) {
+    if (cycles_host) cycles_host[s] = cyc[s];
+    if (relres_host) relres_host[s] = rel[s];
+    if (rtol > 0.0 && !(rel[s] <= rtol)) ++bad;
+  }
+  if (n_unconv) *n_unconv = bad;
+  return MLMC_OK;
+}
+
+}  // namespace
+
+size_t mg_workspace_bytes(int B, int n, int precision) {
+  Carver c(nullptr);
+  if (precision == MLMC_PREC_MIXED) {
+    Hier<float> H;
+    layout<float>(H, c, B, n, true);
+  } else {
+    Hier<double> H;
+    layout<double>(H, c, B, n, false);
+  }
+  return c.off;
+}
+
+int mg_solve_dev(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host, double* relres_host,
+                 int* n_unconv, int* cycles_dev, double* relres_dev) {
+  if (a.cfg.precision == MLMC_PREC_MIXED)
+    return solve_impl<float>(a, ws, st, cycles_host, relres_host, n_unconv, cycles_dev, relres_dev);
+  return solve_impl<double>(a, ws, st, cycles_host, relres_host, n_unconv, cycles_dev, relres_dev);
+}
+
+size_t qoi_scratch_bytes(int B, int n) {
+  const int S = (n - 1) / 2 + 1;
+  return a256((size_t)B * reduce_blocks(cube(S)) * sizeof(double));
+}
+
+int qoi_dev(const double* u, int n, int B, double* Q, void* scratch, cudaStream_t st) {
+  const int S = (n - 1) / 2 + 1;
+  const int NB = reduce_blocks(cube(S));
+  double* partial = (double*)scratch;
+  MLMC_LAUNCH("qoi", B * (double)cube(S) * 8, B * (double)cube(S) * 6, st,
+              (k_qoi<<<dim3(NB, B), kThreads, 0, st>>>(n, u, partial)));
+  const double h = 1.0 / (double)(n - 1);
+  MLMC_LAUNCH("qoi_final", B * NB * 8.0, B * NB * 1.0, st,
+              (k_qoi_final<<<(B + 127) / 128, 128, 0, st>>>(B, NB, 8.0 * h * h * h, partial, Q)));
+  MLMC_CUDA_TRY(cudaGetLastError());
+  return MLMC_OK;
+}
+
+}  // namespace mlmc

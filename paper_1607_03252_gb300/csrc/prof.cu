@@ -1,0 +1,147 @@
+// Launch accounting and optional per-launch CUDA-event timing (see prof.cuh).
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "prof.cuh"
+
+namespace mlmc {
+namespace prof {
+
+namespace {
+
+struct Entry {
+  int64_t launches = 0;
+  double bytes = 0.0, flops = 0.0;
+  double ms = 0.0;      // resolved event time
+  int64_t timed = 0;    // launches with resolved events
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
+struct Registry {
+  std::mutex mu;
+  std::map<std::string, Entry> entries;
+  std::vector<std::pair<std::string, cudaEvent_t>> open;  // token -> (class, start event)
+  std::atomic<bool> timing{false};
+  std::atomic<int64_t> total_launches{0};
+};
+
+Registry& reg() {
+  static Registry* r = new Registry();  // never destroyed: events may outlive static teardown
+  return *r;
+}
+
+cudaEvent_t make_event() {
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void resolve(Entry& e) {
+  for (auto& pr : e.pending) {
+    float ms = 0.f;
+    if (pr.first && pr.second && cudaEventSynchronize(pr.second) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+      e.ms += ms;
+      ++e.timed;
+    }
+    if (pr.first) cudaEventDestroy(pr.first);
+    if (pr.second) cudaEventDestroy(pr.second);
+  }
+  e.pending.clear();
+}
+
+}  // namespace
+
+bool timing_enabled() { return reg().timing.load(); }
+
+int begin(const char* cls, double bytes, double flops, cudaStream_t st) {
+  Registry& r = reg();
+  r.total_launches.fetch_add(1);
+  std::lock_guard<std::mutex> lk(r.mu);
+  Entry& e = r.entries[cls];
+  ++e.launches;
+  e.bytes += bytes;
+  e.flops += flops;
+  if (!r.timing.load()) return -1;
+  cudaEvent_t a = make_event();
+  if (a) cudaEventRecord(a, st);
+  r.open.emplace_back(std::string(cls), a);
+  return (int)r.open.size() - 1;
+}
+
+void end(int token, cudaStream_t st) {
+  if (token < 0) return;
+  Registry& r = reg();
+  std::lock_guard<std::mutex> lk(r.mu);
+  if (token >= (int)r.open.size()) return;
+  cudaEvent_t b = make_event();
+  if (b) cudaEventRecord(b, st);
+  auto& o = r.open[token];
+  r.entries[o.first].pending.emplace_back(o.second, b);
+  o.second = nullptr;
+  // tokens are consumed in LIFO order by the RAII scopes
+  while (!r.open.empty() && r.open.back().second == nullptr) r.open.pop_back();
+}
+
+}  // namespace prof
+}  // namespace mlmc
+
+using namespace mlmc;
+
+extern "C" {
+
+int mlmc_profile_enable(int on) {
+  prof::reg().timing.store(on != 0);
+  return MLMC_OK;
+}
+
+int mlmc_profile_reset(void) {
+  auto& r = prof::reg();
+  std::lock_guard<std::mutex> lk(r.mu);
+  for (auto& kv : r.entries) {
+    for (auto& pr : kv.second.pending) {
+      if (pr.first) cudaEventDestroy(pr.first);
+      if (pr.second) cudaEventDestroy(pr.second);
+    }
+  }
+  r.entries.clear();
+  r.total_launches.store(0);
+  return MLMC_OK;
+}
+
+int64_t mlmc_profile_total_launches(void) { return prof::reg().total_launches.load(); }
+
+int mlmc_profile_count(void) {
+  auto& r = prof::reg();
+  std::lock_guard<std::mutex> lk(r.mu);
+  return (int)r.entries.size();
+}
+
+int mlmc_profile_get(int index, char* name, int name_len, int64_t* launches, int64_t* timed_launches, double* ms,
+                     double* bytes, double* flops) {
+  auto& r = prof::reg();
+  std::lock_guard<std::mutex> lk(r.mu);
+  if (index < 0 || index >= (int)r.entries.size() || !name || name_len < 1) {
+    set_error("mlmc_profile_get: index %d out of range or bad buffer", index);
+    return MLMC_ERR_INVALID;
+  }
+  auto it = r.entries.begin();
+  std::advance(it, index);
+  prof::resolve(it->second);
+  strncpy(name, it->first.c_str(), (size_t)name_len - 1);
+  name[name_len - 1] = 0;
+  if (launches) *launches = it->second.launches;
+  if (timed_launches) *timed_launches = it->second.timed;
+  if (ms) *ms = it->second.ms;
+  if (bytes) *bytes = it->second.bytes;
+  if (flops) *flops = it->second.flops;
+  return MLMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+"""CPU checks of the C-ABI library: it builds, loads, and exports every function that
+include/*.h declares; argument validation runs on the host without touching a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_1607_03252_gb300 as mg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+            if not m.group(0).lstrip().startswith(("#", "typedef", "return")):
+                names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_functions()
+    for required in ("mlmc_field_eval", "mg_solve_batch", "mlmc_level_estimate", "mlmc_last_error_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(mg.library_path())
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(mg.SIGNATURES)
+
+
+def test_version_string():
+    assert b"sm_103a" in mg.lib().mlmc_version()
+
+
+def _no_gpu():
+    try:
+        import torch
+
+        return not torch.cuda.is_available()
+    except Exception:
+        return True
+
+
+def test_invalid_grid_rejected_on_host():
+    L = mg.lib()
+    cfg = mg.mg_cfg()
+    st = L.mg_solve_batch(ctypes.byref(cfg), 1, 6, ctypes.c_void_p(8), None, ctypes.c_void_p(8), None, None)
+    assert st == mg.MLMC_ERR_INVALID
+    assert b"2^p+1" in L.mlmc_last_error_string()
+    st = L.mg_solve_batch(ctypes.byref(cfg), 0, 9, ctypes.c_void_p(8), None, ctypes.c_void_p(8), None, None)
+    assert st == mg.MLMC_ERR_INVALID
+    bad = mg.mg_cfg(max_cycles=0)
+    st = L.mg_solve_batch(ctypes.byref(bad), 1, 9, ctypes.c_void_p(8), None, ctypes.c_void_p(8), None, None)
+    assert st == mg.MLMC_ERR_INVALID
+
+
+def test_invalid_field_cfg_rejected_on_host():
+    L = mg.lib()
+    ids = (ctypes.c_uint64 * 1)(1)
+    for cfg in (mg.field_cfg(1, 1.0, 0.0, 8), mg.field_cfg(1, -1.0, 0.3, 8), mg.field_cfg(1, 1.0, 0.3, 0)):
+        st = L.mlmc_field_eval(ctypes.byref(cfg), ids, 1, 9, mg.MLMC_F64, ctypes.c_void_p(8), None)
+        assert st == mg.MLMC_ERR_INVALID
+
+
+@pytest.mark.skipif(not _no_gpu(), reason="checks the no-device path")
+def test_no_cpu_fallback_without_device():
+    L = mg.lib()
+    cfg = mg.make_mlmc_cfg(1, 1.0, 0.3, 8)
+    out = mg.LevelStats()
+    st = L.mlmc_level_estimate(ctypes.byref(cfg), 0, 0, 1, None, None, None, ctypes.byref(out))
+    assert st == mg.MLMC_ERR_CUDA

@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (derived in the design notes):
+  - field k (FP64): 1e-12 relative (the GPU sums separable phasor products, the oracle
+    calls cos per node; both are FP64 and differ by a few ulp per term);
+  - u after a FIXED number of cycles: 1e-10 relative in the max norm (the same
+    algorithm step by step; only rounding order differs);
+  - converged u (rtol 1e-12): 1e-9 relative in the max norm;
+  - Y_l: |dY| <= 1e-9 * max(|Q_l|, |Q_{l-1}|) per sample in FP64, 1e-9 against the
+    oracle's FP32-faced operator in mixed precision (scale-normalised: Y_l << Q_l);
+  - cycle counts equal the oracle's within one cycle (a sample near the threshold may
+    stop one cycle apart).
+"""
+import numpy as np
+import pytest
+
+import paper_1607_03252_gb300 as mg
+from paper_1607_03252_gb300.workloads import RUN_SEED, level_n, random_coefficient, random_rhs, sample_ids
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def gpu_solve(ks, fs=None, precision=mg.MLMC_PREC_F64, rtol=1e-12, max_cycles=100, nu=(2, 2), allow_nc=False):
+    k = to_dev(np.stack(ks))
+    u = torch.zeros_like(k)
+    f = to_dev(np.stack(fs)) if fs is not None else None
+    cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(nu[0], nu[1], rtol, max_cycles, precision), k, u, f,
+                                     allow_not_converged=allow_nc)
+    torch.cuda.synchronize()
+    return u.cpu().numpy(), cyc, rel, st
+
+
+def relmax(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("n,sigma2,ell,M", [(9, 1.0, 0.3, 256), (17, 2.0, 0.1, 256), (33, 1.0, 0.05, 64)])
+def test_field_eval_f64_matches_oracle(orc, n, sigma2, ell, M):
+    ids = sample_ids(2, 5, 3)
+    k = torch.zeros((3, n, n, n), dtype=torch.float64, device=DEV)
+    mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, sigma2, ell, M), ids, k)
+    k = k.cpu().numpy()
+    for s, sid in enumerate(ids):
+        ko = orc.field(RUN_SEED, int(sid), M, sigma2, ell, n)
+        assert relmax(k[s], ko) < 1e-12
+
+
+def test_field_eval_f32_is_rounded_f64(orc):
+    n, ids = 17, sample_ids(1, 0, 2)
+    cfg = mg.field_cfg(RUN_SEED, 1.0, 0.3, 256)
+    k32 = torch.zeros((2, n, n, n), dtype=torch.float32, device=DEV)
+    mg.mlmc_field_eval(cfg, ids, k32)
+    for s, sid in enumerate(ids):
+        ko = orc.field(RUN_SEED, int(sid), 256, 1.0, 0.3, n).astype(np.float32)
+        diff_ulps = np.abs(k32[s].cpu().numpy().view(np.int32) - ko.view(np.int32))
+        assert diff_ulps.max() <= 1
+
+
+def test_field_sigma_zero_is_one():
+    k = torch.zeros((1, 9, 9, 9), dtype=torch.float64, device=DEV)
+    mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, 0.0, 0.3, 16), [7], k)
+    assert torch.all(k == 1.0)
+
+
+@pytest.mark.parametrize("n", [5, 9, 17, 33])
+def test_fixed_cycles_match_oracle_step_by_step(orc, n):
+    """rtol = 0 runs exactly c cycles: any difference in smoother order, transfer or
+    coarse solve shows up at O(1e-3), far above rounding."""
+    ks = [random_coefficient(n, 100 + s, 1.0) for s in range(3)]
+    fs = [random_rhs(n, 200 + s) for s in range(3)]
+    for cycles in (1, 3):
+        u, cyc, rel, st = gpu_solve(ks, fs, rtol=0.0, max_cycles=cycles)
+        assert st == 0 and np.all(cyc == cycles)
+        for s in range(3):
+            uo, _, co, rro, _ = orc.mg_solve(ks[s], fs[s], rtol=0.0, max_cycles=cycles)
+            assert co == cycles
+            assert relmax(u[s], uo) < 1e-10, (n, cycles, s)
+            assert rel[s] == pytest.approx(rro, rel=1e-8)
+
+
+@pytest.mark.parametrize("nu", [(1, 1), (2, 2), (3, 1)])
+def test_fixed_cycles_other_smoothing_counts(orc, nu):
+    n = 17
+    ks = [random_coefficient(n, 7, 1.0)]
+    u, cyc, rel, st = gpu_solve(ks, None, rtol=0.0, max_cycles=2, nu=nu)
+    uo, *_ = orc.mg_solve(ks[0], None, nu1=nu[0], nu2=nu[1], rtol=0.0, max_cycles=2)
+    assert relmax(u[0], uo) < 1e-10
+
+
+@pytest.mark.parametrize("n", [9, 17, 33, 65])
+def test_converged_solution_matches_oracle(orc, n):
+    B = 3 if n < 65 else 2
+    ks = [orc.field(RUN_SEED, int(i), 256, 1.0, 0.3, n) for i in sample_ids(3, 0, B)]
+    u, cyc, rel, st = gpu_solve(ks, rtol=1e-12)
+    assert st == 0 and np.all(rel <= 1e-12)
+    for s in range(B):
+        uo, sto, co, rro, _ = orc.mg_solve(ks[s], None, rtol=1e-12)
+        assert relmax(u[s], uo) < 1e-9
+        assert abs(int(cyc[s]) - co) <= 1
+    # production tolerance: same cycle counts within one
+    u2, cyc2, rel2, st2 = gpu_solve(ks, rtol=1e-10)
+    for s in range(B):
+        _, _, co, _, _ = orc.mg_solve(ks[s], None, rtol=1e-10)
+        assert abs(int(cyc2[s]) - co) <= 1
+
+
+def test_mixed_precision_matches_oracle_mixed(orc):
+    n = 33
+    ks = [orc.field(RUN_SEED, int(i), 256, 2.0, 0.1, n) for i in sample_ids(2, 0, 2)]
+    u, cyc, rel, st = gpu_solve(ks, precision=mg.MLMC_PREC_MIXED, rtol=1e-12)
+    assert st == 0 and np.all(rel <= 1e-12)
+    for s in range(2):
+        um, *_ = orc.mg_solve(ks[s], None, rtol=1e-12, mixed=True)
+        u64, *_ = orc.mg_solve(ks[s], None, rtol=1e-12)
+        assert relmax(u[s], um) < 1e-9
+        # the FP32 faces perturb the operator: stated error against the FP64 solution
+        assert relmax(u[s], u64) < 1e-6
+
+
+def test_batch_composition_does_not_change_results():
+    n = 17
+    ks = [random_coefficient(n, 300 + s, 1.0) for s in range(5)]
+    for prec in (mg.MLMC_PREC_F64, mg.MLMC_PREC_MIXED):
+        ub, cb, rb, _ = gpu_solve(ks, precision=prec, rtol=1e-10)
+        for s in (0, 3):
+            ua, ca, ra, _ = gpu_solve([ks[s]], precision=prec, rtol=1e-10)
+            assert np.array_equal(ua[0], ub[s]) and ca[0] == cb[s]
+
+
+def test_not_converged_status_and_output_written():
+    n = 17
+    ks = [random_coefficient(n, 9, 1.0)]
+    u, cyc, rel, st = gpu_solve(ks, rtol=1e-10, max_cycles=1, allow_nc=True)
+    assert st == mg.MLMC_ERR_NOT_CONVERGED and cyc[0] == 1 and rel[0] > 1e-10
+    assert np.abs(u).max() > 0
+
+
+def test_invalid_arguments_rejected():
+    k = torch.ones((1, 6, 6, 6), dtype=torch.float64, device=DEV)
+    with pytest.raises(mg.MlmcError) as e:
+        mg.mg_solve_batch(mg.mg_cfg(), k, torch.zeros_like(k))
+    assert e.value.status == mg.MLMC_ERR_INVALID
+    k = torch.ones((1, 9, 9, 9), dtype=torch.float64, device=DEV)
+    with pytest.raises(mg.MlmcError):
+        mg.mg_solve_batch(mg.mg_cfg(nu1=0, nu2=0), k, torch.zeros_like(k))
+    with pytest.raises(mg.MlmcError):
+        mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, 1.0, -1.0, 8), [1], k)
+
+
+def _y_tol(Qf, Qc, tol):
+    return tol * np.maximum(np.abs(Qf), np.abs(Qc))
+
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_level_estimate_matches_oracle(orc, level):
+    ids = sample_ids(level, 0, 6)
+    cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.3, 256, n0=17, rtol=1e-12)
+    stats, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
+    ocfg = orc.make_cfg(RUN_SEED, 1.0, 0.3, 256, rtol=1e-12)
+    nf = level_n(level)
+    nc = level_n(level - 1) if level > 0 else 0
+    Yo, Qfo, Qco, cfo, cco, sto = orc.level_batch(ocfg, nf, nc, ids)
+    assert sto == 0
+    assert np.all(np.abs(Y - Yo) <= _y_tol(Qfo, Qco, 1e-9))
+    assert np.all(np.abs(Qf - Qfo) <= 1e-9 * np.abs(Qfo))
+    assert stats.N == len(ids)
+    assert stats.mean == pytest.approx(orc.stats.level_mean(list(Yo)), abs=1e-9 * np.abs(Qfo).mean())
+    if level == 0:
+        assert np.all(Qc == 0)
+
+
+def test_level_estimate_mixed_matches_oracle_mixed(orc):
+    level, ids = 1, sample_ids(1, 10, 4)
+    cfg = mg.make_mlmc_cfg(RUN_SEED, 2.0, 0.1, 256, n0=17, rtol=1e-12, precision=mg.MLMC_PREC_MIXED)
+    _, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
+    Ym, Qfm, Qcm, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 2.0, 0.1, 256, rtol=1e-12, mixed=True), 33, 17, ids)
+    Y64, Qf64, Qc64, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 2.0, 0.1, 256, rtol=1e-12), 33, 17, ids)
+    assert np.all(np.abs(Y - Ym) <= _y_tol(Qfm, Qcm, 1e-9))
+    # stated error of the mixed form against FP64, normalised by Q
+    assert np.all(np.abs(Y - Y64) <= _y_tol(Qf64, Qc64, 1e-6))
+
+
+def test_level_estimate_batch_size_invariant():
+    cfg1 = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.3, 64, n0=17, rtol=1e-10, max_batch=3)
+    cfg2 = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.3, 64, n0=17, rtol=1e-10, max_batch=0)
+    s1, Y1, _, _ = mg.mlmc_level_estimate(cfg1, 1, int(sample_ids(1, 0, 1)[0]), 7)
+    s2, Y2, _, _ = mg.mlmc_level_estimate(cfg2, 1, int(sample_ids(1, 0, 1)[0]), 7)
+    assert np.array_equal(Y1, Y2)
+    assert s1.mean == s2.mean and s1.M2 == s2.M2
+
+
+def test_c2_level3_full_size_sampled(orc):
+    """Level 3 of the 4-level FP64 workload (129^3 fine, 65^3 coarse) in the batch size
+    the benchmark uses (64); three samples of the batch recomputed by the oracle."""
+    ids = sample_ids(3, 0, 64)
+    cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.3, 256, n0=17, rtol=1e-10, max_batch=64)
+    stats, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, 3, int(ids[0]), 64)
+    pick = [0, 31, 63]
+    ocfg = orc.make_cfg(RUN_SEED, 1.0, 0.3, 256, rtol=1e-10)
+    Yo, Qfo, Qco, cfo, cco, sto = orc.level_batch(ocfg, 129, 65, ids[pick])
+    assert sto == 0
+    # rtol 1e-10 on both sides: the stopping points may differ by one cycle (error ~1e-10)
+    assert np.all(np.abs(Y[pick] - Yo) <= _y_tol(Qfo, Qco, 1e-8))
+    assert np.all(np.isfinite(Y)) and stats.max_cycles_seen < 30
