@@ -168,7 +168,7 @@ def reference_arm(args):
 
     cfg, levels, N, single = workload(args.config)
     threads = oracle.max_threads()
-    counts = [max(1, c // 4) for c in oracle_counts(levels, threads)]
+    counts = oracle_counts(levels, threads)
     step_times, all_rates = [], []
     for i in range(args.warmup + args.steps):
         t = time.perf_counter()
