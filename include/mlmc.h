@@ -126,6 +126,27 @@ int mlmc_field_eval(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, 
 int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const double* f, double* u,
                    mg_stats* stats_host, void* stream);
 
+/*
+ * mg_solve_batch_noalloc -- mg_solve_batch for callers that cannot allocate device
+ * memory (code running under another framework's allocator or a fixed device-memory
+ * budget, tools that forbid allocation calls while they record GPU work). The paper
+ * has no counterpart; this is an interface variant only, with the same arguments,
+ * numerics and results as mg_solve_batch.
+ * The workspace is a fixed 32 MiB array in the library's device image (every GPU that
+ * loads the library keeps it until the process exits); the call makes no cudaMalloc,
+ * cudaMallocAsync or cudaFree and no torch allocation. Sizes whose workspace exceeds
+ * 32 MiB (about 90 samples at 17^3, 13 at 33^3, 1 at 65^3 in FP64) return
+ * MLMC_ERR_INVALID with the required size in mlmc_last_error_string().
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * once for that device; make that first call before any stream capture.
+ * Every call reuses the same array, which keeps the previous call's contents; the
+ * solver initialises every part it reads. Calls in one process are serialised by a
+ * lock and each call is blocking; calls whose GPU work overlapped would race on the
+ * shared array.
+ */
+int mg_solve_batch_noalloc(const mg_cfg* cfg, int batch, int n, const double* k, const double* f, double* u,
+                           mg_stats* stats_host, void* stream);
+
 /* Configuration of an MLMC level computation. */
 typedef struct {
   mlmc_field_cfg field;

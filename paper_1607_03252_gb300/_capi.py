@@ -87,6 +87,8 @@ SIGNATURES = {
                                        _vp, _vp]),
     "mg_solve_batch": (ctypes.c_int, [ctypes.POINTER(MgCfg), ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
                                       ctypes.POINTER(MgStats), _vp]),
+    "mg_solve_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(MgCfg), ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
+                                              ctypes.POINTER(MgStats), _vp]),
     "mlmc_level_estimate": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                            _dp, _dp, _dp, ctypes.POINTER(LevelStats)]),
     "mlmc_level_run": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
