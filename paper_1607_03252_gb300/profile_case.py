@@ -1,0 +1,39 @@
+"""One small batched field evaluation + multigrid solve, for kernel profiling.
+
+  python -m paper_1607_03252_gb300.profile_case --n 129 --batch 8 --prec f64 --cycles 2
+
+Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256) for `batch` realisations
+on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0) through the C ABI, so
+that every kernel class launches with the sizes of that grid. Exits 0 on success.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+
+def main(argv=None):
+    import torch
+
+    import paper_1607_03252_gb300 as mg
+    from paper_1607_03252_gb300.workloads import RUN_SEED, sample_ids
+
+    p = argparse.ArgumentParser()
+    p.add_argument("--n", type=int, default=129)
+    p.add_argument("--batch", type=int, default=8)
+    p.add_argument("--prec", choices=["f64", "mixed"], default="f64")
+    p.add_argument("--cycles", type=int, default=2)
+    p.add_argument("--M", type=int, default=256)
+    a = p.parse_args(argv)
+    prec = mg.MLMC_PREC_F64 if a.prec == "f64" else mg.MLMC_PREC_MIXED
+    k = torch.empty((a.batch, a.n, a.n, a.n), dtype=torch.float64, device="cuda")
+    mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, 1.0, 0.3, a.M), sample_ids(3, 0, a.batch), k)
+    u = torch.zeros_like(k)
+    cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 0.0, a.cycles, prec), k, u)
+    torch.cuda.synchronize()
+    print("n=%d batch=%d prec=%s cycles=%s rel_res=%.3e" % (a.n, a.batch, a.prec, cyc.tolist(), rel.max()))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
