@@ -82,18 +82,33 @@ typedef struct {
   int M;             /* number of Fourier features, >= 1 */
 } mlmc_field_cfg;
 
+/* Smoother implementations (all compute the same red-black sweep, bit for bit). */
+#define MLMC_SMOOTH_AUTO 0      /* the tuned choice for the grid size (mlmc_autotune), else a default */
+#define MLMC_SMOOTH_TWO_PASS 1  /* one kernel per colour */
+#define MLMC_SMOOTH_FUSED_32x8 2  /* both colours in one z-marching pass, 32x8 x-y tiles */
+#define MLMC_SMOOTH_FUSED_32x16 3
+#define MLMC_SMOOTH_FUSED_64x8 4
+
+/* Outer iteration around the V-cycle. */
+#define MLMC_ACCEL_NONE 0 /* stationary: repeat V-cycles (FP64), or FP32 V-cycles as corrections of
+                             FP64 residuals (iterative refinement, MLMC_PREC_MIXED) */
+#define MLMC_ACCEL_CG 1   /* flexible preconditioned conjugate gradients, FP64 recurrences, one
+                             V-cycle (FP64 or FP32) as the preconditioner per iteration */
+
 /* Multigrid parameters. */
 typedef struct {
-  int nu1;        /* pre-smoothing red-black sweeps, 0..8 */
+  int nu1;        /* pre-smoothing red-black sweeps, 0..8 (nu1 = nu2 = 0: the tuned count, else 2) */
   int nu2;        /* post-smoothing red-black sweeps, 0..8 */
   double rtol;    /* stop when ||f - A u|| / ||f|| <= rtol; rtol <= 0 runs exactly max_cycles */
   int max_cycles; /* 1..1000 */
   int precision;  /* MLMC_PREC_F64 or MLMC_PREC_MIXED */
+  int smoother;   /* MLMC_SMOOTH_* */
+  int accel;      /* MLMC_ACCEL_NONE or MLMC_ACCEL_CG */
 } mg_cfg;
 
 /* Per-sample solve statistics. */
 typedef struct {
-  int cycles;     /* V-cycles performed (mixed: outer refinement steps, one V-cycle each) */
+  int cycles;     /* V-cycles performed (mixed refinement and CG: outer steps, one V-cycle each) */
   double rel_res; /* final ||f - A u||_2 / ||f||_2 over interior nodes (FP64) */
 } mg_stats;
 
@@ -135,7 +150,7 @@ int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const d
  * The workspace is a fixed 32 MiB array in the library's device image (every GPU that
  * loads the library keeps it until the process exits); the call makes no cudaMalloc,
  * cudaMallocAsync or cudaFree and no torch allocation. Sizes whose workspace exceeds
- * 32 MiB (about 90 samples at 17^3, 13 at 33^3, 1 at 65^3 in FP64) return
+ * 32 MiB (about 85 samples at 17^3, 12 at 33^3, 1 at 65^3 in FP64) return
  * MLMC_ERR_INVALID with the required size in mlmc_last_error_string().
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * once for that device; make that first call before any stream capture.
@@ -211,6 +226,30 @@ int mlmc_profile_count(void);
 int64_t mlmc_profile_total_launches(void);
 int mlmc_profile_get(int index, char* name, int name_len, int64_t* launches, int64_t* timed_launches, double* ms,
                      double* bytes, double* flops);
+
+/* One measurement of mlmc_autotune. */
+typedef struct {
+  int smoother;              /* MLMC_SMOOTH_* */
+  int nu;                    /* sweeps per side, V(nu, nu) */
+  double seconds_per_sample; /* wall time of the level pipeline per sample */
+  double mean_cycles;        /* fine-grid cycles per sample */
+} mlmc_tune_entry;
+
+/*
+ * mlmc_autotune -- picks the smoother implementation (two-pass, or fused with 32x8,
+ * 32x16 or 64x8 tiles) and the sweep count nu in {1,2,3} of V(nu, nu) for MLMC level
+ * `level` under cfg (no counterpart in the paper; the paper fixes its cycle, Sec. 7.1).
+ * Each candidate runs the whole level pipeline once untimed and once timed on
+ * `samples` realisations first_id .. first_id + samples - 1; the fastest by wall time
+ * per sample is stored in a process-wide table for the level's fine grid size and
+ * precision, where MLMC_SMOOTH_AUTO and nu1 = nu2 = 0 find it. Every candidate solves
+ * to the same rtol, so the choice changes speed, not results beyond rtol.
+ * table: host array of table_len entries (may be NULL) for the measurements; *n_entries,
+ * *best_smoother, *best_nu (each may be NULL) receive the count and the choice.
+ * Blocking. Errors as mlmc_level_estimate.
+ */
+int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples, mlmc_tune_entry* table,
+                  int table_len, int* n_entries, int* best_smoother, int* best_nu);
 
 /* Text of the last error on the calling thread ("" if none). Never NULL. */
 const char* mlmc_last_error_string(void);

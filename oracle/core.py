@@ -69,6 +69,8 @@ def lib():
             L.orc_level_batch.argtypes = [ctypes.POINTER(OrcCfg), ctypes.c_int, ctypes.c_int, _u64p, ctypes.c_int,
                                           _dp, _dp, _dp, _ip, _ip, ctypes.c_int]
             L.orc_max_threads.restype = ctypes.c_int
+            L.orc_assemble_csr.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _dp]
+            L.orc_assemble_csr.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -238,3 +240,19 @@ def level_batch(cfg, n_fine, n_coarse, ids, nthreads=0):
 
 def max_threads():
     return lib().orc_max_threads()
+
+
+def assemble_csr(k, mixed=False):
+    """scipy.sparse CSR matrix of the operator on the interior nodes (x fastest)."""
+    import scipy.sparse as sp
+
+    n = k.shape[0]
+    k = _grid(k, n)
+    m = n - 2
+    N = m ** 3
+    indptr = np.zeros(N + 1, dtype=np.int32)
+    indices = np.zeros(7 * N, dtype=np.int32)
+    data = np.zeros(7 * N)
+    nnz = lib().orc_assemble_csr(n, _d(k), int(mixed), indptr.ctypes.data_as(_ip), indices.ctypes.data_as(_ip),
+                                 _d(data))
+    return sp.csr_matrix((data[:nnz], indices[:nnz], indptr), shape=(N, N))

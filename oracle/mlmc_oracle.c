@@ -220,6 +220,40 @@ void orc_apply(int n, const double* kn, const double* u, double* Au, int mixed) 
         Au[IDX(n, i, j, k)] = is_interior(n, i, j, k) ? apply_at(n, kn, u, i, j, k, mixed) : 0.0;
 }
 
+/* The same operator as a sparse matrix over the interior nodes, numbered x fastest
+ * (CSR; at most 7 entries per row, column indices ascending): row p holds
+ * -h^-2 k_pq for each interior neighbour q and h^-2 sum_q k_pq on the diagonal.
+ * indptr has m^3 + 1 entries, indices / data at least 7 m^3 (m = n - 2).
+ * Returns the number of stored entries. */
+int orc_assemble_csr(int n, const double* kn, int mixed, int* indptr, int* indices, double* data) {
+  static const int off[6][3] = {{0, 0, -1}, {0, -1, 0}, {-1, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  int m = n - 2, nnz = 0, row = 0;
+  double h = 1.0 / (double)(n - 1);
+  for (int k = 1; k < n - 1; ++k)
+    for (int j = 1; j < n - 1; ++j)
+      for (int i = 1; i < n - 1; ++i) {
+        size_t p = IDX(n, i, j, k);
+        int prow = (i - 1) + m * ((j - 1) + m * (k - 1));
+        double diag = 0.0;
+        indptr[row++] = nnz;
+        int diag_pos = -1;
+        for (int d = 0; d < 6; ++d) {
+          int qi = i + off[d][0], qj = j + off[d][1], qk = k + off[d][2];
+          double kf = kface(kn[p], kn[IDX(n, qi, qj, qk)], mixed);
+          diag += kf;
+          if (d == 3 && diag_pos < 0) { diag_pos = nnz; indices[nnz] = prow; data[nnz] = 0.0; ++nnz; }
+          if (is_interior(n, qi, qj, qk)) {
+            indices[nnz] = (qi - 1) + m * ((qj - 1) + m * (qk - 1));
+            data[nnz] = -kf / (h * h);
+            ++nnz;
+          }
+        }
+        data[diag_pos] = diag / (h * h);
+      }
+  indptr[row] = nnz;
+  return nnz;
+}
+
 /* r = f - A u on interior nodes, zero on the boundary. f == NULL means f = 1. */
 void orc_residual(int n, const double* kn, const double* f, const double* u, double* r, int mixed) {
   for (int k = 0; k < n; ++k)

@@ -52,9 +52,21 @@ class FieldCfg(ctypes.Structure):
                 ("M", ctypes.c_int)]
 
 
+MLMC_SMOOTH_AUTO = 0
+MLMC_SMOOTH_TWO_PASS = 1
+MLMC_SMOOTH_FUSED_32x8 = 2
+MLMC_SMOOTH_FUSED_32x16 = 3
+MLMC_SMOOTH_FUSED_64x8 = 4
+
+
+MLMC_ACCEL_NONE = 0
+MLMC_ACCEL_CG = 1
+
+
 class MgCfg(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("rtol", ctypes.c_double),
-                ("max_cycles", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("max_cycles", ctypes.c_int), ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("accel", ctypes.c_int)]
 
 
 class MgStats(ctypes.Structure):
@@ -77,6 +89,11 @@ class LevelStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("nu", ctypes.c_int), ("seconds_per_sample", ctypes.c_double),
+                ("mean_cycles", ctypes.c_double)]
+
+
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -93,6 +110,9 @@ SIGNATURES = {
                                            _dp, _dp, _dp, ctypes.POINTER(LevelStats)]),
     "mlmc_level_run": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
                                       ctypes.POINTER(LevelStats)]),
+    "mlmc_autotune": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                     ctypes.POINTER(TuneEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "mlmc_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mlmc_profile_reset": (ctypes.c_int, []),
     "mlmc_profile_count": (ctypes.c_int, []),
@@ -156,8 +176,9 @@ def field_cfg(run_seed, sigma2, ell, M):
     return FieldCfg(int(run_seed), float(sigma2), float(ell), int(M))
 
 
-def mg_cfg(nu1=2, nu2=2, rtol=1e-10, max_cycles=100, precision=MLMC_PREC_F64):
-    return MgCfg(int(nu1), int(nu2), float(rtol), int(max_cycles), int(precision))
+def mg_cfg(nu1=2, nu2=2, rtol=1e-10, max_cycles=100, precision=MLMC_PREC_F64, smoother=MLMC_SMOOTH_AUTO,
+           accel=MLMC_ACCEL_NONE):
+    return MgCfg(int(nu1), int(nu2), float(rtol), int(max_cycles), int(precision), int(smoother), int(accel))
 
 
 def mlmc_field_eval(cfg: FieldCfg, sample_ids, k_out, stream=None):
@@ -236,6 +257,22 @@ def mlmc_level_run(cfg: MlmcCfg, level: int, ids_dev, Y_dev=None, Qf_dev=None, Q
     return out
 
 
+SMOOTHER_NAMES = {MLMC_SMOOTH_TWO_PASS: "two-pass", MLMC_SMOOTH_FUSED_32x8: "fused 32x8",
+                  MLMC_SMOOTH_FUSED_32x16: "fused 32x16", MLMC_SMOOTH_FUSED_64x8: "fused 64x8"}
+
+
+def mlmc_autotune(cfg: MlmcCfg, level: int, first_id: int, samples: int):
+    """Returns (table as list of dicts, best smoother, best nu); the choice is stored
+    for the level's fine grid in the library's tuning table."""
+    tab = (TuneEntry * 12)()
+    cnt, bs, bnu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().mlmc_autotune(ctypes.byref(cfg), int(level), int(first_id), int(samples), tab, 12,
+                               ctypes.byref(cnt), ctypes.byref(bs), ctypes.byref(bnu)), "mlmc_autotune")
+    rows = [dict(smoother=SMOOTHER_NAMES.get(t.smoother, t.smoother), nu=t.nu,
+                 ms_per_sample=1e3 * t.seconds_per_sample, cycles=t.mean_cycles) for t in tab[:cnt.value]]
+    return rows, bs.value, bnu.value
+
+
 def profile_enable(on=True):
     lib().mlmc_profile_enable(1 if on else 0)
 
@@ -264,9 +301,10 @@ def profile_read():
 
 
 def make_mlmc_cfg(run_seed, sigma2, ell, M, n0=17, nu1=2, nu2=2, rtol=1e-10, max_cycles=100,
-                  precision=MLMC_PREC_F64, max_batch=0, stream=None):
+                  precision=MLMC_PREC_F64, max_batch=0, stream=None, smoother=MLMC_SMOOTH_AUTO,
+                  accel=MLMC_ACCEL_NONE):
     sp = ctypes.c_void_p(0)
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream)
-    return MlmcCfg(field_cfg(run_seed, sigma2, ell, M), mg_cfg(nu1, nu2, rtol, max_cycles, precision), int(n0),
-                   int(max_batch), sp)
+    return MlmcCfg(field_cfg(run_seed, sigma2, ell, M),
+                   mg_cfg(nu1, nu2, rtol, max_cycles, precision, smoother, accel), int(n0), int(max_batch), sp)

@@ -12,6 +12,7 @@
 #include "field.cuh"
 #include "mg.cuh"
 #include "prof.cuh"
+#include "tune.cuh"
 
 namespace mlmc {
 
@@ -49,8 +50,12 @@ static int check_mg(const mg_cfg* c) {
     set_error("mg_cfg is NULL");
     return MLMC_ERR_INVALID;
   }
-  if (c->nu1 < 0 || c->nu1 > 8 || c->nu2 < 0 || c->nu2 > 8 || c->nu1 + c->nu2 < 1) {
-    set_error("nu1=%d nu2=%d out of range (0..8 each, at least one sweep)", c->nu1, c->nu2);
+  if (c->nu1 < 0 || c->nu1 > 8 || c->nu2 < 0 || c->nu2 > 8) {
+    set_error("nu1=%d nu2=%d out of range 0..8 (both 0: tuned count)", c->nu1, c->nu2);
+    return MLMC_ERR_INVALID;
+  }
+  if (c->smoother < MLMC_SMOOTH_AUTO || c->smoother > MLMC_SMOOTH_FUSED_64x8) {
+    set_error("unknown smoother %d", c->smoother);
     return MLMC_ERR_INVALID;
   }
   if (c->max_cycles < 1 || c->max_cycles > 1000) {
@@ -63,6 +68,10 @@ static int check_mg(const mg_cfg* c) {
   }
   if (c->precision != MLMC_PREC_F64 && c->precision != MLMC_PREC_MIXED) {
     set_error("unknown precision %d", c->precision);
+    return MLMC_ERR_INVALID;
+  }
+  if (c->accel != MLMC_ACCEL_NONE && c->accel != MLMC_ACCEL_CG) {
+    set_error("unknown accel %d", c->accel);
     return MLMC_ERR_INVALID;
   }
   return MLMC_OK;
@@ -143,12 +152,12 @@ struct LevelBatch {
   DevBuf ids, k0, uf, uc, Q, cyc, rec, scratch;
   size_t scratch_bytes = 0;
 
-  static size_t scratch_for(int B, int nf, int nc, int M, int prec) {
+  static size_t scratch_for(int B, int nf, int nc, int M, int prec, int accel) {
     size_t s = field_scratch_bytes(B, M, nf);
-    size_t m = mg_workspace_bytes(B, nf, prec);
+    size_t m = mg_workspace_bytes(B, nf, prec, accel);
     if (m > s) s = m;
     if (nc) {
-      m = mg_workspace_bytes(B, nc, prec);
+      m = mg_workspace_bytes(B, nc, prec, accel);
       if (m > s) s = m;
     }
     m = qoi_scratch_bytes(B, nf);
@@ -156,17 +165,17 @@ struct LevelBatch {
     return s;
   }
 
-  static size_t bytes_for(int B, int nf, int nc, int M, int prec) {
-    return scratch_for(B, nf, nc, M, prec) + (size_t)B * (cube(nf) * 16 + (nc ? cube(nc) * 8 : 0) + 64);
+  static size_t bytes_for(int B, int nf, int nc, int M, int prec, int accel) {
+    return scratch_for(B, nf, nc, M, prec, accel) + (size_t)B * (cube(nf) * 16 + (nc ? cube(nc) * 8 : 0) + 64);
   }
 
-  int init(int B_, int nf_, int nc_, int M_, int prec_, cudaStream_t st) {
+  int init(int B_, int nf_, int nc_, int M_, int prec_, int accel, cudaStream_t st) {
     B = B_;
     nf = nf_;
     nc = nc_;
     M = M_;
     prec = prec_;
-    scratch_bytes = scratch_for(B, nf, nc, M, prec);
+    scratch_bytes = scratch_for(B, nf, nc, M, prec, accel);
     MLMC_TRY(ids.alloc((size_t)B * sizeof(uint64_t), st));
     MLMC_TRY(k0.alloc((size_t)B * cube(nf) * sizeof(double), st));
     MLMC_TRY(uf.alloc((size_t)B * cube(nf) * sizeof(double), st));
@@ -271,7 +280,7 @@ static int choose_batch(const mlmc_cfg* cfg, int N, int nf, int nc, int* B) {
   if (b == 0) {
     size_t fr = 0, tot = 0;
     MLMC_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-    const size_t per = LevelBatch::bytes_for(1, nf, nc, cfg->field.M, cfg->mg.precision);
+    const size_t per = LevelBatch::bytes_for(1, nf, nc, cfg->field.M, cfg->mg.precision, cfg->mg.accel);
     size_t fit = (size_t)(0.6 * (double)fr) / (per + 1);
     if (fit < 1) fit = 1;
     b = (int)(fit < (size_t)N ? fit : (size_t)N);
@@ -324,7 +333,7 @@ int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const d
   MLMC_TRY(device_ready());
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf ws;
-  MLMC_TRY(ws.alloc(mg_workspace_bytes(batch, n, cfg->precision), st));
+  MLMC_TRY(ws.alloc(mg_workspace_bytes(batch, n, cfg->precision, cfg->accel), st));
   MGSolveArgs a;
   a.k0 = k;
   a.n_k0 = n;
@@ -362,7 +371,7 @@ int mlmc_level_estimate(const mlmc_cfg* cfg, int level, uint64_t first_id, int N
   int B = 0;
   MLMC_TRY(choose_batch(cfg, N, nf, nc, &B));
   LevelBatch lb;
-  MLMC_TRY(lb.init(B, nf, nc, cfg->field.M, cfg->mg.precision, st));
+  MLMC_TRY(lb.init(B, nf, nc, cfg->field.M, cfg->mg.precision, cfg->mg.accel, st));
   std::vector<uint64_t> ids(B);
   int unconv = 0;
   double* Qf = lb.Q.as<double>();
@@ -407,7 +416,7 @@ int mlmc_level_run(const mlmc_cfg* cfg, int level, const uint64_t* ids_dev, int 
   int B = 0;
   MLMC_TRY(choose_batch(cfg, N, nf, nc, &B));
   LevelBatch lb;
-  MLMC_TRY(lb.init(B, nf, nc, cfg->field.M, cfg->mg.precision, st));
+  MLMC_TRY(lb.init(B, nf, nc, cfg->field.M, cfg->mg.precision, cfg->mg.accel, st));
   int unconv = 0;
   for (int s0 = 0; s0 < N; s0 += B) {
     const int b = (N - s0) < B ? (N - s0) : B;
@@ -425,6 +434,70 @@ int mlmc_level_run(const mlmc_cfg* cfg, int level, const uint64_t* ids_dev, int 
     set_error("%d solves of level %d did not reach rtol=%g", unconv, level, cfg->mg.rtol);
     return MLMC_ERR_NOT_CONVERGED;
   }
+  return MLMC_OK;
+}
+
+int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples, mlmc_tune_entry* table,
+                  int table_len, int* n_entries, int* best_smoother, int* best_nu) {
+  int nf = 0, nc = 0;
+  MLMC_TRY(check_level(cfg, level, samples, &nf, &nc));
+  if (table_len < 0 || (table_len > 0 && !table)) {
+    set_error("mlmc_autotune: bad table");
+    return MLMC_ERR_INVALID;
+  }
+  MLMC_TRY(device_ready());
+  cudaStream_t st = (cudaStream_t)cfg->stream;
+  int B = 0;
+  MLMC_TRY(choose_batch(cfg, samples, nf, nc, &B));
+  const int smoothers[4] = {MLMC_SMOOTH_TWO_PASS, MLMC_SMOOTH_FUSED_32x8, MLMC_SMOOTH_FUSED_32x16,
+                            MLMC_SMOOTH_FUSED_64x8};
+  std::vector<uint64_t> ids(samples);
+  for (int i = 0; i < samples; ++i) ids[i] = first_id + (uint64_t)i;
+  int count = 0, bs = MLMC_SMOOTH_TWO_PASS, bnu = 2;
+  double best = 1e300;
+  for (int nu = 1; nu <= 3; ++nu)
+    for (int si = 0; si < 4; ++si) {
+      mg_cfg mc = cfg->mg;
+      mc.smoother = smoothers[si];
+      mc.nu1 = nu;
+      mc.nu2 = nu;
+      double secs = 0.0;
+      LevelRecord r{};
+      for (int rep = 0; rep < 2; ++rep) {
+        LevelBatch lb;
+        MLMC_TRY(lb.init(B, nf, nc, cfg->field.M, mc.precision, mc.accel, st));
+        MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+        const auto t0 = std::chrono::steady_clock::now();
+        int unconv = 0;
+        for (int s0 = 0; s0 < samples; s0 += B) {
+          const int b = (samples - s0) < B ? (samples - s0) : B;
+          MLMC_CUDA_TRY(cudaMemcpyAsync(lb.ids.get(), ids.data() + s0, (size_t)b * sizeof(uint64_t),
+                                        cudaMemcpyHostToDevice, st));
+          MLMC_TRY(lb.run(cfg->field, mc, lb.ids.as<uint64_t>(), b, lb.Q.as<double>(),
+                          nc ? lb.Q.as<double>() + B : nullptr, nullptr, &unconv, st));
+        }
+        MLMC_TRY(lb.read_record(&r, st));
+        secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (unconv) secs = 1e300;  // a candidate that misses rtol never wins
+      }
+      const double per = secs / samples;
+      if (count < table_len) {
+        table[count].smoother = smoothers[si];
+        table[count].nu = nu;
+        table[count].seconds_per_sample = per;
+        table[count].mean_cycles = r.N > 0 ? r.cyc_f / r.N : 0.0;
+      }
+      ++count;
+      if (per < best) {
+        best = per;
+        bs = smoothers[si];
+        bnu = nu;
+      }
+    }
+  tune_store(nf, cfg->mg.precision, bs, bnu);
+  if (n_entries) *n_entries = count;
+  if (best_smoother) *best_smoother = bs;
+  if (best_nu) *best_nu = bnu;
   return MLMC_OK;
 }
 

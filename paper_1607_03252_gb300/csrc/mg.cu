@@ -29,6 +29,8 @@
 #include "common.cuh"
 #include "mg.cuh"
 #include "prof.cuh"
+#include "smooth.cuh"
+#include "tune.cuh"
 
 namespace mlmc {
 
@@ -414,6 +416,137 @@ __global__ void k_qoi_final(int B, int NB, double scale, const double* __restric
 }
 
 // ---------------------------------------------------------------------------------
+// Flexible preconditioned conjugate gradients (FP64 recurrences; the V-cycle is the
+// preconditioner). All vectors are FP64 on the finest grid; per-sample scalars.
+// ---------------------------------------------------------------------------------
+
+// q = A~ p on interior nodes (0 on the boundary); partial sums of p.q. Grid (NB, B).
+template <typename TK, typename TD>
+__global__ void __launch_bounds__(kThreads)
+    k_apply_dot(int n, const TK* __restrict__ Kx, const TK* __restrict__ Ky, const TK* __restrict__ Kz,
+                const TD* __restrict__ D, const double* __restrict__ p, double* __restrict__ q,
+                double* __restrict__ partial, const int* __restrict__ active) {
+  const int s = blockIdx.y;
+  if (!active[s]) return;
+  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
+  const size_t chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  double acc = 0.0;
+  for (size_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+    const int z = (int)(i / n2), y = (int)((i / n) % n), x = (int)(i % n);
+    const size_t t = (size_t)s * n3 + i;
+    double v = 0.0;
+    if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
+      v = (double)D[t] * p[t];
+      v = fma(-(double)Kx[t - 1], p[t - 1], v);
+      v = fma(-(double)Kx[t], p[t + 1], v);
+      v = fma(-(double)Ky[t - n], p[t - n], v);
+      v = fma(-(double)Ky[t], p[t + n], v);
+      v = fma(-(double)Kz[t - n2], p[t - n2], v);
+      v = fma(-(double)Kz[t], p[t + n2], v);
+      acc = fma(p[t], v, acc);
+    }
+    q[t] = v;
+  }
+  const double b = block_sum<kThreads>(acc);
+  if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = b;
+}
+
+// x += alpha p, r -= alpha q; partials of r.r and r.z (z: the previous preconditioned
+// residual); optionally r32 = (float) r for an FP32 preconditioner. Grid (NB, B).
+__global__ void __launch_bounds__(kThreads)
+    k_cg_update(int n, const double* __restrict__ alpha, const double* __restrict__ p,
+                const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
+                const double* __restrict__ z, float* __restrict__ r32, double* __restrict__ part_rr,
+                double* __restrict__ part_rz, const int* __restrict__ active) {
+  const int s = blockIdx.y;
+  if (!active[s]) return;
+  const size_t n3 = (size_t)n * n * n;
+  const size_t chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  const double a = alpha[s];
+  double rr = 0.0, rz = 0.0;
+  for (size_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+    const size_t t = (size_t)s * n3 + i;
+    x[t] = fma(a, p[t], x[t]);
+    const double rn = fma(-a, q[t], r[t]);  // q and p vanish on the boundary
+    r[t] = rn;
+    if (r32) r32[t] = (float)rn;
+    rr = fma(rn, rn, rr);
+    rz = fma(rn, z[t], rz);
+  }
+  const double b1 = block_sum<kThreads>(rr);
+  if (threadIdx.x == 0) part_rr[(size_t)s * gridDim.x + blockIdx.x] = b1;
+  const double b2 = block_sum<kThreads>(rz);
+  if (threadIdx.x == 0) part_rz[(size_t)s * gridDim.x + blockIdx.x] = b2;
+}
+
+// z = (double) e (when e32 is given) and partial sums of r.z. Grid (NB, B).
+__global__ void __launch_bounds__(kThreads)
+    k_precond_dot(int n, const float* __restrict__ e32, double* __restrict__ z, const double* __restrict__ r,
+                  double* __restrict__ partial, const int* __restrict__ active) {
+  const int s = blockIdx.y;
+  if (!active[s]) return;
+  const size_t n3 = (size_t)n * n * n;
+  const size_t chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  double acc = 0.0;
+  for (size_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+    const size_t t = (size_t)s * n3 + i;
+    double zv;
+    if (e32) {
+      zv = (double)e32[t];
+      z[t] = zv;
+    } else {
+      zv = z[t];
+    }
+    acc = fma(r[t], zv, acc);
+  }
+  const double b = block_sum<kThreads>(acc);
+  if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = b;
+}
+
+// p = z + beta p (beta = 0: p = z).
+__global__ void k_p_update(int n, int B, const double* __restrict__ beta, const double* __restrict__ z,
+                           double* __restrict__ p, const int* __restrict__ active) {
+  const size_t n3 = (size_t)n * n * n, total = (size_t)B * n3;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t s = t / n3;
+    if (!active[s]) continue;
+    p[t] = beta ? fma(beta[s], p[t], z[t]) : z[t];
+  }
+}
+
+__global__ void k_to_f32(size_t total, const double* __restrict__ a, float* __restrict__ b) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x)
+    b[t] = (float)a[t];
+}
+
+// Per-sample CG scalars from block partials (fixed order).
+//   mode 0: rz = sum(part)                         (after the first preconditioning)
+//   mode 1: alpha = rz / sum(part)                 (part = p.q)
+//   mode 2: beta = (sum(part) - rzo) / rz, rz = sum (part = r.z_new; flexible beta)
+//   mode 3: rzo = sum(part)                        (part = r_new.z_old)
+__global__ void k_cg_scalar(int B, int NB, int mode, const double* __restrict__ part, double* __restrict__ rz,
+                            double* __restrict__ rzo, double* __restrict__ alpha, double* __restrict__ beta,
+                            const int* __restrict__ active) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B || !active[s]) return;
+  double t = 0.0;
+  for (int b = 0; b < NB; ++b) t += part[(size_t)s * NB + b];
+  if (mode == 0) {
+    rz[s] = t;
+  } else if (mode == 1) {
+    alpha[s] = t != 0.0 ? rz[s] / t : 0.0;
+  } else if (mode == 2) {
+    beta[s] = rz[s] != 0.0 ? (t - rzo[s]) / rz[s] : 0.0;
+    rz[s] = t;
+  } else {
+    rzo[s] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------
 template <typename T>
@@ -422,6 +555,7 @@ struct Level {
   size_t n3 = 0;
   T *Kx = nullptr, *Ky = nullptr, *Kz = nullptr, *D = nullptr, *Dinv = nullptr;
   T *u = nullptr, *g = nullptr, *r = nullptr;
+  T* u2 = nullptr;  // spare iterate for the fused (double-buffered) sweep
 };
 
 template <typename T>
@@ -440,11 +574,16 @@ struct Hier {
   int* active = nullptr;
   int* n_active = nullptr;
   int NB = 1;
+  // flexible PCG (FP64 vectors on the finest grid) and per-sample scalars
+  double *R = nullptr, *P = nullptr, *Q = nullptr, *Z = nullptr;
+  double *part2 = nullptr, *rz = nullptr, *rzo = nullptr, *alpha = nullptr, *beta = nullptr;
+  int tile[kMaxLevels] = {};      // fused-sweep tile shape per level
+  bool fused[kMaxLevels] = {};    // fused (one pass) or two-pass smoother per level
 };
 
 // Lays out the workspace. Level-0 u of FP64 solves is the caller's array (not carved).
 template <typename T>
-void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed) {
+void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed, bool cg) {
   H.B = B;
   H.L = hierarchy_depth(n);
   int nl = n;
@@ -458,10 +597,11 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed) {
     v.Kz = c.template take<T>(e);
     v.D = c.template take<T>(e);
     v.Dinv = c.template take<T>(e);
-    if (j > 0 || mixed) {
+    if (j > 0 || mixed || cg) {
       v.u = c.template take<T>(e);
-      v.g = c.template take<T>(e);
+      if (j > 0 || mixed) v.g = c.template take<T>(e);  // FP64 CG: the level-0 rhs is R
     }
+    if (j < H.L - 1) v.u2 = c.template take<T>(e);
     if (j < H.L - 1) v.r = c.template take<T>(e);
     nl = (nl + 1) / 2;
   }
@@ -477,6 +617,17 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed) {
   H.cycles = c.template take<int>(B);
   H.active = c.template take<int>(B);
   H.n_active = c.template take<int>(1);
+  if (cg) {
+    H.R = c.template take<double>(e0);
+    H.P = c.template take<double>(e0);
+    H.Q = c.template take<double>(e0);
+    if (mixed) H.Z = c.template take<double>(e0);
+    H.part2 = c.template take<double>((size_t)B * H.NB);
+    H.rz = c.template take<double>(B);
+    H.rzo = c.template take<double>(B);
+    H.alpha = c.template take<double>(B);
+    H.beta = c.template take<double>(B);
+  }
 }
 
 template <typename T>
@@ -519,10 +670,21 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   const unsigned gs = blocks_for(nsweep, kThreads);
   // one colour: half of the 7 words per node of a full sweep; 13 flops per updated node
   const double sweep_bytes = B * interior(v.n) * 3.5 * W, sweep_flops = B * interior(v.n) * 0.5 * 13.0;
-  for (int s = 0; s < nu1; ++s)
-    for (int c = 0; c < 2; ++c)
-      MLMC_LAUNCH(Names<T>::rbgs, sweep_bytes, sweep_flops, st,
-                  (k_rbgs<T><<<gs, kThreads, 0, st>>>(c, v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, act)));
+  auto smooth = [&](int sweeps) {
+    for (int s = 0; s < sweeps; ++s) {
+      if (H.fused[j]) {
+        rbgs_fused_sweep<T>(H.tile[j], v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, v.u2, act, st);
+        T* t = v.u;
+        v.u = v.u2;
+        v.u2 = t;
+      } else {
+        for (int c = 0; c < 2; ++c)
+          MLMC_LAUNCH(Names<T>::rbgs, sweep_bytes, sweep_flops, st,
+                      (k_rbgs<T><<<gs, kThreads, 0, st>>>(c, v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, act)));
+      }
+    }
+  };
+  smooth(nu1);
   dim3 rg(reduce_blocks(v.n3), B);
   MLMC_LAUNCH(Names<T>::residual, B * interior(v.n) * 7.0 * W, B * interior(v.n) * 14.0, st,
               (k_residual<T, T, T, T><<<rg, kThreads, 0, st>>>(v.n, v.Kx, v.Ky, v.Kz, v.D, v.g, v.u, v.r, nullptr,
@@ -534,19 +696,89 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   vcycle(H, j + 1, nu1, nu2, st);
   MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 10.0, st,
               (k_prolong<T><<<blocks_for((size_t)B * v.n3, kThreads), kThreads, 0, st>>>(v.n, B, w.u, v.u, act)));
-  for (int s = 0; s < nu2; ++s)
-    for (int c = 0; c < 2; ++c)
-      MLMC_LAUNCH(Names<T>::rbgs, sweep_bytes, sweep_flops, st,
-                  (k_rbgs<T><<<gs, kThreads, 0, st>>>(c, v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, act)));
+  smooth(nu2);
+}
+
+template <typename T>
+int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, int maxc, cudaStream_t st) {
+  const bool mixed = a.cfg.precision == MLMC_PREC_MIXED;
+  const int B = H.B, n = a.n;
+  Level<T>& l0 = H.lv[0];
+  const double Wk = (double)sizeof(T), nodes = B * interior(n), all = (double)B * l0.n3;
+  dim3 rg(H.NB, B);
+  const unsigned sb = (B + 127) / 128;
+  const unsigned g0 = blocks_for((size_t)B * l0.n3, kThreads);
+  const double* D = mixed ? H.D64 : (const double*)(const void*)l0.D;
+  auto sync_count = [&](int* out) -> int {
+    MLMC_CUDA_TRY(cudaMemcpyAsync(out, H.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+    return MLMC_OK;
+  };
+  // z = M r: one V-cycle from zero on the (FP32 copy of the) residual; partials of r.z
+  auto precondition = [&]() {
+    MLMC_CUDA_TRY(cudaMemsetAsync(H.lv[0].u, 0, (size_t)B * l0.n3 * sizeof(T), st));
+    vcycle<T>(H, 0, nu1, nu2, st);
+    double* z = mixed ? H.Z : (double*)(void*)H.lv[0].u;
+    MLMC_LAUNCH("cg_precond_dot", all * (mixed ? 20.0 : 16.0), nodes * 2.0, st,
+                (k_precond_dot<<<rg, kThreads, 0, st>>>(n, mixed ? (const float*)(const void*)H.lv[0].u : nullptr,
+                                                        z, H.R, H.partial, H.active)));
+    return MLMC_OK;
+  };
+  auto zcur = [&]() -> double* { return mixed ? H.Z : (double*)(void*)H.lv[0].u; };
+  // r = g - A x, ||r||
+  MLMC_CUDA_TRY(cudaMemsetAsync(H.n_active, 0, sizeof(int), st));
+  MLMC_LAUNCH("cg_residual", nodes * (3 * Wk + 32), nodes * 16.0, st,
+              (k_residual<T, double, double, double><<<rg, kThreads, 0, st>>>(n, l0.Kx, l0.Ky, l0.Kz, D, H.g64,
+                                                                             a.u, H.R, H.partial, H.active)));
+  MLMC_LAUNCH("norm_update", B * H.NB * 8.0, B * H.NB * 1.0, st,
+              (k_norm_update<<<sb, 128, 0, st>>>(B, H.NB, H.partial, H.g2, H.relres, H.cycles, H.active, 1, 0, rtol,
+                                                 maxc, H.n_active)));
+  int na = 0;
+  MLMC_TRY(sync_count(&na));
+  if (na == 0) return MLMC_OK;
+  if (mixed)
+    MLMC_LAUNCH("to_f32", all * 12.0, 0.0, st,
+                (k_to_f32<<<g0, kThreads, 0, st>>>((size_t)B * l0.n3, H.R, (float*)(void*)l0.g)));
+  MLMC_TRY(precondition());
+  MLMC_LAUNCH("cg_scalar", B * H.NB * 8.0, 0.0, st,
+              (k_cg_scalar<<<sb, 128, 0, st>>>(B, H.NB, 0, H.partial, H.rz, H.rzo, H.alpha, H.beta, H.active)));
+  MLMC_LAUNCH("cg_p_update", all * 16.0, 0.0, st,
+              (k_p_update<<<g0, kThreads, 0, st>>>(n, B, nullptr, zcur(), H.P, H.active)));
+  while (true) {
+    MLMC_LAUNCH("cg_apply_dot", nodes * (3 * Wk + 8 + 16), nodes * 16.0, st,
+                (k_apply_dot<T, double><<<rg, kThreads, 0, st>>>(n, l0.Kx, l0.Ky, l0.Kz, D, H.P, H.Q, H.partial,
+                                                                 H.active)));
+    MLMC_LAUNCH("cg_scalar", B * H.NB * 8.0, 0.0, st,
+                (k_cg_scalar<<<sb, 128, 0, st>>>(B, H.NB, 1, H.partial, H.rz, H.rzo, H.alpha, H.beta, H.active)));
+    MLMC_LAUNCH("cg_update", all * (mixed ? 60.0 : 56.0), nodes * 8.0, st,
+                (k_cg_update<<<rg, kThreads, 0, st>>>(n, H.alpha, H.P, H.Q, a.u, H.R, zcur(),
+                                                      mixed ? (float*)(void*)l0.g : nullptr, H.partial, H.part2,
+                                                      H.active)));
+    MLMC_LAUNCH("cg_scalar", B * H.NB * 8.0, 0.0, st,
+                (k_cg_scalar<<<sb, 128, 0, st>>>(B, H.NB, 3, H.part2, H.rz, H.rzo, H.alpha, H.beta, H.active)));
+    MLMC_CUDA_TRY(cudaMemsetAsync(H.n_active, 0, sizeof(int), st));
+    MLMC_LAUNCH("norm_update", B * H.NB * 8.0, B * H.NB * 1.0, st,
+                (k_norm_update<<<sb, 128, 0, st>>>(B, H.NB, H.partial, H.g2, H.relres, H.cycles, H.active, 1, 1,
+                                                   rtol, maxc, H.n_active)));
+    MLMC_TRY(sync_count(&na));
+    if (na == 0) break;
+    MLMC_TRY(precondition());
+    MLMC_LAUNCH("cg_scalar", B * H.NB * 8.0, 0.0, st,
+                (k_cg_scalar<<<sb, 128, 0, st>>>(B, H.NB, 2, H.partial, H.rz, H.rzo, H.alpha, H.beta, H.active)));
+    MLMC_LAUNCH("cg_p_update", all * 24.0, nodes * 2.0, st,
+                (k_p_update<<<g0, kThreads, 0, st>>>(n, B, H.beta, zcur(), H.P, H.active)));
+  }
+  return MLMC_OK;
 }
 
 template <typename T>
 int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host, double* relres_host,
                int* n_unconv, int* cycles_dev, double* relres_dev) {
   const bool mixed = a.cfg.precision == MLMC_PREC_MIXED;
+  const bool cg = a.cfg.accel == MLMC_ACCEL_CG;
   Hier<T> H;
   Carver c(ws);
-  layout<T>(H, c, a.B, a.n, mixed);
+  layout<T>(H, c, a.B, a.n, mixed, cg);
   const int B = a.B;
   const double W = (double)sizeof(T);
   // operators of every level (k injected from k0)
@@ -560,6 +792,21 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
                 (k_diag<T, T><<<gb, kThreads, 0, st>>>(v.n, B, v.Kx, v.Ky, v.Kz, v.D, v.Dinv)));
     stride *= 2;
   }
+  // smoother per level (explicit choice, or the tuned / default one for that grid) and
+  // the sweep count of the cycle (tuned for the finest grid, or as given)
+  int nu1 = a.cfg.nu1, nu2 = a.cfg.nu2;
+  {
+    int sm0 = a.cfg.smoother;
+    resolve_tuning(a.n, a.cfg.precision, &sm0, &nu1, &nu2);
+  }
+  for (int j = 0; j < H.L; ++j) {
+    Level<T>& v = H.lv[j];
+    int sm = a.cfg.smoother, d1 = 1, d2 = 1;
+    resolve_tuning(v.n, a.cfg.precision, &sm, &d1, &d2);
+    H.fused[j] = v.u2 != nullptr && sm != MLMC_SMOOTH_TWO_PASS;
+    H.tile[j] = sm == MLMC_SMOOTH_FUSED_32x16 ? kTile32x16 : sm == MLMC_SMOOTH_FUSED_64x8 ? kTile64x8 : kTile32x8;
+    if (v.u2) MLMC_CUDA_TRY(cudaMemsetAsync(v.u2, 0, (size_t)B * v.n3 * sizeof(T), st));
+  }
   Level<T>& l0 = H.lv[0];
   const unsigned g0 = blocks_for((size_t)B * l0.n3, kThreads);
   if (mixed) {
@@ -572,10 +819,11 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   const double h = 1.0 / (double)(a.n - 1);
   MLMC_LAUNCH("prepare", B * (double)l0.n3 * (a.f ? 16.0 : 8.0), B * (double)l0.n3, st,
               (k_prepare<<<g0, kThreads, 0, st>>>(a.n, B, h * h, a.f, H.g64, a.u)));
-  if (!mixed) {
+  if (!mixed && !cg) {
     l0.u = (T*)a.u;
     l0.g = (T*)H.g64;
   }
+  if (!mixed && cg) l0.g = (T*)H.R;  // FP64 CG: the cycle maps R to z (level-0 u)
   dim3 rg(H.NB, B);
   const unsigned sb = (B + 127) / 128;
   MLMC_LAUNCH("norm", B * (double)l0.n3 * 8, B * (double)l0.n3 * 2, st,
@@ -611,20 +859,28 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     MLMC_CUDA_TRY(cudaStreamSynchronize(st));
     return na;
   };
-  int na = residual_check(0);
+  if (cg) {
+    const int st_pcg = pcg_loop<T>(H, a, nu1, nu2, rtol, maxc, st);
+    if (st_pcg < 0) return st_pcg;
+  }
+  int na = cg ? 0 : residual_check(0);
   if (na < 0) return na;
   while (na > 0) {
     if (mixed) {
-      MLMC_CUDA_TRY(cudaMemsetAsync(l0.u, 0, (size_t)B * l0.n3 * sizeof(T), st));
-      vcycle<T>(H, 0, a.cfg.nu1, a.cfg.nu2, st);
+      MLMC_CUDA_TRY(cudaMemsetAsync(H.lv[0].u, 0, (size_t)B * l0.n3 * sizeof(T), st));
+      vcycle<T>(H, 0, nu1, nu2, st);
       MLMC_LAUNCH("update_mixed", B * (double)l0.n3 * (W + 16), B * (double)l0.n3, st,
-                  (k_update_mixed<<<g0, kThreads, 0, st>>>(a.n, B, (const float*)l0.u, a.u, H.active)));
+                  (k_update_mixed<<<g0, kThreads, 0, st>>>(a.n, B, (const float*)H.lv[0].u, a.u, H.active)));
     } else {
-      vcycle<T>(H, 0, a.cfg.nu1, a.cfg.nu2, st);
+      vcycle<T>(H, 0, nu1, nu2, st);
     }
     na = residual_check(1);
     if (na < 0) return na;
   }
+  // FP64 solves iterate in place on the caller's u; the fused smoother may leave the
+  // latest iterate in the spare buffer
+  if (!mixed && !cg && (void*)H.lv[0].u != (void*)a.u)
+    MLMC_CUDA_TRY(cudaMemcpyAsync(a.u, H.lv[0].u, (size_t)B * l0.n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   MLMC_CUDA_TRY(cudaGetLastError());
   if (cycles_dev)
     MLMC_CUDA_TRY(cudaMemcpyAsync(cycles_dev, H.cycles, B * sizeof(int), cudaMemcpyDeviceToDevice, st));
@@ -647,14 +903,14 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
 
 }  // namespace
 
-size_t mg_workspace_bytes(int B, int n, int precision) {
+size_t mg_workspace_bytes(int B, int n, int precision, int accel) {
   Carver c(nullptr);
   if (precision == MLMC_PREC_MIXED) {
     Hier<float> H;
-    layout<float>(H, c, B, n, true);
+    layout<float>(H, c, B, n, true, accel == MLMC_ACCEL_CG);
   } else {
     Hier<double> H;
-    layout<double>(H, c, B, n, false);
+    layout<double>(H, c, B, n, false, accel == MLMC_ACCEL_CG);
   }
   return c.off;
 }

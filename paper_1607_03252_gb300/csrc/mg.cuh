@@ -23,7 +23,7 @@ struct MGSolveArgs {
 };
 
 // Device workspace of a solve (bytes, 256-aligned pieces).
-size_t mg_workspace_bytes(int B, int n, int precision);
+size_t mg_workspace_bytes(int B, int n, int precision, int accel);
 
 // Enqueues the solve on `st` and synchronises it once per cycle to test convergence.
 // cycles_host / relres_host: B entries each (may be NULL); cycles_dev / relres_dev:

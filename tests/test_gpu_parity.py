@@ -149,7 +149,9 @@ def test_invalid_arguments_rejected():
     assert e.value.status == mg.MLMC_ERR_INVALID
     k = torch.ones((1, 9, 9, 9), dtype=torch.float64, device=DEV)
     with pytest.raises(mg.MlmcError):
-        mg.mg_solve_batch(mg.mg_cfg(nu1=0, nu2=0), k, torch.zeros_like(k))
+        mg.mg_solve_batch(mg.mg_cfg(nu1=9, nu2=2), k, torch.zeros_like(k))
+    with pytest.raises(mg.MlmcError):
+        mg.mg_solve_batch(mg.mg_cfg(smoother=7), k, torch.zeros_like(k))
     with pytest.raises(mg.MlmcError):
         mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, 1.0, -1.0, 8), [1], k)
 
@@ -211,3 +213,120 @@ def test_c2_level3_full_size_sampled(orc):
     # rtol 1e-10 on both sides: the stopping points may differ by one cycle (error ~1e-10)
     assert np.all(np.abs(Y[pick] - Yo) <= _y_tol(Qfo, Qco, 1e-8))
     assert np.all(np.isfinite(Y)) and stats.max_cycles_seen < 30
+
+
+SMOOTHERS = [mg.MLMC_SMOOTH_TWO_PASS, mg.MLMC_SMOOTH_FUSED_32x8, mg.MLMC_SMOOTH_FUSED_32x16, mg.MLMC_SMOOTH_FUSED_64x8]
+
+
+@pytest.mark.parametrize("prec", [mg.MLMC_PREC_F64, mg.MLMC_PREC_MIXED])
+@pytest.mark.parametrize("n", [9, 17, 33, 65])
+def test_smoother_variants_identical_fixed_cycles(prec, n):
+    """The fused one-pass sweep (every tile shape) performs the same operations on the
+    same operands as the two-pass colour sweep: identical iterates, bit for bit."""
+    B = 3
+    k = to_dev(np.stack([random_coefficient(n, 500 + s, 1.0) for s in range(B)]))
+    f = to_dev(np.stack([random_rhs(n, 600 + s) for s in range(B)]))
+    outs = []
+    for sm in SMOOTHERS:
+        u = torch.zeros_like(k)
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 0.0, 3, prec, sm), k, u, f)
+        outs.append((u.cpu().numpy(), rel))
+    for u, rel in outs[1:]:
+        assert np.array_equal(u, outs[0][0])
+        assert np.array_equal(rel, outs[0][1])
+
+
+@pytest.mark.parametrize("prec", [mg.MLMC_PREC_F64, mg.MLMC_PREC_MIXED])
+def test_smoother_variants_identical_with_masking(prec, orc):
+    """Samples that converge at different cycle counts: finished samples must keep
+    their iterate under the double-buffered fused sweep."""
+    n, B = 33, 4
+    ks = [orc.field(RUN_SEED, int(i), 256, 1.0 + 0.5 * s, 0.15, n) for s, i in enumerate(sample_ids(4, 0, B))]
+    k = to_dev(np.stack(ks))
+    outs = []
+    for sm in SMOOTHERS:
+        u = torch.zeros_like(k)
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-10, 200, prec, sm), k, u)
+        outs.append((u.cpu().numpy(), cyc))
+    assert len(set(outs[0][1].tolist())) > 1  # the samples did stop at different cycles
+    for u, cyc in outs[1:]:
+        assert np.array_equal(cyc, outs[0][1])
+        assert np.array_equal(u, outs[0][0])
+
+
+def _direct(orc, k, mixed=False, f=None):
+    import scipy.sparse.linalg as spl
+
+    A = orc.assemble_csr(k, mixed)
+    n = k.shape[0]
+    rhs = np.ones(A.shape[0]) if f is None else f[1:-1, 1:-1, 1:-1].ravel()
+    u = np.zeros_like(k)
+    u[1:-1, 1:-1, 1:-1] = spl.spsolve(A.tocsc(), rhs).reshape(n - 2, n - 2, n - 2)
+    return u
+
+
+@pytest.mark.parametrize("prec", [mg.MLMC_PREC_F64, mg.MLMC_PREC_MIXED])
+@pytest.mark.parametrize("n", [17, 33])
+def test_cg_matches_sparse_direct_on_rough_field(orc, prec, n):
+    """sigma^2 = 2, ell = 0.1: the stationary V(2,2) cycle needs 100+ cycles on some
+    realisations; flexible CG with the same cycle as preconditioner reaches the same
+    discrete solution (the oracle's sparse matrix solved directly)."""
+    ids = sample_ids(1, 10, 4)
+    ks = [orc.field(RUN_SEED, int(i), 256, 2.0, 0.1, n) for i in ids]
+    rtol = 1e-12 if prec == mg.MLMC_PREC_F64 else 1e-11
+    k = to_dev(np.stack(ks))
+    u = torch.zeros_like(k)
+    cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, rtol, 200, prec, accel=mg.MLMC_ACCEL_CG), k, u)
+    assert st == 0 and np.all(rel <= rtol)
+    assert cyc.max() < 45
+    u = u.cpu().numpy()
+    for s in range(len(ids)):
+        ud = _direct(orc, ks[s], mixed=(prec == mg.MLMC_PREC_MIXED))
+        assert relmax(u[s], ud) < 1e-9
+
+
+def test_cg_with_rhs_and_smoothers(orc):
+    n = 17
+    ks = [random_coefficient(n, 700 + s, 1.0) for s in range(3)]
+    fs = [random_rhs(n, 800 + s) for s in range(3)]
+    ref = None
+    for sm in SMOOTHERS:
+        u, cyc, rel, st = gpu_solve(ks, fs, rtol=1e-12, max_cycles=100)
+        k = to_dev(np.stack(ks))
+        ug = torch.zeros_like(k)
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-12, 100, mg.MLMC_PREC_F64, sm, mg.MLMC_ACCEL_CG), k, ug,
+                                         to_dev(np.stack(fs)))
+        ug = ug.cpu().numpy()
+        for s in range(3):
+            assert relmax(ug[s], _direct(orc, ks[s], f=fs[s])) < 1e-9
+        if ref is None:
+            ref = ug
+        assert np.array_equal(ug, ref)
+
+
+def test_cg_batch_composition_does_not_change_results(orc):
+    n = 17
+    ks = [orc.field(RUN_SEED, int(i), 256, 2.0, 0.1, n) for i in sample_ids(2, 40, 5)]
+    for prec in (mg.MLMC_PREC_F64, mg.MLMC_PREC_MIXED):
+        cfg = mg.mg_cfg(2, 2, 1e-10, 200, prec, accel=mg.MLMC_ACCEL_CG)
+        k = to_dev(np.stack(ks))
+        ub = torch.zeros_like(k)
+        cb, _, _ = mg.mg_solve_batch(cfg, k, ub)
+        for s in (1, 4):
+            ka = to_dev(ks[s][None])
+            ua = torch.zeros_like(ka)
+            ca, _, _ = mg.mg_solve_batch(cfg, ka, ua)
+            assert ca[0] == cb[s] and torch.equal(ua[0], ub[s])
+
+
+def test_autotune_records_choice():
+    cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.3, 64, n0=17, nu1=0, nu2=0, rtol=1e-10, precision=mg.MLMC_PREC_MIXED)
+    rows, best_sm, best_nu = mg.mlmc_autotune(cfg, 1, int(sample_ids(1, 900, 1)[0]), 16)
+    assert len(rows) == 12 and best_nu in (1, 2, 3)
+    assert all(r["ms_per_sample"] > 0 for r in rows)
+    # a level run with AUTO smoother and nu = 0 uses the choice and matches an explicit run
+    s_auto, Ya, _, _ = mg.mlmc_level_estimate(cfg, 1, int(sample_ids(1, 0, 1)[0]), 8)
+    cfg2 = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.3, 64, n0=17, nu1=best_nu, nu2=best_nu, rtol=1e-10,
+                            precision=mg.MLMC_PREC_MIXED, smoother=best_sm)
+    s_exp, Ye, _, _ = mg.mlmc_level_estimate(cfg2, 1, int(sample_ids(1, 0, 1)[0]), 8)
+    assert s_auto.mean_cycles_fine == s_exp.mean_cycles_fine
