@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="own", choices=["own", "reference"])
-    p.add_argument("--config", default="c2", choices=["c1", "c2"])
+    p.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -67,9 +67,33 @@ def measured_peaks():
 def workload(cfg_name):
     c = CONFIGS[cfg_name]
     levels = c["levels"]
-    N = c["N"]
+    N = c.get("N", c.get("N_init"))
     single = c.get("single_level", False)
     return c, levels, N, single
+
+
+def plan_levels(mg, cfg, levels, stream, rank):
+    """Mixed-precision workloads: autotune each level (smoother x nu), run the pilot
+    N_init, and size N_l by Eq. 11 for the configured eps (theta split of Eq. 6)."""
+    import math
+
+    prec = mg.MLMC_PREC_MIXED
+    accel = mg.MLMC_ACCEL_CG if cfg.get("accel") == "cg" else mg.MLMC_ACCEL_NONE
+    tune, V, C = {}, [], []
+    for l, n0 in zip(levels, cfg["N_init"]):
+        c = mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=17, nu1=0, nu2=0, rtol=cfg["rtol"],
+                             precision=prec, max_batch=n0, stream=stream, accel=accel, max_cycles=300)
+        rows, bs, bnu = mg.mlmc_autotune(c, l, int(sample_ids(l, 1 << 40, 1)[0]), min(n0, 32))
+        tune[str(l)] = {"best": {"smoother": mg._capi.SMOOTHER_NAMES.get(bs, bs), "nu": bnu}, "table": rows}
+        st, _, _, _ = mg.mlmc_level_estimate(c, l, int(sample_ids(l, (1 << 41) + rank * n0, 1)[0]), n0,
+                                             want_samples=False)
+        V.append(max(st.var_unbiased, 1e-30))
+        C.append(st.cost_per_sample)
+    eps_s = math.sqrt(cfg["theta"]) * cfg["eps"]
+    total = sum(math.sqrt(v * c) for v, c in zip(V, C))
+    N = [max(2, int(math.ceil(total * math.sqrt(v / c) / eps_s ** 2))) for v, c in zip(V, C)]
+    return N, {"pilot_N": cfg["N_init"], "pilot_var": V, "pilot_cost_s": C, "eps": cfg["eps"],
+               "theta": cfg["theta"], "N_from_eq11": N, "autotune": tune}
 
 
 class ClockSampler:
@@ -130,12 +154,20 @@ def dist_env():
 # CPU oracle timing (bounded sample)
 # --------------------------------------------------------------------------------------
 def oracle_level_rates(cfg, levels, single, counts):
-    """samples/s of the oracle per level on the given sample counts (OpenMP over samples)."""
+    """samples/s of the oracle per level on the given sample counts (OpenMP over samples).
+    Levels with a count of 0 are not run; their rate is extrapolated from the previous
+    level by the 8x growth of the grid (cost per sample ~ nodes)."""
     import oracle
 
-    ocfg = oracle.make_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], cfg["nu1"], cfg["nu2"], cfg["rtol"], 100)
+    mixed = cfg.get("precision") == "mixed"
+    ocfg = oracle.make_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], cfg["nu1"], cfg["nu2"], cfg["rtol"], 400,
+                           mixed=mixed)
     rates, secs = {}, {}
     for l, cnt in zip(levels, counts):
+        if cnt == 0:
+            rates[l] = rates[l - 1] / 8.0
+            secs[l] = 0.0
+            continue
         ids = sample_ids(l, 0, cnt)
         nc = 0 if (single or l == 0) else level_n(l - 1)
         t = time.perf_counter()
@@ -146,9 +178,11 @@ def oracle_level_rates(cfg, levels, single, counts):
     return rates, secs
 
 
-def oracle_counts(levels, threads):
+def oracle_counts(levels, threads, cfg=None):
     base = {0: max(16, 4 * threads), 1: max(8, threads), 2: max(4, threads // 2), 3: max(1, threads // 2),
-            4: 1, 5: 1}
+            4: 0, 5: 0}
+    if cfg is not None and cfg.get("precision") == "mixed":
+        base[3] = 0  # rough fields: the stationary oracle needs 100+ cycles; extrapolate beyond 65^3
     return [base[l] for l in levels]
 
 
@@ -168,7 +202,7 @@ def reference_arm(args):
 
     cfg, levels, N, single = workload(args.config)
     threads = oracle.max_threads()
-    counts = oracle_counts(levels, threads)
+    counts = oracle_counts(levels, threads, cfg)
     step_times, all_rates = [], []
     for i in range(args.warmup + args.steps):
         t = time.perf_counter()
@@ -213,8 +247,14 @@ def own_arm(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     cfg, levels, N, single = workload(args.config)
     prec = mg.MLMC_PREC_F64 if cfg["precision"] == "f64" else mg.MLMC_PREC_MIXED
+    accel = mg.MLMC_ACCEL_CG if cfg.get("accel") == "cg" else mg.MLMC_ACCEL_NONE
     stream = torch.cuda.Stream()
     dev = torch.device("cuda", local)
+    plan = None
+    nu_cfg = (cfg["nu1"], cfg["nu2"])
+    if "N_init" in cfg:
+        N, plan = plan_levels(mg, cfg, levels, stream, rank)
+        nu_cfg = (0, 0)  # the autotuned sweep count per level
     # inputs resident in HBM: each rank its own realisations (weak scaling)
     ids = {l: torch.from_numpy(sample_ids(l, rank * n, n).view("int64")).to(dev) for l, n in zip(levels, N)}
     Y = {l: torch.empty(n, dtype=torch.float64, device=dev) for l, n in zip(levels, N)}
@@ -222,8 +262,9 @@ def own_arm(args):
     for l, n in zip(levels, N):
         n0 = level_n(l) if single else 17
         lvl = 0 if single else l
-        mcfg[l] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=cfg["nu1"],
-                                    nu2=cfg["nu2"], rtol=cfg["rtol"], precision=prec, max_batch=n, stream=stream), lvl)
+        mcfg[l] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=nu_cfg[0],
+                                    nu2=nu_cfg[1], rtol=cfg["rtol"], precision=prec, max_batch=n, stream=stream,
+                                    accel=accel, max_cycles=300), lvl)
     lev_ev = {l: [] for l in levels}
     stats = {}
 
@@ -290,7 +331,7 @@ def own_arm(args):
     # end to end through the host-buffer C-ABI call
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream)
+        e2e = e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, accel)
 
     line = None
     if rank == 0:
@@ -302,6 +343,8 @@ def own_arm(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == mg.MLMC_PREC_F64 else "f32+f64",
+            "solver": {"precision": cfg["precision"], "accel": cfg.get("accel", "none")},
+            "plan": plan,
             "data": "synthetic (seeded Philox realisations, run_seed %d)" % RUN_SEED,
             "config": {"workload": cfg["name"], "levels": levels, "N_per_gpu": N,
                        "fine_n": [level_n(l) for l in levels], "sigma2": cfg["sigma2"], "ell": cfg["ell"],
@@ -369,7 +412,7 @@ def roofline(prof, peaks):
             "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"]}
 
 
-def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream):
+def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, accel):
     """Same workload through mlmc_level_estimate: ids built on the host and copied in,
     Y/Qf/Qc copied back into pinned host buffers, every step."""
     import ctypes
@@ -380,9 +423,9 @@ def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stre
     cfgs = {}
     for l, n in zip(levels, N):
         n0 = level_n(l) if single else 17
-        cfgs[l] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=cfg["nu1"],
-                                    nu2=cfg["nu2"], rtol=cfg["rtol"], precision=prec, max_batch=n, stream=stream),
-                   0 if single else l)
+        cfgs[l] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=nu_cfg[0],
+                                    nu2=nu_cfg[1], rtol=cfg["rtol"], precision=prec, max_batch=n, stream=stream,
+                                    accel=accel, max_cycles=300), 0 if single else l)
     L = mg.lib()
     dp = ctypes.POINTER(ctypes.c_double)
 
@@ -419,12 +462,13 @@ def cpu_baseline(cfg, levels, N, single):
     import oracle
 
     threads = oracle.max_threads()
-    counts = oracle_counts(levels, threads)
+    counts = oracle_counts(levels, threads, cfg)
     rates, secs = oracle_level_rates(cfg, levels, single, counts)
     value = extrapolated_rate(levels, N, rates)
     return {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
-            "sample": "levels %s: %s samples (same ids as the GPU run), %.1f s of CPU time; per-level samples/s "
-                      "extrapolated to N=%s" % (levels, counts, sum(secs.values()), N),
+            "sample": "levels %s: %s samples (same ids as the GPU run; 0 = rate extrapolated from the level below "
+                      "by 8x nodes), %.1f s of CPU time; per-level samples/s extrapolated to N=%s"
+                      % (levels, counts, sum(secs.values()), N),
             "per_level": {str(l): rates[l] for l in levels}}
 
 

@@ -154,13 +154,98 @@ __global__ void __launch_bounds__(kFieldThreads) k_field(const double2* __restri
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// The same sum in double-float arithmetic on the FP32 pipe (GB300 runs FP32 at ~59x the
+// FP64 rate). Every FP64 factor f is split into f = hi + lo (two floats, hi = fl32(f));
+// a term Re(A Q) = Ar Qr - Ai Qi becomes the exact FP32 products Arh Qrh and Aih Qih
+// (their rounding errors recovered by FMA), an exact TwoSum of the two, the four cross
+// terms hi x lo, and a TwoSum into the (hi, lo) accumulator. The relative error of the
+// sum is ~2^-44 of the magnitudes involved, far below what the FP64 solve can resolve
+// (parity against the FP64 oracle is checked at 1e-12 relative in k).
+__device__ __forceinline__ float4 split2(double2 v) {
+  const float xh = (float)v.x, yh = (float)v.y;
+  return make_float4(xh, (float)(v.x - (double)xh), yh, (float)(v.y - (double)yh));
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bv = s - a;
+  e = (a - (s - bv)) + (b - bv);
+}
+
+template <typename TOut>
+__global__ void __launch_bounds__(kFieldThreads) k_field_df(const double2* __restrict__ tab, int M, int n, int LT,
+                                                             int MC, double scale, TOut* __restrict__ kout) {
+  extern __shared__ float4 smf[];
+  float4* sA = smf;
+  float4* sQ = smf + (size_t)MC * n;
+  const int s = blockIdx.y;
+  const size_t n2 = (size_t)n * n;
+  const size_t L0 = (size_t)blockIdx.x * LT;
+  const int nl = (int)((n2 - L0) < (size_t)LT ? (n2 - L0) : (size_t)LT);
+  const int nout = nl * n;
+  const double2* Tx = tab + (size_t)s * 3 * M * n;
+  const double2* Ty = Tx + (size_t)M * n;
+  const double2* Tz = Ty + (size_t)M * n;
+  int xo[kFieldOut], lo[kFieldOut];
+  float ah[kFieldOut], al[kFieldOut];
+#pragma unroll
+  for (int q = 0; q < kFieldOut; ++q) {
+    const int o = threadIdx.x + q * kFieldThreads;
+    lo[q] = o < nout ? o / n : -1;
+    xo[q] = o < nout ? o - lo[q] * n : 0;
+    ah[q] = 0.f;
+    al[q] = 0.f;
+  }
+  for (int m0 = 0; m0 < M; m0 += MC) {
+    const int mc = min(MC, M - m0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < mc * n; t += kFieldThreads) sA[t] = split2(Tx[(size_t)m0 * n + t]);
+    for (int t = threadIdx.x; t < mc * nl; t += kFieldThreads) {
+      const int mm = t / nl, l = t - mm * nl;
+      const size_t line = L0 + l;
+      const int y = (int)(line % n), z = (int)(line / n);
+      const double2 b = Ty[(size_t)(m0 + mm) * n + y], c = Tz[(size_t)(m0 + mm) * n + z];
+      sQ[mm * LT + l] = split2(make_double2(b.x * c.x - b.y * c.y, b.x * c.y + b.y * c.x));
+    }
+    __syncthreads();
+    for (int mm = 0; mm < mc; ++mm) {
+#pragma unroll
+      for (int q = 0; q < kFieldOut; ++q) {
+        if (lo[q] >= 0) {
+          const float4 a = sA[mm * n + xo[q]];   // (Re hi, Re lo, Im hi, Im lo)
+          const float4 b = sQ[mm * LT + lo[q]];
+          const float p1 = a.x * b.x, e1 = fmaf(a.x, b.x, -p1);
+          const float p2 = a.z * b.z, e2 = fmaf(a.z, b.z, -p2);
+          float th, tl;
+          two_sum(p1, -p2, th, tl);
+          float lw = (e1 - e2) + tl;
+          lw = fmaf(a.x, b.y, lw);
+          lw = fmaf(a.y, b.x, lw);
+          lw = fmaf(-a.z, b.w, lw);
+          lw = fmaf(-a.w, b.z, lw);
+          float sh, se;
+          two_sum(ah[q], th, sh, se);
+          ah[q] = sh;
+          al[q] += se + lw;
+        }
+      }
+    }
+  }
+  TOut* out = kout + (size_t)s * n2 * n + L0 * n;
+#pragma unroll
+  for (int q = 0; q < kFieldOut; ++q) {
+    const int o = threadIdx.x + q * kFieldThreads;
+    if (o < nout) out[o] = (TOut)exp(scale * ((double)ah[q] + (double)al[q]));
+  }
+}
+
 size_t field_scratch_bytes(int B, int M, int n) {
   return a256((size_t)B * M * 3 * sizeof(double)) + a256((size_t)B * M * sizeof(double)) +
          a256((size_t)B * 3 * M * n * sizeof(double2));
 }
 
 int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, int n, int dtype, void* kout,
-                   void* scratch, cudaStream_t st) {
+                   void* scratch, cudaStream_t st, int arith) {
   char* p = (char*)scratch;
   auto carve = [&](size_t bytes) {
     void* r = p;
@@ -184,19 +269,32 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
   int MC = 3072 / (n + LT);
   if (MC > 32) MC = 32;
   if (MC < 1) MC = 1;
-  const size_t smem = (size_t)MC * (n + LT) * sizeof(double2);
+  const size_t smem = (size_t)MC * (n + LT) * sizeof(double2);  // double2 and float4 are both 16 B
   dim3 grid((unsigned)(((size_t)n * n + LT - 1) / LT), (unsigned)B);
   const double scale = sqrt(cfg.sigma2) * sqrt(2.0 / (double)cfg.M);
   // algorithmic work: 2 FMA (4 flops) per node and feature, plus one complex product
   // (6 flops) per line and feature; bytes: the tables once and the output once
   const double flops = (double)B * cube(n) * cfg.M * 4.0 + (double)B * n * n * cfg.M * 6.0;
   const double bytes = (double)B * cube(n) * (dtype == MLMC_F64 ? 8.0 : 4.0) + (double)nt * 16.0;
-  if (dtype == MLMC_F64)
-    MLMC_LAUNCH("field_f64", bytes, flops, st,
-                (k_field<double><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (double*)kout)));
-  else
-    MLMC_LAUNCH("field_f64", bytes, flops, st,
-                (k_field<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (float*)kout)));
+  // double-float form: the same algorithmic flops, executed as ~24 FP32 operations per
+  // node and feature; its roofline is the FP32 pipe
+  if (arith == kFieldFP64) {
+    if (dtype == MLMC_F64)
+      MLMC_LAUNCH("field_f64", bytes, flops, st,
+                  (k_field<double><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (double*)kout)));
+    else
+      MLMC_LAUNCH("field_f64", bytes, flops, st,
+                  (k_field<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (float*)kout)));
+  } else {
+    if (dtype == MLMC_F64)
+      MLMC_LAUNCH("field_df32", bytes, flops, st,
+                  (k_field_df<double><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale,
+                                                                         (double*)kout)));
+    else
+      MLMC_LAUNCH("field_df32", bytes, flops, st,
+                  (k_field_df<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale,
+                                                                        (float*)kout)));
+  }
   MLMC_CUDA_TRY(cudaGetLastError());
   return MLMC_OK;
 }

@@ -42,7 +42,8 @@ CONFIGS = {
                sigma2=1.0, ell=0.3, M=256, precision="f64", rtol=1e-10, nu1=2, nu2=2),
     # mixed-precision 5-level MLMC; N_l from Eq. 11 for eps = 1e-3 after a pilot
     "c3": dict(name="c3_mlmc5_mixed", levels=[0, 1, 2, 3, 4], single_level=False, N_init=[1024, 256, 64, 16, 16],
-               eps=1e-3, theta=0.5, sigma2=2.0, ell=0.1, M=256, precision="mixed", rtol=1e-10, nu1=2, nu2=2),
+               eps=1e-3, theta=0.5, sigma2=2.0, ell=0.1, M=256, precision="mixed", accel="cg", rtol=1e-10,
+               nu1=2, nu2=2),
     # serving: Poisson single-sample requests over levels 0..4 (C3's field)
     "c4": dict(name="c4_serving", levels=[0, 1, 2, 3, 4], sigma2=2.0, ell=0.1, M=256, precision="mixed",
                rtol=1e-10, nu1=2, nu2=2),
