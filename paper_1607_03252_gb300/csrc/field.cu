@@ -92,6 +92,17 @@ __global__ void k_phasors(const double* __restrict__ w, const double* __restrict
   }
 }
 
+// The x-axis table of the double-float kernel, pre-split once: (Re hi, Re lo, Im hi, Im lo).
+__global__ void k_split_x(const double2* __restrict__ tab, int B, int M, int n, float4* __restrict__ xs) {
+  const size_t per = (size_t)M * n, total = (size_t)B * per;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t s = t / per, r = t - s * per;
+    const double2 v = tab[s * 3 * per + r];
+    const float xh = (float)v.x, yh = (float)v.y;
+    xs[t] = make_float4(xh, (float)(v.x - (double)xh), yh, (float)(v.y - (double)yh));
+  }
+}
+
 constexpr int kFieldThreads = 256;
 constexpr int kFieldOut = 8;  // outputs per thread
 
@@ -173,7 +184,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 template <typename TOut>
-__global__ void __launch_bounds__(kFieldThreads) k_field_df(const double2* __restrict__ tab, int M, int n, int LT,
+__global__ void __launch_bounds__(kFieldThreads) k_field_df(const double2* __restrict__ tab,
+                                                             const float4* __restrict__ xsplit, int M, int n, int LT,
                                                              int MC, double scale, TOut* __restrict__ kout) {
   extern __shared__ float4 smf[];
   float4* sA = smf;
@@ -183,9 +195,9 @@ __global__ void __launch_bounds__(kFieldThreads) k_field_df(const double2* __res
   const size_t L0 = (size_t)blockIdx.x * LT;
   const int nl = (int)((n2 - L0) < (size_t)LT ? (n2 - L0) : (size_t)LT);
   const int nout = nl * n;
-  const double2* Tx = tab + (size_t)s * 3 * M * n;
-  const double2* Ty = Tx + (size_t)M * n;
+  const double2* Ty = tab + (size_t)s * 3 * M * n + (size_t)M * n;
   const double2* Tz = Ty + (size_t)M * n;
+  const float4* Xs = xsplit + (size_t)s * M * n;
   int xo[kFieldOut], lo[kFieldOut];
   float ah[kFieldOut], al[kFieldOut];
 #pragma unroll
@@ -199,7 +211,7 @@ __global__ void __launch_bounds__(kFieldThreads) k_field_df(const double2* __res
   for (int m0 = 0; m0 < M; m0 += MC) {
     const int mc = min(MC, M - m0);
     __syncthreads();
-    for (int t = threadIdx.x; t < mc * n; t += kFieldThreads) sA[t] = split2(Tx[(size_t)m0 * n + t]);
+    for (int t = threadIdx.x; t < mc * n; t += kFieldThreads) sA[t] = Xs[(size_t)m0 * n + t];
     for (int t = threadIdx.x; t < mc * nl; t += kFieldThreads) {
       const int mm = t / nl, l = t - mm * nl;
       const size_t line = L0 + l;
@@ -241,7 +253,7 @@ __global__ void __launch_bounds__(kFieldThreads) k_field_df(const double2* __res
 
 size_t field_scratch_bytes(int B, int M, int n) {
   return a256((size_t)B * M * 3 * sizeof(double)) + a256((size_t)B * M * sizeof(double)) +
-         a256((size_t)B * 3 * M * n * sizeof(double2));
+         a256((size_t)B * 3 * M * n * sizeof(double2)) + a256((size_t)B * M * n * sizeof(float4));
 }
 
 int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, int n, int dtype, void* kout,
@@ -255,6 +267,7 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
   double* w = (double*)carve((size_t)B * cfg.M * 3 * sizeof(double));
   double* bph = (double*)carve((size_t)B * cfg.M * sizeof(double));
   double2* tab = (double2*)carve((size_t)B * 3 * cfg.M * n * sizeof(double2));
+  float4* xsplit = (float4*)carve((size_t)B * cfg.M * n * sizeof(float4));
   const size_t nf = (size_t)B * cfg.M;
   MLMC_LAUNCH("features", nf * 40.0, nf * 200.0, st,
               (k_features<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(ids_dev, B, cfg.M, cfg.run_seed,
@@ -286,13 +299,16 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
       MLMC_LAUNCH("field_f64", bytes, flops, st,
                   (k_field<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (float*)kout)));
   } else {
+    const size_t nx = (size_t)B * cfg.M * n;
+    MLMC_LAUNCH("phasors", nx * 32.0, nx * 4.0, st,
+                (k_split_x<<<blocks_for(nx, 256), 256, 0, st>>>(tab, B, cfg.M, n, xsplit)));
     if (dtype == MLMC_F64)
       MLMC_LAUNCH("field_df32", bytes, flops, st,
-                  (k_field_df<double><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale,
+                  (k_field_df<double><<<grid, kFieldThreads, smem, st>>>(tab, xsplit, cfg.M, n, LT, MC, scale,
                                                                          (double*)kout)));
     else
       MLMC_LAUNCH("field_df32", bytes, flops, st,
-                  (k_field_df<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale,
+                  (k_field_df<float><<<grid, kFieldThreads, smem, st>>>(tab, xsplit, cfg.M, n, LT, MC, scale,
                                                                         (float*)kout)));
   }
   MLMC_CUDA_TRY(cudaGetLastError());

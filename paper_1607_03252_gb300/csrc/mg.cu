@@ -106,19 +106,21 @@ __global__ void k_diag(int n, int B, const T* __restrict__ Kx, const T* __restri
   }
 }
 
-// Dense 27x27 scaled operator of the 5^3 grid, Cholesky factor, and its inverse
-// (one thread per sample; L is scratch of 27*27 doubles per sample).
+// Dense 27x27 scaled operator of the 5^3 grid, its Cholesky factor, and the inverse,
+// one warp per sample (lane i < 27 owns row i of the working matrix in global scratch;
+// the factorisation and the 27 triangular solves run column by column across the warp).
 template <typename T>
 __global__ void k_coarse_setup(int B, const T* __restrict__ Kx, const T* __restrict__ Ky, const T* __restrict__ Kz,
                                double* __restrict__ Lws, double* __restrict__ Ainv) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= B) return;
-  const int n = 5, N = 27;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= B) return;
+  const int s = warp, n = 5, N = 27;
   const size_t base = (size_t)s * 125;
   double* A = Lws + (size_t)s * N * N;
   double* X = Ainv + (size_t)s * N * N;
-  for (int i = 0; i < N * N; ++i) A[i] = 0.0;
-  for (int i = 0; i < N; ++i) {
+  const int i = lane;
+  if (i < N) {
+    for (int c = 0; c < N; ++c) A[i * N + c] = 0.0;
     const int x = 1 + i % 3, y = 1 + (i / 3) % 3, z = 1 + i / 9;
     const size_t p = base + (size_t)(z * n + y) * n + x;
     const double f[6] = {(double)Kx[p - 1], (double)Kx[p], (double)Ky[p - n], (double)Ky[p], (double)Kz[p - 25],
@@ -132,32 +134,39 @@ __global__ void k_coarse_setup(int B, const T* __restrict__ Kx, const T* __restr
     }
     A[i * N + i] = d;
   }
-  // Cholesky A = L L^T, lower triangle in place
+  __syncwarp();
+  // Cholesky A = L L^T (lower triangle in place): column j is finished by the warp
   for (int j = 0; j < N; ++j) {
-    double d = A[j * N + j];
-    for (int p = 0; p < j; ++p) d -= A[j * N + p] * A[j * N + p];
-    const double ljj = sqrt(d);
-    A[j * N + j] = ljj;
-    for (int i = j + 1; i < N; ++i) {
+    double ljj = 0.0;
+    if (lane == 0) {
+      double d = A[j * N + j];
+      for (int q = 0; q < j; ++q) d -= A[j * N + q] * A[j * N + q];
+      ljj = sqrt(d);
+      A[j * N + j] = ljj;
+    }
+    ljj = __shfl_sync(0xffffffffu, ljj, 0);
+    __syncwarp();
+    if (i > j && i < N) {
       double v = A[i * N + j];
-      for (int p = 0; p < j; ++p) v -= A[i * N + p] * A[j * N + p];
+      for (int q = 0; q < j; ++q) v -= A[i * N + q] * A[j * N + q];
       A[i * N + j] = v / ljj;
     }
+    __syncwarp();
   }
-  // columns of the inverse: solve L L^T x = e_c
-  for (int c = 0; c < N; ++c) {
+  // column c of the inverse solves L L^T x = e_c; lane c < 27 solves column c
+  if (i < N) {
     double y[27];
-    for (int i = 0; i < N; ++i) {
-      double v = (i == c) ? 1.0 : 0.0;
-      for (int p = 0; p < i; ++p) v -= A[i * N + p] * y[p];
-      y[i] = v / A[i * N + i];
+    for (int r = 0; r < N; ++r) {
+      double v = (r == i) ? 1.0 : 0.0;
+      for (int q = 0; q < r; ++q) v -= A[r * N + q] * y[q];
+      y[r] = v / A[r * N + r];
     }
-    for (int i = N - 1; i >= 0; --i) {
-      double v = y[i];
-      for (int p = i + 1; p < N; ++p) v -= A[p * N + i] * y[p];
-      y[i] = v / A[i * N + i];
+    for (int r = N - 1; r >= 0; --r) {
+      double v = y[r];
+      for (int q = r + 1; q < N; ++q) v -= A[q * N + r] * y[q];
+      y[r] = v / A[r * N + r];
     }
-    for (int i = 0; i < N; ++i) X[i * N + c] = y[i];
+    for (int r = 0; r < N; ++r) X[r * N + i] = y[r];
   }
 }
 
@@ -230,11 +239,13 @@ __device__ __forceinline__ double block_sum(double v) {
   return r;  // valid in thread 0
 }
 
-// Blocks per sample of the deterministic reductions (a function of n only).
+// Blocks per sample of the deterministic reductions: a function of the grid size only
+// (never of the batch), so that a sample's sums do not depend on its batch; up to 1024
+// blocks so that one or two large samples still fill the GPU.
 inline int reduce_blocks(size_t work) {
   size_t nb = (work + 4095) / 4096;
   if (nb < 1) nb = 1;
-  if (nb > 64) nb = 64;
+  if (nb > 1024) nb = 1024;
   return (int)nb;
 }
 
@@ -815,7 +826,7 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   }
   Level<T>& lc = H.lv[H.L - 1];
   MLMC_LAUNCH("coarse_setup", B * 2 * 729.0 * 8, B * 40000.0, st,
-              (k_coarse_setup<T><<<(B + 63) / 64, 64, 0, st>>>(B, lc.Kx, lc.Ky, lc.Kz, H.Lws, H.Ainv)));
+              (k_coarse_setup<T><<<(B + 3) / 4, 128, 0, st>>>(B, lc.Kx, lc.Ky, lc.Kz, H.Lws, H.Ainv)));
   const double h = 1.0 / (double)(a.n - 1);
   MLMC_LAUNCH("prepare", B * (double)l0.n3 * (a.f ? 16.0 : 8.0), B * (double)l0.n3, st,
               (k_prepare<<<g0, kThreads, 0, st>>>(a.n, B, h * h, a.f, H.g64, a.u)));

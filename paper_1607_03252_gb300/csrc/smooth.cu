@@ -49,9 +49,9 @@ struct FusedLayout {
 
 template <typename T, int BX, int BY>
 __global__ void __launch_bounds__(BX* BY)
-    k_rbgs_fused(int n, int ntx, const T* __restrict__ Kx, const T* __restrict__ Ky, const T* __restrict__ Kz,
-                 const T* __restrict__ Dinv, const T* __restrict__ g, const T* __restrict__ uin,
-                 T* __restrict__ uout, const int* __restrict__ active) {
+    k_rbgs_fused(int n, int ntx, int ntiles, int zslab, const T* __restrict__ Kx, const T* __restrict__ Ky,
+                 const T* __restrict__ Kz, const T* __restrict__ Dinv, const T* __restrict__ g,
+                 const T* __restrict__ uin, T* __restrict__ uout, const int* __restrict__ active) {
   using Lay = FusedLayout<T, BX, BY>;
   constexpr int NT = BX * BY, W2 = Lay::W2, P2 = Lay::P2, W1 = Lay::W1, P1 = Lay::P1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -59,13 +59,16 @@ __global__ void __launch_bounds__(BX* BY)
   T* red = stage + (size_t)kArrays * kSlots * P2;   // [3][P1]: plane after its red phase
   const int s = blockIdx.y;
   const int tid = threadIdx.x;
-  const int x0 = (blockIdx.x % ntx) * BX + 1, y0 = (blockIdx.x / ntx) * BY + 1;  // first owned node
+  const int tile = blockIdx.x % ntiles, slab = blockIdx.x / ntiles;
+  const int x0 = (tile % ntx) * BX + 1, y0 = (tile / ntx) * BY + 1;  // first owned node
+  // owned planes [zlo, zhi]; red is also recomputed on the planes just outside them
+  const int zlo = 1 + slab * zslab, zhi = min(n - 2, zlo + zslab - 1);
   const size_t n2 = (size_t)n * n, base = (size_t)s * n2 * n;
   if (active && !active[s]) {
-    // a finished sample keeps its iterate: carry the owned tile over to uout
+    // a finished sample keeps its iterate: carry the owned block over to uout
     const int gx = x0 + tid % BX, gy = y0 + tid / BX;
     if (gx <= n - 2 && gy <= n - 2)
-      for (int z = 1; z <= n - 2; ++z) {
+      for (int z = zlo; z <= zhi; ++z) {
         const size_t p = base + (size_t)z * n2 + (size_t)gy * n + gx;
         uout[p] = uin[p];
       }
@@ -76,6 +79,7 @@ __global__ void __launch_bounds__(BX* BY)
 
   // stage plane z of all arrays (tile + 2-ring) into its slot; zeros outside the grid
   auto issue = [&](int z) {
+    if (z < 0 || z >= n) return;
     const int slot = z & (kSlots - 1);
     for (int t = tid; t < P2; t += NT) {
       const int gx = x0 - 2 + t % W2, gy = y0 - 2 + t / W2;
@@ -98,13 +102,17 @@ __global__ void __launch_bounds__(BX* BY)
   const int o1 = (oy + 1) * W1 + (ox + 1);  // in the 1-ring plane
   T kz_m2 = T(0);                           // Kz(z-2) of the owned column
 
-  issue(0);
+  // steps z = zlo-1 .. zhi+1: red phase on plane z, black phase on plane z-1
+  const int zs = zlo - 1, ze = zhi + 1;
+  issue(zs - 1);
   cp_async_commit();
-  if (n > 1) issue(1);
+  issue(zs);
   cp_async_commit();
-  for (int z = 0; z < n; ++z) {
+  issue(zs + 1);
+  cp_async_commit();
+  for (int z = zs; z <= ze; ++z) {
     __syncthreads();  // the slot of plane z+2 (= plane z-2) is no longer read
-    if (z + 2 < n) issue(z + 2);
+    issue(z + 2);
     cp_async_commit();
     cp_async_wait1();  // planes <= z+1 have landed
     __syncthreads();
@@ -131,10 +139,10 @@ __global__ void __launch_bounds__(BX* BY)
     }
     __syncthreads();
     // black phase on plane z-1 of the owned tile, and output of plane z-1
-    if (z >= 1) {
+    if (z > zs) {
       const int zb = z - 1, sb = szm;
       const T kz_m1 = sm(3, sb, o2);  // Kz(z-1) of the owned column
-      if (zb >= 1 && zb <= n - 2 && own_in) {
+      if (zb >= zlo && zb <= zhi && own_in) {
         const T* rb = red + (size_t)(zb % 3) * P1;
         T v = rb[o1];
         if (((gxo + gyo + zb) & 1) == 1) {
@@ -151,6 +159,8 @@ __global__ void __launch_bounds__(BX* BY)
         uout[base + (size_t)zb * n2 + (size_t)gyo * n + gxo] = v;
       }
       kz_m2 = kz_m1;
+    } else {
+      kz_m2 = sm(3, szm, o2);  // Kz(zs-1): only read if zs-1 is a staged plane
     }
   }
 }
@@ -166,9 +176,17 @@ int launch_shape(int n, int B, const T* Kx, const T* Ky, const T* Kz, const T* D
     configured = true;
   }
   const int m = n - 2;
-  const int ntx = (m + BX - 1) / BX, nty = (m + BY - 1) / BY;
-  dim3 grid((unsigned)(ntx * nty), (unsigned)B);
-  k_rbgs_fused<T, BX, BY><<<grid, BX * BY, Lay::bytes, st>>>(n, ntx, Kx, Ky, Kz, Dinv, g, uin, uout, active);
+  const int ntx = (m + BX - 1) / BX, nty = (m + BY - 1) / BY, ntiles = ntx * nty;
+  // split z into independent slabs until the launch has ~12 CTAs per SM (the result is
+  // the same for any split); slabs of at least 8 planes
+  int slabs = (int)((152LL * 12 + (long long)ntiles * B - 1) / ((long long)ntiles * B));
+  if (slabs > m / 8) slabs = m / 8;
+  if (slabs < 1) slabs = 1;
+  const int zslab = (m + slabs - 1) / slabs;
+  slabs = (m + zslab - 1) / zslab;
+  dim3 grid((unsigned)(ntiles * slabs), (unsigned)B);
+  k_rbgs_fused<T, BX, BY><<<grid, BX * BY, Lay::bytes, st>>>(n, ntx, ntiles, zslab, Kx, Ky, Kz, Dinv, g, uin, uout,
+                                                             active);
   return MLMC_OK;
 }
 
