@@ -16,8 +16,11 @@
 //
 // Plane data (u, Kx, Ky, Kz, Dinv, g on the tile plus a two-cell ring) is staged in
 // shared memory with cp.async, two planes ahead of the plane being updated, in a ring
-// of four plane slots. HBM traffic per sweep is one read of each array and one write of
-// u (7 words per node), against 12+ words for two separate colour passes.
+// of five plane slots; one thread per staged column keeps the work per barrier even.
+// z is split into independent slabs (each recomputes the red plane just outside its
+// ends) so that a launch has enough CTAs. HBM traffic per sweep is one read of each
+// array and one write of u (7 words per node), against 12+ words for two separate
+// colour passes.
 #include "common.cuh"
 #include "prof.cuh"
 #include "smooth.cuh"
@@ -36,24 +39,28 @@ __device__ __forceinline__ void cp_async(double* dst, const double* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-constexpr int kSlots = 4;    // plane ring of the staged arrays
+constexpr int kSlots = 5;    // plane ring of the staged arrays (z-1 .. z+2 live, z+3 in flight)
 constexpr int kArrays = 6;   // u, Kx, Ky, Kz, Dinv, g
 
 template <typename T, int BX, int BY>
 struct FusedLayout {
-  static constexpr int W2 = BX + 4, H2 = BY + 4;  // tile + 2-ring
+  static constexpr int W2 = BX + 4, H2 = BY + 4;  // tile + 2-ring: one thread per column
   static constexpr int W1 = BX + 2, H1 = BY + 2;  // tile + 1-ring
   static constexpr int P2 = W2 * H2, P1 = W1 * H1;
+  static constexpr int threads = P2;
   static constexpr size_t bytes = sizeof(T) * ((size_t)kArrays * kSlots * P2 + 3 * (size_t)P1);
 };
 
+// One thread per column of the tile + 2-ring: every thread stages its own column of the
+// six arrays; ring-1 and tile threads compute the red update of their column; tile
+// threads compute the black update (one plane behind) and write the output.
 template <typename T, int BX, int BY>
-__global__ void __launch_bounds__(BX* BY)
+__global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads)
     k_rbgs_fused(int n, int ntx, int ntiles, int zslab, const T* __restrict__ Kx, const T* __restrict__ Ky,
                  const T* __restrict__ Kz, const T* __restrict__ Dinv, const T* __restrict__ g,
                  const T* __restrict__ uin, T* __restrict__ uout, const int* __restrict__ active) {
   using Lay = FusedLayout<T, BX, BY>;
-  constexpr int NT = BX * BY, W2 = Lay::W2, P2 = Lay::P2, W1 = Lay::W1, P1 = Lay::P1;
+  constexpr int W2 = Lay::W2, H2 = Lay::H2, P2 = Lay::P2, W1 = Lay::W1, P1 = Lay::P1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stage = (T*)smem_raw;                          // [array][slot][P2]
   T* red = stage + (size_t)kArrays * kSlots * P2;   // [3][P1]: plane after its red phase
@@ -61,13 +68,20 @@ __global__ void __launch_bounds__(BX* BY)
   const int tid = threadIdx.x;
   const int tile = blockIdx.x % ntiles, slab = blockIdx.x / ntiles;
   const int x0 = (tile % ntx) * BX + 1, y0 = (tile / ntx) * BY + 1;  // first owned node
-  // owned planes [zlo, zhi]; red is also recomputed on the planes just outside them
   const int zlo = 1 + slab * zslab, zhi = min(n - 2, zlo + zslab - 1);
   const size_t n2 = (size_t)n * n, base = (size_t)s * n2 * n;
+  // this thread's column
+  const int ci = tid % W2, cj = tid / W2;
+  const int gx = x0 - 2 + ci, gy = y0 - 2 + cj;
+  const bool in_grid = gx >= 0 && gx < n && gy >= 0 && gy < n;
+  const bool ring1 = ci >= 1 && ci <= W2 - 2 && cj >= 1 && cj <= H2 - 2;
+  const bool owned = ci >= 2 && ci <= W2 - 3 && cj >= 2 && cj <= H2 - 3;
+  const bool interior_col = gx >= 1 && gx <= n - 2 && gy >= 1 && gy <= n - 2;
+  const int c = tid;                                   // position in the 2-ring plane
+  const int c1 = (cj - 1) * W1 + (ci - 1);             // position in the 1-ring plane (ring1 only)
   if (active && !active[s]) {
     // a finished sample keeps its iterate: carry the owned block over to uout
-    const int gx = x0 + tid % BX, gy = y0 + tid / BX;
-    if (gx <= n - 2 && gy <= n - 2)
+    if (owned && interior_col)
       for (int z = zlo; z <= zhi; ++z) {
         const size_t p = base + (size_t)z * n2 + (size_t)gy * n + gx;
         uout[p] = uin[p];
@@ -76,31 +90,20 @@ __global__ void __launch_bounds__(BX* BY)
   }
   const T* src[kArrays] = {uin, Kx, Ky, Kz, Dinv, g};
   auto sm = [&](int a, int slot, int i) -> T& { return stage[((size_t)a * kSlots + slot) * P2 + i]; };
-
-  // stage plane z of all arrays (tile + 2-ring) into its slot; zeros outside the grid
+  const size_t col = base + (size_t)gy * n + gx;
   auto issue = [&](int z) {
     if (z < 0 || z >= n) return;
-    const int slot = z & (kSlots - 1);
-    for (int t = tid; t < P2; t += NT) {
-      const int gx = x0 - 2 + t % W2, gy = y0 - 2 + t / W2;
-      if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
-        const size_t off = base + (size_t)z * n2 + (size_t)gy * n + gx;
+    const int slot = z % kSlots;
+    if (in_grid) {
+      const size_t off = col + (size_t)z * n2;
 #pragma unroll
-        for (int a = 0; a < kArrays; ++a) cp_async(&sm(a, slot, t), src[a] + off);
-      } else {
+      for (int a = 0; a < kArrays; ++a) cp_async(&sm(a, slot, c), src[a] + off);
+    } else {
 #pragma unroll
-        for (int a = 0; a < kArrays; ++a) sm(a, slot, t) = T(0);
-      }
+      for (int a = 0; a < kArrays; ++a) sm(a, slot, c) = T(0);
     }
   };
-
-  // owned tile position of this thread (black phase / output)
-  const int ox = tid % BX, oy = tid / BX;
-  const int gxo = x0 + ox, gyo = y0 + oy;
-  const bool own_in = gxo <= n - 2 && gyo <= n - 2;
-  const int o2 = (oy + 2) * W2 + (ox + 2);  // in the 2-ring plane
-  const int o1 = (oy + 1) * W1 + (ox + 1);  // in the 1-ring plane
-  T kz_m2 = T(0);                           // Kz(z-2) of the owned column
+  T kz_m2 = T(0);  // Kz(z-2) of this column
 
   // steps z = zlo-1 .. zhi+1: red phase on plane z, black phase on plane z-1
   const int zs = zlo - 1, ze = zhi + 1;
@@ -111,21 +114,16 @@ __global__ void __launch_bounds__(BX* BY)
   issue(zs + 1);
   cp_async_commit();
   for (int z = zs; z <= ze; ++z) {
-    __syncthreads();  // the slot of plane z+2 (= plane z-2) is no longer read
+    // slot of plane z+2 held plane z-3, last read before the previous step's barriers
     issue(z + 2);
     cp_async_commit();
-    cp_async_wait1();  // planes <= z+1 have landed
-    __syncthreads();
-    const int sz = z & (kSlots - 1), szm = (z + kSlots - 1) & (kSlots - 1), szp = (z + 1) & (kSlots - 1);
+    cp_async_wait1();  // planes <= z+1 of this thread's column have landed
+    __syncthreads();   // ... and of every column
+    const int sz = z % kSlots, szm = (z + kSlots - 1) % kSlots, szp = (z + 1) % kSlots;
     T* rz = red + (size_t)(z % 3) * P1;
-    // red phase on the tile + 1-ring: red interior nodes get their new value, all
-    // others keep the old one
-    for (int t = tid; t < P1; t += NT) {
-      const int i1 = t % W1, j1 = t / W1;
-      const int gx = x0 - 1 + i1, gy = y0 - 1 + j1;
-      const int c = (j1 + 1) * W2 + (i1 + 1);
+    if (ring1) {
       T v = sm(0, sz, c);
-      if (z >= 1 && z <= n - 2 && gx >= 1 && gx <= n - 2 && gy >= 1 && gy <= n - 2 && ((gx + gy + z) & 1) == 0) {
+      if (z >= 1 && z <= n - 2 && interior_col && ((gx + gy + z) & 1) == 0) {
         T acc = sm(5, sz, c);
         acc = fma(sm(1, sz, c - 1), sm(0, sz, c - 1), acc);
         acc = fma(sm(1, sz, c), sm(0, sz, c + 1), acc);
@@ -135,32 +133,31 @@ __global__ void __launch_bounds__(BX* BY)
         acc = fma(sm(3, sz, c), sm(0, szp, c), acc);
         v = acc * sm(4, sz, c);
       }
-      rz[t] = v;
+      rz[c1] = v;
     }
     __syncthreads();
-    // black phase on plane z-1 of the owned tile, and output of plane z-1
     if (z > zs) {
       const int zb = z - 1, sb = szm;
-      const T kz_m1 = sm(3, sb, o2);  // Kz(z-1) of the owned column
-      if (zb >= zlo && zb <= zhi && own_in) {
+      const T kz_m1 = sm(3, sb, c);  // Kz(z-1) of this column
+      if (owned && interior_col && zb >= zlo && zb <= zhi) {
         const T* rb = red + (size_t)(zb % 3) * P1;
-        T v = rb[o1];
-        if (((gxo + gyo + zb) & 1) == 1) {
+        T v = rb[c1];
+        if (((gx + gy + zb) & 1) == 1) {
           const T* rbm = red + (size_t)((zb + 2) % 3) * P1;  // plane z-2
-          T acc = sm(5, sb, o2);
-          acc = fma(sm(1, sb, o2 - 1), rb[o1 - 1], acc);
-          acc = fma(sm(1, sb, o2), rb[o1 + 1], acc);
-          acc = fma(sm(2, sb, o2 - W2), rb[o1 - W1], acc);
-          acc = fma(sm(2, sb, o2), rb[o1 + W1], acc);
-          acc = fma(kz_m2, rbm[o1], acc);
-          acc = fma(kz_m1, rz[o1], acc);
-          v = acc * sm(4, sb, o2);
+          T acc = sm(5, sb, c);
+          acc = fma(sm(1, sb, c - 1), rb[c1 - 1], acc);
+          acc = fma(sm(1, sb, c), rb[c1 + 1], acc);
+          acc = fma(sm(2, sb, c - W2), rb[c1 - W1], acc);
+          acc = fma(sm(2, sb, c), rb[c1 + W1], acc);
+          acc = fma(kz_m2, rbm[c1], acc);
+          acc = fma(kz_m1, rz[c1], acc);
+          v = acc * sm(4, sb, c);
         }
-        uout[base + (size_t)zb * n2 + (size_t)gyo * n + gxo] = v;
+        uout[col + (size_t)zb * n2] = v;
       }
       kz_m2 = kz_m1;
     } else {
-      kz_m2 = sm(3, szm, o2);  // Kz(zs-1): only read if zs-1 is a staged plane
+      kz_m2 = sm(3, szm, c);  // Kz(zs-1): only used when zs-1 is a staged plane
     }
   }
 }
@@ -185,8 +182,8 @@ int launch_shape(int n, int B, const T* Kx, const T* Ky, const T* Kz, const T* D
   const int zslab = (m + slabs - 1) / slabs;
   slabs = (m + zslab - 1) / zslab;
   dim3 grid((unsigned)(ntiles * slabs), (unsigned)B);
-  k_rbgs_fused<T, BX, BY><<<grid, BX * BY, Lay::bytes, st>>>(n, ntx, ntiles, zslab, Kx, Ky, Kz, Dinv, g, uin, uout,
-                                                             active);
+  k_rbgs_fused<T, BX, BY><<<grid, Lay::threads, Lay::bytes, st>>>(n, ntx, ntiles, zslab, Kx, Ky, Kz, Dinv, g, uin,
+                                                                  uout, active);
   return MLMC_OK;
 }
 
