@@ -371,20 +371,9 @@ def merge_records(parts):
     """Chan's merge of per-rank (N, mean, M2) rows per level."""
     import numpy as np
 
-    out = []
-    for l in range(parts[0].shape[0]):
-        n, mean, m2 = 0.0, 0.0, 0.0
-        for p in parts:
-            nb, mb, m2b = p[l]
-            if nb == 0:
-                continue
-            tot = n + nb
-            d = mb - mean
-            mean = mean + d * nb / tot
-            m2 = m2 + m2b + d * d * n * nb / tot
-            n = tot
-        out.append((n, mean, m2))
-    return np.array(out)
+    from paper_1607_03252_gb300.stats import merge_levels
+
+    return np.array(merge_levels([[tuple(row) for row in p] for p in parts]))
 
 
 def roofline(prof, peaks):

@@ -227,6 +227,69 @@ int64_t mlmc_profile_total_launches(void);
 int mlmc_profile_get(int index, char* name, int name_len, int64_t* launches, int64_t* timed_launches, double* ms,
                      double* bytes, double* flops);
 
+/*
+ * Solve service with continuous batching (the single-GPU counterpart of the paper's
+ * schedulers, Secs. 4-5, whose dynamic variants hand the next sample to whichever
+ * process group is free). Requests (level, realisation id) are queued per level;
+ * `workers` host threads, each with its own CUDA stream, repeatedly take the level
+ * whose oldest request has waited longest, batch up to max_batch requests of it (fewer
+ * once the oldest has waited batch_wait_ms), admit the batch only while the device
+ * bytes of all running batches stay within hbm_budget_bytes, and run the level pipeline
+ * for it. A request's result does not depend on its batch. All requests share the
+ * service's field and solver configuration.
+ */
+typedef struct {
+  mlmc_field_cfg field;
+  mg_cfg mg;
+  int n0;                  /* nodes per axis of level 0 */
+  int max_level;           /* levels 0..max_level accepted (fine grid <= 1025) */
+  int max_batch;           /* samples per batch, 1..65535 */
+  int workers;             /* concurrent batches (streams), 1..16 */
+  int queue_capacity;      /* pending requests before mlmc_submit returns MLMC_ERR_BUSY */
+  size_t hbm_budget_bytes; /* device bytes the running batches may hold together */
+  double batch_wait_ms;    /* longest wait for batch-mates before a partial batch runs */
+} mlmc_service_cfg;
+
+typedef struct {
+  int level;
+  uint64_t sample_id;
+} mlmc_request;
+
+typedef struct {
+  int status;          /* MLMC_PENDING, MLMC_OK, or an MLMC_ERR_* of the batch */
+  int level;
+  uint64_t sample_id;
+  double Y, Qf, Qc;    /* Y = Qf - Qc; Qc = 0 on level 0 */
+  int cycles_fine, cycles_coarse;
+  double t_submit, t_start, t_done; /* host steady-clock seconds */
+} mlmc_result;
+
+typedef struct {
+  int64_t submitted, completed, rejected, pending;
+  int inflight_batches;
+  size_t bytes_in_use;
+  double samples_per_s;      /* completed / (last completion - first submission) */
+  int64_t count[9];          /* completed requests per level */
+  double p50_ms[9], p99_ms[9]; /* latency (done - submit) per level */
+} mlmc_service_report;
+
+typedef struct mlmc_service mlmc_service;
+
+/* Starts the worker threads on the current device; NULL on invalid cfg (see
+ * mlmc_last_error_string). */
+mlmc_service* mlmc_service_create(const mlmc_service_cfg* cfg);
+/* Stops after the running batches finish; queued requests are dropped. */
+void mlmc_service_destroy(mlmc_service* svc);
+/* Non-blocking. MLMC_ERR_BUSY when queue_capacity requests are pending (backpressure);
+ * MLMC_ERR_INVALID for a level outside 0..max_level. */
+int mlmc_submit(mlmc_service* svc, const mlmc_request* req, uint64_t* ticket);
+/* MLMC_PENDING while queued or running; MLMC_OK once (the result is then released);
+ * MLMC_ERR_NOT_FOUND for an unknown or already delivered ticket. */
+int mlmc_poll(mlmc_service* svc, uint64_t ticket, mlmc_result* res);
+/* Blocks up to timeout_ms; MLMC_ERR_TIMEOUT if still pending. */
+int mlmc_wait(mlmc_service* svc, uint64_t ticket, double timeout_ms, mlmc_result* res);
+int mlmc_service_stats(mlmc_service* svc, mlmc_service_report* out);
+
 /* One measurement of mlmc_autotune. */
 typedef struct {
   int smoother;              /* MLMC_SMOOTH_* */

@@ -89,6 +89,30 @@ class LevelStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServiceCfg(ctypes.Structure):
+    _fields_ = [("field", FieldCfg), ("mg", MgCfg), ("n0", ctypes.c_int), ("max_level", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("workers", ctypes.c_int), ("queue_capacity", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("batch_wait_ms", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("sample_id", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("level", ctypes.c_int), ("sample_id", ctypes.c_uint64),
+                ("Y", ctypes.c_double), ("Qf", ctypes.c_double), ("Qc", ctypes.c_double),
+                ("cycles_fine", ctypes.c_int), ("cycles_coarse", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServiceReport(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("inflight_batches", ctypes.c_int), ("bytes_in_use", ctypes.c_size_t),
+                ("samples_per_s", ctypes.c_double), ("count", ctypes.c_int64 * 9), ("p50_ms", ctypes.c_double * 9),
+                ("p99_ms", ctypes.c_double * 9)]
+
+
 class TuneEntry(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("nu", ctypes.c_int), ("seconds_per_sample", ctypes.c_double),
                 ("mean_cycles", ctypes.c_double)]
@@ -110,6 +134,12 @@ SIGNATURES = {
                                            _dp, _dp, _dp, ctypes.POINTER(LevelStats)]),
     "mlmc_level_run": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp,
                                       ctypes.POINTER(LevelStats)]),
+    "mlmc_service_create": (ctypes.c_void_p, [ctypes.POINTER(ServiceCfg)]),
+    "mlmc_service_destroy": (None, [ctypes.c_void_p]),
+    "mlmc_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "mlmc_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]),
+    "mlmc_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(Result)]),
+    "mlmc_service_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServiceReport)]),
     "mlmc_autotune": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                      ctypes.POINTER(TuneEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -308,3 +338,56 @@ def make_mlmc_cfg(run_seed, sigma2, ell, M, n0=17, nu1=2, nu2=2, rtol=1e-10, max
         sp = ctypes.c_void_p(stream.cuda_stream)
     return MlmcCfg(field_cfg(run_seed, sigma2, ell, M),
                    mg_cfg(nu1, nu2, rtol, max_cycles, precision, smoother, accel), int(n0), int(max_batch), sp)
+
+
+class Service:
+    """Thin wrapper of the mlmc_service_* calls (continuous-batching solve service)."""
+
+    def __init__(self, field, mg, n0=17, max_level=4, max_batch=64, workers=2, queue_capacity=100000,
+                 hbm_budget_bytes=64 << 30, batch_wait_ms=2.0):
+        self.cfg = ServiceCfg(field, mg, int(n0), int(max_level), int(max_batch), int(workers), int(queue_capacity),
+                              int(hbm_budget_bytes), float(batch_wait_ms))
+        self.h = lib().mlmc_service_create(ctypes.byref(self.cfg))
+        if not self.h:
+            raise MlmcError(MLMC_ERR_INVALID, "mlmc_service_create", lib().mlmc_last_error_string().decode())
+
+    def submit(self, level, sample_id):
+        """Returns a ticket, or None when the queue is full (MLMC_ERR_BUSY)."""
+        t = ctypes.c_uint64()
+        st = lib().mlmc_submit(self.h, ctypes.byref(Request(int(level), int(sample_id))), ctypes.byref(t))
+        if st == MLMC_ERR_BUSY:
+            return None
+        _check(st, "mlmc_submit")
+        return t.value
+
+    def poll(self, ticket):
+        """(status, Result): status MLMC_PENDING or MLMC_OK."""
+        r = Result()
+        st = lib().mlmc_poll(self.h, int(ticket), ctypes.byref(r))
+        if st < 0:
+            _check(st, "mlmc_poll")
+        return st, r
+
+    def wait(self, ticket, timeout_ms=60000.0):
+        r = Result()
+        st = lib().mlmc_wait(self.h, int(ticket), float(timeout_ms), ctypes.byref(r))
+        if st == MLMC_ERR_TIMEOUT:
+            return st, r
+        _check(st, "mlmc_wait")
+        return st, r
+
+    def report(self):
+        r = ServiceReport()
+        _check(lib().mlmc_service_stats(self.h, ctypes.byref(r)), "mlmc_service_stats")
+        return r
+
+    def close(self):
+        if self.h:
+            lib().mlmc_service_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

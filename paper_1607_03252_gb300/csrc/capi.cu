@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "field.cuh"
 #include "mg.cuh"
+#include "level.cuh"
 #include "prof.cuh"
 #include "tune.cuh"
 
@@ -236,6 +237,37 @@ struct LevelBatch {
     return MLMC_OK;
   }
 };
+
+int validate_level_cfg(const mlmc_field_cfg& fc, const mg_cfg& mc) {
+  MLMC_TRY(check_field(&fc));
+  MLMC_TRY(check_mg(&mc));
+  return MLMC_OK;
+}
+
+size_t level_batch_bytes(int b, int nf, int nc, int M, int precision, int accel) {
+  return LevelBatch::bytes_for(b, nf, nc, M, precision, accel);
+}
+
+int run_level_batch_host(const mlmc_field_cfg& fc, const mg_cfg& mc, int nf, int nc, const uint64_t* ids_host,
+                         int b, double* Qf, double* Qc, int* cyc_f, int* cyc_c, int* n_unconv, cudaStream_t st) {
+  LevelBatch lb;
+  MLMC_TRY(lb.init(b, nf, nc, fc.M, mc.precision, mc.accel, st));
+  MLMC_CUDA_TRY(cudaMemcpyAsync(lb.ids.get(), ids_host, (size_t)b * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  double* qf = lb.Q.as<double>();
+  double* qc = nc ? lb.Q.as<double>() + b : nullptr;
+  MLMC_TRY(lb.run(fc, mc, lb.ids.as<uint64_t>(), b, qf, qc, nullptr, n_unconv, st));
+  MLMC_CUDA_TRY(cudaMemcpyAsync(Qf, qf, (size_t)b * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (qc) MLMC_CUDA_TRY(cudaMemcpyAsync(Qc, qc, (size_t)b * sizeof(double), cudaMemcpyDeviceToHost, st));
+  MLMC_CUDA_TRY(cudaMemcpyAsync(cyc_f, lb.cyc.as<int>(), (size_t)b * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (nc) MLMC_CUDA_TRY(cudaMemcpyAsync(cyc_c, lb.cyc.as<int>() + b, (size_t)b * sizeof(int), cudaMemcpyDeviceToHost, st));
+  MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!nc)
+    for (int i = 0; i < b; ++i) {
+      Qc[i] = 0.0;
+      cyc_c[i] = 0;
+    }
+  return MLMC_OK;
+}
 
 static void fill_stats(const LevelRecord& r, double secs, mlmc_level_stats* out) {
   if (!out) return;
