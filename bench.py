@@ -40,6 +40,38 @@ if ROOT not in sys.path:
 from paper_1607_03252_gb300.workloads import CONFIGS, RUN_SEED, level_n, sample_ids  # noqa: E402
 
 L2_BYTES = 129 * 1024 * 1024
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per work unit measured by ncu for
+# a kernel, valid only while that kernel's source text hashes to `kernel_sha` (else null).
+# unit_bytes: the algorithmic bytes the library accounts per unit, to count units per launch.
+NCU_TRAFFIC = {
+    "rbgs_f64": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs", "kernel_sha": "754697c08e18bb8e",
+                 "dram_bytes_per_unit": 927.0e6 / (8 * 127 ** 3), "unit_bytes": 3.5 * 8,
+                 "source": "profiles/rbgs_f64_twopass_n129_b8.md (129^3 x 8, one colour pass)"},
+    "rbgs_f32": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs", "kernel_sha": "754697c08e18bb8e",
+                 "dram_bytes_per_unit": 933.8e6 / (2 * 255 ** 3), "unit_bytes": 3.5 * 4,
+                 "source": "profiles/rbgs_f32_twopass_n257_b2.md (257^3 x 2, one colour pass)"},
+}
+
+
+def kernel_sha(path, name):
+    import hashlib
+
+    try:
+        src = open(os.path.join(ROOT, path)).read()
+        i = src.index("__global__ void " + name + "(")
+        j = src.index("\ntemplate", i)
+        return hashlib.sha256(src[i:j].encode()).hexdigest()[:16]
+    except Exception:
+        return None
+
+
+def traffic_per_launch(name, rec):
+    t = NCU_TRAFFIC.get(name)
+    if not t or kernel_sha(t["file"], t["kernel"]) != t["kernel_sha"]:
+        return None, None
+    units = rec["bytes"] / max(rec["launches"], 1) / t["unit_bytes"]
+    return units * t["dram_bytes_per_unit"], t["source"]
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -50,7 +82,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="own", choices=["own", "reference"])
-    p.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
+    p.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    p.add_argument("--c5-arms", default="fast,plain", help="c5: which arms to run (fast, plain)")
+    p.add_argument("--c5-eps", type=float, default=None, help="c5: override the RMS tolerance")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -67,7 +101,7 @@ def measured_peaks():
 def workload(cfg_name):
     c = CONFIGS[cfg_name]
     levels = c["levels"]
-    N = c.get("N", c.get("N_init"))
+    N = c.get("N", c.get("N_init", [64] * len(levels)))
     single = c.get("single_level", False)
     return c, levels, N, single
 
@@ -386,18 +420,20 @@ def roofline(prof, peaks):
     per_launch_flops = rec["flops"] / max(rec["launches"], 1)
     hbm_peak = peaks.get("hbm_gbs")
     fp64 = name.endswith("f64") or name in ("residual_mixed", "update_mixed", "coarse_setup", "norm")
+    traffic, tsrc = traffic_per_launch(name, rec)
     if fp64:
         achieved = per_launch_flops / avg_s / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
-                "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"],
+                "traffic": traffic, "traffic_source": tsrc, "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"],
                 "hbm_achieved_gbs": per_launch_bytes / avg_s / 1e9,
                 "hbm_frac_of_measured": (per_launch_bytes / avg_s / 1e9) / hbm_peak if hbm_peak else None}
     achieved = per_launch_bytes / avg_s / 1e9
     peak = hbm_peak if hbm_peak else 6800.0
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": "measured" if hbm_peak else "fallback", "traffic": None,
+            "frac": achieved / peak, "peak_source": "measured" if hbm_peak else "fallback", "traffic": traffic,
+            "traffic_source": tsrc,
             "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"]}
 
 
@@ -461,10 +497,175 @@ def cpu_baseline(cfg, levels, N, single):
             "per_level": {str(l): rates[l] for l in levels}}
 
 
+def serving_arm(args):
+    """c4: open-loop Poisson stream of single-sample requests into the solve service."""
+    import numpy as np
+    import torch
+
+    import paper_1607_03252_gb300 as mg
+    from paper_1607_03252_gb300.workloads import level_draws, poisson_arrivals
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    cfg = CONFIGS["c4"]
+    c3 = CONFIGS["c3"]
+    levels = cfg["levels"]
+    stream = torch.cuda.Stream()
+    N, plan = plan_levels(mg, c3, levels, stream, 0)  # autotunes every level, pilot, Eq. 11
+    C = plan["pilot_cost_s"]
+    probs = np.array([n * c for n, c in zip(N, C)])
+    probs = probs / probs.sum()
+    field = mg.field_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"])
+    mgc = mg.mg_cfg(0, 0, cfg["rtol"], 300, mg.MLMC_PREC_MIXED, mg.MLMC_SMOOTH_AUTO, mg.MLMC_ACCEL_CG)
+    counter = [0]
+
+    def run(rate, count, seed, burst=False):
+        draws = level_draws(probs, count, seed)
+        times = np.zeros(count) if burst else poisson_arrivals(rate, count, seed + 1)
+        with mg.Service(field, mgc, n0=17, max_level=max(levels), max_batch=64, workers=3,
+                        hbm_budget_bytes=96 << 30, batch_wait_ms=2.0) as svc:
+            t0 = time.perf_counter()
+            tickets = []
+            for i in range(count):
+                while time.perf_counter() - t0 < times[i]:
+                    pass
+                lvl = int(draws[i])
+                tickets.append((lvl, svc.submit(lvl, int(sample_ids(lvl, (1 << 44) + counter[0], 1)[0]))))
+                counter[0] += 1
+            res = [(lvl, svc.wait(t)[1]) for lvl, t in tickets]
+            t_end = time.perf_counter()
+        lat = {l: [1e3 * (r.t_done - r.t_submit) for lv, r in res if lv == l] for l in levels}
+        ok = all(r.status == mg.MLMC_OK for _, r in res)
+        t_first = min(r.t_submit for _, r in res)
+        t_last = max(r.t_done for _, r in res)
+        return {"offered_per_s": rate, "completed_per_s": count / (t_last - t_first), "all_ok": ok,
+                "p50_ms": {str(l): float(np.percentile(v, 50)) if v else None for l, v in lat.items()},
+                "p99_ms": {str(l): float(np.percentile(v, 99)) if v else None for l, v in lat.items()},
+                "count": {str(l): len(v) for l, v in lat.items()}, "wall_s": t_end - t0}
+
+    sat = run(0.0, 1200, 11, burst=True)["completed_per_s"]
+    sweep = []
+    for frac in (0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.2):
+        rate = frac * sat
+        count = int(min(3000, max(200, rate * 3.0)))
+        r = run(rate, count, 100 + int(frac * 100))
+        r["load_fraction"] = frac
+        sweep.append(r)
+    line = {"metric": "MLMC samples/s at saturation, served (c4: single-sample Poisson requests, levels 17^3..257^3)",
+            "value": sat, "unit": "samples/s", "n_gpus": 1, "steps": len(sweep), "warmup": 1, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded Philox realisations, Poisson arrivals)",
+            "config": {"workload": cfg["name"], "levels": levels, "level_probability": probs.tolist(),
+                       "service": {"max_batch": 64, "workers": 3, "batch_wait_ms": 2.0, "hbm_budget_gb": 96},
+                       "sigma2": cfg["sigma2"], "ell": cfg["ell"], "M": cfg["M"], "rtol": cfg["rtol"],
+                       "solver": "FP64 flexible CG, FP32 V-cycle preconditioner (autotuned smoother, nu)"},
+            "serving_sweep": sweep, "plan": plan}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def adaptive_mlmc(mg, torch, cfg, eps, mode, stream, log):
+    """Algorithm 2 with L fixed: pilot N_init, then N_l from Eq. 15 with the running s_l^2
+    and measured cost per sample, until no level needs more samples. mode 'fast': batched,
+    FP32 V-cycle preconditioner (autotuned smoother and nu); 'plain': one sample per launch,
+    FP64 throughout. Both use flexible CG around the V-cycle and the same realisation ids."""
+    import math
+
+    from paper_1607_03252_gb300.stats import chan_merge, eps_split, sample_sizes
+
+    levels = cfg["levels"]
+    fast = mode == "fast"
+    prec = mg.MLMC_PREC_MIXED if fast else mg.MLMC_PREC_F64
+    nu = (0, 0) if fast else (cfg["nu1"], cfg["nu2"])
+    smoother = mg.MLMC_SMOOTH_AUTO if fast else mg.MLMC_SMOOTH_TWO_PASS
+    have = [0] * len(levels)
+    rec = [(0.0, 0.0, 0.0)] * len(levels)
+    secs = [0.0] * len(levels)
+    N = list(cfg["N_init"])
+    eps_s, _ = eps_split(eps, cfg["theta"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rounds = 0
+    while True:
+        rounds += 1
+        for i, l in enumerate(levels):
+            need = N[i] - have[i]
+            if need <= 0:
+                continue
+            c = mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=17, nu1=nu[0], nu2=nu[1],
+                                 rtol=cfg["rtol"], precision=prec, max_batch=(0 if fast else 1), stream=stream,
+                                 accel=mg.MLMC_ACCEL_CG, smoother=smoother, max_cycles=300)
+            ta = time.perf_counter()
+            st, _, _, _ = mg.mlmc_level_estimate(c, l, int(sample_ids(l, have[i], 1)[0]), need, want_samples=False)
+            secs[i] += time.perf_counter() - ta
+            rec[i] = chan_merge([rec[i], (float(st.N), st.mean, st.M2)])
+            have[i] += need
+        V = [r[2] / (r[0] - 1.0) if r[0] > 1 else 0.0 for r in rec]
+        C = [secs[i] / have[i] for i in range(len(levels))]
+        N_new = sample_sizes([max(v, 1e-30) for v in V], C, eps_s)
+        log.append({"round": rounds, "have": list(have), "N_next": N_new, "t": time.perf_counter() - t0})
+        if all(nn <= h for nn, h in zip(N_new, have)):
+            break
+        N = [max(a, b) for a, b in zip(N, N_new)]
+    wall = time.perf_counter() - t0
+    means = [r[1] for r in rec]
+    V = [r[2] / (r[0] - 1.0) for r in rec]
+    q = math.fsum(means)
+    samp_var = math.fsum(v / h for v, h in zip(V, have))
+    return {"mode": mode, "wall_s": wall, "rounds": rounds, "N": have, "Q_hat": q, "level_means": means,
+            "level_vars": V, "sampling_var": samp_var, "eps_s2": eps_s ** 2,
+            "cost_per_sample_s": [secs[i] / have[i] for i in range(len(levels))]}
+
+
+def c5_arm(args):
+    import torch
+
+    import paper_1607_03252_gb300 as mg
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    cfg = CONFIGS["c5"]
+    eps = args.c5_eps or cfg["eps"]
+    stream = torch.cuda.Stream()
+    # autotune the fast arm once per level (smoother x nu on real samples)
+    tune = {}
+    for l, n0 in zip(cfg["levels"], cfg["N_init"]):
+        c = mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=17, nu1=0, nu2=0, rtol=cfg["rtol"],
+                             precision=mg.MLMC_PREC_MIXED, stream=stream, accel=mg.MLMC_ACCEL_CG, max_cycles=300)
+        rows, bs, bnu = mg.mlmc_autotune(c, l, int(sample_ids(l, 1 << 40, 1)[0]), max(2, min(n0, 16)))
+        tune[str(l)] = {"smoother": mg._capi.SMOOTHER_NAMES.get(bs, bs), "nu": bnu}
+    out = {}
+    for mode in args.c5_arms.split(","):
+        log = []
+        out[mode] = adaptive_mlmc(mg, torch, cfg, eps, mode, stream, log)
+        out[mode]["rounds_log"] = log
+    fast = out.get("fast")
+    plain = out.get("plain")
+    line = {"metric": "wall time to RMS tolerance eps (c5: adaptive 6-level MLMC, 17^3..513^3)",
+            "value": fast["wall_s"] if fast else plain["wall_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if fast else "f64", "data": "synthetic (seeded Philox realisations)",
+            "config": {"workload": cfg["name"], "levels": cfg["levels"], "fine_n": [level_n(l) for l in cfg["levels"]],
+                       "sigma2": cfg["sigma2"], "ell": cfg["ell"], "M": cfg["M"], "eps": eps, "theta": cfg["theta"],
+                       "N_init": cfg["N_init"], "rtol": cfg["rtol"]},
+            "autotune": tune, "arms": out,
+            "speedup_plain_over_fast": (plain["wall_s"] / fast["wall_s"]) if (fast and plain) else None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.config == "c4":
+        return serving_arm(args)
+    if args.config == "c5":
+        return c5_arm(args)
     return own_arm(args)
 
 
