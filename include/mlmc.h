@@ -88,6 +88,9 @@ typedef struct {
 #define MLMC_SMOOTH_FUSED_32x8 2  /* both colours in one z-marching pass, 32x8 x-y tiles */
 #define MLMC_SMOOTH_FUSED_32x16 3
 #define MLMC_SMOOTH_FUSED_64x8 4
+#define MLMC_SMOOTH_BULK_32x8 5   /* fused, plane rows staged by TMA bulk copies on mbarriers */
+#define MLMC_SMOOTH_BULK_32x16 6
+#define MLMC_SMOOTH_BULK_64x8 7
 
 /* Outer iteration around the V-cycle. */
 #define MLMC_ACCEL_NONE 0 /* stationary: repeat V-cycles (FP64), or FP32 V-cycles as corrections of
@@ -150,7 +153,7 @@ int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const d
  * The workspace is a fixed 32 MiB array in the library's device image (every GPU that
  * loads the library keeps it until the process exits); the call makes no cudaMalloc,
  * cudaMallocAsync or cudaFree and no torch allocation. Sizes whose workspace exceeds
- * 32 MiB (about 85 samples at 17^3, 12 at 33^3, 1 at 65^3 in FP64) return
+ * 32 MiB (about 75 samples at 17^3, 11 at 33^3, 1 at 65^3 in FP64) return
  * MLMC_ERR_INVALID with the required size in mlmc_last_error_string().
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * once for that device; make that first call before any stream capture.
@@ -300,7 +303,8 @@ typedef struct {
 
 /*
  * mlmc_autotune -- picks the smoother implementation (two-pass, or fused with 32x8,
- * 32x16 or 64x8 tiles) and the sweep count nu in {1,2,3} of V(nu, nu) for MLMC level
+ * 32x16 or 64x8 tiles staged by cp.async or by TMA bulk copies) and the sweep count
+ * nu in {1,2,3} of V(nu, nu) for MLMC level
  * `level` under cfg (no counterpart in the paper; the paper fixes its cycle, Sec. 7.1).
  * Each candidate runs the whole level pipeline once untimed and once timed on
  * `samples` realisations first_id .. first_id + samples - 1; the fastest by wall time

@@ -57,6 +57,9 @@ MLMC_SMOOTH_TWO_PASS = 1
 MLMC_SMOOTH_FUSED_32x8 = 2
 MLMC_SMOOTH_FUSED_32x16 = 3
 MLMC_SMOOTH_FUSED_64x8 = 4
+MLMC_SMOOTH_BULK_32x8 = 5
+MLMC_SMOOTH_BULK_32x16 = 6
+MLMC_SMOOTH_BULK_64x8 = 7
 
 
 MLMC_ACCEL_NONE = 0
@@ -288,15 +291,17 @@ def mlmc_level_run(cfg: MlmcCfg, level: int, ids_dev, Y_dev=None, Qf_dev=None, Q
 
 
 SMOOTHER_NAMES = {MLMC_SMOOTH_TWO_PASS: "two-pass", MLMC_SMOOTH_FUSED_32x8: "fused 32x8",
-                  MLMC_SMOOTH_FUSED_32x16: "fused 32x16", MLMC_SMOOTH_FUSED_64x8: "fused 64x8"}
+                  MLMC_SMOOTH_FUSED_32x16: "fused 32x16", MLMC_SMOOTH_FUSED_64x8: "fused 64x8",
+                  MLMC_SMOOTH_BULK_32x8: "bulk 32x8", MLMC_SMOOTH_BULK_32x16: "bulk 32x16",
+                  MLMC_SMOOTH_BULK_64x8: "bulk 64x8"}
 
 
 def mlmc_autotune(cfg: MlmcCfg, level: int, first_id: int, samples: int):
     """Returns (table as list of dicts, best smoother, best nu); the choice is stored
     for the level's fine grid in the library's tuning table."""
-    tab = (TuneEntry * 12)()
+    tab = (TuneEntry * 24)()
     cnt, bs, bnu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(lib().mlmc_autotune(ctypes.byref(cfg), int(level), int(first_id), int(samples), tab, 12,
+    _check(lib().mlmc_autotune(ctypes.byref(cfg), int(level), int(first_id), int(samples), tab, 24,
                                ctypes.byref(cnt), ctypes.byref(bs), ctypes.byref(bnu)), "mlmc_autotune")
     rows = [dict(smoother=SMOOTHER_NAMES.get(t.smoother, t.smoother), nu=t.nu,
                  ms_per_sample=1e3 * t.seconds_per_sample, cycles=t.mean_cycles) for t in tab[:cnt.value]]

@@ -55,7 +55,7 @@ static int check_mg(const mg_cfg* c) {
     set_error("nu1=%d nu2=%d out of range 0..8 (both 0: tuned count)", c->nu1, c->nu2);
     return MLMC_ERR_INVALID;
   }
-  if (c->smoother < MLMC_SMOOTH_AUTO || c->smoother > MLMC_SMOOTH_FUSED_64x8) {
+  if (c->smoother < MLMC_SMOOTH_AUTO || c->smoother > MLMC_SMOOTH_BULK_64x8) {
     set_error("unknown smoother %d", c->smoother);
     return MLMC_ERR_INVALID;
   }
@@ -481,14 +481,15 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   cudaStream_t st = (cudaStream_t)cfg->stream;
   int B = 0;
   MLMC_TRY(choose_batch(cfg, samples, nf, nc, &B));
-  const int smoothers[4] = {MLMC_SMOOTH_TWO_PASS, MLMC_SMOOTH_FUSED_32x8, MLMC_SMOOTH_FUSED_32x16,
-                            MLMC_SMOOTH_FUSED_64x8};
+  const int smoothers[7] = {MLMC_SMOOTH_TWO_PASS,   MLMC_SMOOTH_FUSED_32x8, MLMC_SMOOTH_FUSED_32x16,
+                            MLMC_SMOOTH_FUSED_64x8, MLMC_SMOOTH_BULK_32x8,  MLMC_SMOOTH_BULK_32x16,
+                            MLMC_SMOOTH_BULK_64x8};
   std::vector<uint64_t> ids(samples);
   for (int i = 0; i < samples; ++i) ids[i] = first_id + (uint64_t)i;
   int count = 0, bs = MLMC_SMOOTH_TWO_PASS, bnu = 2;
   double best = 1e300;
   for (int nu = 1; nu <= 3; ++nu)
-    for (int si = 0; si < 4; ++si) {
+    for (int si = 0; si < 7; ++si) {
       mg_cfg mc = cfg->mg;
       mc.smoother = smoothers[si];
       mc.nu1 = nu;

@@ -49,7 +49,7 @@ struct Carver {
   template <typename T>
   T* take(size_t count) {
     T* p = base ? (T*)(base + off) : nullptr;
-    off += a256(count * sizeof(T));
+    off += a256(count * sizeof(T)) + 256;  // slack: 16-byte-rounded bulk copies may read past the end
     return p;
   }
 };
@@ -584,6 +584,7 @@ struct Hier {
   int* cycles = nullptr;
   int* active = nullptr;
   int* n_active = nullptr;
+  int* err = nullptr;  // device error word of bounded waits
   int NB = 1;
   // flexible PCG (FP64 vectors on the finest grid) and per-sample scalars
   double *R = nullptr, *P = nullptr, *Q = nullptr, *Z = nullptr;
@@ -608,10 +609,10 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed, bool cg) {
     v.Kz = c.template take<T>(e);
     v.D = c.template take<T>(e);
     v.Dinv = c.template take<T>(e);
-    if (j > 0 || mixed || cg) {
-      v.u = c.template take<T>(e);
-      if (j > 0 || mixed) v.g = c.template take<T>(e);  // FP64 CG: the level-0 rhs is R
-    }
+    // level 0 of an FP64 solve iterates in a copy of the caller's u (so that every array
+    // the smoothers stage is carved here, with slack behind it)
+    v.u = c.template take<T>(e);
+    if (j > 0 || mixed) v.g = c.template take<T>(e);  // FP64: the level-0 rhs is g64 (or R for CG)
     if (j < H.L - 1) v.u2 = c.template take<T>(e);
     if (j < H.L - 1) v.r = c.template take<T>(e);
     nl = (nl + 1) / 2;
@@ -628,6 +629,7 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed, bool cg) {
   H.cycles = c.template take<int>(B);
   H.active = c.template take<int>(B);
   H.n_active = c.template take<int>(1);
+  H.err = c.template take<int>(1);
   if (cg) {
     H.R = c.template take<double>(e0);
     H.P = c.template take<double>(e0);
@@ -684,7 +686,7 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   auto smooth = [&](int sweeps) {
     for (int s = 0; s < sweeps; ++s) {
       if (H.fused[j]) {
-        rbgs_fused_sweep<T>(H.tile[j], v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, v.u2, act, st);
+        rbgs_fused_sweep<T>(H.tile[j], v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, v.u2, act, H.err, st);
         T* t = v.u;
         v.u = v.u2;
         v.u2 = t;
@@ -815,7 +817,14 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     int sm = a.cfg.smoother, d1 = 1, d2 = 1;
     resolve_tuning(v.n, a.cfg.precision, &sm, &d1, &d2);
     H.fused[j] = v.u2 != nullptr && sm != MLMC_SMOOTH_TWO_PASS;
-    H.tile[j] = sm == MLMC_SMOOTH_FUSED_32x16 ? kTile32x16 : sm == MLMC_SMOOTH_FUSED_64x8 ? kTile64x8 : kTile32x8;
+    switch (sm) {
+      case MLMC_SMOOTH_FUSED_32x16: H.tile[j] = kTile32x16; break;
+      case MLMC_SMOOTH_FUSED_64x8: H.tile[j] = kTile64x8; break;
+      case MLMC_SMOOTH_BULK_32x8: H.tile[j] = kBulk32x8; break;
+      case MLMC_SMOOTH_BULK_32x16: H.tile[j] = kBulk32x16; break;
+      case MLMC_SMOOTH_BULK_64x8: H.tile[j] = kBulk64x8; break;
+      default: H.tile[j] = kTile32x8;
+    }
     if (v.u2) MLMC_CUDA_TRY(cudaMemsetAsync(v.u2, 0, (size_t)B * v.n3 * sizeof(T), st));
   }
   Level<T>& l0 = H.lv[0];
@@ -831,8 +840,9 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   MLMC_LAUNCH("prepare", B * (double)l0.n3 * (a.f ? 16.0 : 8.0), B * (double)l0.n3, st,
               (k_prepare<<<g0, kThreads, 0, st>>>(a.n, B, h * h, a.f, H.g64, a.u)));
   if (!mixed && !cg) {
-    l0.u = (T*)a.u;
     l0.g = (T*)H.g64;
+    // iterate in the workspace copy; copied back after the last cycle
+    MLMC_CUDA_TRY(cudaMemcpyAsync(l0.u, a.u, (size_t)B * l0.n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   if (!mixed && cg) l0.g = (T*)H.R;  // FP64 CG: the cycle maps R to z (level-0 u)
   dim3 rg(H.NB, B);
@@ -843,6 +853,7 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
               (k_norm_update<<<sb, 128, 0, st>>>(B, H.NB, H.partial, H.g2, nullptr, nullptr, nullptr, 0, 0, 0.0, 0,
                                                  nullptr)));
   MLMC_CUDA_TRY(cudaMemsetAsync(H.cycles, 0, B * sizeof(int), st));
+  MLMC_CUDA_TRY(cudaMemsetAsync(H.err, 0, sizeof(int), st));
   {
     // every sample starts active; the first residual decides
     std::vector<int> ones(B, 1);
@@ -890,7 +901,7 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   }
   // FP64 solves iterate in place on the caller's u; the fused smoother may leave the
   // latest iterate in the spare buffer
-  if (!mixed && !cg && (void*)H.lv[0].u != (void*)a.u)
+  if (!mixed && !cg)
     MLMC_CUDA_TRY(cudaMemcpyAsync(a.u, H.lv[0].u, (size_t)B * l0.n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   MLMC_CUDA_TRY(cudaGetLastError());
   if (cycles_dev)
@@ -899,9 +910,15 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     MLMC_CUDA_TRY(cudaMemcpyAsync(relres_dev, H.relres, B * sizeof(double), cudaMemcpyDeviceToDevice, st));
   std::vector<int> cyc(B);
   std::vector<double> rel(B);
+  int errw = 0;
+  MLMC_CUDA_TRY(cudaMemcpyAsync(&errw, H.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   MLMC_CUDA_TRY(cudaMemcpyAsync(cyc.data(), H.cycles, B * sizeof(int), cudaMemcpyDeviceToHost, st));
   MLMC_CUDA_TRY(cudaMemcpyAsync(rel.data(), H.relres, B * sizeof(double), cudaMemcpyDeviceToHost, st));
   MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (errw) {
+    set_error("a staging wait of the fused smoother ran out of its time budget");
+    return MLMC_ERR_TIMEOUT;
+  }
   int bad = 0;
   for (int s = 0; s < B; ++s) {
     if (cycles_host) cycles_host[s] = cyc[s];

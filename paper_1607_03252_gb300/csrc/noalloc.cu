@@ -13,7 +13,7 @@
 namespace mlmc {
 namespace {
 
-// 32 MiB: enough for a batch of about 85 samples at 17^3, 12 at 33^3 or 1 at 65^3 in
+// 32 MiB: enough for a batch of about 75 samples at 17^3, 11 at 33^3 or 1 at 65^3 in
 // FP64. Every GPU that loads the library keeps this array until the process exits.
 constexpr size_t kNoAllocBytes = (size_t)32 << 20;
 __device__ __align__(256) unsigned char g_noalloc_workspace[kNoAllocBytes];
@@ -61,7 +61,7 @@ extern "C" int mg_solve_batch_noalloc(const mg_cfg* cfg, int batch, int n, const
   if (cfg->nu1 < 0 || cfg->nu1 > 8 || cfg->nu2 < 0 || cfg->nu2 > 8 || cfg->max_cycles < 1 ||
       cfg->max_cycles > 1000 || !(cfg->rtol < 1.0) ||
       (cfg->precision != MLMC_PREC_F64 && cfg->precision != MLMC_PREC_MIXED) ||
-      cfg->smoother < MLMC_SMOOTH_AUTO || cfg->smoother > MLMC_SMOOTH_FUSED_64x8 ||
+      cfg->smoother < MLMC_SMOOTH_AUTO || cfg->smoother > MLMC_SMOOTH_BULK_64x8 ||
       (cfg->accel != MLMC_ACCEL_NONE && cfg->accel != MLMC_ACCEL_CG)) {
     set_error("mg_solve_batch_noalloc: invalid mg_cfg");
     return MLMC_ERR_INVALID;
