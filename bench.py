@@ -289,6 +289,17 @@ def own_arm(args):
     if "N_init" in cfg:
         N, plan = plan_levels(mg, cfg, levels, stream, rank)
         nu_cfg = (0, 0)  # the autotuned sweep count per level
+    else:
+        # the cycle is fixed (V(nu1, nu2)); tune only the smoother implementation per level,
+        # which changes no result bit (bounded sample of tuning-only ids)
+        tune = {}
+        for l, n in zip(levels, N):
+            c = mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=(level_n(l) if single else 17),
+                                 nu1=cfg["nu1"], nu2=cfg["nu2"], rtol=cfg["rtol"], precision=prec,
+                                 max_batch=min(n, 256), stream=stream, accel=accel)
+            rows, bs, bnu = mg.mlmc_autotune(c, 0 if single else l, int(sample_ids(l, 1 << 40, 1)[0]), min(n, 256))
+            tune[str(l)] = {"best": {"smoother": mg._capi.SMOOTHER_NAMES.get(bs, bs), "nu": bnu}, "table": rows}
+        plan = {"autotune": tune}
     # inputs resident in HBM: each rank its own realisations (weak scaling)
     ids = {l: torch.from_numpy(sample_ids(l, rank * n, n).view("int64")).to(dev) for l, n in zip(levels, N)}
     Y = {l: torch.empty(n, dtype=torch.float64, device=dev) for l, n in zip(levels, N)}

@@ -309,7 +309,8 @@ typedef struct {
  * Each candidate runs the whole level pipeline once untimed and once timed on
  * `samples` realisations first_id .. first_id + samples - 1; the fastest by wall time
  * per sample is stored in a process-wide table for the level's fine grid size and
- * precision, where MLMC_SMOOTH_AUTO and nu1 = nu2 = 0 find it. Every candidate solves
+ * precision, where MLMC_SMOOTH_AUTO and nu1 = nu2 = 0 find it. With nu1 = nu2 > 0 in
+ * cfg->mg only the smoother is tuned, at that nu. Every candidate solves
  * to the same rtol, so the choice changes speed, not results beyond rtol.
  * table: host array of table_len entries (may be NULL) for the measurements; *n_entries,
  * *best_smoother, *best_nu (each may be NULL) receive the count and the choice.

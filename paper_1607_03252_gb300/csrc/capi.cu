@@ -488,7 +488,10 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   for (int i = 0; i < samples; ++i) ids[i] = first_id + (uint64_t)i;
   int count = 0, bs = MLMC_SMOOTH_TWO_PASS, bnu = 2;
   double best = 1e300;
-  for (int nu = 1; nu <= 3; ++nu)
+  // an explicit V(nu, nu) in cfg is kept: only the smoother implementation is tuned
+  const bool fixed_nu = cfg->mg.nu1 > 0 && cfg->mg.nu1 == cfg->mg.nu2;
+  const int nu_lo = fixed_nu ? cfg->mg.nu1 : 1, nu_hi = fixed_nu ? cfg->mg.nu1 : 3;
+  for (int nu = nu_lo; nu <= nu_hi; ++nu)
     for (int si = 0; si < 7; ++si) {
       mg_cfg mc = cfg->mg;
       mc.smoother = smoothers[si];
