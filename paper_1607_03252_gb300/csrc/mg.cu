@@ -349,24 +349,35 @@ __global__ void k_restrict(int nf, int B, const T* __restrict__ r, T* __restrict
   }
 }
 
-// u_f += trilinear interpolation of e_c at interior fine nodes.
+// u_f += trilinear interpolation of e_c at interior fine nodes: a fine node with k odd
+// coordinates is the mean of its 2^k coarse neighbours (k = 0: the coincident coarse
+// node). Threads of a row take the even x first and the odd x after them, so that a warp
+// shares one parity pattern and sums only the distinct neighbours (4.3 instead of 8
+// terms per node on average).
 template <typename T>
 __global__ void k_prolong(int nf, int B, const T* __restrict__ ec, T* __restrict__ u, const int* __restrict__ active) {
-  const int nc = (nf + 1) / 2;
+  const int nc = (nf + 1) / 2, he = (nf + 1) / 2;  // he: even x values per row
   const size_t nc3 = (size_t)nc * nc * nc, nf3 = (size_t)nf * nf * nf, nf2 = (size_t)nf * nf;
   const size_t total = (size_t)B * nf3;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const size_t s = t / nf3, q = t - s * nf3;
     if (active && !active[s]) continue;
-    const int z = (int)(q / nf2), y = (int)((q / nf) % nf), x = (int)(q % nf);
+    const int z = (int)(q / nf2), y = (int)((q / nf) % nf), r = (int)(q % nf);
+    const int x = r < he ? 2 * r : 2 * (r - he) + 1;
     if (!(x > 0 && y > 0 && z > 0 && x < nf - 1 && y < nf - 1 && z < nf - 1)) continue;
-    const int xa[2] = {x >> 1, (x + 1) >> 1}, ya[2] = {y >> 1, (y + 1) >> 1}, za[2] = {z >> 1, (z + 1) >> 1};
+    const int xo = x & 1, yo = y & 1, zo = z & 1;
+    const int X = x >> 1, Y = y >> 1, Z = z >> 1;
     const T* eb = ec + s * nc3;
     T v = 0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-      v += eb[((size_t)za[(c >> 2) & 1] * nc + ya[(c >> 1) & 1]) * nc + xa[c & 1]];
-    u[t] += (T)0.125 * v;
+    for (int dz = 0; dz <= zo; ++dz)
+      for (int dy = 0; dy <= yo; ++dy) {
+        const T* row = eb + ((size_t)(Z + dz) * nc + (Y + dy)) * nc + X;
+        v += row[0];
+        if (xo) v += row[1];
+      }
+    const T w = xo + yo + zo == 0 ? T(1) : xo + yo + zo == 1 ? T(0.5) : xo + yo + zo == 2 ? T(0.25) : T(0.125);
+    const size_t p = s * nf3 + (size_t)z * nf2 + (size_t)y * nf + x;
+    u[p] += w * v;
   }
 }
 
@@ -707,7 +718,7 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
               (k_restrict<T><<<blocks_for((size_t)B * w.n3, kThreads), kThreads, 0, st>>>(v.n, B, v.r, w.g, act)));
   cudaMemsetAsync(w.u, 0, (size_t)B * w.n3 * sizeof(T), st);
   vcycle(H, j + 1, nu1, nu2, st);
-  MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 10.0, st,
+  MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
               (k_prolong<T><<<blocks_for((size_t)B * v.n3, kThreads), kThreads, 0, st>>>(v.n, B, w.u, v.u, act)));
   smooth(nu2);
 }
@@ -915,9 +926,13 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   MLMC_CUDA_TRY(cudaMemcpyAsync(cyc.data(), H.cycles, B * sizeof(int), cudaMemcpyDeviceToHost, st));
   MLMC_CUDA_TRY(cudaMemcpyAsync(rel.data(), H.relres, B * sizeof(double), cudaMemcpyDeviceToHost, st));
   MLMC_CUDA_TRY(cudaStreamSynchronize(st));
-  if (errw) {
+  if (errw == 1) {
     set_error("a staging wait of the fused smoother ran out of its time budget");
     return MLMC_ERR_TIMEOUT;
+  }
+  if (errw) {
+    set_error("the fused smoother's bounds check failed (code %d)", errw);
+    return MLMC_ERR_CUDA;
   }
   int bad = 0;
   for (int s = 0; s < B; ++s) {

@@ -263,6 +263,9 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  // row offsets of every slot start at 0 (a slot is read before its first staging only
+  // where the value is unused, but its index must stay inside the staging buffer)
+  for (int t = tid; t < kSlots * H2; t += Lay::threads) offs[t] = 0;
   // rows outside the grid: zeros in every slot, never copied
   for (int t = tid; t < kArrays * kSlots * H2; t += Lay::threads) {
     const int j = t % H2;
@@ -319,8 +322,14 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
     }
   };
   // element (array a, plane slot sl, staged row j, column i of the tile + 2-ring)
+  // (bounds-checked: an index outside the staging buffer records error 2 and reads 0)
   auto at = [&](int a, int sl, int j, int i) -> T {
-    return stage[((size_t)(a * kSlots + sl) * H2 + j) * RP + offs[sl * H2 + j] + i];
+    const long long k = ((long long)(a * kSlots + sl) * H2 + j) * RP + offs[sl * H2 + j] + i;
+    if ((unsigned long long)k >= (unsigned long long)kArrays * kSlots * PLANE) {
+      atomicExch(err, 2);
+      return T(0);
+    }
+    return stage[k];
   };
   T kz_m2 = T(0);
   issue(zs - 1);
@@ -373,8 +382,8 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
         uout[base + (size_t)zb * n2 + (size_t)gy * n + gx] = v;
       }
       kz_m2 = kz_m1;
-    } else if (owned) {
-      kz_m2 = at(3, szm, cj, ci);
+    } else if (owned && zs >= 1) {
+      kz_m2 = at(3, szm, cj, ci);  // Kz(zs-1): plane zs-1 was staged
     }
     __syncthreads();  // slot (z+3) % kSlots = plane z-2 is reused by the next issue
   }
