@@ -1,7 +1,7 @@
 """One small batched field evaluation + multigrid solve, for kernel profiling.
 
   python -m paper_1607_03252_gb300.profile_case --n 129 --batch 8 --prec f64 --cycles 2 \
-      [--smoother two-pass|32x8|32x16|64x8] [--accel cg]
+      [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8] [--accel cg]
 
 Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256) for `batch` realisations
 on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0) through the C ABI, so
@@ -25,12 +25,15 @@ def main(argv=None):
     p.add_argument("--prec", choices=["f64", "mixed"], default="f64")
     p.add_argument("--cycles", type=int, default=2)
     p.add_argument("--M", type=int, default=256)
-    p.add_argument("--smoother", choices=["auto", "two-pass", "32x8", "32x16", "64x8"], default="auto")
+    p.add_argument("--smoother", choices=["auto", "two-pass", "32x8", "32x16", "64x8", "bulk32x8", "bulk32x16",
+                                          "bulk64x8"], default="auto")
     p.add_argument("--accel", choices=["none", "cg"], default="none")
     a = p.parse_args(argv)
     prec = mg.MLMC_PREC_F64 if a.prec == "f64" else mg.MLMC_PREC_MIXED
     sm = {"auto": mg.MLMC_SMOOTH_AUTO, "two-pass": mg.MLMC_SMOOTH_TWO_PASS, "32x8": mg.MLMC_SMOOTH_FUSED_32x8,
-          "32x16": mg.MLMC_SMOOTH_FUSED_32x16, "64x8": mg.MLMC_SMOOTH_FUSED_64x8}[a.smoother]
+          "32x16": mg.MLMC_SMOOTH_FUSED_32x16, "64x8": mg.MLMC_SMOOTH_FUSED_64x8,
+          "bulk32x8": mg.MLMC_SMOOTH_BULK_32x8, "bulk32x16": mg.MLMC_SMOOTH_BULK_32x16,
+          "bulk64x8": mg.MLMC_SMOOTH_BULK_64x8}[a.smoother]
     accel = mg.MLMC_ACCEL_CG if a.accel == "cg" else mg.MLMC_ACCEL_NONE
     k = torch.empty((a.batch, a.n, a.n, a.n), dtype=torch.float64, device="cuda")
     mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, 1.0, 0.3, a.M), sample_ids(3, 0, a.batch), k)
