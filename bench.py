@@ -578,56 +578,26 @@ def serving_arm(args):
 
 
 def adaptive_mlmc(mg, torch, cfg, eps, mode, stream, log):
-    """Algorithm 2 with L fixed: pilot N_init, then N_l from Eq. 15 with the running s_l^2
-    and measured cost per sample, until no level needs more samples. mode 'fast': batched,
-    FP32 V-cycle preconditioner (autotuned smoother and nu); 'plain': one sample per launch,
-    FP64 throughout. Both use flexible CG around the V-cycle and the same realisation ids."""
-    import math
+    """Algorithm 2 with L fixed (paper_1607_03252_gb300.estimator): pilot N_init, then N_l
+    from Eq. 15 with the running s_l^2 and measured cost per sample, until no level needs
+    more samples. mode 'fast': batched, FP32 V-cycle preconditioner (autotuned smoother and
+    nu); 'plain': one sample per launch, FP64 throughout. Both use flexible CG around the
+    V-cycle and the same realisation ids."""
+    from paper_1607_03252_gb300.estimator import MLMCEstimator
 
-    from paper_1607_03252_gb300.stats import chan_merge, eps_split, sample_sizes
-
-    levels = cfg["levels"]
     fast = mode == "fast"
-    prec = mg.MLMC_PREC_MIXED if fast else mg.MLMC_PREC_F64
-    nu = (0, 0) if fast else (cfg["nu1"], cfg["nu2"])
-    smoother = mg.MLMC_SMOOTH_AUTO if fast else mg.MLMC_SMOOTH_TWO_PASS
-    have = [0] * len(levels)
-    rec = [(0.0, 0.0, 0.0)] * len(levels)
-    secs = [0.0] * len(levels)
-    N = list(cfg["N_init"])
-    eps_s, _ = eps_split(eps, cfg["theta"])
+    est = MLMCEstimator(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], cfg["levels"], cfg["N_init"], eps,
+                        cfg["theta"], n0=17, nu=((0, 0) if fast else (cfg["nu1"], cfg["nu2"])), rtol=cfg["rtol"],
+                        precision=(mg.MLMC_PREC_MIXED if fast else mg.MLMC_PREC_F64), accel=mg.MLMC_ACCEL_CG,
+                        smoother=(mg.MLMC_SMOOTH_AUTO if fast else mg.MLMC_SMOOTH_TWO_PASS),
+                        max_batch=(0 if fast else 1), max_cycles=300, stream=stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rounds = 0
-    while True:
-        rounds += 1
-        for i, l in enumerate(levels):
-            need = N[i] - have[i]
-            if need <= 0:
-                continue
-            c = mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=17, nu1=nu[0], nu2=nu[1],
-                                 rtol=cfg["rtol"], precision=prec, max_batch=(0 if fast else 1), stream=stream,
-                                 accel=mg.MLMC_ACCEL_CG, smoother=smoother, max_cycles=300)
-            ta = time.perf_counter()
-            st, _, _, _ = mg.mlmc_level_estimate(c, l, int(sample_ids(l, have[i], 1)[0]), need, want_samples=False)
-            secs[i] += time.perf_counter() - ta
-            rec[i] = chan_merge([rec[i], (float(st.N), st.mean, st.M2)])
-            have[i] += need
-        V = [r[2] / (r[0] - 1.0) if r[0] > 1 else 0.0 for r in rec]
-        C = [secs[i] / have[i] for i in range(len(levels))]
-        N_new = sample_sizes([max(v, 1e-30) for v in V], C, eps_s)
-        log.append({"round": rounds, "have": list(have), "N_next": N_new, "t": time.perf_counter() - t0})
-        if all(nn <= h for nn, h in zip(N_new, have)):
-            break
-        N = [max(a, b) for a, b in zip(N, N_new)]
+    res = est.run()
     wall = time.perf_counter() - t0
-    means = [r[1] for r in rec]
-    V = [r[2] / (r[0] - 1.0) for r in rec]
-    q = math.fsum(means)
-    samp_var = math.fsum(v / h for v, h in zip(V, have))
-    return {"mode": mode, "wall_s": wall, "rounds": rounds, "N": have, "Q_hat": q, "level_means": means,
-            "level_vars": V, "sampling_var": samp_var, "eps_s2": eps_s ** 2,
-            "cost_per_sample_s": [secs[i] / have[i] for i in range(len(levels))]}
+    log.extend(est.log)
+    res.update({"mode": mode, "wall_s": wall})
+    return res
 
 
 def c5_arm(args):

@@ -92,12 +92,11 @@ __global__ void k_phasors(const double* __restrict__ w, const double* __restrict
   }
 }
 
-// The x-axis table of the double-float kernel, pre-split once: (Re hi, Re lo, Im hi, Im lo).
-__global__ void k_split_x(const double2* __restrict__ tab, int B, int M, int n, float4* __restrict__ xs) {
-  const size_t per = (size_t)M * n, total = (size_t)B * per;
+// The phasor tables of the double-float kernels, pre-split once: (Re hi, Re lo, Im hi,
+// Im lo), same [sample][axis][m][i] layout as the FP64 tables.
+__global__ void k_split_x(const double2* __restrict__ tab, size_t total, float4* __restrict__ xs) {
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t s = t / per, r = t - s * per;
-    const double2 v = tab[s * 3 * per + r];
+    const double2 v = tab[t];
     const float xh = (float)v.x, yh = (float)v.y;
     xs[t] = make_float4(xh, (float)(v.x - (double)xh), yh, (float)(v.y - (double)yh));
   }
@@ -197,7 +196,7 @@ __global__ void __launch_bounds__(kFieldThreads) k_field_df(const double2* __res
   const int nout = nl * n;
   const double2* Ty = tab + (size_t)s * 3 * M * n + (size_t)M * n;
   const double2* Tz = Ty + (size_t)M * n;
-  const float4* Xs = xsplit + (size_t)s * M * n;
+  const float4* Xs = xsplit + (size_t)s * 3 * M * n;
   int xo[kFieldOut], lo[kFieldOut];
   float ah[kFieldOut], al[kFieldOut];
 #pragma unroll
@@ -251,9 +250,96 @@ __global__ void __launch_bounds__(kFieldThreads) k_field_df(const double2* __res
   }
 }
 
+// Double-float sum with one (y, z) line and kXC consecutive x-values per thread: the
+// line factor Q_m = B_m[y] C_m[z] is formed once per feature in double-float complex
+// arithmetic and reused for the kXC x-phasors, which every lane of a warp reads at the
+// same shared-memory address (broadcast). No FP64 instruction remains in the loop.
+constexpr int kXC = 8;
+
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+  ph = ah * bh;
+  pl = fmaf(ah, bh, -ph);
+  pl = fmaf(ah, bl, pl);
+  pl = fmaf(al, bh, pl);
+}
+// (sh, sl) = (ah, al) + (bh, bl), renormalised
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e += al + bl;
+  sh = s + e;
+  sl = e - (sh - s);
+}
+
+template <typename TOut>
+__global__ void __launch_bounds__(kFieldThreads) k_field_line(const float4* __restrict__ tsplit, int M, int n, int MC,
+                                                               double scale, TOut* __restrict__ kout) {
+  extern __shared__ float4 sml[];
+  float4* sA = sml;  // [MC][kXC]
+  const int s = blockIdx.z;
+  const int x0 = blockIdx.x * kXC;
+  const size_t n2 = (size_t)n * n;
+  const size_t line = (size_t)blockIdx.y * kFieldThreads + threadIdx.x;
+  const bool valid = line < n2;
+  const int y = valid ? (int)(line % n) : 0, z = valid ? (int)(line / n) : 0;
+  const float4* Tx = tsplit + (size_t)s * 3 * M * n;
+  const float4* Ty = Tx + (size_t)M * n;
+  const float4* Tz = Ty + (size_t)M * n;
+  float ah[kXC], al[kXC];
+#pragma unroll
+  for (int q = 0; q < kXC; ++q) {
+    ah[q] = 0.f;
+    al[q] = 0.f;
+  }
+  for (int m0 = 0; m0 < M; m0 += MC) {
+    const int mc = min(MC, M - m0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < mc * kXC; t += kFieldThreads) {
+      const int mm = t / kXC, xi = t - mm * kXC;
+      const int x = x0 + xi;
+      sA[t] = x < n ? Tx[(size_t)(m0 + mm) * n + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    for (int mm = 0; mm < mc; ++mm) {
+      const float4 b = Ty[(size_t)(m0 + mm) * n + y];
+      const float4 c = Tz[(size_t)(m0 + mm) * n + z];
+      // Q = b c (complex, double-float)
+      float rh, rl, ih, il, t1h, t1l, t2h, t2l;
+      df_mul(b.x, b.y, c.x, c.y, t1h, t1l);
+      df_mul(b.z, b.w, c.z, c.w, t2h, t2l);
+      df_add(t1h, t1l, -t2h, -t2l, rh, rl);
+      df_mul(b.x, b.y, c.z, c.w, t1h, t1l);
+      df_mul(b.z, b.w, c.x, c.y, t2h, t2l);
+      df_add(t1h, t1l, t2h, t2l, ih, il);
+#pragma unroll
+      for (int q = 0; q < kXC; ++q) {
+        const float4 a = sA[mm * kXC + q];  // same address in every lane: broadcast
+        const float p1 = a.x * rh, e1 = fmaf(a.x, rh, -p1);
+        const float p2 = a.z * ih, e2 = fmaf(a.z, ih, -p2);
+        float th, tl;
+        two_sum(p1, -p2, th, tl);
+        float lw = (e1 - e2) + tl;
+        lw = fmaf(a.x, rl, lw);
+        lw = fmaf(a.y, rh, lw);
+        lw = fmaf(-a.z, il, lw);
+        lw = fmaf(-a.w, ih, lw);
+        float sh, se;
+        two_sum(ah[q], th, sh, se);
+        ah[q] = sh;
+        al[q] += se + lw;
+      }
+    }
+  }
+  if (!valid) return;
+  TOut* out = kout + (size_t)s * n2 * n + line * n + x0;
+#pragma unroll
+  for (int q = 0; q < kXC; ++q)
+    if (x0 + q < n) out[q] = (TOut)exp(scale * ((double)ah[q] + (double)al[q]));
+}
+
 size_t field_scratch_bytes(int B, int M, int n) {
   return a256((size_t)B * M * 3 * sizeof(double)) + a256((size_t)B * M * sizeof(double)) +
-         a256((size_t)B * 3 * M * n * sizeof(double2)) + a256((size_t)B * M * n * sizeof(float4));
+         a256((size_t)B * 3 * M * n * sizeof(double2)) + a256((size_t)B * 3 * M * n * sizeof(float4));
 }
 
 int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, int n, int dtype, void* kout,
@@ -267,7 +353,7 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
   double* w = (double*)carve((size_t)B * cfg.M * 3 * sizeof(double));
   double* bph = (double*)carve((size_t)B * cfg.M * sizeof(double));
   double2* tab = (double2*)carve((size_t)B * 3 * cfg.M * n * sizeof(double2));
-  float4* xsplit = (float4*)carve((size_t)B * cfg.M * n * sizeof(float4));
+  float4* xsplit = (float4*)carve((size_t)B * 3 * cfg.M * n * sizeof(float4));
   const size_t nf = (size_t)B * cfg.M;
   MLMC_LAUNCH("features", nf * 40.0, nf * 200.0, st,
               (k_features<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(ids_dev, B, cfg.M, cfg.run_seed,
@@ -298,10 +384,22 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
     else
       MLMC_LAUNCH("field_f64", bytes, flops, st,
                   (k_field<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (float*)kout)));
+  } else if (arith == kFieldDF32Line) {
+    MLMC_LAUNCH("phasors", nt * 32.0, nt * 4.0, st,
+                (k_split_x<<<blocks_for(nt, 256), 256, 0, st>>>(tab, nt, xsplit)));
+    const int MCl = cfg.M < 64 ? cfg.M : 64;
+    dim3 gl((unsigned)((n + kXC - 1) / kXC), (unsigned)(((size_t)n * n + kFieldThreads - 1) / kFieldThreads),
+            (unsigned)B);
+    const size_t sml = (size_t)MCl * kXC * sizeof(float4);
+    if (dtype == MLMC_F64)
+      MLMC_LAUNCH("field_df32", bytes, flops, st,
+                  (k_field_line<double><<<gl, kFieldThreads, sml, st>>>(xsplit, cfg.M, n, MCl, scale, (double*)kout)));
+    else
+      MLMC_LAUNCH("field_df32", bytes, flops, st,
+                  (k_field_line<float><<<gl, kFieldThreads, sml, st>>>(xsplit, cfg.M, n, MCl, scale, (float*)kout)));
   } else {
-    const size_t nx = (size_t)B * cfg.M * n;
-    MLMC_LAUNCH("phasors", nx * 32.0, nx * 4.0, st,
-                (k_split_x<<<blocks_for(nx, 256), 256, 0, st>>>(tab, B, cfg.M, n, xsplit)));
+    MLMC_LAUNCH("phasors", nt * 32.0, nt * 4.0, st,
+                (k_split_x<<<blocks_for(nt, 256), 256, 0, st>>>(tab, nt, xsplit)));
     if (dtype == MLMC_F64)
       MLMC_LAUNCH("field_df32", bytes, flops, st,
                   (k_field_df<double><<<grid, kFieldThreads, smem, st>>>(tab, xsplit, cfg.M, n, LT, MC, scale,

@@ -10,12 +10,13 @@ namespace mlmc {
 // Bytes of device scratch field_eval_dev needs for B samples, M features, n nodes per axis.
 size_t field_scratch_bytes(int B, int M, int n);
 
-// Arithmetic of the log k sum: FP64, or double-float on the FP32 pipe (the default).
-enum { kFieldDF32 = 0, kFieldFP64 = 1 };
+// Arithmetic of the log k sum: double-float on the FP32 pipe with one (y, z) line per
+// thread (the default), the same with flattened outputs, or FP64.
+enum { kFieldDF32Line = 0, kFieldFP64 = 1, kFieldDF32 = 2 };
 
 // k_out[s][z][y][x] = exp(log k) at the n^3 nodes for the B ids in ids_dev (device).
 // dtype MLMC_F64 or MLMC_F32. scratch: field_scratch_bytes(B, M, n) bytes, 256-aligned.
 int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, int n, int dtype, void* k_out,
-                   void* scratch, cudaStream_t st, int arith = kFieldDF32);
+                   void* scratch, cudaStream_t st, int arith = kFieldDF32Line);
 
 }  // namespace mlmc

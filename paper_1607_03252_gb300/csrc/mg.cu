@@ -302,16 +302,27 @@ __global__ void __launch_bounds__(kThreads) k_sumsq(int n, const double* __restr
   if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = b;
 }
 
+// Sum of a sample's NB block partials by one warp: lane l adds partials l, l+32, ...
+// in order, then a fixed shuffle tree; the result depends only on NB (not on the batch).
+__device__ __forceinline__ double warp_sum_partials(const double* __restrict__ p, int NB) {
+  const int lane = threadIdx.x & 31;
+  double t = 0.0;
+  for (int b = lane; b < NB; b += 32) t += p[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
 // Per sample: total of the NB partials (fixed order). mode 0: store ||g||^2.
 // mode 1: relative residual, cycle count and active flag after `inc` cycles.
 __global__ void k_norm_update(int B, int NB, const double* __restrict__ partial, double* __restrict__ g2,
                               double* __restrict__ relres, int* __restrict__ cycles, int* __restrict__ active,
                               int mode, int inc, double rtol, int max_cycles, int* __restrict__ n_active) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // one warp per sample
   if (s >= B) return;
   if (mode == 1 && !active[s]) return;
-  double t = 0.0;
-  for (int b = 0; b < NB; ++b) t += partial[(size_t)s * NB + b];
+  const double t = warp_sum_partials(partial + (size_t)s * NB, NB);
+  if ((threadIdx.x & 31) != 0) return;
   if (mode == 0) {
     g2[s] = t;
     return;
@@ -552,10 +563,10 @@ __global__ void k_to_f32(size_t total, const double* __restrict__ a, float* __re
 __global__ void k_cg_scalar(int B, int NB, int mode, const double* __restrict__ part, double* __restrict__ rz,
                             double* __restrict__ rzo, double* __restrict__ alpha, double* __restrict__ beta,
                             const int* __restrict__ active) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // one warp per sample
   if (s >= B || !active[s]) return;
-  double t = 0.0;
-  for (int b = 0; b < NB; ++b) t += part[(size_t)s * NB + b];
+  const double t = warp_sum_partials(part + (size_t)s * NB, NB);
+  if ((threadIdx.x & 31) != 0) return;
   if (mode == 0) {
     rz[s] = t;
   } else if (mode == 1) {
@@ -730,7 +741,7 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   Level<T>& l0 = H.lv[0];
   const double Wk = (double)sizeof(T), nodes = B * interior(n), all = (double)B * l0.n3;
   dim3 rg(H.NB, B);
-  const unsigned sb = (B + 127) / 128;
+  const unsigned sb = (B + 3) / 4;  // 128-thread blocks, one warp per sample
   const unsigned g0 = blocks_for((size_t)B * l0.n3, kThreads);
   const double* D = mixed ? H.D64 : (const double*)(const void*)l0.D;
   auto sync_count = [&](int* out) -> int {
@@ -857,7 +868,7 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   }
   if (!mixed && cg) l0.g = (T*)H.R;  // FP64 CG: the cycle maps R to z (level-0 u)
   dim3 rg(H.NB, B);
-  const unsigned sb = (B + 127) / 128;
+  const unsigned sb = (B + 3) / 4;  // 128-thread blocks, one warp per sample
   MLMC_LAUNCH("norm", B * (double)l0.n3 * 8, B * (double)l0.n3 * 2, st,
               (k_sumsq<<<rg, kThreads, 0, st>>>(a.n, H.g64, H.partial)));
   MLMC_LAUNCH("norm_update", B * H.NB * 8.0, B * H.NB * 1.0, st,

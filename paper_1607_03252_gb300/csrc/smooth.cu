@@ -44,43 +44,44 @@ constexpr int kArrays = 6;   // u, Kx, Ky, Kz, Dinv, g
 
 template <typename T, int BX, int BY>
 struct FusedLayout {
+  static constexpr int kStaged = 3;               // u, Kx, Ky: read by in-plane neighbours
   static constexpr int W2 = BX + 4, H2 = BY + 4;  // tile + 2-ring: one thread per column
   static constexpr int W1 = BX + 2, H1 = BY + 2;  // tile + 1-ring
   static constexpr int P2 = W2 * H2, P1 = W1 * H1;
   static constexpr int threads = P2;
-  static constexpr size_t bytes = sizeof(T) * ((size_t)kArrays * kSlots * P2 + 3 * (size_t)P1);
+  static constexpr size_t bytes = sizeof(T) * ((size_t)kStaged * kSlots * P2 + 3 * (size_t)P1);
 };
 
-// One thread per column of the tile + 2-ring: every thread stages its own column of the
-// six arrays; ring-1 and tile threads compute the red update of their column; tile
-// threads compute the black update (one plane behind) and write the output.
+// One thread per column of the tile + 2-ring. u, Kx and Ky (which in-plane neighbours
+// read) are staged in shared memory with cp.async; Kz, 1/D and g are read only by the
+// column's own updates and travel in a five-plane register window, loaded two planes
+// ahead. Ring-1 and tile threads compute the red update of their column; tile threads
+// compute the black update (one plane behind) and write the output.
 template <typename T, int BX, int BY>
 __global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads)
     k_rbgs_fused(int n, int ntx, int ntiles, int zslab, const T* __restrict__ Kx, const T* __restrict__ Ky,
                  const T* __restrict__ Kz, const T* __restrict__ Dinv, const T* __restrict__ g,
                  const T* __restrict__ uin, T* __restrict__ uout, const int* __restrict__ active) {
   using Lay = FusedLayout<T, BX, BY>;
-  constexpr int W2 = Lay::W2, H2 = Lay::H2, P2 = Lay::P2, W1 = Lay::W1, P1 = Lay::P1;
+  constexpr int W2 = Lay::W2, H2 = Lay::H2, P2 = Lay::P2, W1 = Lay::W1, P1 = Lay::P1, NS = Lay::kStaged;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* stage = (T*)smem_raw;                          // [array][slot][P2]
-  T* red = stage + (size_t)kArrays * kSlots * P2;   // [3][P1]: plane after its red phase
+  T* stage = (T*)smem_raw;                      // [array][slot][P2]
+  T* red = stage + (size_t)NS * kSlots * P2;    // [3][P1]: plane after its red phase
   const int s = blockIdx.y;
   const int tid = threadIdx.x;
   const int tile = blockIdx.x % ntiles, slab = blockIdx.x / ntiles;
   const int x0 = (tile % ntx) * BX + 1, y0 = (tile / ntx) * BY + 1;  // first owned node
   const int zlo = 1 + slab * zslab, zhi = min(n - 2, zlo + zslab - 1);
   const size_t n2 = (size_t)n * n, base = (size_t)s * n2 * n;
-  // this thread's column
   const int ci = tid % W2, cj = tid / W2;
   const int gx = x0 - 2 + ci, gy = y0 - 2 + cj;
   const bool in_grid = gx >= 0 && gx < n && gy >= 0 && gy < n;
   const bool ring1 = ci >= 1 && ci <= W2 - 2 && cj >= 1 && cj <= H2 - 2;
   const bool owned = ci >= 2 && ci <= W2 - 3 && cj >= 2 && cj <= H2 - 3;
   const bool interior_col = gx >= 1 && gx <= n - 2 && gy >= 1 && gy <= n - 2;
-  const int c = tid;                                   // position in the 2-ring plane
-  const int c1 = (cj - 1) * W1 + (ci - 1);             // position in the 1-ring plane (ring1 only)
+  const int c = tid;
+  const int c1 = (cj - 1) * W1 + (ci - 1);
   if (active && !active[s]) {
-    // a finished sample keeps its iterate: carry the owned block over to uout
     if (owned && interior_col)
       for (int z = zlo; z <= zhi; ++z) {
         const size_t p = base + (size_t)z * n2 + (size_t)gy * n + gx;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads)
       }
     return;
   }
-  const T* src[kArrays] = {uin, Kx, Ky, Kz, Dinv, g};
+  const T* src[NS] = {uin, Kx, Ky};
   auto sm = [&](int a, int slot, int i) -> T& { return stage[((size_t)a * kSlots + slot) * P2 + i]; };
   const size_t col = base + (size_t)gy * n + gx;
   auto issue = [&](int z) {
@@ -97,16 +98,20 @@ __global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads)
     if (in_grid) {
       const size_t off = col + (size_t)z * n2;
 #pragma unroll
-      for (int a = 0; a < kArrays; ++a) cp_async(&sm(a, slot, c), src[a] + off);
+      for (int a = 0; a < NS; ++a) cp_async(&sm(a, slot, c), src[a] + off);
     } else {
 #pragma unroll
-      for (int a = 0; a < kArrays; ++a) sm(a, slot, c) = T(0);
+      for (int a = 0; a < NS; ++a) sm(a, slot, c) = T(0);
     }
   };
-  T kz_m2 = T(0);  // Kz(z-2) of this column
-
-  // steps z = zlo-1 .. zhi+1: red phase on plane z, black phase on plane z-1
+  // this column's Kz, 1/D, g on planes z-2 .. z+2 (m2, m1, c0, p1, p2)
+  const bool need_regs = ring1 && in_grid;
+  auto ld = [&](const T* a, int z) -> T { return (need_regs && z >= 0 && z < n) ? a[col + (size_t)z * n2] : T(0); };
   const int zs = zlo - 1, ze = zhi + 1;
+  T kz_m2 = ld(Kz, zs - 2), kz_m1 = ld(Kz, zs - 1), kz_0 = ld(Kz, zs), kz_p1 = ld(Kz, zs + 1), kz_p2;
+  T di_m1 = ld(Dinv, zs - 1), di_0 = ld(Dinv, zs), di_p1 = ld(Dinv, zs + 1), di_p2;
+  T g_m1 = ld(g, zs - 1), g_0 = ld(g, zs), g_p1 = ld(g, zs + 1), g_p2;
+
   issue(zs - 1);
   cp_async_commit();
   issue(zs);
@@ -117,6 +122,9 @@ __global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads)
     // slot of plane z+2 held plane z-3, last read before the previous step's barriers
     issue(z + 2);
     cp_async_commit();
+    kz_p2 = ld(Kz, z + 2);
+    di_p2 = ld(Dinv, z + 2);
+    g_p2 = ld(g, z + 2);
     cp_async_wait1();  // planes <= z+1 of this thread's column have landed
     __syncthreads();   // ... and of every column
     const int sz = z % kSlots, szm = (z + kSlots - 1) % kSlots, szp = (z + 1) % kSlots;
@@ -124,41 +132,48 @@ __global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads)
     if (ring1) {
       T v = sm(0, sz, c);
       if (z >= 1 && z <= n - 2 && interior_col && ((gx + gy + z) & 1) == 0) {
-        T acc = sm(5, sz, c);
+        T acc = g_0;
         acc = fma(sm(1, sz, c - 1), sm(0, sz, c - 1), acc);
         acc = fma(sm(1, sz, c), sm(0, sz, c + 1), acc);
         acc = fma(sm(2, sz, c - W2), sm(0, sz, c - W2), acc);
         acc = fma(sm(2, sz, c), sm(0, sz, c + W2), acc);
-        acc = fma(sm(3, szm, c), sm(0, szm, c), acc);
-        acc = fma(sm(3, sz, c), sm(0, szp, c), acc);
-        v = acc * sm(4, sz, c);
+        acc = fma(kz_m1, sm(0, szm, c), acc);
+        acc = fma(kz_0, sm(0, szp, c), acc);
+        v = acc * di_0;
       }
       rz[c1] = v;
     }
     __syncthreads();
     if (z > zs) {
       const int zb = z - 1, sb = szm;
-      const T kz_m1 = sm(3, sb, c);  // Kz(z-1) of this column
       if (owned && interior_col && zb >= zlo && zb <= zhi) {
         const T* rb = red + (size_t)(zb % 3) * P1;
         T v = rb[c1];
         if (((gx + gy + zb) & 1) == 1) {
           const T* rbm = red + (size_t)((zb + 2) % 3) * P1;  // plane z-2
-          T acc = sm(5, sb, c);
+          T acc = g_m1;
           acc = fma(sm(1, sb, c - 1), rb[c1 - 1], acc);
           acc = fma(sm(1, sb, c), rb[c1 + 1], acc);
           acc = fma(sm(2, sb, c - W2), rb[c1 - W1], acc);
           acc = fma(sm(2, sb, c), rb[c1 + W1], acc);
           acc = fma(kz_m2, rbm[c1], acc);
           acc = fma(kz_m1, rz[c1], acc);
-          v = acc * sm(4, sb, c);
+          v = acc * di_m1;
         }
         uout[col + (size_t)zb * n2] = v;
       }
-      kz_m2 = kz_m1;
-    } else {
-      kz_m2 = sm(3, szm, c);  // Kz(zs-1): only used when zs-1 is a staged plane
     }
+    // advance the register window by one plane
+    kz_m2 = kz_m1;
+    kz_m1 = kz_0;
+    kz_0 = kz_p1;
+    kz_p1 = kz_p2;
+    di_m1 = di_0;
+    di_0 = di_p1;
+    di_p1 = di_p2;
+    g_m1 = g_0;
+    g_0 = g_p1;
+    g_p1 = g_p2;
   }
 }
 
