@@ -3,7 +3,8 @@ library, with checkpoint / resume.
 
 Each round computes the missing samples of every level (Algorithm 2, step 2.a) through
 `mlmc_level_estimate`, folds their (N, mean, M2) records into the level's running record
-(Chan's merge, Sec. 2.3's Y-hat_l and s_l^2), measures the cost per sample C_l, and sizes
+(Chan's merge, Sec. 2.3's Y-hat_l and s_l^2), estimates the cost per sample C_l (measured
+wall time, or the deterministic node-count model), and sizes
 N_l by Eq. 15 for eps_s^2 = theta eps^2 (Eq. 6); it stops when no level needs more samples
 (step 4). Sample ids of level l are sample_id(l, 0), sample_id(l, 1), ... in order, so a
 run restored from `state()` continues with exactly the ids an uninterrupted run would use
@@ -23,8 +24,10 @@ from .workloads import sample_id
 class MLMCEstimator:
     def __init__(self, run_seed, sigma2, ell, M, levels, N_init, eps, theta=0.5, n0=17, nu=(2, 2), rtol=1e-10,
                  precision=mg.MLMC_PREC_F64, accel=mg.MLMC_ACCEL_NONE, smoother=mg.MLMC_SMOOTH_AUTO,
-                 max_batch=0, max_cycles=300, stream=None):
-        self.params = dict(run_seed=int(run_seed), sigma2=float(sigma2), ell=float(ell), M=int(M),
+                 max_batch=0, max_cycles=300, stream=None, cost_model="measured"):
+        if cost_model not in ("measured", "nodes"):
+            raise ValueError("cost_model must be 'measured' or 'nodes'")
+        self.params = dict(cost_model=cost_model, run_seed=int(run_seed), sigma2=float(sigma2), ell=float(ell), M=int(M),
                            levels=list(levels), N_init=list(N_init), eps=float(eps), theta=float(theta), n0=int(n0),
                            nu=list(nu), rtol=float(rtol), precision=int(precision), accel=int(accel),
                            smoother=int(smoother), max_batch=int(max_batch), max_cycles=int(max_cycles))
@@ -51,7 +54,7 @@ class MLMCEstimator:
         p = state["params"]
         est = cls(p["run_seed"], p["sigma2"], p["ell"], p["M"], p["levels"], p["N_init"], p["eps"], p["theta"],
                   p["n0"], tuple(p["nu"]), p["rtol"], p["precision"], p["accel"], p["smoother"], p["max_batch"],
-                  p["max_cycles"], stream)
+                  p["max_cycles"], stream, p.get("cost_model", "measured"))
         est.have = list(state["have"])
         est.records = [tuple(r) for r in state["records"]]
         est.seconds = list(state["seconds"])
@@ -88,13 +91,26 @@ class MLMCEstimator:
     def variances(self):
         return [r[2] / (r[0] - 1.0) if r[0] > 1 else 0.0 for r in self.records]
 
+    def costs(self):
+        """C_l: measured seconds per sample, or the model cost n_l^3 + n_{l-1}^3 (nodes of
+        the fine and coarse grid, deterministic)."""
+        if self.params["cost_model"] == "nodes":
+            n0 = self.params["n0"]
+            out = []
+            for l in self.params["levels"]:
+                nf = (n0 - 1) * 2 ** l + 1
+                nc = (n0 - 1) * 2 ** (l - 1) + 1 if l > 0 else 0
+                out.append(float(nf ** 3 + nc ** 3))
+            return out
+        return [self.seconds[i] / self.have[i] for i in range(len(self.have))]
+
     def step(self) -> bool:
         """One round of Algorithm 2; returns True when no level needs more samples."""
         self.rounds += 1
         for i in range(len(self.have)):
             self.add_samples(i, self.target[i] - self.have[i])
         V = self.variances()
-        C = [self.seconds[i] / self.have[i] for i in range(len(self.have))]
+        C = self.costs()
         eps_s, _ = eps_split(self.params["eps"], self.params["theta"])
         need = sample_sizes([max(v, 1e-30) for v in V], C, eps_s)
         self.log.append({"round": self.rounds, "have": list(self.have), "N_next": need})
