@@ -336,8 +336,9 @@ def own_arm(args):
     for _ in range(args.warmup):
         step(False)
     torch.cuda.synchronize()
+    # timed region 1: the value (launches counted, no per-launch events)
     mg.profile_reset()
-    mg.profile_enable(True)
+    mg.profile_enable(False)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -354,10 +355,22 @@ def own_arm(args):
         torch.distributed.barrier()
     t_host = time.perf_counter() - t_host0
     clk = clocks.stop()
-    mg.profile_enable(False)
     elapsed_ms = ev0.elapsed_time(ev1)
-    prof = mg.profile_read()
     launches = mg.profile_total_launches()
+    # timed region 2: the same steps with a CUDA event pair around every launch, for the
+    # per-kernel device times of the roofline
+    mg.profile_reset()
+    mg.profile_enable(True)
+    torch.cuda.synchronize()
+    evp0, evp1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evp0.record(stream)
+    for _ in range(args.steps):
+        step(False)
+    evp1.record(stream)
+    torch.cuda.synchronize()
+    mg.profile_enable(False)
+    prof = mg.profile_read()
+    profiled_ms = evp0.elapsed_time(evp1)
     if world > 1:
         t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -403,8 +416,13 @@ def own_arm(args):
                                      "cycles_coarse": stats[l].mean_cycles_coarse} for l in levels},
             "roofline": roof, "gpu_launches": launches, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu,
             "host_wall_s": t_host,
+            "timing_note": "value, per_level, clocks and gpu_launches: timed region 1 (no per-launch events); "
+                           "roofline and kernel_classes: timed region 2 (same steps, CUDA events around "
+                           "every launch on the launching stream)",
+            "profiled_region_ms_per_step": profiled_ms / args.steps,
+            "kernel_ms_per_step": sum(v["ms"] for v in prof.values()) / args.steps,
             "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
-                               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+                               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:10]},
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -23,6 +23,7 @@
 // result therefore does not depend on the batch it is solved in.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <vector>
 
@@ -734,8 +735,53 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   smooth(nu2);
 }
 
+// Runs one V-cycle, as a CUDA graph when enabled: the first call captures the cycle's
+// launches (counted by the launch tape on every replay), later calls replay it.
+inline bool graphs_allowed() {
+  static const bool off = [] {
+    const char* e = getenv("MLMC_NO_GRAPHS");
+    return e && e[0] == '1';
+  }();
+  return !off;
+}
+
 template <typename T>
-int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, int maxc, cudaStream_t st) {
+struct GraphRunner {
+  bool enabled = false;
+  cudaGraphExec_t exec = nullptr;
+  prof::Tape tape;
+  ~GraphRunner() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+  int run(Hier<T>& H, int nu1, int nu2, cudaStream_t st) {
+    if (!enabled) {
+      vcycle<T>(H, 0, nu1, nu2, st);
+      return MLMC_OK;
+    }
+    if (!exec) {
+      MLMC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      prof::tape_begin();
+      vcycle<T>(H, 0, nu1, nu2, st);
+      tape = prof::tape_end();
+      cudaGraph_t graph = nullptr;
+      MLMC_CUDA_TRY(cudaStreamEndCapture(st, &graph));
+      const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        exec = nullptr;
+        set_error("cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+        return MLMC_ERR_CUDA;
+      }
+    }
+    prof::tape_replay(tape);
+    MLMC_CUDA_TRY(cudaGraphLaunch(exec, st));
+    return MLMC_OK;
+  }
+};
+
+template <typename T>
+int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, int maxc, cudaStream_t st,
+             GraphRunner<T>& gr) {
   const bool mixed = a.cfg.precision == MLMC_PREC_MIXED;
   const int B = H.B, n = a.n;
   Level<T>& l0 = H.lv[0];
@@ -752,7 +798,7 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   // z = M r: one V-cycle from zero on the (FP32 copy of the) residual; partials of r.z
   auto precondition = [&]() {
     MLMC_CUDA_TRY(cudaMemsetAsync(H.lv[0].u, 0, (size_t)B * l0.n3 * sizeof(T), st));
-    vcycle<T>(H, 0, nu1, nu2, st);
+    MLMC_TRY(gr.run(H, nu1, nu2, st));
     double* z = mixed ? H.Z : (double*)(void*)H.lv[0].u;
     MLMC_LAUNCH("cg_precond_dot", all * (mixed ? 20.0 : 16.0), nodes * 2.0, st,
                 (k_precond_dot<<<rg, kThreads, 0, st>>>(n, mixed ? (const float*)(const void*)H.lv[0].u : nullptr,
@@ -848,7 +894,14 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
       default: H.tile[j] = kTile32x8;
     }
     if (v.u2) MLMC_CUDA_TRY(cudaMemsetAsync(v.u2, 0, (size_t)B * v.n3 * sizeof(T), st));
+    if (H.fused[j]) MLMC_TRY(rbgs_fused_configure<T>(H.tile[j]));
   }
+  // The V-cycle as a CUDA graph: captured on the first cycle, replayed on the others.
+  // Only when no per-launch events are recorded, the stream can be captured (not the
+  // legacy default stream), and every level's double buffer returns to its starting
+  // pointer after a cycle (nu1 + nu2 even).
+  GraphRunner<T> gr;
+  gr.enabled = !prof::timing_enabled() && st != nullptr && ((nu1 + nu2) % 2 == 0) && graphs_allowed();
   Level<T>& l0 = H.lv[0];
   const unsigned g0 = blocks_for((size_t)B * l0.n3, kThreads);
   if (mixed) {
@@ -904,7 +957,7 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     return na;
   };
   if (cg) {
-    const int st_pcg = pcg_loop<T>(H, a, nu1, nu2, rtol, maxc, st);
+    const int st_pcg = pcg_loop<T>(H, a, nu1, nu2, rtol, maxc, st, gr);
     if (st_pcg < 0) return st_pcg;
   }
   int na = cg ? 0 : residual_check(0);
@@ -912,11 +965,11 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   while (na > 0) {
     if (mixed) {
       MLMC_CUDA_TRY(cudaMemsetAsync(H.lv[0].u, 0, (size_t)B * l0.n3 * sizeof(T), st));
-      vcycle<T>(H, 0, nu1, nu2, st);
+      MLMC_TRY(gr.run(H, nu1, nu2, st));
       MLMC_LAUNCH("update_mixed", B * (double)l0.n3 * (W + 16), B * (double)l0.n3, st,
                   (k_update_mixed<<<g0, kThreads, 0, st>>>(a.n, B, (const float*)H.lv[0].u, a.u, H.active)));
     } else {
-      vcycle<T>(H, 0, nu1, nu2, st);
+      MLMC_TRY(gr.run(H, nu1, nu2, st));
     }
     na = residual_check(1);
     if (na < 0) return na;

@@ -60,7 +60,38 @@ void resolve(Entry& e) {
 
 bool timing_enabled() { return reg().timing.load(); }
 
+static thread_local Tape* t_tape = nullptr;
+static thread_local Tape t_tape_store;
+
+void tape_begin() {
+  t_tape_store = Tape();
+  t_tape = &t_tape_store;
+}
+
+Tape tape_end() {
+  t_tape = nullptr;
+  return t_tape_store;
+}
+
+void tape_replay(const Tape& t) {
+  Registry& r = reg();
+  r.total_launches.fetch_add((int64_t)t.cls.size());
+  std::lock_guard<std::mutex> lk(r.mu);
+  for (size_t i = 0; i < t.cls.size(); ++i) {
+    Entry& e = r.entries[t.cls[i]];
+    ++e.launches;
+    e.bytes += t.bytes[i];
+    e.flops += t.flops[i];
+  }
+}
+
 int begin(const char* cls, double bytes, double flops, cudaStream_t st) {
+  if (t_tape) {  // being captured into a graph: counted when the graph is replayed
+    t_tape->cls.emplace_back(cls);
+    t_tape->bytes.push_back(bytes);
+    t_tape->flops.push_back(flops);
+    return -1;
+  }
   Registry& r = reg();
   r.total_launches.fetch_add(1);
   std::lock_guard<std::mutex> lk(r.mu);

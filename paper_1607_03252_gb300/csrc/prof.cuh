@@ -6,10 +6,24 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
 namespace mlmc {
 namespace prof {
 
 bool timing_enabled();
+
+// Launch tape for CUDA-graph capture: between tape_begin() and tape_end() launches are
+// recorded (class, bytes, flops) instead of counted; tape_replay() counts them once per
+// replay of the captured graph. Per calling thread.
+struct Tape {
+  std::vector<std::string> cls;
+  std::vector<double> bytes, flops;
+};
+void tape_begin();
+Tape tape_end();
+void tape_replay(const Tape& t);
 // Records the start of one launch of `cls`; returns a token for end().
 int begin(const char* cls, double bytes, double flops, cudaStream_t st);
 void end(int token, cudaStream_t st);

@@ -14,13 +14,18 @@
 // around its tile (which needs old values on a two-cell ring). The result equals the
 // sequential red-then-black sweep exactly: same operations on the same operands.
 //
-// Plane data (u, Kx, Ky, Kz, Dinv, g on the tile plus a two-cell ring) is staged in
-// shared memory with cp.async, two planes ahead of the plane being updated, in a ring
-// of five plane slots; one thread per staged column keeps the work per barrier even.
-// z is split into independent slabs (each recomputes the red plane just outside its
-// ends) so that a launch has enough CTAs. HBM traffic per sweep is one read of each
-// array and one write of u (7 words per node), against 12+ words for two separate
-// colour passes.
+// Staging: u, Kx and Ky (read by in-plane neighbours) of the tile + 2-ring are copied
+// into shared memory two planes ahead, in a ring of five plane slots, by 16-byte
+// cp.async copies. Grid rows have odd length, so a row starts at any element offset
+// modulo 16 bytes: each staged row is copied from the 16-byte boundary at or below its
+// first element, and reads add that row's offset (computed from the element index, never
+// stored). Kz, 1/D and g are read only by a column's own updates and travel in a
+// five-plane register window. Each thread owns a column pair (x, y) and (x, y+1) of the
+// staged tile; at every (x, z) one of the two is red and the other black, so each thread
+// does one red update of plane z and one black update of plane z-1 per step. z is split
+// into independent slabs (each recomputes the red plane just outside its ends) so that a
+// launch has enough CTAs. HBM traffic per sweep is one read of each array and one write
+// of u (7 words per node), against 12+ words for two separate colour passes.
 #include "common.cuh"
 #include "prof.cuh"
 #include "smooth.cuh"
@@ -28,152 +33,211 @@
 namespace mlmc {
 namespace {
 
-__device__ __forceinline__ void cp_async(float* dst, const float* src) {
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async(double* dst, const double* src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-constexpr int kSlots = 5;    // plane ring of the staged arrays (z-1 .. z+2 live, z+3 in flight)
-constexpr int kArrays = 6;   // u, Kx, Ky, Kz, Dinv, g
+constexpr int kSlots = 5;    // plane ring (z-1 .. z+1 read, z+2 in flight, one slot of slack)
+constexpr int kArrays = 6;   // u, Kx, Ky, Kz, Dinv, g (bulk-copy variant)
+
+template <int K>
+struct StepK {
+  static constexpr int value = K;
+};
 
 template <typename T, int BX, int BY>
 struct FusedLayout {
-  static constexpr int kStaged = 3;               // u, Kx, Ky: read by in-plane neighbours
-  static constexpr int W2 = BX + 4, H2 = BY + 4;  // tile + 2-ring: one thread per column
-  static constexpr int W1 = BX + 2, H1 = BY + 2;  // tile + 1-ring
-  static constexpr int P2 = W2 * H2, P1 = W1 * H1;
-  static constexpr int threads = P2;
-  static constexpr size_t bytes = sizeof(T) * ((size_t)kStaged * kSlots * P2 + 3 * (size_t)P1);
+  static_assert(BY % 2 == 0, "the tile height must be even (column pairs)");
+  static constexpr int kStaged = 3;                 // u, Kx, Ky
+  static constexpr int E = 16 / (int)sizeof(T);     // elements per 16-byte copy
+  static constexpr int W2 = BX + 4, H2 = BY + 4;    // tile + 2-ring
+  static constexpr int W1 = BX + 2, H1 = BY + 2;    // tile + 1-ring
+  static constexpr int NCH = (W2 + 2 * E - 2) / E;  // 16-byte copies per staged row, any alignment
+  static constexpr int RW = NCH * E;                // staged row pitch (elements)
+  static constexpr int PLANE = H2 * RW;
+  static constexpr int RP = W1 + (W1 & 1);          // red-plane row pitch, even: conflict-free pairs
+  static constexpr int RPLANE = H1 * RP;
+  static constexpr int threads = W2 * (H2 / 2);     // one thread per column pair
+  static constexpr int items = kStaged * H2 * NCH;  // copies per staged plane
+  static constexpr int per_thread = (items + threads - 1) / threads;
+  static constexpr size_t bytes = sizeof(T) * ((size_t)kStaged * kSlots * PLANE + (size_t)kSlots * RPLANE);
 };
 
-// One thread per column of the tile + 2-ring. u, Kx and Ky (which in-plane neighbours
-// read) are staged in shared memory with cp.async; Kz, 1/D and g are read only by the
-// column's own updates and travel in a five-plane register window, loaded two planes
-// ahead. Ring-1 and tile threads compute the red update of their column; tile threads
-// compute the black update (one plane behind) and write the output.
 template <typename T, int BX, int BY>
-__global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads)
+__global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads, sizeof(T) == 4 ? 2 : 1)
     k_rbgs_fused(int n, int ntx, int ntiles, int zslab, const T* __restrict__ Kx, const T* __restrict__ Ky,
                  const T* __restrict__ Kz, const T* __restrict__ Dinv, const T* __restrict__ g,
                  const T* __restrict__ uin, T* __restrict__ uout, const int* __restrict__ active) {
   using Lay = FusedLayout<T, BX, BY>;
-  constexpr int W2 = Lay::W2, H2 = Lay::H2, P2 = Lay::P2, W1 = Lay::W1, P1 = Lay::P1, NS = Lay::kStaged;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* stage = (T*)smem_raw;                      // [array][slot][P2]
-  T* red = stage + (size_t)NS * kSlots * P2;    // [3][P1]: plane after its red phase
-  const int s = blockIdx.y;
-  const int tid = threadIdx.x;
+  constexpr int E = Lay::E, W2 = Lay::W2, H2 = Lay::H2, RW = Lay::RW, PLANE = Lay::PLANE, RP = Lay::RP,
+                RPLANE = Lay::RPLANE, NT = Lay::threads, NCH = Lay::NCH, PT = Lay::per_thread;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* stage = (T*)smem_raw;                                 // [array][slot][H2][RW]
+  T* red = stage + (size_t)Lay::kStaged * kSlots * PLANE;  // [slot][H1][RP]: plane after its red phase
+  const T* U = stage;
+  const T* SKX = stage + (size_t)kSlots * PLANE;
+  const T* SKY = stage + (size_t)2 * kSlots * PLANE;
+  const int s = blockIdx.y, tid = threadIdx.x;
   const int tile = blockIdx.x % ntiles, slab = blockIdx.x / ntiles;
   const int x0 = (tile % ntx) * BX + 1, y0 = (tile / ntx) * BY + 1;  // first owned node
   const int zlo = 1 + slab * zslab, zhi = min(n - 2, zlo + zslab - 1);
-  const size_t n2 = (size_t)n * n, base = (size_t)s * n2 * n;
-  const int ci = tid % W2, cj = tid / W2;
-  const int gx = x0 - 2 + ci, gy = y0 - 2 + cj;
-  const bool in_grid = gx >= 0 && gx < n && gy >= 0 && gy < n;
-  const bool ring1 = ci >= 1 && ci <= W2 - 2 && cj >= 1 && cj <= H2 - 2;
-  const bool owned = ci >= 2 && ci <= W2 - 3 && cj >= 2 && cj <= H2 - 3;
-  const bool interior_col = gx >= 1 && gx <= n - 2 && gy >= 1 && gy <= n - 2;
-  const int c = tid;
-  const int c1 = (cj - 1) * W1 + (ci - 1);
+  const long long n2 = (long long)n * n, base = (long long)s * n2 * n, total = (long long)gridDim.y * n2 * n;
+  const int ci = tid % W2, r0 = 2 * (tid / W2);  // this thread's staged column and first row
+  const int gx = x0 - 2 + ci, gy0 = y0 - 2 + r0;
+  const bool xin = gx >= 1 && gx <= n - 2;
+  const bool yin0 = gy0 >= 1 && gy0 <= n - 2, yin1 = gy0 + 1 >= 1 && gy0 + 1 <= n - 2;
+  const bool cring = ci >= 1 && ci <= W2 - 2;
+  const bool ring0 = cring && r0 >= 1, ring1 = cring && r0 + 1 <= H2 - 2;  // rows r0, r0+1 in the 1-ring
+  const bool owned = ci >= 2 && ci <= W2 - 3 && r0 >= 2 && r0 + 1 <= H2 - 3;
+  const long long col0 = base + (long long)gy0 * n + gx;  // element of (gx, gy0, z = 0)
   if (active && !active[s]) {
-    if (owned && interior_col)
+    if (owned && xin)
       for (int z = zlo; z <= zhi; ++z) {
-        const size_t p = base + (size_t)z * n2 + (size_t)gy * n + gx;
-        uout[p] = uin[p];
+        const long long p = col0 + z * n2;
+        if (yin0) uout[p] = uin[p];
+        if (yin1) uout[p + n] = uin[p + n];
       }
     return;
   }
-  const T* src[NS] = {uin, Kx, Ky};
-  auto sm = [&](int a, int slot, int i) -> T& { return stage[((size_t)a * kSlots + slot) * P2 + i]; };
-  const size_t col = base + (size_t)gy * n + gx;
-  auto issue = [&](int z) {
+  // this thread's 16-byte staging copies: array, destination and the element index of
+  // its row's first staged column (within a plane)
+  int it_a[PT], it_dst[PT], it_row[PT];
+  bool it_on[PT];
+#pragma unroll
+  for (int i = 0; i < PT; ++i) {
+    const int q = tid + i * NT;
+    const int a = q / (H2 * NCH), rem = q % (H2 * NCH), j = rem / NCH, k = rem % NCH;
+    const int gy = y0 - 2 + j;
+    it_on[i] = q < Lay::items && gy >= 0 && gy < n;  // rows outside the grid are never read
+    it_a[i] = a | (k << 2);  // array, and which copy of the row (k E elements after its aligned start)
+    it_dst[i] = (a * kSlots) * PLANE + j * RW + k * E;
+    it_row[i] = gy * n + (x0 - 2);
+  }
+  auto issue = [&](int z, int slot) {
     if (z < 0 || z >= n) return;
-    const int slot = z % kSlots;
-    if (in_grid) {
-      const size_t off = col + (size_t)z * n2;
+    const long long zb = base + z * n2;
 #pragma unroll
-      for (int a = 0; a < NS; ++a) cp_async(&sm(a, slot, c), src[a] + off);
-    } else {
-#pragma unroll
-      for (int a = 0; a < NS; ++a) sm(a, slot, c) = T(0);
+    for (int i = 0; i < PT; ++i) {
+      if (!it_on[i]) continue;
+      const int a = it_a[i] & 3, k = it_a[i] >> 2;
+      const long long cs = ((zb + it_row[i]) & ~(long long)(E - 1)) + (long long)k * E;
+      T* dst = stage + it_dst[i] + slot * PLANE;
+      const T* src = a == 0 ? uin : (a == 1 ? Kx : Ky);
+      if (cs >= 0 && cs + E <= total)
+        cp_async16(dst, src + cs);
+      else
+        *(int4*)dst = make_int4(0, 0, 0, 0);  // beyond the array: never read by an update
     }
   };
-  // this column's Kz, 1/D, g on planes z-2 .. z+2 (m2, m1, c0, p1, p2)
-  const bool need_regs = ring1 && in_grid;
-  auto ld = [&](const T* a, int z) -> T { return (need_regs && z >= 0 && z < n) ? a[col + (size_t)z * n2] : T(0); };
+  // register window of Kz, 1/D, g for both columns of the pair: entry (p - zs + 1) mod 5
+  // holds plane p
+  const bool need0 = ring0 && xin && yin0, need1 = ring1 && xin && yin1;
+  T kz0[kSlots], kz1[kSlots], di0[kSlots], di1[kSlots], g0[kSlots], g1[kSlots];
+  auto load_window = [&](int z, int w) {
+    const bool zin = z >= 0 && z < n;
+    const long long p = col0 + z * n2;
+    kz0[w] = (need0 && zin) ? Kz[p] : T(0);
+    di0[w] = (need0 && zin) ? Dinv[p] : T(0);
+    g0[w] = (need0 && zin) ? g[p] : T(0);
+    kz1[w] = (need1 && zin) ? Kz[p + n] : T(0);
+    di1[w] = (need1 && zin) ? Dinv[p + n] : T(0);
+    g1[w] = (need1 && zin) ? g[p + n] : T(0);
+  };
+  // staged-row offsets: row r0 - 1 + i of plane z starts (zbase + rowlo + i n) mod E
+  // elements after its 16-byte boundary
+  const int colbase = (r0 - 1) * RW + ci;
+  const unsigned rowlo = (unsigned)((long long)(gy0 - 1) * n + (x0 - 2)), un = (unsigned)n;
+  const unsigned ubase = (unsigned)base, un2 = (unsigned)n2;
+  const int rb0 = (r0 - 1) * (RP) + (ci - 1);  // row r0 in red-plane coordinates
   const int zs = zlo - 1, ze = zhi + 1;
-  T kz_m2 = ld(Kz, zs - 2), kz_m1 = ld(Kz, zs - 1), kz_0 = ld(Kz, zs), kz_p1 = ld(Kz, zs + 1), kz_p2;
-  T di_m1 = ld(Dinv, zs - 1), di_0 = ld(Dinv, zs), di_p1 = ld(Dinv, zs + 1), di_p2;
-  T g_m1 = ld(g, zs - 1), g_0 = ld(g, zs), g_p1 = ld(g, zs + 1), g_p2;
 
-  issue(zs - 1);
-  cp_async_commit();
-  issue(zs);
-  cp_async_commit();
-  issue(zs + 1);
-  cp_async_commit();
-  for (int z = zs; z <= ze; ++z) {
-    // slot of plane z+2 held plane z-3, last read before the previous step's barriers
-    issue(z + 2);
+  auto step = [&](auto KC, int z) {
+    constexpr int K = decltype(KC)::value;
+    constexpr int Im2 = (K + 4) % kSlots, Im1 = K % kSlots, I0 = (K + 1) % kSlots, Ip2 = (K + 3) % kSlots;
+    constexpr int S0 = Im1 * PLANE, S1 = I0 * PLANE, S2 = ((K + 2) % kSlots) * PLANE;
+    if (z + 2 <= ze + 1) issue(z + 2, Ip2);
     cp_async_commit();
-    kz_p2 = ld(Kz, z + 2);
-    di_p2 = ld(Dinv, z + 2);
-    g_p2 = ld(g, z + 2);
-    cp_async_wait1();  // planes <= z+1 of this thread's column have landed
-    __syncthreads();   // ... and of every column
-    const int sz = z % kSlots, szm = (z + kSlots - 1) % kSlots, szp = (z + 1) % kSlots;
-    T* rz = red + (size_t)(z % 3) * P1;
-    if (ring1) {
-      T v = sm(0, sz, c);
-      if (z >= 1 && z <= n - 2 && interior_col && ((gx + gy + z) & 1) == 0) {
-        T acc = g_0;
-        acc = fma(sm(1, sz, c - 1), sm(0, sz, c - 1), acc);
-        acc = fma(sm(1, sz, c), sm(0, sz, c + 1), acc);
-        acc = fma(sm(2, sz, c - W2), sm(0, sz, c - W2), acc);
-        acc = fma(sm(2, sz, c), sm(0, sz, c + W2), acc);
-        acc = fma(kz_m1, sm(0, szm, c), acc);
-        acc = fma(kz_0, sm(0, szp, c), acc);
-        v = acc * di_0;
+    load_window(z + 2, Ip2);
+    cp_async_wait1();  // this thread's copies of planes <= z+1 have landed
+    __syncthreads();   // ... and every thread's
+    const int par = (gx + gy0 + z) & 1;  // 0: row r0 is red at z (and black at z-1)
+    const unsigned tz = ubase + (unsigned)z * un2 + rowlo, tm = tz - un2, tp = tz + un2;
+    const int oz0 = (int)(tz & (E - 1)), oz1 = (int)((tz + un) & (E - 1)), oz2 = (int)((tz + 2 * un) & (E - 1)),
+              oz3 = (int)((tz + 3 * un) & (E - 1));
+    const int om0 = (int)(tm & (E - 1)), om1 = (int)((tm + un) & (E - 1)), om2 = (int)((tm + 2 * un) & (E - 1));
+    const int op1 = (int)((tp + un) & (E - 1)), op2 = (int)((tp + 2 * un) & (E - 1));
+    // staged indices (plane z) of the red row, its y neighbours and the other row
+    const int zr0 = colbase + RW + oz1, zr1 = colbase + 2 * RW + oz2;
+    const int rc = par ? zr1 : zr0, oth = par ? zr0 : zr1;
+    const int ym = par ? zr0 : colbase + oz0, yp = par ? colbase + 3 * RW + oz3 : zr1;
+    const int rcm = par ? colbase + 2 * RW + om2 : colbase + RW + om1;  // red row, plane z-1
+    const int ymm = par ? colbase + RW + om1 : colbase + om0;          // its y-1 row, plane z-1
+    const int rcp = par ? colbase + 2 * RW + op2 : colbase + RW + op1;  // red row, plane z+1
+    T* rz = red + I0 * RPLANE;
+    {
+      T vr = U[S1 + rc];
+      const T vo = U[S1 + oth];
+      if ((par ? need1 : need0) && z >= 1 && z <= n - 2) {
+        T acc = par ? g1[I0] : g0[I0];
+        acc = fma(SKX[S1 + rc - 1], U[S1 + rc - 1], acc);
+        acc = fma(SKX[S1 + rc], U[S1 + rc + 1], acc);
+        acc = fma(SKY[S1 + ym], U[S1 + ym], acc);
+        acc = fma(SKY[S1 + rc], U[S1 + yp], acc);
+        acc = fma(par ? kz1[Im1] : kz0[Im1], U[S0 + rcm], acc);
+        acc = fma(par ? kz1[I0] : kz0[I0], U[S2 + rcp], acc);
+        vr = acc * (par ? di1[I0] : di0[I0]);
       }
-      rz[c1] = v;
+      if (ring0) rz[rb0] = par ? vo : vr;
+      if (ring1) rz[rb0 + RP] = par ? vr : vo;
     }
     __syncthreads();
-    if (z > zs) {
-      const int zb = z - 1, sb = szm;
-      if (owned && interior_col && zb >= zlo && zb <= zhi) {
-        const T* rb = red + (size_t)(zb % 3) * P1;
-        T v = rb[c1];
-        if (((gx + gy + zb) & 1) == 1) {
-          const T* rbm = red + (size_t)((zb + 2) % 3) * P1;  // plane z-2
-          T acc = g_m1;
-          acc = fma(sm(1, sb, c - 1), rb[c1 - 1], acc);
-          acc = fma(sm(1, sb, c), rb[c1 + 1], acc);
-          acc = fma(sm(2, sb, c - W2), rb[c1 - W1], acc);
-          acc = fma(sm(2, sb, c), rb[c1 + W1], acc);
-          acc = fma(kz_m2, rbm[c1], acc);
-          acc = fma(kz_m1, rz[c1], acc);
-          v = acc * di_m1;
-        }
-        uout[col + (size_t)zb * n2] = v;
+    const int zb = z - 1;
+    if (owned && xin && zb >= zlo && zb <= zhi) {
+      const T* Rb = red + Im1 * RPLANE;  // plane z-1 after red
+      const T* Rm = red + Im2 * RPLANE;  // plane z-2 after red
+      const int rr = rb0 + (par ? RP : 0);  // the black row of plane z-1 (the red row of plane z)
+      const T yl = Rb[rr - RP], yh = Rb[rr + RP];
+      T vb;
+      {
+        T acc = par ? g1[Im1] : g0[Im1];
+        acc = fma(SKX[S0 + rcm - 1], Rb[rr - 1], acc);
+        acc = fma(SKX[S0 + rcm], Rb[rr + 1], acc);
+        acc = fma(SKY[S0 + ymm], yl, acc);
+        acc = fma(SKY[S0 + rcm], yh, acc);
+        acc = fma(par ? kz1[Im2] : kz0[Im2], Rm[rr], acc);
+        acc = fma(par ? kz1[Im1] : kz0[Im1], rz[rr], acc);
+        vb = acc * (par ? di1[Im1] : di0[Im1]);
       }
+      // row r0 / r0+1 of plane z-1: the black result and the other row's red value
+      const long long p = col0 + zb * n2;
+      if (yin0) uout[p] = par ? yl : vb;
+      if (yin1) uout[p + n] = par ? vb : yh;
     }
-    // advance the register window by one plane
-    kz_m2 = kz_m1;
-    kz_m1 = kz_0;
-    kz_0 = kz_p1;
-    kz_p1 = kz_p2;
-    di_m1 = di_0;
-    di_0 = di_p1;
-    di_p1 = di_p2;
-    g_m1 = g_0;
-    g_0 = g_p1;
-    g_p1 = g_p2;
+  };
+
+  load_window(zs - 2, kSlots - 1);
+  load_window(zs - 1, 0);
+  load_window(zs, 1);
+  load_window(zs + 1, 2);
+  issue(zs - 1, 0);
+  cp_async_commit();
+  issue(zs, 1);
+  cp_async_commit();
+  issue(zs + 1, 2);
+  cp_async_commit();
+  for (int z = zs; z <= ze; z += kSlots) {
+    step(StepK<0>{}, z);
+    if (z + 1 > ze) break;
+    step(StepK<1>{}, z + 1);
+    if (z + 2 > ze) break;
+    step(StepK<2>{}, z + 2);
+    if (z + 3 > ze) break;
+    step(StepK<3>{}, z + 3);
+    if (z + 4 > ze) break;
+    step(StepK<4>{}, z + 4);
   }
 }
 
@@ -408,12 +472,6 @@ template <typename T, int BX, int BY>
 int launch_bulk(int n, int B, const T* Kx, const T* Ky, const T* Kz, const T* Dinv, const T* g, const T* uin,
                 T* uout, const int* active, int* err, cudaStream_t st) {
   using Lay = BulkLayout<T, BX, BY>;
-  static bool configured = false;
-  if (!configured) {
-    MLMC_CUDA_TRY(cudaFuncSetAttribute(k_rbgs_bulk<T, BX, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Lay::bytes));
-    configured = true;
-  }
   const int m = n - 2;
   const int ntx = (m + BX - 1) / BX, nty = (m + BY - 1) / BY, ntiles = ntx * nty;
   int slabs = (int)((152LL * 12 + (long long)ntiles * B - 1) / ((long long)ntiles * B));
@@ -427,23 +485,29 @@ int launch_bulk(int n, int B, const T* Kx, const T* Ky, const T* Kz, const T* Di
   return MLMC_OK;
 }
 
+// z-slab count of a fused sweep: each slab re-stages four planes of u, Kx, Ky and six
+// of Kz, 1/D, g around its ends, and the CTAs of a launch spread over 152 SMs, so the
+// count minimises (CTAs per SM, rounded up) x (planes a CTA streams); slabs of at least
+// 8 planes. The result of the sweep does not depend on the split.
+inline int fused_slabs(int m, long long ctas_per_slab) {
+  int best = 1;
+  long long best_cost = -1;
+  for (int sl = 1; sl <= (m / 8 > 1 ? m / 8 : 1); ++sl) {
+    const int zslab = (m + sl - 1) / sl, used = (m + zslab - 1) / zslab;
+    const long long per_sm = (ctas_per_slab * used + 151) / 152;
+    const long long cost = per_sm * (zslab + 6);
+    if (best_cost < 0 || cost < best_cost) best_cost = cost, best = used;
+  }
+  return best;
+}
+
 template <typename T, int BX, int BY>
 int launch_shape(int n, int B, const T* Kx, const T* Ky, const T* Kz, const T* Dinv, const T* g, const T* uin,
                  T* uout, const int* active, cudaStream_t st) {
   using Lay = FusedLayout<T, BX, BY>;
-  static bool configured = false;  // per template instance; attribute set once per process
-  if (!configured) {
-    MLMC_CUDA_TRY(cudaFuncSetAttribute(k_rbgs_fused<T, BX, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Lay::bytes));
-    configured = true;
-  }
   const int m = n - 2;
   const int ntx = (m + BX - 1) / BX, nty = (m + BY - 1) / BY, ntiles = ntx * nty;
-  // split z into independent slabs until the launch has ~12 CTAs per SM (the result is
-  // the same for any split); slabs of at least 8 planes
-  int slabs = (int)((152LL * 12 + (long long)ntiles * B - 1) / ((long long)ntiles * B));
-  if (slabs > m / 8) slabs = m / 8;
-  if (slabs < 1) slabs = 1;
+  int slabs = fused_slabs(m, (long long)ntiles * B);
   const int zslab = (m + slabs - 1) / slabs;
   slabs = (m + zslab - 1) / zslab;
   dim3 grid((unsigned)(ntiles * slabs), (unsigned)B);
@@ -453,6 +517,42 @@ int launch_shape(int n, int B, const T* Kx, const T* Ky, const T* Kz, const T* D
 }
 
 }  // namespace
+
+// The dynamic shared-memory opt-in of each kernel instance, set once per process (the
+// library drives one device per process). Function-local statics make the first call
+// thread-safe; it happens before any stream capture because solve setup configures
+// every fused level first.
+template <typename T, int BX, int BY>
+int configure_shape() {
+  using Lay = FusedLayout<T, BX, BY>;
+  static const cudaError_t e = cudaFuncSetAttribute(k_rbgs_fused<T, BX, BY>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
+  MLMC_CUDA_TRY(e);
+  return MLMC_OK;
+}
+
+template <typename T, int BX, int BY>
+int configure_bulk() {
+  using Lay = BulkLayout<T, BX, BY>;
+  static const cudaError_t e = cudaFuncSetAttribute(k_rbgs_bulk<T, BX, BY>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
+  MLMC_CUDA_TRY(e);
+  return MLMC_OK;
+}
+
+template <typename T>
+int rbgs_fused_configure(int shape) {
+  switch (shape) {
+    case kTile32x16: return configure_shape<T, 32, 16>();
+    case kTile64x8: return configure_shape<T, 64, 8>();
+    case kBulk32x8: return configure_bulk<T, 32, 8>();
+    case kBulk32x16: return configure_bulk<T, 32, 16>();
+    case kBulk64x8: return configure_bulk<T, 64, 8>();
+    default: return configure_shape<T, 32, 8>();
+  }
+}
+template int rbgs_fused_configure<float>(int);
+template int rbgs_fused_configure<double>(int);
 
 const char* tile_name(int shape) {
   switch (shape) {
@@ -474,6 +574,7 @@ int rbgs_fused_sweep(int shape, int n, int B, const T* Kx, const T* Ky, const T*
   const char* cls = bulk ? (sizeof(T) == 4 ? "rbgs_bulk_f32" : "rbgs_bulk_f64")
                          : (sizeof(T) == 4 ? "rbgs_fused_f32" : "rbgs_fused_f64");
   // one full sweep: 7 words per interior node (u read + write, Kx, Ky, Kz, Dinv, g), 13 flops
+  MLMC_TRY(rbgs_fused_configure<T>(shape));
   prof::Scope scope(cls, B * interior * 7.0 * sizeof(T), B * interior * 13.0, st);
   switch (shape) {
     case kTile32x16:

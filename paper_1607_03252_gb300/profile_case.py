@@ -1,11 +1,13 @@
 """One small batched field evaluation + multigrid solve, for kernel profiling.
 
   python -m paper_1607_03252_gb300.profile_case --n 129 --batch 8 --prec f64 --cycles 2 \
-      [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8] [--accel cg]
+      [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8] [--accel cg] [--timing]
 
 Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256) for `batch` realisations
 on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0) through the C ABI, so
-that every kernel class launches with the sizes of that grid. Exits 0 on success.
+that every kernel class launches with the sizes of that grid. With --timing the solve runs
+twice and the second run records CUDA events around every launch: per kernel class it
+prints launches, device time per launch and algorithmic GB/s. Exits 0 on success.
 """
 from __future__ import annotations
 
@@ -28,6 +30,7 @@ def main(argv=None):
     p.add_argument("--smoother", choices=["auto", "two-pass", "32x8", "32x16", "64x8", "bulk32x8", "bulk32x16",
                                           "bulk64x8"], default="auto")
     p.add_argument("--accel", choices=["none", "cg"], default="none")
+    p.add_argument("--timing", action="store_true")
     a = p.parse_args(argv)
     prec = mg.MLMC_PREC_F64 if a.prec == "f64" else mg.MLMC_PREC_MIXED
     sm = {"auto": mg.MLMC_SMOOTH_AUTO, "two-pass": mg.MLMC_SMOOTH_TWO_PASS, "32x8": mg.MLMC_SMOOTH_FUSED_32x8,
@@ -38,9 +41,25 @@ def main(argv=None):
     k = torch.empty((a.batch, a.n, a.n, a.n), dtype=torch.float64, device="cuda")
     mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, 1.0, 0.3, a.M), sample_ids(3, 0, a.batch), k)
     u = torch.zeros_like(k)
-    cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 0.0, a.cycles, prec, sm, accel), k, u)
+    cfg = mg.mg_cfg(2, 2, 0.0, a.cycles, prec, sm, accel)
+    cyc, rel, st = mg.mg_solve_batch(cfg, k, u)
     torch.cuda.synchronize()
     print("n=%d batch=%d prec=%s cycles=%s rel_res=%.3e" % (a.n, a.batch, a.prec, cyc.tolist(), rel.max()))
+    if a.timing:
+        u.zero_()
+        mg.profile_reset()
+        mg.profile_enable(True)
+        mg.mg_solve_batch(cfg, k, u)
+        torch.cuda.synchronize()
+        mg.profile_enable(False)
+        prof = mg.profile_read()
+        for name, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+            if v["timed"] == 0:
+                continue
+            per = v["ms"] / v["timed"]
+            gbs = v["bytes"] / v["launches"] / (per * 1e-3) / 1e9 if per > 0 else 0.0
+            print("  %-22s launches %5d  %9.3f us/launch  %8.1f GB/s algorithmic" % (name, v["launches"], per * 1e3,
+                                                                                   gbs))
     return 0
 
 
