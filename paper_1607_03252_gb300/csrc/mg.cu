@@ -39,6 +39,15 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxLevels = 12;
+constexpr int kPlaneThreads = 128;
+
+// Plane launches: blockIdx.x (with threadIdx.x) enumerates the work items of one z-plane,
+// blockIdx.y strides over the (sample, z) planes, so every in-sample index is 32-bit
+// (n^3 < 2^31 for every valid n) and no thread divides a 64-bit index.
+inline dim3 plane_grid(int per_plane, long long planes) {
+  return dim3((unsigned)((per_plane + kPlaneThreads - 1) / kPlaneThreads),
+              (unsigned)(planes < 65535 ? (planes > 0 ? planes : 1) : 65535));
+}
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -69,13 +78,15 @@ __device__ __forceinline__ float harm(double a, double b, float) {
 template <typename T>
 __global__ void k_faces(const double* __restrict__ k0, int n0, int st0, int n, int B, T* __restrict__ Kx,
                         T* __restrict__ Ky, T* __restrict__ Kz) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
   const size_t n3 = (size_t)n * n * n, n03 = (size_t)n0 * n0 * n0;
-  const size_t total = (size_t)B * n3;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t s = t / n3, r = t - s * n3;
-    const int z = (int)(r / ((size_t)n * n)), y = (int)((r / n) % n), x = (int)(r % n);
-    const double* kb = k0 + s * n03;
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    const double* kb = k0 + (size_t)s * n03;
     const size_t p0 = ((size_t)(st0 * z) * n0 + (size_t)(st0 * y)) * n0 + (size_t)(st0 * x);
+    const size_t t = (size_t)s * n3 + (size_t)(z * n * n + q);
     const double a = kb[p0];
     Kx[t] = x < n - 1 ? harm(a, kb[p0 + st0], T()) : T(0);
     Ky[t] = y < n - 1 ? harm(a, kb[p0 + (size_t)st0 * n0], T()) : T(0);
@@ -87,11 +98,13 @@ __global__ void k_faces(const double* __restrict__ k0, int n0, int st0, int n, i
 template <typename T, typename TD>
 __global__ void k_diag(int n, int B, const T* __restrict__ Kx, const T* __restrict__ Ky, const T* __restrict__ Kz,
                        TD* __restrict__ D, TD* __restrict__ Dinv) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
   const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
-  const size_t total = (size_t)B * n3;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t r = t % n3;
-    const int z = (int)(r / n2), y = (int)((r / n) % n), x = (int)(r % n);
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    const size_t t = (size_t)s * n3 + (size_t)(z * n * n + q);
     const bool in = x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1;
     TD d = 0;
     if (in) {
@@ -199,18 +212,18 @@ template <typename T>
 __global__ void k_rbgs(int colour, int n, int B, const T* __restrict__ Kx, const T* __restrict__ Ky,
                        const T* __restrict__ Kz, const T* __restrict__ Dinv, const T* __restrict__ g, T* __restrict__ u,
                        const int* __restrict__ active) {
-  const int m = n - 2, half = (n - 1) / 2;
-  const size_t rows = (size_t)m * m, n3 = (size_t)n * n * n, n2 = (size_t)n * n;
-  const size_t total = (size_t)B * rows * half;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int xi = (int)(t % half);
-    const size_t rr = t / half;
-    const size_t row = rr % rows, s = rr / rows;
+  // n = 2^p + 1: a row holds half = 2^(p-1) nodes of each colour
+  const int m = n - 2, half = (n - 1) / 2, lh = 31 - __clz(half);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // colour node of an interior plane
+  if (q >= m * half) return;
+  const int xi = q & (half - 1), y = 1 + (q >> lh);
+  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
+  for (int zz = blockIdx.y; zz < B * m; zz += gridDim.y) {
+    const int s = zz / m, z = 1 + (zz - s * m);
     if (active && !active[s]) continue;
-    const int y = 1 + (int)(row % m), z = 1 + (int)(row / m);
     const int x = (((1 + y + z) & 1) == colour ? 1 : 2) + 2 * xi;
     if (x > n - 2) continue;
-    const size_t p = s * n3 + (size_t)z * n2 + (size_t)y * n + x;
+    const size_t p = (size_t)s * n3 + (size_t)(z * n * n + y * n + x);
     T acc = g[p];
     acc = fma(Kx[p - 1], u[p - 1], acc);
     acc = fma(Kx[p], u[p + 1], acc);
@@ -259,12 +272,13 @@ __global__ void __launch_bounds__(kThreads)
                double* __restrict__ partial, const int* __restrict__ active) {
   const int s = blockIdx.y;
   if (active && !active[s]) return;
-  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
-  const size_t chunk = (n3 + gridDim.x - 1) / gridDim.x;
-  const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  const unsigned n3 = (unsigned)n * n * n, n2 = (unsigned)n * n, un = (unsigned)n;
+  const unsigned chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const unsigned lo = blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
   double sq = 0.0;
-  for (size_t i = lo + threadIdx.x; i < hi; i += kThreads) {
-    const int z = (int)(i / n2), y = (int)((i / n) % n), x = (int)(i % n);
+  for (unsigned i = lo + threadIdx.x; i < hi; i += kThreads) {
+    const unsigned zq = i / n2, rem = i - zq * n2, yq = rem / un;
+    const int z = (int)zq, y = (int)yq, x = (int)(rem - yq * un);
     const size_t p = (size_t)s * n3 + i;
     TD rr = 0;
     if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
@@ -288,12 +302,13 @@ __global__ void __launch_bounds__(kThreads)
 // Sum of squares over interior nodes of an FP64 array (initial ||g||). Grid (NB, B).
 __global__ void __launch_bounds__(kThreads) k_sumsq(int n, const double* __restrict__ v, double* __restrict__ partial) {
   const int s = blockIdx.y;
-  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
-  const size_t chunk = (n3 + gridDim.x - 1) / gridDim.x;
-  const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  const unsigned n3 = (unsigned)n * n * n, n2 = (unsigned)n * n, un = (unsigned)n;
+  const unsigned chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const unsigned lo = blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
   double sq = 0.0;
-  for (size_t i = lo + threadIdx.x; i < hi; i += kThreads) {
-    const int z = (int)(i / n2), y = (int)((i / n) % n), x = (int)(i % n);
+  for (unsigned i = lo + threadIdx.x; i < hi; i += kThreads) {
+    const unsigned zq = i / n2, rem = i - zq * n2, yq = rem / un;
+    const int z = (int)zq, y = (int)yq, x = (int)(rem - yq * un);
     if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
       const double a = v[(size_t)s * n3 + i];
       sq += a * a;
@@ -337,58 +352,63 @@ __global__ void k_norm_update(int B, int NB, const double* __restrict__ partial,
   if (still) atomicAdd(n_active, 1);
 }
 
-// g_c = 4 FW(r~) at interior coarse nodes, 0 on the coarse boundary.
+// g_c = 4 FW(r~) at interior coarse nodes (the coarse boundary of g_c is zeroed once per
+// solve and never written).
 template <typename T>
 __global__ void k_restrict(int nf, int B, const T* __restrict__ r, T* __restrict__ gc, const int* __restrict__ active) {
-  const int nc = (nf + 1) / 2;
-  const size_t nc3 = (size_t)nc * nc * nc, nf3 = (size_t)nf * nf * nf, nf2 = (size_t)nf * nf;
-  const size_t total = (size_t)B * nc3;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t s = t / nc3, q = t - s * nc3;
+  // nc - 1 = 2^(p-1) = hc: an interior coarse row is X = 1 .. hc - 1
+  const int nc = (nf + 1) / 2, hc = nc - 1, lc = 31 - __clz(hc);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // interior coarse node of a plane
+  if (q >= (nc - 2) * hc) return;
+  const int X = 1 + (q & (hc - 1)), Y = 1 + (q >> lc);
+  if (X > nc - 2) return;
+  const size_t nc3 = (size_t)nc * nc * nc, nf3 = (size_t)nf * nf * nf;
+  const int nf2 = nf * nf;
+  for (int zz = blockIdx.y; zz < B * (nc - 2); zz += gridDim.y) {
+    const int s = zz / (nc - 2), Z = 1 + (zz - s * (nc - 2));
     if (active && !active[s]) continue;
-    const int Z = (int)(q / ((size_t)nc * nc)), Y = (int)((q / nc) % nc), X = (int)(q % nc);
+    const T* rb = r + (size_t)s * nf3 + (size_t)(2 * Z * nf2 + 2 * Y * nf + 2 * X);
     T v = 0;
-    if (X > 0 && Y > 0 && Z > 0 && X < nc - 1 && Y < nc - 1 && Z < nc - 1) {
-      const T* rb = r + s * nf3 + (size_t)(2 * Z) * nf2 + (size_t)(2 * Y) * nf + 2 * X;
-      for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            const T wgt = (T)((2 - abs(dx)) * (2 - abs(dy)) * (2 - abs(dz))) * (T)(1.0 / 16.0);
-            v = fma(wgt, rb[(ptrdiff_t)dz * (ptrdiff_t)nf2 + (ptrdiff_t)dy * nf + dx], v);
-          }
-    }
-    gc[t] = v;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const T wgt = (T)((2 - abs(dx)) * (2 - abs(dy)) * (2 - abs(dz))) * (T)(1.0 / 16.0);
+          v = fma(wgt, rb[dz * nf2 + dy * nf + dx], v);
+        }
+    gc[(size_t)s * nc3 + (size_t)((Z * nc + Y) * nc + X)] = v;
   }
 }
 
 // u_f += trilinear interpolation of e_c at interior fine nodes: a fine node with k odd
 // coordinates is the mean of its 2^k coarse neighbours (k = 0: the coincident coarse
-// node). Threads of a row take the even x first and the odd x after them, so that a warp
+// node). Threads of a row take the odd x first and the even x after them, so that a warp
 // shares one parity pattern and sums only the distinct neighbours (4.3 instead of 8
 // terms per node on average).
 template <typename T>
 __global__ void k_prolong(int nf, int B, const T* __restrict__ ec, T* __restrict__ u, const int* __restrict__ active) {
-  const int nc = (nf + 1) / 2, he = (nf + 1) / 2;  // he: even x values per row
-  const size_t nc3 = (size_t)nc * nc * nc, nf3 = (size_t)nf * nf * nf, nf2 = (size_t)nf * nf;
-  const size_t total = (size_t)B * nf3;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t s = t / nf3, q = t - s * nf3;
+  // nf - 1 = 2^p = P: interior x of a row, odd ones (r < P/2: x = 2r + 1) then even ones
+  const int nc = (nf + 1) / 2, P = nf - 1, lp = 31 - __clz(P), hp = P >> 1;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (nf - 2) * P) return;
+  const int rr = q & (P - 1), y = 1 + (q >> lp);
+  const int x = rr < hp ? 2 * rr + 1 : 2 * (rr - hp) + 2;
+  if (x > nf - 2) return;
+  const size_t nc3 = (size_t)nc * nc * nc, nf3 = (size_t)nf * nf * nf;
+  const int xo = x & 1, yo = y & 1, X = x >> 1, Y = y >> 1;
+  for (int zz = blockIdx.y; zz < B * (nf - 2); zz += gridDim.y) {
+    const int s = zz / (nf - 2), z = 1 + (zz - s * (nf - 2));
     if (active && !active[s]) continue;
-    const int z = (int)(q / nf2), y = (int)((q / nf) % nf), r = (int)(q % nf);
-    const int x = r < he ? 2 * r : 2 * (r - he) + 1;
-    if (!(x > 0 && y > 0 && z > 0 && x < nf - 1 && y < nf - 1 && z < nf - 1)) continue;
-    const int xo = x & 1, yo = y & 1, zo = z & 1;
-    const int X = x >> 1, Y = y >> 1, Z = z >> 1;
-    const T* eb = ec + s * nc3;
+    const int zo = z & 1, Z = z >> 1;
+    const T* eb = ec + (size_t)s * nc3;
     T v = 0;
     for (int dz = 0; dz <= zo; ++dz)
       for (int dy = 0; dy <= yo; ++dy) {
-        const T* row = eb + ((size_t)(Z + dz) * nc + (Y + dy)) * nc + X;
+        const T* row = eb + ((Z + dz) * nc + (Y + dy)) * nc + X;
         v += row[0];
         if (xo) v += row[1];
       }
     const T w = xo + yo + zo == 0 ? T(1) : xo + yo + zo == 1 ? T(0.5) : xo + yo + zo == 2 ? T(0.25) : T(0.125);
-    const size_t p = s * nf3 + (size_t)z * nf2 + (size_t)y * nf + x;
+    const size_t p = (size_t)s * nf3 + (size_t)((z * nf + y) * nf + x);
     u[p] += w * v;
   }
 }
@@ -396,11 +416,13 @@ __global__ void k_prolong(int nf, int B, const T* __restrict__ ec, T* __restrict
 // g = h^2 f (f == NULL: h^2) on interior nodes, 0 on the boundary; u boundary := 0.
 __global__ void k_prepare(int n, int B, double h2, const double* __restrict__ f, double* __restrict__ g,
                           double* __restrict__ u) {
-  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
-  const size_t total = (size_t)B * n3;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t r = t % n3;
-    const int z = (int)(r / n2), y = (int)((r / n) % n), x = (int)(r % n);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
+  const size_t n3 = (size_t)n * n * n;
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    const size_t t = (size_t)s * n3 + (size_t)(z * n * n + q);
     const bool in = x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1;
     g[t] = in ? h2 * (f ? f[t] : 1.0) : 0.0;
     if (!in) u[t] = 0.0;
@@ -410,11 +432,13 @@ __global__ void k_prepare(int n, int B, double h2, const double* __restrict__ f,
 // Mixed refinement update u64 += e32 at interior nodes of active samples.
 __global__ void k_update_mixed(int n, int B, const float* __restrict__ e, double* __restrict__ u,
                                const int* __restrict__ active) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
   const size_t n3 = (size_t)n * n * n;
-  const size_t total = (size_t)B * n3;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t s = t / n3;
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
     if (!active[s]) continue;
+    const size_t t = (size_t)s * n3 + (size_t)(z * n * n + q);
     u[t] += (double)e[t];  // e is zero on the boundary
   }
 }
@@ -423,12 +447,14 @@ __global__ void k_update_mixed(int n, int B, const float* __restrict__ e, double
 __global__ void __launch_bounds__(kThreads) k_qoi(int n, const double* __restrict__ u, double* __restrict__ partial) {
   const int s = blockIdx.y;
   const int lo = (n - 1) / 4, S = (n - 1) / 2 + 1;
-  const size_t S3 = (size_t)S * S * S, n3 = (size_t)n * n * n;
-  const size_t chunk = (S3 + gridDim.x - 1) / gridDim.x;
-  const size_t a = (size_t)blockIdx.x * chunk, b = a + chunk < S3 ? a + chunk : S3;
+  const unsigned S3 = (unsigned)S * S * S, S2 = (unsigned)S * S, uS = (unsigned)S;
+  const size_t n3 = (size_t)n * n * n;
+  const unsigned chunk = (S3 + gridDim.x - 1) / gridDim.x;
+  const unsigned a = blockIdx.x * chunk, b = a + chunk < S3 ? a + chunk : S3;
   double sum = 0.0, comp = 0.0;
-  for (size_t i = a + threadIdx.x; i < b; i += kThreads) {
-    const int cz = (int)(i / ((size_t)S * S)), cy = (int)((i / S) % S), cx = (int)(i % S);
+  for (unsigned i = a + threadIdx.x; i < b; i += kThreads) {
+    const unsigned czq = i / S2, rem = i - czq * S2, cyq = rem / uS;
+    const int cz = (int)czq, cy = (int)cyq, cx = (int)(rem - cyq * uS);
     const double w = (cx == 0 || cx == S - 1 ? 0.5 : 1.0) * (cy == 0 || cy == S - 1 ? 0.5 : 1.0) *
                      (cz == 0 || cz == S - 1 ? 0.5 : 1.0);
     const double v = w * u[(size_t)s * n3 + ((size_t)(lo + cz) * n + (lo + cy)) * n + (lo + cx)];
@@ -462,12 +488,13 @@ __global__ void __launch_bounds__(kThreads)
                 double* __restrict__ partial, const int* __restrict__ active) {
   const int s = blockIdx.y;
   if (!active[s]) return;
-  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
-  const size_t chunk = (n3 + gridDim.x - 1) / gridDim.x;
-  const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  const unsigned n3 = (unsigned)n * n * n, n2 = (unsigned)n * n, un = (unsigned)n;
+  const unsigned chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const unsigned lo = blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
   double acc = 0.0;
-  for (size_t i = lo + threadIdx.x; i < hi; i += kThreads) {
-    const int z = (int)(i / n2), y = (int)((i / n) % n), x = (int)(i % n);
+  for (unsigned i = lo + threadIdx.x; i < hi; i += kThreads) {
+    const unsigned zq = i / n2, rem = i - zq * n2, yq = rem / un;
+    const int z = (int)zq, y = (int)yq, x = (int)(rem - yq * un);
     const size_t t = (size_t)s * n3 + i;
     double v = 0.0;
     if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
@@ -495,12 +522,12 @@ __global__ void __launch_bounds__(kThreads)
                 double* __restrict__ part_rz, const int* __restrict__ active) {
   const int s = blockIdx.y;
   if (!active[s]) return;
-  const size_t n3 = (size_t)n * n * n;
-  const size_t chunk = (n3 + gridDim.x - 1) / gridDim.x;
-  const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  const unsigned n3 = (unsigned)n * n * n;
+  const unsigned chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const unsigned lo = blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
   const double a = alpha[s];
   double rr = 0.0, rz = 0.0;
-  for (size_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+  for (unsigned i = lo + threadIdx.x; i < hi; i += kThreads) {
     const size_t t = (size_t)s * n3 + i;
     x[t] = fma(a, p[t], x[t]);
     const double rn = fma(-a, q[t], r[t]);  // q and p vanish on the boundary
@@ -521,11 +548,11 @@ __global__ void __launch_bounds__(kThreads)
                   double* __restrict__ partial, const int* __restrict__ active) {
   const int s = blockIdx.y;
   if (!active[s]) return;
-  const size_t n3 = (size_t)n * n * n;
-  const size_t chunk = (n3 + gridDim.x - 1) / gridDim.x;
-  const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  const unsigned n3 = (unsigned)n * n * n;
+  const unsigned chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const unsigned lo = blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
   double acc = 0.0;
-  for (size_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+  for (unsigned i = lo + threadIdx.x; i < hi; i += kThreads) {
     const size_t t = (size_t)s * n3 + i;
     double zv;
     if (e32) {
@@ -543,10 +570,13 @@ __global__ void __launch_bounds__(kThreads)
 // p = z + beta p (beta = 0: p = z).
 __global__ void k_p_update(int n, int B, const double* __restrict__ beta, const double* __restrict__ z,
                            double* __restrict__ p, const int* __restrict__ active) {
-  const size_t n3 = (size_t)n * n * n, total = (size_t)B * n3;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t s = t / n3;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const size_t n3 = (size_t)n * n * n;
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, zp = zz - s * n;
     if (!active[s]) continue;
+    const size_t t = (size_t)s * n3 + (size_t)(zp * n * n + q);
     p[t] = beta ? fma(beta[s], p[t], z[t]) : z[t];
   }
 }
@@ -702,8 +732,8 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
                 (k_coarse_apply<T><<<(B * 27 + 127) / 128, 128, 0, st>>>(B, H.Ainv, v.g, v.u, act)));
     return;
   }
-  const size_t nsweep = (size_t)B * (v.n - 2) * (v.n - 2) * ((v.n - 1) / 2);
-  const unsigned gs = blocks_for(nsweep, kThreads);
+  const int m = v.n - 2;
+  const dim3 gs = plane_grid(m * ((v.n - 1) / 2), (long long)B * m);
   // one colour: half of the 7 words per node of a full sweep; 13 flops per updated node
   const double sweep_bytes = B * interior(v.n) * 3.5 * W, sweep_flops = B * interior(v.n) * 0.5 * 13.0;
   auto smooth = [&](int sweeps) {
@@ -716,7 +746,7 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
       } else {
         for (int c = 0; c < 2; ++c)
           MLMC_LAUNCH(Names<T>::rbgs, sweep_bytes, sweep_flops, st,
-                      (k_rbgs<T><<<gs, kThreads, 0, st>>>(c, v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, act)));
+                      (k_rbgs<T><<<gs, kPlaneThreads, 0, st>>>(c, v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, act)));
       }
     }
   };
@@ -727,11 +757,13 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
                                                               act)));
   Level<T>& w = H.lv[j + 1];
   MLMC_LAUNCH(Names<T>::restrict_, B * ((double)v.n3 + (double)w.n3) * W, B * interior(w.n) * 54.0, st,
-              (k_restrict<T><<<blocks_for((size_t)B * w.n3, kThreads), kThreads, 0, st>>>(v.n, B, v.r, w.g, act)));
+              (k_restrict<T><<<plane_grid((w.n - 2) * (w.n - 1), (long long)B * (w.n - 2)), kPlaneThreads, 0, st>>>(
+                  v.n, B, v.r, w.g, act)));
   cudaMemsetAsync(w.u, 0, (size_t)B * w.n3 * sizeof(T), st);
   vcycle(H, j + 1, nu1, nu2, st);
   MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
-              (k_prolong<T><<<blocks_for((size_t)B * v.n3, kThreads), kThreads, 0, st>>>(v.n, B, w.u, v.u, act)));
+              (k_prolong<T><<<plane_grid(m * (v.n - 1), (long long)B * m), kPlaneThreads, 0, st>>>(v.n, B, w.u, v.u,
+                                                                                                  act)));
   smooth(nu2);
 }
 
@@ -789,6 +821,7 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   dim3 rg(H.NB, B);
   const unsigned sb = (B + 3) / 4;  // 128-thread blocks, one warp per sample
   const unsigned g0 = blocks_for((size_t)B * l0.n3, kThreads);
+  const dim3 pg = plane_grid(n * n, (long long)B * n);
   const double* D = mixed ? H.D64 : (const double*)(const void*)l0.D;
   auto sync_count = [&](int* out) -> int {
     MLMC_CUDA_TRY(cudaMemcpyAsync(out, H.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -824,7 +857,7 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   MLMC_LAUNCH("cg_scalar", B * H.NB * 8.0, 0.0, st,
               (k_cg_scalar<<<sb, 128, 0, st>>>(B, H.NB, 0, H.partial, H.rz, H.rzo, H.alpha, H.beta, H.active)));
   MLMC_LAUNCH("cg_p_update", all * 16.0, 0.0, st,
-              (k_p_update<<<g0, kThreads, 0, st>>>(n, B, nullptr, zcur(), H.P, H.active)));
+              (k_p_update<<<pg, kPlaneThreads, 0, st>>>(n, B, nullptr, zcur(), H.P, H.active)));
   while (true) {
     MLMC_LAUNCH("cg_apply_dot", nodes * (3 * Wk + 8 + 16), nodes * 16.0, st,
                 (k_apply_dot<T, double><<<rg, kThreads, 0, st>>>(n, l0.Kx, l0.Ky, l0.Kz, D, H.P, H.Q, H.partial,
@@ -847,7 +880,7 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
     MLMC_LAUNCH("cg_scalar", B * H.NB * 8.0, 0.0, st,
                 (k_cg_scalar<<<sb, 128, 0, st>>>(B, H.NB, 2, H.partial, H.rz, H.rzo, H.alpha, H.beta, H.active)));
     MLMC_LAUNCH("cg_p_update", all * 24.0, nodes * 2.0, st,
-                (k_p_update<<<g0, kThreads, 0, st>>>(n, B, H.beta, zcur(), H.P, H.active)));
+                (k_p_update<<<pg, kPlaneThreads, 0, st>>>(n, B, H.beta, zcur(), H.P, H.active)));
   }
   return MLMC_OK;
 }
@@ -866,11 +899,13 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   int stride = a.st0;
   for (int j = 0; j < H.L; ++j) {
     Level<T>& v = H.lv[j];
-    const unsigned gb = blocks_for((size_t)B * v.n3, kThreads);
+    const dim3 gb = plane_grid(v.n * v.n, (long long)B * v.n);
     MLMC_LAUNCH(Names<T>::faces, B * (double)v.n3 * (8.0 + 3 * W), B * (double)v.n3 * 12.0, st,
-                (k_faces<T><<<gb, kThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, v.Kx, v.Ky, v.Kz)));
+                (k_faces<T><<<gb, kPlaneThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, v.Kx, v.Ky, v.Kz)));
     MLMC_LAUNCH(Names<T>::diag, B * (double)v.n3 * 5 * W, B * (double)v.n3 * 6.0, st,
-                (k_diag<T, T><<<gb, kThreads, 0, st>>>(v.n, B, v.Kx, v.Ky, v.Kz, v.D, v.Dinv)));
+                (k_diag<T, T><<<gb, kPlaneThreads, 0, st>>>(v.n, B, v.Kx, v.Ky, v.Kz, v.D, v.Dinv)));
+    // restriction writes only interior coarse nodes: the boundary of g stays zero
+    if (j > 0) MLMC_CUDA_TRY(cudaMemsetAsync(v.g, 0, (size_t)B * v.n3 * sizeof(T), st));
     stride *= 2;
   }
   // smoother per level (explicit choice, or the tuned / default one for that grid) and
@@ -906,14 +941,16 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   const unsigned g0 = blocks_for((size_t)B * l0.n3, kThreads);
   if (mixed) {
     MLMC_LAUNCH("diag64_mixed", B * (double)l0.n3 * (3 * W + 8), B * (double)l0.n3 * 5.0, st,
-                (k_diag<T, double><<<g0, kThreads, 0, st>>>(l0.n, B, l0.Kx, l0.Ky, l0.Kz, H.D64, nullptr)));
+                (k_diag<T, double><<<plane_grid(l0.n * l0.n, (long long)B * l0.n), kPlaneThreads, 0, st>>>(
+                    l0.n, B, l0.Kx, l0.Ky, l0.Kz, H.D64, nullptr)));
   }
   Level<T>& lc = H.lv[H.L - 1];
   MLMC_LAUNCH("coarse_setup", B * 2 * 729.0 * 8, B * 40000.0, st,
               (k_coarse_setup<T><<<(B + 3) / 4, 128, 0, st>>>(B, lc.Kx, lc.Ky, lc.Kz, H.Lws, H.Ainv)));
   const double h = 1.0 / (double)(a.n - 1);
   MLMC_LAUNCH("prepare", B * (double)l0.n3 * (a.f ? 16.0 : 8.0), B * (double)l0.n3, st,
-              (k_prepare<<<g0, kThreads, 0, st>>>(a.n, B, h * h, a.f, H.g64, a.u)));
+              (k_prepare<<<plane_grid(a.n * a.n, (long long)B * a.n), kPlaneThreads, 0, st>>>(a.n, B, h * h, a.f,
+                                                                                             H.g64, a.u)));
   if (!mixed && !cg) {
     l0.g = (T*)H.g64;
     // iterate in the workspace copy; copied back after the last cycle
@@ -967,7 +1004,8 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
       MLMC_CUDA_TRY(cudaMemsetAsync(H.lv[0].u, 0, (size_t)B * l0.n3 * sizeof(T), st));
       MLMC_TRY(gr.run(H, nu1, nu2, st));
       MLMC_LAUNCH("update_mixed", B * (double)l0.n3 * (W + 16), B * (double)l0.n3, st,
-                  (k_update_mixed<<<g0, kThreads, 0, st>>>(a.n, B, (const float*)H.lv[0].u, a.u, H.active)));
+                  (k_update_mixed<<<plane_grid(a.n * a.n, (long long)B * a.n), kPlaneThreads, 0, st>>>(
+                      a.n, B, (const float*)H.lv[0].u, a.u, H.active)));
     } else {
       MLMC_TRY(gr.run(H, nu1, nu2, st));
     }

@@ -14,18 +14,20 @@
 // around its tile (which needs old values on a two-cell ring). The result equals the
 // sequential red-then-black sweep exactly: same operations on the same operands.
 //
-// Staging: u, Kx and Ky (read by in-plane neighbours) of the tile + 2-ring are copied
-// into shared memory two planes ahead, in a ring of five plane slots, by 16-byte
-// cp.async copies. Grid rows have odd length, so a row starts at any element offset
-// modulo 16 bytes: each staged row is copied from the 16-byte boundary at or below its
-// first element, and reads add that row's offset (computed from the element index, never
-// stored). Kz, 1/D and g are read only by a column's own updates and travel in a
-// five-plane register window. Each thread owns a column pair (x, y) and (x, y+1) of the
-// staged tile; at every (x, z) one of the two is red and the other black, so each thread
-// does one red update of plane z and one black update of plane z-1 per step. z is split
-// into independent slabs (each recomputes the red plane just outside its ends) so that a
-// launch has enough CTAs. HBM traffic per sweep is one read of each array and one write
-// of u (7 words per node), against 12+ words for two separate colour passes.
+// Staging: u, Kx and Ky of the tile + 2-ring (the arrays that in-plane neighbours read)
+// are copied into shared memory by 16-byte cp.async copies, u two planes ahead and Kx,
+// Ky one plane ahead, each in a ring of four plane slots. Grid rows have odd length, so
+// a row starts at any element offset modulo 16 bytes: each staged row is copied from the
+// 16-byte boundary at or below its first element (in the frame of the array's element
+// index), and reads add that row's offset, computed from the element index. Kz, 1/D and
+// g, which only a column's own updates read, travel in per-column register windows.
+// Each thread owns four consecutive rows of one column of the staged tile: at every
+// (x, z) two of them are red and two black, so a thread does two independent red
+// updates of plane z and two black updates of plane z-1 per step. In-sample index
+// arithmetic is 32-bit (n^3 < 2^31). z is split into independent slabs (each recomputes
+// the red plane just outside its ends) so that a launch has enough CTAs. HBM traffic
+// per sweep is one read of each array and one write of u (7 words per node), against
+// 12+ words for two separate colour passes.
 #include "common.cuh"
 #include "prof.cuh"
 #include "smooth.cuh"
@@ -40,8 +42,15 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-constexpr int kSlots = 5;    // plane ring (z-1 .. z+1 read, z+2 in flight, one slot of slack)
-constexpr int kArrays = 6;   // u, Kx, Ky, Kz, Dinv, g (bulk-copy variant)
+// Ring depth of the fused sweep. At step z the red phase reads u on planes z-1..z+1 and
+// Kx, Ky on plane z, the black phase Kx, Ky on plane z-1 and the red planes z-2..z; u of
+// plane z+2 and Kx, Ky of plane z+1 are in flight. A thread that has passed step z's
+// second barrier may start step z+1 (and overwrite the slot four planes back) while
+// others still run step z's black phase, which reads nothing that old: four slots
+// suffice for every ring.
+constexpr int kSlots = 4;
+constexpr int kBulkSlots = 5;  // plane ring of the bulk-copy variant
+constexpr int kArrays = 6;     // u, Kx, Ky, Kz, Dinv, g (bulk-copy variant)
 
 template <int K>
 struct StepK {
@@ -50,183 +59,248 @@ struct StepK {
 
 template <typename T, int BX, int BY>
 struct FusedLayout {
-  static_assert(BY % 2 == 0, "the tile height must be even (column pairs)");
+  static_assert(BY % 4 == 0, "the tile height must be a multiple of 4 (column quads)");
   static constexpr int kStaged = 3;                 // u, Kx, Ky
   static constexpr int E = 16 / (int)sizeof(T);     // elements per 16-byte copy
   static constexpr int W2 = BX + 4, H2 = BY + 4;    // tile + 2-ring
   static constexpr int W1 = BX + 2, H1 = BY + 2;    // tile + 1-ring
   static constexpr int NCH = (W2 + 2 * E - 2) / E;  // 16-byte copies per staged row, any alignment
   static constexpr int RW = NCH * E;                // staged row pitch (elements)
-  static constexpr int PLANE = H2 * RW;
-  static constexpr int RP = W1 + (W1 & 1);          // red-plane row pitch, even: conflict-free pairs
-  static constexpr int RPLANE = H1 * RP;
-  static constexpr int threads = W2 * (H2 / 2);     // one thread per column pair
-  static constexpr int items = kStaged * H2 * NCH;  // copies per staged plane
-  static constexpr int per_thread = (items + threads - 1) / threads;
-  static constexpr size_t bytes = sizeof(T) * ((size_t)kStaged * kSlots * PLANE + (size_t)kSlots * RPLANE);
+  // staged plane: rows -1 .. H2 (rows -1 and H2 are padding, never staged, read only
+  // where the value is unused), row r at (r + 1) RW
+  static constexpr int PLANE = (H2 + 2) * RW;
+  static constexpr int ASTRIDE = kSlots * PLANE;    // one staged array, all slots
+  static constexpr int RP = W1 + (W1 & 1);          // red-plane row pitch (even)
+  // red plane: the plane after its red phase on staged rows -1 .. H2 (only rows 1 ..
+  // H2-2, the 1-ring, are written; the others are padding read only where the value is
+  // unused), staged row r at (r + 1) RP
+  static constexpr int RPLANE = (H2 + 2) * RP;
+  static constexpr int threads = W2 * (H2 / 4);     // one thread per column quad
+  static constexpr int pairs = H2 * NCH;            // (row, copy) pairs of a staged plane
+  static constexpr int per_thread = (pairs + threads - 1) / threads;
+  static constexpr size_t bytes = sizeof(T) * ((size_t)kStaged * ASTRIDE + (size_t)kSlots * RPLANE);
 };
 
 template <typename T, int BX, int BY>
-__global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads, sizeof(T) == 4 ? 3 : 2)
     k_rbgs_fused(int n, int ntx, int ntiles, int zslab, const T* __restrict__ Kx, const T* __restrict__ Ky,
                  const T* __restrict__ Kz, const T* __restrict__ Dinv, const T* __restrict__ g,
                  const T* __restrict__ uin, T* __restrict__ uout, const int* __restrict__ active) {
   using Lay = FusedLayout<T, BX, BY>;
   constexpr int E = Lay::E, W2 = Lay::W2, H2 = Lay::H2, RW = Lay::RW, PLANE = Lay::PLANE, RP = Lay::RP,
-                RPLANE = Lay::RPLANE, NT = Lay::threads, NCH = Lay::NCH, PT = Lay::per_thread;
+                RPLANE = Lay::RPLANE, NT = Lay::threads, NCH = Lay::NCH, PT = Lay::per_thread,
+                AS = Lay::ASTRIDE;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  T* stage = (T*)smem_raw;                                 // [array][slot][H2][RW]
-  T* red = stage + (size_t)Lay::kStaged * kSlots * PLANE;  // [slot][H1][RP]: plane after its red phase
+  T* stage = (T*)smem_raw;                     // [array][slot][H2 + 2][RW]: u, Kx, Ky
+  T* red = stage + (size_t)Lay::kStaged * AS;  // [slot][H2 + 2][RP]: plane after its red phase
   const T* U = stage;
-  const T* SKX = stage + (size_t)kSlots * PLANE;
-  const T* SKY = stage + (size_t)2 * kSlots * PLANE;
+  const T* SKX = stage + AS;
+  const T* SKY = stage + 2 * AS;
   const int s = blockIdx.y, tid = threadIdx.x;
   const int tile = blockIdx.x % ntiles, slab = blockIdx.x / ntiles;
   const int x0 = (tile % ntx) * BX + 1, y0 = (tile / ntx) * BY + 1;  // first owned node
   const int zlo = 1 + slab * zslab, zhi = min(n - 2, zlo + zslab - 1);
-  const long long n2 = (long long)n * n, base = (long long)s * n2 * n, total = (long long)gridDim.y * n2 * n;
-  const int ci = tid % W2, r0 = 2 * (tid / W2);  // this thread's staged column and first row
+  const int n2 = n * n, n3 = n2 * n;
+  const size_t base = (size_t)s * (size_t)n3;
+  const int ci = tid % W2, r0 = 4 * (tid / W2);  // staged column, first of the four rows
   const int gx = x0 - 2 + ci, gy0 = y0 - 2 + r0;
   const bool xin = gx >= 1 && gx <= n - 2;
-  const bool yin0 = gy0 >= 1 && gy0 <= n - 2, yin1 = gy0 + 1 >= 1 && gy0 + 1 <= n - 2;
-  const bool cring = ci >= 1 && ci <= W2 - 2;
-  const bool ring0 = cring && r0 >= 1, ring1 = cring && r0 + 1 <= H2 - 2;  // rows r0, r0+1 in the 1-ring
-  const bool owned = ci >= 2 && ci <= W2 - 3 && r0 >= 2 && r0 + 1 <= H2 - 3;
-  const long long col0 = base + (long long)gy0 * n + gx;  // element of (gx, gy0, z = 0)
+  // per-row bits (row r0 + j): red updates (1-ring, interior), outputs (owned, interior)
+  int redmask = 0, outmask = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = r0 + j, gy = gy0 + j;
+    const bool yin = gy >= 1 && gy <= n - 2;
+    if (xin && yin && ci >= 1 && ci <= W2 - 2 && r >= 1 && r <= H2 - 2) redmask |= 1 << j;
+    if (xin && yin && ci >= 2 && ci <= W2 - 3 && r >= 2 && r <= H2 - 3) outmask |= 1 << j;
+  }
+  const int colrow = gy0 * n + gx;  // in-sample offset of (gx, gy0, z = 0)
   if (active && !active[s]) {
-    if (owned && xin)
-      for (int z = zlo; z <= zhi; ++z) {
-        const long long p = col0 + z * n2;
-        if (yin0) uout[p] = uin[p];
-        if (yin1) uout[p + n] = uin[p + n];
-      }
+    for (int z = zlo; z <= zhi; ++z)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (outmask >> j & 1) uout[base + (size_t)(z * n2 + colrow + j * n)] = uin[base + (size_t)(z * n2 + colrow + j * n)];
     return;
   }
-  // this thread's 16-byte staging copies: array, destination and the element index of
-  // its row's first staged column (within a plane)
-  int it_a[PT], it_dst[PT], it_row[PT];
-  bool it_on[PT];
+  // 16-byte alignment is a property of the array's element index: sample s starts sb
+  // elements past a 16-byte boundary, so in-sample offsets are aligned in the frame
+  // shifted by sb
+  const int sb = (int)(base & (size_t)(E - 1));
+  // this thread's (row, copy) pairs: shifted in-sample offset of the copy's row start
+  // (plus k E) and the destination within a staged plane; -1: nothing to copy
+  int pr_row[PT], pr_dst[PT];
 #pragma unroll
   for (int i = 0; i < PT; ++i) {
     const int q = tid + i * NT;
-    const int a = q / (H2 * NCH), rem = q % (H2 * NCH), j = rem / NCH, k = rem % NCH;
+    const int j = q / NCH, k = q - j * NCH;
     const int gy = y0 - 2 + j;
-    it_on[i] = q < Lay::items && gy >= 0 && gy < n;  // rows outside the grid are never read
-    it_a[i] = a | (k << 2);  // array, and which copy of the row (k E elements after its aligned start)
-    it_dst[i] = (a * kSlots) * PLANE + j * RW + k * E;
-    it_row[i] = gy * n + (x0 - 2);
+    const bool on = q < Lay::pairs && gy >= 0 && gy < n;  // rows outside the grid are never read
+    pr_row[i] = sb + gy * n + (x0 - 2) + k * E;
+    pr_dst[i] = on ? (j + 1) * RW + k * E : -1;
   }
-  auto issue = [&](int z, int slot) {
-    if (z < 0 || z >= n) return;
-    const long long zb = base + z * n2;
+  const T* const ub = uin + base;
+  const T* const kxb = Kx + base;
+  const T* const kyb = Ky + base;
+  // copies of plane z of u (into slot su) and, when zk >= 0, of plane zk of Kx, Ky (slot sk)
+  auto issue = [&](int z, int su, int zk, int sk) {
+    const bool zu = z >= 0 && z < n, zkk = zk >= 0 && zk < n;
 #pragma unroll
     for (int i = 0; i < PT; ++i) {
-      if (!it_on[i]) continue;
-      const int a = it_a[i] & 3, k = it_a[i] >> 2;
-      const long long cs = ((zb + it_row[i]) & ~(long long)(E - 1)) + (long long)k * E;
-      T* dst = stage + it_dst[i] + slot * PLANE;
-      const T* src = a == 0 ? uin : (a == 1 ? Kx : Ky);
-      if (cs >= 0 && cs + E <= total)
-        cp_async16(dst, src + cs);
-      else
-        *(int4*)dst = make_int4(0, 0, 0, 0);  // beyond the array: never read by an update
+      if (pr_dst[i] < 0) continue;
+      if (zu) {
+        const int c = ((z * n2 + pr_row[i]) & ~(E - 1)) - sb;  // in-sample start of the copy
+        T* dst = stage + pr_dst[i] + su * PLANE;
+        if (c >= 0 && c + E <= n3)
+          cp_async16(dst, ub + c);
+        else
+          *(int4*)dst = make_int4(0, 0, 0, 0);  // outside the sample: never read by an update
+      }
+      if (zkk) {
+        const int c = ((zk * n2 + pr_row[i]) & ~(E - 1)) - sb;
+        T* dx = stage + AS + pr_dst[i] + sk * PLANE;
+        T* dy = stage + 2 * AS + pr_dst[i] + sk * PLANE;
+        if (c >= 0 && c + E <= n3) {
+          cp_async16(dx, kxb + c);
+          cp_async16(dy, kyb + c);
+        } else {
+          *(int4*)dx = make_int4(0, 0, 0, 0);
+          *(int4*)dy = make_int4(0, 0, 0, 0);
+        }
+      }
     }
   };
-  // register window of Kz, 1/D, g for both columns of the pair: entry (p - zs + 1) mod 5
-  // holds plane p
-  const bool need0 = ring0 && xin && yin0, need1 = ring1 && xin && yin1;
-  T kz0[kSlots], kz1[kSlots], di0[kSlots], di1[kSlots], g0[kSlots], g1[kSlots];
+  // register windows of the four rows: entry (p - zs + 1) mod 4 holds plane p
+  const T* kzs = Kz + base + colrow;
+  const T* dis = Dinv + base + colrow;
+  const T* gs = g + base + colrow;
+  T kz[4][kSlots], di[4][kSlots], gg[4][kSlots];
   auto load_window = [&](int z, int w) {
     const bool zin = z >= 0 && z < n;
-    const long long p = col0 + z * n2;
-    kz0[w] = (need0 && zin) ? Kz[p] : T(0);
-    di0[w] = (need0 && zin) ? Dinv[p] : T(0);
-    g0[w] = (need0 && zin) ? g[p] : T(0);
-    kz1[w] = (need1 && zin) ? Kz[p + n] : T(0);
-    di1[w] = (need1 && zin) ? Dinv[p + n] : T(0);
-    g1[w] = (need1 && zin) ? g[p + n] : T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool on = zin && (redmask >> j & 1);
+      const int o = z * n2 + j * n;
+      kz[j][w] = on ? kzs[o] : T(0);
+      di[j][w] = on ? dis[o] : T(0);
+      gg[j][w] = on ? gs[o] : T(0);
+    }
   };
-  // staged-row offsets: row r0 - 1 + i of plane z starts (zbase + rowlo + i n) mod E
-  // elements after its 16-byte boundary
-  const int colbase = (r0 - 1) * RW + ci;
-  const unsigned rowlo = (unsigned)((long long)(gy0 - 1) * n + (x0 - 2)), un = (unsigned)n;
-  const unsigned ubase = (unsigned)base, un2 = (unsigned)n2;
-  const int rb0 = (r0 - 1) * (RP) + (ci - 1);  // row r0 in red-plane coordinates
+  // staged index of row r0 - 1 + i (i = 0..5) of a plane whose in-sample offset is zo
+  const int cbase = r0 * RW + ci;
+  const int rlo = sb + (gy0 - 1) * n + (x0 - 2);
+  auto rows_at = [&](int zo, int* I) {
+    const int t = zo + rlo;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) I[i] = cbase + i * RW + ((t + i * n) & (E - 1));
+  };
+  const int rpb = r0 * RP + (ci - 1);  // red-plane index of staged row r0 - 1 (+ i RP: row r0 - 1 + i)
+  const bool cr = ci >= 1 && ci <= W2 - 2;  // a 1-ring column: its rows r0..r0+3 go to the red plane
+  const int storemask = cr ? ((r0 >= 1 ? 1 : 0) | 6 | (r0 + 3 <= H2 - 2 ? 8 : 0)) : 0;
   const int zs = zlo - 1, ze = zhi + 1;
+  const int par0 = (gx + gy0 + zs) & 1;
+  int Ia[kSlots][6];  // staged row indices of planes z-1 .. z+1 (same slot map)
 
   auto step = [&](auto KC, int z) {
     constexpr int K = decltype(KC)::value;
-    constexpr int Im2 = (K + 4) % kSlots, Im1 = K % kSlots, I0 = (K + 1) % kSlots, Ip2 = (K + 3) % kSlots;
-    constexpr int S0 = Im1 * PLANE, S1 = I0 * PLANE, S2 = ((K + 2) % kSlots) * PLANE;
-    if (z + 2 <= ze + 1) issue(z + 2, Ip2);
+    constexpr int Im2 = (K + 3) % kSlots, Im1 = K % kSlots, I0 = (K + 1) % kSlots, Ip1 = (K + 2) % kSlots,
+                  Ip2 = (K + 3) % kSlots;
+    constexpr int S0 = Im1 * PLANE, S1 = I0 * PLANE, S2 = Ip1 * PLANE;
+    issue(z + 2 <= ze + 1 ? z + 2 : -1, Ip2, z + 1 <= ze ? z + 1 : -1, Ip1);
     cp_async_commit();
-    load_window(z + 2, Ip2);
-    cp_async_wait1();  // this thread's copies of planes <= z+1 have landed
+    load_window(z + 1, Ip1);
+    rows_at((z + 1) * n2, Ia[Ip1]);
+    cp_async_wait1();  // this thread's copies issued before this step have landed
     __syncthreads();   // ... and every thread's
-    const int par = (gx + gy0 + z) & 1;  // 0: row r0 is red at z (and black at z-1)
-    const unsigned tz = ubase + (unsigned)z * un2 + rowlo, tm = tz - un2, tp = tz + un2;
-    const int oz0 = (int)(tz & (E - 1)), oz1 = (int)((tz + un) & (E - 1)), oz2 = (int)((tz + 2 * un) & (E - 1)),
-              oz3 = (int)((tz + 3 * un) & (E - 1));
-    const int om0 = (int)(tm & (E - 1)), om1 = (int)((tm + un) & (E - 1)), om2 = (int)((tm + 2 * un) & (E - 1));
-    const int op1 = (int)((tp + un) & (E - 1)), op2 = (int)((tp + 2 * un) & (E - 1));
-    // staged indices (plane z) of the red row, its y neighbours and the other row
-    const int zr0 = colbase + RW + oz1, zr1 = colbase + 2 * RW + oz2;
-    const int rc = par ? zr1 : zr0, oth = par ? zr0 : zr1;
-    const int ym = par ? zr0 : colbase + oz0, yp = par ? colbase + 3 * RW + oz3 : zr1;
-    const int rcm = par ? colbase + 2 * RW + om2 : colbase + RW + om1;  // red row, plane z-1
-    const int ymm = par ? colbase + RW + om1 : colbase + om0;          // its y-1 row, plane z-1
-    const int rcp = par ? colbase + 2 * RW + op2 : colbase + RW + op1;  // red row, plane z+1
+    const int par = par0 ^ ((z - zs) & 1);  // rows r0 + par, r0 + par + 2 are red at z
+    const int* Iz = Ia[I0];
+    const int* Im = Ia[Im1];
+    const int* Ip = Ia[Ip1];
+    // rows a = r0 + par, b = a + 2 (staged row indices 1 + par, 3 + par) and neighbours
+    const int ia = par ? Iz[2] : Iz[1], ib = par ? Iz[4] : Iz[3];
+    const int iam = par ? Iz[1] : Iz[0], iab = par ? Iz[3] : Iz[2], ibp = par ? Iz[5] : Iz[4];
     T* rz = red + I0 * RPLANE;
+    const bool zr = z >= 1 && z <= n - 2;
     {
-      T vr = U[S1 + rc];
-      const T vo = U[S1 + oth];
-      if ((par ? need1 : need0) && z >= 1 && z <= n - 2) {
-        T acc = par ? g1[I0] : g0[I0];
-        acc = fma(SKX[S1 + rc - 1], U[S1 + rc - 1], acc);
-        acc = fma(SKX[S1 + rc], U[S1 + rc + 1], acc);
-        acc = fma(SKY[S1 + ym], U[S1 + ym], acc);
-        acc = fma(SKY[S1 + rc], U[S1 + yp], acc);
-        acc = fma(par ? kz1[Im1] : kz0[Im1], U[S0 + rcm], acc);
-        acc = fma(par ? kz1[I0] : kz0[I0], U[S2 + rcp], acc);
-        vr = acc * (par ? di1[I0] : di0[I0]);
+      const T ua_m = U[S1 + iam], u_ab = U[S1 + iab], ub_p = U[S1 + ibp];
+      T va = U[S1 + ia], vb = U[S1 + ib];
+      if (zr && (redmask >> par & 1)) {
+        T acc = par ? gg[1][I0] : gg[0][I0];
+        acc = fma(SKX[S1 + ia - 1], U[S1 + ia - 1], acc);
+        acc = fma(SKX[S1 + ia], U[S1 + ia + 1], acc);
+        acc = fma(SKY[S1 + iam], ua_m, acc);
+        acc = fma(SKY[S1 + ia], u_ab, acc);
+        acc = fma(par ? kz[1][Im1] : kz[0][Im1], U[S0 + (par ? Im[2] : Im[1])], acc);
+        acc = fma(par ? kz[1][I0] : kz[0][I0], U[S2 + (par ? Ip[2] : Ip[1])], acc);
+        va = acc * (par ? di[1][I0] : di[0][I0]);
       }
-      if (ring0) rz[rb0] = par ? vo : vr;
-      if (ring1) rz[rb0 + RP] = par ? vr : vo;
+      if (zr && (redmask >> (par + 2) & 1)) {
+        T acc = par ? gg[3][I0] : gg[2][I0];
+        acc = fma(SKX[S1 + ib - 1], U[S1 + ib - 1], acc);
+        acc = fma(SKX[S1 + ib], U[S1 + ib + 1], acc);
+        acc = fma(SKY[S1 + iab], u_ab, acc);
+        acc = fma(SKY[S1 + ib], ub_p, acc);
+        acc = fma(par ? kz[3][Im1] : kz[2][Im1], U[S0 + (par ? Im[4] : Im[3])], acc);
+        acc = fma(par ? kz[3][I0] : kz[2][I0], U[S2 + (par ? Ip[4] : Ip[3])], acc);
+        vb = acc * (par ? di[3][I0] : di[2][I0]);
+      }
+      // rows r0 .. r0+3 after the red phase: red rows take va / vb, black rows keep u
+      const T w0 = par ? ua_m : va, w1 = par ? va : u_ab, w2 = par ? u_ab : vb, w3 = par ? vb : ub_p;
+      if (storemask & 1) rz[rpb + RP] = w0;
+      if (storemask & 2) rz[rpb + 2 * RP] = w1;
+      if (storemask & 4) rz[rpb + 3 * RP] = w2;
+      if (storemask & 8) rz[rpb + 4 * RP] = w3;
     }
     __syncthreads();
     const int zb = z - 1;
-    if (owned && xin && zb >= zlo && zb <= zhi) {
+    if (outmask && zb >= zlo && zb <= zhi) {
       const T* Rb = red + Im1 * RPLANE;  // plane z-1 after red
       const T* Rm = red + Im2 * RPLANE;  // plane z-2 after red
-      const int rr = rb0 + (par ? RP : 0);  // the black row of plane z-1 (the red row of plane z)
-      const T yl = Rb[rr - RP], yh = Rb[rr + RP];
-      T vb;
-      {
-        T acc = par ? g1[Im1] : g0[Im1];
-        acc = fma(SKX[S0 + rcm - 1], Rb[rr - 1], acc);
-        acc = fma(SKX[S0 + rcm], Rb[rr + 1], acc);
-        acc = fma(SKY[S0 + ymm], yl, acc);
-        acc = fma(SKY[S0 + rcm], yh, acc);
-        acc = fma(par ? kz1[Im2] : kz0[Im2], Rm[rr], acc);
-        acc = fma(par ? kz1[Im1] : kz0[Im1], rz[rr], acc);
-        vb = acc * (par ? di1[Im1] : di0[Im1]);
+      // black rows of plane z-1 are a and b (the red rows of plane z)
+      const int ja = par ? Im[2] : Im[1], jb = par ? Im[4] : Im[3];
+      const int jam = par ? Im[1] : Im[0], jab = par ? Im[3] : Im[2];
+      const int ra = rpb + (1 + par) * RP, rbb = ra + 2 * RP;
+      const T ya = Rb[ra - RP], yab = Rb[ra + RP], yb = Rb[rbb + RP];
+      T va = T(0), vb = T(0);
+      if (outmask >> par & 1) {
+        T acc = par ? gg[1][Im1] : gg[0][Im1];
+        acc = fma(SKX[S0 + ja - 1], Rb[ra - 1], acc);
+        acc = fma(SKX[S0 + ja], Rb[ra + 1], acc);
+        acc = fma(SKY[S0 + jam], ya, acc);
+        acc = fma(SKY[S0 + ja], yab, acc);
+        acc = fma(par ? kz[1][Im2] : kz[0][Im2], Rm[ra], acc);
+        acc = fma(par ? kz[1][Im1] : kz[0][Im1], rz[ra], acc);
+        va = acc * (par ? di[1][Im1] : di[0][Im1]);
       }
-      // row r0 / r0+1 of plane z-1: the black result and the other row's red value
-      const long long p = col0 + zb * n2;
-      if (yin0) uout[p] = par ? yl : vb;
-      if (yin1) uout[p + n] = par ? vb : yh;
+      if (outmask >> (par + 2) & 1) {
+        T acc = par ? gg[3][Im1] : gg[2][Im1];
+        acc = fma(SKX[S0 + jb - 1], Rb[rbb - 1], acc);
+        acc = fma(SKX[S0 + jb], Rb[rbb + 1], acc);
+        acc = fma(SKY[S0 + jab], yab, acc);
+        acc = fma(SKY[S0 + jb], yb, acc);
+        acc = fma(par ? kz[3][Im2] : kz[2][Im2], Rm[rbb], acc);
+        acc = fma(par ? kz[3][Im1] : kz[2][Im1], rz[rbb], acc);
+        vb = acc * (par ? di[3][Im1] : di[2][Im1]);
+      }
+      // rows r0 .. r0+3 of plane z-1: black results and the red rows' values
+      const T o0 = par ? ya : va, o1 = par ? va : yab, o2 = par ? yab : vb, o3 = par ? vb : yb;
+      T* out = uout + base + (size_t)(zb * n2 + colrow);
+      if (outmask & 1) out[0] = o0;
+      if (outmask >> 1 & 1) out[n] = o1;
+      if (outmask >> 2 & 1) out[2 * n] = o2;
+      if (outmask >> 3 & 1) out[3 * n] = o3;
     }
   };
 
+  // prologue: u of planes zs-1, zs, zs+1 and Kx, Ky of plane zs; windows of zs-2 .. zs
   load_window(zs - 2, kSlots - 1);
   load_window(zs - 1, 0);
   load_window(zs, 1);
-  load_window(zs + 1, 2);
-  issue(zs - 1, 0);
+  rows_at((zs - 1) * n2, Ia[0]);
+  rows_at(zs * n2, Ia[1]);
+  issue(zs - 1, 0, -1, 0);
+  issue(zs, 1, zs, 1);
   cp_async_commit();
-  issue(zs, 1);
-  cp_async_commit();
-  issue(zs + 1, 2);
+  issue(zs + 1, 2, -1, 0);
   cp_async_commit();
   for (int z = zs; z <= ze; z += kSlots) {
     step(StepK<0>{}, z);
@@ -236,8 +310,6 @@ __global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads, sizeof(T) == 
     step(StepK<2>{}, z + 2);
     if (z + 3 > ze) break;
     step(StepK<3>{}, z + 3);
-    if (z + 4 > ze) break;
-    step(StepK<4>{}, z + 4);
   }
 }
 
@@ -293,11 +365,11 @@ struct BulkLayout {
   static constexpr int RP = ((W2 + 2 * EPV + EPV - 1) / EPV) * EPV;  // staged row pitch
   static constexpr int PLANE = H2 * RP;
   static constexpr int threads = W2 * H2;
-  static constexpr size_t stage_bytes = sizeof(T) * (size_t)kArrays * kSlots * PLANE;
+  static constexpr size_t stage_bytes = sizeof(T) * (size_t)kArrays * kBulkSlots * PLANE;
   static constexpr size_t red_off = stage_bytes;
   static constexpr size_t offs_off = red_off + sizeof(T) * 3 * (size_t)P1;
-  static constexpr size_t mbar_off = (offs_off + sizeof(int) * kSlots * H2 + 7) & ~(size_t)7;
-  static constexpr size_t flag_off = mbar_off + 8 * kSlots;
+  static constexpr size_t mbar_off = (offs_off + sizeof(int) * kBulkSlots * H2 + 7) & ~(size_t)7;
+  static constexpr size_t flag_off = mbar_off + 8 * kBulkSlots;
   static constexpr size_t bytes = flag_off + 16;
 };
 
@@ -338,15 +410,15 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
   }
   const T* src[kArrays] = {uin, Kx, Ky, Kz, Dinv, g};
   if (tid == 0) {
-    for (int k = 0; k < kSlots; ++k) mbar_init(&mbar[k], 1);
+    for (int k = 0; k < kBulkSlots; ++k) mbar_init(&mbar[k], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   // row offsets of every slot start at 0 (a slot is read before its first staging only
   // where the value is unused, but its index must stay inside the staging buffer)
-  for (int t = tid; t < kSlots * H2; t += Lay::threads) offs[t] = 0;
+  for (int t = tid; t < kBulkSlots * H2; t += Lay::threads) offs[t] = 0;
   // rows outside the grid: zeros in every slot, never copied
-  for (int t = tid; t < kArrays * kSlots * H2; t += Lay::threads) {
+  for (int t = tid; t < kArrays * kBulkSlots * H2; t += Lay::threads) {
     const int j = t % H2;
     const int yy = y0 - 2 + j;
     if (yy < 0 || yy >= n)
@@ -354,10 +426,10 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
   }
   __syncthreads();
   const int zs = zlo - 1, ze = zhi + 1;
-  // warp 0 stages plane z (rows of all six arrays) into slot z % kSlots
+  // warp 0 stages plane z (rows of all six arrays) into slot z % kBulkSlots
   auto issue = [&](int z) {
     if (warp != 0 || z < 0 || z >= n) return;
-    const int slot = z % kSlots;
+    const int slot = z % kBulkSlots;
     unsigned bytes = 0;
     for (int it = lane; it < kArrays * H2; it += 32) {
       const int a = it / H2, j = it % H2;
@@ -385,17 +457,17 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
       const size_t row = base + (size_t)z * n2 + (size_t)yy * n;
       const size_t lo = row + (size_t)max(x0 - 2, 0), hi = row + (size_t)min(x0 + BX + 2, n);
       const size_t A = lo & ~(size_t)(EPV - 1), E = (hi + EPV - 1) & ~(size_t)(EPV - 1);
-      T* dst = stage + ((size_t)(a * kSlots + slot) * H2 + j) * RP;
+      T* dst = stage + ((size_t)(a * kBulkSlots + slot) * H2 + j) * RP;
       bulk_g2s(dst, src[a] + A, (unsigned)((E - A) * sizeof(T)), &mbar[slot]);
     }
   };
   // the k-th plane staged into a slot completes that slot's barrier phase k: the
   // parity counts uses of the slot from the first staged plane of this CTA
   const int pstart = max(zs - 1, 0);
-  auto parity = [&](int z) { return (unsigned)(((z - pstart) / kSlots) & 1); };
+  auto parity = [&](int z) { return (unsigned)(((z - pstart) / kBulkSlots) & 1); };
   auto wait_plane = [&](int z) {
     if (z < 0 || z >= n) return;
-    if (!mbar_wait_bounded(&mbar[z % kSlots], parity(z))) {
+    if (!mbar_wait_bounded(&mbar[z % kBulkSlots], parity(z))) {
       *abort_flag = 1;
       atomicExch(err, 1);
     }
@@ -403,8 +475,8 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
   // element (array a, plane slot sl, staged row j, column i of the tile + 2-ring)
   // (bounds-checked: an index outside the staging buffer records error 2 and reads 0)
   auto at = [&](int a, int sl, int j, int i) -> T {
-    const long long k = ((long long)(a * kSlots + sl) * H2 + j) * RP + offs[sl * H2 + j] + i;
-    if ((unsigned long long)k >= (unsigned long long)kArrays * kSlots * PLANE) {
+    const long long k = ((long long)(a * kBulkSlots + sl) * H2 + j) * RP + offs[sl * H2 + j] + i;
+    if ((unsigned long long)k >= (unsigned long long)kArrays * kBulkSlots * PLANE) {
       atomicExch(err, 2);
       return T(0);
     }
@@ -419,7 +491,7 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
   for (int z = zs; z <= ze; ++z) {
     if (z + 2 <= ze + 1) issue(z + 2);
     wait_plane(z + 1);
-    const int sz = z % kSlots, szm = (z + kSlots - 1) % kSlots, szp = (z + 1) % kSlots;
+    const int sz = z % kBulkSlots, szm = (z + kBulkSlots - 1) % kBulkSlots, szp = (z + 1) % kBulkSlots;
     T* rz = red + (size_t)(z % 3) * P1;
     if (ring1) {
       T v = at(0, sz, cj, ci);
@@ -438,7 +510,7 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
     __syncthreads();
     if (*abort_flag) {
       // a wait ran out: drain the copies still in flight (bounded), then every thread leaves
-      for (int p = z + 1; p <= min(z + 2, min(ze + 1, n - 1)); ++p) mbar_wait_bounded(&mbar[p % kSlots], parity(p));
+      for (int p = z + 1; p <= min(z + 2, min(ze + 1, n - 1)); ++p) mbar_wait_bounded(&mbar[p % kBulkSlots], parity(p));
       return;
     }
     if (z > zs) {
@@ -464,7 +536,7 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
     } else if (owned && zs >= 1) {
       kz_m2 = at(3, szm, cj, ci);  // Kz(zs-1): plane zs-1 was staged
     }
-    __syncthreads();  // slot (z+3) % kSlots = plane z-2 is reused by the next issue
+    __syncthreads();  // slot (z+3) % kBulkSlots = plane z-2 is reused by the next issue
   }
 }
 
