@@ -24,6 +24,7 @@ per step) and reported as the reference arm.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -45,23 +46,29 @@ L2_BYTES = 129 * 1024 * 1024
 # a kernel, valid only while that kernel's source text hashes to `kernel_sha` (else null).
 # unit_bytes: the algorithmic bytes the library accounts per unit, to count units per launch.
 NCU_TRAFFIC = {
-    "rbgs_f64": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs", "kernel_sha": "754697c08e18bb8e",
-                 "dram_bytes_per_unit": 927.0e6 / (8 * 127 ** 3), "unit_bytes": 3.5 * 8,
+    "rbgs_f64": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs", "kernel_sha": "e8e43de9d3e4896e",
+                 "dram_bytes_per_unit": (805.797e6 + 119.737e6) / (8 * 127 ** 3), "unit_bytes": 3.5 * 8,
                  "source": "profiles/rbgs_f64_twopass_n129_b8.md (129^3 x 8, one colour pass)"},
-    "rbgs_f32": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs", "kernel_sha": "754697c08e18bb8e",
-                 "dram_bytes_per_unit": 933.8e6 / (2 * 255 ** 3), "unit_bytes": 3.5 * 4,
-                 "source": "profiles/rbgs_f32_twopass_n257_b2.md (257^3 x 2, one colour pass)"},
+    "rbgs_f32": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs", "kernel_sha": "e8e43de9d3e4896e",
+                 "dram_bytes_per_unit": (805.619e6 + 121.530e6) / (2 * 255 ** 3), "unit_bytes": 3.5 * 4,
+                 "source": "profiles/rbgs_f32_n257_b2.md (257^3 x 2, one colour pass)"},
 }
 
 
 def kernel_sha(path, name):
+    """Hash of one kernel's source: its signature and brace-balanced body."""
     import hashlib
 
     try:
         src = open(os.path.join(ROOT, path)).read()
         i = src.index("__global__ void " + name + "(")
-        j = src.index("\ntemplate", i)
-        return hashlib.sha256(src[i:j].encode()).hexdigest()[:16]
+        j = src.index("{", i)
+        depth = 0
+        for k in range(j, len(src)):
+            depth += {"{": 1, "}": -1}.get(src[k], 0)
+            if depth == 0:
+                return hashlib.sha256(src[i:k + 1].encode()).hexdigest()[:16]
+        return None
     except Exception:
         return None
 
@@ -87,6 +94,10 @@ def parse():
     p.add_argument("--c5-eps", type=float, default=None, help="c5: override the RMS tolerance")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--lanes", type=int, default=2, help="concurrent level streams (1: levels in sequence)")
+    p.add_argument("--plan-from", default=None,
+                   help="reuse the autotuned choices (and pilot-sized N_l) of an earlier JSON line of the same "
+                        "config instead of measuring them again (for runs under a profiler)")
     return p.parse_args()
 
 
@@ -128,6 +139,26 @@ def plan_levels(mg, cfg, levels, stream, rank):
     N = [max(2, int(math.ceil(total * math.sqrt(v / c) / eps_s ** 2))) for v, c in zip(V, C)]
     return N, {"pilot_N": cfg["N_init"], "pilot_var": V, "pilot_cost_s": C, "eps": cfg["eps"],
                "theta": cfg["theta"], "N_from_eq11": N, "autotune": tune}
+
+
+def restore_plan(mg, cfg, levels, N, path):
+    """The plan of an earlier run of the same config (its JSON line): each level's tuned
+    smoother and nu go back into the library's tuning table (mlmc_tune_set, for the
+    level's fine grid and precision), and pilot-sized workloads take its N_l."""
+    with open(path) as fh:
+        line = json.loads([ln for ln in fh.read().splitlines() if ln.strip().startswith("{")][-1])
+    if line.get("config", {}).get("workload") != cfg["name"]:
+        raise SystemExit("--plan-from: %s holds workload %r, not %r" % (path, line.get("config", {}).get("workload"),
+                                                                       cfg["name"]))
+    plan = line["plan"]
+    prec = mg.MLMC_PREC_F64 if cfg["precision"] == "f64" else mg.MLMC_PREC_MIXED
+    for l in levels:
+        best = plan["autotune"][str(l)]["best"]
+        mg.mlmc_tune_set(level_n(l), prec, best["smoother"], best["nu"])
+    if "N_from_eq11" in plan:
+        N = list(plan["N_from_eq11"])
+    plan = dict(plan, restored_from=os.path.basename(path))
+    return N, plan
 
 
 class ClockSampler:
@@ -286,7 +317,11 @@ def own_arm(args):
     dev = torch.device("cuda", local)
     plan = None
     nu_cfg = (cfg["nu1"], cfg["nu2"])
-    if "N_init" in cfg:
+    if args.plan_from:
+        N, plan = restore_plan(mg, cfg, levels, N, args.plan_from)
+        if "N_init" in cfg:
+            nu_cfg = (0, 0)
+    elif "N_init" in cfg:
         N, plan = plan_levels(mg, cfg, levels, stream, rank)
         nu_cfg = (0, 0)  # the autotuned sweep count per level
     else:
@@ -310,19 +345,36 @@ def own_arm(args):
         mcfg[l] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=nu_cfg[0],
                                     nu2=nu_cfg[1], rtol=cfg["rtol"], precision=prec, max_batch=n, stream=stream,
                                     accel=accel, max_cycles=300), lvl)
+    # levels run concurrently on `lanes` streams (the one-GPU form of scheduling the
+    # levels on separate processor groups): the FP64/HBM-bound solves of one level
+    # overlap the FP32-bound field evaluation and solves of others
+    lanes = level_lanes(levels, N, single, args.lanes)
+    lane_streams = [stream] + [torch.cuda.Stream() for _ in lanes[1:]]
+    lane_of = {l: i for i, ls in enumerate(lanes) for l in ls}
+    for l in levels:
+        c, lvl = mcfg[l]
+        c.stream = lane_streams[lane_of[l]].cuda_stream
     lev_ev = {l: [] for l in levels}
     stats = {}
 
-    def step(record):
-        for l in levels:
-            c, lvl = mcfg[l]
-            if record:
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-            stats[l] = mg.mlmc_level_run(c, lvl, ids[l], Y_dev=Y[l])
-            if record:
-                b.record(stream)
-                lev_ev[l].append((a, b))
+    def step(record, sequential=False):
+        def lane(i):
+            st = lane_streams[i]
+            for l in lanes[i]:
+                c, lvl = mcfg[l]
+                if record:
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(st)
+                stats[l] = mg.mlmc_level_run(c, lvl, ids[l], Y_dev=Y[l])
+                if record:
+                    b.record(st)
+                    lev_ev[l].append((a, b))
+
+        if sequential:  # one lane after the other: no kernel overlaps another
+            for i in range(len(lanes)):
+                lane(i)
+        else:
+            run_lanes(torch, lanes, lane_streams, stream, lane)
         if world > 1:
             import torch.distributed as dist
 
@@ -346,26 +398,29 @@ def own_arm(args):
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_host0 = time.perf_counter()
+    # NVTX range "timed_step" marks the timed launches (ncu --nvtx --nvtx-include timed_step/)
+    torch.cuda.nvtx.range_push("timed_step")
     ev0.record(stream)
     for _ in range(args.steps):
         step(True)
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if world > 1:
         torch.distributed.barrier()
     t_host = time.perf_counter() - t_host0
     clk = clocks.stop()
     elapsed_ms = ev0.elapsed_time(ev1)
     launches = mg.profile_total_launches()
-    # timed region 2: the same steps with a CUDA event pair around every launch, for the
-    # per-kernel device times of the roofline
+    # timed region 2: the same steps, levels in sequence, with a CUDA event pair around
+    # every launch, for the per-kernel device times of the roofline (each kernel alone)
     mg.profile_reset()
     mg.profile_enable(True)
     torch.cuda.synchronize()
     evp0, evp1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     evp0.record(stream)
     for _ in range(args.steps):
-        step(False)
+        step(False, sequential=True)
     evp1.record(stream)
     torch.cuda.synchronize()
     mg.profile_enable(False)
@@ -389,7 +444,7 @@ def own_arm(args):
     # end to end through the host-buffer C-ABI call
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, accel)
+        e2e = e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, accel, lanes)
 
     line = None
     if rank == 0:
@@ -408,6 +463,7 @@ def own_arm(args):
                        "fine_n": [level_n(l) for l in levels], "sigma2": cfg["sigma2"], "ell": cfg["ell"],
                        "M": cfg["M"], "cycle": "V(%d,%d)" % (cfg["nu1"], cfg["nu2"]), "rtol": cfg["rtol"],
                        "parallelism": "replicas x%d (samples sharded by rank, no data-path collective)" % world,
+                       "level_streams": [[int(l) for l in ls] for ls in lanes],
                        "l2": "every level's batch working set exceeds the 129 MB L2 (no flush needed)"},
             "per_level": per_level,
             "time_per_estimate_s": elapsed_ms / 1e3 / args.steps,
@@ -416,9 +472,9 @@ def own_arm(args):
                                      "cycles_coarse": stats[l].mean_cycles_coarse} for l in levels},
             "roofline": roof, "gpu_launches": launches, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu,
             "host_wall_s": t_host,
-            "timing_note": "value, per_level, clocks and gpu_launches: timed region 1 (no per-launch events); "
-                           "roofline and kernel_classes: timed region 2 (same steps, CUDA events around "
-                           "every launch on the launching stream)",
+            "timing_note": "value, per_level, clocks and gpu_launches: timed region 1 (levels on concurrent "
+                           "streams, no per-launch events); roofline and kernel_classes: timed region 2 (same "
+                           "steps, levels in sequence, CUDA events around every launch on the launching stream)",
             "profiled_region_ms_per_step": profiled_ms / args.steps,
             "kernel_ms_per_step": sum(v["ms"] for v in prof.values()) / args.steps,
             "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
@@ -466,7 +522,59 @@ def roofline(prof, peaks):
             "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"]}
 
 
-def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, accel):
+def level_lanes(levels, N, single, lanes):
+    """Levels of one step assigned to `lanes` concurrent streams, longest first onto the
+    least-loaded lane, by the nodes a level solves, N_l (n_l^3 + n_{l-1}^3)."""
+    def cost(l, n):
+        nf = level_n(l)
+        nc = level_n(l - 1) if (l > 0 and not single) else 0
+        return float(n) * (nf ** 3 + nc ** 3)
+
+    loads, out = [0.0] * max(1, lanes), [[] for _ in range(max(1, lanes))]
+    for l, n in sorted(zip(levels, N), key=lambda t: -cost(*t)):
+        i = min(range(len(out)), key=lambda k: loads[k])
+        out[i].append(l)
+        loads[i] += cost(l, n)
+    return [o for o in out if o]
+
+
+def run_lanes(torch, lanes, lane_streams, main_stream, body):
+    """Runs body(i) for every lane i, lane 0 on this thread and the others on their own
+    host threads (the library calls release the GIL), each lane's work on its own
+    stream, ordered after the work already on `main_stream`; `main_stream` then waits
+    for every lane."""
+    import threading
+
+    if len(lanes) == 1:
+        body(0)
+        return
+    start = torch.cuda.Event()
+    start.record(main_stream)
+    for st in lane_streams[1:]:
+        st.wait_event(start)
+    errors = []
+
+    def wrap(i):
+        try:
+            body(i)
+        except BaseException as e:  # re-raised on the calling thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=wrap, args=(i,)) for i in range(1, len(lanes))]
+    for t in threads:
+        t.start()
+    wrap(0)
+    for t in threads:
+        t.join()
+    for st in lane_streams[1:]:
+        done = torch.cuda.Event()
+        done.record(st)
+        main_stream.wait_event(done)
+    if errors:
+        raise errors[0]
+
+
+def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, accel, lanes):
     """Same workload through mlmc_level_estimate: ids built on the host and copied in,
     Y/Qf/Qc copied back into pinned host buffers, every step."""
     import ctypes
@@ -474,17 +582,22 @@ def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stre
     import numpy as np
 
     bufs = {l: [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(3)] for l, n in zip(levels, N)}
+    lane_streams = [stream] + [torch.cuda.Stream() for _ in lanes[1:]]
+    lane_of = {l: i for i, ls in enumerate(lanes) for l in ls}
     cfgs = {}
     for l, n in zip(levels, N):
         n0 = level_n(l) if single else 17
         cfgs[l] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=nu_cfg[0],
-                                    nu2=nu_cfg[1], rtol=cfg["rtol"], precision=prec, max_batch=n, stream=stream,
-                                    accel=accel, max_cycles=300), 0 if single else l)
+                                    nu2=nu_cfg[1], rtol=cfg["rtol"], precision=prec, max_batch=n,
+                                    stream=lane_streams[lane_of[l]], accel=accel, max_cycles=300),
+                   0 if single else l)
+    Nof = dict(zip(levels, N))
     L = mg.lib()
     dp = ctypes.POINTER(ctypes.c_double)
 
-    def step():
-        for l, n in zip(levels, N):
+    def lane(i):
+        for l in lanes[i]:
+            n = Nof[l]
             c, lvl = cfgs[l]
             first = int(sample_ids(l, rank * n, 1)[0])
             out = mg.LevelStats()
@@ -492,6 +605,9 @@ def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stre
             st = L.mlmc_level_estimate(ctypes.byref(c), lvl, first, n, y, qf, qc, ctypes.byref(out))
             if st < 0:
                 raise mg.MlmcError(st, "mlmc_level_estimate", L.mlmc_last_error_string().decode())
+
+    def step():
+        run_lanes(torch, lanes, lane_streams, stream, lane)
 
     for _ in range(max(1, min(args.warmup, 2))):
         step()
@@ -595,12 +711,13 @@ def serving_arm(args):
     return 0
 
 
-def adaptive_mlmc(mg, torch, cfg, eps, mode, stream, log):
+def adaptive_mlmc(mg, torch, cfg, eps, mode, stream, log, lanes=1):
     """Algorithm 2 with L fixed (paper_1607_03252_gb300.estimator): pilot N_init, then N_l
     from Eq. 15 with the running s_l^2 and measured cost per sample, until no level needs
     more samples. mode 'fast': batched, FP32 V-cycle preconditioner (autotuned smoother and
     nu); 'plain': one sample per launch, FP64 throughout. Both use flexible CG around the
-    V-cycle and the same realisation ids."""
+    V-cycle and the same realisation ids; the fast arm runs the levels of a round on `lanes`
+    concurrent streams."""
     from paper_1607_03252_gb300.estimator import MLMCEstimator
 
     fast = mode == "fast"
@@ -608,7 +725,8 @@ def adaptive_mlmc(mg, torch, cfg, eps, mode, stream, log):
                         cfg["theta"], n0=17, nu=((0, 0) if fast else (cfg["nu1"], cfg["nu2"])), rtol=cfg["rtol"],
                         precision=(mg.MLMC_PREC_MIXED if fast else mg.MLMC_PREC_F64), accel=mg.MLMC_ACCEL_CG,
                         smoother=(mg.MLMC_SMOOTH_AUTO if fast else mg.MLMC_SMOOTH_TWO_PASS),
-                        max_batch=(0 if fast else 1), max_cycles=300, stream=stream)
+                        max_batch=(0 if fast else 1), max_cycles=300, stream=stream,
+                        streams=([stream] + [torch.cuda.Stream() for _ in range(max(0, lanes - 1))]) if fast else None)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = est.run()
@@ -640,7 +758,7 @@ def c5_arm(args):
     out = {}
     for mode in args.c5_arms.split(","):
         log = []
-        out[mode] = adaptive_mlmc(mg, torch, cfg, eps, mode, stream, log)
+        out[mode] = adaptive_mlmc(mg, torch, cfg, eps, mode, stream, log, lanes=args.lanes)
         out[mode]["rounds_log"] = log
     fast = out.get("fast")
     plain = out.get("plain")

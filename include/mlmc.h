@@ -91,6 +91,10 @@ typedef struct {
 #define MLMC_SMOOTH_BULK_32x8 5   /* fused, plane rows staged by TMA bulk copies on mbarriers */
 #define MLMC_SMOOTH_BULK_32x16 6
 #define MLMC_SMOOTH_BULK_64x8 7
+#define MLMC_SMOOTH_NODAL 8      /* two colour passes that read the nodal coefficient instead of the
+                                    stored faces, recomputing the six harmonic faces, D and 1/D of
+                                    each updated node (same values, fewer bytes); FP32 grids only,
+                                    an FP64 solve uses MLMC_SMOOTH_TWO_PASS */
 
 /* Outer iteration around the V-cycle. */
 #define MLMC_ACCEL_NONE 0 /* stationary: repeat V-cycles (FP64), or FP32 V-cycles as corrections of
@@ -137,6 +141,10 @@ int mlmc_field_eval(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, 
  *   stats_host  host array of `batch` entries, or NULL.
  * Each sample stops independently when its relative residual reaches cfg->rtol, so a
  * sample's result does not depend on the other samples of the batch.
+ * On a created stream (not the legacy default stream) with nu1 + nu2 even, the first
+ * V-cycle of the call is captured as a CUDA graph and the others replay it (same
+ * kernels, same results); per-launch event timing (mlmc_profile_enable) or the
+ * environment variable MLMC_NO_GRAPHS=1 keeps every launch direct.
  * Blocking: synchronises `stream`. Returns MLMC_ERR_NOT_CONVERGED if any sample
  * reached max_cycles without meeting rtol (u is still written); MLMC_ERR_INVALID for
  * bad sizes / parameters / NULL k or u; MLMC_ERR_OOM; MLMC_ERR_CUDA.
@@ -302,8 +310,9 @@ typedef struct {
 } mlmc_tune_entry;
 
 /*
- * mlmc_autotune -- picks the smoother implementation (two-pass, or fused with 32x8,
- * 32x16 or 64x8 tiles staged by cp.async or by TMA bulk copies) and the sweep count
+ * mlmc_autotune -- picks the smoother implementation (two-pass on stored faces, two-pass
+ * on the nodal coefficient, or fused with 32x8, 32x16 or 64x8 tiles staged by cp.async
+ * or by TMA bulk copies: 8 candidates) and the sweep count
  * nu in {1,2,3} of V(nu, nu) for MLMC level
  * `level` under cfg (no counterpart in the paper; the paper fixes its cycle, Sec. 7.1).
  * Each candidate runs the whole level pipeline once untimed and once timed on
@@ -318,6 +327,17 @@ typedef struct {
  */
 int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples, mlmc_tune_entry* table,
                   int table_len, int* n_entries, int* best_smoother, int* best_nu);
+
+/*
+ * mlmc_tune_set -- stores a tuning choice in the process-wide table that mlmc_autotune
+ * fills: grids of n^3 nodes solved at `precision` with MLMC_SMOOTH_AUTO use `smoother`,
+ * and with nu1 = nu2 = 0 the cycle V(nu, nu). For restoring a table measured earlier
+ * (for example in a run without a profiler attached) without measuring again. No
+ * counterpart in the paper. Host-only, thread-safe, no device work. Errors:
+ * MLMC_ERR_INVALID for n not 2^p+1 (5 <= n <= 4097), an unknown precision, smoother
+ * outside MLMC_SMOOTH_TWO_PASS .. MLMC_SMOOTH_NODAL, or nu outside 1..8.
+ */
+int mlmc_tune_set(int n, int precision, int smoother, int nu);
 
 /* Text of the last error on the calling thread ("" if none). Never NULL. */
 const char* mlmc_last_error_string(void);

@@ -60,6 +60,7 @@ MLMC_SMOOTH_FUSED_64x8 = 4
 MLMC_SMOOTH_BULK_32x8 = 5
 MLMC_SMOOTH_BULK_32x16 = 6
 MLMC_SMOOTH_BULK_64x8 = 7
+MLMC_SMOOTH_NODAL = 8
 
 
 MLMC_ACCEL_NONE = 0
@@ -143,6 +144,7 @@ SIGNATURES = {
     "mlmc_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]),
     "mlmc_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(Result)]),
     "mlmc_service_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServiceReport)]),
+    "mlmc_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mlmc_autotune": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                      ctypes.POINTER(TuneEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -293,7 +295,7 @@ def mlmc_level_run(cfg: MlmcCfg, level: int, ids_dev, Y_dev=None, Qf_dev=None, Q
 SMOOTHER_NAMES = {MLMC_SMOOTH_TWO_PASS: "two-pass", MLMC_SMOOTH_FUSED_32x8: "fused 32x8",
                   MLMC_SMOOTH_FUSED_32x16: "fused 32x16", MLMC_SMOOTH_FUSED_64x8: "fused 64x8",
                   MLMC_SMOOTH_BULK_32x8: "bulk 32x8", MLMC_SMOOTH_BULK_32x16: "bulk 32x16",
-                  MLMC_SMOOTH_BULK_64x8: "bulk 64x8"}
+                  MLMC_SMOOTH_BULK_64x8: "bulk 64x8", MLMC_SMOOTH_NODAL: "nodal"}
 
 
 def mlmc_autotune(cfg: MlmcCfg, level: int, first_id: int, samples: int):
@@ -306,6 +308,18 @@ def mlmc_autotune(cfg: MlmcCfg, level: int, first_id: int, samples: int):
     rows = [dict(smoother=SMOOTHER_NAMES.get(t.smoother, t.smoother), nu=t.nu,
                  ms_per_sample=1e3 * t.seconds_per_sample, cycles=t.mean_cycles) for t in tab[:cnt.value]]
     return rows, bs.value, bnu.value
+
+
+SMOOTHER_IDS = {v: k for k, v in {MLMC_SMOOTH_TWO_PASS: "two-pass", MLMC_SMOOTH_FUSED_32x8: "fused 32x8",
+                                   MLMC_SMOOTH_FUSED_32x16: "fused 32x16", MLMC_SMOOTH_FUSED_64x8: "fused 64x8",
+                                   MLMC_SMOOTH_BULK_32x8: "bulk 32x8", MLMC_SMOOTH_BULK_32x16: "bulk 32x16",
+                                   MLMC_SMOOTH_BULK_64x8: "bulk 64x8", MLMC_SMOOTH_NODAL: "nodal"}.items()}
+
+
+def mlmc_tune_set(n: int, precision: int, smoother, nu: int):
+    """Stores a tuning choice (smoother id or name, V(nu, nu)) for n^3 grids at `precision`."""
+    sm = SMOOTHER_IDS[smoother] if isinstance(smoother, str) else int(smoother)
+    _check(lib().mlmc_tune_set(int(n), int(precision), sm, int(nu)), "mlmc_tune_set")
 
 
 def profile_enable(on=True):

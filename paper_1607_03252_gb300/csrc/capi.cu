@@ -55,7 +55,7 @@ static int check_mg(const mg_cfg* c) {
     set_error("nu1=%d nu2=%d out of range 0..8 (both 0: tuned count)", c->nu1, c->nu2);
     return MLMC_ERR_INVALID;
   }
-  if (c->smoother < MLMC_SMOOTH_AUTO || c->smoother > MLMC_SMOOTH_BULK_64x8) {
+  if (c->smoother < MLMC_SMOOTH_AUTO || c->smoother > MLMC_SMOOTH_NODAL) {
     set_error("unknown smoother %d", c->smoother);
     return MLMC_ERR_INVALID;
   }
@@ -481,9 +481,9 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   cudaStream_t st = (cudaStream_t)cfg->stream;
   int B = 0;
   MLMC_TRY(choose_batch(cfg, samples, nf, nc, &B));
-  const int smoothers[7] = {MLMC_SMOOTH_TWO_PASS,   MLMC_SMOOTH_FUSED_32x8, MLMC_SMOOTH_FUSED_32x16,
-                            MLMC_SMOOTH_FUSED_64x8, MLMC_SMOOTH_BULK_32x8,  MLMC_SMOOTH_BULK_32x16,
-                            MLMC_SMOOTH_BULK_64x8};
+  const int smoothers[8] = {MLMC_SMOOTH_TWO_PASS,  MLMC_SMOOTH_FUSED_32x8, MLMC_SMOOTH_FUSED_32x16,
+                            MLMC_SMOOTH_FUSED_64x8, MLMC_SMOOTH_BULK_32x8, MLMC_SMOOTH_BULK_32x16,
+                            MLMC_SMOOTH_BULK_64x8,  MLMC_SMOOTH_NODAL};
   std::vector<uint64_t> ids(samples);
   for (int i = 0; i < samples; ++i) ids[i] = first_id + (uint64_t)i;
   int count = 0, bs = MLMC_SMOOTH_TWO_PASS, bnu = 2;
@@ -492,7 +492,7 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   const bool fixed_nu = cfg->mg.nu1 > 0 && cfg->mg.nu1 == cfg->mg.nu2;
   const int nu_lo = fixed_nu ? cfg->mg.nu1 : 1, nu_hi = fixed_nu ? cfg->mg.nu1 : 3;
   for (int nu = nu_lo; nu <= nu_hi; ++nu)
-    for (int si = 0; si < 7; ++si) {
+    for (int si = 0; si < 8; ++si) {
       mg_cfg mc = cfg->mg;
       mc.smoother = smoothers[si];
       mc.nu1 = nu;
@@ -534,6 +534,16 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   if (n_entries) *n_entries = count;
   if (best_smoother) *best_smoother = bs;
   if (best_nu) *best_nu = bnu;
+  return MLMC_OK;
+}
+
+int mlmc_tune_set(int n, int precision, int smoother, int nu) {
+  if (!valid_grid(n) || (precision != MLMC_PREC_F64 && precision != MLMC_PREC_MIXED) ||
+      smoother < MLMC_SMOOTH_TWO_PASS || smoother > MLMC_SMOOTH_NODAL || nu < 1 || nu > 8) {
+    set_error("mlmc_tune_set: invalid arguments (n=%d precision=%d smoother=%d nu=%d)", n, precision, smoother, nu);
+    return MLMC_ERR_INVALID;
+  }
+  tune_store(n, precision, smoother, nu);
   return MLMC_OK;
 }
 

@@ -235,6 +235,100 @@ __global__ void k_rbgs(int colour, int n, int B, const T* __restrict__ Kx, const
   }
 }
 
+// Nodal coefficient of an MG grid in the grid's precision (injection from the finest k):
+// the input of the nodal-coefficient sweep.
+template <typename T>
+__global__ void k_nodal_k(const double* __restrict__ k0, int n0, int st0, int n, int B, T* __restrict__ kn) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
+  const size_t n3 = (size_t)n * n * n, n03 = (size_t)n0 * n0 * n0;
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    const size_t p0 = ((size_t)(st0 * z) * n0 + (size_t)(st0 * y)) * n0 + (size_t)(st0 * x);
+    kn[(size_t)s * n3 + (size_t)(z * n * n + q)] = (T)k0[(size_t)s * n03 + p0];
+  }
+}
+
+// One colour of a red-black sweep that reads the nodal coefficient (FP32) instead of
+// stored faces: the six harmonic faces, their sum D and 1/D of the updated node are
+// recomputed with the operations and order of k_faces / k_diag (IEEE single precision),
+// so the update equals k_rbgs's bit for bit, while a sweep reads 4 words per node
+// (u read and written, g, k) instead of 7.
+__global__ void k_rbgs_nodal(int colour, int n, int B, const float* __restrict__ kn, const float* __restrict__ g,
+                             float* __restrict__ u, const int* __restrict__ active) {
+  const int m = n - 2, half = (n - 1) / 2, lh = 31 - __clz(half);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // colour node of an interior plane
+  if (q >= m * half) return;
+  const int xi = q & (half - 1), y = 1 + (q >> lh);
+  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
+  auto face = [](float a, float b) { return __fdiv_rn(__fmul_rn(2.0f * a, b), __fadd_rn(a, b)); };
+  for (int zz = blockIdx.y; zz < B * m; zz += gridDim.y) {
+    const int s = zz / m, z = 1 + (zz - s * m);
+    if (active && !active[s]) continue;
+    const int x = (((1 + y + z) & 1) == colour ? 1 : 2) + 2 * xi;
+    if (x > n - 2) continue;
+    const size_t p = (size_t)s * n3 + (size_t)(z * n * n + y * n + x);
+    const float kc = kn[p];
+    const float kxm = face(kn[p - 1], kc), kxp = face(kc, kn[p + 1]);
+    const float kym = face(kn[p - n], kc), kyp = face(kc, kn[p + n]);
+    const float kzm = face(kn[p - n2], kc), kzp = face(kc, kn[p + n2]);
+    float d = kxm;
+    d += kxp;
+    d += kym;
+    d += kyp;
+    d += kzm;
+    d += kzp;
+    const float dinv = 1.0f / d;
+    float acc = g[p];
+    acc = fmaf(kxm, u[p - 1], acc);
+    acc = fmaf(kxp, u[p + 1], acc);
+    acc = fmaf(kym, u[p - n], acc);
+    acc = fmaf(kyp, u[p + n], acc);
+    acc = fmaf(kzm, u[p - n2], acc);
+    acc = fmaf(kzp, u[p + n2], acc);
+    u[p] = acc * dinv;
+  }
+}
+
+// r~ = g - D u + sum K u_q of an FP32 grid from the nodal coefficient (faces and D
+// recomputed as in k_rbgs_nodal, then k_residual's operation order): r~ on interior
+// nodes, 0 on the boundary; 4 words per node instead of 7.
+__global__ void k_residual_nodal(int n, int B, const float* __restrict__ kn, const float* __restrict__ g,
+                                 const float* __restrict__ u, float* __restrict__ r, const int* __restrict__ active) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
+  const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
+  auto face = [](float a, float b) { return __fdiv_rn(__fmul_rn(2.0f * a, b), __fadd_rn(a, b)); };
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    if (active && !active[s]) continue;
+    const size_t p = (size_t)s * n3 + (size_t)(z * n * n + q);
+    float rr = 0.0f;
+    if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
+      const float kc = kn[p];
+      const float kxm = face(kn[p - 1], kc), kxp = face(kc, kn[p + 1]);
+      const float kym = face(kn[p - n], kc), kyp = face(kc, kn[p + n]);
+      const float kzm = face(kn[p - n2], kc), kzp = face(kc, kn[p + n2]);
+      float d = kxm;
+      d += kxp;
+      d += kym;
+      d += kyp;
+      d += kzm;
+      d += kzp;
+      rr = fmaf(-d, u[p], g[p]);
+      rr = fmaf(kxm, u[p - 1], rr);
+      rr = fmaf(kxp, u[p + 1], rr);
+      rr = fmaf(kym, u[p - n], rr);
+      rr = fmaf(kyp, u[p + n], rr);
+      rr = fmaf(kzm, u[p - n2], rr);
+      rr = fmaf(kzp, u[p + n2], rr);
+    }
+    r[p] = rr;
+  }
+}
+
 template <int THREADS>
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double warp_part[THREADS / 32];
@@ -620,6 +714,7 @@ struct Level {
   T *Kx = nullptr, *Ky = nullptr, *Kz = nullptr, *D = nullptr, *Dinv = nullptr;
   T *u = nullptr, *g = nullptr, *r = nullptr;
   T* u2 = nullptr;  // spare iterate for the fused (double-buffered) sweep
+  T* kn = nullptr;  // nodal coefficient (FP32 grids: input of the nodal-coefficient sweep)
 };
 
 template <typename T>
@@ -644,6 +739,7 @@ struct Hier {
   double *part2 = nullptr, *rz = nullptr, *rzo = nullptr, *alpha = nullptr, *beta = nullptr;
   int tile[kMaxLevels] = {};      // fused-sweep tile shape per level
   bool fused[kMaxLevels] = {};    // fused (one pass) or two-pass smoother per level
+  bool nodal[kMaxLevels] = {};    // two-pass sweep on the nodal coefficient (FP32)
 };
 
 // Lays out the workspace. Level-0 u of FP64 solves is the caller's array (not carved).
@@ -668,6 +764,7 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed, bool cg) {
     if (j > 0 || mixed) v.g = c.template take<T>(e);  // FP64: the level-0 rhs is g64 (or R for CG)
     if (j < H.L - 1) v.u2 = c.template take<T>(e);
     if (j < H.L - 1) v.r = c.template take<T>(e);
+    if (mixed && j < H.L - 1) v.kn = c.template take<T>(e);
     nl = (nl + 1) / 2;
   }
   const size_t e0 = (size_t)B * cube(n);
@@ -738,6 +835,15 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   const double sweep_bytes = B * interior(v.n) * 3.5 * W, sweep_flops = B * interior(v.n) * 0.5 * 13.0;
   auto smooth = [&](int sweeps) {
     for (int s = 0; s < sweeps; ++s) {
+      if constexpr (sizeof(T) == 4) {
+        if (H.nodal[j]) {
+          for (int c = 0; c < 2; ++c)
+            MLMC_LAUNCH("rbgs_nodal_f32", B * interior(v.n) * 2.0 * W, B * interior(v.n) * 0.5 * 37.0, st,
+                        (k_rbgs_nodal<<<gs, kPlaneThreads, 0, st>>>(c, v.n, B, (const float*)v.kn,
+                                                                   (const float*)v.g, (float*)v.u, act)));
+          continue;
+        }
+      }
       if (H.fused[j]) {
         rbgs_fused_sweep<T>(H.tile[j], v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, v.u2, act, H.err, st);
         T* t = v.u;
@@ -751,10 +857,21 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
     }
   };
   smooth(nu1);
-  dim3 rg(reduce_blocks(v.n3), B);
-  MLMC_LAUNCH(Names<T>::residual, B * interior(v.n) * 7.0 * W, B * interior(v.n) * 14.0, st,
-              (k_residual<T, T, T, T><<<rg, kThreads, 0, st>>>(v.n, v.Kx, v.Ky, v.Kz, v.D, v.g, v.u, v.r, nullptr,
-                                                              act)));
+  bool nodal_res = false;
+  if constexpr (sizeof(T) == 4) {
+    if (H.nodal[j]) {
+      MLMC_LAUNCH("residual_nodal_f32", B * interior(v.n) * 4.0 * W, B * interior(v.n) * 37.0, st,
+                  (k_residual_nodal<<<plane_grid(v.n * v.n, (long long)B * v.n), kPlaneThreads, 0, st>>>(
+                      v.n, B, (const float*)v.kn, (const float*)v.g, (const float*)v.u, (float*)v.r, act)));
+      nodal_res = true;
+    }
+  }
+  if (!nodal_res) {
+    dim3 rg(reduce_blocks(v.n3), B);
+    MLMC_LAUNCH(Names<T>::residual, B * interior(v.n) * 7.0 * W, B * interior(v.n) * 14.0, st,
+                (k_residual<T, T, T, T><<<rg, kThreads, 0, st>>>(v.n, v.Kx, v.Ky, v.Kz, v.D, v.g, v.u, v.r, nullptr,
+                                                                act)));
+  }
   Level<T>& w = H.lv[j + 1];
   MLMC_LAUNCH(Names<T>::restrict_, B * ((double)v.n3 + (double)w.n3) * W, B * interior(w.n) * 54.0, st,
               (k_restrict<T><<<plane_grid((w.n - 2) * (w.n - 1), (long long)B * (w.n - 2)), kPlaneThreads, 0, st>>>(
@@ -919,7 +1036,14 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     Level<T>& v = H.lv[j];
     int sm = a.cfg.smoother, d1 = 1, d2 = 1;
     resolve_tuning(v.n, a.cfg.precision, &sm, &d1, &d2);
-    H.fused[j] = v.u2 != nullptr && sm != MLMC_SMOOTH_TWO_PASS;
+    // the nodal-coefficient sweep exists for FP32 grids (an FP64 solve takes the two-pass)
+    H.nodal[j] = v.kn != nullptr && sm == MLMC_SMOOTH_NODAL;
+    H.fused[j] = v.u2 != nullptr && sm != MLMC_SMOOTH_TWO_PASS && sm != MLMC_SMOOTH_NODAL;
+    if (H.nodal[j]) {
+      MLMC_LAUNCH("nodal_k", B * (double)v.n3 * (8.0 + W), 0.0, st,
+                  (k_nodal_k<T><<<plane_grid(v.n * v.n, (long long)B * v.n), kPlaneThreads, 0, st>>>(
+                      a.k0, a.n_k0, a.st0 << j, v.n, B, v.kn)));
+    }
     switch (sm) {
       case MLMC_SMOOTH_FUSED_32x16: H.tile[j] = kTile32x16; break;
       case MLMC_SMOOTH_FUSED_64x8: H.tile[j] = kTile64x8; break;

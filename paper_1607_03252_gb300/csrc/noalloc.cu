@@ -61,7 +61,7 @@ extern "C" int mg_solve_batch_noalloc(const mg_cfg* cfg, int batch, int n, const
   if (cfg->nu1 < 0 || cfg->nu1 > 8 || cfg->nu2 < 0 || cfg->nu2 > 8 || cfg->max_cycles < 1 ||
       cfg->max_cycles > 1000 || !(cfg->rtol < 1.0) ||
       (cfg->precision != MLMC_PREC_F64 && cfg->precision != MLMC_PREC_MIXED) ||
-      cfg->smoother < MLMC_SMOOTH_AUTO || cfg->smoother > MLMC_SMOOTH_BULK_64x8 ||
+      cfg->smoother < MLMC_SMOOTH_AUTO || cfg->smoother > MLMC_SMOOTH_NODAL ||
       (cfg->accel != MLMC_ACCEL_NONE && cfg->accel != MLMC_ACCEL_CG)) {
     set_error("mg_solve_batch_noalloc: invalid mg_cfg");
     return MLMC_ERR_INVALID;

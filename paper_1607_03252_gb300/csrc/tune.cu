@@ -35,12 +35,9 @@ void resolve_tuning(int n, int precision, int* smoother, int* nu1, int* nu2) {
   int ts = 0, tnu = 0;
   const bool tuned = tune_lookup(n, precision, &ts, &tnu);
   if (*smoother == MLMC_SMOOTH_AUTO) {
-    if (tuned)
-      *smoother = ts;
-    else if (precision == MLMC_PREC_MIXED)
-      *smoother = n <= 33 ? MLMC_SMOOTH_FUSED_32x8 : MLMC_SMOOTH_FUSED_32x16;
-    else
-      *smoother = MLMC_SMOOTH_TWO_PASS;
+    // untuned grids: the two-pass colour sweep, measured fastest on GB300 at every grid
+    // size in both precisions (the fused sweeps stay available to the autotuner)
+    *smoother = tuned ? ts : MLMC_SMOOTH_TWO_PASS;
   }
   if (*nu1 == 0 && *nu2 == 0) {
     const int nu = tuned ? tnu : 2;

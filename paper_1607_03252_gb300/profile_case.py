@@ -1,7 +1,7 @@
 """One small batched field evaluation + multigrid solve, for kernel profiling.
 
   python -m paper_1607_03252_gb300.profile_case --n 129 --batch 8 --prec f64 --cycles 2 \
-      [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8] [--accel cg] [--timing]
+      [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8|nodal] [--accel cg] [--timing]
 
 Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256) for `batch` realisations
 on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0) through the C ABI, so
@@ -28,7 +28,7 @@ def main(argv=None):
     p.add_argument("--cycles", type=int, default=2)
     p.add_argument("--M", type=int, default=256)
     p.add_argument("--smoother", choices=["auto", "two-pass", "32x8", "32x16", "64x8", "bulk32x8", "bulk32x16",
-                                          "bulk64x8"], default="auto")
+                                          "bulk64x8", "nodal"], default="auto")
     p.add_argument("--accel", choices=["none", "cg"], default="none")
     p.add_argument("--timing", action="store_true")
     a = p.parse_args(argv)
@@ -36,7 +36,7 @@ def main(argv=None):
     sm = {"auto": mg.MLMC_SMOOTH_AUTO, "two-pass": mg.MLMC_SMOOTH_TWO_PASS, "32x8": mg.MLMC_SMOOTH_FUSED_32x8,
           "32x16": mg.MLMC_SMOOTH_FUSED_32x16, "64x8": mg.MLMC_SMOOTH_FUSED_64x8,
           "bulk32x8": mg.MLMC_SMOOTH_BULK_32x8, "bulk32x16": mg.MLMC_SMOOTH_BULK_32x16,
-          "bulk64x8": mg.MLMC_SMOOTH_BULK_64x8}[a.smoother]
+          "bulk64x8": mg.MLMC_SMOOTH_BULK_64x8, "nodal": mg.MLMC_SMOOTH_NODAL}[a.smoother]
     accel = mg.MLMC_ACCEL_CG if a.accel == "cg" else mg.MLMC_ACCEL_NONE
     k = torch.empty((a.batch, a.n, a.n, a.n), dtype=torch.float64, device="cuda")
     mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, 1.0, 0.3, a.M), sample_ids(3, 0, a.batch), k)

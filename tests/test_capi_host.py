@@ -80,3 +80,17 @@ def test_no_cpu_fallback_without_device():
     out = mg.LevelStats()
     st = L.mlmc_level_estimate(ctypes.byref(cfg), 0, 0, 1, None, None, None, ctypes.byref(out))
     assert st == mg.MLMC_ERR_CUDA
+
+
+def test_tune_set_validates_on_host():
+    """mlmc_tune_set is host-only: valid entries are stored, invalid ones rejected, no GPU.
+    (The stored entries equal the untuned defaults, so later solves in this process are
+    unaffected.)"""
+    L = mg.lib()
+    assert L.mlmc_tune_set(33, mg.MLMC_PREC_MIXED, mg.MLMC_SMOOTH_TWO_PASS, 2) == mg.MLMC_OK
+    assert L.mlmc_tune_set(34, mg.MLMC_PREC_MIXED, mg.MLMC_SMOOTH_TWO_PASS, 3) == mg.MLMC_ERR_INVALID
+    assert L.mlmc_tune_set(33, 7, mg.MLMC_SMOOTH_TWO_PASS, 3) == mg.MLMC_ERR_INVALID
+    assert L.mlmc_tune_set(33, mg.MLMC_PREC_F64, mg.MLMC_SMOOTH_AUTO, 3) == mg.MLMC_ERR_INVALID
+    assert L.mlmc_tune_set(33, mg.MLMC_PREC_F64, mg.MLMC_SMOOTH_NODAL + 1, 3) == mg.MLMC_ERR_INVALID
+    assert L.mlmc_tune_set(33, mg.MLMC_PREC_F64, mg.MLMC_SMOOTH_TWO_PASS, 0) == mg.MLMC_ERR_INVALID
+    mg.mlmc_tune_set(65, mg.MLMC_PREC_F64, "two-pass", 2)

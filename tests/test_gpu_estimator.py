@@ -42,3 +42,18 @@ def test_estimator_level_records_match_batch_call():
     st, Y, _, _ = mg.mlmc_level_estimate(cfg, 1, (1 << 48), 8)
     n, mean, m2 = est.records[1]
     assert n == 8 and mean == st.mean and m2 == st.M2
+
+
+def test_concurrent_level_lanes_give_the_same_records():
+    """Levels of a round on two streams from two host threads: the same ids, records and
+    sample counts as the levels in sequence."""
+    import torch
+
+    seq = _est()
+    seq.run()
+    s0, s1 = torch.cuda.Stream(), torch.cuda.Stream()
+    par = MLMCEstimator(RUN_SEED, 1.0, 0.3, 32, levels=[0, 1, 2], N_init=[32, 8, 4], eps=2e-3, n0=9, rtol=1e-10,
+                        cost_model="nodes", stream=s0, streams=[s0, s1])
+    par.run()
+    assert par.have == seq.have
+    assert par.records == seq.records
