@@ -93,8 +93,12 @@ typedef struct {
 #define MLMC_SMOOTH_BULK_64x8 7
 #define MLMC_SMOOTH_NODAL 8      /* two colour passes that read the nodal coefficient instead of the
                                     stored faces, recomputing the six harmonic faces, D and 1/D of
-                                    each updated node (same values, fewer bytes); FP32 grids only,
-                                    an FP64 solve uses MLMC_SMOOTH_TWO_PASS */
+                                    each updated node with fast reciprocals (faces within a few ulps
+                                    of the stored ones, 4 instead of 7 words per node and sweep).
+                                    FP32 correction cycles only (MLMC_PREC_MIXED), where the FP64
+                                    outer residual on the stored faces fixes the solution: results
+                                    agree with the other smoothers to the solve tolerance, not bit
+                                    for bit. An FP64 solve uses MLMC_SMOOTH_TWO_PASS. */
 
 /* Outer iteration around the V-cycle. */
 #define MLMC_ACCEL_NONE 0 /* stationary: repeat V-cycles (FP64), or FP32 V-cycles as corrections of
@@ -203,7 +207,10 @@ typedef struct {
  * first_id + N - 1 (Algorithm 1, step 1.a for one level; step 1.b for `out`).
  * For level 0, Y = Q_0 on grid n0; for level l >= 1 the fine grid has
  * n_l = (n0 - 1) 2^l + 1 nodes and the coarse grid n_{l-1}, both solved on the field
- * of the same id. Y_host, Qf_host, Qc_host: host arrays of N doubles or NULL
+ * of the same id; the coarse solve runs first and the trilinear interpolation of its
+ * solution is the initial guess of the fine solve (nested iteration, the first step of
+ * the full multigrid of Sec. 7.1), which saves about two fine cycles and changes Q_l only
+ * within the solve tolerance. Y_host, Qf_host, Qc_host: host arrays of N doubles or NULL
  * (Qc = 0 for level 0). Blocking. Errors as mg_solve_batch; MLMC_ERR_NOT_CONVERGED
  * if any solve missed rtol (the outputs are still written).
  */

@@ -194,32 +194,38 @@ struct LevelBatch {
   int run(const mlmc_field_cfg& fc, const mg_cfg& mc, const uint64_t* ids_dev, int b, double* Qf, double* Qc,
           double* Y, int* n_unconv, cudaStream_t st) {
     MLMC_TRY(field_eval_dev(fc, ids_dev, b, nf, MLMC_F64, k0.get(), scratch.get(), st));
-    MLMC_CUDA_TRY(cudaMemsetAsync(uf.get(), 0, (size_t)b * cube(nf) * sizeof(double), st));
     MGSolveArgs a;
     a.k0 = k0.as<double>();
     a.n_k0 = nf;
-    a.st0 = 1;
     a.f = nullptr;
-    a.u = uf.as<double>();
-    a.n = nf;
     a.B = b;
     a.cfg = mc;
     int bad = 0;
     int* cf = cyc.as<int>();
     int* cc = cyc.as<int>() + B;
-    MLMC_TRY(mg_solve_dev(a, scratch.get(), st, nullptr, nullptr, &bad, cf, nullptr));
-    *n_unconv += bad;
-    MLMC_TRY(qoi_dev(uf.as<double>(), nf, b, Qf, scratch.get(), st));
+    double* qc = Qc ? Qc : Q.as<double>() + B;
     if (nc) {
-      double* qc = Qc ? Qc : Q.as<double>() + B;
+      // coarse solve first (its coefficient is the fine one injected); its solution,
+      // interpolated, starts the fine solve (nested iteration, the first step of FMG)
       MLMC_CUDA_TRY(cudaMemsetAsync(uc.get(), 0, (size_t)b * cube(nc) * sizeof(double), st));
       a.st0 = 2;
       a.u = uc.as<double>();
       a.n = nc;
-      bad = 0;
       MLMC_TRY(mg_solve_dev(a, scratch.get(), st, nullptr, nullptr, &bad, cc, nullptr));
       *n_unconv += bad;
       MLMC_TRY(qoi_dev(uc.as<double>(), nc, b, qc, scratch.get(), st));
+      MLMC_TRY(interpolate_dev(uc.as<double>(), nf, b, uf.as<double>(), st));
+    } else {
+      MLMC_CUDA_TRY(cudaMemsetAsync(uf.get(), 0, (size_t)b * cube(nf) * sizeof(double), st));
+    }
+    a.st0 = 1;
+    a.u = uf.as<double>();
+    a.n = nf;
+    bad = 0;
+    MLMC_TRY(mg_solve_dev(a, scratch.get(), st, nullptr, nullptr, &bad, cf, nullptr));
+    *n_unconv += bad;
+    MLMC_TRY(qoi_dev(uf.as<double>(), nf, b, Qf, scratch.get(), st));
+    if (nc) {
       MLMC_LAUNCH("level_stats", b * 24.0, b * 10.0, st,
                   (k_level_stats<<<1, 32, 0, st>>>(Qf, qc, cf, cc, b, Y, rec.as<LevelRecord>())));
     } else {

@@ -250,11 +250,21 @@ __global__ void k_nodal_k(const double* __restrict__ k0, int n0, int st0, int n,
   }
 }
 
+// Harmonic face of the nodal-coefficient kernels: 2ab / (a + b) with the fast reciprocal
+// (__fdividef, within 2 ulp). Symmetric in (a, b) (2a*b is 2*(a*b) exactly), so both
+// nodes of a face see the same value; the faces differ from the stored IEEE ones by a
+// few ulps.
+__device__ __forceinline__ float nodal_face(float a, float b) {
+  return __fdividef(__fmul_rn(2.0f * a, b), __fadd_rn(a, b));
+}
+
 // One colour of a red-black sweep that reads the nodal coefficient (FP32) instead of
 // stored faces: the six harmonic faces, their sum D and 1/D of the updated node are
-// recomputed with the operations and order of k_faces / k_diag (IEEE single precision),
-// so the update equals k_rbgs's bit for bit, while a sweep reads 4 words per node
-// (u read and written, g, k) instead of 7.
+// recomputed per update with fast reciprocals, so a sweep reads 4 words per node (u read
+// and written, g, k) instead of 7. It is the Gauss-Seidel sweep of an operator within a
+// few ulps of the stored FP32 one: used only inside the FP32 correction cycle, whose
+// result the FP64 outer residual (stored faces) corrects, so the converged solution is
+// that of the stored operator.
 __global__ void k_rbgs_nodal(int colour, int n, int B, const float* __restrict__ kn, const float* __restrict__ g,
                              float* __restrict__ u, const int* __restrict__ active) {
   const int m = n - 2, half = (n - 1) / 2, lh = 31 - __clz(half);
@@ -262,7 +272,6 @@ __global__ void k_rbgs_nodal(int colour, int n, int B, const float* __restrict__
   if (q >= m * half) return;
   const int xi = q & (half - 1), y = 1 + (q >> lh);
   const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
-  auto face = [](float a, float b) { return __fdiv_rn(__fmul_rn(2.0f * a, b), __fadd_rn(a, b)); };
   for (int zz = blockIdx.y; zz < B * m; zz += gridDim.y) {
     const int s = zz / m, z = 1 + (zz - s * m);
     if (active && !active[s]) continue;
@@ -270,16 +279,16 @@ __global__ void k_rbgs_nodal(int colour, int n, int B, const float* __restrict__
     if (x > n - 2) continue;
     const size_t p = (size_t)s * n3 + (size_t)(z * n * n + y * n + x);
     const float kc = kn[p];
-    const float kxm = face(kn[p - 1], kc), kxp = face(kc, kn[p + 1]);
-    const float kym = face(kn[p - n], kc), kyp = face(kc, kn[p + n]);
-    const float kzm = face(kn[p - n2], kc), kzp = face(kc, kn[p + n2]);
+    const float kxm = nodal_face(kn[p - 1], kc), kxp = nodal_face(kc, kn[p + 1]);
+    const float kym = nodal_face(kn[p - n], kc), kyp = nodal_face(kc, kn[p + n]);
+    const float kzm = nodal_face(kn[p - n2], kc), kzp = nodal_face(kc, kn[p + n2]);
     float d = kxm;
     d += kxp;
     d += kym;
     d += kyp;
     d += kzm;
     d += kzp;
-    const float dinv = 1.0f / d;
+    const float dinv = __fdividef(1.0f, d);
     float acc = g[p];
     acc = fmaf(kxm, u[p - 1], acc);
     acc = fmaf(kxp, u[p + 1], acc);
@@ -292,15 +301,15 @@ __global__ void k_rbgs_nodal(int colour, int n, int B, const float* __restrict__
 }
 
 // r~ = g - D u + sum K u_q of an FP32 grid from the nodal coefficient (faces and D
-// recomputed as in k_rbgs_nodal, then k_residual's operation order): r~ on interior
-// nodes, 0 on the boundary; 4 words per node instead of 7.
+// recomputed as in k_rbgs_nodal, then k_residual's operation order): the residual of the
+// operator the nodal sweep smooths; r~ on interior nodes, 0 on the boundary; 4 words per
+// node instead of 7.
 __global__ void k_residual_nodal(int n, int B, const float* __restrict__ kn, const float* __restrict__ g,
                                  const float* __restrict__ u, float* __restrict__ r, const int* __restrict__ active) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
   if (q >= n * n) return;
   const int y = q / n, x = q - y * n;
   const size_t n3 = (size_t)n * n * n, n2 = (size_t)n * n;
-  auto face = [](float a, float b) { return __fdiv_rn(__fmul_rn(2.0f * a, b), __fadd_rn(a, b)); };
   for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
     const int s = zz / n, z = zz - s * n;
     if (active && !active[s]) continue;
@@ -308,9 +317,9 @@ __global__ void k_residual_nodal(int n, int B, const float* __restrict__ kn, con
     float rr = 0.0f;
     if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
       const float kc = kn[p];
-      const float kxm = face(kn[p - 1], kc), kxp = face(kc, kn[p + 1]);
-      const float kym = face(kn[p - n], kc), kyp = face(kc, kn[p + n]);
-      const float kzm = face(kn[p - n2], kc), kzp = face(kc, kn[p + n2]);
+      const float kxm = nodal_face(kn[p - 1], kc), kxp = nodal_face(kc, kn[p + 1]);
+      const float kym = nodal_face(kn[p - n], kc), kyp = nodal_face(kc, kn[p + n]);
+      const float kzm = nodal_face(kn[p - n2], kc), kzp = nodal_face(kc, kn[p + n2]);
       float d = kxm;
       d += kxp;
       d += kym;
@@ -1189,6 +1198,16 @@ int mg_solve_dev(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_ho
   if (a.cfg.precision == MLMC_PREC_MIXED)
     return solve_impl<float>(a, ws, st, cycles_host, relres_host, n_unconv, cycles_dev, relres_dev);
   return solve_impl<double>(a, ws, st, cycles_host, relres_host, n_unconv, cycles_dev, relres_dev);
+}
+
+int interpolate_dev(const double* uc, int nf, int B, double* uf, cudaStream_t st) {
+  MLMC_CUDA_TRY(cudaMemsetAsync(uf, 0, (size_t)B * cube(nf) * sizeof(double), st));
+  const int m = nf - 2;
+  MLMC_LAUNCH("interpolate_f64", B * (2.0 * (double)cube(nf) + (double)cube((nf + 1) / 2)) * 8.0,
+              B * interior(nf) * 4.375, st,
+              (k_prolong<double><<<plane_grid(m * (nf - 1), (long long)B * m), kPlaneThreads, 0, st>>>(nf, B, uc, uf,
+                                                                                                     nullptr)));
+  return MLMC_OK;
 }
 
 size_t qoi_scratch_bytes(int B, int n) {

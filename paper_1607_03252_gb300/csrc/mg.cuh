@@ -35,4 +35,8 @@ int mg_solve_dev(const MGSolveArgs& a, void* workspace, cudaStream_t st, int* cy
 size_t qoi_scratch_bytes(int B, int n);
 int qoi_dev(const double* u, int n, int B, double* Q_dev, void* scratch, cudaStream_t st);
 
+// uf = trilinear interpolation of uc ((nf+1)/2)^3 onto the nf^3 grid (0 on the boundary):
+// the initial guess of a fine solve from the coarse solution of the same realisation.
+int interpolate_dev(const double* uc, int nf, int B, double* uf, cudaStream_t st);
+
 }  // namespace mlmc

@@ -216,7 +216,7 @@ def test_c2_level3_full_size_sampled(orc):
 
 
 SMOOTHERS = [mg.MLMC_SMOOTH_TWO_PASS, mg.MLMC_SMOOTH_FUSED_32x8, mg.MLMC_SMOOTH_FUSED_32x16, mg.MLMC_SMOOTH_FUSED_64x8,
-             mg.MLMC_SMOOTH_BULK_32x8, mg.MLMC_SMOOTH_BULK_32x16, mg.MLMC_SMOOTH_BULK_64x8, mg.MLMC_SMOOTH_NODAL]
+             mg.MLMC_SMOOTH_BULK_32x8, mg.MLMC_SMOOTH_BULK_32x16, mg.MLMC_SMOOTH_BULK_64x8]
 
 
 @pytest.mark.parametrize("prec", [mg.MLMC_PREC_F64, mg.MLMC_PREC_MIXED])
@@ -284,6 +284,37 @@ def test_graph_replay_matches_direct_launches(orc, prec, accel, sm):
     assert np.array_equal(u0.cpu().numpy(), u1.cpu().numpy())
     if accel == mg.MLMC_ACCEL_NONE:
         assert len(set(cyc0.tolist())) > 1  # masking was exercised
+
+
+@pytest.mark.parametrize("accel", [mg.MLMC_ACCEL_NONE, mg.MLMC_ACCEL_CG])
+def test_nodal_smoother_reaches_the_same_solution(orc, accel):
+    """The nodal-coefficient sweep smooths an operator within a few ulps of the stored
+    FP32 one; the FP64 outer residual (stored faces) fixes the solution, so it converges
+    to the oracle-mixed solution like the stored-face smoothers (not bit for bit)."""
+    n, B = 33, 3
+    ks = [orc.field(RUN_SEED, int(i), 256, 1.0, 0.2, n) for i in sample_ids(2, 60, B)]
+    k = to_dev(np.stack(ks))
+    out = {}
+    for sm in (mg.MLMC_SMOOTH_TWO_PASS, mg.MLMC_SMOOTH_NODAL):
+        u = torch.zeros_like(k)
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-12, 200, mg.MLMC_PREC_MIXED, sm, accel), k, u)
+        assert st == 0 and np.all(rel <= 1e-12)
+        out[sm] = (u.cpu().numpy(), cyc)
+    for s in range(B):
+        um, *_ = orc.mg_solve(ks[s], None, rtol=1e-12, mixed=True)
+        assert relmax(out[mg.MLMC_SMOOTH_NODAL][0][s], um) < 1e-9
+        assert relmax(out[mg.MLMC_SMOOTH_NODAL][0][s], out[mg.MLMC_SMOOTH_TWO_PASS][0][s]) < 1e-9
+    # the smoother's operator differs by ulps: the cycle counts stay within one of each other
+    assert np.all(np.abs(out[mg.MLMC_SMOOTH_NODAL][1] - out[mg.MLMC_SMOOTH_TWO_PASS][1]) <= 1)
+
+
+def test_nodal_smoother_level_estimate_matches_oracle_mixed(orc):
+    level, ids = 1, sample_ids(1, 30, 4)
+    cfg = mg.make_mlmc_cfg(RUN_SEED, 2.0, 0.2, 256, n0=17, rtol=1e-11, precision=mg.MLMC_PREC_MIXED,
+                           smoother=mg.MLMC_SMOOTH_NODAL, accel=mg.MLMC_ACCEL_CG)
+    _, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
+    Ym, Qfm, Qcm, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 2.0, 0.2, 256, rtol=1e-11, mixed=True), 33, 17, ids)
+    assert np.all(np.abs(Y - Ym) <= _y_tol(Qfm, Qcm, 1e-9))
 
 
 def _direct(orc, k, mixed=False, f=None):
