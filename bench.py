@@ -97,7 +97,7 @@ def parse():
     p.add_argument("--c5-eps", type=float, default=None, help="c5: override the RMS tolerance")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--lanes", type=int, default=2, help="concurrent level streams (1: levels in sequence)")
+    p.add_argument("--lanes", type=int, default=4, help="concurrent level streams (1: levels in sequence)")
     p.add_argument("--plan-from", default=None,
                    help="reuse the autotuned choices (and pilot-sized N_l) of an earlier JSON line of the same "
                         "config instead of measuring them again (for runs under a profiler)")
@@ -351,7 +351,19 @@ def own_arm(args):
     # levels run concurrently on `lanes` streams (the one-GPU form of scheduling the
     # levels on separate processor groups): the FP64/HBM-bound solves of one level
     # overlap the FP32-bound field evaluation and solves of others
-    lanes = level_lanes(levels, N, single, args.lanes)
+    # one untimed pass with the levels in sequence measures each level's time (the
+    # lane assignment's costs)
+    seq_ms = {}
+    for _ in range(2):  # the second pass, after first-call set-up
+        for l in levels:
+            c, lvl = mcfg[l]
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mg.mlmc_level_run(c, lvl, ids[l], Y_dev=Y[l])
+            b.record(stream)
+            b.synchronize()
+            seq_ms[l] = a.elapsed_time(b)
+    lanes = level_lanes(levels, N, single, args.lanes, seq_ms)
     lane_streams = [stream] + [torch.cuda.Stream() for _ in lanes[1:]]
     lane_of = {l: i for i, ls in enumerate(lanes) for l in ls}
     for l in levels:
@@ -467,6 +479,7 @@ def own_arm(args):
                        "M": cfg["M"], "cycle": "V(%d,%d)" % (cfg["nu1"], cfg["nu2"]), "rtol": cfg["rtol"],
                        "parallelism": "replicas x%d (samples sharded by rank, no data-path collective)" % world,
                        "level_streams": [[int(l) for l in ls] for ls in lanes],
+                       "level_ms_alone": {str(l): round(v, 3) for l, v in seq_ms.items()},
                        "l2": "every level's batch working set exceeds the 129 MB L2 (no flush needed)"},
             "per_level": per_level,
             "time_per_estimate_s": elapsed_ms / 1e3 / args.steps,
@@ -525,10 +538,14 @@ def roofline(prof, peaks):
             "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"]}
 
 
-def level_lanes(levels, N, single, lanes):
+def level_lanes(levels, N, single, lanes, times=None):
     """Levels of one step assigned to `lanes` concurrent streams, longest first onto the
-    least-loaded lane, by the nodes a level solves, N_l (n_l^3 + n_{l-1}^3)."""
+    least-loaded lane, by measured per-level times when given (small batches are
+    latency-bound, so node counts misjudge them), else by the nodes a level solves,
+    N_l (n_l^3 + n_{l-1}^3)."""
     def cost(l, n):
+        if times:
+            return float(times[l])
         nf = level_n(l)
         nc = level_n(l - 1) if (l > 0 and not single) else 0
         return float(n) * (nf ** 3 + nc ** 3)
