@@ -363,33 +363,46 @@ def own_arm(args):
             b.record(stream)
             b.synchronize()
             seq_ms[l] = a.elapsed_time(b)
-    lanes = level_lanes(levels, N, single, args.lanes, seq_ms)
+    lanes = lane_items(levels, N, seq_ms, args.lanes)
     lane_streams = [stream] + [torch.cuda.Stream() for _ in lanes[1:]]
-    lane_of = {l: i for i, ls in enumerate(lanes) for l in ls}
-    for l in levels:
-        c, lvl = mcfg[l]
-        c.stream = lane_streams[lane_of[l]].cuda_stream
-    lev_ev = {l: [] for l in levels}
+    # one configuration per work item, bound to its lane's stream
+    icfg = {}
+    for i, its in enumerate(lanes):
+        for (l, a, b) in its:
+            c, lvl = mcfg[l]
+            ci = type(c).from_buffer_copy(c)
+            ci.stream = lane_streams[i].cuda_stream
+            icfg[(l, a)] = (ci, lvl)
+    chunks = {l: sorted(a for its in lanes for (ll, a, _) in its if ll == l) for l in levels}
+    lev_ev = {l: [] for l in levels}  # per step: [(start, end) per chunk]
     stats = {}
 
     def step(record, sequential=False):
+        parts = {}
+        evs = {l: [] for l in levels}
+
         def lane(i):
             st = lane_streams[i]
-            for l in lanes[i]:
-                c, lvl = mcfg[l]
+            for (l, a, b) in lanes[i]:
+                c, lvl = icfg[(l, a)]
                 if record:
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record(st)
-                stats[l] = mg.mlmc_level_run(c, lvl, ids[l], Y_dev=Y[l])
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                parts[(l, a)] = mg.mlmc_level_run(c, lvl, ids[l][a:b], Y_dev=Y[l][a:b])
                 if record:
-                    b.record(st)
-                    lev_ev[l].append((a, b))
+                    e1.record(st)
+                    evs[l].append((e0, e1))
 
         if sequential:  # one lane after the other: no kernel overlaps another
             for i in range(len(lanes)):
                 lane(i)
         else:
             run_lanes(torch, lanes, lane_streams, stream, lane)
+        for l in levels:
+            ps = [parts[(l, a)] for a in chunks[l]]
+            stats[l] = ps[0] if len(ps) == 1 else MergedLevel(ps)
+            if record:
+                lev_ev[l].append(evs[l])
         if world > 1:
             import torch.distributed as dist
 
@@ -449,7 +462,9 @@ def own_arm(args):
     value = total_samples / (elapsed_ms / 1e3)
     per_level = {}
     for l, n in zip(levels, N):
-        ms = sum(a.elapsed_time(b) for a, b in lev_ev[l])
+        # a level's time per step: from its first chunk's start to its last chunk's end
+        ms = sum(max(ev0.elapsed_time(e1) for _, e1 in evs) - min(ev0.elapsed_time(e0) for e0, _ in evs)
+                 for evs in lev_ev[l])
         per_level[str(l)] = n * world * args.steps / (ms / 1e3)
 
     # roofline of the dominant kernel class
@@ -478,7 +493,7 @@ def own_arm(args):
                        "fine_n": [level_n(l) for l in levels], "sigma2": cfg["sigma2"], "ell": cfg["ell"],
                        "M": cfg["M"], "cycle": "V(%d,%d)" % (cfg["nu1"], cfg["nu2"]), "rtol": cfg["rtol"],
                        "parallelism": "replicas x%d (samples sharded by rank, no data-path collective)" % world,
-                       "level_streams": [[int(l) for l in ls] for ls in lanes],
+                       "level_streams": [["%d[%d:%d]" % (l, a, b) for (l, a, b) in its] for its in lanes],
                        "level_ms_alone": {str(l): round(v, 3) for l, v in seq_ms.items()},
                        "l2": "every level's batch working set exceeds the 129 MB L2 (no flush needed)"},
             "per_level": per_level,
@@ -538,24 +553,42 @@ def roofline(prof, peaks):
             "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"]}
 
 
-def level_lanes(levels, N, single, lanes, times=None):
-    """Levels of one step assigned to `lanes` concurrent streams, longest first onto the
-    least-loaded lane, by measured per-level times when given (small batches are
-    latency-bound, so node counts misjudge them), else by the nodes a level solves,
-    N_l (n_l^3 + n_{l-1}^3)."""
-    def cost(l, n):
-        if times:
-            return float(times[l])
-        nf = level_n(l)
-        nc = level_n(l - 1) if (l > 0 and not single) else 0
-        return float(n) * (nf ** 3 + nc ** 3)
-
-    loads, out = [0.0] * max(1, lanes), [[] for _ in range(max(1, lanes))]
-    for l, n in sorted(zip(levels, N), key=lambda t: -cost(*t)):
-        i = min(range(len(out)), key=lambda k: loads[k])
-        out[i].append(l)
-        loads[i] += cost(l, n)
+def lane_items(levels, N, times, lanes):
+    """Work items (level, first, last) of one step on `lanes` concurrent streams: a level
+    whose measured time exceeds the per-lane share is split into sample chunks (the
+    one-GPU form of spreading a level's samples over processor groups, Sec. 5; a sample's
+    result does not depend on its batch); items go longest first onto the least-loaded
+    lane. Returns a list of lanes, each a list of (level, first, last)."""
+    lanes = max(1, lanes)
+    total = sum(times[l] for l in levels)
+    share = total / lanes
+    items = []
+    for l, n in zip(levels, N):
+        k = 1
+        if lanes > 1 and times[l] > share and n > 1:
+            k = min(n, lanes, int(math.ceil(times[l] / share)))
+        for c in range(k):
+            a, b = n * c // k, n * (c + 1) // k
+            items.append((l, a, b, times[l] * (b - a) / n))
+    loads, out = [0.0] * lanes, [[] for _ in range(lanes)]
+    for l, a, b, cost in sorted(items, key=lambda t: -t[3]):
+        i = min(range(lanes), key=lambda k: loads[k])
+        out[i].append((l, a, b))
+        loads[i] += cost
     return [o for o in out if o]
+
+
+class MergedLevel:
+    """Level record merged from chunk records (Chan's formula, chunks in id order)."""
+
+    def __init__(self, parts):
+        from paper_1607_03252_gb300.stats import chan_merge
+
+        n, mean, m2 = chan_merge([(float(p.N), p.mean, p.M2) for p in parts])
+        self.N, self.mean, self.M2 = int(n), mean, m2
+        self.var_unbiased = m2 / (n - 1) if n > 1 else 0.0
+        self.mean_cycles_fine = sum(p.N * p.mean_cycles_fine for p in parts) / max(n, 1)
+        self.mean_cycles_coarse = sum(p.N * p.mean_cycles_coarse for p in parts) / max(n, 1)
 
 
 def run_lanes(torch, lanes, lane_streams, main_stream, body):
@@ -603,26 +636,26 @@ def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stre
 
     bufs = {l: [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(3)] for l, n in zip(levels, N)}
     lane_streams = [stream] + [torch.cuda.Stream() for _ in lanes[1:]]
-    lane_of = {l: i for i, ls in enumerate(lanes) for l in ls}
     cfgs = {}
-    for l, n in zip(levels, N):
-        n0 = level_n(l) if single else 17
-        cfgs[l] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=nu_cfg[0],
-                                    nu2=nu_cfg[1], rtol=cfg["rtol"], precision=prec, max_batch=n,
-                                    stream=lane_streams[lane_of[l]], accel=accel, max_cycles=300),
-                   0 if single else l)
     Nof = dict(zip(levels, N))
+    for i, its in enumerate(lanes):
+        for (l, a, b) in its:
+            n0 = level_n(l) if single else 17
+            cfgs[(l, a)] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=nu_cfg[0],
+                                             nu2=nu_cfg[1], rtol=cfg["rtol"], precision=prec, max_batch=Nof[l],
+                                             stream=lane_streams[i], accel=accel, max_cycles=300),
+                            0 if single else l)
     L = mg.lib()
     dp = ctypes.POINTER(ctypes.c_double)
 
     def lane(i):
-        for l in lanes[i]:
+        for (l, a, b) in lanes[i]:
             n = Nof[l]
-            c, lvl = cfgs[l]
-            first = int(sample_ids(l, rank * n, 1)[0])
+            c, lvl = cfgs[(l, a)]
+            first = int(sample_ids(l, rank * n + a, 1)[0])
             out = mg.LevelStats()
-            y, qf, qc = (ctypes.cast(b.data_ptr(), dp) for b in bufs[l])
-            st = L.mlmc_level_estimate(ctypes.byref(c), lvl, first, n, y, qf, qc, ctypes.byref(out))
+            y, qf, qc = (ctypes.cast(buf.data_ptr() + 8 * a, dp) for buf in bufs[l])
+            st = L.mlmc_level_estimate(ctypes.byref(c), lvl, first, b - a, y, qf, qc, ctypes.byref(out))
             if st < 0:
                 raise mg.MlmcError(st, "mlmc_level_estimate", L.mlmc_last_error_string().decode())
 
