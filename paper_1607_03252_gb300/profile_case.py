@@ -3,8 +3,9 @@
   python -m paper_1607_03252_gb300.profile_case --n 129 --batch 8 --prec f64 --cycles 2 \
       [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8|nodal] [--accel cg] [--timing]
 
-Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256) for `batch` realisations
-on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0) through the C ABI, so
+Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256 unless given) for `batch`
+realisations on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0; or V(nu, nu)
+to --rtol) through the C ABI, so
 that every kernel class launches with the sizes of that grid. With --timing the solve runs
 twice and the second run records CUDA events around every launch: per kernel class it
 prints launches, device time per launch and algorithmic GB/s. Exits 0 on success.
@@ -31,6 +32,10 @@ def main(argv=None):
                                           "bulk64x8", "nodal"], default="auto")
     p.add_argument("--accel", choices=["none", "cg"], default="none")
     p.add_argument("--timing", action="store_true")
+    p.add_argument("--nu", type=int, default=2, help="V(nu, nu)")
+    p.add_argument("--rtol", type=float, default=0.0, help="stop at this relative residual (0: exactly --cycles)")
+    p.add_argument("--sigma2", type=float, default=1.0)
+    p.add_argument("--ell", type=float, default=0.3)
     a = p.parse_args(argv)
     prec = mg.MLMC_PREC_F64 if a.prec == "f64" else mg.MLMC_PREC_MIXED
     sm = {"auto": mg.MLMC_SMOOTH_AUTO, "two-pass": mg.MLMC_SMOOTH_TWO_PASS, "32x8": mg.MLMC_SMOOTH_FUSED_32x8,
@@ -39,13 +44,24 @@ def main(argv=None):
           "bulk64x8": mg.MLMC_SMOOTH_BULK_64x8, "nodal": mg.MLMC_SMOOTH_NODAL}[a.smoother]
     accel = mg.MLMC_ACCEL_CG if a.accel == "cg" else mg.MLMC_ACCEL_NONE
     k = torch.empty((a.batch, a.n, a.n, a.n), dtype=torch.float64, device="cuda")
-    mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, 1.0, 0.3, a.M), sample_ids(3, 0, a.batch), k)
+    mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, a.sigma2, a.ell, a.M), sample_ids(3, 0, a.batch), k)
     u = torch.zeros_like(k)
-    cfg = mg.mg_cfg(2, 2, 0.0, a.cycles, prec, sm, accel)
+    cfg = mg.mg_cfg(a.nu, a.nu, a.rtol, a.cycles, prec, sm, accel)
     cyc, rel, st = mg.mg_solve_batch(cfg, k, u)
     torch.cuda.synchronize()
     print("n=%d batch=%d prec=%s cycles=%s rel_res=%.3e" % (a.n, a.batch, a.prec, cyc.tolist(), rel.max()))
     if a.timing:
+        # wall time of a solve on a created stream (graph replay on), then the per-kernel
+        # device times with events around every launch (graphs off)
+        side = torch.cuda.Stream()
+        u.zero_()
+        side.wait_stream(torch.cuda.current_stream())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        mg.mg_solve_batch(cfg, k, u, stream=side)
+        e1.record(side)
+        torch.cuda.synchronize()
+        print("  solve wall time (graph replay): %.3f ms" % e0.elapsed_time(e1))
         u.zero_()
         mg.profile_reset()
         mg.profile_enable(True)
