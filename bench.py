@@ -393,11 +393,12 @@ def own_arm(args):
                     e1.record(st)
                     evs[l].append((e0, e1))
 
-        if sequential:  # one lane after the other: no kernel overlaps another
-            for i in range(len(lanes)):
-                lane(i)
-        else:
-            run_lanes(torch, lanes, lane_streams, stream, lane)
+        if sequential:  # whole levels one after the other: each kernel alone, at its level's batch
+            for l in levels:
+                c, lvl = mcfg[l]
+                stats[l] = mg.mlmc_level_run(c, lvl, ids[l], Y_dev=Y[l])
+            return
+        run_lanes(torch, lanes, lane_streams, stream, lane)
         for l in levels:
             ps = [parts[(l, a)] for a in chunks[l]]
             stats[l] = ps[0] if len(ps) == 1 else MergedLevel(ps)
@@ -505,7 +506,8 @@ def own_arm(args):
             "host_wall_s": t_host,
             "timing_note": "value, per_level, clocks and gpu_launches: timed region 1 (levels on concurrent "
                            "streams, no per-launch events); roofline and kernel_classes: timed region 2 (same "
-                           "steps, levels in sequence, CUDA events around every launch on the launching stream)",
+                           "steps, whole levels in sequence, CUDA events around every launch on the launching "
+                           "stream)",
             "profiled_region_ms_per_step": profiled_ms / args.steps,
             "kernel_ms_per_step": sum(v["ms"] for v in prof.values()) / args.steps,
             "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}

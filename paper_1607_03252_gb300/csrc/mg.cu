@@ -235,8 +235,9 @@ __global__ void k_rbgs(int colour, int n, int B, const T* __restrict__ Kx, const
   }
 }
 
-// Nodal coefficient of an MG grid in the grid's precision (injection from the finest k):
-// the input of the nodal-coefficient sweep.
+// Reciprocal nodal coefficient rho = 1/k of an MG grid in the grid's precision (injection
+// from the finest k): the input of the nodal-coefficient sweep, whose harmonic faces are
+// 2ab/(a+b) = 2/(rho_a + rho_b).
 template <typename T>
 __global__ void k_nodal_k(const double* __restrict__ k0, int n0, int st0, int n, int B, T* __restrict__ kn) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
@@ -246,19 +247,17 @@ __global__ void k_nodal_k(const double* __restrict__ k0, int n0, int st0, int n,
   for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
     const int s = zz / n, z = zz - s * n;
     const size_t p0 = ((size_t)(st0 * z) * n0 + (size_t)(st0 * y)) * n0 + (size_t)(st0 * x);
-    kn[(size_t)s * n3 + (size_t)(z * n * n + q)] = (T)k0[(size_t)s * n03 + p0];
+    kn[(size_t)s * n3 + (size_t)(z * n * n + q)] = (T)(1.0 / k0[(size_t)s * n03 + p0]);
   }
 }
 
-// Harmonic face of the nodal-coefficient kernels: 2ab / (a + b) with the fast reciprocal
-// (__fdividef, within 2 ulp). Symmetric in (a, b) (2a*b is 2*(a*b) exactly), so both
-// nodes of a face see the same value; the faces differ from the stored IEEE ones by a
-// few ulps.
-__device__ __forceinline__ float nodal_face(float a, float b) {
-  return __fdividef(__fmul_rn(2.0f * a, b), __fadd_rn(a, b));
-}
+// Harmonic face of the nodal-coefficient kernels from the reciprocal coefficients:
+// 2ab / (a + b) = 2 / (rho_a + rho_b), with the fast reciprocal (__fdividef, within 2
+// ulp). Symmetric in the two nodes, so both see the same value; the faces differ from the
+// stored IEEE ones by a few ulps.
+__device__ __forceinline__ float nodal_face(float ra, float rb) { return __fdividef(2.0f, __fadd_rn(ra, rb)); }
 
-// One colour of a red-black sweep that reads the nodal coefficient (FP32) instead of
+// One colour of a red-black sweep that reads the (reciprocal) nodal coefficient (FP32) instead of
 // stored faces: the six harmonic faces, their sum D and 1/D of the updated node are
 // recomputed per update with fast reciprocals, so a sweep reads 4 words per node (u read
 // and written, g, k) instead of 7. It is the Gauss-Seidel sweep of an operator within a
@@ -723,7 +722,7 @@ struct Level {
   T *Kx = nullptr, *Ky = nullptr, *Kz = nullptr, *D = nullptr, *Dinv = nullptr;
   T *u = nullptr, *g = nullptr, *r = nullptr;
   T* u2 = nullptr;  // spare iterate for the fused (double-buffered) sweep
-  T* kn = nullptr;  // nodal coefficient (FP32 grids: input of the nodal-coefficient sweep)
+  T* kn = nullptr;  // reciprocal nodal coefficient 1/k (FP32 grids: input of the nodal sweep)
 };
 
 template <typename T>
