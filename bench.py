@@ -546,13 +546,15 @@ def roofline(prof, peaks):
                 "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
                 "traffic": traffic, "traffic_source": tsrc, "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"],
                 "hbm_achieved_gbs": per_launch_bytes / avg_s / 1e9,
-                "hbm_frac_of_measured": (per_launch_bytes / avg_s / 1e9) / hbm_peak if hbm_peak else None}
+                "hbm_frac_of_measured": (per_launch_bytes / avg_s / 1e9) / hbm_peak if hbm_peak else None,
+                "dram_gbs_from_traffic": traffic / avg_s / 1e9 if traffic else None}
     achieved = per_launch_bytes / avg_s / 1e9
     peak = hbm_peak if hbm_peak else 6800.0
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": "measured" if hbm_peak else "fallback", "traffic": traffic,
             "traffic_source": tsrc,
-            "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"]}
+            "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"],
+            "dram_gbs_from_traffic": traffic / avg_s / 1e9 if traffic else None}
 
 
 def lane_items(levels, N, times, lanes):

@@ -471,8 +471,11 @@ __global__ void k_restrict(int nf, int B, const T* __restrict__ r, T* __restrict
     if (active && !active[s]) continue;
     const T* rb = r + (size_t)s * nf3 + (size_t)(2 * Z * nf2 + 2 * Y * nf + 2 * X);
     T v = 0;
+#pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
       for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
           const T wgt = (T)((2 - abs(dx)) * (2 - abs(dy)) * (2 - abs(dz))) * (T)(1.0 / 16.0);
           v = fma(wgt, rb[dz * nf2 + dy * nf + dx], v);
@@ -501,14 +504,25 @@ __global__ void k_prolong(int nf, int B, const T* __restrict__ ec, T* __restrict
     const int s = zz / (nf - 2), z = 1 + (zz - s * (nf - 2));
     if (active && !active[s]) continue;
     const int zo = z & 1, Z = z >> 1;
-    const T* eb = ec + (size_t)s * nc3;
+    // the distinct coarse neighbours in the order (Z, Y), (Z, Y+1), (Z+1, Y), (Z+1, Y+1),
+    // each row X then X+1, as straight-line code (parities decide which exist)
+    const T* r0 = ec + (size_t)s * nc3 + (size_t)((Z * nc + Y) * nc + X);
     T v = 0;
-    for (int dz = 0; dz <= zo; ++dz)
-      for (int dy = 0; dy <= yo; ++dy) {
-        const T* row = eb + ((Z + dz) * nc + (Y + dy)) * nc + X;
-        v += row[0];
-        if (xo) v += row[1];
+    v += r0[0];
+    if (xo) v += r0[1];
+    if (yo) {
+      v += r0[nc];
+      if (xo) v += r0[nc + 1];
+    }
+    if (zo) {
+      const T* r2 = r0 + nc * nc;
+      v += r2[0];
+      if (xo) v += r2[1];
+      if (yo) {
+        v += r2[nc];
+        if (xo) v += r2[nc + 1];
       }
+    }
     const T w = xo + yo + zo == 0 ? T(1) : xo + yo + zo == 1 ? T(0.5) : xo + yo + zo == 2 ? T(0.25) : T(0.125);
     const size_t p = (size_t)s * nf3 + (size_t)((z * nf + y) * nf + x);
     u[p] += w * v;
