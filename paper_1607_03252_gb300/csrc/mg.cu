@@ -64,6 +64,33 @@ struct Carver {
   }
 };
 
+// Widening of an FP32 value to FP64 on the integer pipe only (GB300's FP64 unit, which
+// also performs the hardware conversion, runs at 1/64 of the FP32 rate, and a fallback
+// branch to the hardware conversion is if-converted into every call): for normal numbers
+// the binary64 pattern is the binary32 sign, the exponent re-biased by 1023 - 127 and the
+// 23-bit fraction shifted left by 29 (IEEE 754 layouts), exact; zeros stay zero,
+// infinities and NaNs keep an all-ones exponent, subnormals (below 1.2e-38; faces and
+// diagonals are positive normal numbers) flush to zero.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned hi_e = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + (1023u - 127u));
+  const unsigned frac = e == 0u ? 0u : (b & 0x7fffffu);
+  const unsigned hi = (b & 0x80000000u) | (hi_e << 20) | (frac >> 3);
+  const unsigned lo = frac << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+// x in the arithmetic type TD (FP32 to FP64 through widen)
+template <typename TD, typename T>
+__device__ __forceinline__ TD to_t(T x) {
+  return (TD)x;
+}
+template <>
+__device__ __forceinline__ double to_t<double, float>(float x) {
+  return widen(x);
+}
+
 __device__ __forceinline__ double harm(double a, double b, double) {
   return __ddiv_rn(__dmul_rn(2.0 * a, b), __dadd_rn(a, b));
 }
@@ -108,12 +135,12 @@ __global__ void k_diag(int n, int B, const T* __restrict__ Kx, const T* __restri
     const bool in = x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1;
     TD d = 0;
     if (in) {
-      d = (TD)Kx[t - 1];
-      d += (TD)Kx[t];
-      d += (TD)Ky[t - n];
-      d += (TD)Ky[t];
-      d += (TD)Kz[t - n2];
-      d += (TD)Kz[t];
+      d = to_t<TD>(Kx[t - 1]);
+      d += to_t<TD>(Kx[t]);
+      d += to_t<TD>(Ky[t - n]);
+      d += to_t<TD>(Ky[t]);
+      d += to_t<TD>(Kz[t - n2]);
+      d += to_t<TD>(Kz[t]);
     }
     if (D) D[t] = d;
     if (Dinv) Dinv[t] = in ? (TD)1 / d : (TD)0;
@@ -384,13 +411,13 @@ __global__ void __launch_bounds__(kThreads)
     const size_t p = (size_t)s * n3 + i;
     TD rr = 0;
     if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
-      rr = fma(-D[p], (TD)u[p], g[p]);
-      rr = fma((TD)Kx[p - 1], (TD)u[p - 1], rr);
-      rr = fma((TD)Kx[p], (TD)u[p + 1], rr);
-      rr = fma((TD)Ky[p - n], (TD)u[p - n], rr);
-      rr = fma((TD)Ky[p], (TD)u[p + n], rr);
-      rr = fma((TD)Kz[p - n2], (TD)u[p - n2], rr);
-      rr = fma((TD)Kz[p], (TD)u[p + n2], rr);
+      rr = fma(-D[p], to_t<TD>(u[p]), g[p]);
+      rr = fma(to_t<TD>(Kx[p - 1]), to_t<TD>(u[p - 1]), rr);
+      rr = fma(to_t<TD>(Kx[p]), to_t<TD>(u[p + 1]), rr);
+      rr = fma(to_t<TD>(Ky[p - n]), to_t<TD>(u[p - n]), rr);
+      rr = fma(to_t<TD>(Ky[p]), to_t<TD>(u[p + n]), rr);
+      rr = fma(to_t<TD>(Kz[p - n2]), to_t<TD>(u[p - n2]), rr);
+      rr = fma(to_t<TD>(Kz[p]), to_t<TD>(u[p + n2]), rr);
     }
     if (r) r[p] = (TR)rr;
     sq += (double)rr * (double)rr;
@@ -555,7 +582,7 @@ __global__ void k_update_mixed(int n, int B, const float* __restrict__ e, double
     const int s = zz / n, z = zz - s * n;
     if (!active[s]) continue;
     const size_t t = (size_t)s * n3 + (size_t)(z * n * n + q);
-    u[t] += (double)e[t];  // e is zero on the boundary
+    u[t] += widen(e[t]);  // e is zero on the boundary
   }
 }
 
@@ -596,37 +623,68 @@ __global__ void k_qoi_final(int B, int NB, double scale, const double* __restric
 // preconditioner). All vectors are FP64 on the finest grid; per-sample scalars.
 // ---------------------------------------------------------------------------------
 
-// q = A~ p on interior nodes (0 on the boundary); partial sums of p.q. Grid (NB, B).
+// q = A~ p on interior nodes (0 on the boundary): v = D p, then the six faces in the order
+// -x, +x, -y, +y, -z, +z, and partials of p.q, by column z-marches: a thread owns one
+// (x, y) column of a z-slab and carries p and Kz of the planes below and above in
+// registers (11 loads per node), FP32 faces widened on the integer pipe. Grid (column blocks, z-slabs, B), 128 threads; one partial of p.q per
+// (column block, slab), a partition fixed by n (apply_slabs).
 template <typename TK, typename TD>
-__global__ void __launch_bounds__(kThreads)
-    k_apply_dot(int n, const TK* __restrict__ Kx, const TK* __restrict__ Ky, const TK* __restrict__ Kz,
-                const TD* __restrict__ D, const double* __restrict__ p, double* __restrict__ q,
-                double* __restrict__ partial, const int* __restrict__ active) {
-  const int s = blockIdx.y;
+__global__ void __launch_bounds__(128)
+    k_apply_dot_z(int n, int zslab, const TK* __restrict__ Kx, const TK* __restrict__ Ky, const TK* __restrict__ Kz,
+                  const TD* __restrict__ D, const double* __restrict__ p, double* __restrict__ q,
+                  double* __restrict__ partial, const int* __restrict__ active) {
+  const int s = blockIdx.z;
   if (!active[s]) return;
-  const unsigned n3 = (unsigned)n * n * n, n2 = (unsigned)n * n, un = (unsigned)n;
-  const unsigned chunk = (n3 + gridDim.x - 1) / gridDim.x;
-  const unsigned lo = blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
+  const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
+  const int c = blockIdx.x * 128 + threadIdx.x;  // column y n + x
+  const int zlo = 1 + blockIdx.y * zslab, zhi = min(n - 2, zlo + zslab - 1);
+  const size_t n2 = (size_t)n * n;
   double acc = 0.0;
-  for (unsigned i = lo + threadIdx.x; i < hi; i += kThreads) {
-    const unsigned zq = i / n2, rem = i - zq * n2, yq = rem / un;
-    const int z = (int)zq, y = (int)yq, x = (int)(rem - yq * un);
-    const size_t t = (size_t)s * n3 + i;
-    double v = 0.0;
-    if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
-      v = (double)D[t] * p[t];
-      v = fma(-(double)Kx[t - 1], p[t - 1], v);
-      v = fma(-(double)Kx[t], p[t + 1], v);
-      v = fma(-(double)Ky[t - n], p[t - n], v);
-      v = fma(-(double)Ky[t], p[t + n], v);
-      v = fma(-(double)Kz[t - n2], p[t - n2], v);
-      v = fma(-(double)Kz[t], p[t + n2], v);
-      acc = fma(p[t], v, acc);
+  if (c < n * n) {
+    const int y = c / n, x = c - y * n;
+    const size_t col = (size_t)s * n2 * n + c;
+    if (x > 0 && y > 0 && x < n - 1 && y < n - 1) {
+      double pm = p[col + (size_t)(zlo - 1) * n2], pc = p[col + (size_t)zlo * n2];
+      double kzm = widen(Kz[col + (size_t)(zlo - 1) * n2]);
+      for (int z = zlo; z <= zhi; ++z) {
+        const size_t t = col + (size_t)z * n2;
+        const double pp = p[t + n2];
+        const double kzp = widen(Kz[t]);
+        double v = widen(D[t]) * pc;
+        v = fma(-widen(Kx[t - 1]), p[t - 1], v);
+        v = fma(-widen(Kx[t]), p[t + 1], v);
+        v = fma(-widen(Ky[t - n]), p[t - n], v);
+        v = fma(-widen(Ky[t]), p[t + n], v);
+        v = fma(-kzm, pm, v);
+        v = fma(-kzp, pp, v);
+        acc = fma(pc, v, acc);
+        q[t] = v;
+        pm = pc;
+        pc = pp;
+        kzm = kzp;
+      }
+    } else {
+      for (int z = zlo; z <= zhi; ++z) q[col + (size_t)z * n2] = 0.0;
     }
-    q[t] = v;
+    if (blockIdx.y == 0) q[col] = 0.0;                                    // plane z = 0
+    if (blockIdx.y == gridDim.y - 1) q[col + (size_t)(n - 1) * n2] = 0.0;  // plane z = n-1
   }
-  const double b = block_sum<kThreads>(acc);
-  if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = b;
+  const double bs = block_sum<128>(acc);
+  if (threadIdx.x == 0) partial[(size_t)s * nb + b] = bs;
+}
+
+// z-slabs of k_apply_dot_z: a function of n only (so a sample's sums do not depend on the
+// batch), enough (column, slab) threads per sample to fill the GPU for one sample.
+inline int apply_slabs(int n, int* zslab) {
+  int slabs = (int)((131072LL + (long long)n * n - 1) / ((long long)n * n));
+  if (slabs > n - 2) slabs = n - 2;
+  if (slabs < 1) slabs = 1;
+  *zslab = (n - 2 + slabs - 1) / slabs;
+  return (n - 2 + *zslab - 1) / *zslab;
+}
+inline int apply_blocks(int n) {
+  int zs = 0;
+  return ((n * n + 127) / 128) * apply_slabs(n, &zs);
 }
 
 // x += alpha p, r -= alpha q; partials of r.r and r.z (z: the previous preconditioned
@@ -672,7 +730,7 @@ __global__ void __launch_bounds__(kThreads)
     const size_t t = (size_t)s * n3 + i;
     double zv;
     if (e32) {
-      zv = (double)e32[t];
+      zv = widen(e32[t]);
       z[t] = zv;
     } else {
       zv = z[t];
@@ -759,6 +817,7 @@ struct Hier {
   // flexible PCG (FP64 vectors on the finest grid) and per-sample scalars
   double *R = nullptr, *P = nullptr, *Q = nullptr, *Z = nullptr;
   double *part2 = nullptr, *rz = nullptr, *rzo = nullptr, *alpha = nullptr, *beta = nullptr;
+  double* part_apply = nullptr;  // partials of p.q (k_apply_dot_z's partition)
   int tile[kMaxLevels] = {};      // fused-sweep tile shape per level
   bool fused[kMaxLevels] = {};    // fused (one pass) or two-pass smoother per level
   bool nodal[kMaxLevels] = {};    // two-pass sweep on the nodal coefficient (FP32)
@@ -808,6 +867,7 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed, bool cg) {
     H.Q = c.template take<double>(e0);
     if (mixed) H.Z = c.template take<double>(e0);
     H.part2 = c.template take<double>((size_t)B * H.NB);
+    H.part_apply = c.template take<double>((size_t)B * apply_blocks(n));
     H.rz = c.template take<double>(B);
     H.rzo = c.template take<double>(B);
     H.alpha = c.template take<double>(B);
@@ -961,6 +1021,9 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   const unsigned sb = (B + 3) / 4;  // 128-thread blocks, one warp per sample
   const unsigned g0 = blocks_for((size_t)B * l0.n3, kThreads);
   const dim3 pg = plane_grid(n * n, (long long)B * n);
+  int azslab = 0;
+  const int aslabs = apply_slabs(n, &azslab), NBa = apply_blocks(n);
+  const dim3 ag((unsigned)((n * n + 127) / 128), (unsigned)aslabs, (unsigned)B);
   const double* D = mixed ? H.D64 : (const double*)(const void*)l0.D;
   auto sync_count = [&](int* out) -> int {
     MLMC_CUDA_TRY(cudaMemcpyAsync(out, H.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -999,10 +1062,10 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
               (k_p_update<<<pg, kPlaneThreads, 0, st>>>(n, B, nullptr, zcur(), H.P, H.active)));
   while (true) {
     MLMC_LAUNCH("cg_apply_dot", nodes * (3 * Wk + 8 + 16), nodes * 16.0, st,
-                (k_apply_dot<T, double><<<rg, kThreads, 0, st>>>(n, l0.Kx, l0.Ky, l0.Kz, D, H.P, H.Q, H.partial,
-                                                                 H.active)));
-    MLMC_LAUNCH("cg_scalar", B * H.NB * 8.0, 0.0, st,
-                (k_cg_scalar<<<sb, 128, 0, st>>>(B, H.NB, 1, H.partial, H.rz, H.rzo, H.alpha, H.beta, H.active)));
+                (k_apply_dot_z<T, double><<<ag, 128, 0, st>>>(n, azslab, l0.Kx, l0.Ky, l0.Kz, D, H.P, H.Q,
+                                                               H.part_apply, H.active)));
+    MLMC_LAUNCH("cg_scalar", B * NBa * 8.0, 0.0, st,
+                (k_cg_scalar<<<sb, 128, 0, st>>>(B, NBa, 1, H.part_apply, H.rz, H.rzo, H.alpha, H.beta, H.active)));
     MLMC_LAUNCH("cg_update", all * (mixed ? 60.0 : 56.0), nodes * 8.0, st,
                 (k_cg_update<<<rg, kThreads, 0, st>>>(n, H.alpha, H.P, H.Q, a.u, H.R, zcur(),
                                                       mixed ? (float*)(void*)l0.g : nullptr, H.partial, H.part2,
