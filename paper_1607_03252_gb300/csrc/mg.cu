@@ -327,7 +327,7 @@ __global__ void k_rbgs_nodal(int colour, int n, int B, const float* __restrict__
 }
 
 // r~ = g - D u + sum K u_q of an FP32 grid from the nodal coefficient (faces and D
-// recomputed as in k_rbgs_nodal, then k_residual's operation order): the residual of the
+// recomputed as in k_rbgs_nodal, then k_residual_z's operation order): the residual of the
 // operator the nodal sweep smooths; r~ on interior nodes, 0 on the boundary; 4 words per
 // node instead of 7.
 __global__ void k_residual_nodal(int n, int B, const float* __restrict__ kn, const float* __restrict__ g,
@@ -390,42 +390,6 @@ inline int reduce_blocks(size_t work) {
   if (nb < 1) nb = 1;
   if (nb > 1024) nb = 1024;
   return (int)nb;
-}
-
-// r~ = g - D u + sum K u_q on interior nodes (0 on the boundary); optional store of r~
-// (type TR) and per-block partial sums of r~^2. Grid (NB, B).
-template <typename T, typename TD, typename TU, typename TR>
-__global__ void __launch_bounds__(kThreads)
-    k_residual(int n, const T* __restrict__ Kx, const T* __restrict__ Ky, const T* __restrict__ Kz,
-               const TD* __restrict__ D, const TD* __restrict__ g, const TU* __restrict__ u, TR* __restrict__ r,
-               double* __restrict__ partial, const int* __restrict__ active) {
-  const int s = blockIdx.y;
-  if (active && !active[s]) return;
-  const unsigned n3 = (unsigned)n * n * n, n2 = (unsigned)n * n, un = (unsigned)n;
-  const unsigned chunk = (n3 + gridDim.x - 1) / gridDim.x;
-  const unsigned lo = blockIdx.x * chunk, hi = lo + chunk < n3 ? lo + chunk : n3;
-  double sq = 0.0;
-  for (unsigned i = lo + threadIdx.x; i < hi; i += kThreads) {
-    const unsigned zq = i / n2, rem = i - zq * n2, yq = rem / un;
-    const int z = (int)zq, y = (int)yq, x = (int)(rem - yq * un);
-    const size_t p = (size_t)s * n3 + i;
-    TD rr = 0;
-    if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
-      rr = fma(-D[p], to_t<TD>(u[p]), g[p]);
-      rr = fma(to_t<TD>(Kx[p - 1]), to_t<TD>(u[p - 1]), rr);
-      rr = fma(to_t<TD>(Kx[p]), to_t<TD>(u[p + 1]), rr);
-      rr = fma(to_t<TD>(Ky[p - n]), to_t<TD>(u[p - n]), rr);
-      rr = fma(to_t<TD>(Ky[p]), to_t<TD>(u[p + n]), rr);
-      rr = fma(to_t<TD>(Kz[p - n2]), to_t<TD>(u[p - n2]), rr);
-      rr = fma(to_t<TD>(Kz[p]), to_t<TD>(u[p + n2]), rr);
-    }
-    if (r) r[p] = (TR)rr;
-    sq += (double)rr * (double)rr;
-  }
-  if (partial) {
-    const double b = block_sum<kThreads>(sq);
-    if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = b;
-  }
 }
 
 // Sum of squares over interior nodes of an FP64 array (initial ||g||). Grid (NB, B).
@@ -673,11 +637,14 @@ __global__ void __launch_bounds__(128)
   if (threadIdx.x == 0) partial[(size_t)s * nb + b] = bs;
 }
 
-// z-slabs of k_apply_dot_z: a function of n only (so a sample's sums do not depend on the
-// batch), enough (column, slab) threads per sample to fill the GPU for one sample.
+// z-slabs of the column z-march kernels: a function of n only (so a sample's sums do not
+// depend on the batch): enough (column, slab) threads to fill the GPU for one sample, but
+// slabs of at least 8 planes, so that carrying the planes below and above in registers
+// saves loads (one-plane slabs would load more than the flat kernels).
 inline int apply_slabs(int n, int* zslab) {
   int slabs = (int)((131072LL + (long long)n * n - 1) / ((long long)n * n));
-  if (slabs > n - 2) slabs = n - 2;
+  const int deep = (n - 2) / 8 > 1 ? (n - 2) / 8 : 1;
+  if (slabs > deep) slabs = deep;
   if (slabs < 1) slabs = 1;
   *zslab = (n - 2 + slabs - 1) / slabs;
   return (n - 2 + *zslab - 1) / *zslab;
@@ -685,6 +652,62 @@ inline int apply_slabs(int n, int* zslab) {
 inline int apply_blocks(int n) {
   int zs = 0;
   return ((n * n + 127) / 128) * apply_slabs(n, &zs);
+}
+
+// r~ = g - D u + sum K u_q on interior nodes (0 on the boundary) by column z-marches (the
+// launch shape and partition of k_apply_dot_z): rr = g - D u, then the faces in the order
+// -x, +x, -y, +y, -z, +z; optional store of r~ (type TR) and per-(column block, slab)
+// partials of r~^2 (FP64).
+template <typename T, typename TD, typename TU, typename TR>
+__global__ void __launch_bounds__(128)
+    k_residual_z(int n, int zslab, const T* __restrict__ Kx, const T* __restrict__ Ky, const T* __restrict__ Kz,
+                 const TD* __restrict__ D, const TD* __restrict__ g, const TU* __restrict__ u, TR* __restrict__ r,
+                 double* __restrict__ partial, const int* __restrict__ active) {
+  const int s = blockIdx.z;
+  if (active && !active[s]) return;
+  const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
+  const int c = blockIdx.x * 128 + threadIdx.x;  // column y n + x
+  const int zlo = 1 + blockIdx.y * zslab, zhi = min(n - 2, zlo + zslab - 1);
+  const size_t n2 = (size_t)n * n;
+  double sq = 0.0;
+  if (c < n * n) {
+    const int y = c / n, x = c - y * n;
+    const size_t col = (size_t)s * n2 * n + c;
+    if (x > 0 && y > 0 && x < n - 1 && y < n - 1) {
+      TD um = to_t<TD>(u[col + (size_t)(zlo - 1) * n2]), uc = to_t<TD>(u[col + (size_t)zlo * n2]);
+      TD kzm = to_t<TD>(Kz[col + (size_t)(zlo - 1) * n2]);
+      for (int z = zlo; z <= zhi; ++z) {
+        const size_t t = col + (size_t)z * n2;
+        const TD up = to_t<TD>(u[t + n2]);
+        const TD kzp = to_t<TD>(Kz[t]);
+        TD rr = fma(-D[t], uc, g[t]);
+        rr = fma(to_t<TD>(Kx[t - 1]), to_t<TD>(u[t - 1]), rr);
+        rr = fma(to_t<TD>(Kx[t]), to_t<TD>(u[t + 1]), rr);
+        rr = fma(to_t<TD>(Ky[t - n]), to_t<TD>(u[t - n]), rr);
+        rr = fma(to_t<TD>(Ky[t]), to_t<TD>(u[t + n]), rr);
+        rr = fma(kzm, um, rr);
+        rr = fma(kzp, up, rr);
+        if (r) r[t] = (TR)rr;
+        sq += (double)rr * (double)rr;
+        um = uc;
+        uc = up;
+        kzm = kzp;
+      }
+    } else if (r) {
+      for (int z = zlo; z <= zhi; ++z) r[col + (size_t)z * n2] = TR(0);
+    }
+    if (r && blockIdx.y == 0) r[col] = TR(0);                                    // plane z = 0
+    if (r && blockIdx.y == gridDim.y - 1) r[col + (size_t)(n - 1) * n2] = TR(0);  // plane z = n-1
+  }
+  if (partial) {
+    const double bs = block_sum<128>(sq);
+    if (threadIdx.x == 0) partial[(size_t)s * nb + b] = bs;
+  }
+}
+
+inline dim3 zmarch_grid(int n, int B, int* zslab) {
+  const int slabs = apply_slabs(n, zslab);
+  return dim3((unsigned)((n * n + 127) / 128), (unsigned)slabs, (unsigned)B);
 }
 
 // x += alpha p, r -= alpha q; partials of r.r and r.z (z: the previous preconditioned
@@ -813,7 +836,8 @@ struct Hier {
   int* active = nullptr;
   int* n_active = nullptr;
   int* err = nullptr;  // device error word of bounded waits
-  int NB = 1;
+  int NB = 1;   // partials per sample of the flat-chunk reductions (reduce_blocks)
+  int NBz = 1;  // partials per sample of the column z-march kernels (apply_blocks)
   // flexible PCG (FP64 vectors on the finest grid) and per-sample scalars
   double *R = nullptr, *P = nullptr, *Q = nullptr, *Z = nullptr;
   double *part2 = nullptr, *rz = nullptr, *rzo = nullptr, *alpha = nullptr, *beta = nullptr;
@@ -854,7 +878,8 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed, bool cg) {
   H.Ainv = c.template take<double>((size_t)B * 729);
   H.Lws = c.template take<double>((size_t)B * 729);
   H.NB = reduce_blocks(cube(n));
-  H.partial = c.template take<double>((size_t)B * H.NB);
+  H.NBz = apply_blocks(n);
+  H.partial = c.template take<double>((size_t)B * (H.NB > H.NBz ? H.NB : H.NBz));
   H.g2 = c.template take<double>(B);
   H.relres = c.template take<double>(B);
   H.cycles = c.template take<int>(B);
@@ -949,10 +974,11 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
     }
   }
   if (!nodal_res) {
-    dim3 rg(reduce_blocks(v.n3), B);
+    int zs = 0;
+    const dim3 rz = zmarch_grid(v.n, B, &zs);
     MLMC_LAUNCH(Names<T>::residual, B * interior(v.n) * 7.0 * W, B * interior(v.n) * 14.0, st,
-                (k_residual<T, T, T, T><<<rg, kThreads, 0, st>>>(v.n, v.Kx, v.Ky, v.Kz, v.D, v.g, v.u, v.r, nullptr,
-                                                                act)));
+                (k_residual_z<T, T, T, T><<<rz, 128, 0, st>>>(v.n, zs, v.Kx, v.Ky, v.Kz, v.D, v.g, v.u, v.r, nullptr,
+                                                              act)));
   }
   Level<T>& w = H.lv[j + 1];
   MLMC_LAUNCH(Names<T>::restrict_, B * ((double)v.n3 + (double)w.n3) * W, B * interior(w.n) * 54.0, st,
@@ -1044,10 +1070,10 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   // r = g - A x, ||r||
   MLMC_CUDA_TRY(cudaMemsetAsync(H.n_active, 0, sizeof(int), st));
   MLMC_LAUNCH("cg_residual", nodes * (3 * Wk + 32), nodes * 16.0, st,
-              (k_residual<T, double, double, double><<<rg, kThreads, 0, st>>>(n, l0.Kx, l0.Ky, l0.Kz, D, H.g64,
-                                                                             a.u, H.R, H.partial, H.active)));
-  MLMC_LAUNCH("norm_update", B * H.NB * 8.0, B * H.NB * 1.0, st,
-              (k_norm_update<<<sb, 128, 0, st>>>(B, H.NB, H.partial, H.g2, H.relres, H.cycles, H.active, 1, 0, rtol,
+              (k_residual_z<T, double, double, double><<<ag, 128, 0, st>>>(n, azslab, l0.Kx, l0.Ky, l0.Kz, D, H.g64,
+                                                                          a.u, H.R, H.partial, H.active)));
+  MLMC_LAUNCH("norm_update", B * NBa * 8.0, B * NBa * 1.0, st,
+              (k_norm_update<<<sb, 128, 0, st>>>(B, NBa, H.partial, H.g2, H.relres, H.cycles, H.active, 1, 0, rtol,
                                                  maxc, H.n_active)));
   int na = 0;
   MLMC_TRY(sync_count(&na));
@@ -1185,17 +1211,19 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   const int maxc = a.cfg.max_cycles;
   auto residual_check = [&](int inc) -> int {
     MLMC_CUDA_TRY(cudaMemsetAsync(H.n_active, 0, sizeof(int), st));
+    int zs = 0;
+    const dim3 rz = zmarch_grid(a.n, B, &zs);
     if (mixed) {
       MLMC_LAUNCH("residual_mixed", B * interior(a.n) * (3 * W + 8 * 3 + W), B * interior(a.n) * 16.0, st,
-                  (k_residual<T, double, double, T><<<rg, kThreads, 0, st>>>(a.n, l0.Kx, l0.Ky, l0.Kz, H.D64, H.g64,
-                                                                             a.u, l0.g, H.partial, H.active)));
+                  (k_residual_z<T, double, double, T><<<rz, 128, 0, st>>>(a.n, zs, l0.Kx, l0.Ky, l0.Kz, H.D64, H.g64,
+                                                                          a.u, l0.g, H.partial, H.active)));
     } else {
       MLMC_LAUNCH("residual_norm_f64", B * interior(a.n) * 6.0 * 8, B * interior(a.n) * 16.0, st,
-                  (k_residual<T, T, T, T><<<rg, kThreads, 0, st>>>(a.n, l0.Kx, l0.Ky, l0.Kz, l0.D, l0.g, l0.u,
-                                                                  nullptr, H.partial, H.active)));
+                  (k_residual_z<T, T, T, T><<<rz, 128, 0, st>>>(a.n, zs, l0.Kx, l0.Ky, l0.Kz, l0.D, l0.g, l0.u,
+                                                                nullptr, H.partial, H.active)));
     }
-    MLMC_LAUNCH("norm_update", B * H.NB * 8.0, B * H.NB * 1.0, st,
-                (k_norm_update<<<sb, 128, 0, st>>>(B, H.NB, H.partial, H.g2, H.relres, H.cycles, H.active, 1, inc,
+    MLMC_LAUNCH("norm_update", B * H.NBz * 8.0, B * H.NBz * 1.0, st,
+                (k_norm_update<<<sb, 128, 0, st>>>(B, H.NBz, H.partial, H.g2, H.relres, H.cycles, H.active, 1, inc,
                                                    rtol, maxc, H.n_active)));
     int na = 0;
     MLMC_CUDA_TRY(cudaMemcpyAsync(&na, H.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
