@@ -15,7 +15,9 @@ Parity status (each item's pin lives in tests/test_oracle_*.py):
   Philox4x32-10 words  round structure pinned through the 64-bit variant against
                        numpy's Philox4x64-10; the 32-bit constants are pinned only by
                        statistical tests (no published test vector is available offline);
-  field                pinned by its mean, variance and covariance closed forms;
+  field                pinned by its mean, variance and covariance closed forms, for the
+                       Gaussian covariance and for the exponential one of Sec. 3.2 (the
+                       multivariate Cauchy radial law, isotropy, the characteristic function);
   operator, smoother,  pinned by the exact discrete eigenfunction, the O(h^2)
   transfer, V-cycle    manufactured-solution rate, a dense direct solve, the transfer
                        adjoint and exactness identities, and h-independent convergence;

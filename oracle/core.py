@@ -17,6 +17,10 @@ ORC_ERR_INVALID = -1
 ORC_ERR_OOM = -2
 ORC_ERR_NOT_CONVERGED = -3
 
+# covariance families of the field (Gaussian; exponential, Sec. 3.2)
+COV_GAUSS = 0
+COV_EXP = 1
+
 _lib = None
 _lock = threading.Lock()
 
@@ -37,6 +41,7 @@ class OrcCfg(ctypes.Structure):
         ("rtol", ctypes.c_double),
         ("max_cycles", ctypes.c_int),
         ("mixed", ctypes.c_int),
+        ("cov", ctypes.c_int),
     ]
 
 
@@ -48,12 +53,13 @@ def lib():
             L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
             L.orc_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
             L.orc_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _dp]
-            L.orc_features.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, _dp, _dp]
+            L.orc_features.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       _dp, _dp]
             L.orc_logk_point.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.orc_logk_point.restype = ctypes.c_double
             L.orc_field.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
-                                    ctypes.c_double, ctypes.c_int, _dp]
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp]
             L.orc_apply.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int]
             L.orc_residual.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int]
             L.orc_rbgs_sweep.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int]
@@ -109,10 +115,10 @@ def uniforms(run_seed, sample_id, m):
     return U
 
 
-def features(run_seed, sample_id, M, ell):
+def features(run_seed, sample_id, M, ell, cov=COV_GAUSS):
     w = np.zeros((M, 3))
     b = np.zeros(M)
-    lib().orc_features(run_seed, sample_id, M, ell, _d(w), _d(b))
+    lib().orc_features(run_seed, sample_id, M, ell, int(cov), _d(w), _d(b))
     return w, b
 
 
@@ -122,9 +128,9 @@ def logk_point(w, b, sigma, x, y, z):
     return lib().orc_logk_point(_d(w), _d(b), len(b), sigma, x, y, z)
 
 
-def field(run_seed, sample_id, M, sigma2, ell, n):
+def field(run_seed, sample_id, M, sigma2, ell, n, cov=COV_GAUSS):
     k = np.zeros((n, n, n))
-    st = lib().orc_field(run_seed, sample_id, M, float(np.sqrt(sigma2)), ell, n, _d(k))
+    st = lib().orc_field(run_seed, sample_id, M, float(np.sqrt(sigma2)), ell, int(cov), n, _d(k))
     if st != ORC_OK:
         raise ValueError("orc_field failed: %d" % st)
     return k
@@ -210,8 +216,8 @@ def qoi(u):
     return lib().orc_qoi(n, _d(u))
 
 
-def make_cfg(run_seed, sigma2, ell, M, nu1=2, nu2=2, rtol=1e-10, max_cycles=100, mixed=False):
-    return OrcCfg(run_seed, sigma2, ell, M, nu1, nu2, rtol, max_cycles, int(mixed))
+def make_cfg(run_seed, sigma2, ell, M, nu1=2, nu2=2, rtol=1e-10, max_cycles=100, mixed=False, cov=COV_GAUSS):
+    return OrcCfg(run_seed, sigma2, ell, M, nu1, nu2, rtol, max_cycles, int(mixed), int(cov))
 
 
 def sample(cfg, n_fine, n_coarse, sample_id):

@@ -21,8 +21,12 @@
  *   operator  (A u)_p = h^-2 sum_{q in N(p)} k_pq (u_p - u_q), the vertex-centred
  *             7-point finite-volume form with harmonic-mean face coefficients
  *             k_pq = 2 k_p k_q / (k_p + k_q) of the nodal k (boundary nodes included);
- *   field     log k(x) = sigma sqrt(2/M) sum_m cos(w_m . x + b_m),
- *             w_m ~ N(0, I/ell^2), b_m ~ U[0, 2 pi), drawn by Philox4x32-10;
+ *   field     log k(x) = sigma sqrt(2/M) sum_m cos(w_m . x + b_m), b_m ~ U[0, 2 pi),
+ *             drawn by Philox4x32-10, with w_m from the spectral density of the
+ *             covariance: Gaussian sigma^2 exp(-r^2 / (2 ell^2)) gives w_m ~ N(0, I/ell^2);
+ *             exponential sigma^2 exp(-r / ell) (the paper's covariance, Sec. 3.2) gives
+ *             the 3-D multivariate Cauchy law w_m = z / (ell |chi|), z ~ N(0, I),
+ *             chi ~ N(0, 1) independent (density proportional to (1 + ell^2 |w|^2)^-2);
  *   cycle     V(nu1, nu2) with red-black Gauss-Seidel, full weighting, trilinear
  *             prolongation, rediscretised coarse operators (k injected), exact dense
  *             Cholesky solve on the 5^3 grid; cycles repeat until ||f-Au||/||f|| <= rtol;
@@ -45,6 +49,10 @@
 #define ORC_ERR_NOT_CONVERGED (-3)
 
 static const double ORC_PI = 3.14159265358979323846;
+
+/* covariance families of the field */
+#define ORC_COV_GAUSS 0
+#define ORC_COV_EXP 1
 
 /* ------------------------------------------------------------------------------------
  * Philox4x32-10 and Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
@@ -132,18 +140,25 @@ void orc_uniforms(uint64_t run_seed, uint64_t sample_id, int m, double U[6]) {
   for (int i = 0; i < 6; ++i) U[i] = uniform53(words[2 * i], words[2 * i + 1]);
 }
 
-void orc_features(uint64_t run_seed, uint64_t sample_id, int M, double ell, double* w, double* b) {
+void orc_features(uint64_t run_seed, uint64_t sample_id, int M, double ell, int cov, double* w, double* b) {
   for (int m = 0; m < M; ++m) {
     double U[6];
     orc_uniforms(run_seed, sample_id, m, U);
     double r1 = sqrt(-2.0 * log(U[0]));
     double r2 = sqrt(-2.0 * log(U[2]));
+    /* Box-Muller: two independent standard normals from each uniform pair */
     double g1 = r1 * cos(2.0 * ORC_PI * U[1]);
     double g2 = r1 * sin(2.0 * ORC_PI * U[1]);
     double g3 = r2 * cos(2.0 * ORC_PI * U[3]);
-    w[3 * m + 0] = g1 / ell;
-    w[3 * m + 1] = g2 / ell;
-    w[3 * m + 2] = g3 / ell;
+    double scale = 1.0 / ell;
+    if (cov == ORC_COV_EXP) {
+      /* multivariate Cauchy: divide the Gaussian vector by |chi|, chi the fourth normal */
+      double chi = r2 * sin(2.0 * ORC_PI * U[3]);
+      scale = 1.0 / (ell * fabs(chi));
+    }
+    w[3 * m + 0] = g1 * scale;
+    w[3 * m + 1] = g2 * scale;
+    w[3 * m + 2] = g3 * scale;
     b[m] = 2.0 * ORC_PI * U[4];
   }
 }
@@ -156,12 +171,12 @@ double orc_logk_point(const double* w, const double* b, int M, double sigma, dou
 }
 
 /* Nodal coefficient k = exp(log k) at all n^3 nodes (x fastest). */
-int orc_field(uint64_t run_seed, uint64_t sample_id, int M, double sigma, double ell, int n, double* k) {
-  if (M <= 0 || n < 2) return ORC_ERR_INVALID;
+int orc_field(uint64_t run_seed, uint64_t sample_id, int M, double sigma, double ell, int cov, int n, double* k) {
+  if (M <= 0 || n < 2 || (cov != ORC_COV_GAUSS && cov != ORC_COV_EXP)) return ORC_ERR_INVALID;
   double* w = (double*)malloc(sizeof(double) * 3 * (size_t)M);
   double* b = (double*)malloc(sizeof(double) * (size_t)M);
   if (!w || !b) { free(w); free(b); return ORC_ERR_OOM; }
-  orc_features(run_seed, sample_id, M, ell, w, b);
+  orc_features(run_seed, sample_id, M, ell, cov, w, b);
   double h = 1.0 / (double)(n - 1);
   for (int kz = 0; kz < n; ++kz)
     for (int jy = 0; jy < n; ++jy)
@@ -557,6 +572,7 @@ typedef struct {
   double rtol;
   int max_cycles;
   int mixed;
+  int cov; /* ORC_COV_GAUSS or ORC_COV_EXP */
 } orc_cfg;
 
 static int solve_q(const orc_cfg* c, uint64_t sample_id, int n, double* Q, int* cycles) {
@@ -564,7 +580,7 @@ static int solve_q(const orc_cfg* c, uint64_t sample_id, int n, double* Q, int* 
   double* k = (double*)malloc(n3 * sizeof(double));
   double* u = (double*)calloc(n3, sizeof(double));
   if (!k || !u) { free(k); free(u); return ORC_ERR_OOM; }
-  int st = orc_field(c->run_seed, sample_id, c->M, sqrt(c->sigma2), c->ell, n, k);
+  int st = orc_field(c->run_seed, sample_id, c->M, sqrt(c->sigma2), c->ell, c->cov, n, k);
   if (st == ORC_OK) {
     double relres;
     st = orc_mg_solve(n, k, NULL, u, c->nu1, c->nu2, c->rtol, c->max_cycles, c->mixed, cycles, &relres, NULL);
