@@ -9,7 +9,10 @@ Contents:
                  function citing the passage of Gmeiner et al. it follows;
   core.py        ctypes wrapper around it;
   stats.py       MLMC estimator statistics (Sec. 2: Eqs. 6, 8, 10, 11, 14, 15) from
-                 their plain definitions with exactly rounded sums.
+                 their plain definitions with exactly rounded sums, and the rate fit of
+                 the alpha, beta, gamma exponents (Eqs. 12, 14);
+  adaptive.py    Algorithm 2 (adaptive MLMC with level growth by the bias test) over
+                 any sampler of the level differences.
 
 Parity status (each item's pin lives in tests/test_oracle_*.py):
   Philox4x32-10 words  round structure pinned through the 64-bit variant against
@@ -22,7 +25,12 @@ Parity status (each item's pin lives in tests/test_oracle_*.py):
   transfer, V-cycle    manufactured-solution rate, a dense direct solve, the transfer
                        adjoint and exactness identities, and h-independent convergence;
   QoI                  pinned by trapezoid exactness on multilinear functions;
-  statistics           pinned by math.fsum and a hand-evaluated Eq. 11 case.
+  statistics           pinned by math.fsum and a hand-evaluated Eq. 11 case;
+  rate fit             pinned by exact geometric data and an independent polynomial fit;
+  Algorithm 2          pinned by hand-worked level counts of synthetic samplers (the
+                       eps_b / eps and alpha choices each change them) and by the
+                       stopping invariants (Eq. 10 sampling variance <= eps_s^2, the bias
+                       test met at L and failed at L - 1).
 """
 from .core import *  # noqa: F401,F403
-from . import stats  # noqa: F401
+from . import adaptive, stats  # noqa: F401

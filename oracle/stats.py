@@ -56,3 +56,21 @@ def sampling_variance(V: Sequence[float], N: Sequence[float]) -> float:
 def bias_bound(Y_hat_L: float, alpha: float) -> float:
     """|E[Q_L - Q]| <= |Y-hat_L| / (8^alpha - 1) (Eq. 14, absolute value taken)."""
     return abs(Y_hat_L) / (8.0 ** alpha - 1.0)
+
+
+def fit_rate(levels: Sequence[int], values: Sequence[float]) -> float:
+    """Rate a of values ~ c 8^(-a l) on a uniformly refined hierarchy (M_l ~ 8^l M_0, so
+    |E[Q_l - Q]| ~ M_l^-alpha of Sec. 2.3 gives |Y-hat_l| ~ 8^-alpha l, and Eq. 12's
+    V[Y_l] <= C_v M_l^-beta, C_l <= C_c M_l^gamma give the other two): minus the
+    least-squares slope of log_8 |value| against l, from the normal equations of the
+    line fit with exactly rounded sums. Needs at least two distinct levels."""
+    if len(levels) < 2 or len(set(levels)) < 2:
+        raise ValueError("a rate needs at least two distinct levels")
+    x = [float(l) for l in levels]
+    y = [math.log(abs(v)) / math.log(8.0) for v in values]
+    n = float(len(x))
+    sx, sy = math.fsum(x), math.fsum(y)
+    sxx = math.fsum(a * a for a in x)
+    sxy = math.fsum(a * b for a, b in zip(x, y))
+    slope = (n * sxy - sx * sy) / (n * sxx - sx * sx)
+    return -slope

@@ -68,7 +68,8 @@ def test_invalid_grid_rejected_on_host():
 def test_invalid_field_cfg_rejected_on_host():
     L = mg.lib()
     ids = (ctypes.c_uint64 * 1)(1)
-    for cfg in (mg.field_cfg(1, 1.0, 0.0, 8), mg.field_cfg(1, -1.0, 0.3, 8), mg.field_cfg(1, 1.0, 0.3, 0)):
+    for cfg in (mg.field_cfg(1, 1.0, 0.0, 8), mg.field_cfg(1, -1.0, 0.3, 8), mg.field_cfg(1, 1.0, 0.3, 0),
+                mg.field_cfg(1, 1.0, 0.3, 8, cov=2), mg.field_cfg(1, 1.0, 0.3, 8, cov=-1)):
         st = L.mlmc_field_eval(ctypes.byref(cfg), ids, 1, 9, mg.MLMC_F64, ctypes.c_void_p(8), None)
         assert st == mg.MLMC_ERR_INVALID
 
@@ -94,3 +95,14 @@ def test_tune_set_validates_on_host():
     assert L.mlmc_tune_set(33, mg.MLMC_PREC_F64, mg.MLMC_SMOOTH_NODAL + 1, 3) == mg.MLMC_ERR_INVALID
     assert L.mlmc_tune_set(33, mg.MLMC_PREC_F64, mg.MLMC_SMOOTH_TWO_PASS, 0) == mg.MLMC_ERR_INVALID
     mg.mlmc_tune_set(65, mg.MLMC_PREC_F64, "two-pass", 2)
+
+
+def test_field_cfg_layout_and_cov_default():
+    """cov occupies the former tail padding of mlmc_field_cfg: the size stays 32 bytes and
+    a zero-filled struct selects the Gaussian covariance."""
+    import ctypes
+
+    assert ctypes.sizeof(mg.FieldCfg) == 32
+    assert mg.FieldCfg.cov.offset == 28
+    assert mg.field_cfg(1, 1.0, 0.3, 8).cov == mg.MLMC_COV_GAUSS
+    assert mg.field_cfg(1, 1.0, 0.3, 8, cov=mg.MLMC_COV_EXP).cov == 1

@@ -156,6 +156,31 @@ def test_invalid_arguments_rejected():
         mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, 1.0, -1.0, 8), [1], k)
 
 
+def _exp_field_tol(orc, sid, M, sigma2, ell):
+    """Relative k tolerance for the exponential covariance. Its Cauchy frequencies reach
+    |w| ~ 1e4 / ell, and the GPU rounds w_x x, w_y y, w_z z + b separately where the oracle
+    rounds their sum: per feature the phases differ by at most ~4 eps (|w|_1 + 2 pi), so
+    log k differs by sigma sqrt(2/M) times the sum of those bounds, plus the 1e-12 of the
+    Gaussian case (the separable products in double-float)."""
+    w, _ = orc.features(RUN_SEED, int(sid), M, ell, cov=orc.COV_EXP)
+    eps = np.finfo(np.float64).eps
+    phase = np.sum(4.0 * eps * (np.abs(w).sum(axis=1) + 2.0 * np.pi))
+    return 1e-12 + np.sqrt(sigma2) * np.sqrt(2.0 / M) * phase
+
+
+@pytest.mark.parametrize("n,sigma2,ell,M", [(9, 1.0, 0.3, 256), (17, 2.0, 0.1, 256), (33, 1.0, 0.05, 64)])
+def test_field_eval_exp_covariance_matches_oracle(orc, n, sigma2, ell, M):
+    ids = sample_ids(2, 5, 3)
+    k = torch.zeros((3, n, n, n), dtype=torch.float64, device=DEV)
+    mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, sigma2, ell, M, cov=mg.MLMC_COV_EXP), ids, k)
+    k = k.cpu().numpy()
+    for s, sid in enumerate(ids):
+        ko = orc.field(RUN_SEED, int(sid), M, sigma2, ell, n, cov=orc.COV_EXP)
+        assert np.max(np.abs(k[s] - ko) / ko) < _exp_field_tol(orc, sid, M, sigma2, ell)
+        # and it is not the Gaussian field of the same draws
+        assert relmax(k[s], orc.field(RUN_SEED, int(sid), M, sigma2, ell, n)) > 1e-3
+
+
 def _y_tol(Qf, Qc, tol):
     return tol * np.maximum(np.abs(Qf), np.abs(Qc))
 
@@ -188,6 +213,35 @@ def test_level_estimate_mixed_matches_oracle_mixed(orc):
     Y64, Qf64, Qc64, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 2.0, 0.2, 256, rtol=1e-11), 33, 17, ids)
     assert np.all(np.abs(Y - Ym) <= _y_tol(Qfm, Qcm, 1e-9))
     # stated error of the mixed form against FP64, normalised by Q
+    assert np.all(np.abs(Y - Y64) <= _y_tol(Qf64, Qc64, 1e-6))
+
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_level_estimate_exp_covariance_matches_oracle(orc, level):
+    """The paper's exponential covariance (rougher fields, 15-25 cycles at rtol 1e-12)."""
+    ids = sample_ids(level, 40, 5)
+    cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.1, 256, n0=17, rtol=1e-12, max_cycles=300, cov=mg.MLMC_COV_EXP)
+    stats, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
+    ocfg = orc.make_cfg(RUN_SEED, 1.0, 0.1, 256, rtol=1e-12, max_cycles=300, cov=orc.COV_EXP)
+    nf = level_n(level)
+    nc = level_n(level - 1) if level > 0 else 0
+    Yo, Qfo, Qco, cfo, cco, sto = orc.level_batch(ocfg, nf, nc, ids)
+    assert sto == 0
+    assert np.all(np.abs(Y - Yo) <= _y_tol(Qfo, Qco, 1e-9))
+    assert np.all(np.abs(Qf - Qfo) <= 1e-9 * np.abs(Qfo))
+    assert stats.N == len(ids)
+
+
+def test_level_estimate_exp_covariance_mixed(orc):
+    level, ids = 1, sample_ids(1, 50, 4)
+    kw = dict(rtol=1e-11, max_cycles=300)
+    cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.1, 256, n0=17, precision=mg.MLMC_PREC_MIXED, accel=mg.MLMC_ACCEL_CG,
+                           cov=mg.MLMC_COV_EXP, **kw)
+    _, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
+    Ym, Qfm, Qcm, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 1.0, 0.1, 256, mixed=True, cov=orc.COV_EXP, **kw),
+                                       33, 17, ids)
+    Y64, Qf64, Qc64, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 1.0, 0.1, 256, cov=orc.COV_EXP, **kw), 33, 17, ids)
+    assert np.all(np.abs(Y - Ym) <= _y_tol(Qfm, Qcm, 1e-9))
     assert np.all(np.abs(Y - Y64) <= _y_tol(Qf64, Qc64, 1e-6))
 
 
