@@ -16,13 +16,18 @@
  *            u = 0 on boundary nodes;
  *   operator (A u)_p = h^-2 sum_{q in N(p)} k_pq (u_p - u_q), 7-point, harmonic-mean
  *            faces k_pq = 2 k_p k_q / (k_p + k_q) of the nodal coefficient;
- *   field    log k(x) = sigma sqrt(2/M) sum_m cos(w_m . x + b_m), w_m ~ N(0, I/ell^2),
+ *   field    log k(x) = sigma sqrt(2/M) sum_m cos(w_m . x + b_m), random Fourier features
+ *            of a stationary covariance: w_m ~ N(0, I/ell^2) for the Gaussian covariance
+ *            sigma^2 exp(-r^2 / (2 ell^2)) (MLMC_COV_GAUSS), w_m ~ multivariate Cauchy,
+ *            density proportional to (1 + ell^2 |w|^2)^-2, for the exponential
+ *            covariance sigma^2 exp(-r / ell) of Sec. 3.2 (MLMC_COV_EXP);
  *            b_m ~ U[0, 2 pi), drawn by Philox4x32-10 keyed by (run_seed, sample_id):
  *            key = (seed low, seed high), counter = (id low, id high, m, c), c = 0,1,2;
  *            the 12 words give six 53-bit uniforms U = ((a>>5) 2^26 + (b>>6) + 1/2) 2^-53
  *            from consecutive word pairs; Box-Muller on (U1,U2), (U3,U4) gives
  *            g1, g2 (cos, sin of the first pair) and g3 (cos of the second);
- *            w_m = (g1, g2, g3) / ell, b_m = 2 pi U5;
+ *            w_m = (g1, g2, g3) / ell (Gaussian) or (g1, g2, g3) / (ell |g4|) with g4
+ *            the sin of the second pair (exponential), b_m = 2 pi U5;
  *   solver   V(nu1, nu2) cycles: red ((i+j+k) even) then black Gauss-Seidel sweeps,
  *            full weighting (1/64)(1,2,1)^3, trilinear prolongation, rediscretised
  *            coarse operators (k injected), exact solve on the 5^3 grid; cycles repeat
@@ -74,12 +79,18 @@ extern "C" {
 #define MLMC_PREC_F64 0   /* every step in FP64 */
 #define MLMC_PREC_MIXED 1 /* FP32 faces, FP32 V-cycle as correction; FP64 residual and update */
 
-/* Parameters of the lognormal random field (Sec. 3.2; Fourier-feature form above). */
+/* ---- covariance of log k ---- */
+#define MLMC_COV_GAUSS 0 /* sigma^2 exp(-|x-y|^2 / (2 ell^2)) */
+#define MLMC_COV_EXP 1   /* sigma^2 exp(-|x-y| / ell), the paper's covariance (Sec. 3.2) */
+
+/* Parameters of the lognormal random field (Sec. 3.2; Fourier-feature form above).
+   A zero-initialised `cov` selects the Gaussian covariance. */
 typedef struct {
   uint64_t run_seed; /* Philox key */
   double sigma2;     /* variance of log k, >= 0 */
   double ell;        /* correlation length, > 0 */
   int M;             /* number of Fourier features, >= 1 */
+  int cov;           /* MLMC_COV_GAUSS or MLMC_COV_EXP */
 } mlmc_field_cfg;
 
 /* Smoother implementations (all compute the same red-black sweep, bit for bit). */
@@ -130,7 +141,7 @@ typedef struct {
  * `dtype`: MLMC_F64, or MLMC_F32 = the FP64 value rounded to FP32). The phase is
  * always evaluated in FP64. sample_ids_host is host memory, read before return.
  * Errors: MLMC_ERR_INVALID for n not 2^p+1 (5 <= n <= 4097), batch < 1, M < 1,
- * ell <= 0, sigma2 < 0, unknown dtype or NULL pointers; MLMC_ERR_OOM / _CUDA.
+ * ell <= 0, sigma2 < 0, unknown cov or dtype, or NULL pointers; MLMC_ERR_OOM / _CUDA.
  * Enqueued on `stream`; the library's scratch is released stream-ordered.
  */
 int mlmc_field_eval(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n, int dtype,

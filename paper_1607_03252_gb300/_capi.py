@@ -29,6 +29,8 @@ MLMC_F64 = 0
 MLMC_F32 = 1
 MLMC_PREC_F64 = 0
 MLMC_PREC_MIXED = 1
+MLMC_COV_GAUSS = 0
+MLMC_COV_EXP = 1
 
 _STATUS_NAMES = {
     MLMC_ERR_INVALID: "MLMC_ERR_INVALID",
@@ -49,7 +51,7 @@ class MlmcError(RuntimeError):
 
 class FieldCfg(ctypes.Structure):
     _fields_ = [("run_seed", ctypes.c_uint64), ("sigma2", ctypes.c_double), ("ell", ctypes.c_double),
-                ("M", ctypes.c_int)]
+                ("M", ctypes.c_int), ("cov", ctypes.c_int)]
 
 
 MLMC_SMOOTH_AUTO = 0
@@ -207,8 +209,8 @@ def _grid_tensor(t, dtype, name):
     return t
 
 
-def field_cfg(run_seed, sigma2, ell, M):
-    return FieldCfg(int(run_seed), float(sigma2), float(ell), int(M))
+def field_cfg(run_seed, sigma2, ell, M, cov=MLMC_COV_GAUSS):
+    return FieldCfg(int(run_seed), float(sigma2), float(ell), int(M), int(cov))
 
 
 def mg_cfg(nu1=2, nu2=2, rtol=1e-10, max_cycles=100, precision=MLMC_PREC_F64, smoother=MLMC_SMOOTH_AUTO,
@@ -351,11 +353,11 @@ def profile_read():
 
 def make_mlmc_cfg(run_seed, sigma2, ell, M, n0=17, nu1=2, nu2=2, rtol=1e-10, max_cycles=100,
                   precision=MLMC_PREC_F64, max_batch=0, stream=None, smoother=MLMC_SMOOTH_AUTO,
-                  accel=MLMC_ACCEL_NONE):
+                  accel=MLMC_ACCEL_NONE, cov=MLMC_COV_GAUSS):
     sp = ctypes.c_void_p(0)
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream)
-    return MlmcCfg(field_cfg(run_seed, sigma2, ell, M),
+    return MlmcCfg(field_cfg(run_seed, sigma2, ell, M, cov),
                    mg_cfg(nu1, nu2, rtol, max_cycles, precision, smoother, accel), int(n0), int(max_batch), sp)
 
 

@@ -1,6 +1,7 @@
 // extern "C" entry points of include/mlmc.h, the batched MLMC level pipeline, and
 // error reporting.
 #include <math.h>
+#include <stddef.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -78,13 +79,18 @@ static int check_mg(const mg_cfg* c) {
   return MLMC_OK;
 }
 
+// `cov` sits in what was the struct's tail padding: the size and every other offset are
+// those of the four-field layout, so zero-initialised callers get the Gaussian covariance.
+static_assert(sizeof(mlmc_field_cfg) == 32 && offsetof(mlmc_field_cfg, cov) == 28, "mlmc_field_cfg layout");
+
 static int check_field(const mlmc_field_cfg* c) {
   if (!c) {
     set_error("mlmc_field_cfg is NULL");
     return MLMC_ERR_INVALID;
   }
-  if (c->M < 1 || c->M > 65536 || !(c->ell > 0.0) || !(c->sigma2 >= 0.0) || isinf(c->sigma2) || isinf(c->ell)) {
-    set_error("field cfg invalid: M=%d ell=%g sigma2=%g", c->M, c->ell, c->sigma2);
+  if (c->M < 1 || c->M > 65536 || !(c->ell > 0.0) || !(c->sigma2 >= 0.0) || isinf(c->sigma2) || isinf(c->ell) ||
+      (c->cov != MLMC_COV_GAUSS && c->cov != MLMC_COV_EXP)) {
+    set_error("field cfg invalid: M=%d ell=%g sigma2=%g cov=%d", c->M, c->ell, c->sigma2, c->cov);
     return MLMC_ERR_INVALID;
   }
   return MLMC_OK;

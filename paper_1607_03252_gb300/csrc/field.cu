@@ -41,7 +41,9 @@ __device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
 }
 
 // One thread per (sample, feature): w (B x M x 3), b (B x M).
-__global__ void k_features(const uint64_t* __restrict__ ids, int B, int M, uint64_t seed, double inv_ell,
+// cov = MLMC_COV_EXP divides the Gaussian vector by |g4| (fourth Box-Muller normal), which
+// turns N(0, I/ell^2) into the multivariate Cauchy law of the exponential covariance.
+__global__ void k_features(const uint64_t* __restrict__ ids, int B, int M, uint64_t seed, double ell, int cov,
                            double* __restrict__ w, double* __restrict__ bph) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)B * M) return;
@@ -66,9 +68,11 @@ __global__ void k_features(const uint64_t* __restrict__ ids, int B, int M, uint6
   const double g1 = r1 * cos(two_pi * U2);
   const double g2 = r1 * sin(two_pi * U2);
   const double g3 = r2 * cos(two_pi * U4);
-  w[3 * t + 0] = g1 * inv_ell;
-  w[3 * t + 1] = g2 * inv_ell;
-  w[3 * t + 2] = g3 * inv_ell;
+  double scale = 1.0 / ell;
+  if (cov == MLMC_COV_EXP) scale = 1.0 / (ell * fabs(r2 * sin(two_pi * U4)));
+  w[3 * t + 0] = g1 * scale;
+  w[3 * t + 1] = g2 * scale;
+  w[3 * t + 2] = g3 * scale;
   bph[t] = two_pi * U5;
 }
 
@@ -357,7 +361,7 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
   const size_t nf = (size_t)B * cfg.M;
   MLMC_LAUNCH("features", nf * 40.0, nf * 200.0, st,
               (k_features<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(ids_dev, B, cfg.M, cfg.run_seed,
-                                                                          1.0 / cfg.ell, w, bph)));
+                                                                          cfg.ell, cfg.cov, w, bph)));
   const double h = 1.0 / (double)(n - 1);
   const size_t nt = (size_t)B * 3 * cfg.M * n;
   MLMC_LAUNCH("phasors", nt * 16.0, nt * 40.0, st,
