@@ -3,12 +3,15 @@
   - Chan et al.'s pairwise merge of per-level (N, mean, M2) records, used to combine the
     level statistics of independent replicas (one per GPU) into the estimator's;
   - the sample sizes of Eq. 11 / Eq. 15 (Sec. 2.2-2.3) and the eps split of Eq. 6;
-  - the MLMC estimate of Eq. 8 and its sampling variance (Eq. 10).
+  - the MLMC estimate of Eq. 8 and its sampling variance (Eq. 10);
+  - the decay rates alpha, beta, gamma of Eqs. 12 and 14 on a hierarchy with M_l ~ 8^l.
 """
 from __future__ import annotations
 
 import math
 from typing import Iterable, Sequence
+
+import numpy as np
 
 
 def chan_merge(records: Iterable[Sequence[float]]):
@@ -45,3 +48,13 @@ def sample_sizes(V: Sequence[float], C: Sequence[float], eps_s: float, minimum: 
 def mlmc_estimate(means: Sequence[float], variances: Sequence[float], N: Sequence[float]):
     """(Q-hat^ML = sum of level means (Eq. 8), its sampling variance sum V_l / N_l (Eq. 10))."""
     return math.fsum(means), math.fsum(v / n for v, n in zip(variances, N))
+
+
+def fit_rate(levels: Sequence[int], values: Sequence[float]):
+    """a in |value_l| ~ c 8^(-a l): minus the slope of the degree-1 least-squares fit of
+    log_8 |value| against l; None with fewer than two distinct levels."""
+    if len(set(levels)) < 2 or any(v == 0 for v in values):
+        return None
+    slope = np.polyfit(np.asarray(levels, dtype=np.float64), np.log(np.abs(np.asarray(values, dtype=np.float64)))
+                       / math.log(8.0), 1)[0]
+    return -float(slope)
