@@ -26,6 +26,11 @@ Parity status (each item's pin lives in tests/test_oracle_*.py):
                        adjoint and exactness identities, and h-independent convergence;
   QoI                  pinned by trapezoid exactness on multilinear functions;
   statistics           pinned by math.fsum and a hand-evaluated Eq. 11 case;
+  SPDE sampler         pinned by the FP32 log's error bound, the normals' law, an
+                       independent aggregation of the octant noise (fine and coupled
+                       coarse cells), the operator by hand, the exact solve against the
+                       operator, the sampled covariance against the discrete model's
+                       exact covariance, and that model against Whittle's closed form;
   rate fit             pinned by exact geometric data and an independent polynomial fit;
   Algorithm 2          pinned by hand-worked level counts of synthetic samplers (the
                        eps_b / eps and alpha choices each change them) and by the

@@ -20,6 +20,7 @@ ORC_ERR_NOT_CONVERGED = -3
 # covariance families of the field (Gaussian; exponential, Sec. 3.2)
 COV_GAUSS = 0
 COV_EXP = 1
+COV_SPDE = 2
 
 _lib = None
 _lock = threading.Lock()
@@ -60,14 +61,14 @@ def lib():
             L.orc_logk_point.restype = ctypes.c_double
             L.orc_field.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp]
-            L.orc_apply.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int]
-            L.orc_residual.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int]
-            L.orc_rbgs_sweep.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int]
+            L.orc_apply.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double]
+            L.orc_residual.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double]
+            L.orc_rbgs_sweep.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double]
             L.orc_restrict_fw.argtypes = [ctypes.c_int, _dp, _dp]
             L.orc_prolong_add.argtypes = [ctypes.c_int, _dp, _dp]
-            L.orc_coarse_solve.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int]
+            L.orc_coarse_solve.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double]
             L.orc_mg_solve.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                       ctypes.c_int, ctypes.c_int, _ip, _dp, _dp]
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_double, _ip, _dp, _dp]
             L.orc_qoi.argtypes = [ctypes.c_int, _dp]
             L.orc_qoi.restype = ctypes.c_double
             L.orc_sample.argtypes = [ctypes.POINTER(OrcCfg), ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
@@ -75,8 +76,15 @@ def lib():
             L.orc_level_batch.argtypes = [ctypes.POINTER(OrcCfg), ctypes.c_int, ctypes.c_int, _u64p, ctypes.c_int,
                                           _dp, _dp, _dp, _ip, _ip, ctypes.c_int]
             L.orc_max_threads.restype = ctypes.c_int
-            L.orc_assemble_csr.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _dp]
-            L.orc_assemble_csr.restype = ctypes.c_int
+            L.orc_log_series.argtypes = [ctypes.c_float]
+            L.orc_log_series.restype = ctypes.c_float
+            L.orc_octant_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+            L.orc_octant_normal.restype = ctypes.c_float
+            L.orc_spde_noise.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _dp]
+            L.orc_spde_apply.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
+            L.orc_spde_solve.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
+            L.orc_spde_field.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_int, _dp]
             _lib = L
     return _lib
 
@@ -136,32 +144,32 @@ def field(run_seed, sample_id, M, sigma2, ell, n, cov=COV_GAUSS):
     return k
 
 
-def apply(k, u, mixed=False):
+def apply(k, u, mixed=False, c=0.0):
     n = k.shape[0]
     k = _grid(k, n)
     u = _grid(u, n)
     out = np.zeros_like(k)
-    lib().orc_apply(n, _d(k), _d(u), _d(out), int(mixed))
+    lib().orc_apply(n, _d(k), _d(u), _d(out), int(mixed), float(c))
     return out
 
 
-def residual(k, f, u, mixed=False):
+def residual(k, f, u, mixed=False, c=0.0):
     n = k.shape[0]
     k = _grid(k, n)
     u = _grid(u, n)
     fp = None if f is None else _grid(f, n)
     r = np.zeros_like(k)
-    lib().orc_residual(n, _d(k), None if fp is None else _d(fp), _d(u), _d(r), int(mixed))
+    lib().orc_residual(n, _d(k), None if fp is None else _d(fp), _d(u), _d(r), int(mixed), float(c))
     return r
 
 
-def rbgs_sweep(k, f, u, mixed=False):
+def rbgs_sweep(k, f, u, mixed=False, c=0.0):
     """One red-then-black sweep; returns a new array."""
     n = k.shape[0]
     k = _grid(k, n)
     u = _grid(u, n).copy()
     fp = None if f is None else _grid(f, n)
-    lib().orc_rbgs_sweep(n, _d(k), None if fp is None else _d(fp), _d(u), int(mixed))
+    lib().orc_rbgs_sweep(n, _d(k), None if fp is None else _d(fp), _d(u), int(mixed), float(c))
     return u
 
 
@@ -183,18 +191,18 @@ def prolong_add(ec, u):
     return u
 
 
-def coarse_solve(k, f=None, mixed=False):
+def coarse_solve(k, f=None, mixed=False, c=0.0):
     n = k.shape[0]
     k = _grid(k, n)
     fp = None if f is None else _grid(f, n)
     u = np.zeros_like(k)
-    st = lib().orc_coarse_solve(n, _d(k), None if fp is None else _d(fp), _d(u), int(mixed))
+    st = lib().orc_coarse_solve(n, _d(k), None if fp is None else _d(fp), _d(u), int(mixed), float(c))
     if st != ORC_OK:
         raise ValueError("orc_coarse_solve failed: %d" % st)
     return u
 
 
-def mg_solve(k, f=None, u0=None, nu1=2, nu2=2, rtol=1e-10, max_cycles=100, mixed=False):
+def mg_solve(k, f=None, u0=None, nu1=2, nu2=2, rtol=1e-10, max_cycles=100, mixed=False, c=0.0):
     """Returns (u, status, cycles, relres, per-cycle relative residuals)."""
     n = k.shape[0]
     k = _grid(k, n)
@@ -204,7 +212,7 @@ def mg_solve(k, f=None, u0=None, nu1=2, nu2=2, rtol=1e-10, max_cycles=100, mixed
     rr = ctypes.c_double(0.0)
     hist = np.zeros(max(max_cycles, 1))
     st = lib().orc_mg_solve(n, _d(k), None if fp is None else _d(fp), _d(u), nu1, nu2, rtol, max_cycles,
-                            int(mixed), ctypes.byref(cyc), ctypes.byref(rr), _d(hist))
+                            int(mixed), float(c), ctypes.byref(cyc), ctypes.byref(rr), _d(hist))
     if st == ORC_ERR_INVALID or st == ORC_ERR_OOM:
         raise ValueError("orc_mg_solve failed: %d" % st)
     return u, st, cyc.value, rr.value, hist[: cyc.value].copy()
@@ -248,7 +256,7 @@ def max_threads():
     return lib().orc_max_threads()
 
 
-def assemble_csr(k, mixed=False):
+def assemble_csr(k, mixed=False, c=0.0):
     """scipy.sparse CSR matrix of the operator on the interior nodes (x fastest)."""
     import scipy.sparse as sp
 
@@ -259,6 +267,54 @@ def assemble_csr(k, mixed=False):
     indptr = np.zeros(N + 1, dtype=np.int32)
     indices = np.zeros(7 * N, dtype=np.int32)
     data = np.zeros(7 * N)
-    nnz = lib().orc_assemble_csr(n, _d(k), int(mixed), indptr.ctypes.data_as(_ip), indices.ctypes.data_as(_ip),
-                                 _d(data))
+    nnz = lib().orc_assemble_csr(n, _d(k), int(mixed), float(c), indptr.ctypes.data_as(_ip),
+                                 indices.ctypes.data_as(_ip), _d(data))
     return sp.csr_matrix((data[:nnz], indices[:nnz], indptr), shape=(N, N))
+
+
+# ---- SPDE field sampler (Sec. 3.2) ---------------------------------------------------
+def log_series(s):
+    """The FP32 natural logarithm the octant normals use (float in, float out)."""
+    return lib().orc_log_series(float(s))
+
+
+def octant_normal(run_seed, sample_id, octant):
+    return lib().orc_octant_normal(int(run_seed), int(sample_id), int(octant))
+
+
+def spde_noise(run_seed, sample_id, n, n_noise=None):
+    """Scaled right-hand side g = W(cell) / h on the C^3 cells (C = 2(n-1)) of level grid
+    n, shape (C, C, C) indexed [z, y, x]; the noise lives on the octants of grid n_noise."""
+    n_noise = n if n_noise is None else n_noise
+    C = 2 * (n - 1)
+    g = np.zeros((C, C, C))
+    st = lib().orc_spde_noise(int(run_seed), int(sample_id), n, n_noise, _d(g))
+    if st != ORC_OK:
+        raise ValueError("orc_spde_noise failed: %d" % st)
+    return g
+
+
+def spde_apply(Z, ch2):
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    out = np.zeros_like(Z)
+    lib().orc_spde_apply(Z.shape[0], float(ch2), _d(Z), _d(out))
+    return out
+
+
+def spde_solve(g, ch2):
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    Z = np.zeros_like(g)
+    st = lib().orc_spde_solve(g.shape[0], float(ch2), _d(g), _d(Z))
+    if st != ORC_OK:
+        raise ValueError("orc_spde_solve failed: %d" % st)
+    return Z
+
+
+def spde_field(run_seed, sample_id, sigma2, ell, n, n_noise=None):
+    """k on the n^3 grid of D from the SPDE sampler (Sec. 3.2)."""
+    n_noise = n if n_noise is None else n_noise
+    k = np.zeros((n, n, n))
+    st = lib().orc_spde_field(int(run_seed), int(sample_id), float(sigma2), float(ell), n, n_noise, _d(k))
+    if st != ORC_OK:
+        raise ValueError("orc_spde_field failed: %d" % st)
+    return k

@@ -27,6 +27,7 @@
  *             exponential sigma^2 exp(-r / ell) (the paper's covariance, Sec. 3.2) gives
  *             the 3-D multivariate Cauchy law w_m = z / (ell |chi|), z ~ N(0, I),
  *             chi ~ N(0, 1) independent (density proportional to (1 + ell^2 |w|^2)^-2);
+ *             or the SPDE sampler of Sec. 3.2 (see the SPDE section below);
  *   cycle     V(nu1, nu2) with red-black Gauss-Seidel, full weighting, trilinear
  *             prolongation, rediscretised coarse operators (k injected), exact dense
  *             Cholesky solve on the 5^3 grid; cycles repeat until ||f-Au||/||f|| <= rtol;
@@ -53,6 +54,7 @@ static const double ORC_PI = 3.14159265358979323846;
 /* covariance families of the field */
 #define ORC_COV_GAUSS 0
 #define ORC_COV_EXP 1
+#define ORC_COV_SPDE 2
 
 /* ------------------------------------------------------------------------------------
  * Philox4x32-10 and Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
@@ -211,8 +213,10 @@ static int is_interior(int n, int i, int j, int k) {
   return i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1;
 }
 
-/* (A u)_p for an interior node p; boundary u is taken as zero. */
-static double apply_at(int n, const double* kn, const double* u, int i, int j, int k, int mixed) {
+/* (A u)_p for an interior node p; boundary u is taken as zero. c >= 0 is the reaction
+ * coefficient of -div(k grad u) + c u (0 for the model problem; kappa^2 for the SPDE
+ * field sampler of Sec. 3.2). */
+static double apply_at(int n, const double* kn, const double* u, int i, int j, int k, int mixed, double c) {
   static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
   double h = 1.0 / (double)(n - 1);
   size_t p = IDX(n, i, j, k);
@@ -224,23 +228,23 @@ static double apply_at(int n, const double* kn, const double* u, int i, int j, i
     double uq = is_interior(n, qi, qj, qk) ? u[q] : 0.0;
     s += kface(kn[p], kn[q], mixed) * (up - uq);
   }
-  return s / (h * h);
+  return s / (h * h) + c * up;
 }
 
 /* A u on all interior nodes; boundary entries of Au are set to zero. */
-void orc_apply(int n, const double* kn, const double* u, double* Au, int mixed) {
+void orc_apply(int n, const double* kn, const double* u, double* Au, int mixed, double c) {
   for (int k = 0; k < n; ++k)
     for (int j = 0; j < n; ++j)
       for (int i = 0; i < n; ++i)
-        Au[IDX(n, i, j, k)] = is_interior(n, i, j, k) ? apply_at(n, kn, u, i, j, k, mixed) : 0.0;
+        Au[IDX(n, i, j, k)] = is_interior(n, i, j, k) ? apply_at(n, kn, u, i, j, k, mixed, c) : 0.0;
 }
 
 /* The same operator as a sparse matrix over the interior nodes, numbered x fastest
  * (CSR; at most 7 entries per row, column indices ascending): row p holds
- * -h^-2 k_pq for each interior neighbour q and h^-2 sum_q k_pq on the diagonal.
+ * -h^-2 k_pq for each interior neighbour q and h^-2 sum_q k_pq + c on the diagonal.
  * indptr has m^3 + 1 entries, indices / data at least 7 m^3 (m = n - 2).
  * Returns the number of stored entries. */
-int orc_assemble_csr(int n, const double* kn, int mixed, int* indptr, int* indices, double* data) {
+int orc_assemble_csr(int n, const double* kn, int mixed, double c, int* indptr, int* indices, double* data) {
   static const int off[6][3] = {{0, 0, -1}, {0, -1, 0}, {-1, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
   int m = n - 2, nnz = 0, row = 0;
   double h = 1.0 / (double)(n - 1);
@@ -263,27 +267,27 @@ int orc_assemble_csr(int n, const double* kn, int mixed, int* indptr, int* indic
             ++nnz;
           }
         }
-        data[diag_pos] = diag / (h * h);
+        data[diag_pos] = diag / (h * h) + c;
       }
   indptr[row] = nnz;
   return nnz;
 }
 
 /* r = f - A u on interior nodes, zero on the boundary. f == NULL means f = 1. */
-void orc_residual(int n, const double* kn, const double* f, const double* u, double* r, int mixed) {
+void orc_residual(int n, const double* kn, const double* f, const double* u, double* r, int mixed, double c) {
   for (int k = 0; k < n; ++k)
     for (int j = 0; j < n; ++j)
       for (int i = 0; i < n; ++i) {
         size_t p = IDX(n, i, j, k);
         if (!is_interior(n, i, j, k)) { r[p] = 0.0; continue; }
         double fp = f ? f[p] : 1.0;
-        r[p] = fp - apply_at(n, kn, u, i, j, k, mixed);
+        r[p] = fp - apply_at(n, kn, u, i, j, k, mixed, c);
       }
 }
 
 /* One red-black Gauss-Seidel sweep: red nodes ((i+j+k) even) first, then black.
- * u_p <- (h^2 f_p + sum_q k_pq u_q) / sum_q k_pq with boundary u_q = 0. */
-void orc_rbgs_sweep(int n, const double* kn, const double* f, double* u, int mixed) {
+ * u_p <- (h^2 f_p + sum_q k_pq u_q) / (sum_q k_pq + c h^2) with boundary u_q = 0. */
+void orc_rbgs_sweep(int n, const double* kn, const double* f, double* u, int mixed, double c) {
   static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
   double h = 1.0 / (double)(n - 1);
   for (int colour = 0; colour < 2; ++colour)
@@ -300,7 +304,7 @@ void orc_rbgs_sweep(int n, const double* kn, const double* f, double* u, int mix
             num += kf * (is_interior(n, qi, qj, qk) ? u[q] : 0.0);
             den += kf;
           }
-          u[p] = num / den;
+          u[p] = num / (den + c * h * h);
         }
 }
 
@@ -348,7 +352,7 @@ void orc_prolong_add(int nf, const double* ec, double* u) {
  * (column by column, by applying A to unit vectors), factor A = L L^T by Cholesky,
  * and solve by forward and backward substitution.
  * ---------------------------------------------------------------------------------- */
-int orc_coarse_solve(int n, const double* kn, const double* f, double* u, int mixed) {
+int orc_coarse_solve(int n, const double* kn, const double* f, double* u, int mixed, double c) {
   int m = n - 2, N = m * m * m;
   size_t n3 = (size_t)n * n * n;
   double* A = (double*)calloc((size_t)N * N, sizeof(double));
@@ -357,14 +361,14 @@ int orc_coarse_solve(int n, const double* kn, const double* f, double* u, int mi
   double* y = (double*)calloc((size_t)N, sizeof(double));
   int status = ORC_OK;
   if (!A || !e || !Ae || !y) { status = ORC_ERR_OOM; goto done; }
-  for (int c = 0; c < N; ++c) {
-    int ci = 1 + c % m, cj = 1 + (c / m) % m, ck = 1 + c / (m * m);
+  for (int col = 0; col < N; ++col) {
+    int ci = 1 + col % m, cj = 1 + (col / m) % m, ck = 1 + col / (m * m);
     memset(e, 0, n3 * sizeof(double));
     e[IDX(n, ci, cj, ck)] = 1.0;
-    orc_apply(n, kn, e, Ae, mixed);
+    orc_apply(n, kn, e, Ae, mixed, c);
     for (int r = 0; r < N; ++r) {
       int ri = 1 + r % m, rj = 1 + (r / m) % m, rk = 1 + r / (m * m);
-      A[(size_t)r * N + c] = Ae[IDX(n, ri, rj, rk)];
+      A[(size_t)r * N + col] = Ae[IDX(n, ri, rj, rk)];
     }
   }
   /* Cholesky, lower triangle in place */
@@ -465,18 +469,18 @@ static int hier_build(orc_hierarchy* H, int n, const double* k, const double* f,
 }
 
 /* One V(nu1, nu2) cycle on grid l of the hierarchy (u[l] is updated in place). */
-static int vcycle(orc_hierarchy* H, int l, int nu1, int nu2, int mixed) {
+static int vcycle(orc_hierarchy* H, int l, int nu1, int nu2, int mixed, double c) {
   int n = H->n[l];
-  if (l == H->levels - 1) return orc_coarse_solve(n, H->k[l], H->f[l], H->u[l], mixed);
-  for (int s = 0; s < nu1; ++s) orc_rbgs_sweep(n, H->k[l], H->f[l], H->u[l], mixed);
-  orc_residual(n, H->k[l], H->f[l], H->u[l], H->r[l], mixed);
+  if (l == H->levels - 1) return orc_coarse_solve(n, H->k[l], H->f[l], H->u[l], mixed, c);
+  for (int s = 0; s < nu1; ++s) orc_rbgs_sweep(n, H->k[l], H->f[l], H->u[l], mixed, c);
+  orc_residual(n, H->k[l], H->f[l], H->u[l], H->r[l], mixed, c);
   orc_restrict_fw(n, H->r[l], H->f[l + 1]);
   size_t nc3 = (size_t)H->n[l + 1] * H->n[l + 1] * H->n[l + 1];
   memset(H->u[l + 1], 0, nc3 * sizeof(double));
-  int st = vcycle(H, l + 1, nu1, nu2, mixed);
+  int st = vcycle(H, l + 1, nu1, nu2, mixed, c);
   if (st != ORC_OK) return st;
   orc_prolong_add(n, H->u[l + 1], H->u[l]);
-  for (int s = 0; s < nu2; ++s) orc_rbgs_sweep(n, H->k[l], H->f[l], H->u[l], mixed);
+  for (int s = 0; s < nu2; ++s) orc_rbgs_sweep(n, H->k[l], H->f[l], H->u[l], mixed, c);
   return ORC_OK;
 }
 
@@ -498,8 +502,8 @@ static double interior_norm(int n, const double* v) {
  * max_cycles cycles and returns ORC_OK.
  */
 int orc_mg_solve(int n, const double* k, const double* f, double* u, int nu1, int nu2, double rtol,
-                 int max_cycles, int mixed, int* cycles_out, double* relres_out, double* res_hist) {
-  if (!valid_n(n) || nu1 < 0 || nu2 < 0 || max_cycles < 0) return ORC_ERR_INVALID;
+                 int max_cycles, int mixed, double c, int* cycles_out, double* relres_out, double* res_hist) {
+  if (!valid_n(n) || nu1 < 0 || nu2 < 0 || max_cycles < 0 || !(c >= 0.0)) return ORC_ERR_INVALID;
   size_t n3 = (size_t)n * n * n;
   for (int kz = 0; kz < n; ++kz)
     for (int jy = 0; jy < n; ++jy)
@@ -517,23 +521,23 @@ int orc_mg_solve(int n, const double* k, const double* f, double* u, int nu1, in
   const double* fe = f ? f : fone;
   double fnorm = interior_norm(n, fe);
   double relres = 0.0;
-  orc_residual(n, k, f, u, H.r[0], mixed);
+  orc_residual(n, k, f, u, H.r[0], mixed, c);
   relres = interior_norm(n, H.r[0]) / fnorm;
-  int c = 0;
+  int cyc = 0;
   int status = ORC_OK;
   if (rtol > 0.0 && relres <= rtol) goto finish;
-  for (c = 0; c < max_cycles;) {
-    st = vcycle(&H, 0, nu1, nu2, mixed);
+  for (cyc = 0; cyc < max_cycles;) {
+    st = vcycle(&H, 0, nu1, nu2, mixed, c);
     if (st != ORC_OK) { status = st; goto finish; }
-    ++c;
-    orc_residual(n, k, f, u, H.r[0], mixed);
+    ++cyc;
+    orc_residual(n, k, f, u, H.r[0], mixed, c);
     relres = interior_norm(n, H.r[0]) / fnorm;
-    if (res_hist) res_hist[c - 1] = relres;
+    if (res_hist) res_hist[cyc - 1] = relres;
     if (rtol > 0.0 && relres <= rtol) break;
   }
   if (rtol > 0.0 && relres > rtol) status = ORC_ERR_NOT_CONVERGED;
 finish:
-  if (cycles_out) *cycles_out = c;
+  if (cycles_out) *cycles_out = cyc;
   if (relres_out) *relres_out = relres;
   free(fone);
   hier_free(&H);
@@ -558,6 +562,221 @@ double orc_qoi(int n, const double* u) {
 }
 
 /* ------------------------------------------------------------------------------------
+ * SPDE field sampler (Sec. 3.2): Z solves (kappa^2 - Laplace) Z = W, W Gaussian white
+ * noise, on a box around D with homogeneous Neumann data. In R^3 the solution has the
+ * covariance (8 pi kappa)^-1 exp(-kappa r) (the Green's function exp(-kappa r)/(4 pi r)
+ * convolved with itself; Whittle), so kappa = 1 / lambda gives the exponential
+ * covariance of the paper's field with correlation length lambda = ell, and
+ * log k = sqrt(8 pi kappa sigma^2) Z has variance sigma^2 and covariance
+ * sigma^2 exp(-r / lambda). (The paper's lambda = 2 / kappa is the "practical range"
+ * sqrt(8 nu) / kappa at nu = 1/2, at odds with its own covariance formula; this file
+ * follows the covariance formula.)
+ *
+ * Discretisation (readings of this library; the paper uses P1 finite elements):
+ *   - cell-centred finite volumes on a box around D: for the level grid n of D (spacing
+ *     h = 1/(n-1)) the box (-1/2 - h/2, 3/2 - h/2)^3 of C = 2(n-1) cells of side h per
+ *     axis, cell i centred at -1/2 + i h, so D's node j is the centre of cell
+ *     j + (n-1)/2 (margin 1/2 around D; the paper's box is (-1, 2)^3);
+ *   - cell p, scaled by 1/h: (kappa^2 h^2 + n_p) Z_p - sum_q Z_q = W(cell p) / h, the
+ *     sum over the n_p face neighbours inside the box (zero flux through the box);
+ *   - W(cell) is exact white noise integrated over the cell: the cells of the pair's
+ *     fine grid n_f (spacing h_f) and of its coarse grid (2 h_f) are unions of octants,
+ *     cubes of side h_f/2 tiling (-1/2 - h_f, 3/2 - h_f/2)^3 (4(n_f - 1) + 1 per axis),
+ *     each carrying (h_f/2)^(3/2) xi with one standard normal xi per octant, so both
+ *     grids of one sample see the same realisation of W.
+ *
+ * The normals: Marsaglia's polar method (Marsaglia and Bray 1964) on Philox4x32-10
+ * words, in FP32 with only correctly rounded operations (+, *, /, sqrt, fma) and the
+ * natural logarithm below, so that any IEEE implementation reproduces them exactly.
+ * ---------------------------------------------------------------------------------- */
+
+/* ln s for normal s > 0 in FP32: s = m 2^e with m in [sqrt(1/2), sqrt(2)), ln m =
+ * 2 atanh(t) = 2 t (1 + t^2/3 + t^4/5 + ... + t^10/11), t = (m - 1)/(m + 1), |t| < 0.172
+ * (the series of ln((1+t)/(1-t))), and e ln 2 with ln 2 split into a 16-bit head and a
+ * tail (Cody and Waite), every step rounded once. */
+float orc_log_series(float s) {
+  uint32_t b;
+  memcpy(&b, &s, sizeof b);
+  int e = (int)((b >> 23) & 0xffu) - 127;
+  uint32_t mb = (b & 0x7fffffu) | 0x3f800000u;
+  float m;
+  memcpy(&m, &mb, sizeof m);
+  if (m > 0x1.6a09e6p+0f) {
+    m = 0.5f * m;
+    e += 1;
+  }
+  float t = (m - 1.0f) / (m + 1.0f);
+  float t2 = t * t;
+  float p = fmaf(t2, 0x1.745d18p-4f, 0x1.c71c72p-4f);
+  p = fmaf(t2, p, 0x1.24924ap-3f);
+  p = fmaf(t2, p, 0x1.99999ap-3f);
+  p = fmaf(t2, p, 0x1.555556p-2f);
+  p = fmaf(t2, p, 1.0f);
+  float lm = (2.0f * t) * p;
+  float fe = (float)e;
+  return fmaf(fe, 0x1.62e400p-1f, fmaf(fe, 0x1.7f7d1cp-20f, lm));
+}
+
+/* Standard normal of octant `oct` of sample `sample_id`: attempt a = 0..31 takes the
+ * word pair (2(a&1), 2(a&1)+1) of Philox4x32-10 with key (seed lo, seed hi) and counter
+ * (id lo, id hi, oct lo, 0x5D000000 | (a>>1) << 8 | oct >> 32); a word w gives
+ * U = ((w >> 8) - 2^23 + 1/2) 2^-23 in (-1, 1); the first pair with 0 < s = U1^2 + U2^2
+ * < 1 returns U1 sqrt(-2 ln s / s); none in 32 attempts (probability 5e-22) returns 0. */
+float orc_octant_normal(uint64_t run_seed, uint64_t sample_id, uint64_t oct) {
+  uint32_t key[2] = {(uint32_t)run_seed, (uint32_t)(run_seed >> 32)};
+  for (int call = 0; call < 16; ++call) {
+    uint32_t ctr[4] = {(uint32_t)sample_id, (uint32_t)(sample_id >> 32), (uint32_t)oct,
+                       0x5D000000u | ((uint32_t)call << 8) | (uint32_t)(oct >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    for (int half = 0; half < 2; ++half) {
+      float u1 = ((float)((int32_t)(w[2 * half] >> 8) - 8388608) + 0.5f) * 0x1p-23f;
+      float u2 = ((float)((int32_t)(w[2 * half + 1] >> 8) - 8388608) + 0.5f) * 0x1p-23f;
+      float t = u2 * u2;
+      float sq = fmaf(u1, u1, t);
+      if (sq > 0.0f && sq < 1.0f) {
+        float q = (-2.0f * orc_log_series(sq)) / sq;
+        return u1 * sqrtf(q);
+      }
+    }
+  }
+  return 0.0f;
+}
+
+static int spde_sizes_ok(int n, int n_noise) {
+  return valid_n(n) && (n_noise == n || n_noise == 2 * n - 1) && n_noise <= 1025;
+}
+
+/* Scaled right-hand side g_p = W(cell p) / h on the C^3 cells (C = 2(n-1), x fastest)
+ * of level grid n for the pair whose fine grid is n_noise (n, or 2n - 1 for the coarse
+ * grid of a pair): the octants of cell i along an axis are 2 r i + 2 - r .. 2 r i + 1 + r
+ * with r = h / h_f in {1, 2}; sums taken z, y, x outermost to
+ * innermost. */
+int orc_spde_noise(uint64_t run_seed, uint64_t sample_id, int n, int n_noise, double* g) {
+  if (!spde_sizes_ok(n, n_noise)) return ORC_ERR_INVALID;
+  int C = 2 * (n - 1);
+  long r = (long)((n_noise - 1) / (n - 1));
+  uint64_t Mo = 4 * (uint64_t)(n_noise - 1) + 1;
+  double h = 1.0 / (double)(n - 1), hf = 1.0 / (double)(n_noise - 1);
+  double v = 0.5 * hf;
+  double scale = sqrt(v * v * v) / h;
+  for (long K = 0; K < C; ++K)
+    for (long J = 0; J < C; ++J)
+      for (long I = 0; I < C; ++I) {
+        long az0 = 2 * r * K + 2 - r, ay0 = 2 * r * J + 2 - r, ax0 = 2 * r * I + 2 - r;
+        double sum = 0.0;
+        for (long az = az0; az < az0 + 2 * r; ++az)
+          for (long ay = ay0; ay < ay0 + 2 * r; ++ay)
+            for (long ax = ax0; ax < ax0 + 2 * r; ++ax)
+              sum += (double)orc_octant_normal(run_seed, sample_id,
+                                               ((uint64_t)az * Mo + (uint64_t)ay) * Mo + (uint64_t)ax);
+        g[((size_t)K * C + (size_t)J) * C + (size_t)I] = scale * sum;
+      }
+  return ORC_OK;
+}
+
+/* The scaled SPDE operator on the C^3 cells: (A Z)_p = (c h^2 + n_p) Z_p - sum_q Z_q. */
+void orc_spde_apply(int C, double ch2, const double* Z, double* AZ) {
+  for (int k = 0; k < C; ++k)
+    for (int j = 0; j < C; ++j)
+      for (int i = 0; i < C; ++i) {
+        size_t p = ((size_t)k * C + j) * C + i;
+        double s = 0.0;
+        int np = 0;
+        if (i > 0) { s += Z[p - 1]; ++np; }
+        if (i < C - 1) { s += Z[p + 1]; ++np; }
+        if (j > 0) { s += Z[p - C]; ++np; }
+        if (j < C - 1) { s += Z[p + C]; ++np; }
+        if (k > 0) { s += Z[p - (size_t)C * C]; ++np; }
+        if (k < C - 1) { s += Z[p + (size_t)C * C]; ++np; }
+        AZ[p] = (ch2 + (double)np) * Z[p] - s;
+      }
+}
+
+/* Transform along one axis of a C^3 array: out[.., a, ..] = sum_b M[a][b] in[.., b, ..],
+ * axis 0 = x (stride 1), 1 = y (stride C), 2 = z (stride C^2). */
+static void axis_transform(int C, const double* M, const double* in, double* out, int axis) {
+  size_t st = axis == 0 ? 1 : (axis == 1 ? (size_t)C : (size_t)C * C);
+  for (int k = 0; k < C; ++k)
+    for (int j = 0; j < C; ++j)
+      for (int i = 0; i < C; ++i) {
+        int idx[3] = {i, j, k};
+        size_t p = ((size_t)k * C + j) * C + i;
+        size_t base = p - (size_t)idx[axis] * st;
+        double s = 0.0;
+        for (int b = 0; b < C; ++b) s += M[(size_t)idx[axis] * C + b] * in[base + (size_t)b * st];
+        out[p] = s;
+      }
+}
+
+/* Exact solve of A Z = g by the eigenvectors of the one-dimensional zero-flux
+ * second-difference matrix (the orthonormal DCT-II basis phi_a(i) = w_a cos(pi a (i +
+ * 1/2) / C), eigenvalue 4 sin^2(pi a / (2 C))): transform along the three axes, divide
+ * by c h^2 + the three eigenvalues, transform back. */
+int orc_spde_solve(int C, double ch2, const double* g, double* Z) {
+  if (C < 1 || !(ch2 > 0.0)) return ORC_ERR_INVALID;
+  size_t C3 = (size_t)C * C * C;
+  double* P = (double*)malloc((size_t)C * C * sizeof(double));   /* P[a][i] = phi_a(i) */
+  double* Pt = (double*)malloc((size_t)C * C * sizeof(double));  /* transpose */
+  double* lam = (double*)malloc((size_t)C * sizeof(double));
+  double* t1 = (double*)malloc(C3 * sizeof(double));
+  double* t2 = (double*)malloc(C3 * sizeof(double));
+  int st = ORC_OK;
+  if (!P || !Pt || !lam || !t1 || !t2) { st = ORC_ERR_OOM; goto done; }
+  for (int a = 0; a < C; ++a) {
+    double w = a == 0 ? sqrt(1.0 / C) : sqrt(2.0 / C);
+    double sn = sin(ORC_PI * a / (2.0 * C));
+    lam[a] = 4.0 * sn * sn;
+    for (int i = 0; i < C; ++i) {
+      P[(size_t)a * C + i] = w * cos(ORC_PI * a * (i + 0.5) / C);
+      Pt[(size_t)i * C + a] = P[(size_t)a * C + i];
+    }
+  }
+  axis_transform(C, P, g, t1, 0);
+  axis_transform(C, P, t1, t2, 1);
+  axis_transform(C, P, t2, t1, 2);
+  for (int k = 0; k < C; ++k)
+    for (int j = 0; j < C; ++j)
+      for (int i = 0; i < C; ++i) t1[((size_t)k * C + j) * C + i] /= ch2 + lam[i] + lam[j] + lam[k];
+  axis_transform(C, Pt, t1, t2, 0);
+  axis_transform(C, Pt, t2, t1, 1);
+  axis_transform(C, Pt, t1, Z, 2);
+done:
+  free(P); free(Pt); free(lam); free(t1); free(t2);
+  return st;
+}
+
+/* k = exp(log k) at the n^3 nodes of D for the SPDE field: the noise of orc_spde_noise,
+ * the exact solve with kappa = 1 / lambda, log k = sqrt(8 pi kappa sigma2) Z at the
+ * cells centred on D's nodes. */
+int orc_spde_field(uint64_t run_seed, uint64_t sample_id, double sigma2, double lambda, int n, int n_noise,
+                   double* k) {
+  if (!spde_sizes_ok(n, n_noise) || !(lambda > 0.0) || !(sigma2 >= 0.0)) return ORC_ERR_INVALID;
+  int C = 2 * (n - 1), off = (n - 1) / 2;
+  size_t C3 = (size_t)C * C * C;
+  double* g = (double*)malloc(C3 * sizeof(double));
+  double* Z = (double*)malloc(C3 * sizeof(double));
+  int st = ORC_OK;
+  if (!g || !Z) { st = ORC_ERR_OOM; goto done; }
+  st = orc_spde_noise(run_seed, sample_id, n, n_noise, g);
+  if (st != ORC_OK) goto done;
+  {
+    double h = 1.0 / (double)(n - 1), kappa = 1.0 / lambda;
+    st = orc_spde_solve(C, kappa * kappa * h * h, g, Z);
+    if (st != ORC_OK) goto done;
+    double a = sqrt(8.0 * ORC_PI * kappa * sigma2);
+    for (int kz = 0; kz < n; ++kz)
+      for (int jy = 0; jy < n; ++jy)
+        for (int ix = 0; ix < n; ++ix)
+          k[IDX(n, ix, jy, kz)] = exp(a * Z[((size_t)(kz + off) * C + (size_t)(jy + off)) * C + (size_t)(ix + off)]);
+  }
+done:
+  free(g);
+  free(Z);
+  return st;
+}
+
+/* ------------------------------------------------------------------------------------
  * One MLMC sample (Algorithm 1, steps 1.a.i-ii): set up the coefficient of the
  * realisation `sample_id` on the fine grid n_fine and (if n_coarse > 0) on the
  * coarse grid n_coarse, solve both with f = 1, and return Q on each grid.
@@ -572,18 +791,23 @@ typedef struct {
   double rtol;
   int max_cycles;
   int mixed;
-  int cov; /* ORC_COV_GAUSS or ORC_COV_EXP */
+  int cov; /* ORC_COV_GAUSS, ORC_COV_EXP or ORC_COV_SPDE */
 } orc_cfg;
 
-static int solve_q(const orc_cfg* c, uint64_t sample_id, int n, double* Q, int* cycles) {
+/* n_noise: the grid of the pair's fine solve (the SPDE white noise lives on its octants). */
+static int solve_q(const orc_cfg* c, uint64_t sample_id, int n, int n_noise, double* Q, int* cycles) {
   size_t n3 = (size_t)n * n * n;
   double* k = (double*)malloc(n3 * sizeof(double));
   double* u = (double*)calloc(n3, sizeof(double));
   if (!k || !u) { free(k); free(u); return ORC_ERR_OOM; }
-  int st = orc_field(c->run_seed, sample_id, c->M, sqrt(c->sigma2), c->ell, c->cov, n, k);
+  int st;
+  if (c->cov == ORC_COV_SPDE)
+    st = orc_spde_field(c->run_seed, sample_id, c->sigma2, c->ell, n, n_noise, k);
+  else
+    st = orc_field(c->run_seed, sample_id, c->M, sqrt(c->sigma2), c->ell, c->cov, n, k);
   if (st == ORC_OK) {
     double relres;
-    st = orc_mg_solve(n, k, NULL, u, c->nu1, c->nu2, c->rtol, c->max_cycles, c->mixed, cycles, &relres, NULL);
+    st = orc_mg_solve(n, k, NULL, u, c->nu1, c->nu2, c->rtol, c->max_cycles, c->mixed, 0.0, cycles, &relres, NULL);
     *Q = orc_qoi(n, u);
   }
   free(k);
@@ -593,11 +817,11 @@ static int solve_q(const orc_cfg* c, uint64_t sample_id, int n, double* Q, int* 
 
 int orc_sample(const orc_cfg* c, int n_fine, int n_coarse, uint64_t sample_id, double* Qf, double* Qc,
                int* cycles_f, int* cycles_c) {
-  int st = solve_q(c, sample_id, n_fine, Qf, cycles_f);
+  int st = solve_q(c, sample_id, n_fine, n_fine, Qf, cycles_f);
   if (st != ORC_OK) return st;
   *Qc = 0.0;
   *cycles_c = 0;
-  if (n_coarse > 0) st = solve_q(c, sample_id, n_coarse, Qc, cycles_c);
+  if (n_coarse > 0) st = solve_q(c, sample_id, n_coarse, n_fine, Qc, cycles_c);
   return st;
 }
 
