@@ -85,6 +85,8 @@ def lib():
             L.orc_spde_solve.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
             L.orc_spde_field.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_int, _dp]
+            L.orc_assemble_csr.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, _ip, _ip, _dp]
+            L.orc_assemble_csr.restype = ctypes.c_int
             _lib = L
     return _lib
 

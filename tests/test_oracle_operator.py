@@ -111,6 +111,25 @@ def test_discrete_eigenfunction_exact(orc, n):
     np.testing.assert_allclose(u[interior(n)], (f / lam)[interior(n)], rtol=1e-11, atol=1e-14)
 
 
+@pytest.mark.parametrize("c", [0.5, 40.0])
+def test_discrete_eigenfunction_with_reaction(orc, c):
+    """-Laplace u + c u: the same eigenfunction with eigenvalue lambda_h + c, through the
+    apply, the smoother, the coarse solve and the cycle."""
+    n = 17
+    X, Y, Z, h = coords(n)
+    f = np.sin(math.pi * X) * np.sin(math.pi * Y) * np.sin(math.pi * Z)
+    lam = 12.0 / h ** 2 * math.sin(math.pi * h / 2) ** 2
+    k = np.ones((n, n, n))
+    np.testing.assert_allclose(orc.apply(k, f, c=c)[interior(n)], ((lam + c) * f)[interior(n)], rtol=1e-12,
+                               atol=1e-12)
+    u, st, cyc, rr, _ = orc.mg_solve(k, f, rtol=1e-13, c=c)
+    assert st == 0
+    np.testing.assert_allclose(u[interior(n)], (f / (lam + c))[interior(n)], rtol=1e-11, atol=1e-14)
+    A = orc.assemble_csr(k, c=c)
+    np.testing.assert_allclose(A @ f[interior(n)].ravel(order="C"), ((lam + c) * f)[interior(n)].ravel(), rtol=1e-12,
+                               atol=1e-12)
+
+
 def _manufactured_errors(orc, ns, variable_k):
     errs = []
     for n in ns:
