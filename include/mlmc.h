@@ -82,6 +82,17 @@ extern "C" {
 /* ---- covariance of log k ---- */
 #define MLMC_COV_GAUSS 0 /* sigma^2 exp(-|x-y|^2 / (2 ell^2)) */
 #define MLMC_COV_EXP 1   /* sigma^2 exp(-|x-y| / ell), the paper's covariance (Sec. 3.2) */
+#define MLMC_COV_SPDE 2  /* the paper's sampler for that covariance (Sec. 3.2): log k =
+                            sqrt(8 pi kappa sigma^2) Z, (kappa^2 - Laplace) Z = W, kappa =
+                            1/ell, W white noise; cell-centred finite volumes on the
+                            zero-flux box (-1/2 - h/2, 3/2 - h/2)^3 of 2(n-1) cells of side
+                            h = 1/(n-1) per axis (D's node j at the centre of cell
+                            j + (n-1)/2); W(cell) sums one Philox normal (Marsaglia's polar
+                            method, FP32, correctly rounded steps and an atanh-series log)
+                            per octant of side h_f/2, h_f the spacing of the pair's fine
+                            grid, so both grids of a level pair share one W; each grid's
+                            system solved by cell-centred multigrid to a relative residual
+                            of 1e-12. M is not used. Grids up to 1025 nodes per axis. */
 
 /* Parameters of the lognormal random field (Sec. 3.2; Fourier-feature form above).
    A zero-initialised `cov` selects the Gaussian covariance. */
@@ -146,6 +157,18 @@ typedef struct {
  */
 int mlmc_field_eval(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n, int dtype,
                     void* k_out, void* stream);
+
+/*
+ * mlmc_field_eval_pair -- as mlmc_field_eval, for grid n as one grid of the level pair
+ * whose fine grid is n_fine (n_fine = n: the fine grid itself; n_fine = 2n - 1: the
+ * coarse grid of the pair, Algorithm 1, step 1.a.ii on the same realisation). Fourier-
+ * feature fields are functions of x, so the result does not depend on n_fine; the SPDE
+ * field of the coarse grid solves the coarse discretisation with the fine grid's white
+ * noise. Errors: as mlmc_field_eval, and MLMC_ERR_INVALID for another n_fine;
+ * MLMC_ERR_NOT_CONVERGED if an SPDE solve misses its tolerance in 60 cycles.
+ */
+int mlmc_field_eval_pair(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n, int n_fine,
+                         int dtype, void* k_out, void* stream);
 
 /*
  * mg_solve_batch -- solve A u = f for `batch` independent samples on one grid size n

@@ -31,6 +31,7 @@ MLMC_PREC_F64 = 0
 MLMC_PREC_MIXED = 1
 MLMC_COV_GAUSS = 0
 MLMC_COV_EXP = 1
+MLMC_COV_SPDE = 2
 
 _STATUS_NAMES = {
     MLMC_ERR_INVALID: "MLMC_ERR_INVALID",
@@ -132,6 +133,8 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 SIGNATURES = {
     "mlmc_field_eval": (ctypes.c_int, [ctypes.POINTER(FieldCfg), _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        _vp, _vp]),
+    "mlmc_field_eval_pair": (ctypes.c_int, [ctypes.POINTER(FieldCfg), _u64p, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "mg_solve_batch": (ctypes.c_int, [ctypes.POINTER(MgCfg), ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
                                       ctypes.POINTER(MgStats), _vp]),
     "mg_solve_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(MgCfg), ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
@@ -218,8 +221,10 @@ def mg_cfg(nu1=2, nu2=2, rtol=1e-10, max_cycles=100, precision=MLMC_PREC_F64, sm
     return MgCfg(int(nu1), int(nu2), float(rtol), int(max_cycles), int(precision), int(smoother), int(accel))
 
 
-def mlmc_field_eval(cfg: FieldCfg, sample_ids, k_out, stream=None):
-    """k_out (B, n, n, n) float64 or float32 CUDA tensor <- k of the given sample ids."""
+def mlmc_field_eval(cfg: FieldCfg, sample_ids, k_out, stream=None, n_fine=None):
+    """k_out (B, n, n, n) float64 or float32 CUDA tensor <- k of the given sample ids; with
+    n_fine (n or 2n - 1) the grid's field as a grid of the pair whose fine grid is n_fine
+    (mlmc_field_eval_pair)."""
     import torch
 
     ids = np.ascontiguousarray(np.asarray(sample_ids, dtype=np.uint64))
@@ -232,9 +237,14 @@ def mlmc_field_eval(cfg: FieldCfg, sample_ids, k_out, stream=None):
     _grid_tensor(k_out, k_out.dtype, "k_out")
     if k_out.shape[0] != len(ids):
         raise ValueError("k_out batch %d != %d ids" % (k_out.shape[0], len(ids)))
-    st = lib().mlmc_field_eval(ctypes.byref(cfg), ids.ctypes.data_as(_u64p), len(ids), k_out.shape[1], dt,
-                               ctypes.c_void_p(k_out.data_ptr()), _stream_ptr(stream))
-    _check(st, "mlmc_field_eval")
+    if n_fine is None:
+        st = lib().mlmc_field_eval(ctypes.byref(cfg), ids.ctypes.data_as(_u64p), len(ids), k_out.shape[1], dt,
+                                   ctypes.c_void_p(k_out.data_ptr()), _stream_ptr(stream))
+        _check(st, "mlmc_field_eval")
+    else:
+        st = lib().mlmc_field_eval_pair(ctypes.byref(cfg), ids.ctypes.data_as(_u64p), len(ids), k_out.shape[1],
+                                        int(n_fine), dt, ctypes.c_void_p(k_out.data_ptr()), _stream_ptr(stream))
+        _check(st, "mlmc_field_eval_pair")
 
 
 def mg_solve_batch(cfg: MgCfg, k, u, f=None, stream=None, allow_not_converged=False):

@@ -13,6 +13,7 @@
 #include "field.cuh"
 #include "mg.cuh"
 #include "level.cuh"
+#include "spde.cuh"
 #include "prof.cuh"
 #include "tune.cuh"
 
@@ -89,7 +90,7 @@ static int check_field(const mlmc_field_cfg* c) {
     return MLMC_ERR_INVALID;
   }
   if (c->M < 1 || c->M > 65536 || !(c->ell > 0.0) || !(c->sigma2 >= 0.0) || isinf(c->sigma2) || isinf(c->ell) ||
-      (c->cov != MLMC_COV_GAUSS && c->cov != MLMC_COV_EXP)) {
+      (c->cov != MLMC_COV_GAUSS && c->cov != MLMC_COV_EXP && c->cov != MLMC_COV_SPDE)) {
     set_error("field cfg invalid: M=%d ell=%g sigma2=%g cov=%d", c->M, c->ell, c->sigma2, c->cov);
     return MLMC_ERR_INVALID;
   }
@@ -153,14 +154,16 @@ __global__ void k_level_stats(const double* __restrict__ Qf, const double* __res
 }
 
 // One batch of an MLMC level: field on the fine grid, fine solve, coarse solve on the
-// same field (injection: the coarse grid's nodes are every other fine node), QoI of both.
+// same realisation, QoI of both. Fourier-feature fields: the coarse coefficient is the fine
+// one injected (the coarse grid's nodes are every other fine node). SPDE fields: each grid
+// solves its own discretisation of the SPDE with the white noise of the fine grid.
 struct LevelBatch {
-  int nf = 0, nc = 0, B = 0, M = 0, prec = 0;
-  DevBuf ids, k0, uf, uc, Q, cyc, rec, scratch;
+  int nf = 0, nc = 0, B = 0, M = 0, prec = 0, cov = 0;
+  DevBuf ids, k0, kc, uf, uc, Q, cyc, rec, scratch;
   size_t scratch_bytes = 0;
 
-  static size_t scratch_for(int B, int nf, int nc, int M, int prec, int accel) {
-    size_t s = field_scratch_bytes(B, M, nf);
+  static size_t scratch_for(int B, int nf, int nc, const mlmc_field_cfg& fc, int prec, int accel) {
+    size_t s = fc.cov == MLMC_COV_SPDE ? spde_scratch_bytes(B, nf) : field_scratch_bytes(B, fc.M, nf);
     size_t m = mg_workspace_bytes(B, nf, prec, accel);
     if (m > s) s = m;
     if (nc) {
@@ -172,19 +175,23 @@ struct LevelBatch {
     return s;
   }
 
-  static size_t bytes_for(int B, int nf, int nc, int M, int prec, int accel) {
-    return scratch_for(B, nf, nc, M, prec, accel) + (size_t)B * (cube(nf) * 16 + (nc ? cube(nc) * 8 : 0) + 64);
+  static size_t bytes_for(int B, int nf, int nc, const mlmc_field_cfg& fc, int prec, int accel) {
+    const size_t kc_bytes = (fc.cov == MLMC_COV_SPDE && nc) ? cube(nc) * 8 : 0;
+    return scratch_for(B, nf, nc, fc, prec, accel) + (size_t)B * (cube(nf) * 16 + (nc ? cube(nc) * 8 : 0) +
+                                                                   kc_bytes + 64);
   }
 
-  int init(int B_, int nf_, int nc_, int M_, int prec_, int accel, cudaStream_t st) {
+  int init(int B_, int nf_, int nc_, const mlmc_field_cfg& fc, int prec_, int accel, cudaStream_t st) {
     B = B_;
     nf = nf_;
     nc = nc_;
-    M = M_;
+    M = fc.M;
+    cov = fc.cov;
     prec = prec_;
-    scratch_bytes = scratch_for(B, nf, nc, M, prec, accel);
+    scratch_bytes = scratch_for(B, nf, nc, fc, prec, accel);
     MLMC_TRY(ids.alloc((size_t)B * sizeof(uint64_t), st));
     MLMC_TRY(k0.alloc((size_t)B * cube(nf) * sizeof(double), st));
+    if (cov == MLMC_COV_SPDE && nc) MLMC_TRY(kc.alloc((size_t)B * cube(nc) * sizeof(double), st));
     MLMC_TRY(uf.alloc((size_t)B * cube(nf) * sizeof(double), st));
     if (nc) MLMC_TRY(uc.alloc((size_t)B * cube(nc) * sizeof(double), st));
     MLMC_TRY(Q.alloc((size_t)3 * B * sizeof(double), st));
@@ -199,7 +206,13 @@ struct LevelBatch {
   // NULL). Folds the batch into the level record.
   int run(const mlmc_field_cfg& fc, const mg_cfg& mc, const uint64_t* ids_dev, int b, double* Qf, double* Qc,
           double* Y, int* n_unconv, cudaStream_t st) {
-    MLMC_TRY(field_eval_dev(fc, ids_dev, b, nf, MLMC_F64, k0.get(), scratch.get(), st));
+    const bool spde = fc.cov == MLMC_COV_SPDE;
+    if (spde) {
+      MLMC_TRY(spde_field_dev(fc, ids_dev, b, nf, nf, MLMC_F64, k0.get(), scratch.get(), st));
+      if (nc) MLMC_TRY(spde_field_dev(fc, ids_dev, b, nc, nf, MLMC_F64, kc.get(), scratch.get(), st));
+    } else {
+      MLMC_TRY(field_eval_dev(fc, ids_dev, b, nf, MLMC_F64, k0.get(), scratch.get(), st));
+    }
     MGSolveArgs a;
     a.k0 = k0.as<double>();
     a.n_k0 = nf;
@@ -214,7 +227,13 @@ struct LevelBatch {
       // coarse solve first (its coefficient is the fine one injected); its solution,
       // interpolated, starts the fine solve (nested iteration, the first step of FMG)
       MLMC_CUDA_TRY(cudaMemsetAsync(uc.get(), 0, (size_t)b * cube(nc) * sizeof(double), st));
-      a.st0 = 2;
+      if (spde) {
+        a.k0 = kc.as<double>();
+        a.n_k0 = nc;
+        a.st0 = 1;
+      } else {
+        a.st0 = 2;
+      }
       a.u = uc.as<double>();
       a.n = nc;
       MLMC_TRY(mg_solve_dev(a, scratch.get(), st, nullptr, nullptr, &bad, cc, nullptr));
@@ -224,6 +243,8 @@ struct LevelBatch {
     } else {
       MLMC_CUDA_TRY(cudaMemsetAsync(uf.get(), 0, (size_t)b * cube(nf) * sizeof(double), st));
     }
+    a.k0 = k0.as<double>();
+    a.n_k0 = nf;
     a.st0 = 1;
     a.u = uf.as<double>();
     a.n = nf;
@@ -256,14 +277,14 @@ int validate_level_cfg(const mlmc_field_cfg& fc, const mg_cfg& mc) {
   return MLMC_OK;
 }
 
-size_t level_batch_bytes(int b, int nf, int nc, int M, int precision, int accel) {
-  return LevelBatch::bytes_for(b, nf, nc, M, precision, accel);
+size_t level_batch_bytes(int b, int nf, int nc, const mlmc_field_cfg& fc, int precision, int accel) {
+  return LevelBatch::bytes_for(b, nf, nc, fc, precision, accel);
 }
 
 int run_level_batch_host(const mlmc_field_cfg& fc, const mg_cfg& mc, int nf, int nc, const uint64_t* ids_host,
                          int b, double* Qf, double* Qc, int* cyc_f, int* cyc_c, int* n_unconv, cudaStream_t st) {
   LevelBatch lb;
-  MLMC_TRY(lb.init(b, nf, nc, fc.M, mc.precision, mc.accel, st));
+  MLMC_TRY(lb.init(b, nf, nc, fc, mc.precision, mc.accel, st));
   MLMC_CUDA_TRY(cudaMemcpyAsync(lb.ids.get(), ids_host, (size_t)b * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
   double* qf = lb.Q.as<double>();
   double* qc = nc ? lb.Q.as<double>() + b : nullptr;
@@ -324,7 +345,7 @@ static int choose_batch(const mlmc_cfg* cfg, int N, int nf, int nc, int* B) {
   if (b == 0) {
     size_t fr = 0, tot = 0;
     MLMC_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-    const size_t per = LevelBatch::bytes_for(1, nf, nc, cfg->field.M, cfg->mg.precision, cfg->mg.accel);
+    const size_t per = LevelBatch::bytes_for(1, nf, nc, cfg->field, cfg->mg.precision, cfg->mg.accel);
     size_t fit = (size_t)(0.6 * (double)fr) / (per + 1);
     if (fit < 1) fit = 1;
     b = (int)(fit < (size_t)N ? fit : (size_t)N);
@@ -345,25 +366,47 @@ const char* mlmc_last_error_string(void) { return last_error(); }
 
 const char* mlmc_version(void) { return "mlmc-gb300 0.1 (sm_103a)"; }
 
-int mlmc_field_eval(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n, int dtype,
-                    void* k_out, void* stream) {
+static int field_eval_impl(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n,
+                           int n_fine, int dtype, void* k_out, void* stream) {
   MLMC_TRY(check_field(cfg));
   MLMC_TRY(check_grid(n, batch));
   if (!sample_ids_host || !k_out || (dtype != MLMC_F64 && dtype != MLMC_F32)) {
     set_error("mlmc_field_eval: NULL pointer or unknown dtype %d", dtype);
     return MLMC_ERR_INVALID;
   }
+  if (n_fine != n && n_fine != 2 * n - 1) {
+    set_error("mlmc_field_eval_pair: n_fine=%d is neither n=%d nor 2n-1", n_fine, n);
+    return MLMC_ERR_INVALID;
+  }
+  const bool spde = cfg->cov == MLMC_COV_SPDE;
+  if (spde && n_fine > 1025) {
+    set_error("SPDE field: grids up to 1025 nodes per axis (n_fine=%d)", n_fine);
+    return MLMC_ERR_INVALID;
+  }
   MLMC_TRY(device_ready());
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf ids, scratch;
   MLMC_TRY(ids.alloc((size_t)batch * sizeof(uint64_t), st));
-  MLMC_TRY(scratch.alloc(field_scratch_bytes(batch, cfg->M, n), st));
+  MLMC_TRY(scratch.alloc(spde ? spde_scratch_bytes(batch, n) : field_scratch_bytes(batch, cfg->M, n), st));
   MLMC_CUDA_TRY(
       cudaMemcpyAsync(ids.get(), sample_ids_host, (size_t)batch * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-  MLMC_TRY(field_eval_dev(*cfg, ids.as<uint64_t>(), batch, n, dtype, k_out, scratch.get(), st));
+  if (spde)
+    MLMC_TRY(spde_field_dev(*cfg, ids.as<uint64_t>(), batch, n, n_fine, dtype, k_out, scratch.get(), st));
+  else
+    MLMC_TRY(field_eval_dev(*cfg, ids.as<uint64_t>(), batch, n, dtype, k_out, scratch.get(), st));
   // the host ids may be reused by the caller as soon as this returns
   MLMC_CUDA_TRY(cudaStreamSynchronize(st));
   return MLMC_OK;
+}
+
+int mlmc_field_eval(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n, int dtype,
+                    void* k_out, void* stream) {
+  return field_eval_impl(cfg, sample_ids_host, batch, n, n, dtype, k_out, stream);
+}
+
+int mlmc_field_eval_pair(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n, int n_fine,
+                         int dtype, void* k_out, void* stream) {
+  return field_eval_impl(cfg, sample_ids_host, batch, n, n_fine, dtype, k_out, stream);
 }
 
 int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const double* f, double* u,
@@ -415,7 +458,7 @@ int mlmc_level_estimate(const mlmc_cfg* cfg, int level, uint64_t first_id, int N
   int B = 0;
   MLMC_TRY(choose_batch(cfg, N, nf, nc, &B));
   LevelBatch lb;
-  MLMC_TRY(lb.init(B, nf, nc, cfg->field.M, cfg->mg.precision, cfg->mg.accel, st));
+  MLMC_TRY(lb.init(B, nf, nc, cfg->field, cfg->mg.precision, cfg->mg.accel, st));
   std::vector<uint64_t> ids(B);
   int unconv = 0;
   double* Qf = lb.Q.as<double>();
@@ -460,7 +503,7 @@ int mlmc_level_run(const mlmc_cfg* cfg, int level, const uint64_t* ids_dev, int 
   int B = 0;
   MLMC_TRY(choose_batch(cfg, N, nf, nc, &B));
   LevelBatch lb;
-  MLMC_TRY(lb.init(B, nf, nc, cfg->field.M, cfg->mg.precision, cfg->mg.accel, st));
+  MLMC_TRY(lb.init(B, nf, nc, cfg->field, cfg->mg.precision, cfg->mg.accel, st));
   int unconv = 0;
   for (int s0 = 0; s0 < N; s0 += B) {
     const int b = (N - s0) < B ? (N - s0) : B;
@@ -513,7 +556,7 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
       LevelRecord r{};
       for (int rep = 0; rep < 2; ++rep) {
         LevelBatch lb;
-        MLMC_TRY(lb.init(B, nf, nc, cfg->field.M, mc.precision, mc.accel, st));
+        MLMC_TRY(lb.init(B, nf, nc, cfg->field, mc.precision, mc.accel, st));
         MLMC_CUDA_TRY(cudaStreamSynchronize(st));
         const auto t0 = std::chrono::steady_clock::now();
         int unconv = 0;

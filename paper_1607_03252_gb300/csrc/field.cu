@@ -12,29 +12,10 @@
 
 #include "common.cuh"
 #include "field.cuh"
+#include "philox.cuh"
 #include "prof.cuh"
 
 namespace mlmc {
-
-// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the two-multiplier S-box with a
-// Weyl key schedule.
-__device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3, uint32_t k0,
-                                         uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t t0 = hi1 ^ c1 ^ k0, t2 = hi0 ^ c3 ^ k1;
-    c0 = t0;
-    c1 = lo1;
-    c2 = t2;
-    c3 = lo0;
-  }
-}
 
 __device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
   return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6) + 0.5) * (1.0 / 9007199254740992.0);

@@ -9,7 +9,7 @@ namespace mlmc {
 
 // Device bytes one batch of b samples of a level (fine grid nf, coarse grid nc, 0 for
 // level 0) holds while it runs.
-size_t level_batch_bytes(int b, int nf, int nc, int M, int precision, int accel);
+size_t level_batch_bytes(int b, int nf, int nc, const mlmc_field_cfg& fc, int precision, int accel);
 
 // Runs b samples (host ids) through field, fine and coarse solves and QoI on `st`,
 // allocating and releasing the batch's device memory; host outputs of b entries.

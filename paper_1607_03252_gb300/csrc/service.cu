@@ -114,14 +114,14 @@ void worker_loop(mlmc_service* S) {
             int b = std::min((int)q.size(), S->cfg.max_batch);
             // admission by device bytes: shrink the batch to what fits the budget
             while (b > 0) {
-              need = level_batch_bytes(b, nf, nc, S->cfg.field.M, S->cfg.mg.precision, S->cfg.mg.accel);
+              need = level_batch_bytes(b, nf, nc, S->cfg.field, S->cfg.mg.precision, S->cfg.mg.accel);
               if (S->bytes_in_use + need <= S->cfg.hbm_budget_bytes) break;
               b /= 2;
             }
             if (b == 0 && S->inflight == 0) {
               // a single request larger than the whole budget runs alone
               b = 1;
-              need = level_batch_bytes(1, nf, nc, S->cfg.field.M, S->cfg.mg.precision, S->cfg.mg.accel);
+              need = level_batch_bytes(1, nf, nc, S->cfg.field, S->cfg.mg.precision, S->cfg.mg.accel);
             }
             if (b > 0) {
               for (int i = 0; i < b; ++i) {

@@ -69,7 +69,7 @@ def test_invalid_field_cfg_rejected_on_host():
     L = mg.lib()
     ids = (ctypes.c_uint64 * 1)(1)
     for cfg in (mg.field_cfg(1, 1.0, 0.0, 8), mg.field_cfg(1, -1.0, 0.3, 8), mg.field_cfg(1, 1.0, 0.3, 0),
-                mg.field_cfg(1, 1.0, 0.3, 8, cov=2), mg.field_cfg(1, 1.0, 0.3, 8, cov=-1)):
+                mg.field_cfg(1, 1.0, 0.3, 8, cov=3), mg.field_cfg(1, 1.0, 0.3, 8, cov=-1)):
         st = L.mlmc_field_eval(ctypes.byref(cfg), ids, 1, 9, mg.MLMC_F64, ctypes.c_void_p(8), None)
         assert st == mg.MLMC_ERR_INVALID
 
