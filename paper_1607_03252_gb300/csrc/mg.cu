@@ -32,6 +32,7 @@
 #include "prof.cuh"
 #include "smooth.cuh"
 #include "tune.cuh"
+#include "widen.cuh"
 
 namespace mlmc {
 
@@ -64,23 +65,6 @@ struct Carver {
   }
 };
 
-// Widening of an FP32 value to FP64 on the integer pipe only (GB300's FP64 unit, which
-// also performs the hardware conversion, runs at 1/64 of the FP32 rate, and a fallback
-// branch to the hardware conversion is if-converted into every call): for normal numbers
-// the binary64 pattern is the binary32 sign, the exponent re-biased by 1023 - 127 and the
-// 23-bit fraction shifted left by 29 (IEEE 754 layouts), exact; zeros stay zero,
-// infinities and NaNs keep an all-ones exponent, subnormals (below 1.2e-38; faces and
-// diagonals are positive normal numbers) flush to zero.
-__device__ __forceinline__ double widen(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned e = (b >> 23) & 0xffu;
-  const unsigned hi_e = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + (1023u - 127u));
-  const unsigned frac = e == 0u ? 0u : (b & 0x7fffffu);
-  const unsigned hi = (b & 0x80000000u) | (hi_e << 20) | (frac >> 3);
-  const unsigned lo = frac << 29;
-  return __hiloint2double((int)hi, (int)lo);
-}
-__device__ __forceinline__ double widen(double d) { return d; }
 // x in the arithmetic type TD (FP32 to FP64 through widen)
 template <typename TD, typename T>
 __device__ __forceinline__ TD to_t(T x) {

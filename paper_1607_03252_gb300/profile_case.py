@@ -2,13 +2,16 @@
 
   python -m paper_1607_03252_gb300.profile_case --n 129 --batch 8 --prec f64 --cycles 2 \
       [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8|nodal] [--accel cg] [--timing]
+      [--field gauss|exp|spde]
 
 Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256 unless given) for `batch`
 realisations on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0; or V(nu, nu)
 to --rtol) through the C ABI, so
 that every kernel class launches with the sizes of that grid. With --timing the solve runs
 twice and the second run records CUDA events around every launch: per kernel class it
-prints launches, device time per launch and algorithmic GB/s. Exits 0 on success.
+prints launches, device time per launch and algorithmic GB/s; with --field spde the same
+for the field evaluation (the SPDE sampler of Sec. 3.2), with its wall time. Exits 0 on
+success.
 """
 from __future__ import annotations
 
@@ -36,6 +39,7 @@ def main(argv=None):
     p.add_argument("--rtol", type=float, default=0.0, help="stop at this relative residual (0: exactly --cycles)")
     p.add_argument("--sigma2", type=float, default=1.0)
     p.add_argument("--ell", type=float, default=0.3)
+    p.add_argument("--field", choices=["gauss", "exp", "spde"], default="gauss")
     a = p.parse_args(argv)
     prec = mg.MLMC_PREC_F64 if a.prec == "f64" else mg.MLMC_PREC_MIXED
     sm = {"auto": mg.MLMC_SMOOTH_AUTO, "two-pass": mg.MLMC_SMOOTH_TWO_PASS, "32x8": mg.MLMC_SMOOTH_FUSED_32x8,
@@ -43,13 +47,29 @@ def main(argv=None):
           "bulk32x8": mg.MLMC_SMOOTH_BULK_32x8, "bulk32x16": mg.MLMC_SMOOTH_BULK_32x16,
           "bulk64x8": mg.MLMC_SMOOTH_BULK_64x8, "nodal": mg.MLMC_SMOOTH_NODAL}[a.smoother]
     accel = mg.MLMC_ACCEL_CG if a.accel == "cg" else mg.MLMC_ACCEL_NONE
+    cov = {"gauss": mg.MLMC_COV_GAUSS, "exp": mg.MLMC_COV_EXP, "spde": mg.MLMC_COV_SPDE}[a.field]
+    fcfg = mg.field_cfg(RUN_SEED, a.sigma2, a.ell, a.M, cov=cov)
     k = torch.empty((a.batch, a.n, a.n, a.n), dtype=torch.float64, device="cuda")
-    mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, a.sigma2, a.ell, a.M), sample_ids(3, 0, a.batch), k)
+    mg.mlmc_field_eval(fcfg, sample_ids(3, 0, a.batch), k)
     u = torch.zeros_like(k)
     cfg = mg.mg_cfg(a.nu, a.nu, a.rtol, a.cycles, prec, sm, accel)
     cyc, rel, st = mg.mg_solve_batch(cfg, k, u)
     torch.cuda.synchronize()
     print("n=%d batch=%d prec=%s cycles=%s rel_res=%.3e" % (a.n, a.batch, a.prec, cyc.tolist(), rel.max()))
+    if a.timing and a.field == "spde":
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mg.mlmc_field_eval(fcfg, sample_ids(3, 0, a.batch), k)
+        e1.record()
+        torch.cuda.synchronize()
+        print("  SPDE field wall time: %.3f ms (%.1f samples/s)" % (e0.elapsed_time(e1),
+                                                                  a.batch / (e0.elapsed_time(e1) * 1e-3)))
+        mg.profile_reset()
+        mg.profile_enable(True)
+        mg.mlmc_field_eval(fcfg, sample_ids(3, 0, a.batch), k)
+        torch.cuda.synchronize()
+        mg.profile_enable(False)
+        _print_profile(mg.profile_read())
     if a.timing:
         # wall time of a solve on a created stream (graph replay on), then the per-kernel
         # device times with events around every launch (graphs off)
@@ -68,15 +88,17 @@ def main(argv=None):
         mg.mg_solve_batch(cfg, k, u)
         torch.cuda.synchronize()
         mg.profile_enable(False)
-        prof = mg.profile_read()
-        for name, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
-            if v["timed"] == 0:
-                continue
-            per = v["ms"] / v["timed"]
-            gbs = v["bytes"] / v["launches"] / (per * 1e-3) / 1e9 if per > 0 else 0.0
-            print("  %-22s launches %5d  %9.3f us/launch  %8.1f GB/s algorithmic" % (name, v["launches"], per * 1e3,
-                                                                                   gbs))
+        _print_profile(mg.profile_read())
     return 0
+
+
+def _print_profile(prof):
+    for name, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        if v["timed"] == 0:
+            continue
+        per = v["ms"] / v["timed"]
+        gbs = v["bytes"] / v["launches"] / (per * 1e-3) / 1e9 if per > 0 else 0.0
+        print("  %-22s launches %5d  %9.3f us/launch  %8.1f GB/s algorithmic" % (name, v["launches"], per * 1e3, gbs))
 
 
 if __name__ == "__main__":
