@@ -2,7 +2,7 @@
 
   python -m paper_1607_03252_gb300.profile_case --n 129 --batch 8 --prec f64 --cycles 2 \
       [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8|nodal] [--accel cg] [--timing]
-      [--field gauss|exp|spde]
+      [--field gauss|exp|spde] [--level L --n0 17]
 
 Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256 unless given) for `batch`
 realisations on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0; or V(nu, nu)
@@ -10,8 +10,10 @@ to --rtol) through the C ABI, so
 that every kernel class launches with the sizes of that grid. With --timing the solve runs
 twice and the second run records CUDA events around every launch: per kernel class it
 prints launches, device time per launch and algorithmic GB/s; with --field spde the same
-for the field evaluation (the SPDE sampler of Sec. 3.2), with its wall time. Exits 0 on
-success.
+for the field evaluation (the SPDE sampler of Sec. 3.2), with its wall time. With --level
+it instead runs mlmc_level_estimate for `batch` samples of that MLMC level (grids from n0;
+the precision, smoother and field as given, rtol 1e-10) and, with --timing, prints the
+per-class profile of a second run. Exits 0 on success.
 """
 from __future__ import annotations
 
@@ -40,6 +42,8 @@ def main(argv=None):
     p.add_argument("--sigma2", type=float, default=1.0)
     p.add_argument("--ell", type=float, default=0.3)
     p.add_argument("--field", choices=["gauss", "exp", "spde"], default="gauss")
+    p.add_argument("--level", type=int, default=-1, help="run one MLMC level estimate instead")
+    p.add_argument("--n0", type=int, default=17)
     a = p.parse_args(argv)
     prec = mg.MLMC_PREC_F64 if a.prec == "f64" else mg.MLMC_PREC_MIXED
     sm = {"auto": mg.MLMC_SMOOTH_AUTO, "two-pass": mg.MLMC_SMOOTH_TWO_PASS, "32x8": mg.MLMC_SMOOTH_FUSED_32x8,
@@ -49,6 +53,21 @@ def main(argv=None):
     accel = mg.MLMC_ACCEL_CG if a.accel == "cg" else mg.MLMC_ACCEL_NONE
     cov = {"gauss": mg.MLMC_COV_GAUSS, "exp": mg.MLMC_COV_EXP, "spde": mg.MLMC_COV_SPDE}[a.field]
     fcfg = mg.field_cfg(RUN_SEED, a.sigma2, a.ell, a.M, cov=cov)
+    if a.level >= 0:
+        lcfg = mg.make_mlmc_cfg(RUN_SEED, a.sigma2, a.ell, a.M, n0=a.n0, nu1=a.nu, nu2=a.nu, rtol=1e-10,
+                                max_cycles=300, precision=prec, smoother=sm, accel=accel, cov=cov)
+        first = sample_ids(a.level, 0, 1)[0]
+        st, *_ = mg.mlmc_level_estimate(lcfg, a.level, int(first), a.batch, want_samples=False)
+        print("level=%d n0=%d samples=%d field=%s mean=%.6e var=%.3e" % (a.level, a.n0, a.batch, a.field, st.mean,
+                                                                       st.var_unbiased))
+        if a.timing:
+            mg.profile_reset()
+            mg.profile_enable(True)
+            mg.mlmc_level_estimate(lcfg, a.level, int(first), a.batch, want_samples=False)
+            torch.cuda.synchronize()
+            mg.profile_enable(False)
+            _print_profile(mg.profile_read())
+        return 0
     k = torch.empty((a.batch, a.n, a.n, a.n), dtype=torch.float64, device="cuda")
     mg.mlmc_field_eval(fcfg, sample_ids(3, 0, a.batch), k)
     u = torch.zeros_like(k)
