@@ -558,28 +558,11 @@ def roofline(prof, peaks):
 
 
 def lane_items(levels, N, times, lanes):
-    """Work items (level, first, last) of one step on `lanes` concurrent streams: a level
-    whose measured time exceeds the per-lane share is split into sample chunks (the
-    one-GPU form of spreading a level's samples over processor groups, Sec. 5; a sample's
-    result does not depend on its batch); items go longest first onto the least-loaded
-    lane. Returns a list of lanes, each a list of (level, first, last)."""
-    lanes = max(1, lanes)
-    total = sum(times[l] for l in levels)
-    share = total / lanes
-    items = []
-    for l, n in zip(levels, N):
-        k = 1
-        if lanes > 1 and times[l] > share and n > 1:
-            k = min(n, lanes, int(math.ceil(times[l] / share)))
-        for c in range(k):
-            a, b = n * c // k, n * (c + 1) // k
-            items.append((l, a, b, times[l] * (b - a) / n))
-    loads, out = [0.0] * lanes, [[] for _ in range(lanes)]
-    for l, a, b, cost in sorted(items, key=lambda t: -t[3]):
-        i = min(range(lanes), key=lambda k: loads[k])
-        out[i].append((l, a, b))
-        loads[i] += cost
-    return [o for o in out if o]
+    """The lane plan of one step (paper_1607_03252_gb300.planner.lane_plan: the one-GPU
+    form of the paper's dynamic level scheduling, Sec. 5.3)."""
+    from paper_1607_03252_gb300.planner import lane_plan
+
+    return lane_plan(levels, N, times, lanes)
 
 
 class MergedLevel:

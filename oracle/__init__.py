@@ -12,7 +12,9 @@ Contents:
                  their plain definitions with exactly rounded sums, and the rate fit of
                  the alpha, beta, gamma exponents (Eqs. 12, 14);
   adaptive.py    Algorithm 2 (adaptive MLMC with level growth by the bias test) over
-                 any sampler of the level differences.
+                 any sampler of the level differences;
+  schedule.py    the performance model and scheduling rules of Secs. 4-5, with the
+                 heterogeneous optimum by exhaustive search.
 
 Parity status (each item's pin lives in tests/test_oracle_*.py):
   Philox4x32-10 words  round structure pinned through the 64-bit variant against
@@ -32,6 +34,9 @@ Parity status (each item's pin lives in tests/test_oracle_*.py):
                        operator, the sampled covariance against the discrete model's
                        exact covariance, and that model against Whittle's closed form;
   rate fit             pinned by exact geometric data and an independent polynomial fit;
+  scheduling model     pinned by the paper's worked example (716 s, 684 s on 7783
+                       processors, two sequential steps at 524288 processors) and closed
+                       forms of the Amdahl surrogate;
   Algorithm 2          pinned by hand-worked level counts of synthetic samplers (the
                        eps_b / eps and alpha choices each change them) and by the
                        stopping invariants (Eq. 10 sampling variance <= eps_s^2, the bias
