@@ -14,7 +14,9 @@ Contents:
   adaptive.py    Algorithm 2 (adaptive MLMC with level growth by the bias test) over
                  any sampler of the level differences;
   schedule.py    the performance model and scheduling rules of Secs. 4-5, with the
-                 heterogeneous optimum by exhaustive search.
+                 heterogeneous optimum by exhaustive search;
+  fe.py          P1 finite elements on the tetrahedral mesh (four-vertex quadrature of
+                 k), P1 transfers, FMG-2V(4,4) and the point and flux QoIs (Secs. 3.1, 7).
 
 Parity status (each item's pin lives in tests/test_oracle_*.py):
   Philox4x32-10 words  round structure pinned through the 64-bit variant against
@@ -34,6 +36,10 @@ Parity status (each item's pin lives in tests/test_oracle_*.py):
                        operator, the sampled covariance against the discrete model's
                        exact covariance, and that model against Whittle's closed form;
   rate fit             pinned by exact geometric data and an independent polynomial fit;
+  P1 FE / FMG          pinned by symmetry, conservation, the seven-point structure on
+                       this mesh, the constant-k Laplacian, the patch test, O(h^2)
+                       manufactured convergence, exact linear prolongation, FMG's algebraic
+                       error far below the discretisation error, and closed-form QoIs;
   scheduling model     pinned by the paper's worked example (716 s, 684 s on 7783
                        processors, two sequential steps at 524288 processors) and closed
                        forms of the Amdahl surrogate;
@@ -43,4 +49,4 @@ Parity status (each item's pin lives in tests/test_oracle_*.py):
                        test met at L and failed at L - 1).
 """
 from .core import *  # noqa: F401,F403
-from . import adaptive, stats  # noqa: F401
+from . import adaptive, fe, schedule, stats  # noqa: F401
