@@ -127,6 +127,22 @@ typedef struct {
                              FP64 residuals (iterative refinement, MLMC_PREC_MIXED) */
 #define MLMC_ACCEL_CG 1   /* flexible preconditioned conjugate gradients, FP64 recurrences, one
                              V-cycle (FP64 or FP32) as the preconditioner per iteration */
+#define MLMC_ACCEL_FMG 2  /* one full-multigrid cycle (the paper's FMG-2V(4,4), Sec. 7, with
+                             nu1 = nu2 = 4 and max_cycles = 2): the exact solve on the coarsest
+                             grid, then on each finer grid the interpolated coarser solution and
+                             max_cycles V(nu1, nu2) cycles. Fixed work: rtol is not used (the
+                             statistics report the final relative residual). FP64 and f = 1. */
+
+/* Discretisation of -div(k grad u) = f. */
+#define MLMC_DISC_FV 0 /* vertex-centred finite volumes, harmonic-mean faces; full weighting
+                          and trilinear interpolation between grids */
+#define MLMC_DISC_FE 1 /* P1 finite elements (Sec. 3.1) on the mesh that cuts every grid cube
+                          into the six tetrahedra {O, O+e_a, O+e_a+e_b, O+(1,1,1)}, stiffness
+                          with the four-vertex quadrature of k; on this mesh the operator is
+                          the seven-point stencil with face K_a(P) = (k_P + k_{P+a})/4 +
+                          (k_{P+a+b} + k_{P+a+c} + k_{P+a+b+c} + k_{P-b} + k_{P-c} +
+                          k_{P-b-c})/12 ({a,b,c} = {x,y,z}); P1 interpolation between grids and
+                          its transpose. FP64, stored-face smoothers. */
 
 /* Multigrid parameters. */
 typedef struct {
@@ -136,7 +152,8 @@ typedef struct {
   int max_cycles; /* 1..1000 */
   int precision;  /* MLMC_PREC_F64 or MLMC_PREC_MIXED */
   int smoother;   /* MLMC_SMOOTH_* */
-  int accel;      /* MLMC_ACCEL_NONE or MLMC_ACCEL_CG */
+  int accel;      /* MLMC_ACCEL_NONE, MLMC_ACCEL_CG or MLMC_ACCEL_FMG */
+  int disc;       /* MLMC_DISC_FV (zero-initialised) or MLMC_DISC_FE */
 } mg_cfg;
 
 /* Per-sample solve statistics. */
@@ -212,12 +229,20 @@ int mg_solve_batch_noalloc(const mg_cfg* cfg, int batch, int n, const double* k,
                            mg_stats* stats_host, void* stream);
 
 /* Configuration of an MLMC level computation. */
+/* Quantity of interest of a solve. */
+#define MLMC_QOI_MEAN 0  /* mean of u over [1/4, 3/4]^3, tensor trapezoid rule */
+#define MLMC_QOI_POINT 1 /* u(1/4, 1/4, 1/4) (Sec. 7; a grid node) */
+#define MLMC_QOI_FLUX 2  /* flux of k du/dx_2 across the plane x_2 = 1/4 (Sec. 7): the mean of
+                            k du/dx_2 over the layer of tetrahedra (the P1 mesh above) between
+                            x_2 = 1/4 - h and 1/4, k the vertex mean per element */
+
 typedef struct {
   mlmc_field_cfg field;
   mg_cfg mg;
   int n0;        /* nodes per axis of MLMC level 0 (17 gives 17, 33, 65, ... for levels 0, 1, 2, ...) */
   int max_batch; /* samples per device batch, 0 = choose from free HBM */
   void* stream;  /* cudaStream_t, NULL = default */
+  int qoi;       /* MLMC_QOI_MEAN (zero-initialised), MLMC_QOI_POINT or MLMC_QOI_FLUX */
 } mlmc_cfg;
 
 /* Statistics of one MLMC level (Sec. 2.3: Y-hat_l, s_l^2, C_l). */

@@ -32,6 +32,11 @@ MLMC_PREC_MIXED = 1
 MLMC_COV_GAUSS = 0
 MLMC_COV_EXP = 1
 MLMC_COV_SPDE = 2
+MLMC_DISC_FV = 0
+MLMC_DISC_FE = 1
+MLMC_QOI_MEAN = 0
+MLMC_QOI_POINT = 1
+MLMC_QOI_FLUX = 2
 
 _STATUS_NAMES = {
     MLMC_ERR_INVALID: "MLMC_ERR_INVALID",
@@ -68,12 +73,13 @@ MLMC_SMOOTH_NODAL = 8
 
 MLMC_ACCEL_NONE = 0
 MLMC_ACCEL_CG = 1
+MLMC_ACCEL_FMG = 2
 
 
 class MgCfg(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_cycles", ctypes.c_int), ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("accel", ctypes.c_int)]
+                ("accel", ctypes.c_int), ("disc", ctypes.c_int)]
 
 
 class MgStats(ctypes.Structure):
@@ -82,7 +88,7 @@ class MgStats(ctypes.Structure):
 
 class MlmcCfg(ctypes.Structure):
     _fields_ = [("field", FieldCfg), ("mg", MgCfg), ("n0", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("qoi", ctypes.c_int)]
 
 
 class LevelStats(ctypes.Structure):
@@ -217,8 +223,9 @@ def field_cfg(run_seed, sigma2, ell, M, cov=MLMC_COV_GAUSS):
 
 
 def mg_cfg(nu1=2, nu2=2, rtol=1e-10, max_cycles=100, precision=MLMC_PREC_F64, smoother=MLMC_SMOOTH_AUTO,
-           accel=MLMC_ACCEL_NONE):
-    return MgCfg(int(nu1), int(nu2), float(rtol), int(max_cycles), int(precision), int(smoother), int(accel))
+           accel=MLMC_ACCEL_NONE, disc=MLMC_DISC_FV):
+    return MgCfg(int(nu1), int(nu2), float(rtol), int(max_cycles), int(precision), int(smoother), int(accel),
+                 int(disc))
 
 
 def mlmc_field_eval(cfg: FieldCfg, sample_ids, k_out, stream=None, n_fine=None):
@@ -363,12 +370,13 @@ def profile_read():
 
 def make_mlmc_cfg(run_seed, sigma2, ell, M, n0=17, nu1=2, nu2=2, rtol=1e-10, max_cycles=100,
                   precision=MLMC_PREC_F64, max_batch=0, stream=None, smoother=MLMC_SMOOTH_AUTO,
-                  accel=MLMC_ACCEL_NONE, cov=MLMC_COV_GAUSS):
+                  accel=MLMC_ACCEL_NONE, cov=MLMC_COV_GAUSS, disc=MLMC_DISC_FV, qoi=MLMC_QOI_MEAN):
     sp = ctypes.c_void_p(0)
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream)
     return MlmcCfg(field_cfg(run_seed, sigma2, ell, M, cov),
-                   mg_cfg(nu1, nu2, rtol, max_cycles, precision, smoother, accel), int(n0), int(max_batch), sp)
+                   mg_cfg(nu1, nu2, rtol, max_cycles, precision, smoother, accel, disc), int(n0), int(max_batch), sp,
+                   int(qoi))
 
 
 class Service:

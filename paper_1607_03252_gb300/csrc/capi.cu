@@ -73,8 +73,16 @@ static int check_mg(const mg_cfg* c) {
     set_error("unknown precision %d", c->precision);
     return MLMC_ERR_INVALID;
   }
-  if (c->accel != MLMC_ACCEL_NONE && c->accel != MLMC_ACCEL_CG) {
+  if (c->accel != MLMC_ACCEL_NONE && c->accel != MLMC_ACCEL_CG && c->accel != MLMC_ACCEL_FMG) {
     set_error("unknown accel %d", c->accel);
+    return MLMC_ERR_INVALID;
+  }
+  if (c->disc != MLMC_DISC_FV && c->disc != MLMC_DISC_FE) {
+    set_error("unknown disc %d", c->disc);
+    return MLMC_ERR_INVALID;
+  }
+  if ((c->disc == MLMC_DISC_FE || c->accel == MLMC_ACCEL_FMG) && c->precision != MLMC_PREC_F64) {
+    set_error("the P1 finite elements and the FMG cycle run in FP64 (precision %d)", c->precision);
     return MLMC_ERR_INVALID;
   }
   return MLMC_OK;
@@ -83,6 +91,8 @@ static int check_mg(const mg_cfg* c) {
 // `cov` sits in what was the struct's tail padding: the size and every other offset are
 // those of the four-field layout, so zero-initialised callers get the Gaussian covariance.
 static_assert(sizeof(mlmc_field_cfg) == 32 && offsetof(mlmc_field_cfg, cov) == 28, "mlmc_field_cfg layout");
+static_assert(sizeof(mg_cfg) == 40 && offsetof(mg_cfg, disc) == 32, "mg_cfg layout");
+static_assert(sizeof(mlmc_cfg) == 96 && offsetof(mlmc_cfg, qoi) == 88, "mlmc_cfg layout");
 
 static int check_field(const mlmc_field_cfg* c) {
   if (!c) {
@@ -205,7 +215,7 @@ struct LevelBatch {
   // b <= B samples with device ids; Qf/Qc/Y: device outputs of b entries (Qc, Y may be
   // NULL). Folds the batch into the level record.
   int run(const mlmc_field_cfg& fc, const mg_cfg& mc, const uint64_t* ids_dev, int b, double* Qf, double* Qc,
-          double* Y, int* n_unconv, cudaStream_t st) {
+          double* Y, int* n_unconv, cudaStream_t st, int qoi = MLMC_QOI_MEAN) {
     const bool spde = fc.cov == MLMC_COV_SPDE;
     if (spde) {
       MLMC_TRY(spde_field_dev(fc, ids_dev, b, nf, nf, MLMC_F64, k0.get(), scratch.get(), st));
@@ -238,7 +248,8 @@ struct LevelBatch {
       a.n = nc;
       MLMC_TRY(mg_solve_dev(a, scratch.get(), st, nullptr, nullptr, &bad, cc, nullptr));
       *n_unconv += bad;
-      MLMC_TRY(qoi_dev(uc.as<double>(), nc, b, qc, scratch.get(), st));
+      MLMC_TRY(qoi_any(qoi, uc.as<double>(), nc, b, qc, scratch.get(), spde ? kc.as<double>() : k0.as<double>(),
+                       spde ? nc : nf, spde ? 1 : 2, st));
       MLMC_TRY(interpolate_dev(uc.as<double>(), nf, b, uf.as<double>(), st));
     } else {
       MLMC_CUDA_TRY(cudaMemsetAsync(uf.get(), 0, (size_t)b * cube(nf) * sizeof(double), st));
@@ -251,7 +262,7 @@ struct LevelBatch {
     bad = 0;
     MLMC_TRY(mg_solve_dev(a, scratch.get(), st, nullptr, nullptr, &bad, cf, nullptr));
     *n_unconv += bad;
-    MLMC_TRY(qoi_dev(uf.as<double>(), nf, b, Qf, scratch.get(), st));
+    MLMC_TRY(qoi_any(qoi, uf.as<double>(), nf, b, Qf, scratch.get(), k0.as<double>(), nf, 1, st));
     if (nc) {
       MLMC_LAUNCH("level_stats", b * 24.0, b * 10.0, st,
                   (k_level_stats<<<1, 32, 0, st>>>(Qf, qc, cf, cc, b, Y, rec.as<LevelRecord>())));
@@ -326,6 +337,10 @@ static int check_level(const mlmc_cfg* cfg, int level, int N, int* nf, int* nc) 
   }
   MLMC_TRY(check_field(&cfg->field));
   MLMC_TRY(check_mg(&cfg->mg));
+  if (cfg->qoi != MLMC_QOI_MEAN && cfg->qoi != MLMC_QOI_POINT && cfg->qoi != MLMC_QOI_FLUX) {
+    set_error("unknown qoi %d", cfg->qoi);
+    return MLMC_ERR_INVALID;
+  }
   if (level < 0 || level > 8 || N < 1 || !valid_grid(cfg->n0) || cfg->max_batch < 0) {
     set_error("level=%d N=%d n0=%d max_batch=%d invalid", level, N, cfg->n0, cfg->max_batch);
     return MLMC_ERR_INVALID;
@@ -417,6 +432,10 @@ int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const d
     set_error("mg_solve_batch: k and u must be device pointers");
     return MLMC_ERR_INVALID;
   }
+  if (cfg->accel == MLMC_ACCEL_FMG && f) {
+    set_error("mg_solve_batch: the FMG cycle solves f = 1 (pass f = NULL)");
+    return MLMC_ERR_INVALID;
+  }
   MLMC_TRY(device_ready());
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf ws;
@@ -468,7 +487,7 @@ int mlmc_level_estimate(const mlmc_cfg* cfg, int level, uint64_t first_id, int N
     const int b = (N - s0) < B ? (N - s0) : B;
     for (int i = 0; i < b; ++i) ids[i] = first_id + (uint64_t)(s0 + i);
     MLMC_CUDA_TRY(cudaMemcpyAsync(lb.ids.get(), ids.data(), (size_t)b * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-    MLMC_TRY(lb.run(cfg->field, cfg->mg, lb.ids.as<uint64_t>(), b, Qf, Qc, Y, &unconv, st));
+    MLMC_TRY(lb.run(cfg->field, cfg->mg, lb.ids.as<uint64_t>(), b, Qf, Qc, Y, &unconv, st, cfg->qoi));
     if (Y_host) MLMC_CUDA_TRY(cudaMemcpyAsync(Y_host + s0, Y, b * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (Qf_host) MLMC_CUDA_TRY(cudaMemcpyAsync(Qf_host + s0, Qf, b * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (Qc_host) {
@@ -510,7 +529,7 @@ int mlmc_level_run(const mlmc_cfg* cfg, int level, const uint64_t* ids_dev, int 
     double* Qf = Qf_dev ? Qf_dev + s0 : lb.Q.as<double>();
     double* Qc = Qc_dev ? Qc_dev + s0 : nullptr;
     double* Y = Y_dev ? Y_dev + s0 : nullptr;
-    MLMC_TRY(lb.run(cfg->field, cfg->mg, ids_dev + s0, b, Qf, Qc, Y, &unconv, st));
+    MLMC_TRY(lb.run(cfg->field, cfg->mg, ids_dev + s0, b, Qf, Qc, Y, &unconv, st, cfg->qoi));
   }
   if (out) {
     LevelRecord r;

@@ -567,6 +567,150 @@ __global__ void k_qoi_final(int B, int NB, double scale, const double* __restric
 }
 
 // ---------------------------------------------------------------------------------
+// P1 finite elements on the tetrahedral mesh (Sec. 3.1): every grid cube is cut into the
+// six tetrahedra {O, O + e_a, O + e_a + e_b, O + (1,1,1)}; the stiffness with the four-vertex
+// quadrature of k couples only the axis edges of each element's vertex path (the
+// barycentric gradients of the path's non-adjacent vertices are orthogonal), so the
+// operator keeps the seven-point form with, per axis edge, the mean over the six elements
+// that share it of their vertex-mean coefficient kbar:
+//   K_a(P) = (k_P + k_{P+a}) / 4 + (k_{P+a+b} + k_{P+a+c} + k_{P+a+b+c} + k_{P-b} + k_{P-c}
+//            + k_{P-b-c}) / 12      ({a, b, c} = {x, y, z}),
+// in the h^2-scaled form (FE matrix / h); the load of f = 1 is h^3 per interior node, the
+// g = h^2 f of the scaled form.
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_faces_fe(const double* __restrict__ k0, int n0, int st0, int n, int B, T* __restrict__ Kx,
+                           T* __restrict__ Ky, T* __restrict__ Kz) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
+  const size_t n3 = (size_t)n * n * n, n03 = (size_t)n0 * n0 * n0;
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    const double* kb = k0 + (size_t)s * n03;
+    auto K = [&](int dx, int dy, int dz) {
+      return kb[((size_t)(st0 * (z + dz)) * n0 + (size_t)(st0 * (y + dy))) * n0 + (size_t)(st0 * (x + dx))];
+    };
+    const bool ix = x >= 1 && x <= n - 2, iy = y >= 1 && y <= n - 2, iz = z >= 1 && z <= n - 2;
+    const size_t t = (size_t)s * n3 + (size_t)(z * n * n + q);
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    if (x <= n - 2 && iy && iz)
+      fx = (K(0, 0, 0) + K(1, 0, 0)) * 0.25 +
+           (K(1, 1, 0) + K(1, 0, 1) + K(1, 1, 1) + K(0, -1, 0) + K(0, 0, -1) + K(0, -1, -1)) * (1.0 / 12.0);
+    if (y <= n - 2 && ix && iz)
+      fy = (K(0, 0, 0) + K(0, 1, 0)) * 0.25 +
+           (K(0, 1, 1) + K(1, 1, 0) + K(1, 1, 1) + K(0, 0, -1) + K(-1, 0, 0) + K(-1, 0, -1)) * (1.0 / 12.0);
+    if (z <= n - 2 && ix && iy)
+      fz = (K(0, 0, 0) + K(0, 0, 1)) * 0.25 +
+           (K(1, 0, 1) + K(0, 1, 1) + K(1, 1, 1) + K(-1, 0, 0) + K(0, -1, 0) + K(-1, -1, 0)) * (1.0 / 12.0);
+    Kx[t] = (T)fx;
+    Ky[t] = (T)fy;
+    Kz[t] = (T)fz;
+  }
+}
+
+// P1 interpolation between nested tetrahedral meshes, added on interior fine nodes: a
+// fine node with odd coordinates d (a 0/1 vector) is the midpoint of the coarse edge from
+// c0 = (f - d) / 2 to c0 + d (a mesh edge: every direction e_a, e_a + e_b, (1,1,1) is
+// one), so it takes the mean of the two; a node with d = 0 is a coarse node.
+template <typename T>
+__global__ void k_prolong_p1(int nf, int B, const T* __restrict__ ec, T* __restrict__ u,
+                             const int* __restrict__ active) {
+  const int m = nf - 2, nc = (nf + 1) / 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // interior node of the plane
+  if (q >= m * m) return;
+  const int y = 1 + q / m, x = 1 + q - (y - 1) * m;
+  const size_t nf3 = (size_t)nf * nf * nf, nc3 = (size_t)nc * nc * nc;
+  for (int zz = blockIdx.y; zz < B * m; zz += gridDim.y) {
+    const int s = zz / m, z = 1 + zz - s * m;
+    if (active && !active[s]) continue;
+    const int dx = x & 1, dy = y & 1, dz = z & 1;
+    const T* e = ec + (size_t)s * nc3;
+    const size_t c0 = ((size_t)((z - dz) >> 1) * nc + (size_t)((y - dy) >> 1)) * nc + (size_t)((x - dx) >> 1);
+    T v = e[c0];
+    if (dx | dy | dz) v = T(0.5) * (v + e[c0 + ((size_t)dz * nc + dy) * nc + dx]);
+    u[(size_t)s * nf3 + ((size_t)z * nf + y) * nf + x] += v;
+  }
+}
+
+// Its transpose on interior coarse nodes, scaled for the coarse h^2-scaled system:
+// g_c = (h / h_c) P^T r = (1/2) (r(2c) + (1/2) sum over the 14 mesh-edge directions d of
+// r(2c + d)) (the fine residual r is zero on the boundary).
+template <typename T>
+__global__ void k_restrict_p1(int nf, int B, const T* __restrict__ r, T* __restrict__ gc,
+                              const int* __restrict__ active) {
+  const int nc = (nf + 1) / 2, mc = nc - 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // interior coarse node of the plane
+  if (q >= mc * mc) return;
+  const int Y = 1 + q / mc, X = 1 + q - (Y - 1) * mc;
+  const size_t nf3 = (size_t)nf * nf * nf, nc3 = (size_t)nc * nc * nc, nf2 = (size_t)nf * nf;
+  for (int zz = blockIdx.y; zz < B * mc; zz += gridDim.y) {
+    const int s = zz / mc, Z = 1 + zz - s * mc;
+    if (active && !active[s]) continue;
+    const T* rb = r + (size_t)s * nf3;
+    const size_t f = (size_t)(2 * Z) * nf2 + (size_t)(2 * Y) * nf + 2 * X;
+    const size_t dx = 1, dy = nf, dz = nf2;
+    T acc = rb[f - dx] + rb[f + dx];
+    acc += rb[f - dy] + rb[f + dy];
+    acc += rb[f - dz] + rb[f + dz];
+    acc += rb[f - dx - dy] + rb[f + dx + dy];
+    acc += rb[f - dy - dz] + rb[f + dy + dz];
+    acc += rb[f - dx - dz] + rb[f + dx + dz];
+    acc += rb[f - dx - dy - dz] + rb[f + dx + dy + dz];
+    gc[(size_t)s * nc3 + ((size_t)Z * nc + Y) * nc + X] = T(0.5) * rb[f] + T(0.25) * acc;
+  }
+}
+
+// Q[s] = u(1/4, 1/4, 1/4) (a node: (n - 1) / 4 in every coordinate).
+__global__ void k_qoi_point(int n, int B, const double* __restrict__ u, double* __restrict__ Q) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  const int c = (n - 1) / 4;
+  Q[s] = u[(size_t)s * n * n * n + ((size_t)c * n + c) * n + c];
+}
+
+// Flux of k du/dx_2 across x_2 = 1/4 as the mean over the layer of elements between
+// x_2 = 1/4 - h and 1/4: per cube of the layer (origin y = (n-1)/4 - 1) and each of its
+// six elements (path a, b, c), kbar times the difference of u along the path's y step;
+// per-block partial sums (grid (NB, B)), scaled by h/6 in k_qoi_final. k from the FP64
+// field k0 (stride st0).
+__global__ void __launch_bounds__(kThreads) k_qoi_flux(int n, const double* __restrict__ u,
+                                                       const double* __restrict__ k0, int n0, int st0,
+                                                       double* __restrict__ partial) {
+  const int s = blockIdx.y, NB = gridDim.x;
+  const int m = n - 1, j0 = (n - 1) / 4 - 1;
+  const size_t n3 = (size_t)n * n * n, n03 = (size_t)n0 * n0 * n0;
+  const double* ub = u + (size_t)s * n3;
+  const double* kb = k0 + (size_t)s * n03;
+  double acc = 0.0;
+  for (int c = blockIdx.x * kThreads + threadIdx.x; c < m * m; c += NB * kThreads) {
+    const int zc = c / m, xc = c - zc * m;
+    double uv[8], kv[8];  // cube corners, bit 0 = x, bit 1 = y, bit 2 = z
+    for (int v = 0; v < 8; ++v) {
+      const int X = xc + (v & 1), Y = j0 + ((v >> 1) & 1), Z = zc + (v >> 2);
+      uv[v] = ub[((size_t)Z * n + Y) * n + X];
+      kv[v] = kb[((size_t)(st0 * Z) * n0 + (size_t)(st0 * Y)) * n0 + (size_t)(st0 * X)];
+    }
+    const int ax[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (int e = 0; e < 6; ++e) {
+      int v = 0, vs[4];
+      vs[0] = 0;
+      double dy = 0.0;
+      for (int i = 0; i < 3; ++i) {
+        const int w = v | (1 << ax[e][i]);
+        if (ax[e][i] == 1) dy = uv[w] - uv[v];
+        v = w;
+        vs[i + 1] = v;
+      }
+      const double kbar = 0.25 * (kv[vs[0]] + kv[vs[1]] + kv[vs[2]] + kv[vs[3]]);
+      acc = fma(kbar, dy, acc);
+    }
+  }
+  const double b = block_sum<kThreads>(acc);
+  if (threadIdx.x == 0) partial[(size_t)s * NB + blockIdx.x] = b;
+}
+
+// ---------------------------------------------------------------------------------
 // Flexible preconditioned conjugate gradients (FP64 recurrences; the V-cycle is the
 // preconditioner). All vectors are FP64 on the finest grid; per-sample scalars.
 // ---------------------------------------------------------------------------------
@@ -829,6 +973,7 @@ struct Hier {
   int tile[kMaxLevels] = {};      // fused-sweep tile shape per level
   bool fused[kMaxLevels] = {};    // fused (one pass) or two-pass smoother per level
   bool nodal[kMaxLevels] = {};    // two-pass sweep on the nodal coefficient (FP32)
+  bool p1 = false;                // P1 finite elements: P1 transfers instead of FW / trilinear
 };
 
 // Lays out the workspace. Level-0 u of FP64 solves is the caller's array (not carved).
@@ -965,14 +1110,24 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
                                                               act)));
   }
   Level<T>& w = H.lv[j + 1];
-  MLMC_LAUNCH(Names<T>::restrict_, B * ((double)v.n3 + (double)w.n3) * W, B * interior(w.n) * 54.0, st,
-              (k_restrict<T><<<plane_grid((w.n - 2) * (w.n - 1), (long long)B * (w.n - 2)), kPlaneThreads, 0, st>>>(
-                  v.n, B, v.r, w.g, act)));
+  if (H.p1)
+    MLMC_LAUNCH("restrict_p1", B * ((double)v.n3 + (double)w.n3) * W, B * interior(w.n) * 16.0, st,
+                (k_restrict_p1<T><<<plane_grid((w.n - 2) * (w.n - 2), (long long)B * (w.n - 2)), kPlaneThreads, 0,
+                                    st>>>(v.n, B, v.r, w.g, act)));
+  else
+    MLMC_LAUNCH(Names<T>::restrict_, B * ((double)v.n3 + (double)w.n3) * W, B * interior(w.n) * 54.0, st,
+                (k_restrict<T><<<plane_grid((w.n - 2) * (w.n - 1), (long long)B * (w.n - 2)), kPlaneThreads, 0,
+                                 st>>>(v.n, B, v.r, w.g, act)));
   cudaMemsetAsync(w.u, 0, (size_t)B * w.n3 * sizeof(T), st);
   vcycle(H, j + 1, nu1, nu2, st);
-  MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
-              (k_prolong<T><<<plane_grid(m * (v.n - 1), (long long)B * m), kPlaneThreads, 0, st>>>(v.n, B, w.u, v.u,
-                                                                                                  act)));
+  if (H.p1)
+    MLMC_LAUNCH("prolong_p1", B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 1.5, st,
+                (k_prolong_p1<T><<<plane_grid(m * m, (long long)B * m), kPlaneThreads, 0, st>>>(v.n, B, w.u, v.u,
+                                                                                               act)));
+  else
+    MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
+                (k_prolong<T><<<plane_grid(m * (v.n - 1), (long long)B * m), kPlaneThreads, 0, st>>>(v.n, B, w.u,
+                                                                                                    v.u, act)));
   smooth(nu2);
 }
 
@@ -1102,9 +1257,11 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
                int* n_unconv, int* cycles_dev, double* relres_dev) {
   const bool mixed = a.cfg.precision == MLMC_PREC_MIXED;
   const bool cg = a.cfg.accel == MLMC_ACCEL_CG;
+  const bool fmg = a.cfg.accel == MLMC_ACCEL_FMG;
   Hier<T> H;
   Carver c(ws);
   layout<T>(H, c, a.B, a.n, mixed, cg);
+  H.p1 = a.cfg.disc == MLMC_DISC_FE;
   const int B = a.B;
   const double W = (double)sizeof(T);
   // operators of every level (k injected from k0)
@@ -1112,8 +1269,12 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   for (int j = 0; j < H.L; ++j) {
     Level<T>& v = H.lv[j];
     const dim3 gb = plane_grid(v.n * v.n, (long long)B * v.n);
-    MLMC_LAUNCH(Names<T>::faces, B * (double)v.n3 * (8.0 + 3 * W), B * (double)v.n3 * 12.0, st,
-                (k_faces<T><<<gb, kPlaneThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, v.Kx, v.Ky, v.Kz)));
+    if (a.cfg.disc == MLMC_DISC_FE)
+      MLMC_LAUNCH("faces_fe", B * (double)v.n3 * (8.0 + 3 * W), B * (double)v.n3 * 36.0, st,
+                  (k_faces_fe<T><<<gb, kPlaneThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, v.Kx, v.Ky, v.Kz)));
+    else
+      MLMC_LAUNCH(Names<T>::faces, B * (double)v.n3 * (8.0 + 3 * W), B * (double)v.n3 * 12.0, st,
+                  (k_faces<T><<<gb, kPlaneThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, v.Kx, v.Ky, v.Kz)));
     MLMC_LAUNCH(Names<T>::diag, B * (double)v.n3 * 5 * W, B * (double)v.n3 * 6.0, st,
                 (k_diag<T, T><<<gb, kPlaneThreads, 0, st>>>(v.n, B, v.Kx, v.Ky, v.Kz, v.D, v.Dinv)));
     // restriction writes only interior coarse nodes: the boundary of g stays zero
@@ -1218,7 +1379,47 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     const int st_pcg = pcg_loop<T>(H, a, nu1, nu2, rtol, maxc, st, gr);
     if (st_pcg < 0) return st_pcg;
   }
-  int na = cg ? 0 : residual_check(0);
+  if (fmg) {
+    // One FMG cycle (nested iteration, Sec. 7): every grid's own right-hand side h_j^2 f
+    // (f = 1), the exact solve on the coarsest grid, then per finer grid the P1 (or
+    // trilinear) interpolation of the coarser solution and max_cycles V(nu1, nu2) cycles.
+    for (int j = 1; j < H.L; ++j) {
+      Level<T>& v = H.lv[j];
+      const double hj = 1.0 / (double)(v.n - 1);
+      MLMC_LAUNCH("prepare", B * (double)v.n3 * 8.0, B * (double)v.n3, st,
+                  (k_prepare<<<plane_grid(v.n * v.n, (long long)B * v.n), kPlaneThreads, 0, st>>>(
+                      v.n, B, hj * hj, nullptr, (double*)v.g, (double*)v.u)));
+    }
+    vcycle(H, H.L - 1, nu1, nu2, st);
+    for (int j = H.L - 2; j >= 0; --j) {
+      Level<T>& v = H.lv[j];
+      Level<T>& w = H.lv[j + 1];
+      const int m = v.n - 2;
+      MLMC_CUDA_TRY(cudaMemsetAsync(v.u, 0, (size_t)B * v.n3 * sizeof(T), st));
+      if (H.p1)
+        MLMC_LAUNCH("prolong_p1", B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 1.5, st,
+                    (k_prolong_p1<T><<<plane_grid(m * m, (long long)B * m), kPlaneThreads, 0, st>>>(
+                        v.n, B, w.u, v.u, H.active)));
+      else
+        MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
+                    (k_prolong<T><<<plane_grid(m * (v.n - 1), (long long)B * m), kPlaneThreads, 0, st>>>(
+                        v.n, B, w.u, v.u, H.active)));
+      for (int cyc = 0; cyc < maxc; ++cyc) vcycle(H, j, nu1, nu2, st);
+    }
+    std::vector<int> cyc(B, maxc);
+    MLMC_CUDA_TRY(cudaMemcpyAsync(H.cycles, cyc.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    // the final relative residual, for the statistics only (the cycle's work is fixed)
+    MLMC_CUDA_TRY(cudaMemsetAsync(H.n_active, 0, sizeof(int), st));
+    int zs = 0;
+    const dim3 rz = zmarch_grid(a.n, B, &zs);
+    MLMC_LAUNCH("residual_norm_f64", B * interior(a.n) * 6.0 * 8, B * interior(a.n) * 16.0, st,
+                (k_residual_z<T, T, T, T><<<rz, 128, 0, st>>>(a.n, zs, l0.Kx, l0.Ky, l0.Kz, l0.D, l0.g, l0.u,
+                                                              nullptr, H.partial, H.active)));
+    MLMC_LAUNCH("norm_update", B * H.NBz * 8.0, B * H.NBz * 1.0, st,
+                (k_norm_update<<<sb, 128, 0, st>>>(B, H.NBz, H.partial, H.g2, H.relres, H.cycles, H.active, 1, 0,
+                                                   0.0, maxc, H.n_active)));
+  }
+  int na = (cg || fmg) ? 0 : residual_check(0);
   if (na < 0) return na;
   while (na > 0) {
     if (mixed) {
@@ -1261,7 +1462,7 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   for (int s = 0; s < B; ++s) {
     if (cycles_host) cycles_host[s] = cyc[s];
     if (relres_host) relres_host[s] = rel[s];
-    if (rtol > 0.0 && !(rel[s] <= rtol)) ++bad;
+    if (!fmg && rtol > 0.0 && !(rel[s] <= rtol)) ++bad;
   }
   if (n_unconv) *n_unconv = bad;
   return MLMC_OK;
@@ -1300,7 +1501,9 @@ int interpolate_dev(const double* uc, int nf, int B, double* uf, cudaStream_t st
 
 size_t qoi_scratch_bytes(int B, int n) {
   const int S = (n - 1) / 2 + 1;
-  return a256((size_t)B * reduce_blocks(cube(S)) * sizeof(double));
+  const size_t a = (size_t)B * reduce_blocks(cube(S)) * sizeof(double);
+  const size_t b = (size_t)B * reduce_blocks((size_t)(n - 1) * (n - 1)) * sizeof(double);
+  return a256(a > b ? a : b);
 }
 
 int qoi_dev(const double* u, int n, int B, double* Q, void* scratch, cudaStream_t st) {
@@ -1312,6 +1515,24 @@ int qoi_dev(const double* u, int n, int B, double* Q, void* scratch, cudaStream_
   const double h = 1.0 / (double)(n - 1);
   MLMC_LAUNCH("qoi_final", B * NB * 8.0, B * NB * 1.0, st,
               (k_qoi_final<<<(B + 127) / 128, 128, 0, st>>>(B, NB, 8.0 * h * h * h, partial, Q)));
+  MLMC_CUDA_TRY(cudaGetLastError());
+  return MLMC_OK;
+}
+
+int qoi_any(int qoi, const double* u, int n, int B, double* Q, void* scratch, const double* k0, int n_k0, int st0,
+            cudaStream_t st) {
+  if (qoi == MLMC_QOI_MEAN) return qoi_dev(u, n, B, Q, scratch, st);
+  if (qoi == MLMC_QOI_POINT) {
+    MLMC_LAUNCH("qoi", B * 8.0, 0.0, st, (k_qoi_point<<<(B + 127) / 128, 128, 0, st>>>(n, B, u, Q)));
+    return MLMC_OK;
+  }
+  const int NB = reduce_blocks((size_t)(n - 1) * (n - 1));
+  double* partial = (double*)scratch;
+  MLMC_LAUNCH("qoi", B * (double)(n - 1) * (n - 1) * 8 * 16, B * (double)(n - 1) * (n - 1) * 6 * 8, st,
+              (k_qoi_flux<<<dim3(NB, B), kThreads, 0, st>>>(n, u, k0, n_k0, st0, partial)));
+  const double h = 1.0 / (double)(n - 1);
+  MLMC_LAUNCH("qoi_final", B * NB * 8.0, B * NB * 1.0, st,
+              (k_qoi_final<<<(B + 127) / 128, 128, 0, st>>>(B, NB, h / 6.0, partial, Q)));
   MLMC_CUDA_TRY(cudaGetLastError());
   return MLMC_OK;
 }

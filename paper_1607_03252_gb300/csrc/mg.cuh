@@ -35,6 +35,12 @@ int mg_solve_dev(const MGSolveArgs& a, void* workspace, cudaStream_t st, int* cy
 size_t qoi_scratch_bytes(int B, int n);
 int qoi_dev(const double* u, int n, int B, double* Q_dev, void* scratch, cudaStream_t st);
 
+// Q[s] for the quantity of interest `qoi` (MLMC_QOI_*) of the B solutions u on grid n; the
+// flux reads the FP64 field k0 (n_k0 nodes per axis, stride st0 to grid n). scratch:
+// qoi_scratch_bytes(B, n).
+int qoi_any(int qoi, const double* u, int n, int B, double* Q_dev, void* scratch, const double* k0, int n_k0,
+            int st0, cudaStream_t st);
+
 // uf = trilinear interpolation of uc ((nf+1)/2)^3 onto the nf^3 grid (0 on the boundary):
 // the initial guess of a fine solve from the coarse solution of the same realisation.
 int interpolate_dev(const double* uc, int nf, int B, double* uf, cudaStream_t st);

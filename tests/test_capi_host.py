@@ -106,3 +106,24 @@ def test_field_cfg_layout_and_cov_default():
     assert mg.FieldCfg.cov.offset == 28
     assert mg.field_cfg(1, 1.0, 0.3, 8).cov == mg.MLMC_COV_GAUSS
     assert mg.field_cfg(1, 1.0, 0.3, 8, cov=mg.MLMC_COV_EXP).cov == 1
+
+
+def test_solver_and_level_cfg_layouts():
+    import ctypes
+
+    assert ctypes.sizeof(mg.MgCfg) == 40 and mg.MgCfg.disc.offset == 32
+    assert ctypes.sizeof(mg.MlmcCfg) == 96 and mg.MlmcCfg.qoi.offset == 88
+    c = mg.make_mlmc_cfg(1, 1.0, 0.3, 8)
+    assert c.mg.disc == mg.MLMC_DISC_FV and c.qoi == mg.MLMC_QOI_MEAN
+
+
+def test_fe_and_fmg_cfg_rejected_on_host():
+    L = mg.lib()
+    for cfg in (mg.mg_cfg(disc=2), mg.mg_cfg(accel=3), mg.mg_cfg(precision=mg.MLMC_PREC_MIXED, disc=mg.MLMC_DISC_FE),
+                mg.mg_cfg(precision=mg.MLMC_PREC_MIXED, accel=mg.MLMC_ACCEL_FMG)):
+        st = L.mg_solve_batch(ctypes.byref(cfg), 1, 9, ctypes.c_void_p(8), None, ctypes.c_void_p(8), None, None)
+        assert st == mg.MLMC_ERR_INVALID
+    fmg = mg.mg_cfg(4, 4, 0.0, 2, accel=mg.MLMC_ACCEL_FMG, disc=mg.MLMC_DISC_FE)
+    st = L.mg_solve_batch(ctypes.byref(fmg), 1, 9, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), None,
+                          None)
+    assert st == mg.MLMC_ERR_INVALID  # FMG solves f = 1 only
