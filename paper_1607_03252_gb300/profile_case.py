@@ -2,7 +2,7 @@
 
   python -m paper_1607_03252_gb300.profile_case --n 129 --batch 8 --prec f64 --cycles 2 \
       [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8|nodal] [--accel cg] [--timing]
-      [--field gauss|exp|spde] [--level L --n0 17]
+      [--field gauss|exp|spde] [--level L --n0 17] [--disc fv|fe] [--accel fmg] [--qoi mean|point|flux]
 
 Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256 unless given) for `batch`
 realisations on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0; or V(nu, nu)
@@ -35,7 +35,9 @@ def main(argv=None):
     p.add_argument("--M", type=int, default=256)
     p.add_argument("--smoother", choices=["auto", "two-pass", "32x8", "32x16", "64x8", "bulk32x8", "bulk32x16",
                                           "bulk64x8", "nodal"], default="auto")
-    p.add_argument("--accel", choices=["none", "cg"], default="none")
+    p.add_argument("--accel", choices=["none", "cg", "fmg"], default="none")
+    p.add_argument("--disc", choices=["fv", "fe"], default="fv")
+    p.add_argument("--qoi", choices=["mean", "point", "flux"], default="mean")
     p.add_argument("--timing", action="store_true")
     p.add_argument("--nu", type=int, default=2, help="V(nu, nu)")
     p.add_argument("--rtol", type=float, default=0.0, help="stop at this relative residual (0: exactly --cycles)")
@@ -50,17 +52,28 @@ def main(argv=None):
           "32x16": mg.MLMC_SMOOTH_FUSED_32x16, "64x8": mg.MLMC_SMOOTH_FUSED_64x8,
           "bulk32x8": mg.MLMC_SMOOTH_BULK_32x8, "bulk32x16": mg.MLMC_SMOOTH_BULK_32x16,
           "bulk64x8": mg.MLMC_SMOOTH_BULK_64x8, "nodal": mg.MLMC_SMOOTH_NODAL}[a.smoother]
-    accel = mg.MLMC_ACCEL_CG if a.accel == "cg" else mg.MLMC_ACCEL_NONE
+    accel = {"none": mg.MLMC_ACCEL_NONE, "cg": mg.MLMC_ACCEL_CG, "fmg": mg.MLMC_ACCEL_FMG}[a.accel]
+    disc = mg.MLMC_DISC_FE if a.disc == "fe" else mg.MLMC_DISC_FV
+    qoi = {"mean": mg.MLMC_QOI_MEAN, "point": mg.MLMC_QOI_POINT, "flux": mg.MLMC_QOI_FLUX}[a.qoi]
     cov = {"gauss": mg.MLMC_COV_GAUSS, "exp": mg.MLMC_COV_EXP, "spde": mg.MLMC_COV_SPDE}[a.field]
     fcfg = mg.field_cfg(RUN_SEED, a.sigma2, a.ell, a.M, cov=cov)
     if a.level >= 0:
-        lcfg = mg.make_mlmc_cfg(RUN_SEED, a.sigma2, a.ell, a.M, n0=a.n0, nu1=a.nu, nu2=a.nu, rtol=1e-10,
-                                max_cycles=300, precision=prec, smoother=sm, accel=accel, cov=cov)
+        fmg = accel == mg.MLMC_ACCEL_FMG
+        lcfg = mg.make_mlmc_cfg(RUN_SEED, a.sigma2, a.ell, a.M, n0=a.n0, nu1=a.nu, nu2=a.nu,
+                                rtol=0.0 if fmg else 1e-10, max_cycles=a.cycles if fmg else 300, precision=prec,
+                                smoother=sm, accel=accel, cov=cov, disc=disc, qoi=qoi)
         first = sample_ids(a.level, 0, 1)[0]
         st, *_ = mg.mlmc_level_estimate(lcfg, a.level, int(first), a.batch, want_samples=False)
         print("level=%d n0=%d samples=%d field=%s mean=%.6e var=%.3e" % (a.level, a.n0, a.batch, a.field, st.mean,
                                                                        st.var_unbiased))
         if a.timing:
+            import time
+
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mg.mlmc_level_estimate(lcfg, a.level, int(first), a.batch, want_samples=False)
+            dt = time.perf_counter() - t0
+            print("  level estimate wall time: %.3f ms (%.1f samples/s)" % (dt * 1e3, a.batch / dt))
             mg.profile_reset()
             mg.profile_enable(True)
             mg.mlmc_level_estimate(lcfg, a.level, int(first), a.batch, want_samples=False)
@@ -71,7 +84,7 @@ def main(argv=None):
     k = torch.empty((a.batch, a.n, a.n, a.n), dtype=torch.float64, device="cuda")
     mg.mlmc_field_eval(fcfg, sample_ids(3, 0, a.batch), k)
     u = torch.zeros_like(k)
-    cfg = mg.mg_cfg(a.nu, a.nu, a.rtol, a.cycles, prec, sm, accel)
+    cfg = mg.mg_cfg(a.nu, a.nu, a.rtol, a.cycles, prec, sm, accel, disc)
     cyc, rel, st = mg.mg_solve_batch(cfg, k, u)
     torch.cuda.synchronize()
     print("n=%d batch=%d prec=%s cycles=%s rel_res=%.3e" % (a.n, a.batch, a.prec, cyc.tolist(), rel.max()))
