@@ -378,7 +378,8 @@ typedef struct {
 /*
  * mlmc_autotune -- picks the smoother implementation (two-pass on stored faces, two-pass
  * on the nodal coefficient, or fused with 32x8, 32x16 or 64x8 tiles staged by cp.async
- * or by TMA bulk copies: 8 candidates) and the sweep count
+ * or by TMA bulk copies: 8 candidates; 7 for FP64 solves and P1 finite elements, which
+ * have no nodal-coefficient sweep) and the sweep count
  * nu in {1,2,3} of V(nu, nu) for MLMC level
  * `level` under cfg (no counterpart in the paper; the paper fixes its cycle, Sec. 7.1).
  * Each candidate runs the whole level pipeline once untimed and once timed on

@@ -565,8 +565,10 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   // an explicit V(nu, nu) in cfg is kept: only the smoother implementation is tuned
   const bool fixed_nu = cfg->mg.nu1 > 0 && cfg->mg.nu1 == cfg->mg.nu2;
   const int nu_lo = fixed_nu ? cfg->mg.nu1 : 1, nu_hi = fixed_nu ? cfg->mg.nu1 : 3;
+  // the nodal-coefficient sweep exists only in FP32 correction cycles on finite volumes
+  const int n_sm = (cfg->mg.precision == MLMC_PREC_MIXED && cfg->mg.disc == MLMC_DISC_FV) ? 8 : 7;
   for (int nu = nu_lo; nu <= nu_hi; ++nu)
-    for (int si = 0; si < 8; ++si) {
+    for (int si = 0; si < n_sm; ++si) {
       mg_cfg mc = cfg->mg;
       mc.smoother = smoothers[si];
       mc.nu1 = nu;
