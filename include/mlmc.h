@@ -212,7 +212,8 @@ int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const d
  * memory (code running under another framework's allocator or a fixed device-memory
  * budget, tools that forbid allocation calls while they record GPU work). The paper
  * has no counterpart; this is an interface variant only, with the same arguments,
- * numerics and results as mg_solve_batch.
+ * numerics and results as mg_solve_batch, except that the FMG cycle (MLMC_ACCEL_FMG) is
+ * not offered here (MLMC_ERR_INVALID).
  * The workspace is a fixed 32 MiB array in the library's device image (every GPU that
  * loads the library keeps it until the process exits); the call makes no cudaMalloc,
  * cudaMallocAsync or cudaFree and no torch allocation. Sizes whose workspace exceeds

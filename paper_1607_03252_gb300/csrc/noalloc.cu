@@ -62,8 +62,10 @@ extern "C" int mg_solve_batch_noalloc(const mg_cfg* cfg, int batch, int n, const
       cfg->max_cycles > 1000 || !(cfg->rtol < 1.0) ||
       (cfg->precision != MLMC_PREC_F64 && cfg->precision != MLMC_PREC_MIXED) ||
       cfg->smoother < MLMC_SMOOTH_AUTO || cfg->smoother > MLMC_SMOOTH_NODAL ||
-      (cfg->accel != MLMC_ACCEL_NONE && cfg->accel != MLMC_ACCEL_CG)) {
-    set_error("mg_solve_batch_noalloc: invalid mg_cfg");
+      (cfg->accel != MLMC_ACCEL_NONE && cfg->accel != MLMC_ACCEL_CG) ||
+      (cfg->disc != MLMC_DISC_FV && cfg->disc != MLMC_DISC_FE) ||
+      (cfg->disc == MLMC_DISC_FE && cfg->precision != MLMC_PREC_F64)) {
+    set_error("mg_solve_batch_noalloc: invalid mg_cfg (FMG is not offered here; P1 elements need FP64)");
     return MLMC_ERR_INVALID;
   }
   if (!valid_grid(n) || batch < 1 || batch > 65535) {

@@ -127,3 +127,12 @@ def test_fe_and_fmg_cfg_rejected_on_host():
     st = L.mg_solve_batch(ctypes.byref(fmg), 1, 9, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), None,
                           None)
     assert st == mg.MLMC_ERR_INVALID  # FMG solves f = 1 only
+
+
+def test_noalloc_rejects_unsupported_cfgs_on_host():
+    L = mg.lib()
+    for cfg in (mg.mg_cfg(accel=mg.MLMC_ACCEL_FMG, disc=mg.MLMC_DISC_FE), mg.mg_cfg(disc=5),
+                mg.mg_cfg(precision=mg.MLMC_PREC_MIXED, disc=mg.MLMC_DISC_FE)):
+        st = L.mg_solve_batch_noalloc(ctypes.byref(cfg), 1, 9, ctypes.c_void_p(8), None, ctypes.c_void_p(8), None,
+                                      None)
+        assert st == mg.MLMC_ERR_INVALID
