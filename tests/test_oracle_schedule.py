@@ -59,6 +59,7 @@ def test_optimal_s0_schedule_paper_example():
     assert need > 8192
     T, N_lt, procs = planner.hetero_exact(N_EX, [[r[0]] for r in T_EX], 8192, 1)
     assert T == 684 and procs == 7783
+    assert [row[0] for row in N_lt] == alloc  # the paper's allocation itself
 
 
 def test_exact_s4_schedule_beats_the_annealing_result():
