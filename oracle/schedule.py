@@ -55,6 +55,14 @@ def theta_homogeneous(N_l, l, S, P_max, P0_min, t_row=None, B=None):
     return max(th for th in range(S + 1) if vals[th] <= m * (1 + 1e-12))
 
 
+def sync_makespan(times, J):
+    """Steps of J samples, each as slow as its slowest sample, one after the other."""
+    total = 0.0
+    for start in range(0, len(times), J):
+        total += max(times[start:start + J])
+    return total
+
+
 def static_makespan(times, J):
     """Block j computes samples j, j + J, j + 2J, ...; the run-time is the slowest block's."""
     sums = [0.0] * J

@@ -128,6 +128,12 @@ def theta_runtime_robust(N_l: int, l: int, S: int, P_max: int, P0_min: int, hist
         prev, mu = cur, 2 * mu
 
 
+def sync_makespan(times: Sequence[float], J: int) -> float:
+    """SaSyHom: the samples run in steps of J at a time with a synchronisation after each
+    step; the run-time is the sum over the steps of the slowest sample of the step."""
+    return math.fsum(max(times[i:i + J]) for i in range(0, len(times), J))
+
+
 def static_makespan(times: Sequence[float], J: int) -> float:
     """LeSyHom without synchronisation: block j runs samples j, j + J, j + 2J, ... back to back."""
     return max(math.fsum(times[j::J]) for j in range(min(J, len(times))))

@@ -131,3 +131,32 @@ def test_runtime_robust_equals_homogeneous_for_constant_times():
         a = planner.theta_runtime_robust(Nl, l, 4, 65536, 16, [10.0] * 20, B=0.02, seed=1)
         b = planner.theta_homogeneous(Nl, l, 4, 65536, 16, B=0.02)
         assert a == b
+
+
+def test_runtime_variation_example_of_sec_5_2():
+    """Sec. 5.2: 2048 level-0 samples on 512-processor blocks of a 524288-processor machine
+    (two sequential steps), 3 of them slow (50 s against 45 s). Sample-synchronous steps
+    take 100 s unless all three slow samples share a step: probability
+    1 - 2 C(1024,3) / C(2048,3) = 0.750 ("about 75%"); level-synchronous blocks take 100 s
+    only if two slow samples share a block: 1 - 2044/2047 = 0.15% ("less than 1%"), and
+    95 s otherwise ("<= 96 s")."""
+    J, k, _ = osch.seq_steps(2048, 0, 0, 524288, 512)
+    assert (J, k) == (1024, 2)
+    p_sync = 1 - 2 * math.comb(1024, 3) / math.comb(2048, 3)
+    p_level = 1 - 2044 / 2047
+    assert p_sync == pytest.approx(0.7504, abs=1e-4) and p_level < 0.01
+    rng = random.Random(17)
+    base = [45.0] * 2045 + [50.0] * 3
+    hits_sync = hits_level = 0
+    trials = 4000
+    for _ in range(trials):
+        times = base[:]
+        rng.shuffle(times)
+        s = planner.sync_makespan(times, J)
+        assert s == osch.sync_makespan(times, J) and s in (95.0, 100.0)
+        hits_sync += s == 100.0
+        lv = planner.static_makespan(times, J)
+        assert lv == osch.static_makespan(times, J) and lv <= 100.0
+        hits_level += lv == 100.0
+    assert abs(hits_sync / trials - p_sync) < 5 * math.sqrt(p_sync * (1 - p_sync) / trials)
+    assert abs(hits_level / trials - p_level) < 5 * math.sqrt(p_level * (1 - p_level) / trials) + 1 / trials
