@@ -40,9 +40,10 @@ Parity status (each item's pin lives in tests/test_oracle_*.py):
                        this mesh, the constant-k Laplacian, the patch test, O(h^2)
                        manufactured convergence, exact linear prolongation, FMG's algebraic
                        error far below the discretisation error, and closed-form QoIs;
-  scheduling model     pinned by the paper's worked example (716 s, 684 s on 7783
-                       processors, two sequential steps at 524288 processors) and closed
-                       forms of the Amdahl surrogate;
+  scheduling model     pinned by the paper's worked examples (716 s; 684 s with the
+                       allocation (1031, 172, 36, 6) on 7783 processors; two sequential
+                       steps at 524288 processors and Sec. 5.2's 75% / below-1% chances of
+                       the slow run) and closed forms of the Amdahl surrogate;
   Algorithm 2          pinned by hand-worked level counts of synthetic samplers (the
                        eps_b / eps and alpha choices each change them) and by the
                        stopping invariants (Eq. 10 sampling variance <= eps_s^2, the bias
