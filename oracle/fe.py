@@ -111,29 +111,31 @@ def solve_direct(n, k, f=1.0):
 @functools.lru_cache(maxsize=None)
 def prolongation(nc):
     """P1 interpolation from grid nc to grid 2 nc - 1: each fine node's value is the coarse
-    P1 function at that point (the Kuhn tetrahedron containing it, barycentric weights)."""
+    P1 function at that point (the Kuhn tetrahedron containing it, barycentric weights),
+    evaluated for all fine nodes at once."""
     nf = 2 * nc - 1
+    Zf, Yf, Xf = np.meshgrid(np.arange(nf), np.arange(nf), np.arange(nf), indexing="ij")
+    x = np.stack([Xf.ravel(), Yf.ravel(), Zf.ravel()], -1) / 2.0  # coarse index units (x, y, z)
+    o = np.minimum(np.floor(x).astype(int), nc - 2)
+    loc = x - o
+    order = np.argsort(-loc, axis=1, kind="stable")  # x_a >= x_b >= x_c per node
+    srt = np.take_along_axis(loc, order, axis=1)
+    lam = np.stack([1.0 - srt[:, 0], srt[:, 0] - srt[:, 1], srt[:, 1] - srt[:, 2], srt[:, 2]], -1)
+    verts = [o.copy()]
+    v = o.copy()
+    for step in range(3):
+        v = v.copy()
+        v[np.arange(len(v)), order[:, step]] += 1
+        verts.append(v)
+    fine = node_index(nf, Xf.ravel(), Yf.ravel(), Zf.ravel())
     rows, cols, vals = [], [], []
-    for kz in range(nf):
-        for jy in range(nf):
-            for ix in range(nf):
-                x = np.array([ix, jy, kz]) / 2.0  # coarse index units
-                o = np.minimum(np.floor(x).astype(int), nc - 2)
-                loc = x - o
-                order = np.argsort(-loc, kind="stable")  # x_a >= x_b >= x_c
-                la, lb, lc = loc[order]
-                lam = [1.0 - la, la - lb, lb - lc, lc]
-                v = o.copy()
-                verts = [v.copy()]
-                for ax in order:
-                    v[ax] += 1
-                    verts.append(v.copy())
-                for w, vv in zip(lam, verts):
-                    if w != 0.0:
-                        rows.append(node_index(nf, ix, jy, kz))
-                        cols.append(node_index(nc, *vv))
-                        vals.append(w)
-    return sp.csr_matrix((vals, (rows, cols)), shape=(nf ** 3, nc ** 3))
+    for w, vv in zip(lam.T, verts):
+        keep = w != 0.0
+        rows.append(fine[keep])
+        cols.append(node_index(nc, vv[keep, 0], vv[keep, 1], vv[keep, 2]))
+        vals.append(w[keep])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(nf ** 3, nc ** 3))
 
 
 class Level:
