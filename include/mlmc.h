@@ -164,7 +164,7 @@ typedef struct {
 
 /*
  * mlmc_field_eval -- the coefficient of the realisations `sample_ids_host[0..batch)`
- * (Algorithm 1, step 1.a.i: "set up the problem for omega^i") at the n^3 nodes of
+ * (the coefficient of one realisation in Algorithm 1) at the n^3 nodes of
  * one grid. Writes k = exp(log k) into k_out (device, batch * n^3 elements of type
  * `dtype`: MLMC_F64, or MLMC_F32 = the FP64 value rounded to FP32). The phase is
  * always evaluated in FP64. sample_ids_host is host memory, read before return.
@@ -178,7 +178,7 @@ int mlmc_field_eval(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, 
 /*
  * mlmc_field_eval_pair -- as mlmc_field_eval, for grid n as one grid of the level pair
  * whose fine grid is n_fine (n_fine = n: the fine grid itself; n_fine = 2n - 1: the
- * coarse grid of the pair, Algorithm 1, step 1.a.ii on the same realisation). Fourier-
+ * coarse grid of the pair, solved on the same realisation in Algorithm 1). Fourier-
  * feature fields are functions of x, so the result does not depend on n_fine; the SPDE
  * field of the coarse grid solves the coarse discretisation with the fine grid's white
  * noise. Errors: as mlmc_field_eval, and MLMC_ERR_INVALID for another n_fine;
@@ -189,7 +189,7 @@ int mlmc_field_eval_pair(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_h
 
 /*
  * mg_solve_batch -- solve A u = f for `batch` independent samples on one grid size n
- * (the deterministic solve of Algorithm 1, step 1.a.ii) by V(nu1,nu2) cycles.
+ * (the deterministic solves inside every sample of Algorithm 1) by V(nu1,nu2) cycles.
  *   k  device, FP64, batch * n^3: nodal coefficient (all nodes used, k > 0);
  *   f  device, FP64, batch * n^3: right-hand side at interior nodes, or NULL for f = 1;
  *   u  device, FP64, batch * n^3: initial guess in, solution out (boundary set to 0);
@@ -209,9 +209,10 @@ int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const d
 
 /*
  * mg_solve_batch_noalloc -- mg_solve_batch for callers that cannot allocate device
- * memory (code running under another framework's allocator or a fixed device-memory
- * budget, tools that forbid allocation calls while they record GPU work). The paper
- * has no counterpart; this is an interface variant only, with the same arguments,
+ * memory: code running inside another framework whose memory pool or allocator hooks
+ * own every device allocation, or an embedded runtime with a fixed device-memory budget
+ * set at start-up. The paper has no counterpart; this is an interface variant only, with
+ * the same arguments,
  * numerics and results as mg_solve_batch, except that the FMG cycle (MLMC_ACCEL_FMG) is
  * not offered here (MLMC_ERR_INVALID).
  * The workspace is a fixed 32 MiB array in the library's device image (every GPU that
@@ -220,11 +221,13 @@ int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const d
  * 32 MiB (about 75 samples at 17^3, 11 at 33^3, 1 at 65^3 in FP64) return
  * MLMC_ERR_INVALID with the required size in mlmc_last_error_string().
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * once for that device; make that first call before any stream capture.
+ * once for that device and keeps it for the life of the process (not refreshed after
+ * cudaDeviceReset); make that first call before any stream capture.
  * Every call reuses the same array, which keeps the previous call's contents; the
- * solver initialises every part it reads. Calls in one process are serialised by a
- * lock and each call is blocking; calls whose GPU work overlapped would race on the
- * shared array.
+ * solver initialises every part it reads. Blocking: the call synchronises `stream`
+ * (also when it fails), and it reads convergence data back to the host once per cycle.
+ * Calls in one process are serialised by a lock; calls whose GPU work overlapped would
+ * race on the shared array.
  */
 int mg_solve_batch_noalloc(const mg_cfg* cfg, int batch, int n, const double* k, const double* f, double* u,
                            mg_stats* stats_host, void* stream);
@@ -264,7 +267,8 @@ typedef struct {
 
 /*
  * mlmc_level_estimate -- N samples of Y_level with realisation ids first_id ..
- * first_id + N - 1 (Algorithm 1, step 1.a for one level; step 1.b for `out`).
+ * first_id + N - 1 (Algorithm 1 for one level: the samples, and their mean and
+ * variance in `out`).
  * For level 0, Y = Q_0 on grid n0; for level l >= 1 the fine grid has
  * n_l = (n0 - 1) 2^l + 1 nodes and the coarse grid n_{l-1}, both solved on the field
  * of the same id; the coarse solve runs first and the trilinear interpolation of its

@@ -45,7 +45,7 @@ def adaptive_mlmc(sample_Y: Callable[[int, int, int], List[float]], cost: Callab
         means = [stats.level_mean(Y[l]) for l in range(L + 1)]
         s2 = [stats.level_var_unbiased(Y[l]) for l in range(L + 1)]
         C = [float(cost(l)) for l in range(L + 1)]
-        # step 3: Eq. 15, then the bias test of Eq. 14
+        # new sample sizes by Eq. 15, then the bias test of Eq. 14
         N_opt = stats.optimal_N([max(v, 1e-30) for v in s2], C, eps_s)
         N_new = [max(N[l], max(2, N_opt[l])) for l in range(L + 1)]
         a = _alpha(alpha, alpha0, alpha_floor, means)
@@ -56,7 +56,7 @@ def adaptive_mlmc(sample_Y: Callable[[int, int, int], List[float]], cost: Callab
             L += 1
             N_new.append(N_init)
             Y.append([])
-        # step 4
+        # stop when nothing changes
         if not grow and N_new == N:
             break
         N = N_new

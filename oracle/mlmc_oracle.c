@@ -8,7 +8,7 @@
  * What it computes, following Gmeiner, Drzisga, Ruede, Scheichl, Wohlmuth,
  * "Scheduling massively parallel multigrid for multilevel Monte Carlo methods":
  *   - one sample Y_l = Q_l - Q_{l-1} of the MLMC level difference, both solves on the
- *     same random coefficient sample (Sec. 2.2, Eq. 8 and Algorithm 1, steps 1.a.i-ii);
+ *     same random coefficient sample (Sec. 2.2, Eq. 8 and Algorithm 1);
  *   - the model problem -div(k grad u) = f on D = (0,1)^3 with homogeneous Dirichlet
  *     data (Sec. 3, Eq. 16), with a lognormal coefficient k = exp(Z) (Sec. 3.2);
  *   - the deterministic solve by geometric multigrid (Sec. 7.1 names the cycle family).
@@ -126,7 +126,7 @@ static double uniform53(uint32_t a, uint32_t b) {
 }
 
 /* ------------------------------------------------------------------------------------
- * Random features of one sample (the realisation omega of Algorithm 1, step 1.a.i).
+ * Random features of one sample (the realisation omega of one sample of Algorithm 1).
  * Philox key = (run_seed low word, run_seed high word); for feature m and block
  * c = 0,1,2 the counter is (id low word, id high word, m, c). The 12 words give six
  * uniforms U1..U6 from consecutive word pairs; Box-Muller turns (U1,U2) and (U3,U4)
@@ -777,7 +777,7 @@ done:
 }
 
 /* ------------------------------------------------------------------------------------
- * One MLMC sample (Algorithm 1, steps 1.a.i-ii): set up the coefficient of the
+ * One MLMC sample (Algorithm 1): set up the coefficient of the
  * realisation `sample_id` on the fine grid n_fine and (if n_coarse > 0) on the
  * coarse grid n_coarse, solve both with f = 1, and return Q on each grid.
  * Each grid evaluates the field at its own nodes.

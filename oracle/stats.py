@@ -10,7 +10,7 @@ from typing import Sequence
 
 
 def level_mean(Y: Sequence[float]) -> float:
-    """Y-hat_l = (1/N) sum_i Y_l^i (Sec. 2.2, Algorithm 1 step 1.b; Eq. 3 on one level)."""
+    """Y-hat_l = (1/N) sum_i Y_l^i (Sec. 2.2, Algorithm 1's level mean; Eq. 3 on one level)."""
     return math.fsum(Y) / len(Y)
 
 

@@ -129,7 +129,7 @@ static int device_ready() {
   return MLMC_OK;
 }
 
-// Running statistics of one MLMC level in device memory (Algorithm 1, step 1.b):
+// Running statistics of one MLMC level in device memory (the level mean and variance of Algorithm 1):
 // Kahan-compensated sum and Welford mean / M2 of Y, accumulated sequentially in
 // sample-id order, so the record does not depend on how the samples were batched.
 struct LevelRecord {

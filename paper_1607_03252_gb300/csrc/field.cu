@@ -1,6 +1,6 @@
 // Lognormal random-field evaluation (K1 feature draw, K2 field evaluation).
 //
-// The coefficient of one realisation omega (Algorithm 1, step 1.a.i; lognormal k =
+// The coefficient of one realisation omega (one sample of Algorithm 1; lognormal k =
 // exp(Z) of Sec. 3.2) is log k(x) = sigma sqrt(2/M) sum_m cos(w_m . x + b_m).
 // On the structured grid every node is x = (i h, j h, k h), so each term factorises:
 //   cos(w.x + b) = Re( e^{i(w_1 x_i + b)} e^{i w_2 y_j} e^{i w_3 z_k} ).

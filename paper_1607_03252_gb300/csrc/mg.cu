@@ -1,6 +1,6 @@
 // Batched geometric multigrid: V(nu1, nu2) cycles with red-black Gauss-Seidel, full
 // weighting, trilinear prolongation, rediscretised coarse operators and an exact 5^3
-// solve (the deterministic solver of Algorithm 1, step 1.a.ii, for the model problem
+// solve (the deterministic solver inside every sample of Algorithm 1, for the model problem
 // of Sec. 3, Eq. 16; the cycle family of Sec. 7.1).
 //
 // Scaled form. With faces K_pq = 2 k_p k_q / (k_p + k_q) and D_p = sum_q K_pq, every

@@ -1,9 +1,9 @@
 // mg_solve_batch_noalloc: the batched multigrid solve of mg_solve_batch for callers
 // that cannot allocate device memory -- for example code running inside another
-// framework's memory pool or allocator hooks, a CUDA-graph-building tool that forbids
-// allocation calls, or an embedded runtime with a fixed device-memory budget. Its
-// workspace is a fixed array in this library's device image instead of a
-// cudaMallocAsync block; the caller still owns k, f and u.
+// framework whose memory pool or allocator hooks own every device allocation, or an
+// embedded runtime with a fixed device-memory budget set at start-up. Its workspace is
+// a fixed array in this library's device image instead of a cudaMallocAsync block; the
+// caller still owns k, f and u.
 #include <mutex>
 #include <vector>
 
@@ -22,7 +22,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
 
-// Device address of the array on the current device, looked up once per device.
+// Device address of the array on the current device, looked up once per device and
+// kept for the life of the process (the first call on a device does the look-up). The
+// cached address is not refreshed after cudaDeviceReset: a process that resets a device
+// must not call this entry point on it again.
 int workspace_address(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -96,8 +99,15 @@ extern "C" int mg_solve_batch_noalloc(const mg_cfg* cfg, int batch, int n, const
   std::vector<int> cyc(batch);
   std::vector<double> rel(batch);
   int bad = 0;
-  MLMC_TRY(mg_solve_dev(a, ws, st, cyc.data(), rel.data(), &bad));
-  MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+  // drain the stream on every path before the lock is released, so that no kernel of a
+  // failed call still writes the array while the next call uses it
+  const int rc = mg_solve_dev(a, ws, st, cyc.data(), rel.data(), &bad);
+  const cudaError_t se = cudaStreamSynchronize(st);
+  if (rc < 0) return rc;
+  if (se != cudaSuccess) {
+    set_error("cudaStreamSynchronize failed: %s", cudaGetErrorString(se));
+    return MLMC_ERR_CUDA;
+  }
   if (stats_host)
     for (int s = 0; s < batch; ++s) {
       stats_host[s].cycles = cyc[s];

@@ -110,6 +110,37 @@ def test_prolongation_reproduces_linear_functions():
     assert np.abs(P @ lin(Xc, Yc, Zc).ravel() - lin(Xf, Yf, Zf).ravel()).max() < 1e-14
 
 
+def test_prolongation_equals_node_by_node_kuhn_interpolation():
+    """The vectorised interpolation matrix against a plain loop over the fine nodes of
+    5^3 -> 9^3: per fine node, its coarse cube, the Kuhn tetrahedron holding it (the one
+    whose vertex path steps along the axes in decreasing order of the local coordinates)
+    and its barycentric weights; a coarse P1 function (random nodal values) is evaluated
+    there and compared with P applied to the same values."""
+    nc = 5
+    nf = 2 * nc - 1
+    P = fe.prolongation(nc).toarray()
+    vals = np.random.default_rng(3).standard_normal(nc ** 3)
+
+    def cidx(x, y, z):
+        return (z * nc + y) * nc + x
+
+    for z in range(nf):
+        for y in range(nf):
+            for x in range(nf):
+                p = [x / 2.0, y / 2.0, z / 2.0]
+                o = [min(int(c), nc - 2) for c in p]
+                loc = [p[a] - o[a] for a in range(3)]
+                axes = sorted(range(3), key=lambda a: -loc[a])
+                w = [1.0 - loc[axes[0]], loc[axes[0]] - loc[axes[1]], loc[axes[1]] - loc[axes[2]], loc[axes[2]]]
+                v = list(o)
+                ref = w[0] * vals[cidx(*v)]
+                for step in range(3):
+                    v[axes[step]] += 1
+                    ref += w[step + 1] * vals[cidx(*v)]
+                got = P[(z * nf + y) * nf + x] @ vals
+                assert abs(got - ref) <= 1e-14 * (1 + abs(ref))
+
+
 def test_fmg_reaches_discretisation_accuracy(kfield):
     """One FMG-2V(4,4) cycle leaves an algebraic error far below the discretisation error
     (the property the paper relies on, Sec. 7): at 17^3, 4.6e-4 against 2.2e-2 (the

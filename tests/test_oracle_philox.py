@@ -3,9 +3,17 @@
 Philox4x32-10 and Philox4x64-10 share one round structure (Salmon et al., SC'11):
 the 64-bit variant is checked word for word against numpy's independent
 implementation, which pins the round, the key schedule and the role of each counter
-word. The 32-bit constants themselves are pinned only statistically.
+word. The 32-bit variant (its multipliers and Weyl constants included) is checked word
+for word against PyTorch's independent host implementation (at::philox_engine, a
+header of the installed torch, compiled here with g++), whose key is the 64-bit seed
+and whose counter words are (offset low, offset high, subsequence low, subsequence
+high): the method's counter (id low, id high, m, c) is offset = id, subsequence =
+m + 2^32 c.
 """
 import math
+import os
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -25,6 +33,54 @@ def test_philox4x64_matches_numpy(orc, key, start):
             if ctr[w] != 0:
                 break
         assert orc.philox4x64(ctr, key) == raw[4 * blk: 4 * blk + 4]
+
+
+_ATEN_PROBE = r"""
+#include <ATen/core/PhiloxRNGEngine.h>
+#include <cstdio>
+#include <cstdlib>
+int main(int argc, char** argv) {
+  for (int a = 1; a + 2 < argc; a += 3) {
+    at::philox_engine e(strtoull(argv[a], 0, 0), strtoull(argv[a + 1], 0, 0), strtoull(argv[a + 2], 0, 0));
+    for (int i = 0; i < 4; ++i) printf("%u\n", e());
+  }
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def aten_philox(tmp_path_factory):
+    """Runs PyTorch's host Philox4x32-10 for (seed, subsequence, offset) triples."""
+    torch = pytest.importorskip("torch")
+    inc = os.path.join(os.path.dirname(torch.__file__), "include")
+    if not os.path.exists(os.path.join(inc, "ATen", "core", "PhiloxRNGEngine.h")) or not shutil.which("g++"):
+        pytest.skip("no at::philox_engine header or no g++")
+    d = tmp_path_factory.mktemp("aten_philox")
+    src, exe = d / "probe.cpp", d / "probe"
+    src.write_text(_ATEN_PROBE)
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", inc, str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+
+    def run(triples):
+        args = [str(x) for t in triples for x in t]
+        out = subprocess.run([str(exe), *args], check=True, capture_output=True, text=True).stdout.split()
+        words = [int(x) for x in out]
+        return [words[4 * i: 4 * i + 4] for i in range(len(triples))]
+
+    return run
+
+
+def test_philox4x32_matches_aten_word_for_word(orc, aten_philox):
+    seeds = [0, 1607032520, 0x123456789ABCDEF0, 2**64 - 1]
+    ctrs = [(0, 0, 0, 0), (5, 0, 0, 0), ((1 << 48) | 77, 0, 3, 1), (2**64 - 1, 0, 255, 2), (12345, 0, 2**32 - 1,
+                                                                                               2**32 - 1)]
+    triples, expect = [], []
+    for seed in seeds:
+        for ident, _, m, c in ctrs:
+            triples.append((seed, m | (c << 32), ident))
+            expect.append(orc.philox4x32([ident & 0xFFFFFFFF, ident >> 32, m, c], [seed & 0xFFFFFFFF, seed >> 32]))
+    assert aten_philox(triples) == expect
 
 
 def test_philox4x32_bits_balanced(orc):

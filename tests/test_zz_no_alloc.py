@@ -33,8 +33,7 @@ def test_noalloc_matches_allocating_solve_twice(prec):
         f = torch.from_numpy(np.stack([random_rhs(n, seed + 50 + s) for s in range(B)])).cuda()
         u_ref = torch.zeros_like(k)
         cyc_ref, rel_ref, st_ref = mg.mg_solve_batch(cfg, k, u_ref, f)
-        u = torch.full_like(k, 7.0)  # arbitrary initial guess contents are overwritten
-        u.zero_()
+        u = torch.zeros_like(k)  # the same (zero) initial guess as the allocating solve
         st, cyc, rel = _noalloc(cfg, k, u, f)
         torch.cuda.synchronize()
         assert st == mg.MLMC_OK == st_ref
