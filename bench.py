@@ -123,8 +123,6 @@ def workload(cfg_name):
 def plan_levels(mg, cfg, levels, stream, rank):
     """Mixed-precision workloads: autotune each level (smoother x nu), run the pilot
     N_init, and size N_l by Eq. 11 for the configured eps (theta split of Eq. 6)."""
-    import math
-
     prec = mg.MLMC_PREC_MIXED
     accel = mg.MLMC_ACCEL_CG if cfg.get("accel") == "cg" else mg.MLMC_ACCEL_NONE
     tune, V, C = {}, [], []
@@ -137,9 +135,9 @@ def plan_levels(mg, cfg, levels, stream, rank):
                                              want_samples=False)
         V.append(max(st.var_unbiased, 1e-30))
         C.append(st.cost_per_sample)
-    eps_s = math.sqrt(cfg["theta"]) * cfg["eps"]
-    total = sum(math.sqrt(v * c) for v, c in zip(V, C))
-    N = [max(2, int(math.ceil(total * math.sqrt(v / c) / eps_s ** 2))) for v, c in zip(V, C)]
+    from paper_1607_03252_gb300.stats import sample_sizes
+
+    N = sample_sizes(V, C, cfg["eps"], cfg["theta"])  # Eq. 11 in the library
     return N, {"pilot_N": cfg["N_init"], "pilot_var": V, "pilot_cost_s": C, "eps": cfg["eps"],
                "theta": cfg["theta"], "N_from_eq11": N, "autotune": tune}
 

@@ -70,6 +70,7 @@ extern "C" {
 #define MLMC_ERR_CUDA (-5)
 #define MLMC_ERR_BUSY (-6)
 #define MLMC_ERR_NOT_FOUND (-7)
+#define MLMC_ERR_CANCELLED (-8)
 
 /* ---- element types of grid buffers ---- */
 #define MLMC_F64 0
@@ -294,6 +295,116 @@ int mlmc_level_run(const mlmc_cfg* cfg, int level, const uint64_t* ids_dev, int 
                    double* Qc_dev, mlmc_level_stats* out);
 
 /*
+ * Adaptive MLMC (Algorithm 2 of Sec. 2.4) on levels 0..L, with optional level growth.
+ *
+ * Each round (mlmc_adaptive_step) computes the missing samples of every level -- sample i
+ * of level l is the realisation id (l << 48) | i, in order, through the level pipeline of
+ * mlmc_level_estimate with cfg.level (or through a caller's sampler, below) -- folds them
+ * into the level's running record (Chan's merge of (N, mean, M2): Y-hat_l and s_l^2 of
+ * Sec. 2.3, s_l^2 with 1/(N-1)), takes C_l (measured wall seconds per sample, or the node
+ * count n_l^3 + n_{l-1}^3), and sets N_l = ceil(eps_s^-2 (sum_k sqrt(s_k^2 C_k))
+ * sqrt(s_l^2 / C_l)), at least 2 (Eqs. 11 / 15; eps_s^2 = theta eps^2, eps_b^2 = (1 - theta)
+ * eps^2, Eq. 6). Samples already computed are kept (N_l never decreases). With
+ * max_level > L0 the bias estimate |Y-hat_L| / (8^alpha - 1) of Eq. 14 is compared with
+ * eps_b after each round; while it is larger and L < max_level, level L + 1 joins with its
+ * pilot count. A round that changes neither N_l nor L ends the run (*finished = 1).
+ * alpha: cfg.alpha if > 0, else minus the least-squares slope of log_8 |Y-hat_l| over the
+ * levels l >= 1 with samples (M_l ~ 8^l), alpha0 while fewer than two such levels exist,
+ * never below alpha_floor; beta and gamma (Eq. 12) are fitted the same way from s_l^2 and
+ * C_l and only reported (NAN where no fit exists).
+ * With lanes > 1 the levels of a round run concurrently, one host thread and one stream
+ * per lane (lane_streams[k]; lane 0 uses cfg.level.stream when lane_streams[0] is NULL),
+ * levels placed longest first (count x node cost) onto the least-loaded lane; the records
+ * do not depend on the lanes. Blocking calls; one handle must not be stepped from two
+ * threads at once.
+ */
+#define MLMC_MAX_LEVELS 9
+#define MLMC_COST_MEASURED 0 /* C_l = wall seconds per sample of the level's calls */
+#define MLMC_COST_NODES 1    /* C_l = n_l^3 + n_{l-1}^3 (deterministic decisions) */
+
+typedef struct {
+  mlmc_cfg level;                   /* field, solver, n0, max_batch, stream and QoI of the level calls */
+  int L0;                           /* levels 0..L0 at the start, 0 <= L0 <= 8 */
+  int max_level;                    /* L0 <= max_level <= 8; > L0 enables level growth (then L0 >= 1) */
+  int64_t N_init[MLMC_MAX_LEVELS];  /* pilot count per level (>= 1 for 0..L0; a grown level without
+                                       an entry (0) takes the previous level's) */
+  double eps;                       /* RMS tolerance, > 0 */
+  double theta;                     /* 0 < theta < 1 (Eq. 6) */
+  int cost_model;                   /* MLMC_COST_MEASURED or MLMC_COST_NODES */
+  double alpha;                     /* > 0: fixed; <= 0: fitted online */
+  double alpha0;                    /* alpha before two levels l >= 1 have samples (fitted mode), > 0 */
+  double alpha_floor;               /* lower bound of the fitted alpha, >= 0 */
+  int lanes;                        /* 0 or 1: levels in sequence; up to 8 concurrent lanes */
+  void* lane_streams[8];            /* cudaStream_t per lane (lanes 1.. must be created streams) */
+} mlmc_adaptive_cfg;
+
+/* One round of the run (what the round saw and decided). */
+typedef struct {
+  int round, L, grow;
+  int64_t have[MLMC_MAX_LEVELS];   /* samples per level after the round's computation */
+  int64_t N_next[MLMC_MAX_LEVELS]; /* Eq. 15 counts from the round's statistics */
+  double alpha, bias;              /* alpha used by the bias test, the Eq. 14 estimate */
+} mlmc_adaptive_round;
+
+/* Result of the run so far. */
+typedef struct {
+  int L, rounds, bias_ok;          /* bias_ok: the Eq. 14 estimate <= eps_b */
+  double Q_hat;                    /* sum of the level means (Eq. 8), compensated sum */
+  double sampling_var;             /* sum_l s_l^2 / N_l (Eq. 10) */
+  double eps_s2;                   /* theta eps^2 */
+  double alpha, beta, gamma, bias;
+  int64_t N[MLMC_MAX_LEVELS];
+  double mean[MLMC_MAX_LEVELS], var[MLMC_MAX_LEVELS], M2[MLMC_MAX_LEVELS];
+  double cost[MLMC_MAX_LEVELS], seconds[MLMC_MAX_LEVELS];
+} mlmc_adaptive_summary;
+
+/* Resumable state (plain data: the caller may store it anywhere). The round log is not
+ * part of it. */
+typedef struct {
+  uint32_t magic, version;
+  int L, rounds;
+  int64_t have[MLMC_MAX_LEVELS], target[MLMC_MAX_LEVELS];
+  double N[MLMC_MAX_LEVELS], mean[MLMC_MAX_LEVELS], M2[MLMC_MAX_LEVELS], seconds[MLMC_MAX_LEVELS];
+} mlmc_adaptive_state;
+
+/* A caller's sampler of level l, used instead of the library's level pipeline: the
+ * record (N = count, mean, M2 = sum of squared deviations) of samples first_index ..
+ * first_index + count - 1 of level l. Returns MLMC_OK or a negative status (the step
+ * then fails with it). */
+typedef int (*mlmc_level_sampler)(void* user, int level, uint64_t first_index, int64_t count, double* N,
+                                  double* mean, double* M2);
+
+typedef struct mlmc_adaptive mlmc_adaptive;
+
+/* Eq. 11 / Eq. 15 on their own: N_out[l] = ceil(eps_s^-2 (sum_k sqrt(var_k cost_k))
+ * sqrt(var_l / cost_l)), at least 2, eps_s = sqrt(theta) eps (Eq. 6), for `levels` levels
+ * (1..64) with positive variances and costs. Host-only. */
+int mlmc_sample_sizes(const double* var, const double* cost, int levels, double eps, double theta, int64_t* N_out);
+/* Chan et al.'s pairwise merge, in the given order, of `count` records (N, mean, M2) of
+ * disjoint sample sets (records: count x 3 doubles) into out[3] = (N, mean, M2): how the
+ * level records of replicas, lanes or chunks are combined. Host-only. */
+int mlmc_merge_records(const double* records, int count, double* out);
+
+/* NULL on an invalid cfg (mlmc_last_error_string says why). Host-only. */
+mlmc_adaptive* mlmc_adaptive_create(const mlmc_adaptive_cfg* cfg);
+void mlmc_adaptive_destroy(mlmc_adaptive* est);
+/* fn = NULL restores the library's level pipeline. */
+int mlmc_adaptive_set_sampler(mlmc_adaptive* est, mlmc_level_sampler fn, void* user);
+/* One round; *finished = 1 when it changed neither N_l nor L. Errors of the level calls
+ * (MLMC_ERR_NOT_CONVERGED, _OOM, _CUDA, ...) or of the sampler are returned. */
+int mlmc_adaptive_step(mlmc_adaptive* est, int* finished);
+/* Rounds until finished or max_rounds (>= 1); *finished may be NULL. */
+int mlmc_adaptive_run(mlmc_adaptive* est, int max_rounds, int* finished);
+int mlmc_adaptive_result(const mlmc_adaptive* est, mlmc_adaptive_summary* out);
+int mlmc_adaptive_log_count(const mlmc_adaptive* est);
+int mlmc_adaptive_log_get(const mlmc_adaptive* est, int index, mlmc_adaptive_round* out);
+/* Checkpoint / resume: a state taken after any round, set into a handle created with the
+ * same cfg, continues exactly as the uninterrupted run (same ids, same records).
+ * MLMC_ERR_INVALID for a state that does not fit the handle's cfg. */
+int mlmc_adaptive_get_state(const mlmc_adaptive* est, mlmc_adaptive_state* out);
+int mlmc_adaptive_set_state(mlmc_adaptive* est, const mlmc_adaptive_state* state);
+
+/*
  * Launch accounting (no counterpart in the paper; measurement support). The library
  * counts every kernel launch per kernel class with the algorithmic bytes and flops of
  * that launch. After mlmc_profile_enable(1) it also records a CUDA event pair around
@@ -308,6 +419,11 @@ int mlmc_profile_count(void);
 int64_t mlmc_profile_total_launches(void);
 int mlmc_profile_get(int index, char* name, int name_len, int64_t* launches, int64_t* timed_launches, double* ms,
                      double* bytes, double* flops);
+/* Measured FMA throughput of the current device: *tflops = 2 x FMAs per second / 1e12 of
+ * a probe kernel with 8 independent FMA chains per thread on 8 CTAs of 256 threads per SM,
+ * best of four timed launches (CUDA events on the legacy default stream). precision:
+ * MLMC_PREC_F64 (FP64 FMA) or MLMC_PREC_MIXED (FP32 FMA). Blocking. */
+int mlmc_profile_fma_peak(int precision, double* tflops);
 
 /*
  * Solve service with continuous batching (the single-GPU counterpart of the paper's
@@ -348,6 +464,7 @@ typedef struct {
 
 typedef struct {
   int64_t submitted, completed, rejected, pending;
+  int64_t cancelled;         /* requests withdrawn by mlmc_cancel before they ran */
   int inflight_batches;
   size_t bytes_in_use;
   double samples_per_s;      /* completed / (last completion - first submission) */
@@ -370,6 +487,12 @@ int mlmc_submit(mlmc_service* svc, const mlmc_request* req, uint64_t* ticket);
 int mlmc_poll(mlmc_service* svc, uint64_t ticket, mlmc_result* res);
 /* Blocks up to timeout_ms; MLMC_ERR_TIMEOUT if still pending. */
 int mlmc_wait(mlmc_service* svc, uint64_t ticket, double timeout_ms, mlmc_result* res);
+/* Withdraws a request that is still queued: it will not run, and mlmc_poll / mlmc_wait
+ * then deliver it once with status MLMC_ERR_CANCELLED (so no waiter is left blocked).
+ * Returns MLMC_OK if it was withdrawn; MLMC_ERR_BUSY if its batch is already running or
+ * finished (its result is delivered as usual); MLMC_ERR_NOT_FOUND for an unknown or
+ * already delivered ticket. Non-blocking; no counterpart in the paper. */
+int mlmc_cancel(mlmc_service* svc, uint64_t ticket);
 int mlmc_service_stats(mlmc_service* svc, mlmc_service_report* out);
 
 /* One measurement of mlmc_autotune. */
@@ -410,6 +533,27 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
  * outside MLMC_SMOOTH_TWO_PASS .. MLMC_SMOOTH_NODAL, or nu outside 1..8.
  */
 int mlmc_tune_set(int n, int precision, int smoother, int nu);
+
+/*
+ * Failure-path controls (no counterpart in the paper; for tests of the error paths, and
+ * process-wide).
+ *
+ * mlmc_set_wait_budget -- every bounded wait inside a kernel (the mbarrier waits of the
+ * TMA bulk-copy smoothers) gives up after `clocks` SM clocks: the kernel then records an
+ * error word, waits (bounded by about one second, whatever `clocks` is) for the copies it
+ * still has in flight, and returns; the solve reports MLMC_ERR_TIMEOUT and the context
+ * stays usable. Default 2e9 clocks (about one second). clocks = 0 gives up at the first
+ * wait that finds its data not yet arrived. Read at each launch (a V-cycle captured as a
+ * CUDA graph keeps the budget of its capture). *previous (may be NULL) receives the old
+ * value. MLMC_ERR_INVALID for clocks < 0. Host-only.
+ *
+ * mlmc_inject_alloc_failure -- host-side fault injection: after `after` more successful
+ * device allocations of the library, every later one fails with MLMC_ERR_OOM without
+ * calling the CUDA allocator, until the next call; after = -1 turns it off (the
+ * default). MLMC_ERR_INVALID for after < -1. Host-only.
+ */
+int mlmc_set_wait_budget(int64_t clocks, int64_t* previous);
+int mlmc_inject_alloc_failure(int64_t after);
 
 /* Text of the last error on the calling thread ("" if none). Never NULL. */
 const char* mlmc_last_error_string(void);

@@ -24,6 +24,7 @@ MLMC_ERR_TIMEOUT = -4
 MLMC_ERR_CUDA = -5
 MLMC_ERR_BUSY = -6
 MLMC_ERR_NOT_FOUND = -7
+MLMC_ERR_CANCELLED = -8
 
 MLMC_F64 = 0
 MLMC_F32 = 1
@@ -46,6 +47,7 @@ _STATUS_NAMES = {
     MLMC_ERR_CUDA: "MLMC_ERR_CUDA",
     MLMC_ERR_BUSY: "MLMC_ERR_BUSY",
     MLMC_ERR_NOT_FOUND: "MLMC_ERR_NOT_FOUND",
+    MLMC_ERR_CANCELLED: "MLMC_ERR_CANCELLED",
 }
 
 
@@ -121,9 +123,49 @@ class Result(ctypes.Structure):
 
 class ServiceReport(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
-                ("pending", ctypes.c_int64), ("inflight_batches", ctypes.c_int), ("bytes_in_use", ctypes.c_size_t),
+                ("pending", ctypes.c_int64), ("cancelled", ctypes.c_int64), ("inflight_batches", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t),
                 ("samples_per_s", ctypes.c_double), ("count", ctypes.c_int64 * 9), ("p50_ms", ctypes.c_double * 9),
                 ("p99_ms", ctypes.c_double * 9)]
+
+
+MLMC_MAX_LEVELS = 9
+MLMC_COST_MEASURED = 0
+MLMC_COST_NODES = 1
+_L9 = MLMC_MAX_LEVELS
+
+
+class AdaptiveCfg(ctypes.Structure):
+    _fields_ = [("level", MlmcCfg), ("L0", ctypes.c_int), ("max_level", ctypes.c_int),
+                ("N_init", ctypes.c_int64 * _L9), ("eps", ctypes.c_double), ("theta", ctypes.c_double),
+                ("cost_model", ctypes.c_int), ("alpha", ctypes.c_double), ("alpha0", ctypes.c_double),
+                ("alpha_floor", ctypes.c_double), ("lanes", ctypes.c_int), ("lane_streams", ctypes.c_void_p * 8)]
+
+
+class AdaptiveRound(ctypes.Structure):
+    _fields_ = [("round", ctypes.c_int), ("L", ctypes.c_int), ("grow", ctypes.c_int),
+                ("have", ctypes.c_int64 * _L9), ("N_next", ctypes.c_int64 * _L9), ("alpha", ctypes.c_double),
+                ("bias", ctypes.c_double)]
+
+
+class AdaptiveSummary(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("rounds", ctypes.c_int), ("bias_ok", ctypes.c_int), ("Q_hat", ctypes.c_double),
+                ("sampling_var", ctypes.c_double), ("eps_s2", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("bias", ctypes.c_double),
+                ("N", ctypes.c_int64 * _L9), ("mean", ctypes.c_double * _L9), ("var", ctypes.c_double * _L9),
+                ("M2", ctypes.c_double * _L9), ("cost", ctypes.c_double * _L9), ("seconds", ctypes.c_double * _L9)]
+
+
+class AdaptiveState(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint32), ("version", ctypes.c_uint32), ("L", ctypes.c_int),
+                ("rounds", ctypes.c_int), ("have", ctypes.c_int64 * _L9), ("target", ctypes.c_int64 * _L9),
+                ("N", ctypes.c_double * _L9), ("mean", ctypes.c_double * _L9), ("M2", ctypes.c_double * _L9),
+                ("seconds", ctypes.c_double * _L9)]
+
+
+LEVEL_SAMPLER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64,
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double))
 
 
 class TuneEntry(ctypes.Structure):
@@ -154,17 +196,34 @@ SIGNATURES = {
     "mlmc_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "mlmc_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]),
     "mlmc_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(Result)]),
+    "mlmc_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "mlmc_service_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServiceReport)]),
+    "mlmc_set_wait_budget": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "mlmc_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64]),
     "mlmc_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mlmc_autotune": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                      ctypes.POINTER(TuneEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "mlmc_sample_sizes": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_int64)]),
+    "mlmc_merge_records": (ctypes.c_int, [_dp, ctypes.c_int, _dp]),
+    "mlmc_adaptive_create": (ctypes.c_void_p, [ctypes.POINTER(AdaptiveCfg)]),
+    "mlmc_adaptive_destroy": (None, [ctypes.c_void_p]),
+    "mlmc_adaptive_set_sampler": (ctypes.c_int, [ctypes.c_void_p, LEVEL_SAMPLER, ctypes.c_void_p]),
+    "mlmc_adaptive_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "mlmc_adaptive_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "mlmc_adaptive_result": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(AdaptiveSummary)]),
+    "mlmc_adaptive_log_count": (ctypes.c_int, [ctypes.c_void_p]),
+    "mlmc_adaptive_log_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(AdaptiveRound)]),
+    "mlmc_adaptive_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(AdaptiveState)]),
+    "mlmc_adaptive_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(AdaptiveState)]),
     "mlmc_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mlmc_profile_reset": (ctypes.c_int, []),
     "mlmc_profile_count": (ctypes.c_int, []),
     "mlmc_profile_total_launches": (ctypes.c_int64, []),
     "mlmc_profile_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp]),
+    "mlmc_profile_fma_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
     "mlmc_last_error_string": (ctypes.c_char_p, []),
     "mlmc_version": (ctypes.c_char_p, []),
 }
@@ -353,6 +412,13 @@ def profile_total_launches():
     return int(lib().mlmc_profile_total_launches())
 
 
+def profile_fma_peak(precision=MLMC_PREC_F64) -> float:
+    """Measured FMA throughput in TFLOP/s (FP64 for MLMC_PREC_F64, FP32 for MLMC_PREC_MIXED)."""
+    t = ctypes.c_double()
+    _check(lib().mlmc_profile_fma_peak(int(precision), ctypes.byref(t)), "mlmc_profile_fma_peak")
+    return t.value
+
+
 def profile_read():
     """{class: dict(launches, timed, ms, bytes, flops)} (synchronises on recorded events)."""
     L = lib()
@@ -366,6 +432,19 @@ def profile_read():
         res[name.value.decode()] = dict(launches=la.value, timed=ti.value, ms=ms.value, bytes=by.value,
                                         flops=fl.value)
     return res
+
+
+def set_wait_budget(clocks: int) -> int:
+    """Budget (SM clocks) of the kernels' bounded waits; returns the previous one."""
+    prev = ctypes.c_int64()
+    _check(lib().mlmc_set_wait_budget(int(clocks), ctypes.byref(prev)), "mlmc_set_wait_budget")
+    return prev.value
+
+
+def inject_alloc_failure(after: int):
+    """After `after` more successful device allocations every later one fails with
+    MLMC_ERR_OOM (-1: off)."""
+    _check(lib().mlmc_inject_alloc_failure(int(after)), "mlmc_inject_alloc_failure")
 
 
 def make_mlmc_cfg(run_seed, sigma2, ell, M, n0=17, nu1=2, nu2=2, rtol=1e-10, max_cycles=100,
@@ -414,6 +493,15 @@ class Service:
             return st, r
         _check(st, "mlmc_wait")
         return st, r
+
+    def cancel(self, ticket):
+        """MLMC_OK if the queued request was withdrawn, MLMC_ERR_BUSY if it already ran
+        or is running."""
+        st = lib().mlmc_cancel(self.h, int(ticket))
+        if st in (MLMC_OK, MLMC_ERR_BUSY):
+            return st
+        _check(st, "mlmc_cancel")
+        return st
 
     def report(self):
         r = ServiceReport()

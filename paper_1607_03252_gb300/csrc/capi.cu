@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <vector>
 
@@ -30,10 +31,25 @@ void set_error(const char* fmt, ...) {
 
 const char* last_error() { return g_err; }
 
+// Budget of the kernels' bounded waits (mlmc_set_wait_budget).
+static std::atomic<long long> g_wait_budget{2000000000LL};
+long long wait_budget_clocks() { return g_wait_budget.load(); }
+
+// Host-side allocation-failure injection (mlmc_inject_alloc_failure): -1 = off, else the
+// number of further allocations that still succeed before every later one fails.
+static std::atomic<long long> g_alloc_budget{-1};
+
 int DevBuf::alloc(size_t bytes, cudaStream_t st) {
   release();
   st_ = st;
   if (bytes == 0) bytes = 256;
+  for (long long b = g_alloc_budget.load(); b >= 0;) {
+    if (b == 0) {
+      set_error("cudaMallocAsync(%zu bytes) not attempted: allocation failure injected", bytes);
+      return MLMC_ERR_OOM;
+    }
+    if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+  }
   cudaError_t e = cudaMallocAsync(&p_, bytes, st);
   if (e != cudaSuccess) {
     p_ = nullptr;
@@ -379,7 +395,26 @@ extern "C" {
 
 const char* mlmc_last_error_string(void) { return last_error(); }
 
-const char* mlmc_version(void) { return "mlmc-gb300 0.1 (sm_103a)"; }
+const char* mlmc_version(void) { return "mlmc-gb300 0.2 (sm_103a)"; }
+
+int mlmc_set_wait_budget(int64_t clocks, int64_t* previous) {
+  if (clocks < 0) {
+    set_error("mlmc_set_wait_budget: clocks=%lld must be >= 0", (long long)clocks);
+    return MLMC_ERR_INVALID;
+  }
+  const long long old = g_wait_budget.exchange((long long)clocks);
+  if (previous) *previous = (int64_t)old;
+  return MLMC_OK;
+}
+
+int mlmc_inject_alloc_failure(int64_t after) {
+  if (after < -1) {
+    set_error("mlmc_inject_alloc_failure: after=%lld must be >= -1", (long long)after);
+    return MLMC_ERR_INVALID;
+  }
+  g_alloc_budget.store((long long)after);
+  return MLMC_OK;
+}
 
 static int field_eval_impl(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n,
                            int n_fine, int dtype, void* k_out, void* stream) {

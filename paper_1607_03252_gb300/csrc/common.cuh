@@ -14,6 +14,10 @@ namespace mlmc {
 void set_error(const char* fmt, ...);
 const char* last_error();
 
+// Budget, in SM clocks, of every bounded wait inside a kernel (mlmc_set_wait_budget;
+// about one second by default).
+long long wait_budget_clocks();
+
 #define MLMC_CUDA_TRY(expr)                                                                 \
   do {                                                                                      \
     cudaError_t _e = (expr);                                                                \

@@ -12,11 +12,12 @@
 //   norms         ||r|| / ||f|| = ||r~|| / ||g||.
 // No division runs inside a cycle; faces, D and 1/D are computed once per solve.
 //
-// Precision MLMC_PREC_MIXED: faces are the FP32 harmonic means of the FP32-rounded
-// nodal k, the V-cycle runs entirely in FP32 as a correction solve, and the outer
-// residual g - A~ u (with the FP32 faces read as FP64 values) and the update u += e run
-// in FP64 (iterative refinement): the fixed point is the FP64 solution of the
-// FP32-faced operator.
+// Precision MLMC_PREC_MIXED: the V-cycle's faces are the FP32 harmonic means of the
+// FP32-rounded nodal k and the V-cycle runs entirely in FP32 as a correction solve; the
+// outer residual g - A~ u, on FP64 faces of the FP64 nodal k of the finest grid, and the
+// update u += e run in FP64 (iterative refinement, or flexible CG with the FP32 cycle as
+// preconditioner): the fixed point is the FP64 solution of the FP64 operator, the one
+// an all-FP64 solve reaches.
 //
 // Every kernel skips samples whose `active` flag is 0, so each sample stops at its own
 // cycle count; every per-sample sum is a fixed tree that depends only on n. A sample's
@@ -956,7 +957,9 @@ struct Hier {
   double* Lws = nullptr;
   // level-0 FP64 state
   double* g64 = nullptr;   // h^2 f
-  double* D64 = nullptr;   // mixed: FP64 diagonal of the FP32 faces
+  double* D64 = nullptr;   // mixed: FP64 diagonal of the FP64 faces
+  double *K64x = nullptr, *K64y = nullptr, *K64z = nullptr;  // mixed: FP64 faces of the finest grid
+  int n_act = 0;           // host copy of the number of active samples (launch accounting)
   double* partial = nullptr;
   double* g2 = nullptr;
   double* relres = nullptr;
@@ -1003,7 +1006,12 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed, bool cg) {
   }
   const size_t e0 = (size_t)B * cube(n);
   H.g64 = c.template take<double>(e0);
-  if (mixed) H.D64 = c.template take<double>(e0);
+  if (mixed) {
+    H.D64 = c.template take<double>(e0);
+    H.K64x = c.template take<double>(e0);
+    H.K64y = c.template take<double>(e0);
+    H.K64z = c.template take<double>(e0);
+  }
   H.Ainv = c.template take<double>((size_t)B * 729);
   H.Lws = c.template take<double>((size_t)B * 729);
   H.NB = reduce_blocks(cube(n));
@@ -1059,29 +1067,32 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   Level<T>& v = H.lv[j];
   const int* act = H.active;
   const int B = H.B;
+  // launches cover all B samples; masked (finished) samples do no work, so the
+  // algorithmic bytes and flops count the active ones only
+  const double Ba = (double)H.n_act;
   const double W = (double)sizeof(T);
   if (j == H.L - 1) {
-    MLMC_LAUNCH(Names<T>::coarse, B * (729.0 * 8 + 54 * W), B * 27 * 54.0, st,
+    MLMC_LAUNCH(Names<T>::coarse, Ba * (729.0 * 8 + 54 * W), Ba * 27 * 54.0, st,
                 (k_coarse_apply<T><<<(B * 27 + 127) / 128, 128, 0, st>>>(B, H.Ainv, v.g, v.u, act)));
     return;
   }
   const int m = v.n - 2;
   const dim3 gs = plane_grid(m * ((v.n - 1) / 2), (long long)B * m);
   // one colour: half of the 7 words per node of a full sweep; 13 flops per updated node
-  const double sweep_bytes = B * interior(v.n) * 3.5 * W, sweep_flops = B * interior(v.n) * 0.5 * 13.0;
+  const double sweep_bytes = Ba * interior(v.n) * 3.5 * W, sweep_flops = Ba * interior(v.n) * 0.5 * 13.0;
   auto smooth = [&](int sweeps) {
     for (int s = 0; s < sweeps; ++s) {
       if constexpr (sizeof(T) == 4) {
         if (H.nodal[j]) {
           for (int c = 0; c < 2; ++c)
-            MLMC_LAUNCH("rbgs_nodal_f32", B * interior(v.n) * 2.0 * W, B * interior(v.n) * 0.5 * 37.0, st,
+            MLMC_LAUNCH("rbgs_nodal_f32", Ba * interior(v.n) * 2.0 * W, Ba * interior(v.n) * 0.5 * 37.0, st,
                         (k_rbgs_nodal<<<gs, kPlaneThreads, 0, st>>>(c, v.n, B, (const float*)v.kn,
                                                                    (const float*)v.g, (float*)v.u, act)));
           continue;
         }
       }
       if (H.fused[j]) {
-        rbgs_fused_sweep<T>(H.tile[j], v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, v.u2, act, H.err, st);
+        rbgs_fused_sweep<T>(H.tile[j], v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, v.u2, act, H.err, st, Ba);
         T* t = v.u;
         v.u = v.u2;
         v.u2 = t;
@@ -1096,7 +1107,7 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   bool nodal_res = false;
   if constexpr (sizeof(T) == 4) {
     if (H.nodal[j]) {
-      MLMC_LAUNCH("residual_nodal_f32", B * interior(v.n) * 4.0 * W, B * interior(v.n) * 37.0, st,
+      MLMC_LAUNCH("residual_nodal_f32", Ba * interior(v.n) * 4.0 * W, Ba * interior(v.n) * 37.0, st,
                   (k_residual_nodal<<<plane_grid(v.n * v.n, (long long)B * v.n), kPlaneThreads, 0, st>>>(
                       v.n, B, (const float*)v.kn, (const float*)v.g, (const float*)v.u, (float*)v.r, act)));
       nodal_res = true;
@@ -1105,27 +1116,27 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   if (!nodal_res) {
     int zs = 0;
     const dim3 rz = zmarch_grid(v.n, B, &zs);
-    MLMC_LAUNCH(Names<T>::residual, B * interior(v.n) * 7.0 * W, B * interior(v.n) * 14.0, st,
+    MLMC_LAUNCH(Names<T>::residual, Ba * interior(v.n) * 7.0 * W, Ba * interior(v.n) * 14.0, st,
                 (k_residual_z<T, T, T, T><<<rz, 128, 0, st>>>(v.n, zs, v.Kx, v.Ky, v.Kz, v.D, v.g, v.u, v.r, nullptr,
                                                               act)));
   }
   Level<T>& w = H.lv[j + 1];
   if (H.p1)
-    MLMC_LAUNCH("restrict_p1", B * ((double)v.n3 + (double)w.n3) * W, B * interior(w.n) * 16.0, st,
+    MLMC_LAUNCH("restrict_p1", Ba * ((double)v.n3 + (double)w.n3) * W, Ba * interior(w.n) * 16.0, st,
                 (k_restrict_p1<T><<<plane_grid((w.n - 2) * (w.n - 2), (long long)B * (w.n - 2)), kPlaneThreads, 0,
                                     st>>>(v.n, B, v.r, w.g, act)));
   else
-    MLMC_LAUNCH(Names<T>::restrict_, B * ((double)v.n3 + (double)w.n3) * W, B * interior(w.n) * 54.0, st,
+    MLMC_LAUNCH(Names<T>::restrict_, Ba * ((double)v.n3 + (double)w.n3) * W, Ba * interior(w.n) * 54.0, st,
                 (k_restrict<T><<<plane_grid((w.n - 2) * (w.n - 1), (long long)B * (w.n - 2)), kPlaneThreads, 0,
                                  st>>>(v.n, B, v.r, w.g, act)));
   cudaMemsetAsync(w.u, 0, (size_t)B * w.n3 * sizeof(T), st);
   vcycle(H, j + 1, nu1, nu2, st);
   if (H.p1)
-    MLMC_LAUNCH("prolong_p1", B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 1.5, st,
+    MLMC_LAUNCH("prolong_p1", Ba * (2.0 * (double)v.n3 + (double)w.n3) * W, Ba * interior(v.n) * 1.5, st,
                 (k_prolong_p1<T><<<plane_grid(m * m, (long long)B * m), kPlaneThreads, 0, st>>>(v.n, B, w.u, v.u,
                                                                                                act)));
   else
-    MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
+    MLMC_LAUNCH(Names<T>::prolong, Ba * (2.0 * (double)v.n3 + (double)w.n3) * W, Ba * interior(v.n) * 4.375, st,
                 (k_prolong<T><<<plane_grid(m * (v.n - 1), (long long)B * m), kPlaneThreads, 0, st>>>(v.n, B, w.u,
                                                                                                     v.u, act)));
   smooth(nu2);
@@ -1146,6 +1157,7 @@ struct GraphRunner {
   bool enabled = false;
   cudaGraphExec_t exec = nullptr;
   prof::Tape tape;
+  int cap_act = 1;  // active samples when the cycle was captured (its tape's accounting)
   ~GraphRunner() {
     if (exec) cudaGraphExecDestroy(exec);
   }
@@ -1159,6 +1171,7 @@ struct GraphRunner {
       prof::tape_begin();
       vcycle<T>(H, 0, nu1, nu2, st);
       tape = prof::tape_end();
+      cap_act = H.n_act > 0 ? H.n_act : 1;
       cudaGraph_t graph = nullptr;
       MLMC_CUDA_TRY(cudaStreamEndCapture(st, &graph));
       const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
@@ -1169,7 +1182,7 @@ struct GraphRunner {
         return MLMC_ERR_CUDA;
       }
     }
-    prof::tape_replay(tape);
+    prof::tape_replay(tape, (double)H.n_act / (double)cap_act);
     MLMC_CUDA_TRY(cudaGraphLaunch(exec, st));
     return MLMC_OK;
   }
@@ -1181,7 +1194,13 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   const bool mixed = a.cfg.precision == MLMC_PREC_MIXED;
   const int B = H.B, n = a.n;
   Level<T>& l0 = H.lv[0];
-  const double Wk = (double)sizeof(T), nodes = B * interior(n), all = (double)B * l0.n3;
+  // algorithmic work of the active samples (H.n_act, updated after every convergence test)
+  double nodes = H.n_act * interior(n), all = (double)H.n_act * l0.n3;
+  auto set_active = [&](int na) {
+    H.n_act = na;
+    nodes = na * interior(n);
+    all = (double)na * l0.n3;
+  };
   dim3 rg(H.NB, B);
   const unsigned sb = (B + 3) / 4;  // 128-thread blocks, one warp per sample
   const unsigned g0 = blocks_for((size_t)B * l0.n3, kThreads);
@@ -1189,7 +1208,11 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   int azslab = 0;
   const int aslabs = apply_slabs(n, &azslab), NBa = apply_blocks(n);
   const dim3 ag((unsigned)((n * n + 127) / 128), (unsigned)aslabs, (unsigned)B);
+  // the outer operator is FP64 in both precisions: the FP64 faces of the finest grid
   const double* D = mixed ? H.D64 : (const double*)(const void*)l0.D;
+  const double* Fx = mixed ? H.K64x : (const double*)(const void*)l0.Kx;
+  const double* Fy = mixed ? H.K64y : (const double*)(const void*)l0.Ky;
+  const double* Fz = mixed ? H.K64z : (const double*)(const void*)l0.Kz;
   auto sync_count = [&](int* out) -> int {
     MLMC_CUDA_TRY(cudaMemcpyAsync(out, H.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     MLMC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1208,14 +1231,15 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   auto zcur = [&]() -> double* { return mixed ? H.Z : (double*)(void*)H.lv[0].u; };
   // r = g - A x, ||r||
   MLMC_CUDA_TRY(cudaMemsetAsync(H.n_active, 0, sizeof(int), st));
-  MLMC_LAUNCH("cg_residual", nodes * (3 * Wk + 32), nodes * 16.0, st,
-              (k_residual_z<T, double, double, double><<<ag, 128, 0, st>>>(n, azslab, l0.Kx, l0.Ky, l0.Kz, D, H.g64,
-                                                                          a.u, H.R, H.partial, H.active)));
+  MLMC_LAUNCH("cg_residual", nodes * (3 * 8.0 + 32), nodes * 16.0, st,
+              (k_residual_z<double, double, double, double><<<ag, 128, 0, st>>>(n, azslab, Fx, Fy, Fz, D, H.g64,
+                                                                               a.u, H.R, H.partial, H.active)));
   MLMC_LAUNCH("norm_update", B * NBa * 8.0, B * NBa * 1.0, st,
               (k_norm_update<<<sb, 128, 0, st>>>(B, NBa, H.partial, H.g2, H.relres, H.cycles, H.active, 1, 0, rtol,
                                                  maxc, H.n_active)));
   int na = 0;
   MLMC_TRY(sync_count(&na));
+  set_active(na);
   if (na == 0) return MLMC_OK;
   if (mixed)
     MLMC_LAUNCH("to_f32", all * 12.0, 0.0, st,
@@ -1226,9 +1250,9 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   MLMC_LAUNCH("cg_p_update", all * 16.0, 0.0, st,
               (k_p_update<<<pg, kPlaneThreads, 0, st>>>(n, B, nullptr, zcur(), H.P, H.active)));
   while (true) {
-    MLMC_LAUNCH("cg_apply_dot", nodes * (3 * Wk + 8 + 16), nodes * 16.0, st,
-                (k_apply_dot_z<T, double><<<ag, 128, 0, st>>>(n, azslab, l0.Kx, l0.Ky, l0.Kz, D, H.P, H.Q,
-                                                               H.part_apply, H.active)));
+    MLMC_LAUNCH("cg_apply_dot", nodes * (3 * 8.0 + 8 + 16), nodes * 16.0, st,
+                (k_apply_dot_z<double, double><<<ag, 128, 0, st>>>(n, azslab, Fx, Fy, Fz, D, H.P, H.Q,
+                                                                    H.part_apply, H.active)));
     MLMC_LAUNCH("cg_scalar", B * NBa * 8.0, 0.0, st,
                 (k_cg_scalar<<<sb, 128, 0, st>>>(B, NBa, 1, H.part_apply, H.rz, H.rzo, H.alpha, H.beta, H.active)));
     MLMC_LAUNCH("cg_update", all * (mixed ? 60.0 : 56.0), nodes * 8.0, st,
@@ -1242,6 +1266,7 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
                 (k_norm_update<<<sb, 128, 0, st>>>(B, H.NB, H.partial, H.g2, H.relres, H.cycles, H.active, 1, 1,
                                                    rtol, maxc, H.n_active)));
     MLMC_TRY(sync_count(&na));
+    set_active(na);
     if (na == 0) break;
     MLMC_TRY(precondition());
     MLMC_LAUNCH("cg_scalar", B * H.NB * 8.0, 0.0, st,
@@ -1319,10 +1344,17 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   gr.enabled = !prof::timing_enabled() && st != nullptr && ((nu1 + nu2) % 2 == 0) && graphs_allowed();
   Level<T>& l0 = H.lv[0];
   const unsigned g0 = blocks_for((size_t)B * l0.n3, kThreads);
+  H.n_act = B;
   if (mixed) {
-    MLMC_LAUNCH("diag64_mixed", B * (double)l0.n3 * (3 * W + 8), B * (double)l0.n3 * 5.0, st,
-                (k_diag<T, double><<<plane_grid(l0.n * l0.n, (long long)B * l0.n), kPlaneThreads, 0, st>>>(
-                    l0.n, B, l0.Kx, l0.Ky, l0.Kz, H.D64, nullptr)));
+    // the outer FP64 operator: faces of the FP64 nodal k (not of its FP32 rounding), so
+    // that the refinement converges to the FP64 solution
+    const dim3 gb0 = plane_grid(l0.n * l0.n, (long long)B * l0.n);
+    MLMC_LAUNCH("faces64_mixed", B * (double)l0.n3 * (8.0 + 3 * 8.0), B * (double)l0.n3 * 12.0, st,
+                (k_faces<double><<<gb0, kPlaneThreads, 0, st>>>(a.k0, a.n_k0, a.st0, l0.n, B, H.K64x, H.K64y,
+                                                               H.K64z)));
+    MLMC_LAUNCH("diag64_mixed", B * (double)l0.n3 * (3 * 8.0 + 8), B * (double)l0.n3 * 5.0, st,
+                (k_diag<double, double><<<gb0, kPlaneThreads, 0, st>>>(l0.n, B, H.K64x, H.K64y, H.K64z, H.D64,
+                                                                      nullptr)));
   }
   Level<T>& lc = H.lv[H.L - 1];
   MLMC_LAUNCH("coarse_setup", B * 2 * 729.0 * 8, B * 40000.0, st,
@@ -1358,12 +1390,14 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     MLMC_CUDA_TRY(cudaMemsetAsync(H.n_active, 0, sizeof(int), st));
     int zs = 0;
     const dim3 rz = zmarch_grid(a.n, B, &zs);
+    const double Ba = (double)H.n_act;
     if (mixed) {
-      MLMC_LAUNCH("residual_mixed", B * interior(a.n) * (3 * W + 8 * 3 + W), B * interior(a.n) * 16.0, st,
-                  (k_residual_z<T, double, double, T><<<rz, 128, 0, st>>>(a.n, zs, l0.Kx, l0.Ky, l0.Kz, H.D64, H.g64,
-                                                                          a.u, l0.g, H.partial, H.active)));
+      MLMC_LAUNCH("residual_mixed", Ba * interior(a.n) * (3 * 8.0 + 8 * 3 + W), Ba * interior(a.n) * 16.0, st,
+                  (k_residual_z<double, double, double, T><<<rz, 128, 0, st>>>(a.n, zs, H.K64x, H.K64y, H.K64z, H.D64,
+                                                                               H.g64, a.u, l0.g, H.partial,
+                                                                               H.active)));
     } else {
-      MLMC_LAUNCH("residual_norm_f64", B * interior(a.n) * 6.0 * 8, B * interior(a.n) * 16.0, st,
+      MLMC_LAUNCH("residual_norm_f64", Ba * interior(a.n) * 6.0 * 8, Ba * interior(a.n) * 16.0, st,
                   (k_residual_z<T, T, T, T><<<rz, 128, 0, st>>>(a.n, zs, l0.Kx, l0.Ky, l0.Kz, l0.D, l0.g, l0.u,
                                                                 nullptr, H.partial, H.active)));
     }
@@ -1373,6 +1407,7 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     int na = 0;
     MLMC_CUDA_TRY(cudaMemcpyAsync(&na, H.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+    H.n_act = na;
     return na;
   };
   if (cg) {
@@ -1425,7 +1460,7 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     if (mixed) {
       MLMC_CUDA_TRY(cudaMemsetAsync(H.lv[0].u, 0, (size_t)B * l0.n3 * sizeof(T), st));
       MLMC_TRY(gr.run(H, nu1, nu2, st));
-      MLMC_LAUNCH("update_mixed", B * (double)l0.n3 * (W + 16), B * (double)l0.n3, st,
+      MLMC_LAUNCH("update_mixed", H.n_act * (double)l0.n3 * (W + 16), H.n_act * (double)l0.n3, st,
                   (k_update_mixed<<<plane_grid(a.n * a.n, (long long)B * a.n), kPlaneThreads, 0, st>>>(
                       a.n, B, (const float*)H.lv[0].u, a.u, H.active)));
     } else {

@@ -73,15 +73,15 @@ Tape tape_end() {
   return t_tape_store;
 }
 
-void tape_replay(const Tape& t) {
+void tape_replay(const Tape& t, double scale) {
   Registry& r = reg();
   r.total_launches.fetch_add((int64_t)t.cls.size());
   std::lock_guard<std::mutex> lk(r.mu);
   for (size_t i = 0; i < t.cls.size(); ++i) {
     Entry& e = r.entries[t.cls[i]];
     ++e.launches;
-    e.bytes += t.bytes[i];
-    e.flops += t.flops[i];
+    e.bytes += scale * t.bytes[i];
+    e.flops += scale * t.flops[i];
   }
 }
 
@@ -123,9 +123,69 @@ void end(int token, cudaStream_t st) {
 }  // namespace prof
 }  // namespace mlmc
 
+namespace mlmc {
+namespace {
+// FMA throughput probe: every thread runs 8 independent dependency chains of `iters` FMAs
+// (x = x * a + b); the inputs come from arguments so nothing folds, and the sum of the
+// chains is stored only when it equals a value it never takes (out[0] stays untouched).
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, T a, T b, T never, T* out) {
+  T x0 = (T)threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b);
+    x1 = fma(x1, a, b);
+    x2 = fma(x2, a, b);
+    x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b);
+    x5 = fma(x5, a, b);
+    x6 = fma(x6, a, b);
+    x7 = fma(x7, a, b);
+  }
+  const T t = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+  if (t == never) out[0] = t;
+}
+
+template <typename T>
+int fma_probe(double* tflops) {
+  int dev = 0, sms = 0;
+  MLMC_CUDA_TRY(cudaGetDevice(&dev));
+  MLMC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DevBuf out;
+  MLMC_TRY(out.alloc(sizeof(T), nullptr));
+  const int iters = 1 << 14, threads = 256, blocks = sms * 8;
+  cudaEvent_t e0, e1;
+  MLMC_CUDA_TRY(cudaEventCreate(&e0));
+  MLMC_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 5; ++rep) {  // the first launch warms up; the best of the rest counts
+    cudaEventRecord(e0, nullptr);
+    k_fma_probe<T><<<blocks, threads>>>(iters, (T)0.999999, (T)1e-7, (T)-12345.0, out.as<T>());
+    cudaEventRecord(e1, nullptr);
+    MLMC_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MLMC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MLMC_CUDA_TRY(cudaGetLastError());
+  *tflops = 2.0 * 8.0 * (double)iters * threads * blocks / (best * 1e-3) / 1e12;
+  return MLMC_OK;
+}
+}  // namespace
+}  // namespace mlmc
+
 using namespace mlmc;
 
 extern "C" {
+
+int mlmc_profile_fma_peak(int precision, double* tflops) {
+  if (!tflops || (precision != MLMC_PREC_F64 && precision != MLMC_PREC_MIXED)) {
+    set_error("mlmc_profile_fma_peak: precision must be MLMC_PREC_F64 or MLMC_PREC_MIXED (FP32) and tflops non-NULL");
+    return MLMC_ERR_INVALID;
+  }
+  return precision == MLMC_PREC_F64 ? fma_probe<double>(tflops) : fma_probe<float>(tflops);
+}
 
 int mlmc_profile_enable(int on) {
   prof::reg().timing.store(on != 0);

@@ -23,7 +23,9 @@ struct Tape {
 };
 void tape_begin();
 Tape tape_end();
-void tape_replay(const Tape& t);
+// `scale` multiplies the recorded bytes and flops (the active share of the batch at this
+// replay over that at capture).
+void tape_replay(const Tape& t, double scale = 1.0);
 // Records the start of one launch of `cls`; returns a token for end().
 int begin(const char* cls, double bytes, double flops, cudaStream_t st);
 void end(int token, cudaStream_t st);

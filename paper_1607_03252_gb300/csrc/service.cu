@@ -60,7 +60,7 @@ struct mlmc_service {
   uint64_t next_ticket = 1;
   size_t bytes_in_use = 0;
   int inflight = 0;
-  int64_t submitted = 0, completed = 0, rejected = 0;
+  int64_t submitted = 0, completed = 0, rejected = 0, cancelled = 0;
   int64_t queued = 0;
   double t_first = 0.0, t_last = 0.0;
   std::vector<std::vector<double>> latencies;  // per level, seconds
@@ -287,6 +287,34 @@ int mlmc_poll(mlmc_service* S, uint64_t ticket, mlmc_result* res) {
   return MLMC_OK;
 }
 
+int mlmc_cancel(mlmc_service* S, uint64_t ticket) {
+  if (!S) {
+    set_error("mlmc_cancel: NULL service");
+    return MLMC_ERR_INVALID;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->results.find(ticket);
+    if (it == S->results.end()) {
+      set_error("mlmc_cancel: unknown ticket %llu", (unsigned long long)ticket);
+      return MLMC_ERR_NOT_FOUND;
+    }
+    auto& q = S->queues[it->second.level];
+    auto qi = std::find_if(q.begin(), q.end(), [&](const Req& r) { return r.ticket == ticket; });
+    if (qi == q.end()) {
+      set_error("mlmc_cancel: ticket %llu is already running or finished", (unsigned long long)ticket);
+      return MLMC_ERR_BUSY;
+    }
+    q.erase(qi);
+    --S->queued;
+    ++S->cancelled;
+    it->second.status = MLMC_ERR_CANCELLED;
+    it->second.t_done = now_s();
+  }
+  S->cv_done.notify_all();
+  return MLMC_OK;
+}
+
 int mlmc_wait(mlmc_service* S, uint64_t ticket, double timeout_ms, mlmc_result* res) {
   if (!S || !res) {
     set_error("mlmc_wait: NULL argument");
@@ -323,6 +351,7 @@ int mlmc_service_stats(mlmc_service* S, mlmc_service_report* out) {
   out->submitted = S->submitted;
   out->completed = S->completed;
   out->rejected = S->rejected;
+  out->cancelled = S->cancelled;
   out->pending = S->queued;
   out->inflight_batches = S->inflight;
   out->bytes_in_use = S->bytes_in_use;

@@ -341,13 +341,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
       : "memory");
   return done != 0;
 }
-// bounded wait: about one second of SM clock
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, unsigned parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(b, parity))
-    if (clock64() - t0 > 2000000000LL) return false;
-  return true;
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* b, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return done != 0;
 }
+// bounded wait: one non-blocking test, then waits while fewer than `budget` SM clocks
+// have passed (budget 0: give up at the first test that finds the phase incomplete)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, unsigned parity, long long budget) {
+  if (mbar_test_wait(b, parity)) return true;
+  const long long t0 = clock64();
+  while (clock64() - t0 < budget)
+    if (mbar_try_wait(b, parity)) return true;
+  return false;
+}
+// budget of the drain after an expired wait (the copies still in flight must land before
+// the CTA's shared memory is released): about one second of SM clock, whatever the
+// budget of the normal waits
+constexpr long long kDrainBudget = 2000000000LL;
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
@@ -378,7 +393,7 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
     k_rbgs_bulk(int n, int ntx, int ntiles, int zslab, const T* __restrict__ Kx, const T* __restrict__ Ky,
                 const T* __restrict__ Kz, const T* __restrict__ Dinv, const T* __restrict__ g,
                 const T* __restrict__ uin, T* __restrict__ uout, const int* __restrict__ active,
-                int* __restrict__ err) {
+                int* __restrict__ err, long long budget) {
   using Lay = BulkLayout<T, BX, BY>;
   constexpr int W2 = Lay::W2, H2 = Lay::H2, W1 = Lay::W1, P1 = Lay::P1, RP = Lay::RP, PLANE = Lay::PLANE;
   constexpr int EPV = Lay::EPV;
@@ -467,7 +482,7 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
   auto parity = [&](int z) { return (unsigned)(((z - pstart) / kBulkSlots) & 1); };
   auto wait_plane = [&](int z) {
     if (z < 0 || z >= n) return;
-    if (!mbar_wait_bounded(&mbar[z % kBulkSlots], parity(z))) {
+    if (!mbar_wait_bounded(&mbar[z % kBulkSlots], parity(z), budget)) {
       *abort_flag = 1;
       atomicExch(err, 1);
     }
@@ -483,13 +498,17 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
     return stage[k];
   };
   T kz_m2 = T(0);
+  int last_issued = min(zs + 1, n - 1);  // highest plane whose copies were issued
   issue(zs - 1);
   issue(zs);
   issue(zs + 1);
   wait_plane(zs - 1);
   wait_plane(zs);
   for (int z = zs; z <= ze; ++z) {
-    if (z + 2 <= ze + 1) issue(z + 2);
+    if (z + 2 <= ze + 1) {
+      issue(z + 2);
+      last_issued = min(z + 2, n - 1);
+    }
     wait_plane(z + 1);
     const int sz = z % kBulkSlots, szm = (z + kBulkSlots - 1) % kBulkSlots, szp = (z + 1) % kBulkSlots;
     T* rz = red + (size_t)(z % 3) * P1;
@@ -509,8 +528,11 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
     }
     __syncthreads();
     if (*abort_flag) {
-      // a wait ran out: drain the copies still in flight (bounded), then every thread leaves
-      for (int p = z + 1; p <= min(z + 2, min(ze + 1, n - 1)); ++p) mbar_wait_bounded(&mbar[p % kBulkSlots], parity(p));
+      // a wait ran out: drain the copies of the last kBulkSlots issued planes (any of them
+      // may still be in flight, the early waits included; a completed phase returns at
+      // once), each bounded by kDrainBudget, then every thread leaves
+      for (int p = max(pstart, last_issued - (kBulkSlots - 1)); p <= last_issued; ++p)
+        mbar_wait_bounded(&mbar[p % kBulkSlots], parity(p), kDrainBudget);
       return;
     }
     if (z > zs) {
@@ -542,7 +564,7 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
 
 template <typename T, int BX, int BY>
 int launch_bulk(int n, int B, const T* Kx, const T* Ky, const T* Kz, const T* Dinv, const T* g, const T* uin,
-                T* uout, const int* active, int* err, cudaStream_t st) {
+                T* uout, const int* active, int* err, cudaStream_t st, long long budget) {
   using Lay = BulkLayout<T, BX, BY>;
   const int m = n - 2;
   const int ntx = (m + BX - 1) / BX, nty = (m + BY - 1) / BY, ntiles = ntx * nty;
@@ -553,7 +575,7 @@ int launch_bulk(int n, int B, const T* Kx, const T* Ky, const T* Kz, const T* Di
   slabs = (m + zslab - 1) / zslab;
   dim3 grid((unsigned)(ntiles * slabs), (unsigned)B);
   k_rbgs_bulk<T, BX, BY><<<grid, Lay::threads, Lay::bytes, st>>>(n, ntx, ntiles, zslab, Kx, Ky, Kz, Dinv, g, uin,
-                                                                 uout, active, err);
+                                                                 uout, active, err, budget);
   return MLMC_OK;
 }
 
@@ -640,33 +662,36 @@ const char* tile_name(int shape) {
 
 template <typename T>
 int rbgs_fused_sweep(int shape, int n, int B, const T* Kx, const T* Ky, const T* Kz, const T* Dinv, const T* g,
-                     const T* uin, T* uout, const int* active, int* err, cudaStream_t st) {
+                     const T* uin, T* uout, const int* active, int* err, cudaStream_t st, double active_samples) {
   const double interior = (double)(n - 2) * (n - 2) * (n - 2);
   const bool bulk = shape == kBulk32x8 || shape == kBulk32x16 || shape == kBulk64x8;
   const char* cls = bulk ? (sizeof(T) == 4 ? "rbgs_bulk_f32" : "rbgs_bulk_f64")
                          : (sizeof(T) == 4 ? "rbgs_fused_f32" : "rbgs_fused_f64");
   // one full sweep: 7 words per interior node (u read + write, Kx, Ky, Kz, Dinv, g), 13 flops
   MLMC_TRY(rbgs_fused_configure<T>(shape));
-  prof::Scope scope(cls, B * interior * 7.0 * sizeof(T), B * interior * 13.0, st);
+  // (masked samples are copied, not smoothed: the work counts the active ones)
+  prof::Scope scope(cls, active_samples * interior * 7.0 * sizeof(T), active_samples * interior * 13.0, st);
+  const long long budget = wait_budget_clocks();
   switch (shape) {
     case kTile32x16:
       return launch_shape<T, 32, 16>(n, B, Kx, Ky, Kz, Dinv, g, uin, uout, active, st);
     case kTile64x8:
       return launch_shape<T, 64, 8>(n, B, Kx, Ky, Kz, Dinv, g, uin, uout, active, st);
     case kBulk32x8:
-      return launch_bulk<T, 32, 8>(n, B, Kx, Ky, Kz, Dinv, g, uin, uout, active, err, st);
+      return launch_bulk<T, 32, 8>(n, B, Kx, Ky, Kz, Dinv, g, uin, uout, active, err, st, budget);
     case kBulk32x16:
-      return launch_bulk<T, 32, 16>(n, B, Kx, Ky, Kz, Dinv, g, uin, uout, active, err, st);
+      return launch_bulk<T, 32, 16>(n, B, Kx, Ky, Kz, Dinv, g, uin, uout, active, err, st, budget);
     case kBulk64x8:
-      return launch_bulk<T, 64, 8>(n, B, Kx, Ky, Kz, Dinv, g, uin, uout, active, err, st);
+      return launch_bulk<T, 64, 8>(n, B, Kx, Ky, Kz, Dinv, g, uin, uout, active, err, st, budget);
     default:
       return launch_shape<T, 32, 8>(n, B, Kx, Ky, Kz, Dinv, g, uin, uout, active, st);
   }
 }
 
 template int rbgs_fused_sweep<float>(int, int, int, const float*, const float*, const float*, const float*,
-                                     const float*, const float*, float*, const int*, int*, cudaStream_t);
+                                     const float*, const float*, float*, const int*, int*, cudaStream_t, double);
 template int rbgs_fused_sweep<double>(int, int, int, const double*, const double*, const double*, const double*,
-                                      const double*, const double*, double*, const int*, int*, cudaStream_t);
+                                      const double*, const double*, double*, const int*, int*, cudaStream_t,
+                                      double);
 
 }  // namespace mlmc

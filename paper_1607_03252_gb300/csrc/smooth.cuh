@@ -12,14 +12,16 @@ const char* tile_name(int shape);
 // One full red-black sweep over B samples of an n^3 grid: reads uin, writes uout
 // (distinct buffers; uout's boundary nodes must already be zero). Samples whose
 // active flag is 0 are copied from uin to uout unchanged. The bulk-copy variants set
-// *err (device) to 1 if a staging wait runs out of its time budget.
+// *err (device) to 1 if a staging wait runs out of its time budget (wait_budget_clocks()
+// SM clocks, read at launch).
 // Sets the shared-memory attribute of a fused-sweep variant (once per process); must run
 // before the variant's first launch, and outside stream capture.
 template <typename T>
 int rbgs_fused_configure(int shape);
 
+// active_samples: the number of samples whose flag is 1 (launch accounting only).
 template <typename T>
 int rbgs_fused_sweep(int shape, int n, int B, const T* Kx, const T* Ky, const T* Kz, const T* Dinv, const T* g,
-                     const T* uin, T* uout, const int* active, int* err, cudaStream_t st);
+                     const T* uin, T* uout, const int* active, int* err, cudaStream_t st, double active_samples);
 
 }  // namespace mlmc

@@ -1,223 +1,182 @@
-"""Adaptive MLMC estimator (Algorithm 2) on the GPU library, with checkpoint / resume.
+"""Adaptive MLMC estimator (Algorithm 2) -- a ctypes wrapper of mlmc_adaptive_* in the library.
 
-Each round computes the missing samples of every level (Algorithm 2, step 2.a) through
-`mlmc_level_estimate`, folds their (N, mean, M2) records into the level's running record
-(Chan's merge, Sec. 2.3's Y-hat_l and s_l^2), estimates the cost per sample C_l (measured
-wall time, or the deterministic node-count model), and sizes
-N_l by Eq. 15 for eps_s^2 = theta eps^2 (Eq. 6); it stops when no level needs more samples
-(step 4). Sample ids of level l are sample_id(l, 0), sample_id(l, 1), ... in order, so a
-run restored from `state()` continues with exactly the ids an uninterrupted run would use
-and ends with the same records. With several `streams`, the levels of a round run
-concurrently (one host thread and one stream per lane, levels assigned longest first by
-their node count); a level's records do not depend on that.
+Every decision of the algorithm (sample sizes by Eq. 15, the bias test of Eq. 14, the
+online rate fits, level growth, the lane plan of a round) is made in libmlmc_gb300.so;
+this class marshals the configuration, optionally hands the library a Python sampler in
+place of its GPU level pipeline, and keeps the per-round log and JSON checkpoints.
 
-With `max_level` set, the number of levels adapts too (Algorithm 2, step 3): after each
-round the bias estimate of Eq. 14, |Y-hat_L| / (8^alpha - 1), is compared with eps_b
-(Eq. 6), and while it is larger and L < max_level the next level joins with N_init samples.
-alpha is given, or fitted online from the level means l >= 1 (least squares of
-log_8 |Y-hat_l| against l, M_l ~ 8^l; `alpha0` until two such levels exist, never below
-`alpha_floor`). The rates beta (variances) and gamma (costs) of Eq. 12 are fitted the same
-way and reported.
+Sample ids of level l are (l << 48) | i for i = 0, 1, ... in order, so a run restored
+from `state()` continues with exactly the ids an uninterrupted run would use and ends
+with the same records.
 """
 from __future__ import annotations
 
+import ctypes
 import json
 import math
-import threading
-import time
 
 from . import _capi as mg
-from .stats import chan_merge, eps_split, fit_rate, sample_sizes
-from .workloads import sample_id
 
 
 class MLMCEstimator:
     def __init__(self, run_seed, sigma2, ell, M, levels, N_init, eps, theta=0.5, n0=17, nu=(2, 2), rtol=1e-10,
                  precision=mg.MLMC_PREC_F64, accel=mg.MLMC_ACCEL_NONE, smoother=mg.MLMC_SMOOTH_AUTO,
                  max_batch=0, max_cycles=300, stream=None, cost_model="measured", streams=None, max_level=None,
-                 alpha=None, alpha0=2.0 / 3.0, alpha_floor=0.1, cov=mg.MLMC_COV_GAUSS):
+                 alpha=None, alpha0=2.0 / 3.0, alpha_floor=0.1, cov=mg.MLMC_COV_GAUSS, sampler=None):
+        """levels must be 0..L0. sampler (optional): f(level, first_index, count) -> (N, mean,
+        M2) replaces the GPU level pipeline (e.g. a host model of the level differences)."""
         if cost_model not in ("measured", "nodes"):
             raise ValueError("cost_model must be 'measured' or 'nodes'")
         levels = list(levels)
+        if levels != list(range(len(levels))):
+            raise ValueError("levels must be 0..L0")
         if isinstance(N_init, int):
             N_init = [N_init] * len(levels)
         if len(N_init) != len(levels):
             raise ValueError("N_init needs one count per level")
-        if max_level is not None and (levels != list(range(len(levels))) or len(levels) < 2 or max_level < levels[-1]):
+        if max_level is not None and (len(levels) < 2 or max_level < levels[-1]):
             raise ValueError("level growth starts from levels 0..L (L >= 1) with L <= max_level")
         self.params = dict(cost_model=cost_model, run_seed=int(run_seed), sigma2=float(sigma2), ell=float(ell), M=int(M),
-                           levels=levels, N_init=list(N_init), eps=float(eps), theta=float(theta), n0=int(n0),
-                           nu=list(nu), rtol=float(rtol), precision=int(precision), accel=int(accel),
+                           levels=levels, N_init=[int(x) for x in N_init], eps=float(eps), theta=float(theta),
+                           n0=int(n0), nu=list(nu), rtol=float(rtol), precision=int(precision), accel=int(accel),
                            smoother=int(smoother), max_batch=int(max_batch), max_cycles=int(max_cycles),
                            max_level=None if max_level is None else int(max_level),
                            alpha=None if alpha is None else float(alpha), alpha0=float(alpha0),
                            alpha_floor=float(alpha_floor), cov=int(cov))
         self.stream = stream
         self.streams = list(streams) if streams else [stream]
-        self.levels = list(levels)
-        L = len(self.levels)
-        self.have = [0] * L
-        self.records = [(0.0, 0.0, 0.0)] * L
-        self.seconds = [0.0] * L
-        self.target = list(self.params["N_init"])
-        self.rounds = 0
         self.log = []
+        self._sampler_py = sampler
+        self._sampler_c = None
+        self._h = None
+        self._make_handle()
 
-    # -- state ------------------------------------------------------------------------
+    # -- handle -------------------------------------------------------------------------
+    def _make_handle(self):
+        p = self.params
+        c = mg.AdaptiveCfg()
+        c.level = mg.make_mlmc_cfg(p["run_seed"], p["sigma2"], p["ell"], p["M"], n0=p["n0"], nu1=p["nu"][0],
+                                   nu2=p["nu"][1], rtol=p["rtol"], max_cycles=p["max_cycles"],
+                                   precision=p["precision"], max_batch=p["max_batch"], stream=self.stream,
+                                   smoother=p["smoother"], accel=p["accel"], cov=p["cov"])
+        c.L0 = len(p["levels"]) - 1
+        c.max_level = c.L0 if p["max_level"] is None else p["max_level"]
+        for l, n in enumerate(p["N_init"]):
+            c.N_init[l] = n
+        for l in range(len(p["N_init"]), min(c.max_level + 1, mg.MLMC_MAX_LEVELS)):
+            c.N_init[l] = p["N_init"][-1]  # grown levels start at the last pilot count
+        c.eps, c.theta = p["eps"], p["theta"]
+        c.cost_model = mg.MLMC_COST_NODES if p["cost_model"] == "nodes" else mg.MLMC_COST_MEASURED
+        c.alpha = p["alpha"] if p["alpha"] is not None else 0.0
+        c.alpha0, c.alpha_floor = p["alpha0"], p["alpha_floor"]
+        c.lanes = len(self.streams)
+        for k, st in enumerate(self.streams):
+            c.lane_streams[k] = st.cuda_stream if st is not None else None
+        self._cfg = c
+        h = mg.lib().mlmc_adaptive_create(ctypes.byref(c))
+        if not h:
+            raise mg.MlmcError(mg.MLMC_ERR_INVALID, "mlmc_adaptive_create", mg.lib().mlmc_last_error_string().decode())
+        self._h = h
+        if self._sampler_py is not None:
+            f = self._sampler_py
+
+            def cb(user, level, first, count, N, mean, M2):
+                try:
+                    n, m, m2 = f(int(level), int(first), int(count))
+                except Exception:
+                    return mg.MLMC_ERR_INVALID
+                N[0], mean[0], M2[0] = float(n), float(m), float(m2)
+                return mg.MLMC_OK
+
+            self._sampler_c = mg.LEVEL_SAMPLER(cb)
+            mg._check(mg.lib().mlmc_adaptive_set_sampler(self._h, self._sampler_c, None), "mlmc_adaptive_set_sampler")
+
+    def __del__(self):
+        try:
+            if self._h:
+                mg.lib().mlmc_adaptive_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def _summary(self):
+        s = mg.AdaptiveSummary()
+        mg._check(mg.lib().mlmc_adaptive_result(self._h, ctypes.byref(s)), "mlmc_adaptive_result")
+        return s
+
+    def _state(self):
+        st = mg.AdaptiveState()
+        mg._check(mg.lib().mlmc_adaptive_get_state(self._h, ctypes.byref(st)), "mlmc_adaptive_get_state")
+        return st
+
+    # -- views ---------------------------------------------------------------------------
+    @property
+    def levels(self):
+        return list(range(self._state().L + 1))
+
+    @property
+    def have(self):
+        st = self._state()
+        return [int(st.have[l]) for l in range(st.L + 1)]
+
+    @property
+    def records(self):
+        st = self._state()
+        return [(st.N[l], st.mean[l], st.M2[l]) for l in range(st.L + 1)]
+
+    @property
+    def rounds(self):
+        return self._state().rounds
+
+    # -- state ---------------------------------------------------------------------------
     def state(self) -> dict:
-        return {"params": self.params, "levels": self.levels, "have": self.have,
-                "records": [list(r) for r in self.records],
-                "seconds": self.seconds, "target": self.target, "rounds": self.rounds, "log": self.log}
+        st = self._state()
+        fields = {k: (list(getattr(st, k)) if not isinstance(getattr(st, k), int) else getattr(st, k))
+                  for k, _ in mg.AdaptiveState._fields_}
+        return {"params": self.params, "state": fields, "log": self.log}
 
     def checkpoint(self, path):
         with open(path, "w") as fh:
             json.dump(self.state(), fh)
 
     @classmethod
-    def from_state(cls, state, stream=None):
+    def from_state(cls, state, stream=None, streams=None, sampler=None):
         p = state["params"]
         est = cls(p["run_seed"], p["sigma2"], p["ell"], p["M"], p["levels"], p["N_init"], p["eps"], p["theta"],
                   p["n0"], tuple(p["nu"]), p["rtol"], p["precision"], p["accel"], p["smoother"], p["max_batch"],
-                  p["max_cycles"], stream, p.get("cost_model", "measured"), max_level=p.get("max_level"),
-                  alpha=p.get("alpha"), alpha0=p.get("alpha0", 2.0 / 3.0), alpha_floor=p.get("alpha_floor", 0.1),
-                  cov=p.get("cov", mg.MLMC_COV_GAUSS))
-        est.levels = list(state.get("levels", p["levels"]))
-        est.have = list(state["have"])
-        est.records = [tuple(r) for r in state["records"]]
-        est.seconds = list(state["seconds"])
-        est.target = list(state["target"])
-        est.rounds = int(state["rounds"])
-        est.log = list(state["log"])
+                  p["max_cycles"], stream, p["cost_model"], streams=streams, max_level=p["max_level"],
+                  alpha=p["alpha"], alpha0=p["alpha0"], alpha_floor=p["alpha_floor"], cov=p["cov"], sampler=sampler)
+        st = mg.AdaptiveState()
+        for k, _ in mg.AdaptiveState._fields_:
+            v = state["state"][k]
+            if isinstance(v, list):
+                arr = getattr(st, k)
+                for i, x in enumerate(v):
+                    arr[i] = x
+            else:
+                setattr(st, k, v)
+        mg._check(mg.lib().mlmc_adaptive_set_state(est._h, ctypes.byref(st)), "mlmc_adaptive_set_state")
+        est.log = list(state.get("log", []))
         return est
 
     @classmethod
-    def restore(cls, path, stream=None):
+    def restore(cls, path, stream=None, streams=None, sampler=None):
         with open(path) as fh:
-            return cls.from_state(json.load(fh), stream)
+            return cls.from_state(json.load(fh), stream, streams, sampler)
 
-    # -- computation --------------------------------------------------------------------
-    def _cfg(self, stream=None):
-        p = self.params
-        return mg.make_mlmc_cfg(p["run_seed"], p["sigma2"], p["ell"], p["M"], n0=p["n0"], nu1=p["nu"][0],
-                                nu2=p["nu"][1], rtol=p["rtol"], max_cycles=p["max_cycles"], precision=p["precision"],
-                                max_batch=p["max_batch"], stream=stream if stream is not None else self.stream,
-                                smoother=p["smoother"], accel=p["accel"], cov=p["cov"])
-
-    def add_samples(self, i, count, stream=None):
-        """Computes samples have[i] .. have[i] + count - 1 of level levels[i]."""
-        if count <= 0:
-            return
-        level = self.levels[i]
-        t = time.perf_counter()
-        st, _, _, _ = mg.mlmc_level_estimate(self._cfg(stream), level, sample_id(level, self.have[i]), count,
-                                             want_samples=False)
-        self.seconds[i] += time.perf_counter() - t
-        self.records[i] = chan_merge([self.records[i], (float(st.N), st.mean, st.M2)])
-        self.have[i] += count
-
-    def variances(self):
-        return [r[2] / (r[0] - 1.0) if r[0] > 1 else 0.0 for r in self.records]
-
-    def costs(self):
-        """C_l: measured seconds per sample, or the model cost n_l^3 + n_{l-1}^3 (nodes of
-        the fine and coarse grid, deterministic)."""
-        if self.params["cost_model"] == "nodes":
-            n0 = self.params["n0"]
-            out = []
-            for l in self.levels:
-                nf = (n0 - 1) * 2 ** l + 1
-                nc = (n0 - 1) * 2 ** (l - 1) + 1 if l > 0 else 0
-                out.append(float(nf ** 3 + nc ** 3))
-            return out
-        return [self.seconds[i] / self.have[i] for i in range(len(self.have))]
-
-    def _node_cost(self, i):
-        n0, l = self.params["n0"], self.levels[i]
-        nf = (n0 - 1) * 2 ** l + 1
-        nc = (n0 - 1) * 2 ** (l - 1) + 1 if l > 0 else 0
-        return float(nf ** 3 + nc ** 3)
-
-    def _add_round(self):
-        todo = [(i, self.target[i] - self.have[i]) for i in range(len(self.have)) if self.target[i] > self.have[i]]
-        if len(self.streams) <= 1 or len(todo) <= 1:
-            for i, c in todo:
-                self.add_samples(i, c, self.streams[0])
-            return
-        loads = [0.0] * len(self.streams)
-        lanes = [[] for _ in self.streams]
-        for i, c in sorted(todo, key=lambda t: -t[1] * self._node_cost(t[0])):
-            k = min(range(len(lanes)), key=lambda j: loads[j])
-            lanes[k].append((i, c))
-            loads[k] += c * self._node_cost(i)
-        errors = []
-
-        def run(k):
-            try:
-                for i, c in lanes[k]:
-                    self.add_samples(i, c, self.streams[k])
-            except BaseException as e:  # re-raised on the calling thread
-                errors.append(e)
-
-        threads = [threading.Thread(target=run, args=(k,)) for k in range(1, len(lanes)) if lanes[k]]
-        for t in threads:
-            t.start()
-        run(0)
-        for t in threads:
-            t.join()
-        if errors:
-            raise errors[0]
-
-    def rates(self):
-        """(alpha, beta, gamma) of Eqs. 12 and 14 fitted over the levels l >= 1 with
-        samples (None where fewer than two such levels exist); alpha as the bias test
-        uses it (given, else fitted, else alpha0; at least alpha_floor)."""
-        p = self.params
-        idx = [i for i, l in enumerate(self.levels) if l >= 1 and self.have[i] > 0]
-        ls = [self.levels[i] for i in idx]
-        V, C = self.variances(), self.costs() if self.have and min(self.have) > 0 else None
-        fit_a = fit_rate(ls, [self.records[i][1] for i in idx])
-        beta = fit_rate(ls, [V[i] for i in idx]) if all(V[i] > 0 for i in idx) else None
-        gamma = None
-        if C is not None and all(C[i] > 0 for i in idx):
-            g = fit_rate(ls, [C[i] for i in idx])
-            gamma = -g if g is not None else None
-        if p["alpha"] is not None:
-            alpha = p["alpha"]
-        else:
-            alpha = max(fit_a if fit_a is not None else p["alpha0"], p["alpha_floor"])
-        return alpha, beta, gamma
-
-    def bias_estimate(self):
-        """|Y-hat_L| / (8^alpha - 1) (Eq. 14)."""
-        alpha = self.rates()[0]
-        return abs(self.records[-1][1]) / (8.0 ** alpha - 1.0)
-
+    # -- computation ---------------------------------------------------------------------
     def step(self) -> bool:
-        """One round of Algorithm 2; returns True when neither N_l nor L changes."""
-        p = self.params
-        self.rounds += 1
-        self._add_round()
-        V = self.variances()
-        C = self.costs()
-        eps_s, eps_b = eps_split(p["eps"], p["theta"])
-        need = sample_sizes([max(v, 1e-30) for v in V], C, eps_s)
-        grow = False
-        entry = {"round": self.rounds, "levels": list(self.levels), "have": list(self.have), "N_next": need}
-        if p["max_level"] is not None:
-            bias = self.bias_estimate()
-            grow = bias > eps_b and self.levels[-1] < p["max_level"]
-            entry.update(alpha=self.rates()[0], bias=bias, grow=grow)
-        self.log.append(entry)
-        if not grow and all(nn <= h for nn, h in zip(need, self.have)):
-            return True
-        self.target = [max(a, b) for a, b in zip(self.target, need)]
-        if grow:
-            self.levels.append(self.levels[-1] + 1)
-            self.have.append(0)
-            self.records.append((0.0, 0.0, 0.0))
-            self.seconds.append(0.0)
-            self.target.append(p["N_init"][-1])
-        return False
+        """One round of Algorithm 2 (in the library); returns True when neither N_l nor L
+        changed."""
+        fin = ctypes.c_int()
+        mg._check(mg.lib().mlmc_adaptive_step(self._h, ctypes.byref(fin)), "mlmc_adaptive_step")
+        n = mg.lib().mlmc_adaptive_log_count(self._h)
+        e = mg.AdaptiveRound()
+        mg._check(mg.lib().mlmc_adaptive_log_get(self._h, n - 1, ctypes.byref(e)), "mlmc_adaptive_log_get")
+        nl = e.L + 1
+        self.log.append({"round": e.round, "levels": list(range(nl)), "have": list(e.have[:nl]),
+                         "N_next": list(e.N_next[:nl]), "alpha": e.alpha, "bias": e.bias, "grow": bool(e.grow)})
+        return bool(fin.value)
 
     def run(self, max_rounds=50):
         for _ in range(max_rounds):
@@ -225,15 +184,18 @@ class MLMCEstimator:
                 break
         return self.result()
 
+    def rates(self):
+        """(alpha as the bias test uses it, beta, gamma); None where no fit exists."""
+        s = self._summary()
+        nan = lambda x: None if math.isnan(x) else x
+        return s.alpha, nan(s.beta), nan(s.gamma)
+
     def result(self) -> dict:
-        V = self.variances()
-        means = [r[1] for r in self.records]
-        eps_s, eps_b = eps_split(self.params["eps"], self.params["theta"])
-        alpha, beta, gamma = self.rates()
-        bias = abs(means[-1]) / (8.0 ** alpha - 1.0)
-        return {"Q_hat": math.fsum(means), "level_means": means, "level_vars": V, "N": list(self.have),
-                "levels": list(self.levels), "L": self.levels[-1],
-                "sampling_var": math.fsum(v / max(h, 1) for v, h in zip(V, self.have)), "eps_s2": eps_s ** 2,
-                "cost_per_sample_s": [self.seconds[i] / max(self.have[i], 1) for i in range(len(self.have))],
-                "rounds": self.rounds, "alpha": alpha, "beta": beta, "gamma": gamma, "bias": bias,
-                "bias_ok": bias <= eps_b}
+        s = self._summary()
+        nl = s.L + 1
+        return {"Q_hat": s.Q_hat, "level_means": list(s.mean[:nl]), "level_vars": list(s.var[:nl]),
+                "N": [int(x) for x in s.N[:nl]], "levels": list(range(nl)), "L": s.L,
+                "sampling_var": s.sampling_var, "eps_s2": s.eps_s2,
+                "cost_per_sample_s": [s.seconds[l] / max(int(s.N[l]), 1) for l in range(nl)],
+                "rounds": s.rounds, "alpha": s.alpha, "beta": None if math.isnan(s.beta) else s.beta,
+                "gamma": None if math.isnan(s.gamma) else s.gamma, "bias": s.bias, "bias_ok": bool(s.bias_ok)}

@@ -3,6 +3,7 @@
   python -m paper_1607_03252_gb300.profile_case --n 129 --batch 8 --prec f64 --cycles 2 \
       [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8|nodal] [--accel cg] [--timing]
       [--field gauss|exp|spde] [--level L --n0 17] [--disc fv|fe] [--accel fmg] [--qoi mean|point|flux]
+  python -m paper_1607_03252_gb300.profile_case --fma-peak
 
 Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256 unless given) for `batch`
 realisations on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0; or V(nu, nu)
@@ -13,7 +14,8 @@ prints launches, device time per launch and algorithmic GB/s; with --field spde 
 for the field evaluation (the SPDE sampler of Sec. 3.2), with its wall time. With --level
 it instead runs mlmc_level_estimate for `batch` samples of that MLMC level (grids from n0;
 the precision, smoother and field as given, rtol 1e-10) and, with --timing, prints the
-per-class profile of a second run. Exits 0 on success.
+per-class profile of a second run. With --fma-peak it prints the measured FP64 and FP32
+FMA throughput (mlmc_profile_fma_peak) instead. Exits 0 on success.
 """
 from __future__ import annotations
 
@@ -46,7 +48,14 @@ def main(argv=None):
     p.add_argument("--field", choices=["gauss", "exp", "spde"], default="gauss")
     p.add_argument("--level", type=int, default=-1, help="run one MLMC level estimate instead")
     p.add_argument("--n0", type=int, default=17)
+    p.add_argument("--fma-peak", action="store_true", help="print the measured FP64 and FP32 FMA throughput and exit")
     a = p.parse_args(argv)
+    if a.fma_peak:
+        f64 = mg.profile_fma_peak(mg.MLMC_PREC_F64)
+        f32 = mg.profile_fma_peak(mg.MLMC_PREC_MIXED)
+        print("fma peak: FP64 %.3f TFLOP/s, FP32 %.2f TFLOP/s, ratio %.1f (%s)"
+              % (f64, f32, f32 / f64, torch.cuda.get_device_name()))
+        return 0
     prec = mg.MLMC_PREC_F64 if a.prec == "f64" else mg.MLMC_PREC_MIXED
     sm = {"auto": mg.MLMC_SMOOTH_AUTO, "two-pass": mg.MLMC_SMOOTH_TWO_PASS, "32x8": mg.MLMC_SMOOTH_FUSED_32x8,
           "32x16": mg.MLMC_SMOOTH_FUSED_32x16, "64x8": mg.MLMC_SMOOTH_FUSED_64x8,

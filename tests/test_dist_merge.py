@@ -11,7 +11,7 @@ import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
-from paper_1607_03252_gb300.stats import chan_merge, eps_split, merge_levels, mlmc_estimate, sample_sizes
+from paper_1607_03252_gb300.stats import chan_merge, merge_levels, sample_sizes
 
 
 def _free_port():
@@ -74,9 +74,7 @@ def test_chan_merge_matches_direct_statistics():
     assert m2 == pytest.approx(((v - v.mean()) ** 2).sum(), rel=1e-12)
 
 
-def test_sample_sizes_and_estimate_host_logic():
-    es, eb = eps_split(0.1 * math.sqrt(2.0), 0.5)
-    assert es == pytest.approx(0.1)
-    assert sample_sizes([1.0, 0.25, 0.0625], [1.0, 8.0, 64.0], es) == [442, 79, 14]
-    q, var = mlmc_estimate([1.0, 0.5], [2.0, 1.0], [4, 2])
-    assert q == 1.5 and var == 1.0
+def test_sample_sizes_host_logic():
+    # eps = 0.1 sqrt(2), theta = 1/2: eps_s = 0.1, the hand-worked case of Eq. 11
+    assert sample_sizes([1.0, 0.25, 0.0625], [1.0, 8.0, 64.0], 0.1 * math.sqrt(2.0), 0.5) == [442, 79, 14]
+    assert sample_sizes([1e-12], [1.0], 1.0, 0.5) == [2]  # at least two samples per level

@@ -1,19 +1,17 @@
-"""Host logic of the adaptive estimator (Algorithm 2 with level growth), on the CPU.
+"""Host logic of the adaptive estimator (Algorithm 2 with level growth, in the library's
+mlmc_adaptive_* calls), on the CPU.
 
-The GPU level call is replaced by a synthetic sampler (level l: mean 0.1 * 8^-l, values
-alternating around it), and the estimator's decisions -- the number of levels, the sample
-counts of every round, alpha -- must be those of the oracle's Algorithm 2 on the same
-sampler.
+The GPU level pipeline is replaced, through the C ABI's sampler hook, by a synthetic
+sampler (level l: mean 0.1 * 8^-l, values alternating around it), and the estimator's
+decisions -- the number of levels, the sample counts of every round, alpha -- must be
+those of the oracle's Algorithm 2 on the same sampler.
 """
 import math
-import types
 
 import pytest
 
 from oracle import adaptive as oracle_adaptive
-from paper_1607_03252_gb300 import estimator as est_mod
 from paper_1607_03252_gb300.estimator import MLMCEstimator
-from paper_1607_03252_gb300.workloads import sample_id
 
 
 def _values(l, first, count):
@@ -22,18 +20,17 @@ def _values(l, first, count):
     return [m + (s if (first + i) % 2 == 0 else -s) for i in range(count)]
 
 
-def _fake_level_estimate(cfg, level, first_id, count, want_samples=False):
-    first = first_id - sample_id(level, 0)
+def _sampler(level, first, count):
     y = _values(level, first, count)
     mean = math.fsum(y) / count
     m2 = math.fsum((v - mean) ** 2 for v in y)
-    return types.SimpleNamespace(N=count, mean=mean, M2=m2), None, None, None
+    return count, mean, m2
 
 
-@pytest.fixture
-def fake_gpu(monkeypatch):
-    monkeypatch.setattr(est_mod.mg, "mlmc_level_estimate", _fake_level_estimate)
-    monkeypatch.setattr(est_mod.mg, "make_mlmc_cfg", lambda *a, **k: None)
+def _est(**kw):
+    args = dict(levels=[0, 1], N_init=8, eps=2.5e-4, n0=9, cost_model="nodes", sampler=_sampler)
+    args.update(kw)
+    return MLMCEstimator(1, 1.0, 0.3, 8, **args)
 
 
 def _node_cost(n0):
@@ -45,9 +42,8 @@ def _node_cost(n0):
 
 
 @pytest.mark.parametrize("alpha,eps", [(None, 2.5e-4), (1.0, 2.5e-4), (1.0 / 3.0, 2.5e-4), (None, 1e-4)])
-def test_level_growth_matches_oracle_algorithm(fake_gpu, alpha, eps):
-    e = MLMCEstimator(1, 1.0, 0.3, 8, levels=[0, 1], N_init=8, eps=eps, n0=9, cost_model="nodes", max_level=6,
-                      alpha=alpha)
+def test_level_growth_matches_oracle_algorithm(alpha, eps):
+    e = _est(eps=eps, max_level=6, alpha=alpha)
     res = e.run(max_rounds=100)
     ref = oracle_adaptive.adaptive_mlmc(_values, _node_cost(9), eps=eps, N_init=8, max_level=6, alpha=alpha)
     assert res["L"] == ref["L"]
@@ -59,9 +55,8 @@ def test_level_growth_matches_oracle_algorithm(fake_gpu, alpha, eps):
     assert [entry["levels"][-1] for entry in e.log] == [entry["L"] for entry in ref["log"]]
 
 
-def test_max_level_cap_and_reported_rates(fake_gpu):
-    e = MLMCEstimator(1, 1.0, 0.3, 8, levels=[0, 1], N_init=8, eps=2.5e-4, n0=9, cost_model="nodes", max_level=2,
-                      alpha=1.0)
+def test_max_level_cap_and_reported_rates():
+    e = _est(max_level=2, alpha=1.0)
     res = e.run()
     assert res["L"] == 2 and not res["bias_ok"]
     alpha, beta, gamma = e.rates()
@@ -72,21 +67,21 @@ def test_max_level_cap_and_reported_rates(fake_gpu):
     assert gamma == pytest.approx(1.0, abs=0.1)
 
 
-def test_fixed_levels_unchanged_without_max_level(fake_gpu):
-    e = MLMCEstimator(1, 1.0, 0.3, 8, levels=[0, 1, 2], N_init=[8, 8, 8], eps=2.5e-4, n0=9, cost_model="nodes")
+def test_fixed_levels_unchanged_without_max_level():
+    e = _est(levels=[0, 1, 2], N_init=[8, 8, 8])
     res = e.run()
     assert res["levels"] == [0, 1, 2]
 
 
-def test_checkpoint_resume_after_growth(fake_gpu, tmp_path):
-    full = MLMCEstimator(1, 1.0, 0.3, 8, levels=[0, 1], N_init=8, eps=2.5e-4, n0=9, cost_model="nodes", max_level=6)
+def test_checkpoint_resume_after_growth(tmp_path):
+    full = _est(max_level=6)
     full.run()
-    part = MLMCEstimator(1, 1.0, 0.3, 8, levels=[0, 1], N_init=8, eps=2.5e-4, n0=9, cost_model="nodes", max_level=6)
+    part = _est(max_level=6)
     part.step()
     part.step()
     path = tmp_path / "ck.json"
     part.checkpoint(path)
-    resumed = MLMCEstimator.restore(path)
+    resumed = MLMCEstimator.restore(path, sampler=_sampler)
     while not resumed.step():
         pass
     assert resumed.levels == full.levels
@@ -99,3 +94,32 @@ def test_level_growth_arguments_validated():
         MLMCEstimator(1, 1.0, 0.3, 8, levels=[1, 2], N_init=8, eps=1e-3, max_level=4)
     with pytest.raises(ValueError):
         MLMCEstimator(1, 1.0, 0.3, 8, levels=[0, 1, 2], N_init=[8, 8], eps=1e-3)
+    import paper_1607_03252_gb300 as mg
+
+    for bad in (dict(eps=-1.0), dict(theta=1.0), dict(alpha0=0.0)):
+        with pytest.raises(mg.MlmcError):
+            _est(**bad)
+
+
+def test_state_rejected_by_another_configuration(tmp_path):
+    import paper_1607_03252_gb300 as mg
+
+    e = _est(max_level=6)
+    e.step()
+    e.step()
+    st = e.state()
+    st["params"]["max_level"] = None  # a fixed-level run cannot take a grown state
+    with pytest.raises(mg.MlmcError):
+        MLMCEstimator.from_state(st, sampler=_sampler)
+
+
+def test_sampler_error_is_reported():
+    import paper_1607_03252_gb300 as mg
+
+    def broken(level, first, count):
+        raise RuntimeError("no samples")
+
+    e = _est(sampler=broken)
+    with pytest.raises(mg.MlmcError) as ex:
+        e.step()
+    assert ex.value.status == mg.MLMC_ERR_INVALID

@@ -37,7 +37,7 @@ def test_resume_equals_uninterrupted(tmp_path):
 
 def test_estimator_level_records_match_batch_call():
     est = _est()
-    est.add_samples(1, 8)
+    est.step()  # the pilot round: 8 samples of level 1, ids (1 << 48) + 0 .. 7
     cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.3, 32, n0=9, rtol=1e-10)
     st, Y, _, _ = mg.mlmc_level_estimate(cfg, 1, (1 << 48), 8)
     n, mean, m2 = est.records[1]

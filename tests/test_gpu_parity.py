@@ -6,8 +6,11 @@ Tolerances (derived in the design notes):
   - u after a FIXED number of cycles: 1e-10 relative in the max norm (the same
     algorithm step by step; only rounding order differs);
   - converged u (rtol 1e-12): 1e-9 relative in the max norm;
-  - Y_l: |dY| <= 1e-9 * max(|Q_l|, |Q_{l-1}|) per sample in FP64, 1e-9 against the
-    oracle's FP32-faced operator in mixed precision (scale-normalised: Y_l << Q_l);
+  - Y_l: |dY| <= 1e-9 * max(|Q_l|, |Q_{l-1}|) per sample (scale-normalised: Y_l << Q_l),
+    in FP64 and in mixed precision alike: the mixed form (FP32 V-cycle corrections of
+    residuals taken on the FP64 operator) converges to the FP64 solution, so it is
+    compared with the FP64 oracle, and its error against FP64 is printed per result
+    ("mixed vs FP64"), far inside the 1e-7 that mixed precision is allowed;
   - cycle counts equal the oracle's within one cycle (a sample near the threshold may
     stop one cycle apart).
 """
@@ -111,17 +114,20 @@ def test_converged_solution_matches_oracle(orc, n):
         assert abs(int(cyc2[s]) - co) <= 1
 
 
-def test_mixed_precision_matches_oracle_mixed(orc):
+def test_mixed_precision_converges_to_the_fp64_solution(orc):
     n = 33
     ks = [orc.field(RUN_SEED, int(i), 256, 2.0, 0.1, n) for i in sample_ids(2, 0, 2)]
     u, cyc, rel, st = gpu_solve(ks, precision=mg.MLMC_PREC_MIXED, rtol=1e-12)
     assert st == 0 and np.all(rel <= 1e-12)
     for s in range(2):
-        um, *_ = orc.mg_solve(ks[s], None, rtol=1e-12, mixed=True)
         u64, *_ = orc.mg_solve(ks[s], None, rtol=1e-12)
-        assert relmax(u[s], um) < 1e-9
-        # the FP32 faces perturb the operator: stated error against the FP64 solution
-        assert relmax(u[s], u64) < 1e-6
+        um, *_ = orc.mg_solve(ks[s], None, rtol=1e-12, mixed=True)
+        err = relmax(u[s], u64)
+        print("mixed vs FP64 (u, max norm, sample %d): %.2e" % (s, err))
+        assert err < 1e-9
+        # the FP32-faced operator's solution is a different one (about 1e-7 away), so the
+        # test would see a solver that stopped at the FP32 operator
+        assert relmax(um, u64) > 10 * err
 
 
 def test_batch_composition_does_not_change_results():
@@ -203,17 +209,20 @@ def test_level_estimate_matches_oracle(orc, level):
         assert np.all(Qc == 0)
 
 
-def test_level_estimate_mixed_matches_oracle_mixed(orc):
+def _mixed_err(Y, Y64, Qf64, Qc64, what):
+    err = np.abs(Y - Y64) / np.maximum(np.abs(Qf64), np.abs(Qc64))
+    print("mixed vs FP64 (%s, |dY| / max|Q| per sample): %s" % (what, " ".join("%.1e" % e for e in err)))
+    return err
+
+
+def test_level_estimate_mixed_matches_oracle(orc):
     # sigma^2 = 2, ell = 0.2: the stationary V(2,2) cycle converges on every sample
     # (at ell = 0.1 some samples need far more than 100 cycles, on both sides)
     level, ids = 1, sample_ids(1, 10, 4)
     cfg = mg.make_mlmc_cfg(RUN_SEED, 2.0, 0.2, 256, n0=17, rtol=1e-11, precision=mg.MLMC_PREC_MIXED)
     _, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
-    Ym, Qfm, Qcm, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 2.0, 0.2, 256, rtol=1e-11, mixed=True), 33, 17, ids)
     Y64, Qf64, Qc64, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 2.0, 0.2, 256, rtol=1e-11), 33, 17, ids)
-    assert np.all(np.abs(Y - Ym) <= _y_tol(Qfm, Qcm, 1e-9))
-    # stated error of the mixed form against FP64, normalised by Q
-    assert np.all(np.abs(Y - Y64) <= _y_tol(Qf64, Qc64, 1e-6))
+    assert np.all(_mixed_err(Y, Y64, Qf64, Qc64, "level 1, iterative refinement") <= 1e-9)
 
 
 @pytest.mark.parametrize("level", [0, 1, 2])
@@ -238,11 +247,8 @@ def test_level_estimate_exp_covariance_mixed(orc):
     cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.1, 256, n0=17, precision=mg.MLMC_PREC_MIXED, accel=mg.MLMC_ACCEL_CG,
                            cov=mg.MLMC_COV_EXP, **kw)
     _, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
-    Ym, Qfm, Qcm, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 1.0, 0.1, 256, mixed=True, cov=orc.COV_EXP, **kw),
-                                       33, 17, ids)
     Y64, Qf64, Qc64, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 1.0, 0.1, 256, cov=orc.COV_EXP, **kw), 33, 17, ids)
-    assert np.all(np.abs(Y - Ym) <= _y_tol(Qfm, Qcm, 1e-9))
-    assert np.all(np.abs(Y - Y64) <= _y_tol(Qf64, Qc64, 1e-6))
+    assert np.all(_mixed_err(Y, Y64, Qf64, Qc64, "level 1, exponential covariance, CG") <= 1e-9)
 
 
 def test_level_estimate_batch_size_invariant():
@@ -343,8 +349,8 @@ def test_graph_replay_matches_direct_launches(orc, prec, accel, sm):
 @pytest.mark.parametrize("accel", [mg.MLMC_ACCEL_NONE, mg.MLMC_ACCEL_CG])
 def test_nodal_smoother_reaches_the_same_solution(orc, accel):
     """The nodal-coefficient sweep smooths an operator within a few ulps of the stored
-    FP32 one; the FP64 outer residual (stored faces) fixes the solution, so it converges
-    to the oracle-mixed solution like the stored-face smoothers (not bit for bit)."""
+    FP32 one; the FP64 outer residual (FP64 faces) fixes the solution, so it converges
+    to the FP64 solution like the stored-face smoothers (not bit for bit)."""
     n, B = 33, 3
     ks = [orc.field(RUN_SEED, int(i), 256, 1.0, 0.2, n) for i in sample_ids(2, 60, B)]
     k = to_dev(np.stack(ks))
@@ -355,20 +361,20 @@ def test_nodal_smoother_reaches_the_same_solution(orc, accel):
         assert st == 0 and np.all(rel <= 1e-12)
         out[sm] = (u.cpu().numpy(), cyc)
     for s in range(B):
-        um, *_ = orc.mg_solve(ks[s], None, rtol=1e-12, mixed=True)
-        assert relmax(out[mg.MLMC_SMOOTH_NODAL][0][s], um) < 1e-9
+        u64, *_ = orc.mg_solve(ks[s], None, rtol=1e-12)
+        assert relmax(out[mg.MLMC_SMOOTH_NODAL][0][s], u64) < 1e-9
         assert relmax(out[mg.MLMC_SMOOTH_NODAL][0][s], out[mg.MLMC_SMOOTH_TWO_PASS][0][s]) < 1e-9
     # the smoother's operator differs by ulps: the cycle counts stay within one of each other
     assert np.all(np.abs(out[mg.MLMC_SMOOTH_NODAL][1] - out[mg.MLMC_SMOOTH_TWO_PASS][1]) <= 1)
 
 
-def test_nodal_smoother_level_estimate_matches_oracle_mixed(orc):
+def test_nodal_smoother_level_estimate_matches_oracle(orc):
     level, ids = 1, sample_ids(1, 30, 4)
     cfg = mg.make_mlmc_cfg(RUN_SEED, 2.0, 0.2, 256, n0=17, rtol=1e-11, precision=mg.MLMC_PREC_MIXED,
                            smoother=mg.MLMC_SMOOTH_NODAL, accel=mg.MLMC_ACCEL_CG)
     _, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
-    Ym, Qfm, Qcm, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 2.0, 0.2, 256, rtol=1e-11, mixed=True), 33, 17, ids)
-    assert np.all(np.abs(Y - Ym) <= _y_tol(Qfm, Qcm, 1e-9))
+    Y64, Qf64, Qc64, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 2.0, 0.2, 256, rtol=1e-11), 33, 17, ids)
+    assert np.all(_mixed_err(Y, Y64, Qf64, Qc64, "level 1, nodal smoother, CG") <= 1e-9)
 
 
 def _direct(orc, k, mixed=False, f=None):
@@ -398,7 +404,7 @@ def test_cg_matches_sparse_direct_on_rough_field(orc, prec, n):
     assert cyc.max() < 45
     u = u.cpu().numpy()
     for s in range(len(ids)):
-        ud = _direct(orc, ks[s], mixed=(prec == mg.MLMC_PREC_MIXED))
+        ud = _direct(orc, ks[s])  # both precisions solve the FP64 operator
         assert relmax(u[s], ud) < 1e-9
 
 
