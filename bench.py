@@ -97,6 +97,8 @@ def parse():
     p.add_argument("--c5-eps", type=float, default=None, help="c5: override the RMS tolerance")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="c2: skip the c3 / c5 / c4 sub-records of the default line")
     p.add_argument("--lanes", type=int, default=4, help="concurrent level streams (1: levels in sequence)")
     p.add_argument("--plan-from", default=None,
                    help="reuse the autotuned choices (and pilot-sized N_l) of an earlier JSON line of the same "
@@ -303,22 +305,44 @@ def reference_arm(args):
 def own_arm(args):
     import torch
 
-    import paper_1607_03252_gb300 as mg
-
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    cfg, levels, N, single = workload(args.config)
+    line = measure(args, args.config, full=True)
+    if line is not None and world == 1 and args.config == "c2" and not args.no_extras:
+        # the mixed-precision and adaptive workloads of the same metric family, on the same
+        # GPU in the same run (sub-records; the headline stays the 4-level FP64 workload)
+        t0 = time.perf_counter()
+        line["c3"] = sub_c3(args)
+        line["c5"] = sub_c5(args)
+        line["c4"] = sub_c4(args, line["c3"])
+        line["extras_wall_s"] = time.perf_counter() - t0
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def measure(args, cfg_name, full=True):
+    """One workload's bench line (rank 0; None on other ranks). full: also the e2e and
+    cpu_baseline legs."""
+    import torch
+
+    import paper_1607_03252_gb300 as mg
+
+    rank, world, local = dist_env()
+    cfg, levels, N, single = workload(cfg_name)
     prec = mg.MLMC_PREC_F64 if cfg["precision"] == "f64" else mg.MLMC_PREC_MIXED
     accel = mg.MLMC_ACCEL_CG if cfg.get("accel") == "cg" else mg.MLMC_ACCEL_NONE
     stream = torch.cuda.Stream()
     dev = torch.device("cuda", local)
     plan = None
     nu_cfg = (cfg["nu1"], cfg["nu2"])
-    if args.plan_from:
+    if args.plan_from and cfg_name == args.config:
         N, plan = restore_plan(mg, cfg, levels, N, args.plan_from)
         if "N_init" in cfg:
             nu_cfg = (0, 0)
@@ -472,13 +496,13 @@ def own_arm(args):
 
     # end to end through the host-buffer C-ABI call
     e2e = None
-    if not args.no_e2e:
+    if full and not args.no_e2e:
         e2e = e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, accel, lanes)
 
     line = None
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu_baseline:
+        if full and world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(cfg, levels, N, single)
         line = {
             "metric": "MLMC samples/s (all levels, %s)" % cfg["name"], "value": value, "unit": "samples/s",
@@ -508,13 +532,14 @@ def own_arm(args):
                            "stream)",
             "profiled_region_ms_per_step": profiled_ms / args.steps,
             "kernel_ms_per_step": sum(v["ms"] for v in prof.values()) / args.steps,
-            "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
-                               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:10]},
+            "kernel_classes": class_shares(prof),
+            "kernel_sizes_top": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
+                                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
         }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
-    return 0
+        if prec == mg.MLMC_PREC_MIXED:
+            line["smoother_roofline"] = roofline(prof, peaks, lambda k: k.startswith("rbgs"))
+            line["residual_roofline"] = roofline(prof, peaks, lambda k: k.startswith("residual") and k.endswith("f32"))
+    return line
 
 
 def merge_records(parts):
@@ -526,33 +551,71 @@ def merge_records(parts):
     return np.array(merge_levels([[tuple(row) for row in p] for p in parts]))
 
 
-def roofline(prof, peaks):
-    if not prof:
+def base_class(name):
+    """Launch class without its grid-size tag ("rbgs_f64@129" -> "rbgs_f64")."""
+    return name.split("@")[0]
+
+
+def class_shares(prof):
+    """Device time per launch class (grid sizes merged), share of the profiled total."""
+    agg = {}
+    for k, v in prof.items():
+        a = agg.setdefault(base_class(k), {"launches": 0, "ms": 0.0})
+        a["launches"] += v["launches"]
+        a["ms"] += v["ms"]
+    tot = sum(v["ms"] for v in agg.values()) or 1.0
+    return {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share": round(v["ms"] / tot, 4)}
+            for k, v in sorted(agg.items(), key=lambda kv: -kv[1]["ms"])[:12]}
+
+
+def roofline(prof, peaks, keep=None):
+    """The dominant launch class (one grid size) among those `keep` accepts: algorithmic
+    work per launch (active samples only) over its event-timed average launch time."""
+    items = [(k, v) for k, v in prof.items() if keep is None or keep(base_class(k))]
+    if not items:
         return None
-    name, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    # the dominant kernel class (grid sizes merged), then its grid size with the most time
+    tot = {}
+    for k, v in items:
+        tot[base_class(k)] = tot.get(base_class(k), 0.0) + v["ms"]
+    top = max(tot, key=tot.get)
+    name, rec = max(((k, v) for k, v in items if base_class(k) == top), key=lambda kv: kv[1]["ms"])
+    base = base_class(name)
     timed = max(rec["timed"], 1)
     avg_s = rec["ms"] / 1e3 / timed
     per_launch_bytes = rec["bytes"] / max(rec["launches"], 1)
     per_launch_flops = rec["flops"] / max(rec["launches"], 1)
     hbm_peak = peaks.get("hbm_gbs")
-    fp64 = name.endswith("f64") or name in ("residual_mixed", "update_mixed", "coarse_setup", "norm")
-    traffic, tsrc = traffic_per_launch(name, rec)
+    fp64 = base.endswith("f64") or base in ("residual_mixed", "update_mixed", "coarse_setup", "norm")
+    traffic, tsrc = traffic_per_launch(base, rec)
+    share = rec["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-30)
+    out = {"kernel": name, "share_of_profiled_time": share, "class_share_of_profiled_time":
+           tot[top] / max(sum(v["ms"] for v in prof.values()), 1e-30), "avg_launch_ms": avg_s * 1e3,
+           "launches": rec["launches"], "traffic": traffic, "traffic_source": tsrc,
+           "dram_gbs_from_traffic": traffic / avg_s / 1e9 if traffic else None}
+    if base.startswith("rbgs") and not base.startswith("rbgs_nodal") and per_launch_flops > 0:
+        # the same work at the nodal-coefficient floor of 4 words per node and sweep: a
+        # colour pass (6.5 flops per updated node) updates half the nodes and moves 2 words
+        # per node, i.e. 4 per updated node; a fused sweep (13 flops per node) 4 per node
+        fused = "fused" in base or "bulk" in base
+        nodes = per_launch_flops / 13.0 if fused else per_launch_flops / 6.5
+        word = 8 if base.endswith("f64") else 4
+        floor = nodes * 4 * word / avg_s / 1e9
+        out["hbm_gbs_at_4word_floor"] = floor
+        out["hbm_frac_at_4word_floor"] = floor / hbm_peak if hbm_peak else None
     if fp64:
         achieved = per_launch_flops / avg_s / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
-                "traffic": traffic, "traffic_source": tsrc, "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"],
-                "hbm_achieved_gbs": per_launch_bytes / avg_s / 1e9,
-                "hbm_frac_of_measured": (per_launch_bytes / avg_s / 1e9) / hbm_peak if hbm_peak else None,
-                "dram_gbs_from_traffic": traffic / avg_s / 1e9 if traffic else None}
+        out.update({"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                    "hbm_achieved_gbs": per_launch_bytes / avg_s / 1e9,
+                    "hbm_frac_of_measured": (per_launch_bytes / avg_s / 1e9) / hbm_peak if hbm_peak else None})
+        return out
     achieved = per_launch_bytes / avg_s / 1e9
     peak = hbm_peak if hbm_peak else 6800.0
-    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": "measured" if hbm_peak else "fallback", "traffic": traffic,
-            "traffic_source": tsrc,
-            "avg_launch_ms": avg_s * 1e3, "launches": rec["launches"],
-            "dram_gbs_from_traffic": traffic / avg_s / 1e9 if traffic else None}
+    out.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": "measured" if hbm_peak else "fallback"})
+    return out
 
 
 def lane_items(levels, N, times, lanes):
@@ -680,26 +743,12 @@ def cpu_baseline(cfg, levels, N, single):
             "per_level": {str(l): rates[l] for l in levels}}
 
 
-def serving_arm(args):
-    """c4: open-loop Poisson stream of single-sample requests into the solve service."""
+def serving_run(mg, probs, levels, cfg):
+    """The serving loop of c4: returns run(rate, count, seed, burst) -> latency record."""
     import numpy as np
-    import torch
 
-    import paper_1607_03252_gb300 as mg
     from paper_1607_03252_gb300.workloads import level_draws, poisson_arrivals
 
-    rank, world, local = dist_env()
-    if rank != 0:
-        return 0
-    torch.cuda.set_device(local)
-    cfg = CONFIGS["c4"]
-    c3 = CONFIGS["c3"]
-    levels = cfg["levels"]
-    stream = torch.cuda.Stream()
-    N, plan = plan_levels(mg, c3, levels, stream, 0)  # autotunes every level, pilot, Eq. 11
-    C = plan["pilot_cost_s"]
-    probs = np.array([n * c for n, c in zip(N, C)])
-    probs = probs / probs.sum()
     field = mg.field_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"])
     mgc = mg.mg_cfg(0, 0, cfg["rtol"], 300, mg.MLMC_PREC_MIXED, mg.MLMC_SMOOTH_AUTO, mg.MLMC_ACCEL_CG)
     counter = [0]
@@ -728,25 +777,110 @@ def serving_arm(args):
                 "p99_ms": {str(l): float(np.percentile(v, 99)) if v else None for l, v in lat.items()},
                 "count": {str(l): len(v) for l, v in lat.items()}, "wall_s": t_end - t0}
 
-    sat = run(0.0, 1200, 11, burst=True)["completed_per_s"]
+    return run
+
+
+def serving_line(mg, probs, levels, cfg, plan, burst_count, fracs, max_count, seconds_per_point):
+    run = serving_run(mg, probs, levels, cfg)
+    sat = run(0.0, burst_count, 11, burst=True)["completed_per_s"]
     sweep = []
-    for frac in (0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.2):
+    for frac in fracs:
         rate = frac * sat
-        count = int(min(3000, max(200, rate * 3.0)))
+        count = int(min(max_count, max(150, rate * seconds_per_point)))
         r = run(rate, count, 100 + int(frac * 100))
         r["load_fraction"] = frac
         sweep.append(r)
-    line = {"metric": "MLMC samples/s at saturation, served (c4: single-sample Poisson requests, levels 17^3..257^3)",
+    return {"metric": "MLMC samples/s at saturation, served (c4: single-sample Poisson requests, levels 17^3..257^3)",
             "value": sat, "unit": "samples/s", "n_gpus": 1, "steps": len(sweep), "warmup": 1, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic (seeded Philox realisations, Poisson arrivals)",
-            "config": {"workload": cfg["name"], "levels": levels, "level_probability": probs.tolist(),
+            "config": {"workload": cfg["name"], "levels": levels, "level_probability": list(map(float, probs)),
                        "service": {"max_batch": 64, "workers": 3, "batch_wait_ms": 2.0, "hbm_budget_gb": 96},
                        "sigma2": cfg["sigma2"], "ell": cfg["ell"], "M": cfg["M"], "rtol": cfg["rtol"],
-                       "solver": "FP64 flexible CG, FP32 V-cycle preconditioner (autotuned smoother, nu)"},
+                       "solver": "FP64 flexible CG, FP32 V-cycle preconditioner (autotuned smoother, nu)",
+                       "saturation_burst_requests": burst_count},
             "serving_sweep": sweep, "plan": plan}
+
+
+def serving_arm(args):
+    """c4: open-loop Poisson stream of single-sample requests into the solve service."""
+    import numpy as np
+    import torch
+
+    import paper_1607_03252_gb300 as mg
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    cfg = CONFIGS["c4"]
+    levels = cfg["levels"]
+    stream = torch.cuda.Stream()
+    N, plan = plan_levels(mg, CONFIGS["c3"], levels, stream, 0)  # autotunes every level, pilot, Eq. 11
+    probs = np.array([n * c for n, c in zip(N, plan["pilot_cost_s"])])
+    probs = probs / probs.sum()
+    line = serving_line(mg, probs, levels, cfg, plan, 1200, (0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.2), 3000, 3.0)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def sub_c3(args):
+    """The mixed-precision 5-level workload measured like the headline, plus the error of
+    its Y_l against FP64 solves of the same realisations (first ids of every level)."""
+    import numpy as np
+    import torch
+
+    import paper_1607_03252_gb300 as mg
+
+    line = measure(args, "c3", full=False)
+    cfg = CONFIGS["c3"]
+    stream = torch.cuda.Stream()
+    errs, worst = {}, 0.0
+    for l in cfg["levels"]:
+        K = 4 if l < 4 else 2
+        first = int(sample_ids(l, 0, 1)[0])
+        kw = dict(n0=17, rtol=cfg["rtol"], accel=mg.MLMC_ACCEL_CG, max_cycles=300, stream=stream)
+        cm = mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], nu1=0, nu2=0,
+                              precision=mg.MLMC_PREC_MIXED, **kw)
+        c64 = mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], nu1=2, nu2=2, precision=mg.MLMC_PREC_F64,
+                               smoother=mg.MLMC_SMOOTH_TWO_PASS, **kw)
+        _, Ym, _, _ = mg.mlmc_level_estimate(cm, l, first, K)
+        _, Y64, Qf64, Qc64 = mg.mlmc_level_estimate(c64, l, first, K)
+        e = np.abs(Ym - Y64) / np.maximum(np.abs(Qf64), np.abs(Qc64))
+        errs[str(l)] = float(e.max())
+        worst = max(worst, float(e.max()))
+    line["mixed_err_vs_f64"] = {"max": worst, "per_level": errs, "samples_per_level": "4 (2 on level 4)",
+                                "how": "|Y_mixed - Y_f64| / max(|Qf_f64|, |Qc_f64|) per sample, both solved to "
+                                       "rtol 1e-10 (FP64 flexible CG with an FP64 V-cycle as the reference)"}
+    return line
+
+
+def sub_c4(args, c3line):
+    """A short serving sweep of the c4 workload (levels drawn with probability N_l C_l of
+    the c3 plan just measured; the tuning table of that plan is in place)."""
+    import numpy as np
+
+    import paper_1607_03252_gb300 as mg
+
+    plan = (c3line or {}).get("plan") or {}
+    N, C = plan.get("N_from_eq11"), plan.get("pilot_cost_s")
+    if not N or not C:
+        return None
+    probs = np.array([n * c for n, c in zip(N, C)])
+    probs = probs / probs.sum()
+    return serving_line(mg, probs, CONFIGS["c4"]["levels"], CONFIGS["c4"], {"from": "c3 plan of this run"}, 400,
+                        (0.25, 0.5, 0.9), 600, 2.0)
+
+
+def sub_c5(args):
+    import torch
+
+    import paper_1607_03252_gb300 as mg
+
+    line = c5_results(args, mg, torch)
+    for arm in line["arms"].values():
+        arm.pop("rounds_log", None)
+    return line
 
 
 def adaptive_mlmc(mg, torch, cfg, eps, mode, stream, log, lanes=1):
@@ -783,6 +917,11 @@ def c5_arm(args):
     if rank != 0:
         return 0
     torch.cuda.set_device(local)
+    print(json.dumps(c5_results(args, mg, torch)), flush=True)
+    return 0
+
+
+def c5_results(args, mg, torch):
     cfg = CONFIGS["c5"]
     eps = args.c5_eps or cfg["eps"]
     stream = torch.cuda.Stream()
@@ -809,8 +948,7 @@ def c5_arm(args):
                        "N_init": cfg["N_init"], "rtol": cfg["rtol"]},
             "autotune": tune, "arms": out,
             "speedup_plain_over_fast": (plain["wall_s"] / fast["wall_s"]) if (fast and plain) else None}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def main():

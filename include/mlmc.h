@@ -122,6 +122,17 @@ typedef struct {
                                     outer residual on the stored faces fixes the solution: results
                                     agree with the other smoothers to the solve tolerance, not bit
                                     for bit. An FP64 solve uses MLMC_SMOOTH_TWO_PASS. */
+#define MLMC_SMOOTH_SPLIT 9      /* MLMC_SMOOTH_NODAL's sweep (bit for bit the same iterates) with
+                                    the FP32 hierarchy stored colour-split: per sample the red
+                                    ((x+y+z) even) and the black nodes form two blocks of n x n
+                                    rows of (n+1)/2 slots (node x at slot x/2), so that a colour
+                                    pass streams the rows of the colour it updates and of the
+                                    other colour it reads, 2.5 instead of 4 words per node at
+                                    cache-line granularity. Chosen for the finest grid, it
+                                    applies to every grid of the hierarchy; on a coarser grid
+                                    alone it means MLMC_SMOOTH_NODAL. FP32 correction cycles on
+                                    finite volumes only (an FP64 solve uses
+                                    MLMC_SMOOTH_TWO_PASS). */
 
 /* Outer iteration around the V-cycle. */
 #define MLMC_ACCEL_NONE 0 /* stationary: repeat V-cycles (FP64), or FP32 V-cycles as corrections of
@@ -505,9 +516,9 @@ typedef struct {
 
 /*
  * mlmc_autotune -- picks the smoother implementation (two-pass on stored faces, two-pass
- * on the nodal coefficient, or fused with 32x8, 32x16 or 64x8 tiles staged by cp.async
- * or by TMA bulk copies: 8 candidates; 7 for FP64 solves and P1 finite elements, which
- * have no nodal-coefficient sweep) and the sweep count
+ * on the nodal coefficient in the plain or the colour-split storage, or fused with 32x8,
+ * 32x16 or 64x8 tiles staged by cp.async or by TMA bulk copies: 9 candidates; 7 for FP64
+ * solves and P1 finite elements, which have no nodal-coefficient sweep) and the sweep count
  * nu in {1,2,3} of V(nu, nu) for MLMC level
  * `level` under cfg (no counterpart in the paper; the paper fixes its cycle, Sec. 7.1).
  * Each candidate runs the whole level pipeline once untimed and once timed on
@@ -530,7 +541,7 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
  * (for example in a run without a profiler attached) without measuring again. No
  * counterpart in the paper. Host-only, thread-safe, no device work. Errors:
  * MLMC_ERR_INVALID for n not 2^p+1 (5 <= n <= 4097), an unknown precision, smoother
- * outside MLMC_SMOOTH_TWO_PASS .. MLMC_SMOOTH_NODAL, or nu outside 1..8.
+ * outside MLMC_SMOOTH_TWO_PASS .. MLMC_SMOOTH_SPLIT, or nu outside 1..8.
  */
 int mlmc_tune_set(int n, int precision, int smoother, int nu);
 

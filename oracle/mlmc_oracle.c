@@ -34,7 +34,11 @@
  *   QoI       Q = mean of u over [0.25, 0.75]^3 by the tensor trapezoid rule.
  *
  * Every loop below follows those definitions directly; nothing is blocked, fused or
- * reordered. Compile with -ffp-contract=off so that no multiply-add is contracted.
+ * reordered. Compile with -ffp-contract=off so that no multiply-add is contracted. Loops
+ * whose nodes are computed independently of each other (field, operator application,
+ * residual, one colour of a sweep, restriction, prolongation) run their planes on OpenMP
+ * threads when not already inside a parallel region; no node's arithmetic changes, and
+ * every sum over nodes stays sequential.
  */
 #include <math.h>
 #include <stdint.h>
@@ -180,6 +184,7 @@ int orc_field(uint64_t run_seed, uint64_t sample_id, int M, double sigma, double
   if (!w || !b) { free(w); free(b); return ORC_ERR_OOM; }
   orc_features(run_seed, sample_id, M, ell, cov, w, b);
   double h = 1.0 / (double)(n - 1);
+#pragma omp parallel for schedule(static) if (!omp_in_parallel())
   for (int kz = 0; kz < n; ++kz)
     for (int jy = 0; jy < n; ++jy)
       for (int ix = 0; ix < n; ++ix)
@@ -233,6 +238,7 @@ static double apply_at(int n, const double* kn, const double* u, int i, int j, i
 
 /* A u on all interior nodes; boundary entries of Au are set to zero. */
 void orc_apply(int n, const double* kn, const double* u, double* Au, int mixed, double c) {
+#pragma omp parallel for schedule(static) if (!omp_in_parallel())
   for (int k = 0; k < n; ++k)
     for (int j = 0; j < n; ++j)
       for (int i = 0; i < n; ++i)
@@ -275,6 +281,7 @@ int orc_assemble_csr(int n, const double* kn, int mixed, double c, int* indptr, 
 
 /* r = f - A u on interior nodes, zero on the boundary. f == NULL means f = 1. */
 void orc_residual(int n, const double* kn, const double* f, const double* u, double* r, int mixed, double c) {
+#pragma omp parallel for schedule(static) if (!omp_in_parallel())
   for (int k = 0; k < n; ++k)
     for (int j = 0; j < n; ++j)
       for (int i = 0; i < n; ++i) {
@@ -290,7 +297,9 @@ void orc_residual(int n, const double* kn, const double* f, const double* u, dou
 void orc_rbgs_sweep(int n, const double* kn, const double* f, double* u, int mixed, double c) {
   static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
   double h = 1.0 / (double)(n - 1);
-  for (int colour = 0; colour < 2; ++colour)
+  for (int colour = 0; colour < 2; ++colour) {
+    /* a node of one colour reads only nodes of the other: any order gives the same values */
+#pragma omp parallel for schedule(static) if (!omp_in_parallel())
     for (int k = 1; k < n - 1; ++k)
       for (int j = 1; j < n - 1; ++j)
         for (int i = 1; i < n - 1; ++i) {
@@ -306,6 +315,7 @@ void orc_rbgs_sweep(int n, const double* kn, const double* f, double* u, int mix
           }
           u[p] = num / (den + c * h * h);
         }
+  }
 }
 
 /* Full weighting: coarse value at interior coarse node I is
@@ -313,6 +323,7 @@ void orc_rbgs_sweep(int n, const double* kn, const double* f, double* u, int mix
  * Coarse boundary values are zero. */
 void orc_restrict_fw(int nf, const double* r, double* rc) {
   int nc = (nf + 1) / 2;
+#pragma omp parallel for schedule(static) if (!omp_in_parallel())
   for (int K = 0; K < nc; ++K)
     for (int J = 0; J < nc; ++J)
       for (int I = 0; I < nc; ++I) {
@@ -334,6 +345,7 @@ void orc_restrict_fw(int nf, const double* r, double* rc) {
  * with weight 1 on a coincident axis and 1/2 on each neighbour otherwise. */
 void orc_prolong_add(int nf, const double* ec, double* u) {
   int nc = (nf + 1) / 2;
+#pragma omp parallel for schedule(static) if (!omp_in_parallel())
   for (int k = 1; k < nf - 1; ++k)
     for (int j = 1; j < nf - 1; ++j)
       for (int i = 1; i < nf - 1; ++i) {

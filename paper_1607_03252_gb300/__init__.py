@@ -14,7 +14,7 @@ from ._capi import (  # noqa: F401
     MLMC_ERR_BUSY, MLMC_ERR_CANCELLED, MLMC_ERR_CUDA, MLMC_ERR_INVALID, MLMC_ERR_NOT_CONVERGED, MLMC_ERR_NOT_FOUND, MLMC_ERR_OOM,
     MLMC_ACCEL_FMG, MLMC_COV_EXP, MLMC_COV_GAUSS, MLMC_COV_SPDE, MLMC_DISC_FE, MLMC_DISC_FV, MLMC_QOI_FLUX,
     MLMC_QOI_MEAN, MLMC_QOI_POINT, MLMC_ERR_TIMEOUT, MLMC_F32, MLMC_F64, MLMC_OK, MLMC_PENDING, MLMC_PREC_F64, MLMC_PREC_MIXED, MLMC_ACCEL_NONE, MLMC_ACCEL_CG, MLMC_SMOOTH_AUTO,
-    MLMC_SMOOTH_BULK_32x8, MLMC_SMOOTH_BULK_32x16, MLMC_SMOOTH_BULK_64x8, MLMC_SMOOTH_NODAL, MLMC_SMOOTH_FUSED_32x8,
+    MLMC_SMOOTH_BULK_32x8, MLMC_SMOOTH_BULK_32x16, MLMC_SMOOTH_BULK_64x8, MLMC_SMOOTH_NODAL, MLMC_SMOOTH_SPLIT, MLMC_SMOOTH_FUSED_32x8,
     MLMC_SMOOTH_FUSED_32x16, MLMC_SMOOTH_FUSED_64x8, MLMC_SMOOTH_TWO_PASS, SIGNATURES,
     FieldCfg, LevelStats, MgCfg, MgStats, MlmcCfg, MlmcError, field_cfg, lib, library_path, make_mlmc_cfg, mg_cfg,
     mg_solve_batch, mlmc_field_eval, mlmc_level_estimate, mlmc_level_run, mlmc_autotune, mlmc_tune_set, profile_enable, profile_fma_peak, profile_read,

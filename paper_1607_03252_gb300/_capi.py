@@ -71,6 +71,7 @@ MLMC_SMOOTH_BULK_32x8 = 5
 MLMC_SMOOTH_BULK_32x16 = 6
 MLMC_SMOOTH_BULK_64x8 = 7
 MLMC_SMOOTH_NODAL = 8
+MLMC_SMOOTH_SPLIT = 9
 
 
 MLMC_ACCEL_NONE = 0
@@ -373,15 +374,15 @@ def mlmc_level_run(cfg: MlmcCfg, level: int, ids_dev, Y_dev=None, Qf_dev=None, Q
 SMOOTHER_NAMES = {MLMC_SMOOTH_TWO_PASS: "two-pass", MLMC_SMOOTH_FUSED_32x8: "fused 32x8",
                   MLMC_SMOOTH_FUSED_32x16: "fused 32x16", MLMC_SMOOTH_FUSED_64x8: "fused 64x8",
                   MLMC_SMOOTH_BULK_32x8: "bulk 32x8", MLMC_SMOOTH_BULK_32x16: "bulk 32x16",
-                  MLMC_SMOOTH_BULK_64x8: "bulk 64x8", MLMC_SMOOTH_NODAL: "nodal"}
+                  MLMC_SMOOTH_BULK_64x8: "bulk 64x8", MLMC_SMOOTH_NODAL: "nodal", MLMC_SMOOTH_SPLIT: "split"}
 
 
 def mlmc_autotune(cfg: MlmcCfg, level: int, first_id: int, samples: int):
     """Returns (table as list of dicts, best smoother, best nu); the choice is stored
     for the level's fine grid in the library's tuning table."""
-    tab = (TuneEntry * 24)()
+    tab = (TuneEntry * 32)()
     cnt, bs, bnu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(lib().mlmc_autotune(ctypes.byref(cfg), int(level), int(first_id), int(samples), tab, 24,
+    _check(lib().mlmc_autotune(ctypes.byref(cfg), int(level), int(first_id), int(samples), tab, 32,
                                ctypes.byref(cnt), ctypes.byref(bs), ctypes.byref(bnu)), "mlmc_autotune")
     rows = [dict(smoother=SMOOTHER_NAMES.get(t.smoother, t.smoother), nu=t.nu,
                  ms_per_sample=1e3 * t.seconds_per_sample, cycles=t.mean_cycles) for t in tab[:cnt.value]]
@@ -391,7 +392,8 @@ def mlmc_autotune(cfg: MlmcCfg, level: int, first_id: int, samples: int):
 SMOOTHER_IDS = {v: k for k, v in {MLMC_SMOOTH_TWO_PASS: "two-pass", MLMC_SMOOTH_FUSED_32x8: "fused 32x8",
                                    MLMC_SMOOTH_FUSED_32x16: "fused 32x16", MLMC_SMOOTH_FUSED_64x8: "fused 64x8",
                                    MLMC_SMOOTH_BULK_32x8: "bulk 32x8", MLMC_SMOOTH_BULK_32x16: "bulk 32x16",
-                                   MLMC_SMOOTH_BULK_64x8: "bulk 64x8", MLMC_SMOOTH_NODAL: "nodal"}.items()}
+                                   MLMC_SMOOTH_BULK_64x8: "bulk 64x8", MLMC_SMOOTH_NODAL: "nodal",
+                                   MLMC_SMOOTH_SPLIT: "split"}.items()}
 
 
 def mlmc_tune_set(n: int, precision: int, smoother, nu: int):

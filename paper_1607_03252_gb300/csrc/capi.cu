@@ -73,7 +73,7 @@ static int check_mg(const mg_cfg* c) {
     set_error("nu1=%d nu2=%d out of range 0..8 (both 0: tuned count)", c->nu1, c->nu2);
     return MLMC_ERR_INVALID;
   }
-  if (c->smoother < MLMC_SMOOTH_AUTO || c->smoother > MLMC_SMOOTH_NODAL) {
+  if (c->smoother < MLMC_SMOOTH_AUTO || c->smoother > MLMC_SMOOTH_SPLIT) {
     set_error("unknown smoother %d", c->smoother);
     return MLMC_ERR_INVALID;
   }
@@ -590,9 +590,9 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   cudaStream_t st = (cudaStream_t)cfg->stream;
   int B = 0;
   MLMC_TRY(choose_batch(cfg, samples, nf, nc, &B));
-  const int smoothers[8] = {MLMC_SMOOTH_TWO_PASS,  MLMC_SMOOTH_FUSED_32x8, MLMC_SMOOTH_FUSED_32x16,
+  const int smoothers[9] = {MLMC_SMOOTH_TWO_PASS,  MLMC_SMOOTH_FUSED_32x8, MLMC_SMOOTH_FUSED_32x16,
                             MLMC_SMOOTH_FUSED_64x8, MLMC_SMOOTH_BULK_32x8, MLMC_SMOOTH_BULK_32x16,
-                            MLMC_SMOOTH_BULK_64x8,  MLMC_SMOOTH_NODAL};
+                            MLMC_SMOOTH_BULK_64x8,  MLMC_SMOOTH_NODAL,     MLMC_SMOOTH_SPLIT};
   std::vector<uint64_t> ids(samples);
   for (int i = 0; i < samples; ++i) ids[i] = first_id + (uint64_t)i;
   int count = 0, bs = MLMC_SMOOTH_TWO_PASS, bnu = 2;
@@ -600,8 +600,8 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   // an explicit V(nu, nu) in cfg is kept: only the smoother implementation is tuned
   const bool fixed_nu = cfg->mg.nu1 > 0 && cfg->mg.nu1 == cfg->mg.nu2;
   const int nu_lo = fixed_nu ? cfg->mg.nu1 : 1, nu_hi = fixed_nu ? cfg->mg.nu1 : 3;
-  // the nodal-coefficient sweep exists only in FP32 correction cycles on finite volumes
-  const int n_sm = (cfg->mg.precision == MLMC_PREC_MIXED && cfg->mg.disc == MLMC_DISC_FV) ? 8 : 7;
+  // the nodal-coefficient sweeps exist only in FP32 correction cycles on finite volumes
+  const int n_sm = (cfg->mg.precision == MLMC_PREC_MIXED && cfg->mg.disc == MLMC_DISC_FV) ? 9 : 7;
   for (int nu = nu_lo; nu <= nu_hi; ++nu)
     for (int si = 0; si < n_sm; ++si) {
       mg_cfg mc = cfg->mg;
@@ -650,7 +650,7 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
 
 int mlmc_tune_set(int n, int precision, int smoother, int nu) {
   if (!valid_grid(n) || (precision != MLMC_PREC_F64 && precision != MLMC_PREC_MIXED) ||
-      smoother < MLMC_SMOOTH_TWO_PASS || smoother > MLMC_SMOOTH_NODAL || nu < 1 || nu > 8) {
+      smoother < MLMC_SMOOTH_TWO_PASS || smoother > MLMC_SMOOTH_SPLIT || nu < 1 || nu > 8) {
     set_error("mlmc_tune_set: invalid arguments (n=%d precision=%d smoother=%d nu=%d)", n, precision, smoother, nu);
     return MLMC_ERR_INVALID;
   }

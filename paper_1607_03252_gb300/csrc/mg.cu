@@ -53,6 +53,16 @@ inline dim3 plane_grid(int per_plane, long long planes) {
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Colour-split storage (see the colour-split kernels below).
+__host__ __device__ __forceinline__ int split_pitch(int n) { return (n + 1) >> 1; }
+// elements of one sample in colour-split storage
+__host__ __device__ __forceinline__ size_t split_elems(int n) { return (size_t)n * n * (size_t)(n + 1); }
+__device__ __forceinline__ unsigned split_index(int n, int x, int y, int z) {
+  const int P = split_pitch(n);
+  return (unsigned)((x + y + z) & 1) * (unsigned)(n * n * P) + (unsigned)((z * n + y) * P + (x >> 1));
+}
+
+
 // Carves 256-byte aligned pieces; with base == nullptr it only measures.
 struct Carver {
   char* base;
@@ -196,8 +206,9 @@ __global__ void k_coarse_setup(int B, const T* __restrict__ Kx, const T* __restr
   }
 }
 
-// u = A~^-1 g on the 5^3 grid (interior nodes; boundary untouched).
-template <typename T>
+// u = A~^-1 g on the 5^3 grid (interior nodes; boundary untouched); SPLIT: g and u in
+// colour-split storage.
+template <typename T, bool SPLIT = false>
 __global__ void k_coarse_apply(int B, const double* __restrict__ Ainv, const T* __restrict__ g, T* __restrict__ u,
                                const int* __restrict__ active) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -205,14 +216,17 @@ __global__ void k_coarse_apply(int B, const double* __restrict__ Ainv, const T* 
   const int s = t / 27, i = t - s * 27;
   if (active && !active[s]) return;
   const double* X = Ainv + (size_t)s * 729 + (size_t)i * 27;
-  const size_t base = (size_t)s * 125;
+  const size_t base = (size_t)s * (SPLIT ? split_elems(5) : (size_t)125);
+  auto at = [&](int x, int y, int z) -> size_t {
+    return base + (SPLIT ? (size_t)split_index(5, x, y, z) : (size_t)((z * 5 + y) * 5 + x));
+  };
   double v = 0.0;
   for (int j = 0; j < 27; ++j) {
     const int x = 1 + j % 3, y = 1 + (j / 3) % 3, z = 1 + j / 9;
-    v = fma(X[j], (double)g[base + (z * 5 + y) * 5 + x], v);
+    v = fma(X[j], (double)g[at(x, y, z)], v);
   }
   const int x = 1 + i % 3, y = 1 + (i / 3) % 3, z = 1 + i / 9;
-  u[base + (z * 5 + y) * 5 + x] = (T)v;
+  u[at(x, y, z)] = (T)v;
 }
 
 // ---------------------------------------------------------------------------------
@@ -349,6 +363,182 @@ __global__ void k_residual_nodal(int n, int B, const float* __restrict__ kn, con
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Colour-split storage of the FP32 correction hierarchy (MLMC_SMOOTH_SPLIT): per sample
+// the nodes of colour c = (x + y + z) & 1 form one block of n x n rows of P = (n + 1) / 2
+// slots, node (x, y, z) at slot x >> 1 of row (z, y) of its colour's block. A colour pass
+// of the red-black sweep then streams the lines of the colour it updates plus those of
+// the other colour it reads (2.5 instead of 4 words per node and pass at line
+// granularity). Neighbours of node x = 2 xi + q (q = x parity) in the other colour: x - 1
+// at slot xi - 1 + q, x + 1 at slot xi + q, y +- 1 and z +- 1 at slot xi. The slot x = n
+// of odd-parity rows does not exist in the grid and is never read.
+// ---------------------------------------------------------------------------------
+// Reciprocal nodal coefficient 1/k of an FP32 grid (every node) into colour-split storage.
+__global__ void k_nodal_k_split(const double* __restrict__ k0, int n0, int st0, int n, int B, float* __restrict__ kn) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
+  const size_t ns = split_elems(n), n03 = (size_t)n0 * n0 * n0;
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    const size_t p0 = ((size_t)(st0 * z) * n0 + (size_t)(st0 * y)) * n0 + (size_t)(st0 * x);
+    kn[(size_t)s * ns + split_index(n, x, y, z)] = (float)(1.0 / k0[(size_t)s * n03 + p0]);
+  }
+}
+
+// Compile-time geometry of a colour-split grid of n = 2^LG + 1 nodes per axis: with n a
+// constant, the row / slot split of a thread index and every neighbour offset are
+// shifts, multiplications by constants and immediate load offsets (the runtime-n form of
+// these kernels spent about 280 instructions per updated node and was issue-bound).
+template <int LG>
+struct SplitGeo {
+  static constexpr int n = (1 << LG) + 1, m = n - 2, P = (n + 1) / 2, NP = n * P, BLK = n * n * P;
+  static constexpr size_t NS = (size_t)2 * BLK;  // elements per sample
+};
+
+// One colour of the nodal-coefficient red-black sweep on colour-split storage: the same
+// operations in the same order as k_rbgs_nodal (bit for bit the same iterate). Grid
+// (slot blocks of the interior rows of a plane, interior planes, samples).
+template <int LG>
+__global__ void __launch_bounds__(128) k_rbgs_split(int colour, const float* __restrict__ kn,
+                                                    const float* __restrict__ g, float* __restrict__ u,
+                                                    const int* __restrict__ active) {
+  using G = SplitGeo<LG>;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // slot of an interior row
+  if (q >= G::m * G::P) return;
+  const int s = blockIdx.z;
+  if (active && !active[s]) return;
+  const int yi = q / G::P, xi = q - yi * G::P, y = 1 + yi, z = 1 + (int)blockIdx.y;
+  const int par = (colour + y + z) & 1, x = 2 * xi + par;
+  if (x < 1 || x > G::n - 2) return;
+  const int o = (z * G::n + y) * G::P + xi;  // slot of the node (own colour) and of y, z neighbours
+  const size_t cb = (size_t)s * G::NS + (size_t)colour * G::BLK, ob = (size_t)s * G::NS + (size_t)(1 - colour) * G::BLK;
+  const float* kc_ = kn + cb;
+  const float* ko = kn + ob;
+  const float* uo = u + ob;
+  const int l = o - 1 + par, r = o + par;
+  const float kc = kc_[o];
+  const float kxm = nodal_face(ko[l], kc), kxp = nodal_face(kc, ko[r]);
+  const float kym = nodal_face(ko[o - G::P], kc), kyp = nodal_face(kc, ko[o + G::P]);
+  const float kzm = nodal_face(ko[o - G::NP], kc), kzp = nodal_face(kc, ko[o + G::NP]);
+  float d = kxm;
+  d += kxp;
+  d += kym;
+  d += kyp;
+  d += kzm;
+  d += kzp;
+  const float dinv = __fdividef(1.0f, d);
+  float acc = g[cb + o];
+  acc = fmaf(kxm, uo[l], acc);
+  acc = fmaf(kxp, uo[r], acc);
+  acc = fmaf(kym, uo[o - G::P], acc);
+  acc = fmaf(kyp, uo[o + G::P], acc);
+  acc = fmaf(kzm, uo[o - G::NP], acc);
+  acc = fmaf(kzp, uo[o + G::NP], acc);
+  u[cb + o] = acc * dinv;
+}
+
+// r~ = g - D u + sum K u_q (k_residual_nodal's operations and order) from colour-split
+// kn, g and u, written to r in the plain layout (read by the restriction); 0 on the
+// boundary. Grid (node blocks of a plane, planes, samples).
+template <int LG>
+__global__ void __launch_bounds__(128) k_residual_split(const float* __restrict__ kn, const float* __restrict__ g,
+                                                        const float* __restrict__ u, float* __restrict__ r,
+                                                        const int* __restrict__ active) {
+  using G = SplitGeo<LG>;
+  constexpr int n = G::n;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const int s = blockIdx.z;
+  if (active && !active[s]) return;
+  const int y = q / n, x = q - y * n, z = (int)blockIdx.y;
+  float rr = 0.0f;
+  if (x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1) {
+    const int c = (x + y + z) & 1, par = x & 1;
+    const int o = (z * n + y) * G::P + (x >> 1);
+    const size_t cb = (size_t)s * G::NS + (size_t)c * G::BLK, ob = (size_t)s * G::NS + (size_t)(1 - c) * G::BLK;
+    const float* ko = kn + ob;
+    const float* uo = u + ob;
+    // other-colour slots of x - 1 and x + 1: (x - 1) >> 1 and (x + 1) >> 1
+    const int l = o - 1 + par, rt = o + par;
+    const float kc = kn[cb + o];
+    const float kxm = nodal_face(ko[l], kc), kxp = nodal_face(kc, ko[rt]);
+    const float kym = nodal_face(ko[o - G::P], kc), kyp = nodal_face(kc, ko[o + G::P]);
+    const float kzm = nodal_face(ko[o - G::NP], kc), kzp = nodal_face(kc, ko[o + G::NP]);
+    float d = kxm;
+    d += kxp;
+    d += kym;
+    d += kyp;
+    d += kzm;
+    d += kzp;
+    rr = fmaf(-d, u[cb + o], g[cb + o]);
+    rr = fmaf(kxm, uo[l], rr);
+    rr = fmaf(kxp, uo[rt], rr);
+    rr = fmaf(kym, uo[o - G::P], rr);
+    rr = fmaf(kyp, uo[o + G::P], rr);
+    rr = fmaf(kzm, uo[o - G::NP], rr);
+    rr = fmaf(kzp, uo[o + G::NP], rr);
+  }
+  r[(size_t)s * n * n * n + (size_t)(z * n * n + q)] = rr;
+}
+
+// u_f += trilinear interpolation of e_c on colour-split storage of both grids: the
+// coarse terms of k_prolong in its order (rows (Z, Y), (Z, Y+1), (Z+1, Y), (Z+1, Y+1),
+// each X then X+1) and its weights, so the result is bit for bit that of k_prolong.
+// LG: the fine grid's. Grid (interior nodes of a plane, interior planes, samples).
+template <int LG>
+__global__ void __launch_bounds__(128) k_prolong_split(const float* __restrict__ ec, float* __restrict__ u,
+                                                       const int* __restrict__ active) {
+  using F = SplitGeo<LG>;
+  using C = SplitGeo<LG - 1>;
+  constexpr int m = F::m;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // interior node of the plane
+  if (q >= m * m) return;
+  const int s = blockIdx.z;
+  if (active && !active[s]) return;
+  const int y = 1 + q / m, x = 1 + q - (y - 1) * m, z = 1 + (int)blockIdx.y;
+  const int xo = x & 1, yo = y & 1, zo = z & 1, X = x >> 1, Y = y >> 1, Z = z >> 1;
+  const float* e = ec + (size_t)s * C::NS;
+  // coarse node (X + a, Y + b, Z + c): colour (X + Y + Z + a + b + c) & 1, slot
+  // ((Z + c) n_c + Y + b) P_c + ((X + a) >> 1)
+  auto at = [&](int a, int b, int c) -> float {
+    const int cx = X + a, cy = Y + b, cz = Z + c;
+    return e[(size_t)((cx + cy + cz) & 1) * C::BLK + (size_t)((cz * C::n + cy) * C::P + (cx >> 1))];
+  };
+  float v = 0.0f;
+  v += at(0, 0, 0);
+  if (xo) v += at(1, 0, 0);
+  if (yo) {
+    v += at(0, 1, 0);
+    if (xo) v += at(1, 1, 0);
+  }
+  if (zo) {
+    v += at(0, 0, 1);
+    if (xo) v += at(1, 0, 1);
+    if (yo) {
+      v += at(0, 1, 1);
+      if (xo) v += at(1, 1, 1);
+    }
+  }
+  const float w = xo + yo + zo == 0 ? 1.0f : xo + yo + zo == 1 ? 0.5f : xo + yo + zo == 2 ? 0.25f : 0.125f;
+  const int c = (x + y + z) & 1;
+  u[(size_t)s * F::NS + (size_t)c * F::BLK + (size_t)((z * F::n + y) * F::P + (x >> 1))] += w * v;
+}
+
+// Dispatch of a colour-split kernel template on n = 2^LG + 1 (5 .. 1025).
+#define MLMC_SPLIT_DISPATCH(n, CALL)         \
+  switch (n) {                               \
+    case 5: { constexpr int LG = 2; CALL; } break;   \
+    case 9: { constexpr int LG = 3; CALL; } break;   \
+    case 17: { constexpr int LG = 4; CALL; } break;  \
+    case 33: { constexpr int LG = 5; CALL; } break;  \
+    case 65: { constexpr int LG = 6; CALL; } break;  \
+    case 129: { constexpr int LG = 7; CALL; } break; \
+    case 257: { constexpr int LG = 8; CALL; } break; \
+    case 513: { constexpr int LG = 9; CALL; } break; \
+    default: { constexpr int LG = 10; CALL; } break; \
+  }
+
 template <int THREADS>
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double warp_part[THREADS / 32];
@@ -432,7 +622,7 @@ __global__ void k_norm_update(int B, int NB, const double* __restrict__ partial,
 
 // g_c = 4 FW(r~) at interior coarse nodes (the coarse boundary of g_c is zeroed once per
 // solve and never written).
-template <typename T>
+template <typename T, bool SPLIT_OUT = false>
 __global__ void k_restrict(int nf, int B, const T* __restrict__ r, T* __restrict__ gc, const int* __restrict__ active) {
   // nc - 1 = 2^(p-1) = hc: an interior coarse row is X = 1 .. hc - 1
   const int nc = (nf + 1) / 2, hc = nc - 1, lc = 31 - __clz(hc);
@@ -456,7 +646,10 @@ __global__ void k_restrict(int nf, int B, const T* __restrict__ r, T* __restrict
           const T wgt = (T)((2 - abs(dx)) * (2 - abs(dy)) * (2 - abs(dz))) * (T)(1.0 / 16.0);
           v = fma(wgt, rb[dz * nf2 + dy * nf + dx], v);
         }
-    gc[(size_t)s * nc3 + (size_t)((Z * nc + Y) * nc + X)] = v;
+    if (SPLIT_OUT)
+      gc[(size_t)s * split_elems(nc) + split_index(nc, X, Y, Z)] = v;
+    else
+      gc[(size_t)s * nc3 + (size_t)((Z * nc + Y) * nc + X)] = v;
   }
 }
 
@@ -521,17 +714,21 @@ __global__ void k_prepare(int n, int B, double h2, const double* __restrict__ f,
   }
 }
 
-// Mixed refinement update u64 += e32 at interior nodes of active samples.
+// Mixed refinement update u64 += e32 at interior nodes of active samples (SPLIT: e in
+// colour-split storage).
+template <bool SPLIT>
 __global__ void k_update_mixed(int n, int B, const float* __restrict__ e, double* __restrict__ u,
                                const int* __restrict__ active) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
   if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
   const size_t n3 = (size_t)n * n * n;
   for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
     const int s = zz / n, z = zz - s * n;
     if (!active[s]) continue;
     const size_t t = (size_t)s * n3 + (size_t)(z * n * n + q);
-    u[t] += widen(e[t]);  // e is zero on the boundary
+    const float ev = SPLIT ? e[(size_t)s * split_elems(n) + split_index(n, x, y, z)] : e[t];
+    u[t] += widen(ev);  // e is zero on the boundary
   }
 }
 
@@ -787,7 +984,7 @@ inline int apply_blocks(int n) {
 // launch shape and partition of k_apply_dot_z): rr = g - D u, then the faces in the order
 // -x, +x, -y, +y, -z, +z; optional store of r~ (type TR) and per-(column block, slab)
 // partials of r~^2 (FP64).
-template <typename T, typename TD, typename TU, typename TR>
+template <typename T, typename TD, typename TU, typename TR, bool SPLIT_OUT = false>
 __global__ void __launch_bounds__(128)
     k_residual_z(int n, int zslab, const T* __restrict__ Kx, const T* __restrict__ Ky, const T* __restrict__ Kz,
                  const TD* __restrict__ D, const TD* __restrict__ g, const TU* __restrict__ u, TR* __restrict__ r,
@@ -799,8 +996,13 @@ __global__ void __launch_bounds__(128)
   const int zlo = 1 + blockIdx.y * zslab, zhi = min(n - 2, zlo + zslab - 1);
   const size_t n2 = (size_t)n * n;
   double sq = 0.0;
+  // store index of r~ at plane z of this column
+  const int cy = c < n * n ? c / n : 0, cx = c - cy * n;
+  auto rix = [&](size_t t, int z) -> size_t {
+    return SPLIT_OUT ? (size_t)s * split_elems(n) + split_index(n, cx, cy, z) : t;
+  };
   if (c < n * n) {
-    const int y = c / n, x = c - y * n;
+    const int y = cy, x = cx;
     const size_t col = (size_t)s * n2 * n + c;
     if (x > 0 && y > 0 && x < n - 1 && y < n - 1) {
       TD um = to_t<TD>(u[col + (size_t)(zlo - 1) * n2]), uc = to_t<TD>(u[col + (size_t)zlo * n2]);
@@ -816,17 +1018,17 @@ __global__ void __launch_bounds__(128)
         rr = fma(to_t<TD>(Ky[t]), to_t<TD>(u[t + n]), rr);
         rr = fma(kzm, um, rr);
         rr = fma(kzp, up, rr);
-        if (r) r[t] = (TR)rr;
+        if (r) r[rix(t, z)] = (TR)rr;
         sq += (double)rr * (double)rr;
         um = uc;
         uc = up;
         kzm = kzp;
       }
     } else if (r) {
-      for (int z = zlo; z <= zhi; ++z) r[col + (size_t)z * n2] = TR(0);
+      for (int z = zlo; z <= zhi; ++z) r[rix(col + (size_t)z * n2, z)] = TR(0);
     }
-    if (r && blockIdx.y == 0) r[col] = TR(0);                                    // plane z = 0
-    if (r && blockIdx.y == gridDim.y - 1) r[col + (size_t)(n - 1) * n2] = TR(0);  // plane z = n-1
+    if (r && blockIdx.y == 0) r[rix(col, 0)] = TR(0);                                          // plane z = 0
+    if (r && blockIdx.y == gridDim.y - 1) r[rix(col + (size_t)(n - 1) * n2, n - 1)] = TR(0);  // plane z = n-1
   }
   if (partial) {
     const double bs = block_sum<128>(sq);
@@ -840,7 +1042,9 @@ inline dim3 zmarch_grid(int n, int B, int* zslab) {
 }
 
 // x += alpha p, r -= alpha q; partials of r.r and r.z (z: the previous preconditioned
-// residual); optionally r32 = (float) r for an FP32 preconditioner. Grid (NB, B).
+// residual); optionally r32 = (float) r for an FP32 preconditioner (SPLIT: in colour-split
+// storage). Grid (NB, B).
+template <bool SPLIT>
 __global__ void __launch_bounds__(kThreads)
     k_cg_update(int n, const double* __restrict__ alpha, const double* __restrict__ p,
                 const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
@@ -858,7 +1062,14 @@ __global__ void __launch_bounds__(kThreads)
     x[t] = fma(a, p[t], x[t]);
     const double rn = fma(-a, q[t], r[t]);  // q and p vanish on the boundary
     r[t] = rn;
-    if (r32) r32[t] = (float)rn;
+    if (r32) {
+      if (SPLIT) {
+        const unsigned zq = i / (unsigned)(n * n), rem = i - zq * (unsigned)(n * n), yq = rem / (unsigned)n;
+        r32[(size_t)s * split_elems(n) + split_index(n, (int)(rem - yq * (unsigned)n), (int)yq, (int)zq)] = (float)rn;
+      } else {
+        r32[t] = (float)rn;
+      }
+    }
     rr = fma(rn, rn, rr);
     rz = fma(rn, z[t], rz);
   }
@@ -868,7 +1079,9 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) part_rz[(size_t)s * gridDim.x + blockIdx.x] = b2;
 }
 
-// z = (double) e (when e32 is given) and partial sums of r.z. Grid (NB, B).
+// z = (double) e (when e32 is given; SPLIT: in colour-split storage) and partial sums of
+// r.z. Grid (NB, B).
+template <bool SPLIT>
 __global__ void __launch_bounds__(kThreads)
     k_precond_dot(int n, const float* __restrict__ e32, double* __restrict__ z, const double* __restrict__ r,
                   double* __restrict__ partial, const int* __restrict__ active) {
@@ -882,7 +1095,12 @@ __global__ void __launch_bounds__(kThreads)
     const size_t t = (size_t)s * n3 + i;
     double zv;
     if (e32) {
-      zv = widen(e32[t]);
+      if (SPLIT) {
+        const unsigned zq = i / (unsigned)(n * n), rem = i - zq * (unsigned)(n * n), yq = rem / (unsigned)n;
+        zv = widen(e32[(size_t)s * split_elems(n) + split_index(n, (int)(rem - yq * (unsigned)n), (int)yq, (int)zq)]);
+      } else {
+        zv = widen(e32[t]);
+      }
       z[t] = zv;
     } else {
       zv = z[t];
@@ -910,6 +1128,18 @@ __global__ void k_p_update(int n, int B, const double* __restrict__ beta, const 
 __global__ void k_to_f32(size_t total, const double* __restrict__ a, float* __restrict__ b) {
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x)
     b[t] = (float)a[t];
+}
+
+// b = (float) a, a in the plain layout, b in colour-split storage (plane launch).
+__global__ void k_to_f32_split(int n, int B, const double* __restrict__ a, float* __restrict__ b) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
+  const size_t n3 = (size_t)n * n * n, ns = split_elems(n);
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    b[(size_t)s * ns + split_index(n, x, y, z)] = (float)a[(size_t)s * n3 + (size_t)(z * n * n + q)];
+  }
 }
 
 // Per-sample CG scalars from block partials (fixed order).
@@ -977,6 +1207,7 @@ struct Hier {
   bool fused[kMaxLevels] = {};    // fused (one pass) or two-pass smoother per level
   bool nodal[kMaxLevels] = {};    // two-pass sweep on the nodal coefficient (FP32)
   bool p1 = false;                // P1 finite elements: P1 transfers instead of FW / trilinear
+  bool split = false;             // FP32 hierarchy in colour-split storage (MLMC_SMOOTH_SPLIT)
 };
 
 // Lays out the workspace. Level-0 u of FP64 solves is the caller's array (not carved).
@@ -997,11 +1228,14 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed, bool cg) {
     v.Dinv = c.template take<T>(e);
     // level 0 of an FP64 solve iterates in a copy of the caller's u (so that every array
     // the smoothers stage is carved here, with slack behind it)
-    v.u = c.template take<T>(e);
-    if (j > 0 || mixed) v.g = c.template take<T>(e);  // FP64: the level-0 rhs is g64 (or R for CG)
+    // FP32 (mixed) grids hold u, g and 1/k in room for the colour-split storage too
+    // (n^2 (n + 1) instead of n^3 elements per sample)
+    const size_t es = mixed ? (size_t)B * split_elems(nl) : e;
+    v.u = c.template take<T>(es);
+    if (j > 0 || mixed) v.g = c.template take<T>(es);  // FP64: the level-0 rhs is g64 (or R for CG)
     if (j < H.L - 1) v.u2 = c.template take<T>(e);
     if (j < H.L - 1) v.r = c.template take<T>(e);
-    if (mixed && j < H.L - 1) v.kn = c.template take<T>(e);
+    if (mixed && j < H.L - 1) v.kn = c.template take<T>(es);
     nl = (nl + 1) / 2;
   }
   const size_t e0 = (size_t)B * cube(n);
@@ -1063,6 +1297,47 @@ struct Names<float> {
 inline double interior(int n) { return (double)(n - 2) * (n - 2) * (n - 2); }
 
 template <typename T>
+void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st);
+
+// One level of the V-cycle on colour-split FP32 storage: nodal-coefficient colour passes,
+// the residual into the plain r, full weighting into the coarse grid's split g, the
+// coarser levels, the trilinear correction on split storage, post-smoothing.
+template <typename T>
+void vcycle_split(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
+  Level<T>& v = H.lv[j];
+  Level<T>& w = H.lv[j + 1];
+  const int* act = H.active;
+  const int B = H.B, m = v.n - 2;
+  const double Ba = (double)H.n_act, W = 4.0;
+  float* u = (float*)(void*)v.u;
+  const float* g = (const float*)(const void*)v.g;
+  const float* kn = (const float*)(const void*)v.kn;
+  const dim3 gs((unsigned)((m * split_pitch(v.n) + 127) / 128), (unsigned)m, (unsigned)B);
+  auto smooth = [&](int sweeps) {
+    for (int s = 0; s < sweeps; ++s)
+      for (int c = 0; c < 2; ++c)
+        MLMC_LAUNCH(prof::sized("rbgs_split_f32", v.n), Ba * interior(v.n) * 2.0 * W, Ba * interior(v.n) * 0.5 * 37.0,
+                    st, MLMC_SPLIT_DISPATCH(v.n, (k_rbgs_split<LG><<<gs, 128, 0, st>>>(c, kn, g, u, act))));
+  };
+  smooth(nu1);
+  MLMC_LAUNCH(prof::sized("residual_split_f32", v.n), Ba * interior(v.n) * 4.0 * W, Ba * interior(v.n) * 37.0, st,
+              MLMC_SPLIT_DISPATCH(v.n, (k_residual_split<LG><<<dim3((unsigned)((v.n * v.n + 127) / 128), (unsigned)v.n,
+                                                                     (unsigned)B), 128, 0, st>>>(
+                                                kn, g, u, (float*)(void*)v.r, act))));
+  MLMC_LAUNCH(Names<T>::restrict_, Ba * ((double)v.n3 + (double)w.n3) * W, Ba * interior(w.n) * 54.0, st,
+              (k_restrict<T, true><<<plane_grid((w.n - 2) * (w.n - 1), (long long)B * (w.n - 2)), kPlaneThreads, 0,
+                                     st>>>(v.n, B, v.r, w.g, act)));
+  cudaMemsetAsync(w.u, 0, (size_t)B * split_elems(w.n) * sizeof(T), st);
+  vcycle(H, j + 1, nu1, nu2, st);
+  MLMC_LAUNCH(prof::sized("prolong_split_f32", v.n), Ba * (2.0 * (double)v.n3 + (double)w.n3) * W,
+              Ba * interior(v.n) * 4.375, st,
+              MLMC_SPLIT_DISPATCH(v.n, (k_prolong_split<LG><<<dim3((unsigned)((m * m + 127) / 128), (unsigned)m,
+                                                                    (unsigned)B), 128, 0, st>>>(
+                                                (const float*)(const void*)w.u, u, act))));
+  smooth(nu2);
+}
+
+template <typename T>
 void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   Level<T>& v = H.lv[j];
   const int* act = H.active;
@@ -1072,9 +1347,19 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   const double Ba = (double)H.n_act;
   const double W = (double)sizeof(T);
   if (j == H.L - 1) {
-    MLMC_LAUNCH(Names<T>::coarse, Ba * (729.0 * 8 + 54 * W), Ba * 27 * 54.0, st,
-                (k_coarse_apply<T><<<(B * 27 + 127) / 128, 128, 0, st>>>(B, H.Ainv, v.g, v.u, act)));
+    if (H.split)
+      MLMC_LAUNCH(Names<T>::coarse, Ba * (729.0 * 8 + 54 * W), Ba * 27 * 54.0, st,
+                  (k_coarse_apply<T, true><<<(B * 27 + 127) / 128, 128, 0, st>>>(B, H.Ainv, v.g, v.u, act)));
+    else
+      MLMC_LAUNCH(Names<T>::coarse, Ba * (729.0 * 8 + 54 * W), Ba * 27 * 54.0, st,
+                  (k_coarse_apply<T><<<(B * 27 + 127) / 128, 128, 0, st>>>(B, H.Ainv, v.g, v.u, act)));
     return;
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (H.split) {
+      vcycle_split(H, j, nu1, nu2, st);
+      return;
+    }
   }
   const int m = v.n - 2;
   const dim3 gs = plane_grid(m * ((v.n - 1) / 2), (long long)B * m);
@@ -1085,7 +1370,7 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
       if constexpr (sizeof(T) == 4) {
         if (H.nodal[j]) {
           for (int c = 0; c < 2; ++c)
-            MLMC_LAUNCH("rbgs_nodal_f32", Ba * interior(v.n) * 2.0 * W, Ba * interior(v.n) * 0.5 * 37.0, st,
+            MLMC_LAUNCH(prof::sized("rbgs_nodal_f32", v.n), Ba * interior(v.n) * 2.0 * W, Ba * interior(v.n) * 0.5 * 37.0, st,
                         (k_rbgs_nodal<<<gs, kPlaneThreads, 0, st>>>(c, v.n, B, (const float*)v.kn,
                                                                    (const float*)v.g, (float*)v.u, act)));
           continue;
@@ -1098,7 +1383,7 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
         v.u2 = t;
       } else {
         for (int c = 0; c < 2; ++c)
-          MLMC_LAUNCH(Names<T>::rbgs, sweep_bytes, sweep_flops, st,
+          MLMC_LAUNCH(prof::sized(Names<T>::rbgs, v.n), sweep_bytes, sweep_flops, st,
                       (k_rbgs<T><<<gs, kPlaneThreads, 0, st>>>(c, v.n, B, v.Kx, v.Ky, v.Kz, v.Dinv, v.g, v.u, act)));
       }
     }
@@ -1107,7 +1392,7 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   bool nodal_res = false;
   if constexpr (sizeof(T) == 4) {
     if (H.nodal[j]) {
-      MLMC_LAUNCH("residual_nodal_f32", Ba * interior(v.n) * 4.0 * W, Ba * interior(v.n) * 37.0, st,
+      MLMC_LAUNCH(prof::sized("residual_nodal_f32", v.n), Ba * interior(v.n) * 4.0 * W, Ba * interior(v.n) * 37.0, st,
                   (k_residual_nodal<<<plane_grid(v.n * v.n, (long long)B * v.n), kPlaneThreads, 0, st>>>(
                       v.n, B, (const float*)v.kn, (const float*)v.g, (const float*)v.u, (float*)v.r, act)));
       nodal_res = true;
@@ -1116,7 +1401,7 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   if (!nodal_res) {
     int zs = 0;
     const dim3 rz = zmarch_grid(v.n, B, &zs);
-    MLMC_LAUNCH(Names<T>::residual, Ba * interior(v.n) * 7.0 * W, Ba * interior(v.n) * 14.0, st,
+    MLMC_LAUNCH(prof::sized(Names<T>::residual, v.n), Ba * interior(v.n) * 7.0 * W, Ba * interior(v.n) * 14.0, st,
                 (k_residual_z<T, T, T, T><<<rz, 128, 0, st>>>(v.n, zs, v.Kx, v.Ky, v.Kz, v.D, v.g, v.u, v.r, nullptr,
                                                               act)));
   }
@@ -1219,13 +1504,18 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
     return MLMC_OK;
   };
   // z = M r: one V-cycle from zero on the (FP32 copy of the) residual; partials of r.z
+  const size_t u0_elems = H.split ? split_elems(n) : l0.n3;
   auto precondition = [&]() {
-    MLMC_CUDA_TRY(cudaMemsetAsync(H.lv[0].u, 0, (size_t)B * l0.n3 * sizeof(T), st));
+    MLMC_CUDA_TRY(cudaMemsetAsync(H.lv[0].u, 0, (size_t)B * u0_elems * sizeof(T), st));
     MLMC_TRY(gr.run(H, nu1, nu2, st));
     double* z = mixed ? H.Z : (double*)(void*)H.lv[0].u;
-    MLMC_LAUNCH("cg_precond_dot", all * (mixed ? 20.0 : 16.0), nodes * 2.0, st,
-                (k_precond_dot<<<rg, kThreads, 0, st>>>(n, mixed ? (const float*)(const void*)H.lv[0].u : nullptr,
-                                                        z, H.R, H.partial, H.active)));
+    const float* e32 = mixed ? (const float*)(const void*)H.lv[0].u : nullptr;
+    if (H.split)
+      MLMC_LAUNCH("cg_precond_dot", all * 20.0, nodes * 2.0, st,
+                  (k_precond_dot<true><<<rg, kThreads, 0, st>>>(n, e32, z, H.R, H.partial, H.active)));
+    else
+      MLMC_LAUNCH("cg_precond_dot", all * (mixed ? 20.0 : 16.0), nodes * 2.0, st,
+                  (k_precond_dot<false><<<rg, kThreads, 0, st>>>(n, e32, z, H.R, H.partial, H.active)));
     return MLMC_OK;
   };
   auto zcur = [&]() -> double* { return mixed ? H.Z : (double*)(void*)H.lv[0].u; };
@@ -1241,7 +1531,10 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
   MLMC_TRY(sync_count(&na));
   set_active(na);
   if (na == 0) return MLMC_OK;
-  if (mixed)
+  if (mixed && H.split)
+    MLMC_LAUNCH("to_f32", all * 12.0, 0.0, st,
+                (k_to_f32_split<<<pg, kPlaneThreads, 0, st>>>(n, B, H.R, (float*)(void*)l0.g)));
+  else if (mixed)
     MLMC_LAUNCH("to_f32", all * 12.0, 0.0, st,
                 (k_to_f32<<<g0, kThreads, 0, st>>>((size_t)B * l0.n3, H.R, (float*)(void*)l0.g)));
   MLMC_TRY(precondition());
@@ -1255,10 +1548,15 @@ int pcg_loop(Hier<T>& H, const MGSolveArgs& a, int nu1, int nu2, double rtol, in
                                                                     H.part_apply, H.active)));
     MLMC_LAUNCH("cg_scalar", B * NBa * 8.0, 0.0, st,
                 (k_cg_scalar<<<sb, 128, 0, st>>>(B, NBa, 1, H.part_apply, H.rz, H.rzo, H.alpha, H.beta, H.active)));
-    MLMC_LAUNCH("cg_update", all * (mixed ? 60.0 : 56.0), nodes * 8.0, st,
-                (k_cg_update<<<rg, kThreads, 0, st>>>(n, H.alpha, H.P, H.Q, a.u, H.R, zcur(),
-                                                      mixed ? (float*)(void*)l0.g : nullptr, H.partial, H.part2,
-                                                      H.active)));
+    if (H.split)
+      MLMC_LAUNCH("cg_update", all * 60.0, nodes * 8.0, st,
+                  (k_cg_update<true><<<rg, kThreads, 0, st>>>(n, H.alpha, H.P, H.Q, a.u, H.R, zcur(),
+                                                              (float*)(void*)l0.g, H.partial, H.part2, H.active)));
+    else
+      MLMC_LAUNCH("cg_update", all * (mixed ? 60.0 : 56.0), nodes * 8.0, st,
+                  (k_cg_update<false><<<rg, kThreads, 0, st>>>(n, H.alpha, H.P, H.Q, a.u, H.R, zcur(),
+                                                               mixed ? (float*)(void*)l0.g : nullptr, H.partial,
+                                                               H.part2, H.active)));
     MLMC_LAUNCH("cg_scalar", B * H.NB * 8.0, 0.0, st,
                 (k_cg_scalar<<<sb, 128, 0, st>>>(B, H.NB, 3, H.part2, H.rz, H.rzo, H.alpha, H.beta, H.active)));
     MLMC_CUDA_TRY(cudaMemsetAsync(H.n_active, 0, sizeof(int), st));
@@ -1289,11 +1587,28 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   H.p1 = a.cfg.disc == MLMC_DISC_FE;
   const int B = a.B;
   const double W = (double)sizeof(T);
-  // operators of every level (k injected from k0)
+  // the sweep count of the cycle (tuned for the finest grid, or as given) and whether the
+  // FP32 hierarchy runs on colour-split storage (the finest grid's smoother decides for
+  // every grid)
+  int nu1 = a.cfg.nu1, nu2 = a.cfg.nu2;
+  {
+    int sm0 = a.cfg.smoother;
+    resolve_tuning(a.n, a.cfg.precision, &sm0, &nu1, &nu2);
+    H.split = mixed && a.cfg.disc == MLMC_DISC_FV && sm0 == MLMC_SMOOTH_SPLIT;
+  }
+  // operators of every level (k injected from k0); colour-split grids need no faces
+  // except on the coarsest grid (its dense solve)
   int stride = a.st0;
   for (int j = 0; j < H.L; ++j) {
     Level<T>& v = H.lv[j];
     const dim3 gb = plane_grid(v.n * v.n, (long long)B * v.n);
+    if (H.split) {
+      if (j > 0) MLMC_CUDA_TRY(cudaMemsetAsync(v.g, 0, (size_t)B * split_elems(v.n) * sizeof(T), st));
+      if (j < H.L - 1) {
+        stride *= 2;
+        continue;
+      }
+    }
     if (a.cfg.disc == MLMC_DISC_FE)
       MLMC_LAUNCH("faces_fe", B * (double)v.n3 * (8.0 + 3 * W), B * (double)v.n3 * 36.0, st,
                   (k_faces_fe<T><<<gb, kPlaneThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, v.Kx, v.Ky, v.Kz)));
@@ -1303,20 +1618,23 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     MLMC_LAUNCH(Names<T>::diag, B * (double)v.n3 * 5 * W, B * (double)v.n3 * 6.0, st,
                 (k_diag<T, T><<<gb, kPlaneThreads, 0, st>>>(v.n, B, v.Kx, v.Ky, v.Kz, v.D, v.Dinv)));
     // restriction writes only interior coarse nodes: the boundary of g stays zero
-    if (j > 0) MLMC_CUDA_TRY(cudaMemsetAsync(v.g, 0, (size_t)B * v.n3 * sizeof(T), st));
+    if (j > 0 && !H.split) MLMC_CUDA_TRY(cudaMemsetAsync(v.g, 0, (size_t)B * v.n3 * sizeof(T), st));
     stride *= 2;
   }
-  // smoother per level (explicit choice, or the tuned / default one for that grid) and
-  // the sweep count of the cycle (tuned for the finest grid, or as given)
-  int nu1 = a.cfg.nu1, nu2 = a.cfg.nu2;
-  {
-    int sm0 = a.cfg.smoother;
-    resolve_tuning(a.n, a.cfg.precision, &sm0, &nu1, &nu2);
-  }
+  // smoother per level (explicit choice, or the tuned / default one for that grid)
   for (int j = 0; j < H.L; ++j) {
     Level<T>& v = H.lv[j];
+    if (H.split) {
+      H.nodal[j] = H.fused[j] = false;
+      if (j < H.L - 1)
+        MLMC_LAUNCH("nodal_k", B * (double)v.n3 * (8.0 + W), 0.0, st,
+                    (k_nodal_k_split<<<plane_grid(v.n * v.n, (long long)B * v.n), kPlaneThreads, 0, st>>>(
+                        a.k0, a.n_k0, a.st0 << j, v.n, B, (float*)(void*)v.kn)));
+      continue;
+    }
     int sm = a.cfg.smoother, d1 = 1, d2 = 1;
     resolve_tuning(v.n, a.cfg.precision, &sm, &d1, &d2);
+    if (sm == MLMC_SMOOTH_SPLIT) sm = MLMC_SMOOTH_NODAL;  // split storage only for the whole hierarchy
     // the nodal-coefficient sweep exists for FP32 grids (an FP64 solve takes the two-pass)
     H.nodal[j] = v.kn != nullptr && sm == MLMC_SMOOTH_NODAL;
     H.fused[j] = v.u2 != nullptr && sm != MLMC_SMOOTH_TWO_PASS && sm != MLMC_SMOOTH_NODAL;
@@ -1391,7 +1709,11 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     int zs = 0;
     const dim3 rz = zmarch_grid(a.n, B, &zs);
     const double Ba = (double)H.n_act;
-    if (mixed) {
+    if (mixed && H.split) {
+      MLMC_LAUNCH("residual_mixed", Ba * interior(a.n) * (3 * 8.0 + 8 * 3 + W), Ba * interior(a.n) * 16.0, st,
+                  (k_residual_z<double, double, double, T, true><<<rz, 128, 0, st>>>(
+                      a.n, zs, H.K64x, H.K64y, H.K64z, H.D64, H.g64, a.u, l0.g, H.partial, H.active)));
+    } else if (mixed) {
       MLMC_LAUNCH("residual_mixed", Ba * interior(a.n) * (3 * 8.0 + 8 * 3 + W), Ba * interior(a.n) * 16.0, st,
                   (k_residual_z<double, double, double, T><<<rz, 128, 0, st>>>(a.n, zs, H.K64x, H.K64y, H.K64z, H.D64,
                                                                                H.g64, a.u, l0.g, H.partial,
@@ -1458,11 +1780,18 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   if (na < 0) return na;
   while (na > 0) {
     if (mixed) {
-      MLMC_CUDA_TRY(cudaMemsetAsync(H.lv[0].u, 0, (size_t)B * l0.n3 * sizeof(T), st));
+      MLMC_CUDA_TRY(
+          cudaMemsetAsync(H.lv[0].u, 0, (size_t)B * (H.split ? split_elems(a.n) : l0.n3) * sizeof(T), st));
       MLMC_TRY(gr.run(H, nu1, nu2, st));
-      MLMC_LAUNCH("update_mixed", H.n_act * (double)l0.n3 * (W + 16), H.n_act * (double)l0.n3, st,
-                  (k_update_mixed<<<plane_grid(a.n * a.n, (long long)B * a.n), kPlaneThreads, 0, st>>>(
-                      a.n, B, (const float*)H.lv[0].u, a.u, H.active)));
+      const dim3 ug = plane_grid(a.n * a.n, (long long)B * a.n);
+      if (H.split)
+        MLMC_LAUNCH("update_mixed", H.n_act * (double)l0.n3 * (W + 16), H.n_act * (double)l0.n3, st,
+                    (k_update_mixed<true><<<ug, kPlaneThreads, 0, st>>>(a.n, B, (const float*)H.lv[0].u, a.u,
+                                                                          H.active)));
+      else
+        MLMC_LAUNCH("update_mixed", H.n_act * (double)l0.n3 * (W + 16), H.n_act * (double)l0.n3, st,
+                    (k_update_mixed<false><<<ug, kPlaneThreads, 0, st>>>(a.n, B, (const float*)H.lv[0].u, a.u,
+                                                                           H.active)));
     } else {
       MLMC_TRY(gr.run(H, nu1, nu2, st));
     }

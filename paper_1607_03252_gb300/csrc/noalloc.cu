@@ -64,7 +64,7 @@ extern "C" int mg_solve_batch_noalloc(const mg_cfg* cfg, int batch, int n, const
   if (cfg->nu1 < 0 || cfg->nu1 > 8 || cfg->nu2 < 0 || cfg->nu2 > 8 || cfg->max_cycles < 1 ||
       cfg->max_cycles > 1000 || !(cfg->rtol < 1.0) ||
       (cfg->precision != MLMC_PREC_F64 && cfg->precision != MLMC_PREC_MIXED) ||
-      cfg->smoother < MLMC_SMOOTH_AUTO || cfg->smoother > MLMC_SMOOTH_NODAL ||
+      cfg->smoother < MLMC_SMOOTH_AUTO || cfg->smoother > MLMC_SMOOTH_SPLIT ||
       (cfg->accel != MLMC_ACCEL_NONE && cfg->accel != MLMC_ACCEL_CG) ||
       (cfg->disc != MLMC_DISC_FV && cfg->disc != MLMC_DISC_FE) ||
       (cfg->disc == MLMC_DISC_FE && cfg->precision != MLMC_PREC_F64)) {

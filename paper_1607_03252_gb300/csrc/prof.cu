@@ -1,4 +1,5 @@
 // Launch accounting and optional per-launch CUDA-event timing (see prof.cuh).
+#include <stdio.h>
 #include <string.h>
 
 #include <atomic>
@@ -59,6 +60,12 @@ void resolve(Entry& e) {
 }  // namespace
 
 bool timing_enabled() { return reg().timing.load(); }
+
+const char* sized(const char* base, int n) {
+  static thread_local char buf[96];
+  snprintf(buf, sizeof(buf), "%s@%d", base, n);
+  return buf;
+}
 
 static thread_local Tape* t_tape = nullptr;
 static thread_local Tape t_tape_store;

@@ -30,6 +30,9 @@ void tape_replay(const Tape& t, double scale = 1.0);
 int begin(const char* cls, double bytes, double flops, cudaStream_t st);
 void end(int token, cudaStream_t st);
 
+// "base@n": a launch class per grid size (the name is copied when the launch is counted).
+const char* sized(const char* base, int n);
+
 // RAII scope around one kernel launch.
 struct Scope {
   int tok;

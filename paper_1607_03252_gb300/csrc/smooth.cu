@@ -670,7 +670,8 @@ int rbgs_fused_sweep(int shape, int n, int B, const T* Kx, const T* Ky, const T*
   // one full sweep: 7 words per interior node (u read + write, Kx, Ky, Kz, Dinv, g), 13 flops
   MLMC_TRY(rbgs_fused_configure<T>(shape));
   // (masked samples are copied, not smoothed: the work counts the active ones)
-  prof::Scope scope(cls, active_samples * interior * 7.0 * sizeof(T), active_samples * interior * 13.0, st);
+  prof::Scope scope(prof::sized(cls, n), active_samples * interior * 7.0 * sizeof(T), active_samples * interior * 13.0,
+                    st);
   const long long budget = wait_budget_clocks();
   switch (shape) {
     case kTile32x16:

@@ -1,7 +1,7 @@
 """One small batched field evaluation + multigrid solve, for kernel profiling.
 
   python -m paper_1607_03252_gb300.profile_case --n 129 --batch 8 --prec f64 --cycles 2 \
-      [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8|nodal] [--accel cg] [--timing]
+      [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8|nodal|split] [--accel cg] [--timing]
       [--field gauss|exp|spde] [--level L --n0 17] [--disc fv|fe] [--accel fmg] [--qoi mean|point|flux]
   python -m paper_1607_03252_gb300.profile_case --fma-peak
 
@@ -36,7 +36,7 @@ def main(argv=None):
     p.add_argument("--cycles", type=int, default=2)
     p.add_argument("--M", type=int, default=256)
     p.add_argument("--smoother", choices=["auto", "two-pass", "32x8", "32x16", "64x8", "bulk32x8", "bulk32x16",
-                                          "bulk64x8", "nodal"], default="auto")
+                                          "bulk64x8", "nodal", "split"], default="auto")
     p.add_argument("--accel", choices=["none", "cg", "fmg"], default="none")
     p.add_argument("--disc", choices=["fv", "fe"], default="fv")
     p.add_argument("--qoi", choices=["mean", "point", "flux"], default="mean")
@@ -60,7 +60,8 @@ def main(argv=None):
     sm = {"auto": mg.MLMC_SMOOTH_AUTO, "two-pass": mg.MLMC_SMOOTH_TWO_PASS, "32x8": mg.MLMC_SMOOTH_FUSED_32x8,
           "32x16": mg.MLMC_SMOOTH_FUSED_32x16, "64x8": mg.MLMC_SMOOTH_FUSED_64x8,
           "bulk32x8": mg.MLMC_SMOOTH_BULK_32x8, "bulk32x16": mg.MLMC_SMOOTH_BULK_32x16,
-          "bulk64x8": mg.MLMC_SMOOTH_BULK_64x8, "nodal": mg.MLMC_SMOOTH_NODAL}[a.smoother]
+          "bulk64x8": mg.MLMC_SMOOTH_BULK_64x8, "nodal": mg.MLMC_SMOOTH_NODAL,
+          "split": mg.MLMC_SMOOTH_SPLIT}[a.smoother]
     accel = {"none": mg.MLMC_ACCEL_NONE, "cg": mg.MLMC_ACCEL_CG, "fmg": mg.MLMC_ACCEL_FMG}[a.accel]
     disc = mg.MLMC_DISC_FE if a.disc == "fe" else mg.MLMC_DISC_FV
     qoi = {"mean": mg.MLMC_QOI_MEAN, "point": mg.MLMC_QOI_POINT, "flux": mg.MLMC_QOI_FLUX}[a.qoi]

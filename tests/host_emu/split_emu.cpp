@@ -1,0 +1,142 @@
+// Host runs of the colour-split FP32 kernels beside their plain-layout counterparts (their
+// text extracted from the sources; see tests/test_split_host.py). The launch is a loop
+// over every block and thread. Mode:
+//   split n B in.bin perm.bin out.bin
+//     in.bin   float32: kn, g, u (B n^3 each, plain layout), k0 (float64, B n^3), ec
+//              (float32, B nc^3, plain), r (float32, B n^3, plain)
+//     perm.bin int64: for every plain index of B n^3 (then of B nc^3), its index in the
+//              colour-split storage (computed by the test from the definition)
+//     out.bin  float32: u after a red and a black pass (plain kernel, then split kernel
+//              mapped back), r~ of the nodal residual (plain, split), u + P ec (plain,
+//              split mapped back), 4 FW(r) (plain, split mapped back), 1/k (plain, split
+//              mapped back)
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+struct dim3 {
+  unsigned x = 1, y = 1, z = 1;
+  dim3(unsigned a = 1, unsigned b = 1, unsigned c = 1) : x(a), y(b), z(c) {}
+};
+static dim3 blockIdx, threadIdx, blockDim, gridDim;
+static float __fdividef(float a, float b) { return a / b; }
+static float __fadd_rn(float a, float b) { return a + b; }
+static int __clz(int x) { return x == 0 ? 32 : __builtin_clz((unsigned)x); }
+static float fmaf_(float a, float b, float c) { return std::fmaf(a, b, c); }
+#define fmaf fmaf_
+using std::fma;
+
+#include "split_kernels.inc"
+
+template <typename F>
+static void launch(dim3 grid, dim3 block, F body) {
+  gridDim = grid;
+  blockDim = block;
+  for (unsigned bz = 0; bz < grid.z; ++bz)
+    for (unsigned by = 0; by < grid.y; ++by)
+      for (unsigned bx = 0; bx < grid.x; ++bx)
+        for (unsigned t = 0; t < block.x; ++t) {
+          blockIdx = dim3(bx, by, bz);
+          threadIdx = dim3(t, 0, 0);
+          body();
+        }
+}
+
+template <typename T>
+static std::vector<T> readv(FILE* f, size_t n) {
+  std::vector<T> v(n);
+  if (std::fread(v.data(), sizeof(T), n, f) != n) std::exit(3);
+  return v;
+}
+
+int main(int argc, char** argv) {
+  if (argc < 7 || std::string(argv[1]) != "split") return 2;
+  const int n = std::atoi(argv[2]), B = std::atoi(argv[3]), nc = (n + 1) / 2;
+  const size_t n3 = (size_t)n * n * n, nc3 = (size_t)nc * nc * nc;
+  FILE* fi = std::fopen(argv[4], "rb");
+  FILE* fp = std::fopen(argv[5], "rb");
+  if (!fi || !fp) return 3;
+  auto kn = readv<float>(fi, B * n3), g = readv<float>(fi, B * n3), u = readv<float>(fi, B * n3);
+  auto k0 = readv<double>(fi, B * n3);
+  auto ec = readv<float>(fi, B * nc3), r = readv<float>(fi, B * n3);
+  auto perm = readv<int64_t>(fp, B * n3), permc = readv<int64_t>(fp, B * nc3);
+  std::fclose(fi);
+  std::fclose(fp);
+  const float nan = std::numeric_limits<float>::quiet_NaN();
+  const size_t ns = mlmc::split_elems(n), nsc = mlmc::split_elems(nc);
+  auto to_split = [&](const std::vector<float>& a, const std::vector<int64_t>& pm, size_t total) {
+    std::vector<float> b(total, nan);  // slots without a node stay NaN: reading one poisons the result
+    for (size_t i = 0; i < a.size(); ++i) b[pm[i]] = a[i];
+    return b;
+  };
+  auto from_split = [&](const std::vector<float>& b, const std::vector<int64_t>& pm) {
+    std::vector<float> a(pm.size());
+    for (size_t i = 0; i < pm.size(); ++i) a[i] = b[pm[i]];
+    return a;
+  };
+  const unsigned T = 64;
+  std::vector<float> out;
+  // a red and a black pass
+  std::vector<float> up = u, us = to_split(u, perm, B * ns), ks = to_split(kn, perm, B * ns),
+                     gs = to_split(g, perm, B * ns);
+  const int m = n - 2, half = (n - 1) / 2, P = (n + 1) / 2;
+  for (int c = 0; c < 2; ++c) {
+    launch(dim3((unsigned)((m * half + T - 1) / T), (unsigned)(B * m)), dim3(T),
+           [&] { mlmc::k_rbgs_nodal(c, n, B, kn.data(), g.data(), up.data(), nullptr); });
+    MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * P + 127) / 128), (unsigned)m, (unsigned)B), dim3(128), [&] {
+      mlmc::k_rbgs_split<LG>(c, ks.data(), gs.data(), us.data(), nullptr);
+    }));
+  }
+  auto usb = from_split(us, perm);
+  out.insert(out.end(), up.begin(), up.end());
+  out.insert(out.end(), usb.begin(), usb.end());
+  // the nodal residual of the swept iterate
+  std::vector<float> rp(B * n3, nan), rs(B * n3, nan);
+  launch(dim3((unsigned)((n * n + T - 1) / T), (unsigned)(B * n)), dim3(T),
+         [&] { mlmc::k_residual_nodal(n, B, kn.data(), g.data(), up.data(), rp.data(), nullptr); });
+  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((n * n + 127) / 128), (unsigned)n, (unsigned)B), dim3(128), [&] {
+    mlmc::k_residual_split<LG>(ks.data(), gs.data(), us.data(), rs.data(), nullptr);
+  }));
+  out.insert(out.end(), rp.begin(), rp.end());
+  out.insert(out.end(), rs.begin(), rs.end());
+  // the trilinear correction
+  std::vector<float> pp = u, ps = to_split(u, perm, B * ns), ecs = to_split(ec, permc, B * nsc);
+  const int P2 = n - 1;
+  launch(dim3((unsigned)((m * P2 + T - 1) / T), (unsigned)(B * m)), dim3(T),
+         [&] { mlmc::k_prolong<float>(n, B, ec.data(), pp.data(), nullptr); });
+  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * m + 127) / 128), (unsigned)m, (unsigned)B), dim3(128), [&] {
+    mlmc::k_prolong_split<LG>(ecs.data(), ps.data(), nullptr);
+  }));
+  auto psb = from_split(ps, perm);
+  out.insert(out.end(), pp.begin(), pp.end());
+  out.insert(out.end(), psb.begin(), psb.end());
+  // full weighting into the plain and the split coarse storage
+  std::vector<float> gcp(B * nc3, 0.0f), gcs(B * nsc, 0.0f);
+  for (size_t i = 0; i < permc.size(); ++i) gcs[permc[i]] = 0.0f;
+  const int hc = nc - 1;
+  launch(dim3((unsigned)(((nc - 2) * hc + T - 1) / T), (unsigned)(B * (nc - 2))), dim3(T),
+         [&] { mlmc::k_restrict<float, false>(n, B, r.data(), gcp.data(), nullptr); });
+  launch(dim3((unsigned)(((nc - 2) * hc + T - 1) / T), (unsigned)(B * (nc - 2))), dim3(T),
+         [&] { mlmc::k_restrict<float, true>(n, B, r.data(), gcs.data(), nullptr); });
+  auto gcsb = from_split(gcs, permc);
+  out.insert(out.end(), gcp.begin(), gcp.end());
+  out.insert(out.end(), gcsb.begin(), gcsb.end());
+  // the reciprocal nodal coefficient
+  std::vector<float> knp(B * n3, nan), kns(B * ns, nan);
+  launch(dim3((unsigned)((n * n + T - 1) / T), (unsigned)(B * n)), dim3(T),
+         [&] { mlmc::k_nodal_k<float>(k0.data(), n, 1, n, B, knp.data()); });
+  launch(dim3((unsigned)((n * n + T - 1) / T), (unsigned)(B * n)), dim3(T),
+         [&] { mlmc::k_nodal_k_split(k0.data(), n, 1, n, B, kns.data()); });
+  auto knsb = from_split(kns, perm);
+  out.insert(out.end(), knp.begin(), knp.end());
+  out.insert(out.end(), knsb.begin(), knsb.end());
+  FILE* fo = std::fopen(argv[6], "wb");
+  std::fwrite(out.data(), sizeof(float), out.size(), fo);
+  std::fclose(fo);
+  return 0;
+}

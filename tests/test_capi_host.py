@@ -100,7 +100,7 @@ def test_tune_set_validates_on_host():
     assert L.mlmc_tune_set(34, mg.MLMC_PREC_MIXED, mg.MLMC_SMOOTH_TWO_PASS, 3) == mg.MLMC_ERR_INVALID
     assert L.mlmc_tune_set(33, 7, mg.MLMC_SMOOTH_TWO_PASS, 3) == mg.MLMC_ERR_INVALID
     assert L.mlmc_tune_set(33, mg.MLMC_PREC_F64, mg.MLMC_SMOOTH_AUTO, 3) == mg.MLMC_ERR_INVALID
-    assert L.mlmc_tune_set(33, mg.MLMC_PREC_F64, mg.MLMC_SMOOTH_NODAL + 1, 3) == mg.MLMC_ERR_INVALID
+    assert L.mlmc_tune_set(33, mg.MLMC_PREC_F64, mg.MLMC_SMOOTH_SPLIT + 1, 3) == mg.MLMC_ERR_INVALID
     assert L.mlmc_tune_set(33, mg.MLMC_PREC_F64, mg.MLMC_SMOOTH_TWO_PASS, 0) == mg.MLMC_ERR_INVALID
     mg.mlmc_tune_set(65, mg.MLMC_PREC_F64, "two-pass", 2)
 

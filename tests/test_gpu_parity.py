@@ -320,6 +320,8 @@ GRAPH_CASES = [(mg.MLMC_PREC_F64, mg.MLMC_ACCEL_NONE, mg.MLMC_SMOOTH_TWO_PASS),
                (mg.MLMC_PREC_MIXED, mg.MLMC_ACCEL_NONE, mg.MLMC_SMOOTH_FUSED_32x8),
                (mg.MLMC_PREC_MIXED, mg.MLMC_ACCEL_CG, mg.MLMC_SMOOTH_FUSED_64x8),
                (mg.MLMC_PREC_MIXED, mg.MLMC_ACCEL_CG, mg.MLMC_SMOOTH_NODAL),
+               (mg.MLMC_PREC_MIXED, mg.MLMC_ACCEL_CG, mg.MLMC_SMOOTH_SPLIT),
+               (mg.MLMC_PREC_MIXED, mg.MLMC_ACCEL_NONE, mg.MLMC_SMOOTH_SPLIT),
                (mg.MLMC_PREC_F64, mg.MLMC_ACCEL_CG, mg.MLMC_SMOOTH_TWO_PASS)]
 
 
@@ -366,6 +368,36 @@ def test_nodal_smoother_reaches_the_same_solution(orc, accel):
         assert relmax(out[mg.MLMC_SMOOTH_NODAL][0][s], out[mg.MLMC_SMOOTH_TWO_PASS][0][s]) < 1e-9
     # the smoother's operator differs by ulps: the cycle counts stay within one of each other
     assert np.all(np.abs(out[mg.MLMC_SMOOTH_NODAL][1] - out[mg.MLMC_SMOOTH_TWO_PASS][1]) <= 1)
+
+
+@pytest.mark.parametrize("accel", [mg.MLMC_ACCEL_NONE, mg.MLMC_ACCEL_CG])
+@pytest.mark.parametrize("n", [9, 17, 33, 65])
+def test_split_storage_equals_nodal_sweep_bitwise(orc, accel, n):
+    """MLMC_SMOOTH_SPLIT runs the nodal-coefficient sweep, residual, transfers and coarse
+    solve on colour-split storage with the same operations in the same order: iterates,
+    cycle counts and residuals equal MLMC_SMOOTH_NODAL's bit for bit, samples stopping at
+    different cycles."""
+    B = 4 if n < 65 else 2
+    ks = [orc.field(RUN_SEED, int(i), 256, 1.0 + 0.5 * s, 0.15, n) for s, i in enumerate(sample_ids(4, 0, B))]
+    k = to_dev(np.stack(ks))
+    out = {}
+    for sm in (mg.MLMC_SMOOTH_NODAL, mg.MLMC_SMOOTH_SPLIT):
+        u = torch.zeros_like(k)
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-10, 200, mg.MLMC_PREC_MIXED, sm, accel), k, u)
+        assert st == 0
+        out[sm] = (u.cpu().numpy(), cyc, rel)
+    a, b = out[mg.MLMC_SMOOTH_NODAL], out[mg.MLMC_SMOOTH_SPLIT]
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert np.array_equal(a[0], b[0])
+
+
+def test_split_storage_level_estimate_matches_oracle(orc):
+    level, ids = 2, sample_ids(2, 30, 3)
+    cfg = mg.make_mlmc_cfg(RUN_SEED, 2.0, 0.2, 256, n0=17, rtol=1e-11, precision=mg.MLMC_PREC_MIXED,
+                           smoother=mg.MLMC_SMOOTH_SPLIT, accel=mg.MLMC_ACCEL_CG)
+    _, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
+    Y64, Qf64, Qc64, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 2.0, 0.2, 256, rtol=1e-11), 65, 33, ids)
+    assert np.all(_mixed_err(Y, Y64, Qf64, Qc64, "level 2, colour-split storage, CG") <= 1e-9)
 
 
 def test_nodal_smoother_level_estimate_matches_oracle(orc):
@@ -445,7 +477,7 @@ def test_cg_batch_composition_does_not_change_results(orc):
 def test_autotune_records_choice():
     cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.3, 64, n0=17, nu1=0, nu2=0, rtol=1e-10, precision=mg.MLMC_PREC_MIXED)
     rows, best_sm, best_nu = mg.mlmc_autotune(cfg, 1, int(sample_ids(1, 900, 1)[0]), 16)
-    assert len(rows) == 24 and best_nu in (1, 2, 3)
+    assert len(rows) == 27 and best_nu in (1, 2, 3)  # 9 smoothers x nu in {1, 2, 3}
     assert all(r["ms_per_sample"] > 0 for r in rows)
     # a level run with AUTO smoother and nu = 0 uses the choice and matches an explicit run
     s_auto, Ya, _, _ = mg.mlmc_level_estimate(cfg, 1, int(sample_ids(1, 0, 1)[0]), 8)
