@@ -156,6 +156,21 @@ typedef struct {
                           k_{P-b-c})/12 ({a,b,c} = {x,y,z}); P1 interpolation between grids and
                           its transpose. FP64, stored-face smoothers. */
 
+/* Execution engine of a solve (no counterpart in the paper; same results bit for bit).
+ * MLMC_ENGINE_BATCHED: every phase of the cycle is a kernel over the whole batch, one
+ * convergence test per cycle on the host. MLMC_ENGINE_CTA (finite volumes, stationary
+ * cycles, refinement or CG, grids up to 33^3; otherwise the batched engine runs): one
+ * persistent launch for the whole solve, each CTA taking the next sample from a device
+ * counter and running all of its cycles, the convergence tests and the CG recurrences
+ * with block barriers; the sums follow the batched kernels' partitions and trees, so
+ * iterates, cycle counts and residuals are identical. MLMC_ENGINE_AUTO: the CTA engine
+ * for grids up to 17^3 (where the batched engine waits on launches and host round trips),
+ * the batched engine above; the environment variable MLMC_ENGINE=1 or 2 overrides the
+ * automatic choice. */
+#define MLMC_ENGINE_AUTO 0
+#define MLMC_ENGINE_BATCHED 1
+#define MLMC_ENGINE_CTA 2
+
 /* Multigrid parameters. */
 typedef struct {
   int nu1;        /* pre-smoothing red-black sweeps, 0..8 (nu1 = nu2 = 0: the tuned count, else 2) */
@@ -166,6 +181,7 @@ typedef struct {
   int smoother;   /* MLMC_SMOOTH_* */
   int accel;      /* MLMC_ACCEL_NONE, MLMC_ACCEL_CG or MLMC_ACCEL_FMG */
   int disc;       /* MLMC_DISC_FV (zero-initialised) or MLMC_DISC_FE */
+  int engine;     /* MLMC_ENGINE_AUTO (zero-initialised), MLMC_ENGINE_BATCHED or MLMC_ENGINE_CTA */
 } mg_cfg;
 
 /* Per-sample solve statistics. */

@@ -12,7 +12,7 @@ imported on machines without a GPU.
 """
 from ._capi import (  # noqa: F401
     MLMC_ERR_BUSY, MLMC_ERR_CANCELLED, MLMC_ERR_CUDA, MLMC_ERR_INVALID, MLMC_ERR_NOT_CONVERGED, MLMC_ERR_NOT_FOUND, MLMC_ERR_OOM,
-    MLMC_ACCEL_FMG, MLMC_COV_EXP, MLMC_COV_GAUSS, MLMC_COV_SPDE, MLMC_DISC_FE, MLMC_DISC_FV, MLMC_QOI_FLUX,
+    MLMC_ACCEL_FMG, MLMC_ENGINE_AUTO, MLMC_ENGINE_BATCHED, MLMC_ENGINE_CTA, MLMC_COV_EXP, MLMC_COV_GAUSS, MLMC_COV_SPDE, MLMC_DISC_FE, MLMC_DISC_FV, MLMC_QOI_FLUX,
     MLMC_QOI_MEAN, MLMC_QOI_POINT, MLMC_ERR_TIMEOUT, MLMC_F32, MLMC_F64, MLMC_OK, MLMC_PENDING, MLMC_PREC_F64, MLMC_PREC_MIXED, MLMC_ACCEL_NONE, MLMC_ACCEL_CG, MLMC_SMOOTH_AUTO,
     MLMC_SMOOTH_BULK_32x8, MLMC_SMOOTH_BULK_32x16, MLMC_SMOOTH_BULK_64x8, MLMC_SMOOTH_NODAL, MLMC_SMOOTH_SPLIT, MLMC_SMOOTH_FUSED_32x8,
     MLMC_SMOOTH_FUSED_32x16, MLMC_SMOOTH_FUSED_64x8, MLMC_SMOOTH_TWO_PASS, SIGNATURES,

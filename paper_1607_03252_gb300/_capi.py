@@ -79,10 +79,15 @@ MLMC_ACCEL_CG = 1
 MLMC_ACCEL_FMG = 2
 
 
+MLMC_ENGINE_AUTO = 0
+MLMC_ENGINE_BATCHED = 1
+MLMC_ENGINE_CTA = 2
+
+
 class MgCfg(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_cycles", ctypes.c_int), ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("accel", ctypes.c_int), ("disc", ctypes.c_int)]
+                ("accel", ctypes.c_int), ("disc", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
 class MgStats(ctypes.Structure):
@@ -283,9 +288,9 @@ def field_cfg(run_seed, sigma2, ell, M, cov=MLMC_COV_GAUSS):
 
 
 def mg_cfg(nu1=2, nu2=2, rtol=1e-10, max_cycles=100, precision=MLMC_PREC_F64, smoother=MLMC_SMOOTH_AUTO,
-           accel=MLMC_ACCEL_NONE, disc=MLMC_DISC_FV):
+           accel=MLMC_ACCEL_NONE, disc=MLMC_DISC_FV, engine=MLMC_ENGINE_AUTO):
     return MgCfg(int(nu1), int(nu2), float(rtol), int(max_cycles), int(precision), int(smoother), int(accel),
-                 int(disc))
+                 int(disc), int(engine))
 
 
 def mlmc_field_eval(cfg: FieldCfg, sample_ids, k_out, stream=None, n_fine=None):
@@ -451,13 +456,14 @@ def inject_alloc_failure(after: int):
 
 def make_mlmc_cfg(run_seed, sigma2, ell, M, n0=17, nu1=2, nu2=2, rtol=1e-10, max_cycles=100,
                   precision=MLMC_PREC_F64, max_batch=0, stream=None, smoother=MLMC_SMOOTH_AUTO,
-                  accel=MLMC_ACCEL_NONE, cov=MLMC_COV_GAUSS, disc=MLMC_DISC_FV, qoi=MLMC_QOI_MEAN):
+                  accel=MLMC_ACCEL_NONE, cov=MLMC_COV_GAUSS, disc=MLMC_DISC_FV, qoi=MLMC_QOI_MEAN,
+                  engine=MLMC_ENGINE_AUTO):
     sp = ctypes.c_void_p(0)
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream)
     return MlmcCfg(field_cfg(run_seed, sigma2, ell, M, cov),
-                   mg_cfg(nu1, nu2, rtol, max_cycles, precision, smoother, accel, disc), int(n0), int(max_batch), sp,
-                   int(qoi))
+                   mg_cfg(nu1, nu2, rtol, max_cycles, precision, smoother, accel, disc, engine), int(n0),
+                   int(max_batch), sp, int(qoi))
 
 
 class Service:

@@ -97,6 +97,10 @@ static int check_mg(const mg_cfg* c) {
     set_error("unknown disc %d", c->disc);
     return MLMC_ERR_INVALID;
   }
+  if (c->engine != MLMC_ENGINE_AUTO && c->engine != MLMC_ENGINE_BATCHED && c->engine != MLMC_ENGINE_CTA) {
+    set_error("unknown engine %d", c->engine);
+    return MLMC_ERR_INVALID;
+  }
   if ((c->disc == MLMC_DISC_FE || c->accel == MLMC_ACCEL_FMG) && c->precision != MLMC_PREC_F64) {
     set_error("the P1 finite elements and the FMG cycle run in FP64 (precision %d)", c->precision);
     return MLMC_ERR_INVALID;
@@ -107,7 +111,8 @@ static int check_mg(const mg_cfg* c) {
 // `cov` sits in what was the struct's tail padding: the size and every other offset are
 // those of the four-field layout, so zero-initialised callers get the Gaussian covariance.
 static_assert(sizeof(mlmc_field_cfg) == 32 && offsetof(mlmc_field_cfg, cov) == 28, "mlmc_field_cfg layout");
-static_assert(sizeof(mg_cfg) == 40 && offsetof(mg_cfg, disc) == 32, "mg_cfg layout");
+static_assert(sizeof(mg_cfg) == 40 && offsetof(mg_cfg, disc) == 32 && offsetof(mg_cfg, engine) == 36,
+              "mg_cfg layout");
 static_assert(sizeof(mlmc_cfg) == 96 && offsetof(mlmc_cfg, qoi) == 88, "mlmc_cfg layout");
 
 static int check_field(const mlmc_field_cfg* c) {

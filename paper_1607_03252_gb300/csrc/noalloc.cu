@@ -67,7 +67,8 @@ extern "C" int mg_solve_batch_noalloc(const mg_cfg* cfg, int batch, int n, const
       cfg->smoother < MLMC_SMOOTH_AUTO || cfg->smoother > MLMC_SMOOTH_SPLIT ||
       (cfg->accel != MLMC_ACCEL_NONE && cfg->accel != MLMC_ACCEL_CG) ||
       (cfg->disc != MLMC_DISC_FV && cfg->disc != MLMC_DISC_FE) ||
-      (cfg->disc == MLMC_DISC_FE && cfg->precision != MLMC_PREC_F64)) {
+      (cfg->disc == MLMC_DISC_FE && cfg->precision != MLMC_PREC_F64) || cfg->engine < MLMC_ENGINE_AUTO ||
+      cfg->engine > MLMC_ENGINE_CTA) {
     set_error("mg_solve_batch_noalloc: invalid mg_cfg (FMG is not offered here; P1 elements need FP64)");
     return MLMC_ERR_INVALID;
   }

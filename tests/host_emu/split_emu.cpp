@@ -27,6 +27,10 @@ static dim3 blockIdx, threadIdx, blockDim, gridDim;
 static float __fdividef(float a, float b) { return a / b; }
 static float __fadd_rn(float a, float b) { return a + b; }
 static int __clz(int x) { return x == 0 ? 32 : __builtin_clz((unsigned)x); }
+struct float4 {
+  float x, y, z, w;
+};
+static float4 make_float4(float a, float b, float c, float d) { return float4{a, b, c, d}; }
 static float fmaf_(float a, float b, float c) { return std::fmaf(a, b, c); }
 #define fmaf fmaf_
 using std::fma;
@@ -84,11 +88,11 @@ int main(int argc, char** argv) {
   // a red and a black pass
   std::vector<float> up = u, us = to_split(u, perm, B * ns), ks = to_split(kn, perm, B * ns),
                      gs = to_split(g, perm, B * ns);
-  const int m = n - 2, half = (n - 1) / 2, P = (n + 1) / 2;
+  const int m = n - 2, half = (n - 1) / 2, P = mlmc::split_pitch(n);
   for (int c = 0; c < 2; ++c) {
     launch(dim3((unsigned)((m * half + T - 1) / T), (unsigned)(B * m)), dim3(T),
            [&] { mlmc::k_rbgs_nodal(c, n, B, kn.data(), g.data(), up.data(), nullptr); });
-    MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * P + 127) / 128), (unsigned)m, (unsigned)B), dim3(128), [&] {
+    MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * (P / 4) + 127) / 128), (unsigned)m, (unsigned)B), dim3(128), [&] {
       mlmc::k_rbgs_split<LG>(c, ks.data(), gs.data(), us.data(), nullptr);
     }));
   }
@@ -96,12 +100,13 @@ int main(int argc, char** argv) {
   out.insert(out.end(), up.begin(), up.end());
   out.insert(out.end(), usb.begin(), usb.end());
   // the nodal residual of the swept iterate
-  std::vector<float> rp(B * n3, nan), rs(B * n3, nan);
+  std::vector<float> rp(B * n3, nan), rss(B * ns, 0.0f);
   launch(dim3((unsigned)((n * n + T - 1) / T), (unsigned)(B * n)), dim3(T),
          [&] { mlmc::k_residual_nodal(n, B, kn.data(), g.data(), up.data(), rp.data(), nullptr); });
-  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((n * n + 127) / 128), (unsigned)n, (unsigned)B), dim3(128), [&] {
-    mlmc::k_residual_split<LG>(ks.data(), gs.data(), us.data(), rs.data(), nullptr);
+  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * (P / 4) + 127) / 128), (unsigned)m, (unsigned)(2 * B)), dim3(128), [&] {
+    mlmc::k_residual_split<LG>(ks.data(), gs.data(), us.data(), rss.data(), nullptr);
   }));
+  auto rs = from_split(rss, perm);  // the split residual leaves boundary slots unwritten (zero here)
   out.insert(out.end(), rp.begin(), rp.end());
   out.insert(out.end(), rs.begin(), rs.end());
   // the trilinear correction
@@ -116,13 +121,12 @@ int main(int argc, char** argv) {
   out.insert(out.end(), pp.begin(), pp.end());
   out.insert(out.end(), psb.begin(), psb.end());
   // full weighting into the plain and the split coarse storage
-  std::vector<float> gcp(B * nc3, 0.0f), gcs(B * nsc, 0.0f);
-  for (size_t i = 0; i < permc.size(); ++i) gcs[permc[i]] = 0.0f;
+  std::vector<float> gcp(B * nc3, 0.0f), gcs(B * nsc, 0.0f), r_s = to_split(r, perm, B * ns);
   const int hc = nc - 1;
   launch(dim3((unsigned)(((nc - 2) * hc + T - 1) / T), (unsigned)(B * (nc - 2))), dim3(T),
          [&] { mlmc::k_restrict<float, false>(n, B, r.data(), gcp.data(), nullptr); });
-  launch(dim3((unsigned)(((nc - 2) * hc + T - 1) / T), (unsigned)(B * (nc - 2))), dim3(T),
-         [&] { mlmc::k_restrict<float, true>(n, B, r.data(), gcs.data(), nullptr); });
+  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)(((nc - 2) * (nc - 2) + 127) / 128), (unsigned)(nc - 2), (unsigned)B),
+                                dim3(128), [&] { mlmc::k_restrict_split<LG>(r_s.data(), gcs.data(), nullptr); }));
   auto gcsb = from_split(gcs, permc);
   out.insert(out.end(), gcp.begin(), gcp.end());
   out.insert(out.end(), gcsb.begin(), gcsb.end());

@@ -283,14 +283,15 @@ SMOOTHERS = [mg.MLMC_SMOOTH_TWO_PASS, mg.MLMC_SMOOTH_FUSED_32x8, mg.MLMC_SMOOTH_
 @pytest.mark.parametrize("n", [9, 17, 33, 65])
 def test_smoother_variants_identical_fixed_cycles(prec, n):
     """The fused one-pass sweep (every tile shape) performs the same operations on the
-    same operands as the two-pass colour sweep: identical iterates, bit for bit."""
+    same operands as the two-pass colour sweep: identical iterates, bit for bit (batched
+    engine: the kernels themselves)."""
     B = 3
     k = to_dev(np.stack([random_coefficient(n, 500 + s, 1.0) for s in range(B)]))
     f = to_dev(np.stack([random_rhs(n, 600 + s) for s in range(B)]))
     outs = []
     for sm in SMOOTHERS:
         u = torch.zeros_like(k)
-        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 0.0, 3, prec, sm), k, u, f)
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 0.0, 3, prec, sm, engine=mg.MLMC_ENGINE_BATCHED), k, u, f)
         outs.append((u.cpu().numpy(), rel))
     for u, rel in outs[1:]:
         assert np.array_equal(u, outs[0][0])
@@ -307,7 +308,7 @@ def test_smoother_variants_identical_with_masking(prec, orc):
     outs = []
     for sm in SMOOTHERS:
         u = torch.zeros_like(k)
-        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-10, 200, prec, sm), k, u)
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-10, 200, prec, sm, engine=mg.MLMC_ENGINE_BATCHED), k, u)
         outs.append((u.cpu().numpy(), cyc))
     assert len(set(outs[0][1].tolist())) > 1  # the samples did stop at different cycles
     for u, cyc in outs[1:]:
@@ -333,7 +334,7 @@ def test_graph_replay_matches_direct_launches(orc, prec, accel, sm):
     n, B = 33, 4
     ks = [orc.field(RUN_SEED, int(i), 256, 1.0 + 0.5 * s, 0.15, n) for s, i in enumerate(sample_ids(4, 0, B))]
     k = to_dev(np.stack(ks))
-    cfg = mg.mg_cfg(2, 2, 1e-10, 200, prec, sm, accel)
+    cfg = mg.mg_cfg(2, 2, 1e-10, 200, prec, sm, accel, engine=mg.MLMC_ENGINE_BATCHED)
     u0 = torch.zeros_like(k)
     cyc0, rel0, st0 = mg.mg_solve_batch(cfg, k, u0)
     side = torch.cuda.Stream()
@@ -359,7 +360,7 @@ def test_nodal_smoother_reaches_the_same_solution(orc, accel):
     out = {}
     for sm in (mg.MLMC_SMOOTH_TWO_PASS, mg.MLMC_SMOOTH_NODAL):
         u = torch.zeros_like(k)
-        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-12, 200, mg.MLMC_PREC_MIXED, sm, accel), k, u)
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-12, 200, mg.MLMC_PREC_MIXED, sm, accel, engine=mg.MLMC_ENGINE_BATCHED), k, u)
         assert st == 0 and np.all(rel <= 1e-12)
         out[sm] = (u.cpu().numpy(), cyc)
     for s in range(B):
@@ -383,7 +384,7 @@ def test_split_storage_equals_nodal_sweep_bitwise(orc, accel, n):
     out = {}
     for sm in (mg.MLMC_SMOOTH_NODAL, mg.MLMC_SMOOTH_SPLIT):
         u = torch.zeros_like(k)
-        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-10, 200, mg.MLMC_PREC_MIXED, sm, accel), k, u)
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-10, 200, mg.MLMC_PREC_MIXED, sm, accel, engine=mg.MLMC_ENGINE_BATCHED), k, u)
         assert st == 0
         out[sm] = (u.cpu().numpy(), cyc, rel)
     a, b = out[mg.MLMC_SMOOTH_NODAL], out[mg.MLMC_SMOOTH_SPLIT]
@@ -394,7 +395,7 @@ def test_split_storage_equals_nodal_sweep_bitwise(orc, accel, n):
 def test_split_storage_level_estimate_matches_oracle(orc):
     level, ids = 2, sample_ids(2, 30, 3)
     cfg = mg.make_mlmc_cfg(RUN_SEED, 2.0, 0.2, 256, n0=17, rtol=1e-11, precision=mg.MLMC_PREC_MIXED,
-                           smoother=mg.MLMC_SMOOTH_SPLIT, accel=mg.MLMC_ACCEL_CG)
+                           smoother=mg.MLMC_SMOOTH_SPLIT, accel=mg.MLMC_ACCEL_CG, engine=mg.MLMC_ENGINE_BATCHED)
     _, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
     Y64, Qf64, Qc64, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 2.0, 0.2, 256, rtol=1e-11), 65, 33, ids)
     assert np.all(_mixed_err(Y, Y64, Qf64, Qc64, "level 2, colour-split storage, CG") <= 1e-9)
@@ -449,7 +450,7 @@ def test_cg_with_rhs_and_smoothers(orc):
         u, cyc, rel, st = gpu_solve(ks, fs, rtol=1e-12, max_cycles=100)
         k = to_dev(np.stack(ks))
         ug = torch.zeros_like(k)
-        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-12, 100, mg.MLMC_PREC_F64, sm, mg.MLMC_ACCEL_CG), k, ug,
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 1e-12, 100, mg.MLMC_PREC_F64, sm, mg.MLMC_ACCEL_CG, engine=mg.MLMC_ENGINE_BATCHED), k, ug,
                                          to_dev(np.stack(fs)))
         ug = ug.cpu().numpy()
         for s in range(3):

@@ -2,7 +2,7 @@
 plain-layout counterparts, no GPU: the kernels' own text compiled with g++, the launch a
 loop over every block and thread. The split storage map is computed here from its
 definition (per sample, colour c = (x + y + z) % 2 block of n x n rows of (n + 1) / 2
-slots, node x at slot x // 2); slots that hold no node are NaN, so a kernel that read one
+slots rounded up to a multiple of 4, node x at slot x // 2); slots that hold no node are NaN, so a kernel that read one
 would poison its result. A red and a black pass, the nodal residual, the trilinear
 correction, full weighting into split coarse storage and the reciprocal coefficient must
 equal the plain kernels bit for bit."""
@@ -40,9 +40,10 @@ def _host(text):
 
 
 def split_perm(n, B):
-    """Plain index (s, z, y, x) -> colour-split index, from the definition."""
-    P = (n + 1) // 2
-    ns = n * n * (n + 1)
+    """Plain index (s, z, y, x) -> colour-split index, from the definition (rows of
+    (n + 1) / 2 slots padded to a multiple of 4)."""
+    P = ((n + 1) // 2 + 3) // 4 * 4
+    ns = 2 * n * n * P
     z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
     c = (x + y + z) % 2
     within = c * (n * n * P) + (z * n + y) * P + x // 2
@@ -52,7 +53,8 @@ def split_perm(n, B):
 def test_split_map_is_a_bijection_onto_its_slots():
     for n in (5, 9, 17, 33):
         p = split_perm(n, 2)
-        assert len(np.unique(p)) == len(p) and p.max() < 2 * n * n * (n + 1)
+        P = ((n + 1) // 2 + 3) // 4 * 4
+        assert len(np.unique(p)) == len(p) and p.max() < 2 * (2 * n * n * P)  # two samples
 
 
 @pytest.fixture(scope="module")
