@@ -52,6 +52,9 @@ NCU_TRAFFIC = {
     "rbgs_f32": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs", "kernel_sha": "e8e43de9d3e4896e",
                  "dram_bytes_per_unit": (805.619e6 + 121.530e6) / (2 * 255 ** 3), "unit_bytes": 3.5 * 4,
                  "source": "profiles/rbgs_f32_n257_b2.md (257^3 x 2, one colour pass)"},
+    "rbgs_split_f32": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs_split", "kernel_sha": "9d3393d2d0414e4e",
+                       "dram_bytes_per_unit": (281.681e6 + 55.126e6) / (2 * 255 ** 3), "unit_bytes": 2.0 * 4,
+                       "source": "profiles/rbgs_split_f32_n257_b2.md (257^3 x 2, one colour pass)"},
     "rbgs_nodal_f32": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs_nodal", "kernel_sha": "cb8a0fa77df739fc",
                        "dram_bytes_per_unit": (405.356e6 + 107.601e6) / (2 * 255 ** 3), "unit_bytes": 2.0 * 4,
                        "source": "profiles/rbgs_nodal_f32_n257_b2.md (257^3 x 2, one colour pass)"},
@@ -63,8 +66,11 @@ def kernel_sha(path, name):
     import hashlib
 
     try:
+        import re
+
         src = open(os.path.join(ROOT, path)).read()
-        i = src.index("__global__ void " + name + "(")
+        m = re.search(r"__global__ void (__launch_bounds__\([^)]*\) )?" + re.escape(name) + r"\(", src)
+        i = m.start()
         j = src.index("{", i)
         depth = 0
         for k in range(j, len(src)):

@@ -537,8 +537,9 @@ typedef struct {
  * solves and P1 finite elements, which have no nodal-coefficient sweep) and the sweep count
  * nu in {1,2,3} of V(nu, nu) for MLMC level
  * `level` under cfg (no counterpart in the paper; the paper fixes its cycle, Sec. 7.1).
- * Each candidate runs the whole level pipeline once untimed and once timed on
- * `samples` realisations first_id .. first_id + samples - 1; the fastest by wall time
+ * Each candidate runs the whole level pipeline on the batched engine
+ * (MLMC_ENGINE_BATCHED) once untimed and once timed on `samples` realisations
+ * first_id .. first_id + samples - 1; the fastest by wall time
  * per sample is stored in a process-wide table for the level's fine grid size and
  * precision, where MLMC_SMOOTH_AUTO and nu1 = nu2 = 0 find it. With nu1 = nu2 > 0 in
  * cfg->mg only the smoother is tuned, at that nu. Every candidate solves

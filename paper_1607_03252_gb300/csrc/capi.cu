@@ -613,6 +613,10 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
       mc.smoother = smoothers[si];
       mc.nu1 = nu;
       mc.nu2 = nu;
+      // the batched engine: the stored choice also serves this grid size as a level inside
+      // the batched V-cycles of larger grids (the small-grid engine runs every smoother of
+      // one arithmetic family in the same time, so it could not tell them apart)
+      mc.engine = MLMC_ENGINE_BATCHED;
       double secs = 0.0;
       LevelRecord r{};
       for (int rep = 0; rep < 2; ++rep) {

@@ -594,45 +594,71 @@ __global__ void __launch_bounds__(128) k_restrict_split(const float* __restrict_
 
 // u_f += trilinear interpolation of e_c on colour-split storage of both grids: the
 // coarse terms of k_prolong in its order (rows (Z, Y), (Z, Y+1), (Z+1, Y), (Z+1, Y+1),
-// each X then X+1) and its weights, so the result is bit for bit that of k_prolong.
-// LG: the fine grid's. Grid (interior nodes of a plane, interior planes, samples).
+// each X then X+1) and its weights, so the result is bit for bit that of k_prolong. A
+// thread corrects the four fine nodes of one four-slot group of one colour (x = x0 + 2 i,
+// coarse X = xi0 + i, one x parity, hence one weight pattern) with a 16-byte update of u;
+// each coarse row it needs is gathered once for the group (X = xi0 .. xi0 + 4). LG: the
+// fine grid's. Grid (groups of the interior rows of a plane, interior planes,
+// 2 x samples: colour = blockIdx.z & 1).
 template <int LG>
 __global__ void __launch_bounds__(128) k_prolong_split(const float* __restrict__ ec, float* __restrict__ u,
                                                        const int* __restrict__ active) {
   using F = SplitGeo<LG>;
   using C = SplitGeo<LG - 1>;
-  constexpr int m = F::m;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // interior node of the plane
-  if (q >= m * m) return;
-  const int s = blockIdx.z;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= F::m * F::Q4) return;
+  const int s = blockIdx.z >> 1, colour = blockIdx.z & 1;
   if (active && !active[s]) return;
-  const int y = 1 + q / m, x = 1 + q - (y - 1) * m, z = 1 + (int)blockIdx.y;
-  const int xo = x & 1, yo = y & 1, zo = z & 1, X = x >> 1, Y = y >> 1, Z = z >> 1;
+  const int yi = q / F::Q4, qi = q - yi * F::Q4, y = 1 + yi, z = 1 + (int)blockIdx.y;
+  const int xo = (colour + y + z) & 1, xi0 = 4 * qi, x0 = 2 * xi0 + xo;
+  if (x0 > F::n - 2) return;
+  const int yo = y & 1, zo = z & 1, Y = y >> 1, Z = z >> 1;
   const float* e = ec + (size_t)s * C::NS;
-  // coarse node (X + a, Y + b, Z + c): colour (X + Y + Z + a + b + c) & 1, slot
-  // ((Z + c) n_c + Y + b) P_c + ((X + a) >> 1)
-  auto at = [&](int a, int b, int c) -> float {
-    const int cx = X + a, cy = Y + b, cz = Z + c;
-    return e[(size_t)((cx + cy + cz) & 1) * C::BLK + (size_t)((cz * C::n + cy) * C::P + (cx >> 1))];
+  // coarse row (Y + b, Z + c) at X = xi0 + t, t = 0 .. 4 (xi0 even: colour (t + Y + b + Z + c) & 1,
+  // slot xi0 / 2 + t / 2)
+  auto row = [&](int b, int c, float* cv) {
+    const int cy = Y + b, cz = Z + c, base = (cz * C::n + cy) * C::P + (xi0 >> 1);
+#pragma unroll
+    for (int t = 0; t < 5; ++t)
+      if (t < 4 || xo) cv[t] = e[(size_t)((t + cy + cz) & 1) * C::BLK + (size_t)(base + (t >> 1))];
   };
-  float v = 0.0f;
-  v += at(0, 0, 0);
-  if (xo) v += at(1, 0, 0);
-  if (yo) {
-    v += at(0, 1, 0);
-    if (xo) v += at(1, 1, 0);
-  }
+  float r00[5], r10[5], r01[5], r11[5];  // rows (Y, Z), (Y+1, Z), (Y, Z+1), (Y+1, Z+1)
+  row(0, 0, r00);
+  if (yo) row(1, 0, r10);
   if (zo) {
-    v += at(0, 0, 1);
-    if (xo) v += at(1, 0, 1);
-    if (yo) {
-      v += at(0, 1, 1);
-      if (xo) v += at(1, 1, 1);
-    }
+    row(0, 1, r01);
+    if (yo) row(1, 1, r11);
   }
   const float w = xo + yo + zo == 0 ? 1.0f : xo + yo + zo == 1 ? 0.5f : xo + yo + zo == 2 ? 0.25f : 0.125f;
-  const int c = (x + y + z) & 1;
-  u[(size_t)s * F::NS + (size_t)c * F::BLK + (size_t)((z * F::n + y) * F::P + (x >> 1))] += w * v;
+  float* uc = u + (size_t)s * F::NS + (size_t)colour * F::BLK + (size_t)((z * F::n + y) * F::P + xi0);
+  const float4 u4 = ld4(uc);
+  float out[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float v = 0.0f;
+    v += r00[i];
+    if (xo) v += r00[i + 1];
+    if (yo) {
+      v += r10[i];
+      if (xo) v += r10[i + 1];
+    }
+    if (zo) {
+      v += r01[i];
+      if (xo) v += r01[i + 1];
+      if (yo) {
+        v += r11[i];
+        if (xo) v += r11[i + 1];
+      }
+    }
+    out[i] = comp(u4, i) + w * v;
+  }
+  if (x0 >= 1 && x0 + 6 <= F::n - 2) {
+    *reinterpret_cast<float4*>(uc) = make_float4(out[0], out[1], out[2], out[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (x0 + 2 * i >= 1 && x0 + 2 * i <= F::n - 2) uc[i] = out[i];
+  }
 }
 
 // Dispatch of a colour-split kernel template on n = 2^LG + 1 (5 .. 1025).
@@ -1443,9 +1469,8 @@ void vcycle_split(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   vcycle(H, j + 1, nu1, nu2, st);
   MLMC_LAUNCH(prof::sized("prolong_split_f32", v.n), Ba * (2.0 * (double)v.n3 + (double)w.n3) * W,
               Ba * interior(v.n) * 4.375, st,
-              MLMC_SPLIT_DISPATCH(v.n, (k_prolong_split<LG><<<dim3((unsigned)((m * m + 127) / 128), (unsigned)m,
-                                                                    (unsigned)B), 128, 0, st>>>(
-                                                (const float*)(const void*)w.u, u, act))));
+              MLMC_SPLIT_DISPATCH(v.n, (k_prolong_split<LG><<<dim3(groups, (unsigned)m, (unsigned)(2 * B)), 128, 0,
+                                                               st>>>((const float*)(const void*)w.u, u, act))));
   smooth(nu2);
 }
 

@@ -4,6 +4,7 @@
       [--smoother two-pass|32x8|32x16|64x8|bulk32x8|bulk32x16|bulk64x8|nodal|split] [--accel cg] [--timing]
       [--field gauss|exp|spde] [--level L --n0 17] [--disc fv|fe] [--accel fmg] [--qoi mean|point|flux]
   python -m paper_1607_03252_gb300.profile_case --fma-peak
+  python -m paper_1607_03252_gb300.profile_case --level 0 --batch 64 --engine cta|batched --timing
 
 Evaluates the lognormal field (sigma^2 = 1, ell = 0.3, M = 256 unless given) for `batch`
 realisations on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0; or V(nu, nu)
@@ -49,6 +50,8 @@ def main(argv=None):
     p.add_argument("--level", type=int, default=-1, help="run one MLMC level estimate instead")
     p.add_argument("--n0", type=int, default=17)
     p.add_argument("--fma-peak", action="store_true", help="print the measured FP64 and FP32 FMA throughput and exit")
+    p.add_argument("--engine", choices=["auto", "batched", "cta"], default="auto",
+                   help="execution engine of the solves (mg_cfg.engine)")
     a = p.parse_args(argv)
     if a.fma_peak:
         f64 = mg.profile_fma_peak(mg.MLMC_PREC_F64)
@@ -67,11 +70,12 @@ def main(argv=None):
     qoi = {"mean": mg.MLMC_QOI_MEAN, "point": mg.MLMC_QOI_POINT, "flux": mg.MLMC_QOI_FLUX}[a.qoi]
     cov = {"gauss": mg.MLMC_COV_GAUSS, "exp": mg.MLMC_COV_EXP, "spde": mg.MLMC_COV_SPDE}[a.field]
     fcfg = mg.field_cfg(RUN_SEED, a.sigma2, a.ell, a.M, cov=cov)
+    engine = {"auto": mg.MLMC_ENGINE_AUTO, "batched": mg.MLMC_ENGINE_BATCHED, "cta": mg.MLMC_ENGINE_CTA}[a.engine]
     if a.level >= 0:
         fmg = accel == mg.MLMC_ACCEL_FMG
         lcfg = mg.make_mlmc_cfg(RUN_SEED, a.sigma2, a.ell, a.M, n0=a.n0, nu1=a.nu, nu2=a.nu,
                                 rtol=0.0 if fmg else 1e-10, max_cycles=a.cycles if fmg else 300, precision=prec,
-                                smoother=sm, accel=accel, cov=cov, disc=disc, qoi=qoi)
+                                smoother=sm, accel=accel, cov=cov, disc=disc, qoi=qoi, engine=engine)
         first = sample_ids(a.level, 0, 1)[0]
         st, *_ = mg.mlmc_level_estimate(lcfg, a.level, int(first), a.batch, want_samples=False)
         print("level=%d n0=%d samples=%d field=%s mean=%.6e var=%.3e" % (a.level, a.n0, a.batch, a.field, st.mean,
@@ -80,10 +84,12 @@ def main(argv=None):
             import time
 
             torch.cuda.synchronize()
+            mg.profile_reset()
             t0 = time.perf_counter()
             mg.mlmc_level_estimate(lcfg, a.level, int(first), a.batch, want_samples=False)
             dt = time.perf_counter() - t0
-            print("  level estimate wall time: %.3f ms (%.1f samples/s)" % (dt * 1e3, a.batch / dt))
+            print("  level estimate wall time: %.3f ms (%.1f samples/s), %d launches (engine %s)"
+                  % (dt * 1e3, a.batch / dt, mg.profile_total_launches(), a.engine))
             mg.profile_reset()
             mg.profile_enable(True)
             mg.mlmc_level_estimate(lcfg, a.level, int(first), a.batch, want_samples=False)
@@ -94,7 +100,7 @@ def main(argv=None):
     k = torch.empty((a.batch, a.n, a.n, a.n), dtype=torch.float64, device="cuda")
     mg.mlmc_field_eval(fcfg, sample_ids(3, 0, a.batch), k)
     u = torch.zeros_like(k)
-    cfg = mg.mg_cfg(a.nu, a.nu, a.rtol, a.cycles, prec, sm, accel, disc)
+    cfg = mg.mg_cfg(a.nu, a.nu, a.rtol, a.cycles, prec, sm, accel, disc, engine)
     cyc, rel, st = mg.mg_solve_batch(cfg, k, u)
     torch.cuda.synchronize()
     print("n=%d batch=%d prec=%s cycles=%s rel_res=%.3e" % (a.n, a.batch, a.prec, cyc.tolist(), rel.max()))

@@ -114,7 +114,7 @@ int main(int argc, char** argv) {
   const int P2 = n - 1;
   launch(dim3((unsigned)((m * P2 + T - 1) / T), (unsigned)(B * m)), dim3(T),
          [&] { mlmc::k_prolong<float>(n, B, ec.data(), pp.data(), nullptr); });
-  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * m + 127) / 128), (unsigned)m, (unsigned)B), dim3(128), [&] {
+  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * (P / 4) + 127) / 128), (unsigned)m, (unsigned)(2 * B)), dim3(128), [&] {
     mlmc::k_prolong_split<LG>(ecs.data(), ps.data(), nullptr);
   }));
   auto psb = from_split(ps, perm);
