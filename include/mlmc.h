@@ -122,17 +122,21 @@ typedef struct {
                                     outer residual on the stored faces fixes the solution: results
                                     agree with the other smoothers to the solve tolerance, not bit
                                     for bit. An FP64 solve uses MLMC_SMOOTH_TWO_PASS. */
-#define MLMC_SMOOTH_SPLIT 9      /* MLMC_SMOOTH_NODAL's sweep (bit for bit the same iterates) with
-                                    the FP32 hierarchy stored colour-split: per sample the red
+#define MLMC_SMOOTH_SPLIT 9      /* the hierarchy stored colour-split: per sample the red
                                     ((x+y+z) even) and the black nodes form two blocks of n x n
-                                    rows of (n+1)/2 slots (node x at slot x/2), so that a colour
-                                    pass streams the rows of the colour it updates and of the
-                                    other colour it reads, 2.5 instead of 4 words per node at
-                                    cache-line granularity. Chosen for the finest grid, it
-                                    applies to every grid of the hierarchy; on a coarser grid
-                                    alone it means MLMC_SMOOTH_NODAL. FP32 correction cycles on
-                                    finite volumes only (an FP64 solve uses
-                                    MLMC_SMOOTH_TWO_PASS). */
+                                    rows of (n+1)/2 slots rounded up to a multiple of 4 (node x
+                                    at slot x/2), so that a colour pass streams only the rows of
+                                    the colour it updates and of the other colour it reads. In
+                                    FP32 correction cycles (MLMC_PREC_MIXED) the sweep is
+                                    MLMC_SMOOTH_NODAL's (bit for bit the same iterates; 2.5
+                                    instead of 4 words per node at cache-line granularity); in
+                                    FP64 stationary cycles (MLMC_ACCEL_NONE) it is the stored-face
+                                    sweep of MLMC_SMOOTH_TWO_PASS (bit for bit the same iterates,
+                                    cycles and residuals; 5 instead of ~7 words per node and
+                                    pass). Finite volumes and n <= 1025 only. Chosen for the
+                                    finest grid, it applies to every grid of the hierarchy; on a
+                                    coarser grid alone, or where it does not apply, it means
+                                    MLMC_SMOOTH_NODAL (FP32) or MLMC_SMOOTH_TWO_PASS (FP64). */
 
 /* Outer iteration around the V-cycle. */
 #define MLMC_ACCEL_NONE 0 /* stationary: repeat V-cycles (FP64), or FP32 V-cycles as corrections of
@@ -533,8 +537,9 @@ typedef struct {
 /*
  * mlmc_autotune -- picks the smoother implementation (two-pass on stored faces, two-pass
  * on the nodal coefficient in the plain or the colour-split storage, or fused with 32x8,
- * 32x16 or 64x8 tiles staged by cp.async or by TMA bulk copies: 9 candidates; 7 for FP64
- * solves and P1 finite elements, which have no nodal-coefficient sweep) and the sweep count
+ * 32x16 or 64x8 tiles staged by cp.async or by TMA bulk copies: 9 candidates for FP32
+ * correction cycles on finite volumes; 8 for FP64 stationary cycles on finite volumes
+ * (the colour-split stored-face sweep, no nodal-coefficient sweep); 7 otherwise) and the sweep count
  * nu in {1,2,3} of V(nu, nu) for MLMC level
  * `level` under cfg (no counterpart in the paper; the paper fixes its cycle, Sec. 7.1).
  * Each candidate runs the whole level pipeline on the batched engine

@@ -130,7 +130,7 @@ static int check_field(const mlmc_field_cfg* c) {
 
 static int check_grid(int n, int batch) {
   if (!valid_grid(n)) {
-    set_error("n=%d is not 2^p+1 with 5 <= n <= 1025", n);
+    set_error("n=%d is not 2^p+1 with 5 <= n <= 4097", n);
     return MLMC_ERR_INVALID;
   }
   if (batch < 1 || batch > 65535) {
@@ -605,12 +605,19 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   // an explicit V(nu, nu) in cfg is kept: only the smoother implementation is tuned
   const bool fixed_nu = cfg->mg.nu1 > 0 && cfg->mg.nu1 == cfg->mg.nu2;
   const int nu_lo = fixed_nu ? cfg->mg.nu1 : 1, nu_hi = fixed_nu ? cfg->mg.nu1 : 3;
-  // the nodal-coefficient sweeps exist only in FP32 correction cycles on finite volumes
-  const int n_sm = (cfg->mg.precision == MLMC_PREC_MIXED && cfg->mg.disc == MLMC_DISC_FV) ? 9 : 7;
+  // the nodal-coefficient sweeps exist only in FP32 correction cycles on finite volumes;
+  // the colour-split storage there and in FP64 stationary cycles on finite volumes
+  const bool fv = cfg->mg.disc == MLMC_DISC_FV, mixed = cfg->mg.precision == MLMC_PREC_MIXED;
+  int cand[9], n_sm = 0;
+  for (int si = 0; si < 9; ++si) {
+    if (smoothers[si] == MLMC_SMOOTH_NODAL && !(fv && mixed)) continue;
+    if (smoothers[si] == MLMC_SMOOTH_SPLIT && !(fv && (mixed || cfg->mg.accel == MLMC_ACCEL_NONE))) continue;
+    cand[n_sm++] = smoothers[si];
+  }
   for (int nu = nu_lo; nu <= nu_hi; ++nu)
     for (int si = 0; si < n_sm; ++si) {
       mg_cfg mc = cfg->mg;
-      mc.smoother = smoothers[si];
+      mc.smoother = cand[si];
       mc.nu1 = nu;
       mc.nu2 = nu;
       // the batched engine: the stored choice also serves this grid size as a level inside
@@ -638,7 +645,7 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
       }
       const double per = secs / samples;
       if (count < table_len) {
-        table[count].smoother = smoothers[si];
+        table[count].smoother = cand[si];
         table[count].nu = nu;
         table[count].seconds_per_sample = per;
         table[count].mean_cycles = r.N > 0 ? r.cyc_f / r.N : 0.0;
@@ -646,7 +653,7 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
       ++count;
       if (per < best) {
         best = per;
-        bs = smoothers[si];
+        bs = cand[si];
         bnu = nu;
       }
     }

@@ -566,8 +566,8 @@ __global__ void __launch_bounds__(128) k_residual_split(const float* __restrict_
 // g_c = 4 FW(r~) (k_restrict's weights and order) from r~ in colour-split storage into the
 // coarse grid's colour-split g, at interior coarse nodes. LG: the fine grid's. Grid
 // (interior coarse nodes of a plane, interior coarse planes, samples).
-template <int LG>
-__global__ void __launch_bounds__(128) k_restrict_split(const float* __restrict__ r, float* __restrict__ gc,
+template <int LG, typename T = float>
+__global__ void __launch_bounds__(128) k_restrict_split(const T* __restrict__ r, T* __restrict__ gc,
                                                         const int* __restrict__ active) {
   using F = SplitGeo<LG>;
   using C = SplitGeo<LG - 1>;
@@ -577,17 +577,17 @@ __global__ void __launch_bounds__(128) k_restrict_split(const float* __restrict_
   const int s = blockIdx.z;
   if (active && !active[s]) return;
   const int Y = 1 + q / mc, X = 1 + q - (Y - 1) * mc, Z = 1 + (int)blockIdx.y;
-  const float* rb = r + (size_t)s * F::NS;
-  float v = 0.0f;
+  const T* rb = r + (size_t)s * F::NS;
+  T v = 0;
 #pragma unroll
   for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
-        const float wgt = (float)((2 - abs(dx)) * (2 - abs(dy)) * (2 - abs(dz))) * (float)(1.0 / 16.0);
+        const T wgt = (T)((2 - abs(dx)) * (2 - abs(dy)) * (2 - abs(dz))) * (T)(1.0 / 16.0);
         const int fx = 2 * X + dx, fy = 2 * Y + dy, fz = 2 * Z + dz;  // colour (dx + dy + dz) & 1
-        v = fmaf(wgt, rb[(size_t)((dx + dy + dz) & 1) * F::BLK + (size_t)((fz * F::n + fy) * F::P + (fx >> 1))], v);
+        v = fma(wgt, rb[(size_t)((dx + dy + dz) & 1) * F::BLK + (size_t)((fz * F::n + fy) * F::P + (fx >> 1))], v);
       }
   gc[(size_t)s * C::NS + (size_t)((X + Y + Z) & 1) * C::BLK + (size_t)((Z * C::n + Y) * C::P + (X >> 1))] = v;
 }
@@ -657,6 +657,265 @@ __global__ void __launch_bounds__(128) k_prolong_split(const float* __restrict__
   } else {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
+      if (x0 + 2 * i >= 1 && x0 + 2 * i <= F::n - 2) uc[i] = out[i];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Colour-split storage of FP64 stored-face grids (MLMC_SMOOTH_SPLIT in an FP64 solve):
+// u, g, r, the faces Kx, Ky, Kz (each at its lower node), D and 1/D of every grid but the
+// coarsest in the split storage. A colour pass then reads its own colour's faces, 1/D and
+// g, the other colour's three lower faces and u, and writes its own u: 5 words per node and
+// pass at line granularity against the plain layout's ~7. Every kernel performs the
+// two-pass kernels' operations in their order, so the iterates are those of
+// MLMC_SMOOTH_TWO_PASS bit for bit.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ double comp2(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+
+// harmonic faces of the (injected) FP64 nodal k into colour-split storage (k_faces).
+__global__ void k_faces_split(const double* __restrict__ k0, int n0, int st0, int n, int B, double* __restrict__ Kx,
+                              double* __restrict__ Ky, double* __restrict__ Kz) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
+  const size_t ns = split_elems(n), n03 = (size_t)n0 * n0 * n0;
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    const double* kb = k0 + (size_t)s * n03;
+    const size_t p0 = ((size_t)(st0 * z) * n0 + (size_t)(st0 * y)) * n0 + (size_t)(st0 * x);
+    const size_t t = (size_t)s * ns + split_index(n, x, y, z);
+    const double a = kb[p0];
+    Kx[t] = x < n - 1 ? harm(a, kb[p0 + st0], double()) : 0.0;
+    Ky[t] = y < n - 1 ? harm(a, kb[p0 + (size_t)st0 * n0], double()) : 0.0;
+    Kz[t] = z < n - 1 ? harm(a, kb[p0 + (size_t)st0 * n0 * n0], double()) : 0.0;
+  }
+}
+
+// D = sum of the six faces (k_diag's order) and 1/D at interior nodes, 0 on the boundary,
+// all in colour-split storage.
+__global__ void k_diag_split(int n, int B, const double* __restrict__ Kx, const double* __restrict__ Ky,
+                             const double* __restrict__ Kz, double* __restrict__ D, double* __restrict__ Dinv) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
+  const size_t ns = split_elems(n);
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    const size_t b = (size_t)s * ns, t = b + split_index(n, x, y, z);
+    const bool in = x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1;
+    double d = 0.0;
+    if (in) {
+      d = Kx[b + split_index(n, x - 1, y, z)];
+      d += Kx[t];
+      d += Ky[b + split_index(n, x, y - 1, z)];
+      d += Ky[t];
+      d += Kz[b + split_index(n, x, y, z - 1)];
+      d += Kz[t];
+    }
+    D[t] = d;
+    Dinv[t] = in ? 1.0 / d : 0.0;
+  }
+}
+
+// plain <-> colour-split copies of B samples of an n^3 grid (every node)
+template <typename T, bool TO_SPLIT>
+__global__ void k_split_copy(int n, int B, const T* __restrict__ a, T* __restrict__ b) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * n) return;
+  const int y = q / n, x = q - y * n;
+  const size_t n3 = (size_t)n * n * n, ns = split_elems(n);
+  for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
+    const int s = zz / n, z = zz - s * n;
+    const size_t tp = (size_t)s * n3 + (size_t)(z * n * n + q), ts = (size_t)s * ns + split_index(n, x, y, z);
+    if (TO_SPLIT)
+      b[ts] = a[tp];
+    else
+      b[tp] = a[ts];
+  }
+}
+
+// One colour of the stored-face sweep on colour-split FP64 storage (k_rbgs's operations
+// and order), two nodes per thread on 16-byte loads: its own Kx, Ky, Kz, 1/D and g, the
+// other colour's lower faces (x - 1, y - 1, z - 1 nodes) and u of the six neighbours.
+// Grid (two-slot groups of the interior rows of a plane, interior planes, samples).
+template <int LG>
+__global__ void __launch_bounds__(128) k_rbgs_split64(int colour, const double* __restrict__ Kx,
+                                                      const double* __restrict__ Ky, const double* __restrict__ Kz,
+                                                      const double* __restrict__ Dinv, const double* __restrict__ g,
+                                                      double* __restrict__ u, const int* __restrict__ active) {
+  using G = SplitGeo<LG>;
+  constexpr int Q2 = G::P / 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= G::m * Q2) return;
+  const int s = blockIdx.z;
+  if (active && !active[s]) return;
+  const int yi = q / Q2, qi = q - yi * Q2, y = 1 + yi, z = 1 + (int)blockIdx.y;
+  const int par = (colour + y + z) & 1, xi0 = 2 * qi, x0 = 2 * xi0 + par;  // node i: x = x0 + 2 i
+  if (x0 > G::n - 2) return;
+  const int o = (z * G::n + y) * G::P + xi0;
+  const size_t cb = (size_t)s * G::NS + (size_t)colour * G::BLK, ob = (size_t)s * G::NS + (size_t)(1 - colour) * G::BLK;
+  const double2 kx2 = ld2(Kx + cb + o), ky2 = ld2(Ky + cb + o), kz2 = ld2(Kz + cb + o);
+  const double2 di2 = ld2(Dinv + cb + o), g2 = ld2(g + cb + o);
+  const double* kxo = Kx + ob;
+  const double* uo = u + ob;
+  const double2 kxm2 = ld2(kxo + o), kym2 = ld2(Ky + ob + o - G::P), kzm2 = ld2(Kz + ob + o - G::NP);
+  const double2 um2 = ld2(uo + o), uym2 = ld2(uo + o - G::P), uyp2 = ld2(uo + o + G::P);
+  const double2 uzm2 = ld2(uo + o - G::NP), uzp2 = ld2(uo + o + G::NP);
+  // the other-colour slot beside the pair: left of node 0 (x parity 0) or right of node 1
+  double kext = 0.0, uext = 0.0;
+  if (par) {
+    uext = uo[o + 2];
+  } else if (x0 > 0) {
+    kext = kxo[o - 1];
+    uext = uo[o - 1];
+  }
+  double out[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    // lower x face at the x - 1 node: slot xi0 + i - 1 + par of the other colour
+    const double kl = par ? comp2(kxm2, i) : (i == 0 ? kext : comp2(kxm2, i - 1));
+    const double ul = par ? comp2(um2, i) : (i == 0 ? uext : comp2(um2, i - 1));
+    const double ur = par ? (i == 1 ? uext : comp2(um2, i + 1)) : comp2(um2, i);
+    double acc = comp2(g2, i);
+    acc = fma(kl, ul, acc);
+    acc = fma(comp2(kx2, i), ur, acc);
+    acc = fma(comp2(kym2, i), comp2(uym2, i), acc);
+    acc = fma(comp2(ky2, i), comp2(uyp2, i), acc);
+    acc = fma(comp2(kzm2, i), comp2(uzm2, i), acc);
+    acc = fma(comp2(kz2, i), comp2(uzp2, i), acc);
+    out[i] = acc * comp2(di2, i);
+  }
+  double* uc = u + cb + o;
+  if (x0 >= 1 && x0 + 2 <= G::n - 2) {
+    *reinterpret_cast<double2*>(uc) = make_double2(out[0], out[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      if (x0 + 2 * i >= 1 && x0 + 2 * i <= G::n - 2) uc[i] = out[i];
+  }
+}
+
+// r~ = g - D u + sum K u_q (k_residual_z's operations and order) at the interior nodes of
+// one colour, two per thread, into r in colour-split storage (interior nodes only).
+// Grid (two-slot groups of the interior rows of a plane, interior planes, 2 x samples:
+// colour = blockIdx.z & 1).
+template <int LG>
+__global__ void __launch_bounds__(128) k_residual_split64(const double* __restrict__ Kx, const double* __restrict__ Ky,
+                                                          const double* __restrict__ Kz, const double* __restrict__ D,
+                                                          const double* __restrict__ g, const double* __restrict__ u,
+                                                          double* __restrict__ r, const int* __restrict__ active) {
+  using G = SplitGeo<LG>;
+  constexpr int Q2 = G::P / 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= G::m * Q2) return;
+  const int s = blockIdx.z >> 1, colour = blockIdx.z & 1;
+  if (active && !active[s]) return;
+  const int yi = q / Q2, qi = q - yi * Q2, y = 1 + yi, z = 1 + (int)blockIdx.y;
+  const int par = (colour + y + z) & 1, xi0 = 2 * qi, x0 = 2 * xi0 + par;
+  if (x0 > G::n - 2) return;
+  const int o = (z * G::n + y) * G::P + xi0;
+  const size_t cb = (size_t)s * G::NS + (size_t)colour * G::BLK, ob = (size_t)s * G::NS + (size_t)(1 - colour) * G::BLK;
+  const double2 kx2 = ld2(Kx + cb + o), ky2 = ld2(Ky + cb + o), kz2 = ld2(Kz + cb + o);
+  const double2 d2 = ld2(D + cb + o), g2 = ld2(g + cb + o), up2 = ld2(u + cb + o);
+  const double* kxo = Kx + ob;
+  const double* uo = u + ob;
+  const double2 kxm2 = ld2(kxo + o), kym2 = ld2(Ky + ob + o - G::P), kzm2 = ld2(Kz + ob + o - G::NP);
+  const double2 um2 = ld2(uo + o), uym2 = ld2(uo + o - G::P), uyp2 = ld2(uo + o + G::P);
+  const double2 uzm2 = ld2(uo + o - G::NP), uzp2 = ld2(uo + o + G::NP);
+  double kext = 0.0, uext = 0.0;
+  if (par) {
+    uext = uo[o + 2];
+  } else if (x0 > 0) {
+    kext = kxo[o - 1];
+    uext = uo[o - 1];
+  }
+  double out[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double kl = par ? comp2(kxm2, i) : (i == 0 ? kext : comp2(kxm2, i - 1));
+    const double ul = par ? comp2(um2, i) : (i == 0 ? uext : comp2(um2, i - 1));
+    const double ur = par ? (i == 1 ? uext : comp2(um2, i + 1)) : comp2(um2, i);
+    double rr = fma(-comp2(d2, i), comp2(up2, i), comp2(g2, i));
+    rr = fma(kl, ul, rr);
+    rr = fma(comp2(kx2, i), ur, rr);
+    rr = fma(comp2(kym2, i), comp2(uym2, i), rr);
+    rr = fma(comp2(ky2, i), comp2(uyp2, i), rr);
+    rr = fma(comp2(kzm2, i), comp2(uzm2, i), rr);
+    rr = fma(comp2(kz2, i), comp2(uzp2, i), rr);
+    out[i] = rr;
+  }
+  double* rc = r + cb + o;
+  if (x0 >= 1 && x0 + 2 <= G::n - 2) {
+    *reinterpret_cast<double2*>(rc) = make_double2(out[0], out[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      if (x0 + 2 * i >= 1 && x0 + 2 * i <= G::n - 2) rc[i] = out[i];
+  }
+}
+
+// u_f += trilinear interpolation of e_c on colour-split FP64 storage of both grids
+// (k_prolong's order and weights), two fine nodes of one colour per thread, 16-byte
+// update of u. Grid as k_rbgs_split64's with 2 x samples (colour = blockIdx.z & 1).
+template <int LG>
+__global__ void __launch_bounds__(128) k_prolong_split64(const double* __restrict__ ec, double* __restrict__ u,
+                                                         const int* __restrict__ active) {
+  using F = SplitGeo<LG>;
+  using C = SplitGeo<LG - 1>;
+  constexpr int Q2 = F::P / 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= F::m * Q2) return;
+  const int s = blockIdx.z >> 1, colour = blockIdx.z & 1;
+  if (active && !active[s]) return;
+  const int yi = q / Q2, qi = q - yi * Q2, y = 1 + yi, z = 1 + (int)blockIdx.y;
+  const int xo = (colour + y + z) & 1, xi0 = 2 * qi, x0 = 2 * xi0 + xo;
+  if (x0 > F::n - 2) return;
+  const int yo = y & 1, zo = z & 1, Y = y >> 1, Z = z >> 1;
+  const double* e = ec + (size_t)s * C::NS;
+  // coarse row (Y + b, Z + c) at X = xi0 + t, t = 0 .. 2 (xi0 even: colour (t + Y + b + Z + c) & 1,
+  // slot xi0 / 2 + t / 2)
+  auto row = [&](int b, int c, double* cv) {
+    const int cy = Y + b, cz = Z + c, base = (cz * C::n + cy) * C::P + (xi0 >> 1);
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+      if (t < 2 || xo) cv[t] = e[(size_t)((t + cy + cz) & 1) * C::BLK + (size_t)(base + (t >> 1))];
+  };
+  double r00[3], r10[3], r01[3], r11[3];
+  row(0, 0, r00);
+  if (yo) row(1, 0, r10);
+  if (zo) {
+    row(0, 1, r01);
+    if (yo) row(1, 1, r11);
+  }
+  const double w = xo + yo + zo == 0 ? 1.0 : xo + yo + zo == 1 ? 0.5 : xo + yo + zo == 2 ? 0.25 : 0.125;
+  double* uc = u + (size_t)s * F::NS + (size_t)colour * F::BLK + (size_t)((z * F::n + y) * F::P + xi0);
+  const double2 u2 = ld2(uc);
+  double out[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    double v = 0.0;
+    v += r00[i];
+    if (xo) v += r00[i + 1];
+    if (yo) {
+      v += r10[i];
+      if (xo) v += r10[i + 1];
+    }
+    if (zo) {
+      v += r01[i];
+      if (xo) v += r01[i + 1];
+      if (yo) {
+        v += r11[i];
+        if (xo) v += r11[i + 1];
+      }
+    }
+    out[i] = comp2(u2, i) + w * v;
+  }
+  if (x0 >= 1 && x0 + 2 <= F::n - 2) {
+    *reinterpret_cast<double2*>(uc) = make_double2(out[0], out[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
       if (x0 + 2 * i >= 1 && x0 + 2 * i <= F::n - 2) uc[i] = out[i];
   }
 }
@@ -1172,6 +1431,48 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// The convergence residual of an FP64 colour-split grid: k_residual_z's column z-march,
+// launch shape and partition (partials of r~^2 per (column block, slab)), reading the
+// split storage; nothing stored. Grid (column blocks, z-slabs, samples), 128 threads.
+__global__ void __launch_bounds__(128)
+    k_residual_norm_split(int n, int zslab, const double* __restrict__ Kx, const double* __restrict__ Ky,
+                          const double* __restrict__ Kz, const double* __restrict__ D, const double* __restrict__ g,
+                          const double* __restrict__ u, double* __restrict__ partial, const int* __restrict__ active) {
+  const int s = blockIdx.z;
+  if (active && !active[s]) return;
+  const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
+  const int c = blockIdx.x * 128 + threadIdx.x;
+  const int zlo = 1 + blockIdx.y * zslab, zhi = min(n - 2, zlo + zslab - 1);
+  const size_t base = (size_t)s * split_elems(n);
+  double sq = 0.0;
+  if (c < n * n) {
+    const int y = c / n, x = c - y * n;
+    if (x > 0 && y > 0 && x < n - 1 && y < n - 1) {
+      auto at = [&](int xx, int yy, int zz) -> size_t { return base + split_index(n, xx, yy, zz); };
+      double um = u[at(x, y, zlo - 1)], uc = u[at(x, y, zlo)];
+      double kzm = Kz[at(x, y, zlo - 1)];
+      for (int z = zlo; z <= zhi; ++z) {
+        const size_t t = at(x, y, z);
+        const double up = u[at(x, y, z + 1)];
+        const double kzp = Kz[t];
+        double rr = fma(-D[t], uc, g[t]);
+        rr = fma(Kx[at(x - 1, y, z)], u[at(x - 1, y, z)], rr);
+        rr = fma(Kx[t], u[at(x + 1, y, z)], rr);
+        rr = fma(Ky[at(x, y - 1, z)], u[at(x, y - 1, z)], rr);
+        rr = fma(Ky[t], u[at(x, y + 1, z)], rr);
+        rr = fma(kzm, um, rr);
+        rr = fma(kzp, up, rr);
+        sq += (double)rr * (double)rr;
+        um = uc;
+        uc = up;
+        kzm = kzp;
+      }
+    }
+  }
+  const double bs = block_sum<128>(sq);
+  if (threadIdx.x == 0) partial[(size_t)s * nb + b] = bs;
+}
+
 inline dim3 zmarch_grid(int n, int B, int* zslab) {
   const int slabs = apply_slabs(n, zslab);
   return dim3((unsigned)((n * n + 127) / 128), (unsigned)slabs, (unsigned)B);
@@ -1357,18 +1658,19 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed, bool cg) {
     v.n = nl;
     v.n3 = cube(nl);
     const size_t e = (size_t)B * v.n3;
-    v.Kx = c.template take<T>(e);
-    v.Ky = c.template take<T>(e);
-    v.Kz = c.template take<T>(e);
-    v.D = c.template take<T>(e);
-    v.Dinv = c.template take<T>(e);
+    // every per-level array has room for the colour-split storage (2 n^2 P instead of n^3
+    // elements per sample, P = (n + 1) / 2 rounded up to a multiple of 4)
+    const size_t es = (size_t)B * split_elems(nl);
+    v.Kx = c.template take<T>(es);
+    v.Ky = c.template take<T>(es);
+    v.Kz = c.template take<T>(es);
+    v.D = c.template take<T>(es);
+    v.Dinv = c.template take<T>(es);
     // level 0 of an FP64 solve iterates in a copy of the caller's u (so that every array
-    // the smoothers stage is carved here, with slack behind it)
-    // FP32 (mixed) grids hold u, g and 1/k in room for the colour-split storage too
-    // (n^2 (n + 1) instead of n^3 elements per sample)
-    const size_t es = mixed ? (size_t)B * split_elems(nl) : e;
+    // the smoothers stage is carved here, with slack behind it); its g is g64 (or R for CG),
+    // or the colour-split copy of g64 (MLMC_SMOOTH_SPLIT)
     v.u = c.template take<T>(es);
-    if (j > 0 || mixed) v.g = c.template take<T>(es);  // FP64: the level-0 rhs is g64 (or R for CG)
+    v.g = c.template take<T>(es);
     if (j < H.L - 1) v.u2 = c.template take<T>(e);
     if (j < H.L - 1) v.r = c.template take<T>(es);
     if (mixed && j < H.L - 1) v.kn = c.template take<T>(es);
@@ -1474,6 +1776,50 @@ void vcycle_split(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   smooth(nu2);
 }
 
+// One level of the V-cycle on colour-split FP64 storage (stored faces): two-pass colour
+// sweeps, the residual into split r, full weighting into the coarse split g, the coarser
+// levels, the trilinear correction on split storage, post-smoothing.
+template <typename T>
+void vcycle_split64(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
+  Level<T>& v = H.lv[j];
+  Level<T>& w = H.lv[j + 1];
+  const int* act = H.active;
+  const int B = H.B, m = v.n - 2;
+  const double Ba = (double)H.n_act, W = 8.0;
+  const double* Kx = (const double*)(const void*)v.Kx;
+  const double* Ky = (const double*)(const void*)v.Ky;
+  const double* Kz = (const double*)(const void*)v.Kz;
+  const double* D = (const double*)(const void*)v.D;
+  const double* Dinv = (const double*)(const void*)v.Dinv;
+  const double* g = (const double*)(const void*)v.g;
+  double* u = (double*)(void*)v.u;
+  double* r = (double*)(void*)v.r;
+  const unsigned pairs = (unsigned)((m * (split_pitch(v.n) / 2) + 127) / 128);
+  auto smooth = [&](int sweeps) {
+    for (int s = 0; s < sweeps; ++s)
+      for (int c = 0; c < 2; ++c)
+        MLMC_LAUNCH(prof::sized("rbgs_split_f64", v.n), Ba * interior(v.n) * 3.5 * W, Ba * interior(v.n) * 0.5 * 13.0,
+                    st, MLMC_SPLIT_DISPATCH(v.n, (k_rbgs_split64<LG><<<dim3(pairs, (unsigned)m, (unsigned)B), 128, 0,
+                                                                         st>>>(c, Kx, Ky, Kz, Dinv, g, u, act))));
+  };
+  smooth(nu1);
+  MLMC_LAUNCH(prof::sized("residual_split_f64", v.n), Ba * interior(v.n) * 7.0 * W, Ba * interior(v.n) * 14.0, st,
+              MLMC_SPLIT_DISPATCH(v.n, (k_residual_split64<LG><<<dim3(pairs, (unsigned)m, (unsigned)(2 * B)), 128, 0,
+                                                                  st>>>(Kx, Ky, Kz, D, g, u, r, act))));
+  MLMC_LAUNCH(Names<T>::restrict_, Ba * ((double)v.n3 + (double)w.n3) * W, Ba * interior(w.n) * 54.0, st,
+              MLMC_SPLIT_DISPATCH(v.n, (k_restrict_split<LG, double><<<dim3((unsigned)(((w.n - 2) * (w.n - 2) + 127) /
+                                                                                    128),
+                                                                            (unsigned)(w.n - 2), (unsigned)B), 128,
+                                                                       0, st>>>(r, (double*)(void*)w.g, act))));
+  cudaMemsetAsync(w.u, 0, (size_t)B * split_elems(w.n) * sizeof(T), st);
+  vcycle(H, j + 1, nu1, nu2, st);
+  MLMC_LAUNCH(prof::sized("prolong_split_f64", v.n), Ba * (2.0 * (double)v.n3 + (double)w.n3) * W,
+              Ba * interior(v.n) * 4.375, st,
+              MLMC_SPLIT_DISPATCH(v.n, (k_prolong_split64<LG><<<dim3(pairs, (unsigned)m, (unsigned)(2 * B)), 128, 0,
+                                                                 st>>>((const double*)(const void*)w.u, u, act))));
+  smooth(nu2);
+}
+
 template <typename T>
 void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   Level<T>& v = H.lv[j];
@@ -1492,11 +1838,12 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
                   (k_coarse_apply<T><<<(B * 27 + 127) / 128, 128, 0, st>>>(B, H.Ainv, v.g, v.u, act)));
     return;
   }
-  if constexpr (sizeof(T) == 4) {
-    if (H.split) {
+  if (H.split) {
+    if constexpr (sizeof(T) == 4)
       vcycle_split(H, j, nu1, nu2, st);
-      return;
-    }
+    else
+      vcycle_split64(H, j, nu1, nu2, st);
+    return;
   }
   const int m = v.n - 2;
   const dim3 gs = plane_grid(m * ((v.n - 1) / 2), (long long)B * m);
@@ -2226,7 +2573,10 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   {
     int sm0 = a.cfg.smoother;
     resolve_tuning(a.n, a.cfg.precision, &sm0, &nu1, &nu2);
-    H.split = !use_cta && mixed && a.cfg.disc == MLMC_DISC_FV && sm0 == MLMC_SMOOTH_SPLIT;
+    // FP32 correction cycles (mixed) or FP64 stationary cycles
+    // (the split kernels are instantiated for n = 5 .. 1025)
+    H.split = !use_cta && a.cfg.disc == MLMC_DISC_FV && sm0 == MLMC_SMOOTH_SPLIT && a.n <= 1025 &&
+              (mixed || (!cg && !fmg));
   }
   // operators of every level (k injected from k0); colour-split grids need no faces
   // except on the coarsest grid (its dense solve)
@@ -2237,6 +2587,17 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     if (H.split) {
       if (j > 0) MLMC_CUDA_TRY(cudaMemsetAsync(v.g, 0, (size_t)B * split_elems(v.n) * sizeof(T), st));
       if (j < H.L - 1) {
+        if constexpr (sizeof(T) == 8) {
+          // FP64: stored faces, D and 1/D in the split storage (the coarsest grid keeps the
+          // plain faces its dense factorisation reads)
+          MLMC_LAUNCH(Names<T>::faces, B * (double)v.n3 * (8.0 + 3 * W), B * (double)v.n3 * 12.0, st,
+                      (k_faces_split<<<gb, kPlaneThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, (double*)v.Kx,
+                                                                    (double*)v.Ky, (double*)v.Kz)));
+          MLMC_LAUNCH(Names<T>::diag, B * (double)v.n3 * 5 * W, B * (double)v.n3 * 6.0, st,
+                      (k_diag_split<<<gb, kPlaneThreads, 0, st>>>(v.n, B, (const double*)v.Kx, (const double*)v.Ky,
+                                                                   (const double*)v.Kz, (double*)v.D,
+                                                                   (double*)v.Dinv)));
+        }
         stride *= 2;
         continue;
       }
@@ -2258,7 +2619,7 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     Level<T>& v = H.lv[j];
     if (H.split) {
       H.nodal[j] = H.fused[j] = false;
-      if (j < H.L - 1)
+      if (mixed && j < H.L - 1)
         MLMC_LAUNCH("nodal_k", B * (double)v.n3 * (8.0 + W), 0.0, st,
                     (k_nodal_k_split<<<plane_grid(v.n * v.n, (long long)B * v.n), kPlaneThreads, 0, st>>>(
                         a.k0, a.n_k0, a.st0 << j, v.n, B, (float*)(void*)v.kn)));
@@ -2316,7 +2677,14 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   MLMC_LAUNCH("prepare", B * (double)l0.n3 * (a.f ? 16.0 : 8.0), B * (double)l0.n3, st,
               (k_prepare<<<plane_grid(a.n * a.n, (long long)B * a.n), kPlaneThreads, 0, st>>>(a.n, B, h * h, a.f,
                                                                                              H.g64, a.u)));
-  if (!mixed && !cg) {
+  if (!mixed && !cg && H.split) {
+    // colour-split copies of g = h^2 f and of the initial guess; copied back at the end
+    const dim3 pg0 = plane_grid(a.n * a.n, (long long)B * a.n);
+    MLMC_LAUNCH("split_copy", B * (double)l0.n3 * 16.0, 0.0, st,
+                (k_split_copy<double, true><<<pg0, kPlaneThreads, 0, st>>>(a.n, B, H.g64, (double*)(void*)l0.g)));
+    MLMC_LAUNCH("split_copy", B * (double)l0.n3 * 16.0, 0.0, st,
+                (k_split_copy<double, true><<<pg0, kPlaneThreads, 0, st>>>(a.n, B, a.u, (double*)(void*)l0.u)));
+  } else if (!mixed && !cg) {
     l0.g = (T*)H.g64;
     // iterate in the workspace copy; copied back after the last cycle
     MLMC_CUDA_TRY(cudaMemcpyAsync(l0.u, a.u, (size_t)B * l0.n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -2353,6 +2721,12 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
                   (k_residual_z<double, double, double, T><<<rz, 128, 0, st>>>(a.n, zs, H.K64x, H.K64y, H.K64z, H.D64,
                                                                                H.g64, a.u, l0.g, H.partial,
                                                                                H.active)));
+    } else if (H.split) {
+      MLMC_LAUNCH("residual_norm_f64", Ba * interior(a.n) * 6.0 * 8, Ba * interior(a.n) * 16.0, st,
+                  (k_residual_norm_split<<<rz, 128, 0, st>>>(a.n, zs, (const double*)l0.Kx, (const double*)l0.Ky,
+                                                             (const double*)l0.Kz, (const double*)l0.D,
+                                                             (const double*)l0.g, (const double*)l0.u, H.partial,
+                                                             H.active)));
     } else {
       MLMC_LAUNCH("residual_norm_f64", Ba * interior(a.n) * 6.0 * 8, Ba * interior(a.n) * 16.0, st,
                   (k_residual_z<T, T, T, T><<<rz, 128, 0, st>>>(a.n, zs, l0.Kx, l0.Ky, l0.Kz, l0.D, l0.g, l0.u,
@@ -2485,7 +2859,11 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   }
   // FP64 solves iterate in place on the caller's u; the fused smoother may leave the
   // latest iterate in the spare buffer
-  if (!mixed && !cg)
+  if (!mixed && !cg && H.split)
+    MLMC_LAUNCH("split_copy", B * (double)l0.n3 * 16.0, 0.0, st,
+                (k_split_copy<double, false><<<plane_grid(a.n * a.n, (long long)B * a.n), kPlaneThreads, 0, st>>>(
+                    a.n, B, (const double*)(const void*)H.lv[0].u, a.u)));
+  else if (!mixed && !cg)
     MLMC_CUDA_TRY(cudaMemcpyAsync(a.u, H.lv[0].u, (size_t)B * l0.n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   MLMC_CUDA_TRY(cudaGetLastError());
   if (cycles_dev)

@@ -323,6 +323,7 @@ GRAPH_CASES = [(mg.MLMC_PREC_F64, mg.MLMC_ACCEL_NONE, mg.MLMC_SMOOTH_TWO_PASS),
                (mg.MLMC_PREC_MIXED, mg.MLMC_ACCEL_CG, mg.MLMC_SMOOTH_NODAL),
                (mg.MLMC_PREC_MIXED, mg.MLMC_ACCEL_CG, mg.MLMC_SMOOTH_SPLIT),
                (mg.MLMC_PREC_MIXED, mg.MLMC_ACCEL_NONE, mg.MLMC_SMOOTH_SPLIT),
+               (mg.MLMC_PREC_F64, mg.MLMC_ACCEL_NONE, mg.MLMC_SMOOTH_SPLIT),
                (mg.MLMC_PREC_F64, mg.MLMC_ACCEL_CG, mg.MLMC_SMOOTH_TWO_PASS)]
 
 
@@ -390,6 +391,61 @@ def test_split_storage_equals_nodal_sweep_bitwise(orc, accel, n):
     a, b = out[mg.MLMC_SMOOTH_NODAL], out[mg.MLMC_SMOOTH_SPLIT]
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
     assert np.array_equal(a[0], b[0])
+
+
+@pytest.mark.parametrize("n", [9, 17, 33, 65, 129])
+def test_split_storage_fp64_equals_two_pass_bitwise(orc, n):
+    """FP64 stationary cycles with MLMC_SMOOTH_SPLIT: stored faces, D, 1/D, u, g and r in
+    colour-split storage, the two-pass sweep's, residual's and transfers' operations in
+    their order, the convergence residual on the same partition. Iterates, cycle counts
+    and residuals equal MLMC_SMOOTH_TWO_PASS's bit for bit, samples stopping at different
+    cycles, with and without a right-hand side."""
+    B = 4 if n < 65 else 2
+    ks = [orc.field(RUN_SEED, int(i), 256, 1.0 + 0.5 * s, 0.15, n) for s, i in enumerate(sample_ids(4, 0, B))]
+    k = to_dev(np.stack(ks))
+    f = to_dev(np.stack([random_rhs(n, 700 + s) for s in range(B)]))
+    for rhs in (None, f):
+        out = {}
+        for sm in (mg.MLMC_SMOOTH_TWO_PASS, mg.MLMC_SMOOTH_SPLIT):
+            u = torch.zeros_like(k)
+            cfg = mg.mg_cfg(2, 2, 1e-10, 200, mg.MLMC_PREC_F64, sm, engine=mg.MLMC_ENGINE_BATCHED)
+            cyc, rel, st = mg.mg_solve_batch(cfg, k, u, rhs)
+            assert st == 0
+            out[sm] = (u.cpu().numpy(), cyc, rel)
+        a, b = out[mg.MLMC_SMOOTH_TWO_PASS], out[mg.MLMC_SMOOTH_SPLIT]
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+        assert np.array_equal(a[0], b[0])
+        if rhs is None and n >= 17:
+            assert len(set(a[1].tolist())) > 1  # masking was exercised
+
+
+def test_split_storage_fp64_fixed_cycles_from_a_nonzero_guess(orc):
+    """The initial guess enters the split storage and the result leaves it: three fixed
+    cycles from a random interior guess equal the two-pass iterate bit for bit."""
+    n, B = 65, 3
+    k = to_dev(np.stack([random_coefficient(n, 800 + s, 1.0) for s in range(B)]))
+    rng = np.random.default_rng(5)
+    u0 = np.zeros((B, n, n, n))
+    u0[:, 1:-1, 1:-1, 1:-1] = rng.standard_normal((B, n - 2, n - 2, n - 2))
+    res = []
+    for sm in (mg.MLMC_SMOOTH_TWO_PASS, mg.MLMC_SMOOTH_SPLIT):
+        u = to_dev(u0)
+        cyc, rel, st = mg.mg_solve_batch(mg.mg_cfg(2, 2, 0.0, 3, mg.MLMC_PREC_F64, sm,
+                                                   engine=mg.MLMC_ENGINE_BATCHED), k, u)
+        res.append((u.cpu().numpy(), rel))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert not np.array_equal(res[0][0], u0)
+
+
+def test_split_storage_fp64_level_estimate_matches_oracle(orc):
+    level, ids = 2, sample_ids(2, 30, 3)
+    cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.2, 256, n0=17, rtol=1e-11, smoother=mg.MLMC_SMOOTH_SPLIT,
+                           engine=mg.MLMC_ENGINE_BATCHED)
+    _, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
+    Y64, Qf64, Qc64, *_ = orc.level_batch(orc.make_cfg(RUN_SEED, 1.0, 0.2, 256, rtol=1e-11), 65, 33, ids)
+    scale = np.max(np.abs(Qf64))
+    assert np.max(np.abs(Y - Y64)) <= 1e-9 * scale
+    assert np.max(np.abs(Qf - Qf64)) <= 1e-9 * scale
 
 
 def test_split_storage_level_estimate_matches_oracle(orc):
@@ -486,3 +542,15 @@ def test_autotune_records_choice():
                             precision=mg.MLMC_PREC_MIXED, smoother=best_sm)
     s_exp, Ye, _, _ = mg.mlmc_level_estimate(cfg2, 1, int(sample_ids(1, 0, 1)[0]), 8)
     assert s_auto.mean_cycles_fine == s_exp.mean_cycles_fine
+
+
+def test_autotune_fp64_candidates():
+    """FP64 stationary cycles on finite volumes: 8 candidates (the colour-split stored-face
+    sweep, no nodal-coefficient sweep); with CG: 7."""
+    for accel, count in ((mg.MLMC_ACCEL_NONE, 8), (mg.MLMC_ACCEL_CG, 7)):
+        cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.3, 64, n0=9, nu1=2, nu2=2, rtol=1e-10, accel=accel)
+        rows, best_sm, best_nu = mg.mlmc_autotune(cfg, 1, int(sample_ids(1, 950, 1)[0]), 8)
+        assert len(rows) == count and best_nu == 2
+        sms = [r["smoother"] for r in rows]
+        assert "nodal" not in sms
+        assert ("split" in sms) == (accel == mg.MLMC_ACCEL_NONE)

@@ -1,11 +1,11 @@
-"""Host runs of the colour-split FP32 kernels (MLMC_SMOOTH_SPLIT) against their
-plain-layout counterparts, no GPU: the kernels' own text compiled with g++, the launch a
-loop over every block and thread. The split storage map is computed here from its
+"""Host runs of the colour-split kernels (MLMC_SMOOTH_SPLIT; FP32 nodal coefficient and
+FP64 stored faces) against their plain-layout counterparts, no GPU: the kernels' own text
+compiled with g++, the launch a loop over every block and thread. The split storage map is computed here from its
 definition (per sample, colour c = (x + y + z) % 2 block of n x n rows of (n + 1) / 2
 slots rounded up to a multiple of 4, node x at slot x // 2); slots that hold no node are NaN, so a kernel that read one
-would poison its result. A red and a black pass, the nodal residual, the trilinear
-correction, full weighting into split coarse storage and the reciprocal coefficient must
-equal the plain kernels bit for bit."""
+would poison its result. A red and a black pass, the residual, the trilinear correction,
+full weighting into split coarse storage and the operator set-up (reciprocal coefficient;
+faces, D and 1/D) must equal the plain kernels bit for bit."""
 import os
 import shutil
 import subprocess
@@ -29,6 +29,7 @@ def _host(text):
     text = text.replace("__host__ __device__ __forceinline__", "static inline")
     text = text.replace("__device__ __forceinline__", "static inline").replace("__device__", "static")
     text = text.replace("__global__", "static").replace("__restrict__", "")
+    text = text.replace("template <>\nstatic inline", "template <>\ninline")  # no storage class on a specialisation
     while "__launch_bounds__(" in text:
         i = text.index("__launch_bounds__(")
         j, depth = i + len("__launch_bounds__("), 1
@@ -66,7 +67,10 @@ def emu(tmp_path_factory):
     parts = [
         "namespace mlmc {",
         _cut(mgcu, "__host__ __device__ __forceinline__ int split_pitch(int n)", "// Carves 256-byte"),
-        _cut(mgcu, "template <typename T>\n__global__ void k_nodal_k(", "template <int THREADS>"),
+        _cut(mgcu, "// x in the arithmetic type TD", "// Dense 27x27 scaled operator"),
+        _cut(mgcu, "// One colour of a red-black sweep: threads enumerate", "// Reciprocal nodal coefficient rho"),
+        _cut(mgcu, "template <typename T>\n__global__ void k_nodal_k(", "// Blocks per sample of the deterministic"),
+        _cut(mgcu, "// r~ = g - D u + sum K u_q on interior nodes (0 on the boundary)", "inline dim3 zmarch_grid"),
         _cut(mgcu, "template <typename T, bool SPLIT_OUT = false>\n__global__ void k_restrict(", "// g = h^2 f (f == NULL"),
         "}  // namespace mlmc",
     ]
@@ -120,3 +124,43 @@ def test_split_kernels_equal_plain_kernels_bitwise(emu, n, B):
         assert np.array_equal(plain.view(np.uint32), split.view(np.uint32)), name
     # the sweep changed the interior (the comparison is not of untouched arrays)
     assert not np.array_equal(parts[0].reshape(B, n, n, n), u)
+
+
+@pytest.mark.parametrize("n,B", [(5, 2), (9, 2), (17, 3), (33, 2)])
+def test_split64_kernels_equal_plain_kernels_bitwise(emu, n, B):
+    exe, d = emu
+    nc = (n + 1) // 2
+    rng = np.random.default_rng(100 + n)
+    k = np.stack([random_coefficient(n, 30 * n + s, 1.0) for s in range(B)])
+    g = np.stack([random_rhs(n, 40 * n + s) for s in range(B)]) * 1e-3
+    g[:, [0, -1], :, :] = 0.0
+    g[:, :, [0, -1], :] = 0.0
+    g[:, :, :, [0, -1]] = 0.0
+    u = np.zeros((B, n, n, n))
+    u[:, 1:-1, 1:-1, 1:-1] = rng.standard_normal((B, n - 2, n - 2, n - 2))
+    ec = np.zeros((B, nc, nc, nc))
+    ec[:, 1:-1, 1:-1, 1:-1] = rng.standard_normal((B, nc - 2, nc - 2, nc - 2))
+    r = np.zeros((B, n, n, n))
+    r[:, 1:-1, 1:-1, 1:-1] = rng.standard_normal((B, n - 2, n - 2, n - 2))
+    src, pm, dst = d / ("in64_%d.bin" % n), d / ("perm64_%d.bin" % n), d / ("out64_%d.bin" % n)
+    with open(src, "wb") as fh:
+        for a in (k, g, u, ec, r):
+            fh.write(np.ascontiguousarray(a, dtype=np.float64).tobytes())
+    with open(pm, "wb") as fh:
+        fh.write(split_perm(n, B).tobytes())
+        fh.write(split_perm(nc, B).tobytes())
+    subprocess.run([exe, "split64", str(n), str(B), str(src), str(pm), str(dst)], check=True)
+    out = np.fromfile(dst, dtype=np.float64)
+    n3, nc3 = B * n ** 3, B * nc ** 3
+    names = ["Kx", "Ky", "Kz", "D", "1/D", "sweep", "residual", "prolongation", "restriction", "copies"]
+    sizes = [nc3 if name == "restriction" else n3 for name in names]
+    off, got = 0, {}
+    for name, sz in zip(names, sizes):
+        got[name] = (out[off:off + sz], out[off + sz:off + 2 * sz])
+        off += 2 * sz
+    assert off == out.size
+    for name in names:
+        plain, split = got[name]
+        assert np.all(np.isfinite(plain)), name
+        assert np.array_equal(plain.view(np.uint64), split.view(np.uint64)), name
+    assert not np.array_equal(got["sweep"][0].reshape(B, n, n, n), u)
