@@ -55,6 +55,9 @@ NCU_TRAFFIC = {
     "rbgs_split_f32": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs_split", "kernel_sha": "9d3393d2d0414e4e",
                        "dram_bytes_per_unit": (281.681e6 + 55.126e6) / (2 * 255 ** 3), "unit_bytes": 2.0 * 4,
                        "source": "profiles/rbgs_split_f32_n257_b2.md (257^3 x 2, one colour pass)"},
+    "rbgs_split_f64": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs_split64", "kernel_sha": "771506262551874d",
+                       "dram_bytes_per_unit": (636.264e6 + 59.780e6) / (8 * 127 ** 3), "unit_bytes": 3.5 * 8,
+                       "source": "profiles/rbgs_split_f64_n129_b8.md (129^3 x 8, one colour pass)"},
     "rbgs_nodal_f32": {"file": "paper_1607_03252_gb300/csrc/mg.cu", "kernel": "k_rbgs_nodal", "kernel_sha": "cb8a0fa77df739fc",
                        "dram_bytes_per_unit": (405.356e6 + 107.601e6) / (2 * 255 ** 3), "unit_bytes": 2.0 * 4,
                        "source": "profiles/rbgs_nodal_f32_n257_b2.md (257^3 x 2, one colour pass)"},
@@ -599,7 +602,9 @@ def roofline(prof, peaks, keep=None):
            tot[top] / max(sum(v["ms"] for v in prof.values()), 1e-30), "avg_launch_ms": avg_s * 1e3,
            "launches": rec["launches"], "traffic": traffic, "traffic_source": tsrc,
            "dram_gbs_from_traffic": traffic / avg_s / 1e9 if traffic else None}
-    if base.startswith("rbgs") and not base.startswith("rbgs_nodal") and per_launch_flops > 0:
+    # (the nodal-coefficient sweeps, plain or colour-split FP32, account 4 words already)
+    nodal = base.startswith("rbgs_nodal") or base == "rbgs_split_f32"
+    if base.startswith("rbgs") and not nodal and per_launch_flops > 0:
         # the same work at the nodal-coefficient floor of 4 words per node and sweep: a
         # colour pass (6.5 flops per updated node) updates half the nodes and moves 2 words
         # per node, i.e. 4 per updated node; a fused sweep (13 flops per node) 4 per node

@@ -250,7 +250,7 @@ int mg_solve_batch(const mg_cfg* cfg, int batch, int n, const double* k, const d
  * The workspace is a fixed 32 MiB array in the library's device image (every GPU that
  * loads the library keeps it until the process exits); the call makes no cudaMalloc,
  * cudaMallocAsync or cudaFree and no torch allocation. Sizes whose workspace exceeds
- * 32 MiB (about 75 samples at 17^3, 11 at 33^3, 1 at 65^3 in FP64) return
+ * 32 MiB (about 50 samples at 17^3, 8 at 33^3, 1 at 65^3 in FP64) return
  * MLMC_ERR_INVALID with the required size in mlmc_last_error_string().
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * once for that device and keeps it for the life of the process (not refreshed after

@@ -157,31 +157,51 @@ struct LevelRecord {
   double N, sum, comp, mean, M2, cyc_f, cyc_c, max_cyc;
 };
 
-// Y = Qf - Qc (Qc NULL: level 0) for b samples, folded into *rec in order.
+// Y = Qf - Qc (Qc NULL: level 0) for b samples, folded into *rec in order. One warp: the
+// lanes load (and store Y for) 32 samples at a time, lane 0 folds them in order, so that
+// the loads of a chunk overlap instead of sitting on the fold's dependency chain.
 __global__ void k_level_stats(const double* __restrict__ Qf, const double* __restrict__ Qc,
                               const int* __restrict__ cf, const int* __restrict__ cc, int b, double* __restrict__ Y,
                               LevelRecord* __restrict__ rec) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  LevelRecord r = *rec;
-  for (int i = 0; i < b; ++i) {
-    const double y = Qc ? Qf[i] - Qc[i] : Qf[i];
-    if (Y) Y[i] = y;
-    const double yk = y - r.comp;
-    const double tk = r.sum + yk;
-    r.comp = (tk - r.sum) - yk;
-    r.sum = tk;
-    r.N += 1.0;
-    const double d = y - r.mean;
-    r.mean += d / r.N;
-    r.M2 += d * (y - r.mean);
-    r.cyc_f += cf[i];
-    r.max_cyc = fmax(r.max_cyc, (double)cf[i]);
-    if (cc) {
-      r.cyc_c += cc[i];
-      r.max_cyc = fmax(r.max_cyc, (double)cc[i]);
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  __shared__ double ys[32];
+  __shared__ int cfs[32], ccs[32];
+  const int lane = threadIdx.x;
+  LevelRecord r{};
+  if (lane == 0) r = *rec;
+  for (int i0 = 0; i0 < b; i0 += 32) {
+    const int i = i0 + lane;
+    if (i < b) {
+      const double y = Qc ? Qf[i] - Qc[i] : Qf[i];
+      if (Y) Y[i] = y;
+      ys[lane] = y;
+      cfs[lane] = cf[i];
+      ccs[lane] = cc ? cc[i] : 0;
     }
+    __syncwarp();
+    if (lane == 0) {
+      const int cnt = b - i0 < 32 ? b - i0 : 32;
+      for (int j = 0; j < cnt; ++j) {
+        const double y = ys[j];
+        const double yk = y - r.comp;
+        const double tk = r.sum + yk;
+        r.comp = (tk - r.sum) - yk;
+        r.sum = tk;
+        r.N += 1.0;
+        const double d = y - r.mean;
+        r.mean += d / r.N;
+        r.M2 += d * (y - r.mean);
+        r.cyc_f += cfs[j];
+        r.max_cyc = fmax(r.max_cyc, (double)cfs[j]);
+        if (cc) {
+          r.cyc_c += ccs[j];
+          r.max_cyc = fmax(r.max_cyc, (double)ccs[j]);
+        }
+      }
+    }
+    __syncwarp();
   }
-  *rec = r;
+  if (lane == 0) *rec = r;
 }
 
 // One batch of an MLMC level: field on the fine grid, fine solve, coarse solve on the

@@ -1658,21 +1658,24 @@ void layout(Hier<T>& H, Carver& c, int B, int n, bool mixed, bool cg) {
     v.n = nl;
     v.n3 = cube(nl);
     const size_t e = (size_t)B * v.n3;
-    // every per-level array has room for the colour-split storage (2 n^2 P instead of n^3
-    // elements per sample, P = (n + 1) / 2 rounded up to a multiple of 4)
+    // room for the colour-split storage (2 n^2 P instead of n^3 elements per sample, P =
+    // (n + 1) / 2 rounded up to a multiple of 4) where a solve may take it: u, g, r and 1/k
+    // of FP32 correction cycles; every array of FP64 stationary cycles (not of CG)
+    const bool split64 = !mixed && !cg;
     const size_t es = (size_t)B * split_elems(nl);
-    v.Kx = c.template take<T>(es);
-    v.Ky = c.template take<T>(es);
-    v.Kz = c.template take<T>(es);
-    v.D = c.template take<T>(es);
-    v.Dinv = c.template take<T>(es);
+    const size_t ef = split64 ? es : e, eu = (mixed || split64) ? es : e;
+    v.Kx = c.template take<T>(ef);
+    v.Ky = c.template take<T>(ef);
+    v.Kz = c.template take<T>(ef);
+    v.D = c.template take<T>(ef);
+    v.Dinv = c.template take<T>(ef);
     // level 0 of an FP64 solve iterates in a copy of the caller's u (so that every array
     // the smoothers stage is carved here, with slack behind it); its g is g64 (or R for CG),
     // or the colour-split copy of g64 (MLMC_SMOOTH_SPLIT)
-    v.u = c.template take<T>(es);
-    v.g = c.template take<T>(es);
+    v.u = c.template take<T>(eu);
+    if (j > 0 || mixed || split64) v.g = c.template take<T>(eu);
     if (j < H.L - 1) v.u2 = c.template take<T>(e);
-    if (j < H.L - 1) v.r = c.template take<T>(es);
+    if (j < H.L - 1) v.r = c.template take<T>(eu);
     if (mixed && j < H.L - 1) v.kn = c.template take<T>(es);
     nl = (nl + 1) / 2;
   }
