@@ -168,9 +168,9 @@ typedef struct {
  * counter and running all of its cycles, the convergence tests and the CG recurrences
  * with block barriers; the sums follow the batched kernels' partitions and trees, so
  * iterates, cycle counts and residuals are identical. MLMC_ENGINE_AUTO: the CTA engine
- * for grids up to 17^3 (where the batched engine waits on launches and host round trips),
- * the batched engine above; the environment variable MLMC_ENGINE=1 or 2 overrides the
- * automatic choice. */
+ * for grids up to 17^3 (where the batched engine waits on launches and host round trips)
+ * and for 33^3 grids in batches of at least 1024 samples, the batched engine otherwise;
+ * the environment variable MLMC_ENGINE=1 or 2 overrides the automatic choice. */
 #define MLMC_ENGINE_AUTO 0
 #define MLMC_ENGINE_BATCHED 1
 #define MLMC_ENGINE_CTA 2

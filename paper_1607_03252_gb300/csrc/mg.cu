@@ -511,8 +511,9 @@ __global__ void __launch_bounds__(128) k_rbgs_split(int colour, const float* __r
 // r~ = g - D u + sum K u_q (k_residual_nodal's operations and order) at the interior
 // nodes of one colour, four slots per thread as in k_rbgs_split, into r in colour-split
 // storage (the restriction reads only interior fine nodes; boundary and padding slots of
-// r are not written). Grid (groups of the interior rows of a plane, interior planes,
-// 2 x samples: colour = blockIdx.z & 1).
+// r are not written). Grid (groups of the interior rows of a plane, 2 x interior planes,
+// samples): colour = blockIdx.y & 1, so the two colours of a plane run back to back and
+// the 1/k and u rows each reads as the other colour's are still in L2.
 template <int LG>
 __global__ void __launch_bounds__(128) k_residual_split(const float* __restrict__ kn, const float* __restrict__ g,
                                                         const float* __restrict__ u, float* __restrict__ r,
@@ -520,9 +521,9 @@ __global__ void __launch_bounds__(128) k_residual_split(const float* __restrict_
   using G = SplitGeo<LG>;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= G::m * G::Q4) return;
-  const int s = blockIdx.z >> 1, colour = blockIdx.z & 1;
+  const int s = blockIdx.z, colour = blockIdx.y & 1;
   if (active && !active[s]) return;
-  const int yi = q / G::Q4, qi = q - yi * G::Q4, y = 1 + yi, z = 1 + (int)blockIdx.y;
+  const int yi = q / G::Q4, qi = q - yi * G::Q4, y = 1 + yi, z = 1 + (int)(blockIdx.y >> 1);
   const int par = (colour + y + z) & 1, xi0 = 4 * qi, x0 = 2 * xi0 + par;
   if (x0 > G::n - 2) return;
   const int o = (z * G::n + y) * G::P + xi0;
@@ -798,8 +799,8 @@ __global__ void __launch_bounds__(128) k_rbgs_split64(int colour, const double* 
 
 // r~ = g - D u + sum K u_q (k_residual_z's operations and order) at the interior nodes of
 // one colour, two per thread, into r in colour-split storage (interior nodes only).
-// Grid (two-slot groups of the interior rows of a plane, interior planes, 2 x samples:
-// colour = blockIdx.z & 1).
+// Grid (two-slot groups of the interior rows of a plane, 2 x interior planes, samples):
+// colour = blockIdx.y & 1 (the two colours of a plane back to back).
 template <int LG>
 __global__ void __launch_bounds__(128) k_residual_split64(const double* __restrict__ Kx, const double* __restrict__ Ky,
                                                           const double* __restrict__ Kz, const double* __restrict__ D,
@@ -809,9 +810,9 @@ __global__ void __launch_bounds__(128) k_residual_split64(const double* __restri
   constexpr int Q2 = G::P / 2;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= G::m * Q2) return;
-  const int s = blockIdx.z >> 1, colour = blockIdx.z & 1;
+  const int s = blockIdx.z, colour = blockIdx.y & 1;
   if (active && !active[s]) return;
-  const int yi = q / Q2, qi = q - yi * Q2, y = 1 + yi, z = 1 + (int)blockIdx.y;
+  const int yi = q / Q2, qi = q - yi * Q2, y = 1 + yi, z = 1 + (int)(blockIdx.y >> 1);
   const int par = (colour + y + z) & 1, xi0 = 2 * qi, x0 = 2 * xi0 + par;
   if (x0 > G::n - 2) return;
   const int o = (z * G::n + y) * G::P + xi0;
@@ -852,71 +853,6 @@ __global__ void __launch_bounds__(128) k_residual_split64(const double* __restri
 #pragma unroll
     for (int i = 0; i < 2; ++i)
       if (x0 + 2 * i >= 1 && x0 + 2 * i <= G::n - 2) rc[i] = out[i];
-  }
-}
-
-// u_f += trilinear interpolation of e_c on colour-split FP64 storage of both grids
-// (k_prolong's order and weights), two fine nodes of one colour per thread, 16-byte
-// update of u. Grid as k_rbgs_split64's with 2 x samples (colour = blockIdx.z & 1).
-template <int LG>
-__global__ void __launch_bounds__(128) k_prolong_split64(const double* __restrict__ ec, double* __restrict__ u,
-                                                         const int* __restrict__ active) {
-  using F = SplitGeo<LG>;
-  using C = SplitGeo<LG - 1>;
-  constexpr int Q2 = F::P / 2;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= F::m * Q2) return;
-  const int s = blockIdx.z >> 1, colour = blockIdx.z & 1;
-  if (active && !active[s]) return;
-  const int yi = q / Q2, qi = q - yi * Q2, y = 1 + yi, z = 1 + (int)blockIdx.y;
-  const int xo = (colour + y + z) & 1, xi0 = 2 * qi, x0 = 2 * xi0 + xo;
-  if (x0 > F::n - 2) return;
-  const int yo = y & 1, zo = z & 1, Y = y >> 1, Z = z >> 1;
-  const double* e = ec + (size_t)s * C::NS;
-  // coarse row (Y + b, Z + c) at X = xi0 + t, t = 0 .. 2 (xi0 even: colour (t + Y + b + Z + c) & 1,
-  // slot xi0 / 2 + t / 2)
-  auto row = [&](int b, int c, double* cv) {
-    const int cy = Y + b, cz = Z + c, base = (cz * C::n + cy) * C::P + (xi0 >> 1);
-#pragma unroll
-    for (int t = 0; t < 3; ++t)
-      if (t < 2 || xo) cv[t] = e[(size_t)((t + cy + cz) & 1) * C::BLK + (size_t)(base + (t >> 1))];
-  };
-  double r00[3], r10[3], r01[3], r11[3];
-  row(0, 0, r00);
-  if (yo) row(1, 0, r10);
-  if (zo) {
-    row(0, 1, r01);
-    if (yo) row(1, 1, r11);
-  }
-  const double w = xo + yo + zo == 0 ? 1.0 : xo + yo + zo == 1 ? 0.5 : xo + yo + zo == 2 ? 0.25 : 0.125;
-  double* uc = u + (size_t)s * F::NS + (size_t)colour * F::BLK + (size_t)((z * F::n + y) * F::P + xi0);
-  const double2 u2 = ld2(uc);
-  double out[2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    double v = 0.0;
-    v += r00[i];
-    if (xo) v += r00[i + 1];
-    if (yo) {
-      v += r10[i];
-      if (xo) v += r10[i + 1];
-    }
-    if (zo) {
-      v += r01[i];
-      if (xo) v += r01[i + 1];
-      if (yo) {
-        v += r11[i];
-        if (xo) v += r11[i + 1];
-      }
-    }
-    out[i] = comp2(u2, i) + w * v;
-  }
-  if (x0 >= 1 && x0 + 2 <= F::n - 2) {
-    *reinterpret_cast<double2*>(uc) = make_double2(out[0], out[1]);
-  } else {
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-      if (x0 + 2 * i >= 1 && x0 + 2 * i <= F::n - 2) uc[i] = out[i];
   }
 }
 
@@ -1090,6 +1026,92 @@ __global__ void k_prolong(int nf, int B, const T* __restrict__ ec, T* __restrict
     const T w = xo + yo + zo == 0 ? T(1) : xo + yo + zo == 1 ? T(0.5) : xo + yo + zo == 2 ? T(0.25) : T(0.125);
     const size_t p = (size_t)s * nf3 + (size_t)((z * nf + y) * nf + x);
     u[p] += w * v;
+  }
+}
+
+// The sums of k_prolong for the eight fine nodes (2X + dx, 2Y + dy, 2Z + dz) of one coarse
+// cell, c = e_c at (X, Y, Z), (X+1, Y, Z), (X, Y+1, Z), (X+1, Y+1, Z), then the same at Z+1:
+// every node's sum takes its terms in k_prolong's order, and the nodes whose term
+// sequences share a prefix share its partial sum (14 additions for the block instead of 27).
+// v[dx + 2 dy + 4 dz].
+template <typename T>
+__device__ __forceinline__ void prolong_block_sums(const T (&c)[8], T (&v)[8]) {
+  T sa = 0;
+  sa += c[0];
+  const T sab = sa + c[1], sac = sa + c[2];
+  const T sabcd = (sab + c[2]) + c[3];
+  v[0] = sa;
+  v[1] = sab;
+  v[2] = sac;
+  v[3] = sabcd;
+  v[4] = sa + c[4];
+  v[5] = (sab + c[4]) + c[5];
+  v[6] = (sac + c[4]) + c[6];
+  v[7] = (((sabcd + c[4]) + c[5]) + c[6]) + c[7];
+}
+
+// k_prolong's result (bit for bit) with one thread per coarse cell: the eight fine nodes
+// (2X + dx, 2Y + dy, 2Z + dz) of the cell, their sums from prolong_block_sums, u += w v at
+// the interior ones. Every thread runs the same operations (no parity divergence) and the
+// block shares partial sums: 2.75 instead of 4.4 FP64 operations per fine node. Grid: coarse
+// cells of a plane, (sample, cell plane) planes.
+template <typename T>
+__global__ void __launch_bounds__(128) k_prolong_blk(int nf, int B, const T* __restrict__ ec, T* __restrict__ u,
+                                                     const int* __restrict__ active) {
+  const int nc = (nf + 1) / 2, mc = nc - 1;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= mc * mc) return;
+  const int Y = q / mc, X = q - Y * mc;
+  const size_t nc3 = (size_t)nc * nc * nc, nf3 = (size_t)nf * nf * nf, nc2 = (size_t)nc * nc;
+  for (int zz = blockIdx.y; zz < B * mc; zz += gridDim.y) {
+    const int s = zz / mc, Z = zz - s * mc;
+    if (active && !active[s]) continue;
+    const T* e = ec + (size_t)s * nc3 + (size_t)((Z * nc + Y) * nc + X);
+    const T c[8] = {e[0], e[1], e[nc], e[nc + 1], e[nc2], e[nc2 + 1], e[nc2 + nc], e[nc2 + nc + 1]};
+    T v[8];
+    prolong_block_sums(c, v);
+    T* ub = u + (size_t)s * nf3;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+      const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
+      if (x < 1 || y < 1 || z < 1 || x > nf - 2 || y > nf - 2 || z > nf - 2) continue;
+      const T w = dx + dy + dz == 0 ? T(1) : dx + dy + dz == 1 ? T(0.5) : dx + dy + dz == 2 ? T(0.25) : T(0.125);
+      ub[(size_t)((z * nf + y) * nf + x)] += w * v[k];
+    }
+  }
+}
+
+// k_prolong_blk on colour-split storage of both grids (LG: the fine grid's). Fine node
+// (2X + dx, ...) is colour (dx + dy + dz) & 1, slot X; coarse (X', Y', Z') colour
+// (X' + Y' + Z') & 1, slot X' / 2. Grid (coarse cells of a plane, cell planes, samples).
+template <int LG, typename T>
+__global__ void __launch_bounds__(128) k_prolong_blk_split(const T* __restrict__ ec, T* __restrict__ u,
+                                                           const int* __restrict__ active) {
+  using F = SplitGeo<LG>;
+  using C = SplitGeo<LG - 1>;
+  constexpr int mc = C::n - 1;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= mc * mc) return;
+  const int s = blockIdx.z;
+  if (active && !active[s]) return;
+  const int Y = q / mc, X = q - Y * mc, Z = (int)blockIdx.y;
+  const T* e = ec + (size_t)s * C::NS;
+  auto at = [&](int i, int j, int k) -> T {
+    const int xx = X + i, yy = Y + j, zz = Z + k;
+    return e[(size_t)((xx + yy + zz) & 1) * C::BLK + (size_t)((zz * C::n + yy) * C::P + (xx >> 1))];
+  };
+  const T c[8] = {at(0, 0, 0), at(1, 0, 0), at(0, 1, 0), at(1, 1, 0), at(0, 0, 1), at(1, 0, 1), at(0, 1, 1), at(1, 1, 1)};
+  T v[8];
+  prolong_block_sums(c, v);
+  T* ub = u + (size_t)s * F::NS;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
+    if (x < 1 || y < 1 || z < 1 || x > F::n - 2 || y > F::n - 2 || z > F::n - 2) continue;
+    const T w = dx + dy + dz == 0 ? T(1) : dx + dy + dz == 1 ? T(0.5) : dx + dy + dz == 2 ? T(0.25) : T(0.125);
+    ub[(size_t)((dx + dy + dz) & 1) * F::BLK + (size_t)((z * F::n + y) * F::P + X)] += w * v[k];
   }
 }
 
@@ -1764,7 +1786,7 @@ void vcycle_split(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   const unsigned groups = (unsigned)((m * (split_pitch(v.n) / 4) + 127) / 128);
   float* r = (float*)(void*)v.r;  // colour-split r~ (room for n^2 (n+1) elements: carved as n^3 + slack)
   MLMC_LAUNCH(prof::sized("residual_split_f32", v.n), Ba * interior(v.n) * 4.0 * W, Ba * interior(v.n) * 37.0, st,
-              MLMC_SPLIT_DISPATCH(v.n, (k_residual_split<LG><<<dim3(groups, (unsigned)m, (unsigned)(2 * B)), 128, 0,
+              MLMC_SPLIT_DISPATCH(v.n, (k_residual_split<LG><<<dim3(groups, (unsigned)(2 * m), (unsigned)B), 128, 0,
                                                                 st>>>(kn, g, u, r, act))));
   MLMC_LAUNCH(Names<T>::restrict_, Ba * ((double)v.n3 + (double)w.n3) * W, Ba * interior(w.n) * 54.0, st,
               MLMC_SPLIT_DISPATCH(v.n, (k_restrict_split<LG><<<dim3((unsigned)(((w.n - 2) * (w.n - 2) + 127) / 128),
@@ -1807,7 +1829,7 @@ void vcycle_split64(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   };
   smooth(nu1);
   MLMC_LAUNCH(prof::sized("residual_split_f64", v.n), Ba * interior(v.n) * 7.0 * W, Ba * interior(v.n) * 14.0, st,
-              MLMC_SPLIT_DISPATCH(v.n, (k_residual_split64<LG><<<dim3(pairs, (unsigned)m, (unsigned)(2 * B)), 128, 0,
+              MLMC_SPLIT_DISPATCH(v.n, (k_residual_split64<LG><<<dim3(pairs, (unsigned)(2 * m), (unsigned)B), 128, 0,
                                                                   st>>>(Kx, Ky, Kz, D, g, u, r, act))));
   MLMC_LAUNCH(Names<T>::restrict_, Ba * ((double)v.n3 + (double)w.n3) * W, Ba * interior(w.n) * 54.0, st,
               MLMC_SPLIT_DISPATCH(v.n, (k_restrict_split<LG, double><<<dim3((unsigned)(((w.n - 2) * (w.n - 2) + 127) /
@@ -1818,8 +1840,11 @@ void vcycle_split64(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   vcycle(H, j + 1, nu1, nu2, st);
   MLMC_LAUNCH(prof::sized("prolong_split_f64", v.n), Ba * (2.0 * (double)v.n3 + (double)w.n3) * W,
               Ba * interior(v.n) * 4.375, st,
-              MLMC_SPLIT_DISPATCH(v.n, (k_prolong_split64<LG><<<dim3(pairs, (unsigned)m, (unsigned)(2 * B)), 128, 0,
-                                                                 st>>>((const double*)(const void*)w.u, u, act))));
+              MLMC_SPLIT_DISPATCH(v.n, (k_prolong_blk_split<LG, double><<<dim3((unsigned)(((w.n - 1) * (w.n - 1) +
+                                                                                          127) / 128),
+                                                                                (unsigned)(w.n - 1), (unsigned)B),
+                                                                           128, 0, st>>>(
+                                           (const double*)(const void*)w.u, u, act))));
   smooth(nu2);
 }
 
@@ -1909,8 +1934,8 @@ void vcycle(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
                                                                                                act)));
   else
     MLMC_LAUNCH(Names<T>::prolong, Ba * (2.0 * (double)v.n3 + (double)w.n3) * W, Ba * interior(v.n) * 4.375, st,
-                (k_prolong<T><<<plane_grid(m * (v.n - 1), (long long)B * m), kPlaneThreads, 0, st>>>(v.n, B, w.u,
-                                                                                                    v.u, act)));
+                (k_prolong_blk<T><<<plane_grid((w.n - 1) * (w.n - 1), (long long)B * (w.n - 1)), 128, 0, st>>>(
+                    v.n, B, w.u, v.u, act)));
   smooth(nu2);
 }
 
@@ -2090,8 +2115,11 @@ inline bool cta_engine_chosen(const mg_cfg& c, int n, int B) {
   }();
   if (env == MLMC_ENGINE_BATCHED) return false;
   if (env == MLMC_ENGINE_CTA) return true;
-  (void)B;
-  return n <= 17;
+  // measured: 17^3 1.15-1.4x the batched kernels at 1..4096 samples; 33^3 about even at
+  // 1024 samples (FP64 stationary: 73.6 against 74.8 ms, 34 against 757 launches) and
+  // slower below (256 samples of mixed CG: 31.0 against 24.8 ms; one CTA per sample leaves
+  // SMs idle while fewer samples than resident CTAs remain)
+  return n <= 17 || (n <= 33 && B >= 1024);
 }
 constexpr int kCtaMaxPartials = 64;
 
@@ -2265,30 +2293,24 @@ __device__ void cta_restrict(const CtaLevel<T>& v, const CtaLevel<T>& w, int s) 
 // u_f += trilinear interpolation of e_c (k_prolong's operations)
 template <typename T>
 __device__ void cta_prolong(const CtaLevel<T>& w, const CtaLevel<T>& v, int s) {
-  const int nf = v.n, nc = w.n, m = nf - 2;
-  const size_t nf3 = (size_t)nf * nf * nf, nc3 = (size_t)nc * nc * nc;
-  for (int i = threadIdx.x; i < m * m * m; i += blockDim.x) {
-    const int z = 1 + i / (m * m), rem = i - (z - 1) * m * m, y = 1 + rem / m, x = 1 + rem - (y - 1) * m;
-    const int xo = x & 1, yo = y & 1, zo = z & 1, X = x >> 1, Y = y >> 1, Z = z >> 1;
-    const T* r0 = w.u + (size_t)s * nc3 + (size_t)((Z * nc + Y) * nc + X);
-    T val = 0;
-    val += r0[0];
-    if (xo) val += r0[1];
-    if (yo) {
-      val += r0[nc];
-      if (xo) val += r0[nc + 1];
+  // one coarse cell per thread (k_prolong_blk's sums, bit for bit k_prolong's)
+  const int nf = v.n, nc = w.n, mc = nc - 1;
+  const size_t nf3 = (size_t)nf * nf * nf, nc3 = (size_t)nc * nc * nc, nc2 = (size_t)nc * nc;
+  for (int i = threadIdx.x; i < mc * mc * mc; i += blockDim.x) {
+    const int Z = i / (mc * mc), rem = i - Z * mc * mc, Y = rem / mc, X = rem - Y * mc;
+    const T* e = w.u + (size_t)s * nc3 + (size_t)((Z * nc + Y) * nc + X);
+    const T c[8] = {e[0], e[1], e[nc], e[nc + 1], e[nc2], e[nc2 + 1], e[nc2 + nc], e[nc2 + nc + 1]};
+    T val[8];
+    prolong_block_sums(c, val);
+    T* ub = v.u + (size_t)s * nf3;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+      const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
+      if (x < 1 || y < 1 || z < 1 || x > nf - 2 || y > nf - 2 || z > nf - 2) continue;
+      const T wgt = dx + dy + dz == 0 ? T(1) : dx + dy + dz == 1 ? T(0.5) : dx + dy + dz == 2 ? T(0.25) : T(0.125);
+      ub[(size_t)((z * nf + y) * nf + x)] += wgt * val[k];
     }
-    if (zo) {
-      const T* r2 = r0 + nc * nc;
-      val += r2[0];
-      if (xo) val += r2[1];
-      if (yo) {
-        val += r2[nc];
-        if (xo) val += r2[nc + 1];
-      }
-    }
-    const T wgt = xo + yo + zo == 0 ? T(1) : xo + yo + zo == 1 ? T(0.5) : xo + yo + zo == 2 ? T(0.25) : T(0.125);
-    v.u[(size_t)s * nf3 + (size_t)((z * nf + y) * nf + x)] += wgt * val;
   }
 }
 
@@ -2821,7 +2843,7 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
                         v.n, B, w.u, v.u, H.active)));
       else
         MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
-                    (k_prolong<T><<<plane_grid(m * (v.n - 1), (long long)B * m), kPlaneThreads, 0, st>>>(
+                    (k_prolong_blk<T><<<plane_grid((w.n - 1) * (w.n - 1), (long long)B * (w.n - 1)), 128, 0, st>>>(
                         v.n, B, w.u, v.u, H.active)));
       for (int cyc = 0; cyc < maxc; ++cyc) vcycle(H, j, nu1, nu2, st);
     }
@@ -2921,11 +2943,11 @@ int mg_solve_dev(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_ho
 
 int interpolate_dev(const double* uc, int nf, int B, double* uf, cudaStream_t st) {
   MLMC_CUDA_TRY(cudaMemsetAsync(uf, 0, (size_t)B * cube(nf) * sizeof(double), st));
-  const int m = nf - 2;
+  const int mc = (nf + 1) / 2 - 1;
   MLMC_LAUNCH("interpolate_f64", B * (2.0 * (double)cube(nf) + (double)cube((nf + 1) / 2)) * 8.0,
               B * interior(nf) * 4.375, st,
-              (k_prolong<double><<<plane_grid(m * (nf - 1), (long long)B * m), kPlaneThreads, 0, st>>>(nf, B, uc, uf,
-                                                                                                     nullptr)));
+              (k_prolong_blk<double><<<plane_grid(mc * mc, (long long)B * mc), 128, 0, st>>>(nf, B, uc, uf,
+                                                                                             nullptr)));
   return MLMC_OK;
 }
 

@@ -13,8 +13,9 @@
 //   split64 n B in.bin perm.bin out.bin          (FP64 stored-face kernels)
 //     in.bin   float64: k0, g, u (B n^3 each, plain), ec (B nc^3), r (B n^3)
 //     out.bin  float64, each plain then split mapped back: Kx, Ky, Kz, D, 1/D, u after a
-//              red and a black pass, r~, u + P ec, FW(r) (B nc^3), u through the plain ->
-//              split -> plain copies
+//              red and a black pass, r~, then u + P ec of k_prolong against the block
+//              form (plain; split mapped back; FP32 widened), FW(r) (B nc^3), u through
+//              the plain -> split -> plain copies
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -128,7 +129,7 @@ int main(int argc, char** argv) {
   std::vector<float> rp(B * n3, nan), rss(B * ns, 0.0f);
   launch(dim3((unsigned)((n * n + T - 1) / T), (unsigned)(B * n)), dim3(T),
          [&] { mlmc::k_residual_nodal(n, B, kn.data(), g.data(), up.data(), rp.data(), nullptr); });
-  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * (P / 4) + 127) / 128), (unsigned)m, (unsigned)(2 * B)), dim3(128), [&] {
+  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * (P / 4) + 127) / 128), (unsigned)(2 * m), (unsigned)B), dim3(128), [&] {
     mlmc::k_residual_split<LG>(ks.data(), gs.data(), us.data(), rss.data(), nullptr);
   }));
   auto rs = from_split(rss, perm);  // the split residual leaves boundary slots unwritten (zero here)
@@ -236,19 +237,33 @@ static int split64(char** argv) {
     mlmc::k_residual_z<double, double, double, double>(n, n - 2, Kx.data(), Ky.data(), Kz.data(), D.data(), g.data(),
                                                        up.data(), rp.data(), nullptr, nullptr);
   });
-  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * (P / 2) + 127) / 128), (unsigned)m, (unsigned)(2 * B)), dim3(128), [&] {
+  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * (P / 2) + 127) / 128), (unsigned)(2 * m), (unsigned)B), dim3(128), [&] {
     mlmc::k_residual_split64<LG>(sKx.data(), sKy.data(), sKz.data(), sD.data(), gs.data(), us.data(), rss.data(),
                                  nullptr);
   }));
   emit(rp, from_split(rss, perm));  // the split residual leaves boundary slots unwritten (zero here)
-  // the trilinear correction
-  std::vector<double> pp = u, ps = to_split(u, perm, B * ns), ecs = to_split(ec, permc, B * nsc);
+  // the trilinear correction: k_prolong against the block form (one thread per coarse
+  // cell), plain and split, and in FP32
+  std::vector<double> pp = u, ecs = to_split(ec, permc, B * nsc);
   launch(dim3((unsigned)((m * (n - 1) + T - 1) / T), (unsigned)(B * m)), dim3(T),
          [&] { mlmc::k_prolong<double>(n, B, ec.data(), pp.data(), nullptr); });
-  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((m * (P / 2) + 127) / 128), (unsigned)m, (unsigned)(2 * B)), dim3(128), [&] {
-    mlmc::k_prolong_split64<LG>(ecs.data(), ps.data(), nullptr);
+  // the block form (one thread per coarse cell), plain and split, and in FP32
+  const int mc = nc - 1;
+  std::vector<double> pb = u, pbs = to_split(u, perm, B * ns);
+  launch(dim3((unsigned)((mc * mc + 127) / 128), (unsigned)(B * mc)), dim3(128),
+         [&] { mlmc::k_prolong_blk<double>(n, B, ec.data(), pb.data(), nullptr); });
+  MLMC_SPLIT_DISPATCH(n, launch(dim3((unsigned)((mc * mc + 127) / 128), (unsigned)mc, (unsigned)B), dim3(128), [&] {
+    mlmc::k_prolong_blk_split<LG, double>(ecs.data(), pbs.data(), nullptr);
   }));
-  emit(pp, from_split(ps, perm));
+  emit(pp, pb);
+  emit(pp, from_split(pbs, perm));
+  std::vector<float> uf(u.begin(), u.end()), ecf(ec.begin(), ec.end());
+  std::vector<float> pf = uf, pbf = uf;
+  launch(dim3((unsigned)((m * (n - 1) + T - 1) / T), (unsigned)(B * m)), dim3(T),
+         [&] { mlmc::k_prolong<float>(n, B, ecf.data(), pf.data(), nullptr); });
+  launch(dim3((unsigned)((mc * mc + 127) / 128), (unsigned)(B * mc)), dim3(128),
+         [&] { mlmc::k_prolong_blk<float>(n, B, ecf.data(), pbf.data(), nullptr); });
+  emit(std::vector<double>(pf.begin(), pf.end()), std::vector<double>(pbf.begin(), pbf.end()));
   // full weighting into the plain and the split coarse storage
   std::vector<double> gcp(B * nc3, 0.0), gcs(B * nsc, 0.0), r_s = to_split(r, perm, B * ns);
   const int hc = nc - 1;

@@ -152,7 +152,8 @@ def test_split64_kernels_equal_plain_kernels_bitwise(emu, n, B):
     subprocess.run([exe, "split64", str(n), str(B), str(src), str(pm), str(dst)], check=True)
     out = np.fromfile(dst, dtype=np.float64)
     n3, nc3 = B * n ** 3, B * nc ** 3
-    names = ["Kx", "Ky", "Kz", "D", "1/D", "sweep", "residual", "prolongation", "restriction", "copies"]
+    names = ["Kx", "Ky", "Kz", "D", "1/D", "sweep", "residual", "block prolongation", "block prolongation, split",
+             "block prolongation, FP32", "restriction", "copies"]
     sizes = [nc3 if name == "restriction" else n3 for name in names]
     off, got = 0, {}
     for name, sz in zip(names, sizes):
