@@ -101,7 +101,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="own", choices=["own", "reference"])
-    p.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    p.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c6"])
     p.add_argument("--c5-arms", default="fast,plain", help="c5: which arms to run (fast, plain)")
     p.add_argument("--c5-eps", type=float, default=None, help="c5: override the RMS tolerance")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -121,6 +121,17 @@ def measured_peaks():
             return json.load(fh)
     except Exception:
         return {}
+
+
+def solver_kw(mg, cfg):
+    """The solver settings of a workload as make_mlmc_cfg keywords: outer iteration (none,
+    flexible CG, one FMG cycle), discretisation, QoI, covariance and the cycle budget (the
+    FMG cycle's V-cycles per grid; otherwise the cap of a solve to rtol)."""
+    accel = {"cg": mg.MLMC_ACCEL_CG, "fmg": mg.MLMC_ACCEL_FMG}.get(cfg.get("accel"), mg.MLMC_ACCEL_NONE)
+    return dict(accel=accel, disc=mg.MLMC_DISC_FE if cfg.get("disc") == "fe" else mg.MLMC_DISC_FV,
+                qoi={"point": mg.MLMC_QOI_POINT, "flux": mg.MLMC_QOI_FLUX}.get(cfg.get("qoi"), mg.MLMC_QOI_MEAN),
+                cov=mg.MLMC_COV_EXP if cfg.get("cov") == "exp" else mg.MLMC_COV_GAUSS,
+                max_cycles=cfg.get("cycles", 300))
 
 
 def workload(cfg_name):
@@ -239,6 +250,10 @@ def oracle_level_rates(cfg, levels, single, counts):
     mixed = cfg.get("precision") == "mixed"
     ocfg = oracle.make_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], cfg["nu1"], cfg["nu2"], cfg["rtol"], 400,
                            mixed=mixed)
+    fe = cfg.get("disc") == "fe"
+    if fe:
+        from oracle import core as ocore
+        from oracle import fe as ofe
     rates, secs = {}, {}
     for l, cnt in zip(levels, counts):
         if cnt == 0:
@@ -248,7 +263,13 @@ def oracle_level_rates(cfg, levels, single, counts):
         ids = sample_ids(l, 0, cnt)
         nc = 0 if (single or l == 0) else level_n(l - 1)
         t = time.perf_counter()
-        oracle.level_batch(ocfg, level_n(l), nc, ids)
+        if fe:  # the P1 / FMG-2V(4,4) oracle (plain numpy, one sample at a time)
+            cov = ocore.COV_EXP if cfg.get("cov") == "exp" else ocore.COV_GAUSS
+            for i in ids:
+                ofe.level_sample(RUN_SEED, int(i), cfg["M"], cfg["sigma2"], cfg["ell"], level_n(l), nc,
+                                 qoi=cfg.get("qoi", "point"), cov=cov)
+        else:
+            oracle.level_batch(ocfg, level_n(l), nc, ids)
         dt = time.perf_counter() - t
         rates[l] = cnt / dt
         secs[l] = dt
@@ -260,6 +281,8 @@ def oracle_counts(levels, threads, cfg=None):
             4: 0, 5: 0}
     if cfg is not None and cfg.get("precision") == "mixed":
         base[3] = 0  # rough fields: the stationary oracle needs 100+ cycles; extrapolate beyond 65^3
+    if cfg is not None and cfg.get("disc") == "fe":
+        base = {0: 32, 1: 8, 2: 2, 3: 0}  # numpy FE oracle, one thread: ~0.03 / 0.25 / 3 s per sample
     return [base[l] for l in levels]
 
 
@@ -278,7 +301,7 @@ def reference_arm(args):
     import oracle
 
     cfg, levels, N, single = workload(args.config)
-    threads = oracle.max_threads()
+    threads = 1 if cfg.get("disc") == "fe" else oracle.max_threads()  # the FE oracle is plain numpy
     counts = oracle_counts(levels, threads, cfg)
     step_times, all_rates = [], []
     for i in range(args.warmup + args.steps):
@@ -290,8 +313,9 @@ def reference_arm(args):
             all_rates.append(rates)
     mean_rates = {l: statistics.mean(r[l] for r in all_rates) for l in levels}
     value = extrapolated_rate(levels, N, mean_rates)
-    sample = "per step: %s samples on levels %s (ids of the benchmark workload), OpenMP over samples; " \
-             "samples/s per level extrapolated to N=%s" % (counts, levels, N)
+    how = "one sample at a time (numpy)" if cfg.get("disc") == "fe" else "OpenMP over samples"
+    sample = ("per step: %s samples on levels %s (ids of the benchmark workload), %s; "
+              "samples/s per level extrapolated to N=%s" % (counts, levels, how, N))
     line = {
         "impl": "reference", "metric": "MLMC samples/s (all levels, %s)" % cfg["name"], "value": value,
         "unit": "samples/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -328,6 +352,7 @@ def own_arm(args):
         line["c3"] = sub_c3(args)
         line["c5"] = sub_c5(args)
         line["c4"] = sub_c4(args, line["c3"])
+        line["c6"] = measure(args, "c6", full=False)
         line["extras_wall_s"] = time.perf_counter() - t0
     if line is not None:
         print(json.dumps(line), flush=True)
@@ -346,7 +371,8 @@ def measure(args, cfg_name, full=True):
     rank, world, local = dist_env()
     cfg, levels, N, single = workload(cfg_name)
     prec = mg.MLMC_PREC_F64 if cfg["precision"] == "f64" else mg.MLMC_PREC_MIXED
-    accel = mg.MLMC_ACCEL_CG if cfg.get("accel") == "cg" else mg.MLMC_ACCEL_NONE
+    skw = solver_kw(mg, cfg)
+    accel = skw["accel"]
     stream = torch.cuda.Stream()
     dev = torch.device("cuda", local)
     plan = None
@@ -365,7 +391,7 @@ def measure(args, cfg_name, full=True):
         for l, n in zip(levels, N):
             c = mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=(level_n(l) if single else 17),
                                  nu1=cfg["nu1"], nu2=cfg["nu2"], rtol=cfg["rtol"], precision=prec,
-                                 max_batch=min(n, 256), stream=stream, accel=accel)
+                                 max_batch=min(n, 256), stream=stream, **skw)
             rows, bs, bnu = mg.mlmc_autotune(c, 0 if single else l, int(sample_ids(l, 1 << 40, 1)[0]), min(n, 256))
             tune[str(l)] = {"best": {"smoother": mg._capi.SMOOTHER_NAMES.get(bs, bs), "nu": bnu}, "table": rows}
         plan = {"autotune": tune}
@@ -378,7 +404,7 @@ def measure(args, cfg_name, full=True):
         lvl = 0 if single else l
         mcfg[l] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=nu_cfg[0],
                                     nu2=nu_cfg[1], rtol=cfg["rtol"], precision=prec, max_batch=n, stream=stream,
-                                    accel=accel, max_cycles=300), lvl)
+                                    **skw), lvl)
     # levels run concurrently on `lanes` streams (the one-GPU form of scheduling the
     # levels on separate processor groups): the FP64/HBM-bound solves of one level
     # overlap the FP32-bound field evaluation and solves of others
@@ -506,7 +532,7 @@ def measure(args, cfg_name, full=True):
     # end to end through the host-buffer C-ABI call
     e2e = None
     if full and not args.no_e2e:
-        e2e = e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, accel, lanes)
+        e2e = e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, skw, lanes)
 
     line = None
     if rank == 0:
@@ -518,12 +544,15 @@ def measure(args, cfg_name, full=True):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == mg.MLMC_PREC_F64 else "f32+f64",
-            "solver": {"precision": cfg["precision"], "accel": cfg.get("accel", "none")},
+            "solver": {"precision": cfg["precision"], "accel": cfg.get("accel", "none"),
+                       "disc": cfg.get("disc", "fv"), "qoi": cfg.get("qoi", "mean"), "cov": cfg.get("cov", "gauss")},
             "plan": plan,
             "data": "synthetic (seeded Philox realisations, run_seed %d)" % RUN_SEED,
             "config": {"workload": cfg["name"], "levels": levels, "N_per_gpu": N,
                        "fine_n": [level_n(l) for l in levels], "sigma2": cfg["sigma2"], "ell": cfg["ell"],
-                       "M": cfg["M"], "cycle": "V(%d,%d)" % (cfg["nu1"], cfg["nu2"]), "rtol": cfg["rtol"],
+                       "M": cfg["M"], "rtol": cfg["rtol"],
+                       "cycle": ("FMG-%dV(%d,%d)" % (cfg["cycles"], cfg["nu1"], cfg["nu2"]) if cfg.get("accel") == "fmg"
+                                 else "V(%d,%d)" % (cfg["nu1"], cfg["nu2"])),
                        "parallelism": "replicas x%d (samples sharded by rank, no data-path collective)" % world,
                        "level_streams": [["%d[%d:%d]" % (l, a, b) for (l, a, b) in its] for its in lanes],
                        "level_ms_alone": {str(l): round(v, 3) for l, v in seq_ms.items()},
@@ -686,7 +715,7 @@ def run_lanes(torch, lanes, lane_streams, main_stream, body):
         raise errors[0]
 
 
-def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, accel, lanes):
+def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stream, nu_cfg, skw, lanes):
     """Same workload through mlmc_level_estimate: ids built on the host and copied in,
     Y/Qf/Qc copied back into pinned host buffers, every step."""
     import ctypes
@@ -702,7 +731,7 @@ def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stre
             n0 = level_n(l) if single else 17
             cfgs[(l, a)] = (mg.make_mlmc_cfg(RUN_SEED, cfg["sigma2"], cfg["ell"], cfg["M"], n0=n0, nu1=nu_cfg[0],
                                              nu2=nu_cfg[1], rtol=cfg["rtol"], precision=prec, max_batch=Nof[l],
-                                             stream=lane_streams[i], accel=accel, max_cycles=300),
+                                             stream=lane_streams[i], **skw),
                             0 if single else l)
     L = mg.lib()
     dp = ctypes.POINTER(ctypes.c_double)
@@ -743,7 +772,7 @@ def e2e_measure(args, mg, torch, cfg, levels, N, single, prec, rank, world, stre
 def cpu_baseline(cfg, levels, N, single):
     import oracle
 
-    threads = oracle.max_threads()
+    threads = 1 if cfg.get("disc") == "fe" else oracle.max_threads()  # the FE oracle is plain numpy
     counts = oracle_counts(levels, threads, cfg)
     rates, secs = oracle_level_rates(cfg, levels, single, counts)
     value = extrapolated_rate(levels, N, rates)

@@ -248,14 +248,17 @@ def qoi_flux(u, k):
     return total / h
 
 
-def level_sample(run_seed, sample_id, M, sigma2, ell, nf, nc, qoi="point"):
+def level_sample(run_seed, sample_id, M, sigma2, ell, nf, nc, qoi="point", cov=None):
     """(Q_f, Q_c) of one MLMC sample on the FE discretisation: the Fourier-feature field
-    of the sample on each grid (orc_field), one FMG-2V(4,4) cycle each, the QoI ("point":
-    u(1/4, 1/4, 1/4); "flux": across x_2 = 1/4); Q_c = 0 when nc = 0."""
+    of the sample on each grid (orc_field; cov: the covariance, Gaussian by default), one
+    FMG-2V(4,4) cycle each, the QoI ("point": u(1/4, 1/4, 1/4); "flux": across x_2 = 1/4);
+    Q_c = 0 when nc = 0."""
     from . import core
 
+    cv = core.COV_GAUSS if cov is None else cov
+
     def q(n):
-        k = core.field(run_seed, sample_id, M, sigma2, ell, n)
+        k = core.field(run_seed, sample_id, M, sigma2, ell, n, cov=cv)
         u = fmg(n, k)
         return qoi_point(u) if qoi == "point" else qoi_flux(u, k)
 

@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(128) k_rbgs_split(int colour, const float* __r
 // samples): colour = blockIdx.y & 1, so the two colours of a plane run back to back and
 // the 1/k and u rows each reads as the other colour's are still in L2.
 template <int LG>
-__global__ void __launch_bounds__(128) k_residual_split(const float* __restrict__ kn, const float* __restrict__ g,
+__global__ void __launch_bounds__(128, 8) k_residual_split(const float* __restrict__ kn, const float* __restrict__ g,
                                                         const float* __restrict__ u, float* __restrict__ r,
                                                         const int* __restrict__ active) {
   using G = SplitGeo<LG>;

@@ -11,8 +11,9 @@ realisations on an n^3 grid and runs exactly `cycles` V(2,2) cycles (rtol = 0; o
 to --rtol) through the C ABI, so
 that every kernel class launches with the sizes of that grid. With --timing the solve runs
 twice and the second run records CUDA events around every launch: per kernel class it
-prints launches, device time per launch and algorithmic GB/s; with --field spde the same
-for the field evaluation (the SPDE sampler of Sec. 3.2), with its wall time. With --level
+prints launches, device time per launch and algorithmic GB/s, and the same for the field
+evaluation (Fourier features, or the SPDE sampler of Sec. 3.2), with its wall
+time (MLMC_FIELD_ARITH=0..3 selects the field's arithmetic). With --level
 it instead runs mlmc_level_estimate for `batch` samples of that MLMC level (grids from n0;
 the precision, smoother and field as given, rtol 1e-10) and, with --timing, prints the
 per-class profile of a second run. With --fma-peak it prints the measured FP64 and FP32
@@ -104,14 +105,14 @@ def main(argv=None):
     cyc, rel, st = mg.mg_solve_batch(cfg, k, u)
     torch.cuda.synchronize()
     print("n=%d batch=%d prec=%s cycles=%s rel_res=%.3e" % (a.n, a.batch, a.prec, cyc.tolist(), rel.max()))
-    if a.timing and a.field == "spde":
+    if a.timing:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         mg.mlmc_field_eval(fcfg, sample_ids(3, 0, a.batch), k)
         e1.record()
         torch.cuda.synchronize()
-        print("  SPDE field wall time: %.3f ms (%.1f samples/s)" % (e0.elapsed_time(e1),
-                                                                  a.batch / (e0.elapsed_time(e1) * 1e-3)))
+        print("  %s field wall time: %.3f ms (%.1f samples/s)" % (a.field, e0.elapsed_time(e1),
+                                                                a.batch / (e0.elapsed_time(e1) * 1e-3)))
         mg.profile_reset()
         mg.profile_enable(True)
         mg.mlmc_field_eval(fcfg, sample_ids(3, 0, a.batch), k)

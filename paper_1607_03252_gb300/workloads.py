@@ -1,7 +1,7 @@
 """Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
 
 This module holds no arithmetic of the method: only seeds, sample ids, grid sizes and
-the configuration parameters of the five workloads, plus seeded random arrays used
+the configuration parameters of the six workloads, plus seeded random arrays used
 as inputs to the batched solver. Both the CUDA path and the CPU oracle receive the
 same values from here; neither side's computation lives here.
 
@@ -47,6 +47,12 @@ CONFIGS = {
     # serving: Poisson single-sample requests over levels 0..4 (C3's field)
     "c4": dict(name="c4_serving", levels=[0, 1, 2, 3, 4], sigma2=2.0, ell=0.1, M=256, precision="mixed",
                rtol=1e-10, nu1=2, nu2=2),
+    # the paper's static 4-level run (Sec. 7.1: P1 elements, one FMG-2V(4,4) cycle per solve,
+    # the point QoI, N = (4123, 688, 108, 16)) on 17^3..129^3, exponential covariance with
+    # a correlation length of ~20 finest-grid spacings, as in the paper
+    "c6": dict(name="c6_e9_fe_fmg", levels=[0, 1, 2, 3], single_level=False, N=[4123, 688, 108, 16],
+               sigma2=1.0, ell=0.15, M=256, cov="exp", precision="f64", disc="fe", accel="fmg", qoi="point",
+               nu1=4, nu2=4, cycles=2, rtol=0.0),
     # 6-level adaptive MLMC to RMS tolerance 2e-4
     "c5": dict(name="c5_mlmc6_adaptive", levels=[0, 1, 2, 3, 4, 5], single_level=False,
                N_init=[256, 64, 16, 8, 4, 2], eps=2e-4, theta=0.5, sigma2=1.0, ell=0.05, M=1024,

@@ -77,6 +77,29 @@ def test_fe_fmg_level_estimate_matches_oracle(orc, level, qoi):
         assert abs(Y[s] - (qf - qc)) <= 1e-10 * scale
 
 
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_fe_fmg_exponential_covariance_level_matches_oracle(orc, level):
+    """The settings of the paper's static run (Sec. 7.1) as the c6 workload uses them: P1
+    elements, one FMG-2V(4,4) cycle, the point QoI, exponential covariance with a short
+    correlation length (ell = 0.15, M = 256), grids 17^3..65^3."""
+    from oracle import core, fe
+
+    ids = sample_ids(level, 40, 3)
+    cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.15, 256, n0=17, nu1=4, nu2=4, rtol=0.0, max_cycles=2,
+                           accel=mg.MLMC_ACCEL_FMG, disc=mg.MLMC_DISC_FE, qoi=mg.MLMC_QOI_POINT,
+                           cov=mg.MLMC_COV_EXP)
+    st, Y, Qf, Qc = mg.mlmc_level_estimate(cfg, level, int(ids[0]), len(ids))
+    nf = 16 * 2 ** level + 1
+    nc = 16 * 2 ** (level - 1) + 1 if level > 0 else 0
+    for s, sid in enumerate(ids):
+        qf, qc = fe.level_sample(RUN_SEED, int(sid), 256, 1.0, 0.15, nf, nc, "point", cov=core.COV_EXP)
+        scale = max(abs(qf), abs(qc))
+        # 1e-9: the exponential covariance's heavy-tailed frequencies round the phases of
+        # the field to a few ulps of |w| (as in the FV exponential-covariance level test)
+        assert abs(Qf[s] - qf) <= 1e-9 * scale
+        assert abs(Y[s] - (qf - qc)) <= 1e-9 * scale
+
+
 def test_qoi_choice_on_the_fv_path(orc):
     """The point QoI reads u(1/4, 1/4, 1/4) of the finite-volume solution as well."""
     ids = sample_ids(0, 1, 2)
