@@ -4,7 +4,6 @@
 #include <stddef.h>
 #include <stdarg.h>
 #include <stdio.h>
-#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -210,22 +209,9 @@ __global__ void k_level_stats(const double* __restrict__ Qf, const double* __res
 // one injected (the coarse grid's nodes are every other fine node). SPDE fields: each grid
 // solves its own discretisation of the SPDE with the white noise of the fine grid.
 struct LevelBatch {
-  static constexpr int kMaxChunks = 8;
   int nf = 0, nc = 0, B = 0, M = 0, prec = 0, cov = 0;
-  int chunks = 1;  // sample chunks whose fields overlap the previous chunks' solves
-  DevBuf ids, k0, kc, uf, uc, Q, cyc, rec, scratch, fscr;
+  DevBuf ids, k0, kc, uf, uc, Q, cyc, rec, scratch;
   size_t scratch_bytes = 0;
-  cudaStream_t side_ = nullptr;
-  cudaEvent_t ev_[kMaxChunks + 2] = {};
-
-  LevelBatch() = default;
-  LevelBatch(const LevelBatch&) = delete;
-  LevelBatch& operator=(const LevelBatch&) = delete;
-  ~LevelBatch() {
-    for (auto& e : ev_)
-      if (e) cudaEventDestroy(e);
-    if (side_) cudaStreamDestroy(side_);
-  }
 
   static size_t scratch_for(int B, int nf, int nc, const mlmc_field_cfg& fc, int prec, int accel) {
     size_t s = fc.cov == MLMC_COV_SPDE ? spde_scratch_bytes(B, nf) : field_scratch_bytes(B, fc.M, nf);
@@ -264,131 +250,67 @@ struct LevelBatch {
     MLMC_TRY(rec.alloc(sizeof(LevelRecord), st));
     MLMC_CUDA_TRY(cudaMemsetAsync(rec.get(), 0, sizeof(LevelRecord), st));
     MLMC_TRY(scratch.alloc(scratch_bytes, st));
-    chunks = level_chunks();
-    if (chunks > 1 && cov != MLMC_COV_SPDE && B > 1) {
-      const int bc = (B + chunks - 1) / chunks;
-      MLMC_TRY(fscr.alloc(field_scratch_bytes(bc, M, nf), st));
-      MLMC_CUDA_TRY(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
-      for (auto& e : ev_) MLMC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
     return MLMC_OK;
   }
 
-  // Sample chunks of a level batch (environment variable MLMC_LEVEL_CHUNKS, 1..8, read
-  // once; 1: the whole batch's field, then its solves).
-  static int level_chunks() {
-    static const int c = [] {
-      const char* e = getenv("MLMC_LEVEL_CHUNKS");
-      const int v = e ? atoi(e) : 1;
-      return v < 1 ? 1 : v > kMaxChunks ? kMaxChunks : v;
-    }();
-    return c;
-  }
-
   // b <= B samples with device ids; Qf/Qc/Y: device outputs of b entries (Qc, Y may be
-  // NULL). Folds the batch into the level record. With chunks > 1 (Fourier-feature fields)
-  // the fields of the batch's sample chunks are evaluated on a side stream while the
-  // previous chunks solve on `st`: the field is FP32-pipe work (double-float sums), the
-  // solves FP64-pipe work, and the two can share the SMs. Every sample's field and solve
-  // are independent of its chunk, and the chunks fold into the record in sample order, so
-  // the results are those of one batch bit for bit.
+  // NULL). Folds the batch into the level record.
   int run(const mlmc_field_cfg& fc, const mg_cfg& mc, const uint64_t* ids_dev, int b, double* Qf, double* Qc,
           double* Y, int* n_unconv, cudaStream_t st, int qoi = MLMC_QOI_MEAN) {
     const bool spde = fc.cov == MLMC_COV_SPDE;
     if (spde) {
       MLMC_TRY(spde_field_dev(fc, ids_dev, b, nf, nf, MLMC_F64, k0.get(), scratch.get(), st));
       if (nc) MLMC_TRY(spde_field_dev(fc, ids_dev, b, nc, nf, MLMC_F64, kc.get(), scratch.get(), st));
-      return solve_part(fc, mc, 0, b, Qf, Qc, Y, n_unconv, st, qoi);
-    }
-    const int nch = side_ ? (b < chunks ? b : chunks) : 1;
-    if (nch <= 1) {
+    } else {
       MLMC_TRY(field_eval_dev(fc, ids_dev, b, nf, MLMC_F64, k0.get(), scratch.get(), st));
-      return solve_part(fc, mc, 0, b, Qf, Qc, Y, n_unconv, st, qoi);
     }
-    const int bc = (b + nch - 1) / nch;
-    const size_t nf3 = cube(nf);
-    // the side stream starts after the work already on st (ids, buffers)
-    MLMC_CUDA_TRY(cudaEventRecord(ev_[kMaxChunks], st));
-    MLMC_CUDA_TRY(cudaStreamWaitEvent(side_, ev_[kMaxChunks], 0));
-    int rc = MLMC_OK;
-    for (int c = 0; c < nch && rc == MLMC_OK; ++c) {
-      const int off = c * bc, cnt = b - off < bc ? b - off : bc;
-      rc = field_eval_dev(fc, ids_dev + off, cnt, nf, MLMC_F64, k0.as<double>() + (size_t)off * nf3, fscr.get(),
-                          side_);
-      if (rc == MLMC_OK && cudaEventRecord(ev_[c], side_) != cudaSuccess) rc = MLMC_ERR_CUDA;
-    }
-    for (int c = 0; c < nch && rc == MLMC_OK; ++c) {
-      const int off = c * bc, cnt = b - off < bc ? b - off : bc;
-      if (cudaStreamWaitEvent(st, ev_[c], 0) != cudaSuccess) {
-        rc = MLMC_ERR_CUDA;
-        break;
-      }
-      rc = solve_part(fc, mc, off, cnt, Qf, Qc, Y, n_unconv, st, qoi);
-    }
-    // whatever happened, later work on st (the buffers' release included) waits for the side stream
-    cudaEventRecord(ev_[kMaxChunks + 1], side_);
-    cudaStreamWaitEvent(st, ev_[kMaxChunks + 1], 0);
-    return rc;
-  }
-
-  // Coarse and fine solves, QoIs and the record fold of samples [off, off + bc) of the
-  // batch, whose fine coefficient is in k0 at sample offset off.
-  int solve_part(const mlmc_field_cfg& fc, const mg_cfg& mc, int off, int b, double* Qf, double* Qc, double* Y,
-                 int* n_unconv, cudaStream_t st, int qoi) {
-    const bool spde = fc.cov == MLMC_COV_SPDE;
-    const size_t nf3 = cube(nf), nc3 = nc ? cube(nc) : 0;
-    double* kf = k0.as<double>() + (size_t)off * nf3;
-    double* kcs = (spde && nc) ? kc.as<double>() + (size_t)off * nc3 : nullptr;
-    double* ufp = uf.as<double>() + (size_t)off * nf3;
-    double* ucp = nc ? uc.as<double>() + (size_t)off * nc3 : nullptr;
-    double* qf = Qf + off;
-    double* y = Y ? Y + off : nullptr;
     MGSolveArgs a;
-    a.k0 = kf;
+    a.k0 = k0.as<double>();
     a.n_k0 = nf;
     a.f = nullptr;
     a.B = b;
     a.cfg = mc;
     int bad = 0;
-    int* cf = cyc.as<int>() + off;
-    int* cc = cyc.as<int>() + B + off;
-    double* qc = (Qc ? Qc : Q.as<double>() + B) + off;
+    int* cf = cyc.as<int>();
+    int* cc = cyc.as<int>() + B;
+    double* qc = Qc ? Qc : Q.as<double>() + B;
     if (nc) {
       // coarse solve first (its coefficient is the fine one injected); its solution,
       // interpolated, starts the fine solve (nested iteration, the first step of FMG)
-      MLMC_CUDA_TRY(cudaMemsetAsync(ucp, 0, (size_t)b * nc3 * sizeof(double), st));
+      MLMC_CUDA_TRY(cudaMemsetAsync(uc.get(), 0, (size_t)b * cube(nc) * sizeof(double), st));
       if (spde) {
-        a.k0 = kcs;
+        a.k0 = kc.as<double>();
         a.n_k0 = nc;
         a.st0 = 1;
       } else {
         a.st0 = 2;
       }
-      a.u = ucp;
+      a.u = uc.as<double>();
       a.n = nc;
       MLMC_TRY(mg_solve_dev(a, scratch.get(), st, nullptr, nullptr, &bad, cc, nullptr));
       *n_unconv += bad;
-      MLMC_TRY(qoi_any(qoi, ucp, nc, b, qc, scratch.get(), spde ? kcs : kf, spde ? nc : nf, spde ? 1 : 2, st));
-      MLMC_TRY(interpolate_dev(ucp, nf, b, ufp, st));
+      MLMC_TRY(qoi_any(qoi, uc.as<double>(), nc, b, qc, scratch.get(), spde ? kc.as<double>() : k0.as<double>(),
+                       spde ? nc : nf, spde ? 1 : 2, st));
+      MLMC_TRY(interpolate_dev(uc.as<double>(), nf, b, uf.as<double>(), st));
     } else {
-      MLMC_CUDA_TRY(cudaMemsetAsync(ufp, 0, (size_t)b * nf3 * sizeof(double), st));
+      MLMC_CUDA_TRY(cudaMemsetAsync(uf.get(), 0, (size_t)b * cube(nf) * sizeof(double), st));
     }
-    a.k0 = kf;
+    a.k0 = k0.as<double>();
     a.n_k0 = nf;
     a.st0 = 1;
-    a.u = ufp;
+    a.u = uf.as<double>();
     a.n = nf;
     bad = 0;
     MLMC_TRY(mg_solve_dev(a, scratch.get(), st, nullptr, nullptr, &bad, cf, nullptr));
     *n_unconv += bad;
-    MLMC_TRY(qoi_any(qoi, ufp, nf, b, qf, scratch.get(), kf, nf, 1, st));
+    MLMC_TRY(qoi_any(qoi, uf.as<double>(), nf, b, Qf, scratch.get(), k0.as<double>(), nf, 1, st));
     if (nc) {
       MLMC_LAUNCH("level_stats", b * 24.0, b * 10.0, st,
-                  (k_level_stats<<<1, 32, 0, st>>>(qf, qc, cf, cc, b, y, rec.as<LevelRecord>())));
+                  (k_level_stats<<<1, 32, 0, st>>>(Qf, qc, cf, cc, b, Y, rec.as<LevelRecord>())));
     } else {
-      if (Qc) MLMC_CUDA_TRY(cudaMemsetAsync(Qc + off, 0, (size_t)b * sizeof(double), st));
+      if (Qc) MLMC_CUDA_TRY(cudaMemsetAsync(Qc, 0, (size_t)b * sizeof(double), st));
       MLMC_LAUNCH("level_stats", b * 16.0, b * 10.0, st,
-                  (k_level_stats<<<1, 32, 0, st>>>(qf, nullptr, cf, nullptr, b, y, rec.as<LevelRecord>())));
+                  (k_level_stats<<<1, 32, 0, st>>>(Qf, nullptr, cf, nullptr, b, Y, rec.as<LevelRecord>())));
     }
     MLMC_CUDA_TRY(cudaGetLastError());
     return MLMC_OK;

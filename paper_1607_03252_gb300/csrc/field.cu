@@ -324,98 +324,6 @@ __global__ void __launch_bounds__(kFieldThreads) k_field_line(const float4* __re
     if (x0 + q < n) out[q] = (TOut)exp(scale * ((double)ah[q] + (double)al[q]));
 }
 
-// The sum split between the two pipes: of every chunk of MC features the first MCd go
-// through k_field_line's double-float arithmetic on the FP32 pipe and the others through
-// k_field's FP64 arithmetic (line factor Q_m = B_m[y] C_m[z] once per line, then two FP64
-// FMAs per node), which the FP64 pipe runs beside the FP32 work of the other warps. A
-// double-float node-feature costs ~24 FP32 operations (0.19 SM clocks at 128 per clock), an
-// FP64 one 2 FP64 FMAs (1 SM clock at 2 per clock), so about a fifth of the features goes to
-// the FP64 pipe. The two partial sums meet in FP64 at the end.
-template <typename TOut>
-__global__ void __launch_bounds__(kFieldThreads, 4) k_field_mix(const float4* __restrict__ tsplit,
-                                                              const double2* __restrict__ tab, int M, int n, int MC,
-                                                              int MCd, double scale, TOut* __restrict__ kout) {
-  extern __shared__ float4 sml[];
-  float4* sA = sml;                                  // [MC][kXC], double-float x-phasors
-  double2* sA64 = reinterpret_cast<double2*>(sml);  // the same slots, FP64 x-phasors
-  const int s = blockIdx.z;
-  const int x0 = blockIdx.x * kXC;
-  const size_t n2 = (size_t)n * n;
-  const size_t line = (size_t)blockIdx.y * kFieldThreads + threadIdx.x;
-  const bool valid = line < n2;
-  const int y = valid ? (int)(line % n) : 0, z = valid ? (int)(line / n) : 0;
-  const float4* Tx = tsplit + (size_t)s * 3 * M * n;
-  const float4* Ty = Tx + (size_t)M * n;
-  const float4* Tz = Ty + (size_t)M * n;
-  const double2* Tx64 = tab + (size_t)s * 3 * M * n;
-  const double2* Ty64 = Tx64 + (size_t)M * n;
-  const double2* Tz64 = Ty64 + (size_t)M * n;
-  float ah[kXC], al[kXC];
-  double a64[kXC];
-#pragma unroll
-  for (int q = 0; q < kXC; ++q) {
-    ah[q] = 0.f;
-    al[q] = 0.f;
-    a64[q] = 0.0;
-  }
-  for (int m0 = 0; m0 < M; m0 += MC) {
-    const int mc = min(MC, M - m0);
-    const int md = min(MCd, mc);
-    __syncthreads();
-    for (int t = threadIdx.x; t < mc * kXC; t += kFieldThreads) {
-      const int mm = t / kXC, xi = t - mm * kXC;
-      const int x = x0 + xi;
-      if (mm < md)
-        sA[t] = x < n ? Tx[(size_t)(m0 + mm) * n + x] : make_float4(0.f, 0.f, 0.f, 0.f);
-      else
-        sA64[t] = x < n ? Tx64[(size_t)(m0 + mm) * n + x] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-    for (int mm = 0; mm < md; ++mm) {
-      const float4 b = Ty[(size_t)(m0 + mm) * n + y];
-      const float4 c = Tz[(size_t)(m0 + mm) * n + z];
-      float rh, rl, ih, il, t1h, t1l, t2h, t2l;
-      df_mul(b.x, b.y, c.x, c.y, t1h, t1l);
-      df_mul(b.z, b.w, c.z, c.w, t2h, t2l);
-      df_add(t1h, t1l, -t2h, -t2l, rh, rl);
-      df_mul(b.x, b.y, c.z, c.w, t1h, t1l);
-      df_mul(b.z, b.w, c.x, c.y, t2h, t2l);
-      df_add(t1h, t1l, t2h, t2l, ih, il);
-#pragma unroll
-      for (int q = 0; q < kXC; ++q) {
-        const float4 a = sA[mm * kXC + q];
-        const float p1 = a.x * rh, e1 = fmaf(a.x, rh, -p1);
-        const float p2 = a.z * ih, e2 = fmaf(a.z, ih, -p2);
-        float th, tl;
-        two_sum(p1, -p2, th, tl);
-        float lw = (e1 - e2) + tl;
-        lw = fmaf(a.x, rl, lw);
-        lw = fmaf(a.y, rh, lw);
-        lw = fmaf(-a.z, il, lw);
-        lw = fmaf(-a.w, ih, lw);
-        float sh, se;
-        two_sum(ah[q], th, sh, se);
-        ah[q] = sh;
-        al[q] += se + lw;
-      }
-    }
-    for (int mm = md; mm < mc; ++mm) {
-      const double2 b = Ty64[(size_t)(m0 + mm) * n + y], c = Tz64[(size_t)(m0 + mm) * n + z];
-      const double qr = b.x * c.x - b.y * c.y, qi = b.x * c.y + b.y * c.x;
-#pragma unroll
-      for (int q = 0; q < kXC; ++q) {
-        const double2 a = sA64[mm * kXC + q];
-        a64[q] = fma(a.x, qr, fma(-a.y, qi, a64[q]));
-      }
-    }
-  }
-  if (!valid) return;
-  TOut* out = kout + (size_t)s * n2 * n + line * n + x0;
-#pragma unroll
-  for (int q = 0; q < kXC; ++q)
-    if (x0 + q < n) out[q] = (TOut)exp(scale * (((double)ah[q] + (double)al[q]) + a64[q]));
-}
-
 size_t field_scratch_bytes(int B, int M, int n) {
   return a256((size_t)B * M * 3 * sizeof(double)) + a256((size_t)B * M * sizeof(double)) +
          a256((size_t)B * 3 * M * n * sizeof(double2)) + a256((size_t)B * 3 * M * n * sizeof(float4));
@@ -425,7 +333,7 @@ int field_arith_default() {
   static const int a = [] {
     const char* e = getenv("MLMC_FIELD_ARITH");
     const int v = e ? atoi(e) : (int)kFieldDF32Line;
-    return v >= kFieldDF32Line && v <= kFieldMixLine ? v : (int)kFieldDF32Line;
+    return v >= kFieldDF32Line && v <= kFieldDF32 ? v : (int)kFieldDF32Line;
   }();
   return a;
 }
@@ -473,22 +381,6 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
     else
       MLMC_LAUNCH("field_f64", bytes, flops, st,
                   (k_field<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (float*)kout)));
-  } else if (arith == kFieldMixLine) {
-    MLMC_LAUNCH("phasors", nt * 32.0, nt * 4.0, st,
-                (k_split_x<<<blocks_for(nt, 256), 256, 0, st>>>(tab, nt, xsplit)));
-    const int MCl = cfg.M < 64 ? cfg.M : 64;
-    const int MCd = MCl - (MCl * 13 + 32) / 64;  // ~20% of each chunk to the FP64 pipe
-    dim3 gl((unsigned)((n + kXC - 1) / kXC), (unsigned)(((size_t)n * n + kFieldThreads - 1) / kFieldThreads),
-            (unsigned)B);
-    const size_t sml = (size_t)MCl * kXC * sizeof(float4);
-    if (dtype == MLMC_F64)
-      MLMC_LAUNCH("field_mix", bytes, flops, st,
-                  (k_field_mix<double><<<gl, kFieldThreads, sml, st>>>(xsplit, tab, cfg.M, n, MCl, MCd, scale,
-                                                                       (double*)kout)));
-    else
-      MLMC_LAUNCH("field_mix", bytes, flops, st,
-                  (k_field_mix<float><<<gl, kFieldThreads, sml, st>>>(xsplit, tab, cfg.M, n, MCl, MCd, scale,
-                                                                      (float*)kout)));
   } else if (arith == kFieldDF32Line) {
     MLMC_LAUNCH("phasors", nt * 32.0, nt * 4.0, st,
                 (k_split_x<<<blocks_for(nt, 256), 256, 0, st>>>(tab, nt, xsplit)));

@@ -11,12 +11,11 @@ namespace mlmc {
 size_t field_scratch_bytes(int B, int M, int n);
 
 // Arithmetic of the log k sum: double-float on the FP32 pipe with one (y, z) line per
-// thread (the default), the same with flattened outputs, FP64, or the line form with about
-// a fifth of the features in FP64 (both pipes busy).
-enum { kFieldDF32Line = 0, kFieldFP64 = 1, kFieldDF32 = 2, kFieldMixLine = 3 };
+// thread (the default), FP64, or double-float with flattened outputs.
+enum { kFieldDF32Line = 0, kFieldFP64 = 1, kFieldDF32 = 2 };
 
 // The arithmetic field_eval_dev uses by default: kFieldDF32Line, or the value of the
-// environment variable MLMC_FIELD_ARITH (0..3) read once.
+// environment variable MLMC_FIELD_ARITH (0..2) read once.
 int field_arith_default();
 
 // k_out[s][z][y][x] = exp(log k) at the n^3 nodes for the B ids in ids_dev (device).

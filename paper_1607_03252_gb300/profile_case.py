@@ -13,7 +13,7 @@ that every kernel class launches with the sizes of that grid. With --timing the 
 twice and the second run records CUDA events around every launch: per kernel class it
 prints launches, device time per launch and algorithmic GB/s, and the same for the field
 evaluation (Fourier features, or the SPDE sampler of Sec. 3.2), with its wall
-time (MLMC_FIELD_ARITH=0..3 selects the field's arithmetic). With --level
+time (MLMC_FIELD_ARITH=0..2 selects the field's arithmetic). With --level
 it instead runs mlmc_level_estimate for `batch` samples of that MLMC level (grids from n0;
 the precision, smoother and field as given, rtol 1e-10) and, with --timing, prints the
 per-class profile of a second run. With --fma-peak it prints the measured FP64 and FP32
