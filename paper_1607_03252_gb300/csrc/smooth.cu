@@ -31,6 +31,7 @@
 #include "common.cuh"
 #include "prof.cuh"
 #include "smooth.cuh"
+#include "bulk.cuh"
 
 namespace mlmc {
 namespace {
@@ -324,53 +325,6 @@ __global__ void __launch_bounds__(FusedLayout<T, BX, BY>::threads, sizeof(T) == 
 // Every mbarrier wait is bounded by a clock budget; on expiry the CTA records an error
 // word and leaves at the next barrier.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(smem_addr(b)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* b, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(smem_addr(b)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-// bounded wait: one non-blocking test, then waits while fewer than `budget` SM clocks
-// have passed (budget 0: give up at the first test that finds the phase incomplete)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, unsigned parity, long long budget) {
-  if (mbar_test_wait(b, parity)) return true;
-  const long long t0 = clock64();
-  while (clock64() - t0 < budget)
-    if (mbar_try_wait(b, parity)) return true;
-  return false;
-}
-// budget of the drain after an expired wait (the copies still in flight must land before
-// the CTA's shared memory is released): about one second of SM clock, whatever the
-// budget of the normal waits
-constexpr long long kDrainBudget = 2000000000LL;
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(b))
-      : "memory");
-}
-
 template <typename T, int BX, int BY>
 struct BulkLayout {
   static constexpr int W2 = BX + 4, H2 = BY + 4;
@@ -427,7 +381,7 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
   if (tid == 0) {
     for (int k = 0; k < kBulkSlots; ++k) mbar_init(&mbar[k], 1);
     *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    mbar_fence_init();
   }
   // row offsets of every slot start at 0 (a slot is read before its first staging only
   // where the value is unused, but its index must stay inside the staging buffer)
@@ -461,7 +415,7 @@ __global__ void __launch_bounds__(BulkLayout<T, BX, BY>::threads)
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    fence_proxy_async();
     __syncwarp();
     if (lane == 0) mbar_arrive_expect_tx(&mbar[slot], bytes);
     __syncwarp();

@@ -373,13 +373,13 @@ def test_nodal_smoother_reaches_the_same_solution(orc, accel):
 
 
 @pytest.mark.parametrize("accel", [mg.MLMC_ACCEL_NONE, mg.MLMC_ACCEL_CG])
-@pytest.mark.parametrize("n", [9, 17, 33, 65])
+@pytest.mark.parametrize("n", [9, 17, 33, 65, 129])
 def test_split_storage_equals_nodal_sweep_bitwise(orc, accel, n):
     """MLMC_SMOOTH_SPLIT runs the nodal-coefficient sweep, residual, transfers and coarse
     solve on colour-split storage with the same operations in the same order: iterates,
     cycle counts and residuals equal MLMC_SMOOTH_NODAL's bit for bit, samples stopping at
     different cycles."""
-    B = 4 if n < 65 else 2
+    B = 4 if n < 65 else 2  # 129^3: the sweeps stage their rows through shared memory
     ks = [orc.field(RUN_SEED, int(i), 256, 1.0 + 0.5 * s, 0.15, n) for s, i in enumerate(sample_ids(4, 0, B))]
     k = to_dev(np.stack(ks))
     out = {}
