@@ -181,6 +181,10 @@ __global__ void k_level_stats(const double* __restrict__ Qf, const double* __res
     __syncwarp();
     if (lane == 0) {
       const int cnt = b - i0 < 32 ? b - i0 : 32;
+      // cycle counts summed and maximised as integers (exact, the same values as adding
+      // them to the FP64 fields one by one), off the FP64 pipe that the fold waits on
+      long long sf = 0, sc = 0;
+      int mx = 0;
       for (int j = 0; j < cnt; ++j) {
         const double y = ys[j];
         const double yk = y - r.comp;
@@ -191,13 +195,16 @@ __global__ void k_level_stats(const double* __restrict__ Qf, const double* __res
         const double d = y - r.mean;
         r.mean += d / r.N;
         r.M2 += d * (y - r.mean);
-        r.cyc_f += cfs[j];
-        r.max_cyc = fmax(r.max_cyc, (double)cfs[j]);
+        sf += cfs[j];
+        mx = cfs[j] > mx ? cfs[j] : mx;
         if (cc) {
-          r.cyc_c += ccs[j];
-          r.max_cyc = fmax(r.max_cyc, (double)ccs[j]);
+          sc += ccs[j];
+          mx = ccs[j] > mx ? ccs[j] : mx;
         }
       }
+      r.cyc_f += (double)sf;
+      if (cc) r.cyc_c += (double)sc;
+      r.max_cyc = fmax(r.max_cyc, (double)mx);
     }
     __syncwarp();
   }

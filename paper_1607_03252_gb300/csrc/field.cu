@@ -237,10 +237,13 @@ __global__ void __launch_bounds__(kFieldThreads) k_field_df(const double2* __res
   }
 }
 
-// Double-float sum with one (y, z) line and kXC consecutive x-values per thread: the
+// Double-float sum with one (y, z) line and XC consecutive x-values per thread: the
 // line factor Q_m = B_m[y] C_m[z] is formed once per feature in double-float complex
-// arithmetic and reused for the kXC x-phasors, which every lane of a warp reads at the
-// same shared-memory address (broadcast). No FP64 instruction remains in the loop.
+// arithmetic and reused for the XC x-phasors, which every lane of a warp reads at the
+// same shared-memory address (broadcast). No FP64 instruction remains in the loop. A grid
+// of n = 2^p + 1 nodes per line runs as tiles of 8 x-values over x < n - 1 (8 divides
+// n - 1 from n = 9) and one of a single x-value for x = n - 1, so no thread computes
+// x-values past the line's end; every node's sum is the same whatever its tile.
 constexpr int kXC = 8;
 
 __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
@@ -258,13 +261,13 @@ __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, f
   sl = e - (sh - s);
 }
 
-template <typename TOut>
+template <typename TOut, int XC>
 __global__ void __launch_bounds__(kFieldThreads) k_field_line(const float4* __restrict__ tsplit, int M, int n, int MC,
-                                                               double scale, TOut* __restrict__ kout) {
+                                                               int xbase, double scale, TOut* __restrict__ kout) {
   extern __shared__ float4 sml[];
-  float4* sA = sml;  // [MC][kXC]
+  float4* sA = sml;  // [MC][XC]
   const int s = blockIdx.z;
-  const int x0 = blockIdx.x * kXC;
+  const int x0 = xbase + (int)blockIdx.x * XC;
   const size_t n2 = (size_t)n * n;
   const size_t line = (size_t)blockIdx.y * kFieldThreads + threadIdx.x;
   const bool valid = line < n2;
@@ -272,17 +275,17 @@ __global__ void __launch_bounds__(kFieldThreads) k_field_line(const float4* __re
   const float4* Tx = tsplit + (size_t)s * 3 * M * n;
   const float4* Ty = Tx + (size_t)M * n;
   const float4* Tz = Ty + (size_t)M * n;
-  float ah[kXC], al[kXC];
+  float ah[XC], al[XC];
 #pragma unroll
-  for (int q = 0; q < kXC; ++q) {
+  for (int q = 0; q < XC; ++q) {
     ah[q] = 0.f;
     al[q] = 0.f;
   }
   for (int m0 = 0; m0 < M; m0 += MC) {
     const int mc = min(MC, M - m0);
     __syncthreads();
-    for (int t = threadIdx.x; t < mc * kXC; t += kFieldThreads) {
-      const int mm = t / kXC, xi = t - mm * kXC;
+    for (int t = threadIdx.x; t < mc * XC; t += kFieldThreads) {
+      const int mm = t / XC, xi = t - mm * XC;
       const int x = x0 + xi;
       sA[t] = x < n ? Tx[(size_t)(m0 + mm) * n + x] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -299,8 +302,8 @@ __global__ void __launch_bounds__(kFieldThreads) k_field_line(const float4* __re
       df_mul(b.z, b.w, c.x, c.y, t2h, t2l);
       df_add(t1h, t1l, t2h, t2l, ih, il);
 #pragma unroll
-      for (int q = 0; q < kXC; ++q) {
-        const float4 a = sA[mm * kXC + q];  // same address in every lane: broadcast
+      for (int q = 0; q < XC; ++q) {
+        const float4 a = sA[mm * XC + q];  // same address in every lane: broadcast
         const float p1 = a.x * rh, e1 = fmaf(a.x, rh, -p1);
         const float p2 = a.z * ih, e2 = fmaf(a.z, ih, -p2);
         float th, tl;
@@ -320,8 +323,27 @@ __global__ void __launch_bounds__(kFieldThreads) k_field_line(const float4* __re
   if (!valid) return;
   TOut* out = kout + (size_t)s * n2 * n + line * n + x0;
 #pragma unroll
-  for (int q = 0; q < kXC; ++q)
+  for (int q = 0; q < XC; ++q)
     if (x0 + q < n) out[q] = (TOut)exp(scale * ((double)ah[q] + (double)al[q]));
+}
+
+// One launch of k_field_line<., XC> over `tiles` x-tiles from x = xbase; `share` is the
+// fraction of the field's nodes it evaluates (for the launch accounting).
+template <int XC>
+int field_line_launch(const float4* xsplit, int M, int n, int MC, int xbase, unsigned tiles, unsigned lines, int B,
+                      double scale, int dtype, void* kout, double bytes, double flops, cudaStream_t st,
+                      double share) {
+  const dim3 gl(tiles, lines, (unsigned)B);
+  const size_t sml = (size_t)MC * XC * sizeof(float4);
+  if (dtype == MLMC_F64)
+    MLMC_LAUNCH("field_df32", bytes * share, flops * share, st,
+                (k_field_line<double, XC><<<gl, kFieldThreads, sml, st>>>(xsplit, M, n, MC, xbase, scale,
+                                                                           (double*)kout)));
+  else
+    MLMC_LAUNCH("field_df32", bytes * share, flops * share, st,
+                (k_field_line<float, XC><<<gl, kFieldThreads, sml, st>>>(xsplit, M, n, MC, xbase, scale,
+                                                                          (float*)kout)));
+  return MLMC_OK;
 }
 
 size_t field_scratch_bytes(int B, int M, int n) {
@@ -385,15 +407,18 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
     MLMC_LAUNCH("phasors", nt * 32.0, nt * 4.0, st,
                 (k_split_x<<<blocks_for(nt, 256), 256, 0, st>>>(tab, nt, xsplit)));
     const int MCl = cfg.M < 64 ? cfg.M : 64;
-    dim3 gl((unsigned)((n + kXC - 1) / kXC), (unsigned)(((size_t)n * n + kFieldThreads - 1) / kFieldThreads),
-            (unsigned)B);
-    const size_t sml = (size_t)MCl * kXC * sizeof(float4);
-    if (dtype == MLMC_F64)
-      MLMC_LAUNCH("field_df32", bytes, flops, st,
-                  (k_field_line<double><<<gl, kFieldThreads, sml, st>>>(xsplit, cfg.M, n, MCl, scale, (double*)kout)));
+    const unsigned lines = (unsigned)(((size_t)n * n + kFieldThreads - 1) / kFieldThreads);
+    // x < n - 1 in tiles of 8 (of 4 on the 5-node grid), then x = n - 1
+    const int xt = (n - 1) % kXC == 0 ? kXC : 4;
+    const unsigned tiles = (unsigned)((n - 1) / xt);
+    if (xt == kXC)
+      MLMC_TRY(field_line_launch<kXC>(xsplit, cfg.M, n, MCl, 0, tiles, lines, B, scale, dtype, kout, bytes, flops, st,
+                                     (double)(n - 1) / n));
     else
-      MLMC_LAUNCH("field_df32", bytes, flops, st,
-                  (k_field_line<float><<<gl, kFieldThreads, sml, st>>>(xsplit, cfg.M, n, MCl, scale, (float*)kout)));
+      MLMC_TRY(field_line_launch<4>(xsplit, cfg.M, n, MCl, 0, tiles, lines, B, scale, dtype, kout, bytes, flops, st,
+                                   (double)(n - 1) / n));
+    MLMC_TRY(field_line_launch<1>(xsplit, cfg.M, n, MCl, n - 1, 1, lines, B, scale, dtype, kout, bytes, flops, st,
+                                 1.0 / n));
   } else {
     MLMC_LAUNCH("phasors", nt * 32.0, nt * 4.0, st,
                 (k_split_x<<<blocks_for(nt, 256), 256, 0, st>>>(tab, nt, xsplit)));
