@@ -16,6 +16,7 @@
 #include "field.cuh"
 #include "philox.cuh"
 #include "prof.cuh"
+#include "widen.cuh"
 
 namespace mlmc {
 
@@ -59,33 +60,44 @@ __global__ void k_features(const uint64_t* __restrict__ ids, int B, int M, uint6
   bph[t] = two_pi * U5;
 }
 
-// Phasor tables tab[s][axis][m][i] = (cos, sin) of (w_axis x_i (+ b_m on axis 0)).
+// Phasor tables tab[s][axis][m][i] = (cos, sin) of (w_axis x_i (+ b_m on axis 0)), and
+// the same pre-split for the double-float kernels, xs = (Re hi, Re lo, Im hi, Im lo). A
+// thread fills a run of kPhRun consecutive i of one (sample, axis, feature) row: the first
+// entry by sincos of its phase, the next ones by multiplying by the step e^{i w h} (one
+// sincos per run), so each entry costs one complex product instead of a sincos on the FP64
+// unit; over a run the products add a few ulps (below 2e-15 relative). The split is done
+// by the integer-pipe narrowing (hi = fl32(v), lo = fl32(v - hi), the difference exact in
+// FP64).
+constexpr int kPhRun = 8;
 __global__ void k_phasors(const double* __restrict__ w, const double* __restrict__ bph, int B, int M, int n,
-                          double h, double2* __restrict__ tab) {
-  const size_t total = (size_t)B * 3 * M * n;
+                          double h, double2* __restrict__ tab, float4* __restrict__ xs) {
+  const int runs = (n + kPhRun - 1) / kPhRun;
+  const size_t total = (size_t)B * 3 * M * runs;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t % n);
-    const size_t r = t / n;
+    const int run = (int)(t % runs);
+    const size_t r = t / runs;  // row (s, axis, m)
     const int m = (int)(r % M);
     const size_t r2 = r / M;
     const int axis = (int)(r2 % 3);
     const int s = (int)(r2 / 3);
     const size_t f = (size_t)s * M + m;
-    double ph = w[3 * f + axis] * ((double)i * h);
+    const double wa = w[3 * f + axis];
+    const int i0 = run * kPhRun;
+    double ph = wa * ((double)i0 * h);
     if (axis == 0) ph += bph[f];
-    double sn, cs;
+    double sn, cs, ds, dc;
     sincos(ph, &sn, &cs);
-    tab[t] = make_double2(cs, sn);
-  }
-}
-
-// The phasor tables of the double-float kernels, pre-split once: (Re hi, Re lo, Im hi,
-// Im lo), same [sample][axis][m][i] layout as the FP64 tables.
-__global__ void k_split_x(const double2* __restrict__ tab, size_t total, float4* __restrict__ xs) {
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const double2 v = tab[t];
-    const float xh = (float)v.x, yh = (float)v.y;
-    xs[t] = make_float4(xh, (float)(v.x - (double)xh), yh, (float)(v.y - (double)yh));
+    sincos(wa * h, &ds, &dc);
+    const int i1 = i0 + kPhRun < n ? i0 + kPhRun : n;
+    for (int i = i0; i < i1; ++i) {
+      const size_t o = r * n + i;
+      tab[o] = make_double2(cs, sn);
+      const float ch = narrow(cs), sh = narrow(sn);
+      xs[o] = make_float4(ch, narrow(cs - widen(ch)), sh, narrow(sn - widen(sh)));
+      const double c2 = cs * dc - sn * ds, s2 = sn * dc + cs * ds;
+      cs = c2;
+      sn = s2;
+    }
   }
 }
 
@@ -151,7 +163,7 @@ __global__ void __launch_bounds__(kFieldThreads) k_field(const double2* __restri
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// The same sum in double-float arithmetic on the FP32 pipe (GB300 runs FP32 at ~59x the
+// The same sum in double-float arithmetic on the FP32 pipe (GB300 runs FP32 at 64x the
 // FP64 rate). Every FP64 factor f is split into f = hi + lo (two floats, hi = fl32(f));
 // a term Re(A Q) = Ar Qr - Ai Qi becomes the exact FP32 products Arh Qrh and Aih Qih
 // (their rounding errors recovered by FMA), an exact TwoSum of the two, the four cross
@@ -379,8 +391,8 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
                                                                           cfg.ell, cfg.cov, w, bph)));
   const double h = 1.0 / (double)(n - 1);
   const size_t nt = (size_t)B * 3 * cfg.M * n;
-  MLMC_LAUNCH("phasors", nt * 16.0, nt * 40.0, st,
-              (k_phasors<<<blocks_for(nt, 256), 256, 0, st>>>(w, bph, B, cfg.M, n, h, tab)));
+  MLMC_LAUNCH("phasors", nt * 32.0, nt * 12.0, st,
+              (k_phasors<<<blocks_for(nt / kPhRun + 1, 256), 256, 0, st>>>(w, bph, B, cfg.M, n, h, tab, xsplit)));
   int LT = 2048 / n;
   if (LT < 1) LT = 1;
   if ((size_t)LT > (size_t)n * n) LT = n * n;
@@ -404,8 +416,6 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
       MLMC_LAUNCH("field_f64", bytes, flops, st,
                   (k_field<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (float*)kout)));
   } else if (arith == kFieldDF32Line) {
-    MLMC_LAUNCH("phasors", nt * 32.0, nt * 4.0, st,
-                (k_split_x<<<blocks_for(nt, 256), 256, 0, st>>>(tab, nt, xsplit)));
     const int MCl = cfg.M < 64 ? cfg.M : 64;
     const unsigned lines = (unsigned)(((size_t)n * n + kFieldThreads - 1) / kFieldThreads);
     // x < n - 1 in tiles of 8 (of 4 on the 5-node grid), then x = n - 1
@@ -420,8 +430,6 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
     MLMC_TRY(field_line_launch<1>(xsplit, cfg.M, n, MCl, n - 1, 1, lines, B, scale, dtype, kout, bytes, flops, st,
                                  1.0 / n));
   } else {
-    MLMC_LAUNCH("phasors", nt * 32.0, nt * 4.0, st,
-                (k_split_x<<<blocks_for(nt, 256), 256, 0, st>>>(tab, nt, xsplit)));
     if (dtype == MLMC_F64)
       MLMC_LAUNCH("field_df32", bytes, flops, st,
                   (k_field_df<double><<<grid, kFieldThreads, smem, st>>>(tab, xsplit, cfg.M, n, LT, MC, scale,
