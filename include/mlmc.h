@@ -130,10 +130,11 @@ typedef struct {
                                     FP32 correction cycles (MLMC_PREC_MIXED) the sweep is
                                     MLMC_SMOOTH_NODAL's (bit for bit the same iterates; 2.5
                                     instead of 4 words per node at cache-line granularity); in
-                                    FP64 stationary cycles (MLMC_ACCEL_NONE) it is the stored-face
-                                    sweep of MLMC_SMOOTH_TWO_PASS (bit for bit the same iterates,
-                                    cycles and residuals; 5 instead of ~7 words per node and
-                                    pass). Finite volumes and n <= 1025 only. Chosen for the
+                                    FP64 stationary and FMG cycles (MLMC_ACCEL_NONE, _FMG; finite
+                                    volumes or P1 elements) it is the stored-face sweep of
+                                    MLMC_SMOOTH_TWO_PASS (bit for bit the same iterates, cycles
+                                    and residuals; 5 instead of ~7 words per node and pass).
+                                    n <= 1025 only. Chosen for the
                                     finest grid, it applies to every grid of the hierarchy; on a
                                     coarser grid alone, or where it does not apply, it means
                                     MLMC_SMOOTH_NODAL (FP32) or MLMC_SMOOTH_TWO_PASS (FP64). */
@@ -538,8 +539,8 @@ typedef struct {
  * mlmc_autotune -- picks the smoother implementation (two-pass on stored faces, two-pass
  * on the nodal coefficient in the plain or the colour-split storage, or fused with 32x8,
  * 32x16 or 64x8 tiles staged by cp.async or by TMA bulk copies: 9 candidates for FP32
- * correction cycles on finite volumes; 8 for FP64 stationary cycles on finite volumes
- * (the colour-split stored-face sweep, no nodal-coefficient sweep); 7 otherwise) and the sweep count
+ * correction cycles on finite volumes; 8 for FP64 stationary or FMG cycles (the
+ * colour-split stored-face sweep, no nodal-coefficient sweep); 7 for FP64 CG) and the sweep count
  * nu in {1,2,3} of V(nu, nu) for MLMC level
  * `level` under cfg (no counterpart in the paper; the paper fixes its cycle, Sec. 7.1).
  * Each candidate runs the whole level pipeline on the batched engine

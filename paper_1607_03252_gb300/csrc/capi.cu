@@ -633,12 +633,12 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   const bool fixed_nu = cfg->mg.nu1 > 0 && cfg->mg.nu1 == cfg->mg.nu2;
   const int nu_lo = fixed_nu ? cfg->mg.nu1 : 1, nu_hi = fixed_nu ? cfg->mg.nu1 : 3;
   // the nodal-coefficient sweeps exist only in FP32 correction cycles on finite volumes;
-  // the colour-split storage there and in FP64 stationary cycles on finite volumes
+  // the colour-split storage there and in FP64 stationary and FMG cycles
   const bool fv = cfg->mg.disc == MLMC_DISC_FV, mixed = cfg->mg.precision == MLMC_PREC_MIXED;
   int cand[9], n_sm = 0;
   for (int si = 0; si < 9; ++si) {
     if (smoothers[si] == MLMC_SMOOTH_NODAL && !(fv && mixed)) continue;
-    if (smoothers[si] == MLMC_SMOOTH_SPLIT && !(fv && (mixed || cfg->mg.accel == MLMC_ACCEL_NONE))) continue;
+    if (smoothers[si] == MLMC_SMOOTH_SPLIT && !(mixed ? fv : cfg->mg.accel != MLMC_ACCEL_CG)) continue;
     cand[n_sm++] = smoothers[si];
   }
   for (int nu = nu_lo; nu <= nu_hi; ++nu)

@@ -62,6 +62,13 @@ __device__ __forceinline__ unsigned split_index(int n, int x, int y, int z) {
   return (unsigned)((x + y + z) & 1) * (unsigned)(n * n * P) + (unsigned)((z * n + y) * P + (x >> 1));
 }
 
+// Index of node (x, y, z) of sample s of an n^3 grid in the plain or (SPLIT) the
+// colour-split storage.
+template <bool SPLIT>
+__device__ __forceinline__ size_t node_at(int n, int s, int x, int y, int z) {
+  return SPLIT ? (size_t)s * split_elems(n) + split_index(n, x, y, z)
+               : (((size_t)s * n + z) * n + y) * n + x;
+}
 
 // Carves 256-byte aligned pieces; with base == nullptr it only measures.
 struct Carver {
@@ -1116,6 +1123,7 @@ __global__ void __launch_bounds__(128) k_prolong_blk_split(const T* __restrict__
 }
 
 // g = h^2 f (f == NULL: h^2) on interior nodes, 0 on the boundary; u boundary := 0.
+template <bool SPLIT = false>
 __global__ void k_prepare(int n, int B, double h2, const double* __restrict__ f, double* __restrict__ g,
                           double* __restrict__ u) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;  // node of the plane
@@ -1124,9 +1132,9 @@ __global__ void k_prepare(int n, int B, double h2, const double* __restrict__ f,
   const size_t n3 = (size_t)n * n * n;
   for (int zz = blockIdx.y; zz < B * n; zz += gridDim.y) {
     const int s = zz / n, z = zz - s * n;
-    const size_t t = (size_t)s * n3 + (size_t)(z * n * n + q);
+    const size_t tp = (size_t)s * n3 + (size_t)(z * n * n + q), t = SPLIT ? node_at<true>(n, s, x, y, z) : tp;
     const bool in = x > 0 && y > 0 && z > 0 && x < n - 1 && y < n - 1 && z < n - 1;
-    g[t] = in ? h2 * (f ? f[t] : 1.0) : 0.0;
+    g[t] = in ? h2 * (f ? f[tp] : 1.0) : 0.0;
     if (!in) u[t] = 0.0;
   }
 }
@@ -1228,51 +1236,46 @@ __global__ void k_faces_fe(const double* __restrict__ k0, int n0, int st0, int n
 // fine node with odd coordinates d (a 0/1 vector) is the midpoint of the coarse edge from
 // c0 = (f - d) / 2 to c0 + d (a mesh edge: every direction e_a, e_a + e_b, (1,1,1) is
 // one), so it takes the mean of the two; a node with d = 0 is a coarse node.
-template <typename T>
+template <typename T, bool SPLIT = false>
 __global__ void k_prolong_p1(int nf, int B, const T* __restrict__ ec, T* __restrict__ u,
                              const int* __restrict__ active) {
   const int m = nf - 2, nc = (nf + 1) / 2;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;  // interior node of the plane
   if (q >= m * m) return;
   const int y = 1 + q / m, x = 1 + q - (y - 1) * m;
-  const size_t nf3 = (size_t)nf * nf * nf, nc3 = (size_t)nc * nc * nc;
   for (int zz = blockIdx.y; zz < B * m; zz += gridDim.y) {
     const int s = zz / m, z = 1 + zz - s * m;
     if (active && !active[s]) continue;
     const int dx = x & 1, dy = y & 1, dz = z & 1;
-    const T* e = ec + (size_t)s * nc3;
-    const size_t c0 = ((size_t)((z - dz) >> 1) * nc + (size_t)((y - dy) >> 1)) * nc + (size_t)((x - dx) >> 1);
-    T v = e[c0];
-    if (dx | dy | dz) v = T(0.5) * (v + e[c0 + ((size_t)dz * nc + dy) * nc + dx]);
-    u[(size_t)s * nf3 + ((size_t)z * nf + y) * nf + x] += v;
+    const int X0 = (x - dx) >> 1, Y0 = (y - dy) >> 1, Z0 = (z - dz) >> 1;
+    T v = ec[node_at<SPLIT>(nc, s, X0, Y0, Z0)];
+    if (dx | dy | dz) v = T(0.5) * (v + ec[node_at<SPLIT>(nc, s, X0 + dx, Y0 + dy, Z0 + dz)]);
+    u[node_at<SPLIT>(nf, s, x, y, z)] += v;
   }
 }
 
 // Its transpose on interior coarse nodes, scaled for the coarse h^2-scaled system:
 // g_c = (h / h_c) P^T r = (1/2) (r(2c) + (1/2) sum over the 14 mesh-edge directions d of
 // r(2c + d)) (the fine residual r is zero on the boundary).
-template <typename T>
+template <typename T, bool SPLIT = false>
 __global__ void k_restrict_p1(int nf, int B, const T* __restrict__ r, T* __restrict__ gc,
                               const int* __restrict__ active) {
   const int nc = (nf + 1) / 2, mc = nc - 2;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;  // interior coarse node of the plane
   if (q >= mc * mc) return;
   const int Y = 1 + q / mc, X = 1 + q - (Y - 1) * mc;
-  const size_t nf3 = (size_t)nf * nf * nf, nc3 = (size_t)nc * nc * nc, nf2 = (size_t)nf * nf;
   for (int zz = blockIdx.y; zz < B * mc; zz += gridDim.y) {
     const int s = zz / mc, Z = 1 + zz - s * mc;
     if (active && !active[s]) continue;
-    const T* rb = r + (size_t)s * nf3;
-    const size_t f = (size_t)(2 * Z) * nf2 + (size_t)(2 * Y) * nf + 2 * X;
-    const size_t dx = 1, dy = nf, dz = nf2;
-    T acc = rb[f - dx] + rb[f + dx];
-    acc += rb[f - dy] + rb[f + dy];
-    acc += rb[f - dz] + rb[f + dz];
-    acc += rb[f - dx - dy] + rb[f + dx + dy];
-    acc += rb[f - dy - dz] + rb[f + dy + dz];
-    acc += rb[f - dx - dz] + rb[f + dx + dz];
-    acc += rb[f - dx - dy - dz] + rb[f + dx + dy + dz];
-    gc[(size_t)s * nc3 + ((size_t)Z * nc + Y) * nc + X] = T(0.5) * rb[f] + T(0.25) * acc;
+    auto R = [&](int dx, int dy, int dz) { return r[node_at<SPLIT>(nf, s, 2 * X + dx, 2 * Y + dy, 2 * Z + dz)]; };
+    T acc = R(-1, 0, 0) + R(1, 0, 0);
+    acc += R(0, -1, 0) + R(0, 1, 0);
+    acc += R(0, 0, -1) + R(0, 0, 1);
+    acc += R(-1, -1, 0) + R(1, 1, 0);
+    acc += R(0, -1, -1) + R(0, 1, 1);
+    acc += R(-1, 0, -1) + R(1, 0, 1);
+    acc += R(-1, -1, -1) + R(1, 1, 1);
+    gc[node_at<SPLIT>(nc, s, X, Y, Z)] = T(0.5) * R(0, 0, 0) + T(0.25) * acc;
   }
 }
 
@@ -1831,13 +1834,26 @@ void vcycle_split64(Hier<T>& H, int j, int nu1, int nu2, cudaStream_t st) {
   MLMC_LAUNCH(prof::sized("residual_split_f64", v.n), Ba * interior(v.n) * 7.0 * W, Ba * interior(v.n) * 14.0, st,
               MLMC_SPLIT_DISPATCH(v.n, (k_residual_split64<LG><<<dim3(pairs, (unsigned)(2 * m), (unsigned)B), 128, 0,
                                                                   st>>>(Kx, Ky, Kz, D, g, u, r, act))));
-  MLMC_LAUNCH(Names<T>::restrict_, Ba * ((double)v.n3 + (double)w.n3) * W, Ba * interior(w.n) * 54.0, st,
-              MLMC_SPLIT_DISPATCH(v.n, (k_restrict_split<LG, double><<<dim3((unsigned)(((w.n - 2) * (w.n - 2) + 127) /
-                                                                                    128),
-                                                                            (unsigned)(w.n - 2), (unsigned)B), 128,
-                                                                       0, st>>>(r, (double*)(void*)w.g, act))));
+  if (H.p1)
+    MLMC_LAUNCH("restrict_p1", Ba * ((double)v.n3 + (double)w.n3) * W, Ba * interior(w.n) * 16.0, st,
+                (k_restrict_p1<double, true><<<plane_grid((w.n - 2) * (w.n - 2), (long long)B * (w.n - 2)),
+                                               kPlaneThreads, 0, st>>>(v.n, B, r, (double*)(void*)w.g, act)));
+  else
+    MLMC_LAUNCH(Names<T>::restrict_, Ba * ((double)v.n3 + (double)w.n3) * W, Ba * interior(w.n) * 54.0, st,
+                MLMC_SPLIT_DISPATCH(v.n, (k_restrict_split<LG, double><<<dim3((unsigned)(((w.n - 2) * (w.n - 2) +
+                                                                                       127) / 128),
+                                                                              (unsigned)(w.n - 2), (unsigned)B),
+                                                                         128, 0, st>>>(r, (double*)(void*)w.g,
+                                                                                       act))));
   cudaMemsetAsync(w.u, 0, (size_t)B * split_elems(w.n) * sizeof(T), st);
   vcycle(H, j + 1, nu1, nu2, st);
+  if (H.p1) {
+    MLMC_LAUNCH("prolong_p1", Ba * (2.0 * (double)v.n3 + (double)w.n3) * W, Ba * interior(v.n) * 1.5, st,
+                (k_prolong_p1<double, true><<<plane_grid(m * m, (long long)B * m), kPlaneThreads, 0, st>>>(
+                    v.n, B, (const double*)(const void*)w.u, u, act)));
+    smooth(nu2);
+    return;
+  }
   MLMC_LAUNCH(prof::sized("prolong_split_f64", v.n), Ba * (2.0 * (double)v.n3 + (double)w.n3) * W,
               Ba * interior(v.n) * 4.375, st,
               MLMC_SPLIT_DISPATCH(v.n, (k_prolong_blk_split<LG, double><<<dim3((unsigned)(((w.n - 1) * (w.n - 1) +
@@ -2598,10 +2614,10 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
   {
     int sm0 = a.cfg.smoother;
     resolve_tuning(a.n, a.cfg.precision, &sm0, &nu1, &nu2);
-    // FP32 correction cycles (mixed) or FP64 stationary cycles
-    // (the split kernels are instantiated for n = 5 .. 1025)
-    H.split = !use_cta && a.cfg.disc == MLMC_DISC_FV && sm0 == MLMC_SMOOTH_SPLIT && a.n <= 1025 &&
-              (mixed || (!cg && !fmg));
+    // FP32 correction cycles on finite volumes (mixed), or FP64 stationary and FMG cycles
+    // on finite volumes or P1 elements (the split kernels are instantiated for n = 5 .. 1025)
+    H.split = !use_cta && sm0 == MLMC_SMOOTH_SPLIT && a.n <= 1025 &&
+              (mixed ? a.cfg.disc == MLMC_DISC_FV : !cg);
   }
   // operators of every level (k injected from k0); colour-split grids need no faces
   // except on the coarsest grid (its dense solve)
@@ -2614,10 +2630,22 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
       if (j < H.L - 1) {
         if constexpr (sizeof(T) == 8) {
           // FP64: stored faces, D and 1/D in the split storage (the coarsest grid keeps the
-          // plain faces its dense factorisation reads)
-          MLMC_LAUNCH(Names<T>::faces, B * (double)v.n3 * (8.0 + 3 * W), B * (double)v.n3 * 12.0, st,
-                      (k_faces_split<<<gb, kPlaneThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, (double*)v.Kx,
-                                                                    (double*)v.Ky, (double*)v.Kz)));
+          // plain faces its dense factorisation reads); P1 faces are assembled in the plain
+          // layout into the level's spare arrays and copied over
+          if (a.cfg.disc == MLMC_DISC_FE) {
+            double* t[3] = {(double*)(void*)v.u2, (double*)(void*)v.r, (double*)(void*)v.u};
+            MLMC_LAUNCH("faces_fe", B * (double)v.n3 * (8.0 + 3 * W), B * (double)v.n3 * 36.0, st,
+                        (k_faces_fe<double><<<gb, kPlaneThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, t[0], t[1],
+                                                                          t[2])));
+            double* K[3] = {(double*)(void*)v.Kx, (double*)(void*)v.Ky, (double*)(void*)v.Kz};
+            for (int d = 0; d < 3; ++d)
+              MLMC_LAUNCH("split_copy", B * (double)v.n3 * 16.0, 0.0, st,
+                          (k_split_copy<double, true><<<gb, kPlaneThreads, 0, st>>>(v.n, B, t[d], K[d])));
+          } else {
+            MLMC_LAUNCH(Names<T>::faces, B * (double)v.n3 * (8.0 + 3 * W), B * (double)v.n3 * 12.0, st,
+                        (k_faces_split<<<gb, kPlaneThreads, 0, st>>>(a.k0, a.n_k0, stride, v.n, B, (double*)v.Kx,
+                                                                      (double*)v.Ky, (double*)v.Kz)));
+          }
           MLMC_LAUNCH(Names<T>::diag, B * (double)v.n3 * 5 * W, B * (double)v.n3 * 6.0, st,
                       (k_diag_split<<<gb, kPlaneThreads, 0, st>>>(v.n, B, (const double*)v.Kx, (const double*)v.Ky,
                                                                    (const double*)v.Kz, (double*)v.D,
@@ -2827,21 +2855,38 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     for (int j = 1; j < H.L; ++j) {
       Level<T>& v = H.lv[j];
       const double hj = 1.0 / (double)(v.n - 1);
-      MLMC_LAUNCH("prepare", B * (double)v.n3 * 8.0, B * (double)v.n3, st,
-                  (k_prepare<<<plane_grid(v.n * v.n, (long long)B * v.n), kPlaneThreads, 0, st>>>(
-                      v.n, B, hj * hj, nullptr, (double*)v.g, (double*)v.u)));
+      if (H.split)
+        MLMC_LAUNCH("prepare", B * (double)v.n3 * 8.0, B * (double)v.n3, st,
+                    (k_prepare<true><<<plane_grid(v.n * v.n, (long long)B * v.n), kPlaneThreads, 0, st>>>(
+                        v.n, B, hj * hj, nullptr, (double*)v.g, (double*)v.u)));
+      else
+        MLMC_LAUNCH("prepare", B * (double)v.n3 * 8.0, B * (double)v.n3, st,
+                    (k_prepare<<<plane_grid(v.n * v.n, (long long)B * v.n), kPlaneThreads, 0, st>>>(
+                        v.n, B, hj * hj, nullptr, (double*)v.g, (double*)v.u)));
     }
     vcycle(H, H.L - 1, nu1, nu2, st);
     for (int j = H.L - 2; j >= 0; --j) {
       Level<T>& v = H.lv[j];
       Level<T>& w = H.lv[j + 1];
       const int m = v.n - 2;
-      MLMC_CUDA_TRY(cudaMemsetAsync(v.u, 0, (size_t)B * v.n3 * sizeof(T), st));
-      if (H.p1)
+      MLMC_CUDA_TRY(cudaMemsetAsync(v.u, 0, (size_t)B * (H.split ? split_elems(v.n) : v.n3) * sizeof(T), st));
+      if (H.p1 && H.split)
+        MLMC_LAUNCH("prolong_p1", B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 1.5, st,
+                    (k_prolong_p1<T, true><<<plane_grid(m * m, (long long)B * m), kPlaneThreads, 0, st>>>(
+                        v.n, B, w.u, v.u, H.active)));
+      else if (H.p1)
         MLMC_LAUNCH("prolong_p1", B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 1.5, st,
                     (k_prolong_p1<T><<<plane_grid(m * m, (long long)B * m), kPlaneThreads, 0, st>>>(
                         v.n, B, w.u, v.u, H.active)));
-      else
+      else if (H.split) {
+        if constexpr (sizeof(T) == 8)
+          MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
+                      MLMC_SPLIT_DISPATCH(v.n, (k_prolong_blk_split<LG, double><<<
+                                                   dim3((unsigned)(((w.n - 1) * (w.n - 1) + 127) / 128),
+                                                        (unsigned)(w.n - 1), (unsigned)B),
+                                                   128, 0, st>>>((const double*)(const void*)w.u,
+                                                                 (double*)(void*)v.u, H.active))));
+      } else
         MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
                     (k_prolong_blk<T><<<plane_grid((w.n - 1) * (w.n - 1), (long long)B * (w.n - 1)), 128, 0, st>>>(
                         v.n, B, w.u, v.u, H.active)));
@@ -2853,9 +2898,16 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
     MLMC_CUDA_TRY(cudaMemsetAsync(H.n_active, 0, sizeof(int), st));
     int zs = 0;
     const dim3 rz = zmarch_grid(a.n, B, &zs);
-    MLMC_LAUNCH("residual_norm_f64", B * interior(a.n) * 6.0 * 8, B * interior(a.n) * 16.0, st,
-                (k_residual_z<T, T, T, T><<<rz, 128, 0, st>>>(a.n, zs, l0.Kx, l0.Ky, l0.Kz, l0.D, l0.g, l0.u,
-                                                              nullptr, H.partial, H.active)));
+    if (H.split)
+      MLMC_LAUNCH("residual_norm_f64", B * interior(a.n) * 6.0 * 8, B * interior(a.n) * 16.0, st,
+                  (k_residual_norm_split<<<rz, 128, 0, st>>>(a.n, zs, (const double*)l0.Kx, (const double*)l0.Ky,
+                                                             (const double*)l0.Kz, (const double*)l0.D,
+                                                             (const double*)l0.g, (const double*)l0.u, H.partial,
+                                                             H.active)));
+    else
+      MLMC_LAUNCH("residual_norm_f64", B * interior(a.n) * 6.0 * 8, B * interior(a.n) * 16.0, st,
+                  (k_residual_z<T, T, T, T><<<rz, 128, 0, st>>>(a.n, zs, l0.Kx, l0.Ky, l0.Kz, l0.D, l0.g, l0.u,
+                                                                nullptr, H.partial, H.active)));
     MLMC_LAUNCH("norm_update", B * H.NBz * 8.0, B * H.NBz * 1.0, st,
                 (k_norm_update<<<sb, 128, 0, st>>>(B, H.NBz, H.partial, H.g2, H.relres, H.cycles, H.active, 1, 0,
                                                    0.0, maxc, H.n_active)));

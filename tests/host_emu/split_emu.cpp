@@ -15,7 +15,7 @@
 //     out.bin  float64, each plain then split mapped back: Kx, Ky, Kz, D, 1/D, u after a
 //              red and a black pass, r~, then u + P ec of k_prolong against the block
 //              form (plain; split mapped back; FP32 widened), FW(r) (B nc^3), u through
-//              the plain -> split -> plain copies
+//              the plain -> split -> plain copies, u + P1 ec, the P1 restriction (B nc^3)
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -276,6 +276,24 @@ static int split64(char** argv) {
   std::vector<double> back(B * n3, nan);
   launch(pgrid, dim3(T), [&] { mlmc::k_split_copy<double, false>(n, B, us.data(), back.data()); });
   emit(from_split(us, perm), back);
+  // the P1 transfers of the finite-element path, plain and colour-split
+  {
+    std::vector<double> pl = u, ps1 = to_split(u, perm, B * ns);
+    const std::vector<double> ecs1 = to_split(ec, permc, B * nsc);
+    launch(dim3((unsigned)((m * m + T - 1) / T), (unsigned)(B * m)), dim3(T),
+           [&] { mlmc::k_prolong_p1<double, false>(n, B, ec.data(), pl.data(), nullptr); });
+    launch(dim3((unsigned)((m * m + T - 1) / T), (unsigned)(B * m)), dim3(T),
+           [&] { mlmc::k_prolong_p1<double, true>(n, B, ecs1.data(), ps1.data(), nullptr); });
+    emit(pl, from_split(ps1, perm));
+    const int mc = nc - 2;
+    std::vector<double> gp(B * nc3, 0.0), gsp(B * nsc, 0.0);
+    const std::vector<double> rsp = to_split(r, perm, B * ns);
+    launch(dim3((unsigned)((mc * mc + T - 1) / T), (unsigned)(B * mc)), dim3(T),
+           [&] { mlmc::k_restrict_p1<double, false>(n, B, r.data(), gp.data(), nullptr); });
+    launch(dim3((unsigned)((mc * mc + T - 1) / T), (unsigned)(B * mc)), dim3(T),
+           [&] { mlmc::k_restrict_p1<double, true>(n, B, rsp.data(), gsp.data(), nullptr); });
+    emit(gp, from_split(gsp, permc));
+  }
   FILE* fo = std::fopen(argv[6], "wb");
   std::fwrite(out.data(), sizeof(double), out.size(), fo);
   std::fclose(fo);

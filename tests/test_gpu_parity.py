@@ -437,6 +437,29 @@ def test_split_storage_fp64_fixed_cycles_from_a_nonzero_guess(orc):
     assert not np.array_equal(res[0][0], u0)
 
 
+@pytest.mark.parametrize("disc,accel", [(mg.MLMC_DISC_FE, mg.MLMC_ACCEL_FMG), (mg.MLMC_DISC_FE, mg.MLMC_ACCEL_NONE),
+                                         (mg.MLMC_DISC_FV, mg.MLMC_ACCEL_FMG)])
+@pytest.mark.parametrize("n", [17, 65])
+def test_split_storage_fe_and_fmg_equal_two_pass_bitwise(orc, disc, accel, n):
+    """P1 elements (faces assembled plain and copied into the split storage, P1 transfers
+    on split storage) and the FMG cycle (every grid's right-hand side, interpolation and
+    cycles on split storage): the iterate and residual of MLMC_SMOOTH_TWO_PASS bit for bit."""
+    B = 3
+    k = to_dev(np.stack([orc.field(RUN_SEED, int(i), 64, 1.0, 0.3, n) for i in sample_ids(2, 90, B)]))
+    fmg = accel == mg.MLMC_ACCEL_FMG
+    out = {}
+    for sm in (mg.MLMC_SMOOTH_TWO_PASS, mg.MLMC_SMOOTH_SPLIT):
+        u = torch.zeros_like(k)
+        cfg = mg.mg_cfg(4 if fmg else 2, 4 if fmg else 2, 0.0 if fmg else 1e-10, 2 if fmg else 200,
+                        mg.MLMC_PREC_F64, sm, accel, disc, engine=mg.MLMC_ENGINE_BATCHED)
+        cyc, rel, st = mg.mg_solve_batch(cfg, k, u)
+        assert st == 0
+        out[sm] = (u.cpu().numpy(), cyc, rel)
+    a, b = out[mg.MLMC_SMOOTH_TWO_PASS], out[mg.MLMC_SMOOTH_SPLIT]
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert np.array_equal(a[0], b[0])
+
+
 def test_split_storage_fp64_level_estimate_matches_oracle(orc):
     level, ids = 2, sample_ids(2, 30, 3)
     cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.2, 256, n0=17, rtol=1e-11, smoother=mg.MLMC_SMOOTH_SPLIT,

@@ -25,6 +25,7 @@ def _cut(text, start, end):
 
 
 def _host(text):
+    text = text.replace("__host__ __device__ __forceinline__", "static inline")
     text = text.replace("__device__ __forceinline__", "static inline").replace("__device__", "static")
     text = text.replace("__global__", "static").replace("__restrict__", "")
     while "__launch_bounds__(" in text:
@@ -48,6 +49,7 @@ def emu(tmp_path_factory):
     parts = [
         _cut(philox, "__device__ __forceinline__ void philox10(", "}  // namespace mlmc"),
         _cut(spde, "__device__ __forceinline__ float log_series(float s) {", "// One colour of red-black Gauss-Seidel"),
+        _cut(mgcu, "__host__ __device__ __forceinline__ int split_pitch(int n)", "// Carves 256-byte"),
         _cut(mgcu, "template <typename T>\n__global__ void k_faces_fe(", "// Q[s] = u(1/4, 1/4, 1/4)"),
     ]
     d = tmp_path_factory.mktemp("kemu")

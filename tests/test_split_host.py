@@ -71,6 +71,7 @@ def emu(tmp_path_factory):
         _cut(mgcu, "// One colour of a red-black sweep: threads enumerate", "// Reciprocal nodal coefficient rho"),
         _cut(mgcu, "template <typename T>\n__global__ void k_nodal_k(", "// Blocks per sample of the deterministic"),
         _cut(mgcu, "// r~ = g - D u + sum K u_q on interior nodes (0 on the boundary)", "inline dim3 zmarch_grid"),
+        _cut(mgcu, "template <typename T, bool SPLIT = false>\n__global__ void k_prolong_p1(", "// Q[s] = u(1/4, 1/4, 1/4)"),
         _cut(mgcu, "template <typename T, bool SPLIT_OUT = false>\n__global__ void k_restrict(", "// g = h^2 f (f == NULL"),
         "}  // namespace mlmc",
     ]
@@ -153,8 +154,8 @@ def test_split64_kernels_equal_plain_kernels_bitwise(emu, n, B):
     out = np.fromfile(dst, dtype=np.float64)
     n3, nc3 = B * n ** 3, B * nc ** 3
     names = ["Kx", "Ky", "Kz", "D", "1/D", "sweep", "residual", "block prolongation", "block prolongation, split",
-             "block prolongation, FP32", "restriction", "copies"]
-    sizes = [nc3 if name == "restriction" else n3 for name in names]
+             "block prolongation, FP32", "restriction", "copies", "P1 prolongation", "P1 restriction"]
+    sizes = [nc3 if name in ("restriction", "P1 restriction") else n3 for name in names]
     off, got = 0, {}
     for name, sz in zip(names, sizes):
         got[name] = (out[off:off + sz], out[off + sz:off + 2 * sz])
