@@ -1974,15 +1974,16 @@ struct GraphRunner {
   ~GraphRunner() {
     if (exec) cudaGraphExecDestroy(exec);
   }
-  int run(Hier<T>& H, int nu1, int nu2, cudaStream_t st) {
+  // one V-cycle from grid j0 (the same j0 on every call of one runner)
+  int run(Hier<T>& H, int nu1, int nu2, cudaStream_t st, int j0 = 0) {
     if (!enabled) {
-      vcycle<T>(H, 0, nu1, nu2, st);
+      vcycle<T>(H, j0, nu1, nu2, st);
       return MLMC_OK;
     }
     if (!exec) {
       MLMC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       prof::tape_begin();
-      vcycle<T>(H, 0, nu1, nu2, st);
+      vcycle<T>(H, j0, nu1, nu2, st);
       tape = prof::tape_end();
       cap_act = H.n_act > 0 ? H.n_act : 1;
       cudaGraph_t graph = nullptr;
@@ -2890,7 +2891,10 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
         MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
                     (k_prolong_blk<T><<<plane_grid((w.n - 1) * (w.n - 1), (long long)B * (w.n - 1)), 128, 0, st>>>(
                         v.n, B, w.u, v.u, H.active)));
-      for (int cyc = 0; cyc < maxc; ++cyc) vcycle(H, j, nu1, nu2, st);
+      // the cycles of grid j replay one captured graph (on created streams)
+      GraphRunner<T> fr;
+      fr.enabled = gr.enabled;
+      for (int cyc = 0; cyc < maxc; ++cyc) MLMC_TRY(fr.run(H, nu1, nu2, st, j));
     }
     std::vector<int> cyc(B, maxc);
     MLMC_CUDA_TRY(cudaMemcpyAsync(H.cycles, cyc.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
