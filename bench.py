@@ -410,16 +410,18 @@ def measure(args, cfg_name, full=True):
     # overlap the FP32-bound field evaluation and solves of others
     # one untimed pass with the levels in sequence measures each level's time (the
     # lane assignment's costs)
-    seq_ms = {}
+    seq_ms, seq_launches = {}, {}
     for _ in range(2):  # the second pass, after first-call set-up
         for l in levels:
             c, lvl = mcfg[l]
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            mg.profile_reset()
             a.record(stream)
             mg.mlmc_level_run(c, lvl, ids[l], Y_dev=Y[l])
             b.record(stream)
             b.synchronize()
             seq_ms[l] = a.elapsed_time(b)
+            seq_launches[l] = mg.profile_total_launches()
     lanes = lane_items(levels, N, seq_ms, args.lanes)
     lane_streams = [stream] + [torch.cuda.Stream() for _ in lanes[1:]]
     # one configuration per work item, bound to its lane's stream
@@ -556,6 +558,7 @@ def measure(args, cfg_name, full=True):
                        "parallelism": "replicas x%d (samples sharded by rank, no data-path collective)" % world,
                        "level_streams": [["%d[%d:%d]" % (l, a, b) for (l, a, b) in its] for its in lanes],
                        "level_ms_alone": {str(l): round(v, 3) for l, v in seq_ms.items()},
+                       "level_launches_alone": {str(l): v for l, v in seq_launches.items()},
                        "l2": "every level's batch working set exceeds the 129 MB L2 (no flush needed)"},
             "per_level": per_level,
             "time_per_estimate_s": elapsed_ms / 1e3 / args.steps,
