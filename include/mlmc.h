@@ -541,7 +541,7 @@ typedef struct {
  * 32x16 or 64x8 tiles staged by cp.async or by TMA bulk copies: 9 candidates for FP32
  * correction cycles on finite volumes; 8 for FP64 stationary or FMG cycles (the
  * colour-split stored-face sweep, no nodal-coefficient sweep); 7 for FP64 CG) and the sweep count
- * nu in {1,2,3} of V(nu, nu) for MLMC level
+ * nu in {1,2,3,4} of V(nu, nu) for MLMC level
  * `level` under cfg (no counterpart in the paper; the paper fixes its cycle, Sec. 7.1).
  * Each candidate runs the whole level pipeline on the batched engine
  * (MLMC_ENGINE_BATCHED) once untimed and once timed on `samples` realisations

@@ -385,12 +385,14 @@ SMOOTHER_NAMES = {MLMC_SMOOTH_TWO_PASS: "two-pass", MLMC_SMOOTH_FUSED_32x8: "fus
 def mlmc_autotune(cfg: MlmcCfg, level: int, first_id: int, samples: int):
     """Returns (table as list of dicts, best smoother, best nu); the choice is stored
     for the level's fine grid in the library's tuning table."""
-    tab = (TuneEntry * 32)()
+    cap = 64  # 9 smoothers x 4 sweep counts at most
+    tab = (TuneEntry * cap)()
     cnt, bs, bnu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(lib().mlmc_autotune(ctypes.byref(cfg), int(level), int(first_id), int(samples), tab, 32,
+    _check(lib().mlmc_autotune(ctypes.byref(cfg), int(level), int(first_id), int(samples), tab, cap,
                                ctypes.byref(cnt), ctypes.byref(bs), ctypes.byref(bnu)), "mlmc_autotune")
     rows = [dict(smoother=SMOOTHER_NAMES.get(t.smoother, t.smoother), nu=t.nu,
-                 ms_per_sample=1e3 * t.seconds_per_sample, cycles=t.mean_cycles) for t in tab[:cnt.value]]
+                 ms_per_sample=1e3 * t.seconds_per_sample, cycles=t.mean_cycles)
+            for t in tab[:min(cnt.value, cap)]]
     return rows, bs.value, bnu.value
 
 

@@ -631,7 +631,7 @@ int mlmc_autotune(const mlmc_cfg* cfg, int level, uint64_t first_id, int samples
   double best = 1e300;
   // an explicit V(nu, nu) in cfg is kept: only the smoother implementation is tuned
   const bool fixed_nu = cfg->mg.nu1 > 0 && cfg->mg.nu1 == cfg->mg.nu2;
-  const int nu_lo = fixed_nu ? cfg->mg.nu1 : 1, nu_hi = fixed_nu ? cfg->mg.nu1 : 3;
+  const int nu_lo = fixed_nu ? cfg->mg.nu1 : 1, nu_hi = fixed_nu ? cfg->mg.nu1 : 4;
   // the nodal-coefficient sweeps exist only in FP32 correction cycles on finite volumes;
   // the colour-split storage there and in FP64 stationary and FMG cycles
   const bool fv = cfg->mg.disc == MLMC_DISC_FV, mixed = cfg->mg.precision == MLMC_PREC_MIXED;

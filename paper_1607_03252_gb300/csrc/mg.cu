@@ -1965,6 +1965,14 @@ inline bool graphs_allowed() {
   return !off;
 }
 
+inline bool fmg_graphs() {
+  static const bool on = [] {
+    const char* e = getenv("MLMC_FMG_GRAPHS");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
 template <typename T>
 struct GraphRunner {
   bool enabled = false;
@@ -2891,9 +2899,12 @@ int solve_impl(const MGSolveArgs& a, void* ws, cudaStream_t st, int* cycles_host
         MLMC_LAUNCH(Names<T>::prolong, B * (2.0 * (double)v.n3 + (double)w.n3) * W, B * interior(v.n) * 4.375, st,
                     (k_prolong_blk<T><<<plane_grid((w.n - 1) * (w.n - 1), (long long)B * (w.n - 1)), 128, 0, st>>>(
                         v.n, B, w.u, v.u, H.active)));
-      // the cycles of grid j replay one captured graph (on created streams)
+      // with MLMC_FMG_GRAPHS=1 the cycles of grid j replay one graph captured for them (on
+      // created streams): a level alone runs 4-6% faster, but the capture and instantiation
+      // of every grid's graph in every solve cost more than they save while other level
+      // streams keep the GPU busy, so direct launches are the default
       GraphRunner<T> fr;
-      fr.enabled = gr.enabled;
+      fr.enabled = gr.enabled && fmg_graphs();
       for (int cyc = 0; cyc < maxc; ++cyc) MLMC_TRY(fr.run(H, nu1, nu2, st, j));
     }
     std::vector<int> cyc(B, maxc);

@@ -100,27 +100,45 @@ def test_fe_fmg_exponential_covariance_level_matches_oracle(orc, level):
         assert abs(Y[s] - (qf - qc)) <= 1e-9 * scale
 
 
-@pytest.mark.parametrize("sm", [mg.MLMC_SMOOTH_TWO_PASS, mg.MLMC_SMOOTH_SPLIT])
-def test_fmg_graph_replay_matches_direct_launches(sm):
-    """On a created stream the FMG cycle replays each grid's V-cycles from one captured
-    graph; on the legacy default stream every kernel is launched directly: the same
-    iterate and residual bit for bit."""
-    import torch
-
-    n, B = 65, 3
-    k = torch.from_numpy(np.stack([random_coefficient(n, 300 + s, 1.0) for s in range(B)])).cuda()
+FMG_GRAPH_CHILD = r"""
+import sys
+import numpy as np, torch
+import paper_1607_03252_gb300 as mg
+from paper_1607_03252_gb300.workloads import random_coefficient
+n, B = 65, 3
+k = torch.from_numpy(np.stack([random_coefficient(n, 300 + s, 1.0) for s in range(B)])).cuda()
+out = {}
+for sm in (mg.MLMC_SMOOTH_TWO_PASS, mg.MLMC_SMOOTH_SPLIT):
     cfg = mg.mg_cfg(4, 4, 0.0, 2, mg.MLMC_PREC_F64, sm, mg.MLMC_ACCEL_FMG, mg.MLMC_DISC_FE,
                     engine=mg.MLMC_ENGINE_BATCHED)
     u0 = torch.zeros_like(k)
-    _, rel0, st0 = mg.mg_solve_batch(cfg, k, u0)
+    _, rel0, st0 = mg.mg_solve_batch(cfg, k, u0)  # legacy default stream: direct launches
     side = torch.cuda.Stream()
     u1 = torch.zeros_like(k)
     side.wait_stream(torch.cuda.current_stream())
-    _, rel1, st1 = mg.mg_solve_batch(cfg, k, u1, stream=side)
+    _, rel1, st1 = mg.mg_solve_batch(cfg, k, u1, stream=side)  # created stream: graph replay
     torch.cuda.synchronize()
     assert st0 == st1 == 0
     assert np.array_equal(rel0, rel1)
     assert np.array_equal(u0.cpu().numpy(), u1.cpu().numpy())
+print("ok")
+"""
+
+
+def test_fmg_graph_replay_matches_direct_launches():
+    """With MLMC_FMG_GRAPHS=1 (read once per process, so in a child process) the FMG cycle
+    on a created stream replays each grid's V-cycles from one captured graph; on the
+    legacy default stream every kernel is launched directly: the same iterate and
+    residual bit for bit, on the plain and the colour-split storage."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, MLMC_FMG_GRAPHS="1")
+    res = subprocess.run([sys.executable, "-c", FMG_GRAPH_CHILD], cwd=root, env=env, capture_output=True, text=True,
+                         timeout=600)
+    assert res.returncode == 0 and "ok" in res.stdout, res.stdout[-2000:] + res.stderr[-4000:]
 
 
 def test_qoi_choice_on_the_fv_path(orc):

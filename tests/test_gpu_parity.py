@@ -557,7 +557,7 @@ def test_cg_batch_composition_does_not_change_results(orc):
 def test_autotune_records_choice():
     cfg = mg.make_mlmc_cfg(RUN_SEED, 1.0, 0.3, 64, n0=17, nu1=0, nu2=0, rtol=1e-10, precision=mg.MLMC_PREC_MIXED)
     rows, best_sm, best_nu = mg.mlmc_autotune(cfg, 1, int(sample_ids(1, 900, 1)[0]), 16)
-    assert len(rows) == 27 and best_nu in (1, 2, 3)  # 9 smoothers x nu in {1, 2, 3}
+    assert len(rows) == 36 and best_nu in (1, 2, 3, 4)  # 9 smoothers x nu in {1, 2, 3, 4}
     assert all(r["ms_per_sample"] > 0 for r in rows)
     # a level run with AUTO smoother and nu = 0 uses the choice and matches an explicit run
     s_auto, Ya, _, _ = mg.mlmc_level_estimate(cfg, 1, int(sample_ids(1, 0, 1)[0]), 8)
