@@ -565,7 +565,8 @@ def measure(args, cfg_name, full=True):
             "level_stats": {str(l): {"mean": stats[l].mean, "var": stats[l].var_unbiased,
                                      "cycles_fine": stats[l].mean_cycles_fine,
                                      "cycles_coarse": stats[l].mean_cycles_coarse} for l in levels},
-            "roofline": roof, "gpu_launches": launches, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu,
+            "roofline": roof, "field_roofline": field_roofline(prof), "gpu_launches": launches, "e2e": e2e,
+            "clocks": clk, "cpu_baseline": cpu,
             "host_wall_s": t_host,
             "timing_note": "value, per_level, clocks and gpu_launches: timed region 1 (levels on concurrent "
                            "streams, no per-launch events); roofline and kernel_classes: timed region 2 (same "
@@ -609,18 +610,30 @@ def class_shares(prof):
             for k, v in sorted(agg.items(), key=lambda kv: -kv[1]["ms"])[:12]}
 
 
+def family(base):
+    """The operation a launch class performs, whatever its storage ("rbgs_split_f64" and
+    "rbgs_f64" are both the FP64 colour sweep)."""
+    return base.replace("_split", "")
+
+
+def solver_class(base):
+    """Launch classes of the multigrid solves (the field evaluation has its own roofline)."""
+    return not (base.startswith("field") or base == "phasors" or base == "features")
+
+
 def roofline(prof, peaks, keep=None):
-    """The dominant launch class (one grid size) among those `keep` accepts: algorithmic
-    work per launch (active samples only) over its event-timed average launch time."""
-    items = [(k, v) for k, v in prof.items() if keep is None or keep(base_class(k))]
+    """The dominant solver operation (storages and grid sizes merged), then its launch
+    class and grid size with the most time, among those `keep` accepts: algorithmic work
+    per launch (active samples only) over its event-timed average launch time."""
+    keep = keep or solver_class
+    items = [(k, v) for k, v in prof.items() if keep(base_class(k))]
     if not items:
         return None
-    # the dominant kernel class (grid sizes merged), then its grid size with the most time
     tot = {}
     for k, v in items:
-        tot[base_class(k)] = tot.get(base_class(k), 0.0) + v["ms"]
+        tot[family(base_class(k))] = tot.get(family(base_class(k)), 0.0) + v["ms"]
     top = max(tot, key=tot.get)
-    name, rec = max(((k, v) for k, v in items if base_class(k) == top), key=lambda kv: kv[1]["ms"])
+    name, rec = max(((k, v) for k, v in items if family(base_class(k)) == top), key=lambda kv: kv[1]["ms"])
     base = base_class(name)
     timed = max(rec["timed"], 1)
     avg_s = rec["ms"] / 1e3 / timed
@@ -630,7 +643,7 @@ def roofline(prof, peaks, keep=None):
     fp64 = base.endswith("f64") or base in ("residual_mixed", "update_mixed", "coarse_setup", "norm")
     traffic, tsrc = traffic_per_launch(base, rec)
     share = rec["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-30)
-    out = {"kernel": name, "share_of_profiled_time": share, "class_share_of_profiled_time":
+    out = {"kernel": name, "share_of_profiled_time": share, "operation_share_of_profiled_time":
            tot[top] / max(sum(v["ms"] for v in prof.values()), 1e-30), "avg_launch_ms": avg_s * 1e3,
            "launches": rec["launches"], "traffic": traffic, "traffic_source": tsrc,
            "dram_gbs_from_traffic": traffic / avg_s / 1e9 if traffic else None}
@@ -659,6 +672,24 @@ def roofline(prof, peaks, keep=None):
     out.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured" if hbm_peak else "fallback"})
     return out
+
+
+def field_roofline(prof):
+    """The double-float field evaluation: node-features per second (2 FMA-equivalents each,
+    executed as ~24 FP32 operations), its share of the profiled time; its bound is the
+    FP32 pipe (ncu: profiles/field_df32_n129_b8.md)."""
+    recs = [v for k, v in prof.items() if base_class(k).startswith("field")]
+    if not recs:
+        return None
+    ms = sum(v["ms"] for v in recs)
+    timed_share = sum(v["ms"] * v["launches"] / max(v["timed"], 1) for v in recs)
+    node_features = sum(v["flops"] for v in recs) / 4.0
+    secs = timed_share / 1e3
+    return {"kernel": "field_df32", "bound": "alu (FP32 pipe, double-float)",
+            "node_features_per_s": node_features / secs if secs > 0 else None,
+            "fp32_ops_per_s": 24.0 * node_features / secs if secs > 0 else None,
+            "share_of_profiled_time": ms / max(sum(v["ms"] for v in prof.values()), 1e-30),
+            "ncu": "FP32 pipe 69.6% busy at 129^3 x 8 (profiles/field_df32_n129_b8.md)"}
 
 
 def lane_items(levels, N, times, lanes):
