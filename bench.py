@@ -565,7 +565,7 @@ def measure(args, cfg_name, full=True):
             "level_stats": {str(l): {"mean": stats[l].mean, "var": stats[l].var_unbiased,
                                      "cycles_fine": stats[l].mean_cycles_fine,
                                      "cycles_coarse": stats[l].mean_cycles_coarse} for l in levels},
-            "roofline": roof, "field_roofline": field_roofline(prof), "gpu_launches": launches, "e2e": e2e,
+            "roofline": roof, "field_roofline": field_roofline(prof, peaks), "gpu_launches": launches, "e2e": e2e,
             "clocks": clk, "cpu_baseline": cpu,
             "host_wall_s": t_host,
             "timing_note": "value, per_level, clocks and gpu_launches: timed region 1 (levels on concurrent "
@@ -618,7 +618,7 @@ def family(base):
 
 def solver_class(base):
     """Launch classes of the multigrid solves (the field evaluation has its own roofline)."""
-    return not (base.startswith("field") or base == "phasors" or base == "features")
+    return not (base.startswith("field") or base in ("phasors", "features", "xslices", "face_factors"))
 
 
 def roofline(prof, peaks, keep=None):
@@ -674,22 +674,40 @@ def roofline(prof, peaks, keep=None):
     return out
 
 
-def field_roofline(prof):
-    """The double-float field evaluation: node-features per second (2 FMA-equivalents each,
-    executed as ~24 FP32 operations), its share of the profiled time; its bound is the
-    FP32 pipe (ncu: profiles/field_df32_n129_b8.md)."""
-    recs = [v for k, v in prof.items() if base_class(k).startswith("field")]
+def field_roofline(prof, peaks=None):
+    """The field evaluation: node-features per second and its share of the profiled time.
+    The tensor-core form (field_tc: the volume x < n - 1; field_tc_face: the face x = n - 1)
+    executes 28 slice-pair products of 2 terms per node-feature (112 bf16 flops), reported
+    against the measured sustained bf16 rate; the
+    double-float form (field_df32) ~24 FP32 operations per node-feature on the FP32 pipe
+    (ncu: profiles/field_df32_n129_b8.md)."""
+    recs = [(base_class(k), v) for k, v in prof.items()
+            if base_class(k).startswith("field") or base_class(k) in ("xslices", "face_factors")]
     if not recs:
         return None
-    ms = sum(v["ms"] for v in recs)
-    timed_share = sum(v["ms"] * v["launches"] / max(v["timed"], 1) for v in recs)
-    node_features = sum(v["flops"] for v in recs) / 4.0
-    secs = timed_share / 1e3
-    return {"kernel": "field_df32", "bound": "alu (FP32 pipe, double-float)",
-            "node_features_per_s": node_features / secs if secs > 0 else None,
-            "fp32_ops_per_s": 24.0 * node_features / secs if secs > 0 else None,
-            "share_of_profiled_time": ms / max(sum(v["ms"] for v in prof.values()), 1e-30),
-            "ncu": "FP32 pipe 69.6% busy at 129^3 x 8 (profiles/field_df32_n129_b8.md)"}
+
+    def secs(rs):
+        return sum(v["ms"] * v["launches"] / max(v["timed"], 1) for _, v in rs) / 1e3
+
+    ms = sum(v["ms"] for _, v in recs)
+    node_features = sum(v["flops"] for b, v in recs if b.startswith("field")) / 4.0
+    out = {"node_features_per_s": node_features / secs(recs) if secs(recs) > 0 else None,
+           "share_of_profiled_time": ms / max(sum(v["ms"] for v in prof.values()), 1e-30)}
+    tc = [(b, v) for b, v in recs if b in ("field_tc", "field_tc_face")]
+    if tc and secs(tc) > 0:
+        peaks = peaks or {}
+        peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        achieved = 112.0 * sum(v["flops"] for _, v in tc) / 4.0 / secs(tc) / 1e12
+        out.update({"kernel": "field_tc", "bound": "tensor (bf16 mma.sync, exact FP32 group sums)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak if peak else None,
+                    "peak_source": "measured sustained cuBLAS bf16" if peak else None,
+                    "ncu": "profiles/field_tc_n129_b8.md"})
+        return out
+    out.update({"kernel": "field_df32", "bound": "alu (FP32 pipe, double-float)",
+                "fp32_ops_per_s": 24.0 * out["node_features_per_s"] if out["node_features_per_s"] else None,
+                "ncu": "FP32 pipe 69.6% busy at 129^3 x 8 (profiles/field_df32_n129_b8.md)"})
+    return out
 
 
 def lane_items(levels, N, times, lanes):

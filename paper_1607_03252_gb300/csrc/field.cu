@@ -8,11 +8,13 @@
 // and evaluate the sum as Re(A_m[i] * Q_m[j,k]) with Q_m[j,k] = B_m[j] C_m[k]:
 // two FP64 FMAs per node and feature instead of one FP64 cos (about 20x fewer FP64
 // instructions; FP64 throughput is the binding resource of this kernel on GB300).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <cstdlib>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "field.cuh"
 #include "philox.cuh"
 #include "prof.cuh"
@@ -358,16 +360,417 @@ int field_line_launch(const float4* xsplit, int M, int n, int MC, int xbase, uns
   return MLMC_OK;
 }
 
+// The phasor sum on the tensor cores. For one sample, log k / scale at node (x, l) (l the
+// (y, z) line) is the product of an x-by-2M matrix and a 2M-by-line matrix: A[x][2m] = Re X_m[x],
+// A[x][2m+1] = -Im X_m[x], B[2m][l] = Re Q_m[l], B[2m+1][l] = Im Q_m[l], Q_m[l] = Y_m[y] Z_m[z],
+// every entry in [-1, 1]. Each entry is split (df::slice7) into seven bf16 slices on the fixed
+// grids 2^-7, ..., 2^-49, so slice i of A times slice j of B is an integer multiple of
+// 2^(-7(i+j+2)): the bf16 products are exact, and an FP32 sum of them is exact while it stays
+// below 2^24 grid steps. The 28 pairs i + j <= 6 go into seven FP32 group sums (group i + j);
+// over 256 features (512 terms) the groups i + j <= 4 are exact in the worst case and the
+// groups 5 and 6 round by at most 4e-13 in all; the groups are folded into a double-float
+// sum every 256 features. The dropped pairs and the slices' remainders leave below 3e-12 of
+// the sum (worst case; 1e-13 for random-signed terms), against the 1e-11 that k's 1e-12
+// relative accuracy allows at sigma sqrt(2/M) = 0.09. This is the splitting of Ozaki, Ogita,
+// Oishi and Rump (Numer. Algorithms 59, 2012) on a fixed grid, which suffices because every
+// entry is bounded by 1. The final exp is Tang's double-float exp on the FP32 pipe (dfloat.cuh).
+//
+// Fragments follow the register layout of mma.m16n8k16 with bf16 operands: A is 16 x-values by
+// 16 k (8 features), B is 16 k by 8 lines; lane (g = lane / 4, c = lane % 4) holds A rows g and
+// g + 8 at the feature pairs c and c + 4, B column g at the same features, and D rows g, g + 8
+// at the columns 2c, 2c + 1. A (the x-phasors) is the same for every line of a sample and is
+// sliced once per sample into Xf[s][rt][ks][slice][lane] (one uint4 of four bf16 pairs per
+// lane); B is sliced per block into shared memory.
+constexpr int kTcSlices = 7;
+constexpr int kTcThreads = 256;
+constexpr int kTcFold = 256;  // features per exact FP32 group sum
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // exact: every slice fits in bf16
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint4& a, const uint2& b) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+}
+
+size_t tc_xslice_bytes(int B, int M, int n) {
+  return (size_t)B * ((n - 1) / 16) * ((M + 7) / 8) * kTcSlices * 32 * sizeof(uint4);
+}
+
+// One thread per (axis, sample, row tile, k-step, lane): the lane's four A registers of every
+// slice, for the x-phasors (axis 0, into Xf) and the y-phasors (axis 1, into Xf + the size of
+// one axis: the A operand of the x = n - 1 face). Threads 0..31 also write 2^(j/32) as
+// double-floats (e2tab[j], e2tab[32 + j]) for the exp.
+__global__ void k_xslices(const float4* __restrict__ xsplit, int B, int M, int n, int KS, uint4* __restrict__ Xf,
+                          float* __restrict__ e2tab) {
+  const int RT = (n - 1) / 16;
+  const size_t per_axis = (size_t)B * RT * KS * 32;
+  const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 < 32) {
+    const double v = exp2((double)t0 / 32.0);
+    const float h = narrow(v);
+    e2tab[t0] = h;
+    e2tab[32 + t0] = narrow(v - widen(h));
+  }
+  for (size_t t = t0; t < 2 * per_axis; t += (size_t)gridDim.x * blockDim.x) {
+    const int axis = t < per_axis ? 0 : 1;
+    const size_t ta = t - axis * per_axis;
+    const int lane = (int)(ta & 31);
+    size_t r = ta >> 5;
+    const int ks = (int)(r % KS);
+    r /= KS;
+    const int rt = (int)(r % RT);
+    const int s = (int)(r / RT);
+    const int g = lane >> 2, c = lane & 3;
+    uint32_t reg[4][kTcSlices];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int x = 16 * rt + g + (q & 1) * 8;
+      const int f = 8 * ks + c + (q >> 1) * 4;
+      float re[kTcSlices], im[kTcSlices];
+      if (f < M) {
+        const float4 v = xsplit[(((size_t)s * 3 + axis) * M + f) * n + x];
+        df::slice7(v.x, v.y, re);
+        df::slice7(-v.z, -v.w, im);
+      } else {
+#pragma unroll
+        for (int i = 0; i < kTcSlices; ++i) re[i] = im[i] = 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < kTcSlices; ++i) reg[q][i] = pack_bf16x2(re[i], im[i]);
+    }
+    uint4* o = Xf + axis * per_axis * kTcSlices + ((size_t)(s * RT + rt) * KS + ks) * kTcSlices * 32 + lane;
+#pragma unroll
+    for (int i = 0; i < kTcSlices; ++i) o[i * 32] = make_uint4(reg[0][i], reg[1][i], reg[2][i], reg[3][i]);
+  }
+}
+
+// The line factors of the x = n - 1 face: P_m[z] = X_m[n - 1] Z_m[z] in double-float, laid out
+// as the tables (pt[s][m][z] = (Re hi, Re lo, Im hi, Im lo)). On that face log k / scale is
+// sum_m Re(Y_m[y] P_m[z]): the same product as the volume with y for x and z for the line.
+__global__ void k_face_factors(const float4* __restrict__ xsplit, int B, int M, int n, float4* __restrict__ pt) {
+  const size_t total = (size_t)B * M * n;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int z = (int)(t % n);
+    const size_t sm = t / n;  // s * M + m
+    const int m = (int)(sm % M);
+    const int s = (int)(sm / M);
+    const float4 a = xsplit[((size_t)s * 3 * M + m) * n + (n - 1)];
+    const float4 d = xsplit[(((size_t)s * 3 + 2) * M + m) * n + z];
+    float t1h, t1l, t2h, t2l, rh, rl, ih, il;
+    df::mul(a.x, a.y, d.x, d.y, t1h, t1l);
+    df::mul(a.z, a.w, d.z, d.w, t2h, t2l);
+    df::add(t1h, t1l, -t2h, -t2l, rh, rl);
+    df::mul(a.x, a.y, d.z, d.w, t1h, t1l);
+    df::mul(a.z, a.w, d.x, d.y, t2h, t2l);
+    df::add(t1h, t1l, t2h, t2l, ih, il);
+    pt[t] = make_float4(rh, rl, ih, il);
+  }
+}
+
+// The edge x = y = n - 1 in FP64 (n nodes per sample): one warp per (sample, z), lanes over the
+// features, log k / scale = sum_m Re(X_m[n - 1] Y_m[n - 1] Z_m[z]), a butterfly sum over the lanes.
+template <typename TOut>
+__global__ void k_field_edge(const double2* __restrict__ tab, int B, int M, int n, double scale,
+                             TOut* __restrict__ kout) {
+  const size_t gw = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= (size_t)B * n) return;
+  const int s = (int)(gw / n), z = (int)(gw % n);
+  const double2* Tx = tab + (size_t)s * 3 * M * n;
+  const double2* Ty = Tx + (size_t)M * n;
+  const double2* Tz = Ty + (size_t)M * n;
+  double acc = 0.0;
+  for (int m = lane; m < M; m += 32) {
+    const double2 x = Tx[(size_t)m * n + n - 1], y = Ty[(size_t)m * n + n - 1], zz = Tz[(size_t)m * n + z];
+    const double cr = x.x * y.x - x.y * y.y, ci = x.x * y.y + x.y * y.x;
+    acc = fma(cr, zz.x, fma(-ci, zz.y, acc));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) kout[(size_t)s * n * n * n + ((size_t)z * n + n - 1) * n + n - 1] = (TOut)exp(scale * acc);
+}
+
+// Block: RX row tiles (16 rows each, from row 16 RX blockIdx.x) by 256 / RX lines (from
+// blockIdx.y * 256 / RX) of sample blockIdx.z; warp w takes row tile w % RX and the 32 lines
+// (four column tiles) of line group w / RX. Features come in chunks of 8 RX (RX k-steps): every
+// thread forms double-float Q_m[l] of 8 (line, feature) pairs of a chunk, slices it and stores
+// the bf16 pairs (Re, Im) of each slice in the B-fragment order sq[k-step][slice][column
+// tile][lane]. The chunks are double-buffered: a warp stages its items of the next chunk
+// between the k-steps of the current one (8 / RX items after each k-step), so the FP32 work of
+// the staging and the tensor-core work of the products overlap; one barrier per chunk. The
+// double-float running sums of the group folds live in shared memory (used every 256
+// features only). FACE = false: the volume x < n - 1 (rows x, lines (y, z), Q_m = Y_m[y] Z_m[z]
+// from the tables); FACE = true: the face x = n - 1, y < n - 1 (rows y, lines z, Q_m = P_m[z]
+// from k_face_factors, A from the y-phasor slices).
+template <int RX>
+struct TcShape {
+  static constexpr int LQ = 256 / RX;                        // lines per block
+  static constexpr int CT = LQ / 8;                          // column tiles per block
+  static constexpr int KCF = 8 * RX;                         // features per chunk
+  static constexpr int BUF = KCF / 8 * kTcSlices * CT * 32;  // uint2 per chunk buffer
+  static constexpr size_t smem =
+      (2 * (size_t)BUF) * sizeof(uint2) + 32 * kTcThreads * sizeof(float) + (size_t)LQ * sizeof(int4);
+};
+
+// Q_m[line] of item `it` (of LQ * KCF) of the chunk at feature m0, sliced into buffer buf.
+template <int RX, bool FACE>
+__device__ __forceinline__ void tc_stage(int it, int m0, int M, int n, const float4* tsplit, const float4* pt,
+                                         const int4* sline, uint2* buf) {
+  using S = TcShape<RX>;
+  const int cc = it & 3, gg = (it >> 2) & 7, half = (it >> 5) & 1;
+  const int rest = it >> 6;
+  const int ctl = rest % S::CT, ksl = rest / S::CT;
+  const int f = m0 + ksl * 8 + half * 4 + cc;
+  const int4 L = sline[ctl * 8 + gg];  // (sample, y or z, z, valid) of the block's line slot
+  const bool valid = L.w != 0;
+  const int si = L.x;
+  float qr[kTcSlices], qi[kTcSlices];
+  if (valid && f < M) {
+    float rh, rl, ih, il;
+    if (FACE) {
+      const float4 p = pt[((size_t)si * M + f) * n + L.y];
+      rh = p.x;
+      rl = p.y;
+      ih = p.z;
+      il = p.w;
+    } else {
+      const float4* Ty = tsplit + ((size_t)si * 3 + 1) * M * n;
+      const float4 b = Ty[(size_t)f * n + L.y], d = Ty[((size_t)M + f) * n + L.z];
+      float t1h, t1l, t2h, t2l;
+      df::mul(b.x, b.y, d.x, d.y, t1h, t1l);
+      df::mul(b.z, b.w, d.z, d.w, t2h, t2l);
+      df::add(t1h, t1l, -t2h, -t2l, rh, rl);
+      df::mul(b.x, b.y, d.z, d.w, t1h, t1l);
+      df::mul(b.z, b.w, d.x, d.y, t2h, t2l);
+      df::add(t1h, t1l, t2h, t2l, ih, il);
+    }
+    df::slice7(rh, rl, qr);
+    df::slice7(ih, il, qi);
+  } else {
+#pragma unroll
+    for (int j = 0; j < kTcSlices; ++j) qr[j] = qi[j] = 0.f;
+  }
+  uint32_t* dst = reinterpret_cast<uint32_t*>(buf) + ((size_t)(ksl * kTcSlices * S::CT + ctl) * 32 + gg * 4 + cc) * 2 + half;
+#pragma unroll
+  for (int j = 0; j < kTcSlices; ++j) dst[j * S::CT * 64] = pack_bf16x2(qr[j], qi[j]);
+}
+
+template <typename TOut, int RX, bool FACE>
+__global__ void __launch_bounds__(kTcThreads, 1) k_field_tc(const float4* __restrict__ tsplit,
+                                                             const float4* __restrict__ pt,
+                                                             const uint4* __restrict__ Xf,
+                                                             const float* __restrict__ e2tab, int B, int M, int n,
+                                                             int KS, double scale, TOut* __restrict__ kout) {
+  using S = TcShape<RX>;
+  constexpr int IPK = 8 / RX;  // staged items per thread after each k-step
+  extern __shared__ uint2 sq[];
+  float* sacc = reinterpret_cast<float*>(sq + 2 * S::BUF);  // [32][kTcThreads]: th[16], tl[16]
+  int4* sline = reinterpret_cast<int4*>(sacc + 32 * kTcThreads);  // [LQ]
+  __shared__ float se2[64];
+  const int RT = (n - 1) / 16;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, c = lane & 3;
+  const int rt = blockIdx.x * RX + warp % RX;
+  const int ct0 = (warp / RX) * 4;  // its column tiles in the block's staged chunk
+  // the warp's line group: 32 consecutive lines of one sample (ceil(lines / 32) groups per
+  // sample, 8 / RX groups per block; the last group of a sample is partly empty)
+  const size_t nl = FACE ? (size_t)n : (size_t)n * n;
+  const int lgps = (int)((nl + 31) / 32);
+  const int glg = (int)blockIdx.y * (8 / RX) + warp / RX;
+  int s = glg / lgps;
+  const size_t wline0 = (size_t)(glg % lgps) * 32;
+  const bool wvalid = s < B;
+  if (!wvalid) s = B - 1;  // its products are computed and dropped
+  const uint4* xa = Xf + (size_t)(s * RT + rt) * KS * kTcSlices * 32 + lane;
+  if (threadIdx.x < 64) se2[threadIdx.x] = e2tab[threadIdx.x];
+  for (int t = threadIdx.x; t < S::LQ; t += kTcThreads) {  // line slot t: column tile t / 8, lane row t % 8
+    const int lg = (int)blockIdx.y * (8 / RX) + t / 32;
+    const int ls = lg / lgps;
+    const int line = (lg % lgps) * 32 + t % 32;
+    const bool ok = ls < B && (size_t)line < nl;
+    sline[t] = FACE ? make_int4(ls, line, 0, ok) : make_int4(ls, line % n, line / n, ok);
+  }
+#pragma unroll
+  for (int q = 0; q < 32; ++q) sacc[q * kTcThreads + threadIdx.x] = 0.f;
+  float acc[kTcSlices][4][4];
+#pragma unroll
+  for (int q = 0; q < kTcSlices; ++q)
+#pragma unroll
+    for (int ct = 0; ct < 4; ++ct)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[q][ct][e] = 0.f;
+  uint4 a[kTcSlices];
+#pragma unroll
+  for (int i = 0; i < kTcSlices; ++i) a[i] = xa[i * 32];
+  __syncthreads();  // the line table
+#pragma unroll 1
+  for (int r = 0; r < 8; ++r) tc_stage<RX, FACE>(threadIdx.x + r * kTcThreads, 0, M, n, tsplit, pt, sline, sq);
+  __syncthreads();
+  for (int m0 = 0, cb = 0; m0 < M; m0 += S::KCF, cb ^= 1) {
+    const uint2* cur = sq + cb * S::BUF;
+    uint2* nxt = sq + (cb ^ 1) * S::BUF;
+    const bool more = m0 + S::KCF < M;
+    const int ksb = m0 / 8;
+    const int ksn = min(RX, KS - ksb);
+    for (int ksl = 0; ksl < ksn; ++ksl) {
+      const int ks = ksb + ksl;
+      uint4 an[kTcSlices];
+      if (ks + 1 < KS) {
+#pragma unroll
+        for (int i = 0; i < kTcSlices; ++i) an[i] = xa[((size_t)(ks + 1) * kTcSlices + i) * 32];
+      } else {
+#pragma unroll
+        for (int i = 0; i < kTcSlices; ++i) an[i] = a[i];
+      }
+#pragma unroll
+      for (int j = 0; j < kTcSlices; ++j) {
+        uint2 b[4];
+#pragma unroll
+        for (int ct = 0; ct < 4; ++ct) b[ct] = cur[((ksl * kTcSlices + j) * S::CT + ct0 + ct) * 32 + lane];
+#pragma unroll
+        for (int i = kTcSlices - 1 - j; i >= 0; --i)  // the highest group first: its chain is the longest
+#pragma unroll
+          for (int ct = 0; ct < 4; ++ct) mma_bf16_16816(acc[i + j][ct], a[i], b[ct]);
+      }
+#pragma unroll
+      for (int i = 0; i < kTcSlices; ++i) a[i] = an[i];
+      if (more) {
+#pragma unroll
+        for (int r = 0; r < IPK; ++r)
+          tc_stage<RX, FACE>(threadIdx.x + (ksl * IPK + r) * kTcThreads, m0 + S::KCF, M, n, tsplit, pt, sline, nxt);
+      }
+    }
+    if ((m0 + S::KCF) % kTcFold == 0 || !more) {
+#pragma unroll
+      for (int ct = 0; ct < 4; ++ct)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float gs[kTcSlices], sh, sl;
+#pragma unroll
+          for (int q = 0; q < kTcSlices; ++q) {
+            gs[q] = acc[q][ct][e];
+            acc[q][ct][e] = 0.f;
+          }
+          df::sum7(gs, sh, sl);
+          float* th = sacc + (ct * 4 + e) * kTcThreads + threadIdx.x;
+          float* tl = th + 16 * kTcThreads;
+          float h, l;
+          df::add(*th, *tl, sh, sl, h, l);
+          *th = h;
+          *tl = l;
+        }
+    }
+    __syncthreads();
+  }
+  const float sch = narrow(scale), scl = narrow(scale - widen(sch));
+  TOut* out = kout + (size_t)s * n * n * n;
+#pragma unroll
+  for (int ct = 0; ct < 4; ++ct)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = 16 * rt + g + (e >> 1) * 8;
+      const size_t line = wline0 + ct * 8 + 2 * c + (e & 1);
+      if (!wvalid || line >= nl) continue;
+      float yh, yl, eh, el;
+      int m;
+      const float* th = sacc + (ct * 4 + e) * kTcThreads + threadIdx.x;
+      df::mul(th[0], th[16 * kTcThreads], sch, scl, yh, yl);
+      df::exp_df(yh, yl, se2, se2 + 32, eh, el, m);
+      const size_t o = FACE ? ((size_t)line * n + r) * n + (n - 1) : line * n + r;
+      if constexpr (sizeof(TOut) == 8)
+        out[o] = (widen(eh) + widen(el)) * __hiloint2double((m + 1023) << 20, 0);
+      else
+        out[o] = (m > -126 && m < 128) ? __fmul_rn(eh, __int_as_float((m + 127) << 23)) : ldexpf(eh, m);
+    }
+}
+
+template <typename TOut, int RX, bool FACE>
+int field_tc_launch(const float4* xsplit, const float4* pt, const uint4* Xf, const float* e2tab, int M, int n, int KS,
+                    int B, double scale, void* kout, double bytes, double flops, cudaStream_t st, double share) {
+  const size_t smem = TcShape<RX>::smem;
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_field_tc<TOut, RX, FACE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  MLMC_CUDA_TRY(attr);
+  // line groups of 32 lines, ceil(lines / 32) per sample, 8 / RX per block; samples in
+  // chunks that keep the grid's y-extent within 65535
+  const size_t nl = FACE ? (size_t)n : (size_t)n * n;
+  const size_t lgps = (nl + 31) / 32;
+  const int per_chunk = (int)(65535 * (size_t)(8 / RX) / lgps);
+  if (per_chunk < 1) {
+    set_error("field: grid too large for the tensor-core form (n = %d)", n);
+    return MLMC_ERR_INVALID;
+  }
+  const int RT = (n - 1) / 16;
+  for (int s0 = 0; s0 < B; s0 += per_chunk) {
+    const int b = B - s0 < per_chunk ? B - s0 : per_chunk;
+    const dim3 grid((unsigned)(RT / RX), (unsigned)(((size_t)b * lgps + 8 / RX - 1) / (8 / RX)), 1u);
+    MLMC_LAUNCH(FACE ? "field_tc_face" : "field_tc", bytes * share * b / B, flops * share * b / B, st,
+                (k_field_tc<TOut, RX, FACE><<<grid, kTcThreads, smem, st>>>(
+                    xsplit + (size_t)s0 * 3 * M * n, pt + (size_t)s0 * M * n,
+                    Xf + (size_t)s0 * RT * KS * kTcSlices * 32, e2tab, b, M, n, KS, scale,
+                    (TOut*)kout + (size_t)s0 * n * n * n)));
+  }
+  return MLMC_OK;
+}
+
+template <typename TOut, bool FACE>
+int field_tc_dispatch(const float4* xsplit, const float4* pt, const uint4* Xf, const float* e2tab, int M, int n,
+                      int KS, int B, double scale, void* kout, double bytes, double flops, cudaStream_t st,
+                      double share) {
+  const int rts = (n - 1) / 16;
+  if (rts % 8 == 0)
+    return field_tc_launch<TOut, 8, FACE>(xsplit, pt, Xf, e2tab, M, n, KS, B, scale, kout, bytes, flops, st, share);
+  if (rts % 4 == 0)
+    return field_tc_launch<TOut, 4, FACE>(xsplit, pt, Xf, e2tab, M, n, KS, B, scale, kout, bytes, flops, st, share);
+  if (rts % 2 == 0)
+    return field_tc_launch<TOut, 2, FACE>(xsplit, pt, Xf, e2tab, M, n, KS, B, scale, kout, bytes, flops, st, share);
+  return field_tc_launch<TOut, 1, FACE>(xsplit, pt, Xf, e2tab, M, n, KS, B, scale, kout, bytes, flops, st, share);
+}
+
+// All of the tensor-core form: slices of the x- and y-phasors, the face factors, the volume
+// x < n - 1, the face x = n - 1 (y < n - 1), the edge x = y = n - 1.
+template <typename TOut>
+int field_tc_all(const double2* tab, const float4* xsplit, float4* pt, uint4* Xf, float* e2tab, int M, int n, int B,
+                 double scale, void* kout, double bytes, double flops, cudaStream_t st) {
+  const int KS = (M + 7) / 8;
+  const size_t nxs = (size_t)B * ((n - 1) / 16) * KS * 32;
+  MLMC_LAUNCH("xslices", (double)nxs * 2 * 112.0, (double)nxs * 2 * 500.0, st,
+              (k_xslices<<<blocks_for(2 * nxs, 256), 256, 0, st>>>(xsplit, B, M, n, KS, Xf, e2tab)));
+  const size_t nf = (size_t)B * M * n;
+  MLMC_LAUNCH("face_factors", (double)nf * 48.0, (double)nf * 40.0, st,
+              (k_face_factors<<<blocks_for(nf, 256), 256, 0, st>>>(xsplit, B, M, n, pt)));
+  const double n3 = (double)n * n * n;
+  MLMC_TRY((field_tc_dispatch<TOut, false>(xsplit, pt, Xf, e2tab, M, n, KS, B, scale, kout, bytes, flops, st,
+                                           (double)(n - 1) * n * n / n3)));
+  MLMC_TRY((field_tc_dispatch<TOut, true>(xsplit, pt, Xf + nxs * kTcSlices, e2tab, M, n, KS, B, scale, kout, bytes,
+                                          flops, st, (double)(n - 1) * n / n3)));
+  MLMC_LAUNCH("field_edge", bytes * n / n3, flops * n / n3, st,
+              (k_field_edge<TOut><<<(unsigned)(((size_t)B * n + 3) / 4), 128, 0, st>>>(tab, B, M, n, scale,
+                                                                                       (TOut*)kout)));
+  return MLMC_OK;
+}
+
+// The tensor-core form applies where the x-values below n - 1 make whole row tiles.
+static bool tc_applies(int n) { return n >= 17 && (n - 1) % 16 == 0; }
+
 size_t field_scratch_bytes(int B, int M, int n) {
   return a256((size_t)B * M * 3 * sizeof(double)) + a256((size_t)B * M * sizeof(double)) +
-         a256((size_t)B * 3 * M * n * sizeof(double2)) + a256((size_t)B * 3 * M * n * sizeof(float4));
+         a256((size_t)B * 3 * M * n * sizeof(double2)) + a256((size_t)B * 3 * M * n * sizeof(float4)) +
+         (tc_applies(n) ? a256(2 * tc_xslice_bytes(B, M, n)) + a256(64 * sizeof(float)) +
+                              a256((size_t)B * M * n * sizeof(float4))
+                        : 0);
 }
 
 int field_arith_default() {
   static const int a = [] {
     const char* e = getenv("MLMC_FIELD_ARITH");
-    const int v = e ? atoi(e) : (int)kFieldDF32Line;
-    return v >= kFieldDF32Line && v <= kFieldDF32 ? v : (int)kFieldDF32Line;
+    const int v = e ? atoi(e) : (int)kFieldTC;
+    return v >= kFieldDF32Line && v <= kFieldTC ? v : (int)kFieldTC;
   }();
   return a;
 }
@@ -385,6 +788,9 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
   double* bph = (double*)carve((size_t)B * cfg.M * sizeof(double));
   double2* tab = (double2*)carve((size_t)B * 3 * cfg.M * n * sizeof(double2));
   float4* xsplit = (float4*)carve((size_t)B * 3 * cfg.M * n * sizeof(float4));
+  uint4* Xf = tc_applies(n) ? (uint4*)carve(2 * tc_xslice_bytes(B, cfg.M, n)) : nullptr;
+  float* e2tab = tc_applies(n) ? (float*)carve(64 * sizeof(float)) : nullptr;
+  float4* pt = tc_applies(n) ? (float4*)carve((size_t)B * cfg.M * n * sizeof(float4)) : nullptr;
   const size_t nf = (size_t)B * cfg.M;
   MLMC_LAUNCH("features", nf * 40.0, nf * 200.0, st,
               (k_features<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(ids_dev, B, cfg.M, cfg.run_seed,
@@ -415,20 +821,27 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
     else
       MLMC_LAUNCH("field_f64", bytes, flops, st,
                   (k_field<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (float*)kout)));
-  } else if (arith == kFieldDF32Line) {
+  } else if (arith == kFieldDF32Line || arith == kFieldTC) {
     const int MCl = cfg.M < 64 ? cfg.M : 64;
     const unsigned lines = (unsigned)(((size_t)n * n + kFieldThreads - 1) / kFieldThreads);
-    // x < n - 1 in tiles of 8 (of 4 on the 5-node grid), then x = n - 1
-    const int xt = (n - 1) % kXC == 0 ? kXC : 4;
-    const unsigned tiles = (unsigned)((n - 1) / xt);
-    if (xt == kXC)
-      MLMC_TRY(field_line_launch<kXC>(xsplit, cfg.M, n, MCl, 0, tiles, lines, B, scale, dtype, kout, bytes, flops, st,
+    if (arith == kFieldTC && tc_applies(n)) {
+      if (dtype == MLMC_F64)
+        MLMC_TRY(field_tc_all<double>(tab, xsplit, pt, Xf, e2tab, cfg.M, n, B, scale, kout, bytes, flops, st));
+      else
+        MLMC_TRY(field_tc_all<float>(tab, xsplit, pt, Xf, e2tab, cfg.M, n, B, scale, kout, bytes, flops, st));
+    } else {
+      // x < n - 1 in tiles of 8 (of 4 on the 5-node grid), then x = n - 1
+      const int xt = (n - 1) % kXC == 0 ? kXC : 4;
+      const unsigned tiles = (unsigned)((n - 1) / xt);
+      if (xt == kXC)
+        MLMC_TRY(field_line_launch<kXC>(xsplit, cfg.M, n, MCl, 0, tiles, lines, B, scale, dtype, kout, bytes, flops,
+                                       st, (double)(n - 1) / n));
+      else
+        MLMC_TRY(field_line_launch<4>(xsplit, cfg.M, n, MCl, 0, tiles, lines, B, scale, dtype, kout, bytes, flops, st,
                                      (double)(n - 1) / n));
-    else
-      MLMC_TRY(field_line_launch<4>(xsplit, cfg.M, n, MCl, 0, tiles, lines, B, scale, dtype, kout, bytes, flops, st,
-                                   (double)(n - 1) / n));
-    MLMC_TRY(field_line_launch<1>(xsplit, cfg.M, n, MCl, n - 1, 1, lines, B, scale, dtype, kout, bytes, flops, st,
-                                 1.0 / n));
+      MLMC_TRY(field_line_launch<1>(xsplit, cfg.M, n, MCl, n - 1, 1, lines, B, scale, dtype, kout, bytes, flops, st,
+                                   1.0 / n));
+    }
   } else {
     if (dtype == MLMC_F64)
       MLMC_LAUNCH("field_df32", bytes, flops, st,

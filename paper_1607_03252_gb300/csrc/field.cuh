@@ -11,11 +11,13 @@ namespace mlmc {
 size_t field_scratch_bytes(int B, int M, int n);
 
 // Arithmetic of the log k sum: double-float on the FP32 pipe with one (y, z) line per
-// thread (the default), FP64, or double-float with flattened outputs.
-enum { kFieldDF32Line = 0, kFieldFP64 = 1, kFieldDF32 = 2 };
+// thread, FP64, double-float with flattened outputs, or bf16 slices on the tensor cores with
+// exact FP32 group sums (the default; on grids with (n - 1) a multiple of 16 from n = 17,
+// other grids take the double-float line form).
+enum { kFieldDF32Line = 0, kFieldFP64 = 1, kFieldDF32 = 2, kFieldTC = 3 };
 
-// The arithmetic field_eval_dev uses by default: kFieldDF32Line, or the value of the
-// environment variable MLMC_FIELD_ARITH (0..2) read once.
+// The arithmetic field_eval_dev uses by default: kFieldTC, or the value of the environment
+// variable MLMC_FIELD_ARITH (0..3) read once.
 int field_arith_default();
 
 // k_out[s][z][y][x] = exp(log k) at the n^3 nodes for the B ids in ids_dev (device).

@@ -12,8 +12,9 @@ to --rtol) through the C ABI, so
 that every kernel class launches with the sizes of that grid. With --timing the solve runs
 twice and the second run records CUDA events around every launch: per kernel class it
 prints launches, device time per launch and algorithmic GB/s, and the same for the field
-evaluation (Fourier features, or the SPDE sampler of Sec. 3.2), with its wall
-time (MLMC_FIELD_ARITH=0..2 selects the field's arithmetic). With --level
+evaluation (Fourier features, or the SPDE sampler of Sec. 3.2), with its wall time
+(MLMC_FIELD_ARITH=0..3 selects the field's arithmetic; 3, the tensor-core form, is the
+default). With --level
 it instead runs mlmc_level_estimate for `batch` samples of that MLMC level (grids from n0;
 the precision, smoother and field as given, rtol 1e-10) and, with --timing, prints the
 per-class profile of a second run. With --fma-peak it prints the measured FP64 and FP32

@@ -46,3 +46,20 @@ def test_fp32_classes_use_hbm_bound(bench):
     assert roof["kernel"] == "rbgs_split_f32@257" and roof["bound"] == "hbm"
     assert roof["achieved"] == pytest.approx(2.65e8 / 6.57e-3 / 1e9)
     assert roof["frac"] == pytest.approx(roof["achieved"] / 6785.9)
+
+
+def test_tensor_core_field_record(bench):
+    """With the tensor-core field, its record counts 112 bf16 flops per node-feature of the
+    field_tc launches against the measured sustained bf16 rate; the node-features per second
+    cover every field launch (the x = n - 1 column runs in double-float); xslices is field
+    work, not a solver operation."""
+    prof = {"field_tc": rec(100.0, 40, 1e9, 4e12), "field_df32": rec(5.0, 40, 1e7, 4e10),
+            "xslices": rec(1.0, 40, 1e6, 1e6), "rbgs_split_f64@129": rec(312.7, 400, 400 * 4.6e8, 400 * 1.07e8)}
+    peaks = {"hbm_gbs": 6785.9, "bf16_tflops": 1949.3, "bf16_tflops_sustained": 1708.4}
+    field = bench.field_roofline(prof, peaks)
+    assert field["kernel"] == "field_tc" and field["unit"] == "TFLOP/s"
+    assert field["achieved"] == pytest.approx(112 * 1e12 / 0.1 / 1e12)
+    assert field["frac"] == pytest.approx(field["achieved"] / 1708.4)
+    assert field["node_features_per_s"] == pytest.approx((1e12 + 1e10) / 0.106)
+    assert bench.roofline(prof, peaks)["kernel"] == "rbgs_split_f64@129"
+    assert not bench.solver_class("xslices")
