@@ -698,7 +698,7 @@ def field_roofline(prof, peaks=None):
         peaks = peaks or {}
         peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
         achieved = 112.0 * sum(v["flops"] for _, v in tc) / 4.0 / secs(tc) / 1e12
-        out.update({"kernel": "field_tc", "bound": "tensor (bf16 mma.sync, exact FP32 group sums)",
+        out.update({"kernel": "field_tc", "bound": "tensor (bf16 slices, exact FP32 group sums; tcgen05 from 65^3)",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak if peak else None,
                     "peak_source": "measured sustained cuBLAS bf16" if peak else None,

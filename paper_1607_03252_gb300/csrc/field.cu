@@ -13,11 +13,13 @@
 
 #include <cstdlib>
 
+#include "bulk.cuh"
 #include "common.cuh"
 #include "dfloat.cuh"
 #include "field.cuh"
 #include "philox.cuh"
 #include "prof.cuh"
+#include "umma.cuh"
 #include "widen.cuh"
 
 namespace mlmc {
@@ -732,11 +734,295 @@ int field_tc_dispatch(const float4* xsplit, const float4* pt, const uint4* Xf, c
   return field_tc_launch<TOut, 1, FACE>(xsplit, pt, Xf, e2tab, M, n, KS, B, scale, kout, bytes, flops, st, share);
 }
 
-// All of the tensor-core form: slices of the x- and y-phasors, the face factors, the volume
-// x < n - 1, the face x = n - 1 (y < n - 1), the edge x = y = n - 1.
+// The volume product on the fifth-generation tensor cores (grids from n = 65): one block
+// computes 128 lines by 64 x-values with tcgen05.mma (M = 128, N = 64, K = 16, bf16 operands
+// from shared memory, FP32 accumulators in tensor memory: the seven slice groups take 7 x 64
+// of the 512 columns). The A operand (the line factors' slices) is staged by all 256 threads
+// into K-major core matrices; the B operand (the x-phasors' slices, the same for every line
+// of a sample) is laid out in that form once per sample (k_uxslices) and brought in by one
+// bulk copy per chunk. Chunks of two k-steps are double-buffered: one thread issues the 56
+// products of a chunk and commits them to the buffer's mbarrier while the block stages the
+// next chunk, so the staging's FP32 work runs under the tensor cores' work. Every 256
+// features (and at the end) the group sums are read from tensor memory and folded into a
+// double-float; the next product overwrites them. Every wait is bounded: a block whose wait
+// runs out records *err, drains its copies and products, writes NaN to its nodes and frees
+// its tensor memory.
+constexpr int kUmM = 128, kUmN = 64, kUmKC = 2;
+constexpr unsigned kUmCols = 512;
+constexpr int kUmATile = kUmM * 32, kUmBTile = kUmN * 32;  // bytes of one (k-step, slice) tile
+constexpr int kUmAChunk = kUmKC * kTcSlices * kUmATile, kUmBChunk = kUmKC * kTcSlices * kUmBTile;
+constexpr int kUmStage = kUmAChunk + kUmBChunk;
+constexpr size_t kUmSmem = 2 * (size_t)kUmStage + 128 + kUmM * sizeof(int2) + 64 * sizeof(float) + 64;
+
+static bool umma_applies(int n) { return n >= 65 && (n - 1) % kUmN == 0; }
+
+size_t tc_uxslice_bytes(int B, int M, int n) {
+  return umma_applies(n) ? (size_t)B * ((n - 1) / kUmN) * ((M + 7) / 8) * kTcSlices * kUmBTile : 0;
+}
+
+// XU[s][x block][k-step][slice]: 64 x-rows by 16 k in K-major core matrices, (Re X, -Im X) of
+// feature 8 ks + fl at k = 2 fl, 2 fl + 1. One thread per (sample, x block, k-step, x, feature).
+__global__ void k_uxslices(const float4* __restrict__ xsplit, int B, int M, int n, int KS,
+                           unsigned char* __restrict__ XU) {
+  const int XB = (n - 1) / kUmN;
+  const size_t total = (size_t)B * XB * KS * kUmN * 8;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int fl = (int)(t & 7);
+    size_t r = t >> 3;
+    const int xr = (int)(r % kUmN);
+    r /= kUmN;
+    const int ks = (int)(r % KS);
+    r /= KS;
+    const int xb = (int)(r % XB);
+    const int s = (int)(r / XB);
+    const int f = ks * 8 + fl;
+    float re[kTcSlices], im[kTcSlices];
+    if (f < M) {
+      const float4 v = xsplit[((size_t)s * 3 * M + f) * n + xb * kUmN + xr];
+      df::slice7(v.x, v.y, re);
+      df::slice7(-v.z, -v.w, im);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kTcSlices; ++i) re[i] = im[i] = 0.f;
+    }
+    unsigned char* o = XU + (((size_t)(s * XB + xb) * KS + ks) * kTcSlices) * kUmBTile + (xr >> 3) * 256 +
+                       (fl >> 2) * 128 + (xr & 7) * 16 + (fl & 3) * 4;
+#pragma unroll
+    for (int i = 0; i < kTcSlices; ++i) *reinterpret_cast<uint32_t*>(o + (size_t)i * kUmBTile) = pack_bf16x2(re[i], im[i]);
+  }
+}
+
+template <typename TOut, bool MULTI, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_field_umma(const float4* __restrict__ tsplit,
+                                                               const unsigned char* __restrict__ XU,
+                                                               const float* __restrict__ e2tab, int M, int n, int KS,
+                                                               double scale, long long budget, int* err,
+                                                               TOut* __restrict__ kout) {
+  extern __shared__ unsigned char um_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)um_raw + 127) & ~(uintptr_t)127);
+  int2* sline = reinterpret_cast<int2*>(sm + 2 * kUmStage);  // (y, z) of line slot l, y = -1: none
+  float* se2 = reinterpret_cast<float*>(sline + kUmM);
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(se2 + 64);  // [2]: B chunk landed
+  uint64_t* mdone = bfull + 2;                               // [2]: the chunk's products done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s = blockIdx.z, xb = blockIdx.x, XB = (n - 1) / kUmN;
+  const size_t n2 = (size_t)n * n, L0 = (size_t)blockIdx.y * kUmM;
+  if (tid < kUmM) {
+    const size_t line = L0 + tid;
+    sline[tid] = line < n2 ? make_int2((int)(line % n), (int)(line / n)) : make_int2(-1, 0);
+  }
+  if (tid < 64) se2[tid] = e2tab[tid];
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&bfull[q], 1);
+      mbar_init(&mdone[q], 1);
+    }
+    mbar_fence_init();
+  }
+  if (warp == 0) umma::alloc(tslot, kUmCols);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const float4* Ty = tsplit + ((size_t)s * 3 + 1) * M * n;
+  const float4* Tz = Ty + (size_t)M * n;
+  const unsigned char* xu = XU + ((size_t)(s * XB + xb) * KS) * kTcSlices * kUmBTile;
+  const uint32_t idesc = umma::idesc_bf16_f32(kUmM, kUmN);
+  const int nchunks = (KS + kUmKC - 1) / kUmKC;
+  // the thread's outputs: tensor-memory lane 32 (warp % 4) + lane, XW x-values from XW (warp / 4)
+  constexpr int XW = kUmN / (THREADS / 128);
+  const int myl = 32 * (warp & 3) + lane, xh = XW * (warp >> 2);
+  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)xh;
+  // MULTI (more than 256 features): the double-float running sums of the folds
+  float th[MULTI ? XW : 1], tl[MULTI ? XW : 1];
+#pragma unroll
+  for (int q = 0; q < (MULTI ? XW : 1); ++q) th[q] = tl[q] = 0.f;
+  int last_commit = -1, last_copy = -1;  // (thread 0's) the last chunk whose products / copy were issued
+  bool bad = false;                       // a bounded wait of this thread ran out
+  auto wait = [&](uint64_t* mb, int chunk, long long bud) {
+    if (!mbar_wait_bounded(mb, (unsigned)((chunk >> 1) & 1), bud)) {
+      bad = true;
+      atomicExch(err, 1);
+    }
+  };
+  const float sch = narrow(scale), scl = narrow(scale - widen(sch));
+  const size_t myline = L0 + myl;
+  TOut* out = kout + (size_t)s * n2 * n + myline * n + xb * kUmN + xh;
+  // the groups' current sums of the thread's 32 x-values: folded into (th, tl) (last = false)
+  // or, with the earlier folds, turned into k and stored (last = true)
+  auto fold = [&](bool last) {
+#pragma unroll
+    for (int c0 = 0; c0 < XW; c0 += 16) {
+      float v[kTcSlices][16];
+#pragma unroll
+      for (int g = 0; g < kTcSlices; ++g) umma::ld16(trow + (uint32_t)(g * kUmN + c0), v[g]);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        float gs[kTcSlices], sh, sl;
+#pragma unroll
+        for (int g = 0; g < kTcSlices; ++g) gs[g] = v[g][q];
+        df::sum7(gs, sh, sl);
+        if (MULTI) df::add(th[c0 + q], tl[c0 + q], sh, sl, sh, sl);
+        if (!last) {
+          if (MULTI) {
+            th[c0 + q] = sh;
+            tl[c0 + q] = sl;
+          }
+          continue;
+        }
+        if (myline >= n2) continue;
+        float yh, yl, eh, el;
+        int m;
+        df::mul(sh, sl, sch, scl, yh, yl);
+        df::exp_df(yh, yl, se2, se2 + 32, eh, el, m);
+        if constexpr (sizeof(TOut) == 8)
+          out[c0 + q] = (widen(eh) + widen(el)) * __hiloint2double((m + 1023) << 20, 0);
+        else
+          out[c0 + q] = (m > -126 && m < 128) ? __fmul_rn(eh, __int_as_float((m + 127) << 23)) : ldexpf(eh, m);
+      }
+    }
+  };
+  for (int c = 0; c < nchunks; ++c) {
+    const int b = c & 1;
+    const int ks0 = c * kUmKC, kn = min(kUmKC, KS - ks0);
+    unsigned char* sA = sm + (size_t)b * kUmStage;
+    unsigned char* sB = sA + kUmAChunk;
+    // the buffer is free once the products of chunk c - 2 are done
+    if (c >= 2) wait(&mdone[b], c - 2, budget);
+    umma::fence_after_sync();
+    if (tid == 0 && !bad) {
+      const unsigned bytes = (unsigned)(kn * kTcSlices * kUmBTile);
+      mbar_arrive_expect_tx(&bfull[b], bytes);
+      bulk_g2s(sB, xu + (size_t)ks0 * kTcSlices * kUmBTile, bytes, &bfull[b]);
+      last_copy = c;
+    }
+    // staging: 2048 / THREADS (line, feature) items per thread, their table loads issued four
+    // at a time
+#pragma unroll 1
+    for (int h = 0; h < 2048 / THREADS / 4 && !bad; ++h) {
+      float4 bq[4], dq[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int it = tid + (4 * h + r) * THREADS;
+        const int fl4 = it & 3, rr = (it >> 2) & 7, kg = (it >> 5) & 1, rg = (it >> 6) & 15, ksl = it >> 10;
+        const int f = (ks0 + ksl) * 8 + kg * 4 + fl4;
+        const int2 yz = sline[rg * 8 + rr];
+        if (ksl < kn && yz.x >= 0 && f < M) {
+          bq[r] = Ty[(size_t)f * n + yz.x];
+          dq[r] = Tz[(size_t)f * n + yz.y];
+        } else {
+          bq[r] = dq[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int it = tid + (4 * h + r) * THREADS;
+        const int fl4 = it & 3, rr = (it >> 2) & 7, kg = (it >> 5) & 1, rg = (it >> 6) & 15, ksl = it >> 10;
+        if (ksl >= kn) continue;
+        float t1h, t1l, t2h, t2l, rh, rl, ih, il, qr[kTcSlices], qi[kTcSlices];
+        df::mul(bq[r].x, bq[r].y, dq[r].x, dq[r].y, t1h, t1l);
+        df::mul(bq[r].z, bq[r].w, dq[r].z, dq[r].w, t2h, t2l);
+        df::add(t1h, t1l, -t2h, -t2l, rh, rl);
+        df::mul(bq[r].x, bq[r].y, dq[r].z, dq[r].w, t1h, t1l);
+        df::mul(bq[r].z, bq[r].w, dq[r].x, dq[r].y, t2h, t2l);
+        df::add(t1h, t1l, t2h, t2l, ih, il);
+        df::slice7(rh, rl, qr);  // zero tables give zero slices
+        df::slice7(ih, il, qi);
+        unsigned char* dst = sA + (size_t)ksl * kTcSlices * kUmATile + rg * 256 + kg * 128 + rr * 16 + fl4 * 4;
+#pragma unroll
+        for (int j = 0; j < kTcSlices; ++j)
+          *reinterpret_cast<uint32_t*>(dst + (size_t)j * kUmATile) = pack_bf16x2(qr[j], qi[j]);
+      }
+    }
+    fence_proxy_async();
+    umma::fence_before_sync();
+    bad = __syncthreads_or(bad);
+    if (bad) break;
+    if (tid == 0) {
+      wait(&bfull[b], c, budget);
+      if (!bad) {
+        umma::fence_after_sync();
+        const bool fresh = (ks0 * 8) % kTcFold == 0;  // the first chunk of a fold period
+        for (int ksl = 0; ksl < kn; ++ksl)
+#pragma unroll
+          for (int j = 0; j < kTcSlices; ++j)
+#pragma unroll
+            for (int i = kTcSlices - 1 - j; i >= 0; --i) {
+              const uint64_t ad = umma::smem_desc(smem_addr(sA + (size_t)(ksl * kTcSlices + i) * kUmATile), 128, 256);
+              const uint64_t bd = umma::smem_desc(smem_addr(sB + (size_t)(ksl * kTcSlices + j) * kUmBTile), 128, 256);
+              umma::mma_bf16(tmem + (uint32_t)((i + j) * kUmN), ad, bd, idesc,
+                             (fresh && ksl == 0 && j == 0) ? 0u : 1u);
+            }
+        umma::commit(&mdone[b]);
+        last_commit = c;
+      }
+    }
+    // every 256 features, before the next chunk overwrites the groups: fold them
+    if (((ks0 + kn) * 8) % kTcFold == 0 && c + 1 < nchunks) {
+      bad = __syncthreads_or(bad);
+      if (bad) break;
+      wait(&mdone[b], c, budget);
+      umma::fence_after_sync();
+      bad = __syncthreads_or(bad);
+      if (bad) break;
+      fold(false);
+      umma::fence_before_sync();
+      __syncthreads();
+    }
+  }
+  bad = __syncthreads_or(bad);
+  if (!bad) wait(&mdone[(nchunks - 1) & 1], nchunks - 1, budget);
+  bad = __syncthreads_or(bad);
+  if (bad && tid == 0) {
+    // drain: the last issued products and copy land before the block leaves
+    if (last_commit >= 0) mbar_wait_bounded(&mdone[last_commit & 1], (unsigned)((last_commit >> 1) & 1), kDrainBudget);
+    if (last_copy >= 0) mbar_wait_bounded(&bfull[last_copy & 1], (unsigned)((last_copy >> 1) & 1), kDrainBudget);
+  }
+  umma::fence_after_sync();
+  if (!bad) {
+    fold(true);
+  } else if (myline < n2) {
+#pragma unroll 4
+    for (int q = 0; q < XW; ++q) out[q] = (TOut)__int_as_float(0x7fc00000);
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::dealloc(tmem, kUmCols);
+}
+
 template <typename TOut>
-int field_tc_all(const double2* tab, const float4* xsplit, float4* pt, uint4* Xf, float* e2tab, int M, int n, int B,
-                 double scale, void* kout, double bytes, double flops, cudaStream_t st) {
+int field_umma_launch(const float4* xsplit, const unsigned char* XU, const float* e2tab, int* err, int M, int n,
+                      int KS, int B, double scale, void* kout, double bytes, double flops, cudaStream_t st,
+                      double share) {
+  // one fold (up to 256 features): 16 warps at 128 registers; more: 8 warps, which also hold
+  // the running double-float sums
+  static const cudaError_t attr1 = cudaFuncSetAttribute(k_field_umma<TOut, false, 512>,
+                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmem);
+  static const cudaError_t attr2 = cudaFuncSetAttribute(k_field_umma<TOut, true, 256>,
+                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmem);
+  MLMC_CUDA_TRY(attr1);
+  MLMC_CUDA_TRY(attr2);
+  const dim3 grid((unsigned)((n - 1) / kUmN), (unsigned)(((size_t)n * n + kUmM - 1) / kUmM), (unsigned)B);
+  const long long budget = wait_budget_clocks();
+  if (M > kTcFold)
+    MLMC_LAUNCH("field_tc", bytes * share, flops * share, st,
+                (k_field_umma<TOut, true, 256><<<grid, 256, kUmSmem, st>>>(xsplit, XU, e2tab, M, n, KS, scale, budget,
+                                                                            err, (TOut*)kout)));
+  else
+    MLMC_LAUNCH("field_tc", bytes * share, flops * share, st,
+                (k_field_umma<TOut, false, 512><<<grid, 512, kUmSmem, st>>>(xsplit, XU, e2tab, M, n, KS, scale, budget,
+                                                                             err, (TOut*)kout)));
+  return MLMC_OK;
+}
+
+// All of the tensor-core form: slices of the x- and y-phasors, the face factors, the volume
+// x < n - 1 (tcgen05 from n = 65 unless warp_mma, warp-level mma.sync otherwise), the face
+// x = n - 1 (y < n - 1), the edge x = y = n - 1.
+template <typename TOut>
+int field_tc_all(const double2* tab, const float4* xsplit, float4* pt, uint4* Xf, unsigned char* XU, int* err,
+                 float* e2tab, int M, int n, int B, double scale, void* kout, double bytes, double flops,
+                 cudaStream_t st, bool warp_mma) {
   const int KS = (M + 7) / 8;
   const size_t nxs = (size_t)B * ((n - 1) / 16) * KS * 32;
   MLMC_LAUNCH("xslices", (double)nxs * 2 * 112.0, (double)nxs * 2 * 500.0, st,
@@ -745,8 +1031,16 @@ int field_tc_all(const double2* tab, const float4* xsplit, float4* pt, uint4* Xf
   MLMC_LAUNCH("face_factors", (double)nf * 48.0, (double)nf * 40.0, st,
               (k_face_factors<<<blocks_for(nf, 256), 256, 0, st>>>(xsplit, B, M, n, pt)));
   const double n3 = (double)n * n * n;
-  MLMC_TRY((field_tc_dispatch<TOut, false>(xsplit, pt, Xf, e2tab, M, n, KS, B, scale, kout, bytes, flops, st,
-                                           (double)(n - 1) * n * n / n3)));
+  const double vshare = (double)(n - 1) * n * n / n3;
+  if (!warp_mma && umma_applies(n)) {
+    const size_t nux = (size_t)B * ((n - 1) / kUmN) * KS * kUmN * 8;
+    MLMC_LAUNCH("xslices", (double)nux * 28.0, (double)nux * 250.0, st,
+                (k_uxslices<<<blocks_for(nux, 256), 256, 0, st>>>(xsplit, B, M, n, KS, XU)));
+    MLMC_TRY(field_umma_launch<TOut>(xsplit, XU, e2tab, err, M, n, KS, B, scale, kout, bytes, flops, st, vshare));
+  } else {
+    MLMC_TRY((field_tc_dispatch<TOut, false>(xsplit, pt, Xf, e2tab, M, n, KS, B, scale, kout, bytes, flops, st,
+                                             vshare)));
+  }
   MLMC_TRY((field_tc_dispatch<TOut, true>(xsplit, pt, Xf + nxs * kTcSlices, e2tab, M, n, KS, B, scale, kout, bytes,
                                           flops, st, (double)(n - 1) * n / n3)));
   MLMC_LAUNCH("field_edge", bytes * n / n3, flops * n / n3, st,
@@ -762,7 +1056,7 @@ size_t field_scratch_bytes(int B, int M, int n) {
   return a256((size_t)B * M * 3 * sizeof(double)) + a256((size_t)B * M * sizeof(double)) +
          a256((size_t)B * 3 * M * n * sizeof(double2)) + a256((size_t)B * 3 * M * n * sizeof(float4)) +
          (tc_applies(n) ? a256(2 * tc_xslice_bytes(B, M, n)) + a256(64 * sizeof(float)) +
-                              a256((size_t)B * M * n * sizeof(float4))
+                              a256((size_t)B * M * n * sizeof(float4)) + a256(tc_uxslice_bytes(B, M, n)) + 256
                         : 0);
 }
 
@@ -770,7 +1064,7 @@ int field_arith_default() {
   static const int a = [] {
     const char* e = getenv("MLMC_FIELD_ARITH");
     const int v = e ? atoi(e) : (int)kFieldTC;
-    return v >= kFieldDF32Line && v <= kFieldTC ? v : (int)kFieldTC;
+    return v >= kFieldDF32Line && v <= kFieldTCWarp ? v : (int)kFieldTC;
   }();
   return a;
 }
@@ -791,6 +1085,8 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
   uint4* Xf = tc_applies(n) ? (uint4*)carve(2 * tc_xslice_bytes(B, cfg.M, n)) : nullptr;
   float* e2tab = tc_applies(n) ? (float*)carve(64 * sizeof(float)) : nullptr;
   float4* pt = tc_applies(n) ? (float4*)carve((size_t)B * cfg.M * n * sizeof(float4)) : nullptr;
+  unsigned char* XU = tc_applies(n) ? (unsigned char*)carve(tc_uxslice_bytes(B, cfg.M, n)) : nullptr;
+  int* err = tc_applies(n) ? (int*)carve(256) : nullptr;
   const size_t nf = (size_t)B * cfg.M;
   MLMC_LAUNCH("features", nf * 40.0, nf * 200.0, st,
               (k_features<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(ids_dev, B, cfg.M, cfg.run_seed,
@@ -821,14 +1117,17 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
     else
       MLMC_LAUNCH("field_f64", bytes, flops, st,
                   (k_field<float><<<grid, kFieldThreads, smem, st>>>(tab, cfg.M, n, LT, MC, scale, (float*)kout)));
-  } else if (arith == kFieldDF32Line || arith == kFieldTC) {
+  } else if (arith == kFieldDF32Line || arith == kFieldTC || arith == kFieldTCWarp) {
     const int MCl = cfg.M < 64 ? cfg.M : 64;
     const unsigned lines = (unsigned)(((size_t)n * n + kFieldThreads - 1) / kFieldThreads);
-    if (arith == kFieldTC && tc_applies(n)) {
+    if ((arith == kFieldTC || arith == kFieldTCWarp) && tc_applies(n)) {
+      const bool warp_mma = arith == kFieldTCWarp;
       if (dtype == MLMC_F64)
-        MLMC_TRY(field_tc_all<double>(tab, xsplit, pt, Xf, e2tab, cfg.M, n, B, scale, kout, bytes, flops, st));
+        MLMC_TRY(field_tc_all<double>(tab, xsplit, pt, Xf, XU, err, e2tab, cfg.M, n, B, scale, kout, bytes, flops, st,
+                                      warp_mma));
       else
-        MLMC_TRY(field_tc_all<float>(tab, xsplit, pt, Xf, e2tab, cfg.M, n, B, scale, kout, bytes, flops, st));
+        MLMC_TRY(field_tc_all<float>(tab, xsplit, pt, Xf, XU, err, e2tab, cfg.M, n, B, scale, kout, bytes, flops, st,
+                                     warp_mma));
     } else {
       // x < n - 1 in tiles of 8 (of 4 on the 5-node grid), then x = n - 1
       const int xt = (n - 1) % kXC == 0 ? kXC : 4;

@@ -12,12 +12,13 @@ size_t field_scratch_bytes(int B, int M, int n);
 
 // Arithmetic of the log k sum: double-float on the FP32 pipe with one (y, z) line per
 // thread, FP64, double-float with flattened outputs, or bf16 slices on the tensor cores with
-// exact FP32 group sums (the default; on grids with (n - 1) a multiple of 16 from n = 17,
-// other grids take the double-float line form).
-enum { kFieldDF32Line = 0, kFieldFP64 = 1, kFieldDF32 = 2, kFieldTC = 3 };
+// exact FP32 group sums (on grids with (n - 1) a multiple of 16 from n = 17, other grids take
+// the double-float line form): kFieldTC (the default) runs the volume on tcgen05 from n = 65
+// and on the warp-level mma.sync below, kFieldTCWarp on mma.sync everywhere.
+enum { kFieldDF32Line = 0, kFieldFP64 = 1, kFieldDF32 = 2, kFieldTC = 3, kFieldTCWarp = 4 };
 
 // The arithmetic field_eval_dev uses by default: kFieldTC, or the value of the environment
-// variable MLMC_FIELD_ARITH (0..3) read once.
+// variable MLMC_FIELD_ARITH (0..4) read once.
 int field_arith_default();
 
 // k_out[s][z][y][x] = exp(log k) at the n^3 nodes for the B ids in ids_dev (device).

@@ -1,0 +1,77 @@
+// tcgen05 (fifth-generation tensor core) building blocks: tensor-memory allocation, the
+// shared-memory matrix descriptor of a K-major operand without swizzle, the instruction
+// descriptor of kind::f16 with bf16 operands and FP32 accumulation, the MMA, its commit to an
+// mbarrier, and the 32-lane tensor-memory load. Inline PTX for sm_100a-family targets.
+//
+// Operand layout (K-major, no swizzle): the matrix is cut into core matrices of 8 rows by 16
+// bytes (8 bf16 along K), each stored as 128 contiguous bytes (row r at byte 16 r). The
+// descriptor's leading byte offset is the distance between core matrices adjacent along K,
+// its stride byte offset the distance between core matrices adjacent along M (or N); both
+// readings were checked on the GB300 against a CPU product before this layout was used.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mlmc {
+namespace umma {
+
+// 64-bit shared-memory descriptor: start address, leading (K) and stride (M/N) byte offsets,
+// descriptor version 1 (bits 46-47), base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B bf16 (bits
+// 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bits 17-22, M / 16 at 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Allocates ncols tensor-memory columns (a power of two, 32..512) for this CTA; the address
+// lands in shared memory at slot. Executed by one whole warp.
+__device__ __forceinline__ void alloc(uint32_t* slot, unsigned ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void dealloc(uint32_t taddr, unsigned ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// D[tmem] (+)= A * B^T for one K = 16 step; accumulate = 0 overwrites D. One thread issues.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// The mbarrier receives one arrival when every MMA this thread issued before has completed.
+__device__ __forceinline__ void commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(mbar))
+               : "memory");
+}
+// 16 consecutive FP32 columns of the warp's 32 lanes (thread i: lane base + i), waited for
+// inside the same statement so that no use of the values can be scheduled before the wait.
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+}  // namespace umma
+}  // namespace mlmc

@@ -1,10 +1,12 @@
 """The field's arithmetic variants (MLMC_FIELD_ARITH, read once per process, so each runs
 in a child process): double-float per line, FP64, double-float with flattened outputs,
-bf16 slices on the tensor cores (the default). Each must give the oracle's field to
+bf16 slices on the tensor cores (3, the default: tcgen05 for the volume from 65^3, the
+warp-level mma.sync below; 4: mma.sync everywhere). Each must give the oracle's field to
 1e-12 relative, and its FP32 output must be its FP64 output rounded. The tensor-core form
 also runs every block shape (16 to 128 x-values per block, 17^3 to 257^3), a feature count
 that is not a multiple of the 8 features of a k-step, the fold of its group sums every 256
-features (M = 1024), the exponential covariance, and a batch whose samples differ."""
+features (M = 1024, both forms), the exponential covariance, and a batch whose samples
+differ."""
 import os
 import subprocess
 import sys
@@ -25,8 +27,8 @@ import os, sys
 worst = 0.0
 cases = [(33, 3, 256, 0.3, 0), (17, 2, 100, 0.1, 0)]
 if len(sys.argv) > 1:
-    cases = [(65, 2, 256, 0.3, 0), (129, 1, 256, 0.15, 1), (33, 2, 1024, 0.3, 0), (257, 1, 64, 0.2, 0),
-             (17, 40, 256, 0.3, 1)]
+    cases = [(65, 2, 256, 0.3, 0), (129, 1, 256, 0.15, 1), (33, 2, 1024, 0.3, 0), (65, 1, 1024, 0.3, 0),
+             (257, 1, 64, 0.2, 0), (17, 40, 256, 0.3, 1)]
 for n, B, M, ell, cov in cases:
     ids = sample_ids(2, 7, B)
     fc = mg.field_cfg(RUN_SEED, 1.0, ell, M, cov)
@@ -52,7 +54,7 @@ assert worst <= 1.0
 """
 
 
-@pytest.mark.parametrize("arith", [0, 1, 2, 3])
+@pytest.mark.parametrize("arith", [0, 1, 2, 3, 4])
 def test_field_arithmetic_variant_matches_oracle(arith):
     env = dict(os.environ, MLMC_FIELD_ARITH=str(arith))
     res = subprocess.run([sys.executable, "-c", CHILD], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
@@ -60,8 +62,10 @@ def test_field_arithmetic_variant_matches_oracle(arith):
     print(arith, res.stdout.strip())
 
 
-def test_field_tensor_core_shapes_match_oracle():
-    env = dict(os.environ, MLMC_FIELD_ARITH="3")
+@pytest.mark.parametrize("arith", [3, 4])
+def test_field_tensor_core_shapes_match_oracle(arith):
+    """3: tcgen05 for the 65^3-257^3 volumes, 4: the warp-level mma.sync everywhere."""
+    env = dict(os.environ, MLMC_FIELD_ARITH=str(arith))
     res = subprocess.run([sys.executable, "-c", CHILD, "tc"], cwd=ROOT, env=env, capture_output=True, text=True,
                          timeout=900)
     assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-4000:]
