@@ -702,7 +702,8 @@ def field_roofline(prof, peaks=None):
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak if peak else None,
                     "peak_source": "measured sustained cuBLAS bf16" if peak else None,
-                    "ncu": "profiles/field_tc_n129_b8.md"})
+                    "ncu": "profiles/field_umma_n129_b8.md (tcgen05 volume), profiles/field_tc_n129_b8.md "
+                           "(mma.sync form)"})
         return out
     out.update({"kernel": "field_df32", "bound": "alu (FP32 pipe, double-float)",
                 "fp32_ops_per_s": 24.0 * out["node_features_per_s"] if out["node_features_per_s"] else None,

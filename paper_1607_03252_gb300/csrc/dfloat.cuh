@@ -66,7 +66,10 @@ MLMC_DF_HD void add(float ah, float al, float bh, float bl, float& sh, float& sl
 // every slice has at most 8 significant bits (exact in bf16), and |v - sum t| <= 2^-50 + 2^-60.
 // A slice is v rounded to its grid by adding and subtracting 1.5 * 2^23 times the grid step
 // (the sum lands in the binade whose ulp is the step); the remainder is exact. The first three
-// come from h alone; l is added (TwoSum) before the fourth, the TwoSum error before the sixth.
+// come from h alone; l is added before the fourth, that sum's error before the sixth. Both
+// additions are FastTwoSum: the remainder is a multiple of the ulp of the value it came from
+// (h, then the first sum), so it is zero or at least as large as the addend (at most half that
+// ulp), which makes FastTwoSum exact.
 MLMC_DF_HD void slice7(float h, float l, float t[7]) {
   const float C0 = 98304.f;                     // 1.5 * 2^16: step 2^-7
   const float C1 = 768.f;                       // 1.5 * 2^9: 2^-14
@@ -82,12 +85,12 @@ MLMC_DF_HD void slice7(float h, float l, float t[7]) {
   r = sub(r, t[1]);
   t[2] = sub(add(r, C2), C2);
   r = sub(r, t[2]);
-  two_sum(r, l, r, e);
+  fast_two_sum(r, l, r, e);
   t[3] = sub(add(r, C3), C3);
   r = sub(r, t[3]);
   t[4] = sub(add(r, C4), C4);
   r = sub(r, t[4]);
-  two_sum(r, e, r, e2);
+  fast_two_sum(r, e, r, e2);
   t[5] = sub(add(r, C5), C5);
   r = sub(r, t[5]);
   t[6] = sub(add(r, C6), C6);
@@ -151,4 +154,5 @@ MLMC_DF_HD void exp_df(float yh, float yl, const float* tab_h, const float* tab_
 }
 
 }  // namespace df
+
 }  // namespace mlmc

@@ -392,6 +392,24 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+// The seven bf16 pairs (Re, Im) of the slices of Q = Y Z, Y and Z double-float complex
+// (Re hi, Re lo, Im hi, Im lo): Re Q = Re Y Re Z - Im Y Im Z, Im Q = Re Y Im Z + Im Y Re Z.
+// (The paired FP32 instructions, f32x2, with Re and Im as the two lanes measured slower here:
+// the packing of the lanes costs more integer instructions than the pairing saves.)
+__device__ __forceinline__ void q_slices(const float4& y, const float4& z, uint32_t (&q)[kTcSlices]) {
+  float t1h, t1l, t2h, t2l, rh, rl, ih, il, qr[kTcSlices], qi[kTcSlices];
+  df::mul(y.x, y.y, z.x, z.y, t1h, t1l);
+  df::mul(y.z, y.w, z.z, z.w, t2h, t2l);
+  df::add(t1h, t1l, -t2h, -t2l, rh, rl);
+  df::mul(y.x, y.y, z.z, z.w, t1h, t1l);
+  df::mul(y.z, y.w, z.x, z.y, t2h, t2l);
+  df::add(t1h, t1l, t2h, t2l, ih, il);
+  df::slice7(rh, rl, qr);
+  df::slice7(ih, il, qi);
+#pragma unroll
+  for (int j = 0; j < kTcSlices; ++j) q[j] = pack_bf16x2(qr[j], qi[j]);
+}
+
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint4& a, const uint2& b) {
   asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
       "{%0, %1, %2, %3};\n"
@@ -407,8 +425,8 @@ size_t tc_xslice_bytes(int B, int M, int n) {
 // slice, for the x-phasors (axis 0, into Xf) and the y-phasors (axis 1, into Xf + the size of
 // one axis: the A operand of the x = n - 1 face). Threads 0..31 also write 2^(j/32) as
 // double-floats (e2tab[j], e2tab[32 + j]) for the exp.
-__global__ void k_xslices(const float4* __restrict__ xsplit, int B, int M, int n, int KS, uint4* __restrict__ Xf,
-                          float* __restrict__ e2tab) {
+__global__ void k_xslices(const float4* __restrict__ xsplit, int B, int M, int n, int KS, int axis0,
+                          uint4* __restrict__ Xf, float* __restrict__ e2tab) {
   const int RT = (n - 1) / 16;
   const size_t per_axis = (size_t)B * RT * KS * 32;
   const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -418,7 +436,7 @@ __global__ void k_xslices(const float4* __restrict__ xsplit, int B, int M, int n
     e2tab[t0] = h;
     e2tab[32 + t0] = narrow(v - widen(h));
   }
-  for (size_t t = t0; t < 2 * per_axis; t += (size_t)gridDim.x * blockDim.x) {
+  for (size_t t = t0 + axis0 * per_axis; t < 2 * per_axis; t += (size_t)gridDim.x * blockDim.x) {
     const int axis = t < per_axis ? 0 : 1;
     const size_t ta = t - axis * per_axis;
     const int lane = (int)(ta & 31);
@@ -531,35 +549,27 @@ __device__ __forceinline__ void tc_stage(int it, int m0, int M, int n, const flo
   const int4 L = sline[ctl * 8 + gg];  // (sample, y or z, z, valid) of the block's line slot
   const bool valid = L.w != 0;
   const int si = L.x;
-  float qr[kTcSlices], qi[kTcSlices];
+  uint32_t q[kTcSlices];
   if (valid && f < M) {
-    float rh, rl, ih, il;
     if (FACE) {
       const float4 p = pt[((size_t)si * M + f) * n + L.y];
-      rh = p.x;
-      rl = p.y;
-      ih = p.z;
-      il = p.w;
+      float qr[kTcSlices], qi[kTcSlices];
+      df::slice7(p.x, p.y, qr);
+      df::slice7(p.z, p.w, qi);
+#pragma unroll
+      for (int j = 0; j < kTcSlices; ++j) q[j] = pack_bf16x2(qr[j], qi[j]);
     } else {
       const float4* Ty = tsplit + ((size_t)si * 3 + 1) * M * n;
-      const float4 b = Ty[(size_t)f * n + L.y], d = Ty[((size_t)M + f) * n + L.z];
-      float t1h, t1l, t2h, t2l;
-      df::mul(b.x, b.y, d.x, d.y, t1h, t1l);
-      df::mul(b.z, b.w, d.z, d.w, t2h, t2l);
-      df::add(t1h, t1l, -t2h, -t2l, rh, rl);
-      df::mul(b.x, b.y, d.z, d.w, t1h, t1l);
-      df::mul(b.z, b.w, d.x, d.y, t2h, t2l);
-      df::add(t1h, t1l, t2h, t2l, ih, il);
+      q_slices(Ty[(size_t)f * n + L.y], Ty[((size_t)M + f) * n + L.z], q);
     }
-    df::slice7(rh, rl, qr);
-    df::slice7(ih, il, qi);
   } else {
 #pragma unroll
-    for (int j = 0; j < kTcSlices; ++j) qr[j] = qi[j] = 0.f;
+    for (int j = 0; j < kTcSlices; ++j) q[j] = 0u;
   }
-  uint32_t* dst = reinterpret_cast<uint32_t*>(buf) + ((size_t)(ksl * kTcSlices * S::CT + ctl) * 32 + gg * 4 + cc) * 2 + half;
+  uint32_t* dst =
+      reinterpret_cast<uint32_t*>(buf) + ((size_t)(ksl * kTcSlices * S::CT + ctl) * 32 + gg * 4 + cc) * 2 + half;
 #pragma unroll
-  for (int j = 0; j < kTcSlices; ++j) dst[j * S::CT * 64] = pack_bf16x2(qr[j], qi[j]);
+  for (int j = 0; j < kTcSlices; ++j) dst[j * S::CT * 64] = q[j];
 }
 
 template <typename TOut, int RX, bool FACE>
@@ -788,12 +798,13 @@ __global__ void k_uxslices(const float4* __restrict__ xsplit, int B, int M, int 
     unsigned char* o = XU + (((size_t)(s * XB + xb) * KS + ks) * kTcSlices) * kUmBTile + (xr >> 3) * 256 +
                        (fl >> 2) * 128 + (xr & 7) * 16 + (fl & 3) * 4;
 #pragma unroll
-    for (int i = 0; i < kTcSlices; ++i) *reinterpret_cast<uint32_t*>(o + (size_t)i * kUmBTile) = pack_bf16x2(re[i], im[i]);
+    for (int i = 0; i < kTcSlices; ++i)
+      *reinterpret_cast<uint32_t*>(o + (size_t)i * kUmBTile) = pack_bf16x2(re[i], im[i]);
   }
 }
 
-template <typename TOut, bool MULTI, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1) k_field_umma(const float4* __restrict__ tsplit,
+template <typename TOut, bool MULTI, int SW>
+__global__ void __launch_bounds__(32 * (SW + 1), 1) k_field_umma(const float4* __restrict__ tsplit,
                                                                const unsigned char* __restrict__ XU,
                                                                const float* __restrict__ e2tab, int M, int n, int KS,
                                                                double scale, long long budget, int* err,
@@ -831,7 +842,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_field_umma(const float4* __restr
   const uint32_t idesc = umma::idesc_bf16_f32(kUmM, kUmN);
   const int nchunks = (KS + kUmKC - 1) / kUmKC;
   // the thread's outputs: tensor-memory lane 32 (warp % 4) + lane, XW x-values from XW (warp / 4)
-  constexpr int XW = kUmN / (THREADS / 128);
+  // SW staging warps (they also read the accumulators out) and one issuing warp, warp SW
+  constexpr int STAGERS = 32 * SW;
+  const bool stager = warp < SW;
+  const int issuer = STAGERS;  // the thread that issues the copies and the products
+  constexpr int XW = kUmN / (SW / 4);
   const int myl = 32 * (warp & 3) + lane, xh = XW * (warp >> 2);
   const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)xh;
   // MULTI (more than 256 features): the double-float running sums of the folds
@@ -853,12 +868,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_field_umma(const float4* __restr
   // or, with the earlier folds, turned into k and stored (last = true)
   auto fold = [&](bool last) {
 #pragma unroll
-    for (int c0 = 0; c0 < XW; c0 += 16) {
-      float v[kTcSlices][16];
+    for (int c0 = 0; c0 < XW; c0 += 8) {
+      float v[kTcSlices][8];
 #pragma unroll
-      for (int g = 0; g < kTcSlices; ++g) umma::ld16(trow + (uint32_t)(g * kUmN + c0), v[g]);
+      for (int g = 0; g < kTcSlices; ++g) umma::ld8(trow + (uint32_t)(g * kUmN + c0), v[g]);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
+      for (int q = 0; q < 8; ++q) {
         float gs[kTcSlices], sh, sl;
 #pragma unroll
         for (int g = 0; g < kTcSlices; ++g) gs[g] = v[g][q];
@@ -883,6 +898,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_field_umma(const float4* __restr
       }
     }
   };
+  // (thread 0) the bulk copy of chunk cc's x-slices into its buffer
+  auto issue_copy = [&](int cc) {
+    const int k0 = cc * kUmKC, kk = min(kUmKC, KS - k0);
+    const unsigned bytes = (unsigned)(kk * kTcSlices * kUmBTile);
+    mbar_arrive_expect_tx(&bfull[cc & 1], bytes);
+    bulk_g2s(sm + (size_t)(cc & 1) * kUmStage + kUmAChunk, xu + (size_t)k0 * kTcSlices * kUmBTile, bytes,
+             &bfull[cc & 1]);
+    last_copy = cc;
+  };
+  if (tid == issuer) issue_copy(0);
   for (int c = 0; c < nchunks; ++c) {
     const int b = c & 1;
     const int ks0 = c * kUmKC, kn = min(kUmKC, KS - ks0);
@@ -891,20 +916,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_field_umma(const float4* __restr
     // the buffer is free once the products of chunk c - 2 are done
     if (c >= 2) wait(&mdone[b], c - 2, budget);
     umma::fence_after_sync();
-    if (tid == 0 && !bad) {
-      const unsigned bytes = (unsigned)(kn * kTcSlices * kUmBTile);
-      mbar_arrive_expect_tx(&bfull[b], bytes);
-      bulk_g2s(sB, xu + (size_t)ks0 * kTcSlices * kUmBTile, bytes, &bfull[b]);
-      last_copy = c;
-    }
-    // staging: 2048 / THREADS (line, feature) items per thread, their table loads issued four
-    // at a time
+    // staging: 2048 / STAGERS (line, feature) items per staging thread, their table loads
+    // issued four at a time
 #pragma unroll 1
-    for (int h = 0; h < 2048 / THREADS / 4 && !bad; ++h) {
+    for (int h = 0; h < 2048 / STAGERS / 4 && stager && !bad; ++h) {
       float4 bq[4], dq[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const int it = tid + (4 * h + r) * THREADS;
+        const int it = tid + (4 * h + r) * STAGERS;
         const int fl4 = it & 3, rr = (it >> 2) & 7, kg = (it >> 5) & 1, rg = (it >> 6) & 15, ksl = it >> 10;
         const int f = (ks0 + ksl) * 8 + kg * 4 + fl4;
         const int2 yz = sline[rg * 8 + rr];
@@ -917,43 +936,46 @@ __global__ void __launch_bounds__(THREADS, 1) k_field_umma(const float4* __restr
       }
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const int it = tid + (4 * h + r) * THREADS;
+        const int it = tid + (4 * h + r) * STAGERS;
         const int fl4 = it & 3, rr = (it >> 2) & 7, kg = (it >> 5) & 1, rg = (it >> 6) & 15, ksl = it >> 10;
         if (ksl >= kn) continue;
-        float t1h, t1l, t2h, t2l, rh, rl, ih, il, qr[kTcSlices], qi[kTcSlices];
-        df::mul(bq[r].x, bq[r].y, dq[r].x, dq[r].y, t1h, t1l);
-        df::mul(bq[r].z, bq[r].w, dq[r].z, dq[r].w, t2h, t2l);
-        df::add(t1h, t1l, -t2h, -t2l, rh, rl);
-        df::mul(bq[r].x, bq[r].y, dq[r].z, dq[r].w, t1h, t1l);
-        df::mul(bq[r].z, bq[r].w, dq[r].x, dq[r].y, t2h, t2l);
-        df::add(t1h, t1l, t2h, t2l, ih, il);
-        df::slice7(rh, rl, qr);  // zero tables give zero slices
-        df::slice7(ih, il, qi);
+        uint32_t q[kTcSlices];
+        q_slices(bq[r], dq[r], q);  // zero tables give zero slices
         unsigned char* dst = sA + (size_t)ksl * kTcSlices * kUmATile + rg * 256 + kg * 128 + rr * 16 + fl4 * 4;
 #pragma unroll
-        for (int j = 0; j < kTcSlices; ++j)
-          *reinterpret_cast<uint32_t*>(dst + (size_t)j * kUmATile) = pack_bf16x2(qr[j], qi[j]);
+        for (int j = 0; j < kTcSlices; ++j) *reinterpret_cast<uint32_t*>(dst + (size_t)j * kUmATile) = q[j];
       }
     }
     fence_proxy_async();
     umma::fence_before_sync();
     bad = __syncthreads_or(bad);
     if (bad) break;
-    if (tid == 0) {
-      wait(&bfull[b], c, budget);
+    if (tid == issuer) {
+      // the x-slices of chunk c + 1 go to the other buffer once the products of chunk c - 1,
+      // its last readers, are done (they are by now as a rule), a chunk ahead of their use
+      if (c + 1 < nchunks) {
+        if (c >= 1) wait(&mdone[b ^ 1], c - 1, budget);
+        if (!bad) issue_copy(c + 1);
+      }
+      if (!bad) wait(&bfull[b], c, budget);
       if (!bad) {
         umma::fence_after_sync();
         const bool fresh = (ks0 * 8) % kTcFold == 0;  // the first chunk of a fold period
-        for (int ksl = 0; ksl < kn; ++ksl)
+        // a tile's descriptor is the chunk base's plus its byte offset / 16 (shared-memory
+        // addresses stay below 2^18, so the 14-bit address field does not carry)
+        const uint64_t ad0 = umma::smem_desc(smem_addr(sA), 128, 256), bd0 = umma::smem_desc(smem_addr(sB), 128, 256);
+#pragma unroll
+        for (int ksl = 0; ksl < kUmKC; ++ksl) {
+          if (ksl >= kn) break;
 #pragma unroll
           for (int j = 0; j < kTcSlices; ++j)
 #pragma unroll
-            for (int i = kTcSlices - 1 - j; i >= 0; --i) {
-              const uint64_t ad = umma::smem_desc(smem_addr(sA + (size_t)(ksl * kTcSlices + i) * kUmATile), 128, 256);
-              const uint64_t bd = umma::smem_desc(smem_addr(sB + (size_t)(ksl * kTcSlices + j) * kUmBTile), 128, 256);
-              umma::mma_bf16(tmem + (uint32_t)((i + j) * kUmN), ad, bd, idesc,
+            for (int i = kTcSlices - 1 - j; i >= 0; --i)
+              umma::mma_bf16(tmem + (uint32_t)((i + j) * kUmN),
+                             ad0 + (uint64_t)(((ksl * kTcSlices + i) * kUmATile) >> 4),
+                             bd0 + (uint64_t)(((ksl * kTcSlices + j) * kUmBTile) >> 4), idesc,
                              (fresh && ksl == 0 && j == 0) ? 0u : 1u);
-            }
+        }
         umma::commit(&mdone[b]);
         last_commit = c;
       }
@@ -966,7 +988,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_field_umma(const float4* __restr
       umma::fence_after_sync();
       bad = __syncthreads_or(bad);
       if (bad) break;
-      fold(false);
+      if (stager) fold(false);
       umma::fence_before_sync();
       __syncthreads();
     }
@@ -974,13 +996,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_field_umma(const float4* __restr
   bad = __syncthreads_or(bad);
   if (!bad) wait(&mdone[(nchunks - 1) & 1], nchunks - 1, budget);
   bad = __syncthreads_or(bad);
-  if (bad && tid == 0) {
+  if (bad && tid == issuer) {
     // drain: the last issued products and copy land before the block leaves
     if (last_commit >= 0) mbar_wait_bounded(&mdone[last_commit & 1], (unsigned)((last_commit >> 1) & 1), kDrainBudget);
-    if (last_copy >= 0) mbar_wait_bounded(&bfull[last_copy & 1], (unsigned)((last_copy >> 1) & 1), kDrainBudget);
+    for (int cc = last_copy - 1; cc <= last_copy; ++cc)  // the copies run up to one chunk ahead
+      if (cc >= 0) mbar_wait_bounded(&bfull[cc & 1], (unsigned)((cc >> 1) & 1), kDrainBudget);
   }
   umma::fence_after_sync();
-  if (!bad) {
+  if (!stager) {
+  } else if (!bad) {
     fold(true);
   } else if (myline < n2) {
 #pragma unroll 4
@@ -995,11 +1019,11 @@ template <typename TOut>
 int field_umma_launch(const float4* xsplit, const unsigned char* XU, const float* e2tab, int* err, int M, int n,
                       int KS, int B, double scale, void* kout, double bytes, double flops, cudaStream_t st,
                       double share) {
-  // one fold (up to 256 features): 16 warps at 128 registers; more: 8 warps, which also hold
-  // the running double-float sums
-  static const cudaError_t attr1 = cudaFuncSetAttribute(k_field_umma<TOut, false, 512>,
+  // one fold (up to 256 features): 16 staging warps at 120 registers; more: 8, which also hold
+  // the running double-float sums; and the issuing warp
+  static const cudaError_t attr1 = cudaFuncSetAttribute(k_field_umma<TOut, false, 16>,
                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmem);
-  static const cudaError_t attr2 = cudaFuncSetAttribute(k_field_umma<TOut, true, 256>,
+  static const cudaError_t attr2 = cudaFuncSetAttribute(k_field_umma<TOut, true, 8>,
                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmem);
   MLMC_CUDA_TRY(attr1);
   MLMC_CUDA_TRY(attr2);
@@ -1007,12 +1031,12 @@ int field_umma_launch(const float4* xsplit, const unsigned char* XU, const float
   const long long budget = wait_budget_clocks();
   if (M > kTcFold)
     MLMC_LAUNCH("field_tc", bytes * share, flops * share, st,
-                (k_field_umma<TOut, true, 256><<<grid, 256, kUmSmem, st>>>(xsplit, XU, e2tab, M, n, KS, scale, budget,
-                                                                            err, (TOut*)kout)));
+                (k_field_umma<TOut, true, 8><<<grid, 32 * 9, kUmSmem, st>>>(xsplit, XU, e2tab, M, n, KS, scale, budget,
+                                                                             err, (TOut*)kout)));
   else
     MLMC_LAUNCH("field_tc", bytes * share, flops * share, st,
-                (k_field_umma<TOut, false, 512><<<grid, 512, kUmSmem, st>>>(xsplit, XU, e2tab, M, n, KS, scale, budget,
-                                                                             err, (TOut*)kout)));
+                (k_field_umma<TOut, false, 16><<<grid, 32 * 17, kUmSmem, st>>>(xsplit, XU, e2tab, M, n, KS, scale,
+                                                                                budget, err, (TOut*)kout)));
   return MLMC_OK;
 }
 
@@ -1025,14 +1049,17 @@ int field_tc_all(const double2* tab, const float4* xsplit, float4* pt, uint4* Xf
                  cudaStream_t st, bool warp_mma) {
   const int KS = (M + 7) / 8;
   const size_t nxs = (size_t)B * ((n - 1) / 16) * KS * 32;
-  MLMC_LAUNCH("xslices", (double)nxs * 2 * 112.0, (double)nxs * 2 * 500.0, st,
-              (k_xslices<<<blocks_for(2 * nxs, 256), 256, 0, st>>>(xsplit, B, M, n, KS, Xf, e2tab)));
+  const bool umma_volume = !warp_mma && umma_applies(n);
+  const int axis0 = umma_volume ? 1 : 0;  // the tcgen05 volume takes its x-slices from k_uxslices
+  MLMC_LAUNCH("xslices", (double)nxs * (2 - axis0) * 112.0, (double)nxs * (2 - axis0) * 500.0, st,
+              (k_xslices<<<blocks_for((2 - axis0) * nxs, 256), 256, 0, st>>>(xsplit, B, M, n, KS, axis0, Xf,
+                                                                               e2tab)));
   const size_t nf = (size_t)B * M * n;
   MLMC_LAUNCH("face_factors", (double)nf * 48.0, (double)nf * 40.0, st,
               (k_face_factors<<<blocks_for(nf, 256), 256, 0, st>>>(xsplit, B, M, n, pt)));
   const double n3 = (double)n * n * n;
   const double vshare = (double)(n - 1) * n * n / n3;
-  if (!warp_mma && umma_applies(n)) {
+  if (umma_volume) {
     const size_t nux = (size_t)B * ((n - 1) / kUmN) * KS * kUmN * 8;
     MLMC_LAUNCH("xslices", (double)nux * 28.0, (double)nux * 250.0, st,
                 (k_uxslices<<<blocks_for(nux, 256), 256, 0, st>>>(xsplit, B, M, n, KS, XU)));

@@ -11,6 +11,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -70,3 +71,31 @@ def test_field_tensor_core_shapes_match_oracle(arith):
                          timeout=900)
     assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-4000:]
     print(res.stdout.strip())
+
+
+DUMP = r"""
+import sys, numpy as np, torch
+import paper_1607_03252_gb300 as mg
+from paper_1607_03252_gb300.workloads import RUN_SEED, sample_ids
+out = {}
+for n, B, M in ((65, 3, 256), (129, 1, 256), (65, 1, 1024)):
+    k = torch.empty((B, n, n, n), dtype=torch.float64, device="cuda")
+    mg.mlmc_field_eval(mg.field_cfg(RUN_SEED, 1.0, 0.3, M), sample_ids(3, 2, B), k)
+    out["%d_%d" % (n, M)] = k.cpu().numpy()
+np.savez(sys.argv[1], **out)
+"""
+
+
+def test_field_tcgen05_matches_warp_mma_bitwise(tmp_path):
+    """The tcgen05 volume and the mma.sync volume form the same slices and exact group sums,
+    so the whole field is bitwise the same (65^3 and 129^3, one and four folds)."""
+    res = {}
+    for arith in (3, 4):
+        f = tmp_path / ("k%d.npz" % arith)
+        env = dict(os.environ, MLMC_FIELD_ARITH=str(arith))
+        r = subprocess.run([sys.executable, "-c", DUMP, str(f)], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+        res[arith] = dict(np.load(f))
+    for key in res[3]:
+        assert np.array_equal(res[3][key], res[4][key]), key
