@@ -20,6 +20,7 @@
 #include "philox.cuh"
 #include "prof.cuh"
 #include "umma.cuh"
+#include "umma_layout.h"
 #include "widen.cuh"
 
 namespace mlmc {
@@ -795,8 +796,7 @@ __global__ void k_uxslices(const float4* __restrict__ xsplit, int B, int M, int 
 #pragma unroll
       for (int i = 0; i < kTcSlices; ++i) re[i] = im[i] = 0.f;
     }
-    unsigned char* o = XU + (((size_t)(s * XB + xb) * KS + ks) * kTcSlices) * kUmBTile + (xr >> 3) * 256 +
-                       (fl >> 2) * 128 + (xr & 7) * 16 + (fl & 3) * 4;
+    unsigned char* o = XU + (((size_t)(s * XB + xb) * KS + ks) * kTcSlices) * kUmBTile + umma::pair_offset(xr, fl);
 #pragma unroll
     for (int i = 0; i < kTcSlices; ++i)
       *reinterpret_cast<uint32_t*>(o + (size_t)i * kUmBTile) = pack_bf16x2(re[i], im[i]);
@@ -941,7 +941,7 @@ __global__ void __launch_bounds__(32 * (SW + 1), 1) k_field_umma(const float4* _
         if (ksl >= kn) continue;
         uint32_t q[kTcSlices];
         q_slices(bq[r], dq[r], q);  // zero tables give zero slices
-        unsigned char* dst = sA + (size_t)ksl * kTcSlices * kUmATile + rg * 256 + kg * 128 + rr * 16 + fl4 * 4;
+        unsigned char* dst = sA + (size_t)ksl * kTcSlices * kUmATile + umma::pair_offset(rg * 8 + rr, kg * 4 + fl4);
 #pragma unroll
         for (int j = 0; j < kTcSlices; ++j) *reinterpret_cast<uint32_t*>(dst + (size_t)j * kUmATile) = q[j];
       }
@@ -963,7 +963,8 @@ __global__ void __launch_bounds__(32 * (SW + 1), 1) k_field_umma(const float4* _
         const bool fresh = (ks0 * 8) % kTcFold == 0;  // the first chunk of a fold period
         // a tile's descriptor is the chunk base's plus its byte offset / 16 (shared-memory
         // addresses stay below 2^18, so the 14-bit address field does not carry)
-        const uint64_t ad0 = umma::smem_desc(smem_addr(sA), 128, 256), bd0 = umma::smem_desc(smem_addr(sB), 128, 256);
+        const uint64_t ad0 = umma::smem_desc(smem_addr(sA), umma::kLeadingBytes, umma::kStrideBytes);
+        const uint64_t bd0 = umma::smem_desc(smem_addr(sB), umma::kLeadingBytes, umma::kStrideBytes);
 #pragma unroll
         for (int ksl = 0; ksl < kUmKC; ++ksl) {
           if (ksl >= kn) break;
