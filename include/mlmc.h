@@ -573,7 +573,7 @@ int mlmc_tune_set(int n, int precision, int smoother, int nu);
  * process-wide).
  *
  * mlmc_set_wait_budget -- every bounded wait inside a kernel (the mbarrier waits of the
- * TMA bulk-copy smoothers) gives up after `clocks` SM clocks: the kernel then records an
+ * TMA bulk-copy smoothers and of the tcgen05 field kernel) gives up after `clocks` SM clocks: the kernel then records an
  * error word, waits (bounded by about one second, whatever `clocks` is) for the copies it
  * still has in flight, and returns; the solve reports MLMC_ERR_TIMEOUT and the context
  * stays usable. Default 2e9 clocks (about one second). clocks = 0 gives up at the first
@@ -585,9 +585,18 @@ int mlmc_tune_set(int n, int precision, int smoother, int nu);
  * device allocations of the library, every later one fails with MLMC_ERR_OOM without
  * calling the CUDA allocator, until the next call; after = -1 turns it off (the
  * default). MLMC_ERR_INVALID for after < -1. Host-only.
+ *
+ * mlmc_inject_wait_failure -- host-side fault injection for the tensor-core field (the
+ * tcgen05 volume kernel, grids from 65^3): each of the next `launches` launches of that
+ * kernel also waits, in its issuing thread, on an mbarrier that nothing arrives on, so the
+ * wait runs out after the wait budget (mlmc_set_wait_budget); the blocks then drain their
+ * copies and products, write NaN to their nodes, free their tensor memory and return, and
+ * mlmc_field_eval (or the level call) reports MLMC_ERR_TIMEOUT. launches = 0 turns it off
+ * (the default). MLMC_ERR_INVALID for launches < 0. Host-only.
  */
 int mlmc_set_wait_budget(int64_t clocks, int64_t* previous);
 int mlmc_inject_alloc_failure(int64_t after);
+int mlmc_inject_wait_failure(int launches);
 
 /* Text of the last error on the calling thread ("" if none). Never NULL. */
 const char* mlmc_last_error_string(void);

@@ -18,5 +18,5 @@ from ._capi import (  # noqa: F401
     MLMC_SMOOTH_FUSED_32x16, MLMC_SMOOTH_FUSED_64x8, MLMC_SMOOTH_TWO_PASS, SIGNATURES,
     FieldCfg, LevelStats, MgCfg, MgStats, MlmcCfg, MlmcError, field_cfg, lib, library_path, make_mlmc_cfg, mg_cfg,
     mg_solve_batch, mlmc_field_eval, mlmc_level_estimate, mlmc_level_run, mlmc_autotune, mlmc_tune_set, profile_enable, profile_fma_peak, profile_read,
-    profile_reset, profile_total_launches, Service, set_wait_budget, inject_alloc_failure,
+    profile_reset, profile_total_launches, Service, set_wait_budget, inject_alloc_failure, inject_wait_failure,
 )

@@ -206,6 +206,7 @@ SIGNATURES = {
     "mlmc_service_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServiceReport)]),
     "mlmc_set_wait_budget": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mlmc_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int64]),
+    "mlmc_inject_wait_failure": (ctypes.c_int, [ctypes.c_int]),
     "mlmc_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mlmc_autotune": (ctypes.c_int, [ctypes.POINTER(MlmcCfg), ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                      ctypes.POINTER(TuneEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -454,6 +455,12 @@ def inject_alloc_failure(after: int):
     """After `after` more successful device allocations every later one fails with
     MLMC_ERR_OOM (-1: off)."""
     _check(lib().mlmc_inject_alloc_failure(int(after)), "mlmc_inject_alloc_failure")
+
+
+def inject_wait_failure(launches: int):
+    """The next `launches` launches of the tcgen05 field kernel wait on an mbarrier that
+    nothing arrives on, so the wait runs out after the wait budget (0: off)."""
+    _check(lib().mlmc_inject_wait_failure(int(launches)), "mlmc_inject_wait_failure")
 
 
 def make_mlmc_cfg(run_seed, sigma2, ell, M, n0=17, nu1=2, nu2=2, rtol=1e-10, max_cycles=100,

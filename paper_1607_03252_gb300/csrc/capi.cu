@@ -327,6 +327,11 @@ struct LevelBatch {
   int read_record(LevelRecord* r, cudaStream_t st) {
     MLMC_CUDA_TRY(cudaMemcpyAsync(r, rec.get(), sizeof(LevelRecord), cudaMemcpyDeviceToHost, st));
     MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (field_wait_error_take()) {
+      set_error("level batch: a bounded wait of the tensor-core field ran out (budget %lld SM clocks)",
+                wait_budget_clocks());
+      return MLMC_ERR_TIMEOUT;
+    }
     return MLMC_OK;
   }
 };
@@ -449,6 +454,15 @@ int mlmc_inject_alloc_failure(int64_t after) {
   return MLMC_OK;
 }
 
+int mlmc_inject_wait_failure(int launches) {
+  if (launches < 0) {
+    set_error("mlmc_inject_wait_failure: launches=%d must be >= 0", launches);
+    return MLMC_ERR_INVALID;
+  }
+  field_inject_wait_failure(launches);
+  return MLMC_OK;
+}
+
 static int field_eval_impl(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n,
                            int n_fine, int dtype, void* k_out, void* stream) {
   MLMC_TRY(check_field(cfg));
@@ -479,6 +493,12 @@ static int field_eval_impl(const mlmc_field_cfg* cfg, const uint64_t* sample_ids
     MLMC_TRY(field_eval_dev(*cfg, ids.as<uint64_t>(), batch, n, dtype, k_out, scratch.get(), st));
   // the host ids may be reused by the caller as soon as this returns
   MLMC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!spde && field_wait_error_take()) {
+    set_error("mlmc_field_eval: a bounded wait of the tensor-core field ran out (budget %lld SM clocks); the "
+              "nodes of the blocks concerned hold NaN",
+              wait_budget_clocks());
+    return MLMC_ERR_TIMEOUT;
+  }
   return MLMC_OK;
 }
 

@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <atomic>
 #include <cstdlib>
 
 #include "bulk.cuh"
@@ -759,6 +760,22 @@ int field_tc_dispatch(const float4* xsplit, const float4* pt, const uint4* Xf, c
 // runs out records *err, drains its copies and products, writes NaN to its nodes and frees
 // its tensor memory.
 constexpr int kUmM = 128, kUmN = 64, kUmKC = 2;
+
+// Set to 1 by a tensor-core field block whose bounded wait ran out (field_wait_error_take).
+__device__ int g_field_wait_err = 0;
+
+static std::atomic<int> g_inject_wait{0};
+void field_inject_wait_failure(int launches) { g_inject_wait.store(launches); }
+
+int field_wait_error_take() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_field_wait_err, sizeof(int)) != cudaSuccess) return 0;
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_field_wait_err, &zero, sizeof(int));
+  }
+  return v;
+}
 constexpr unsigned kUmCols = 512;
 constexpr int kUmATile = kUmM * 32, kUmBTile = kUmN * 32;  // bytes of one (k-step, slice) tile
 constexpr int kUmAChunk = kUmKC * kTcSlices * kUmATile, kUmBChunk = kUmKC * kTcSlices * kUmBTile;
@@ -807,7 +824,7 @@ template <typename TOut, bool MULTI, int SW>
 __global__ void __launch_bounds__(32 * (SW + 1), 1) k_field_umma(const float4* __restrict__ tsplit,
                                                                const unsigned char* __restrict__ XU,
                                                                const float* __restrict__ e2tab, int M, int n, int KS,
-                                                               double scale, long long budget, int* err,
+                                                               double scale, long long budget, int inject, int* err,
                                                                TOut* __restrict__ kout) {
   extern __shared__ unsigned char um_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)um_raw + 127) & ~(uintptr_t)127);
@@ -815,7 +832,8 @@ __global__ void __launch_bounds__(32 * (SW + 1), 1) k_field_umma(const float4* _
   float* se2 = reinterpret_cast<float*>(sline + kUmM);
   uint64_t* bfull = reinterpret_cast<uint64_t*>(se2 + 64);  // [2]: B chunk landed
   uint64_t* mdone = bfull + 2;                               // [2]: the chunk's products done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 2);
+  uint64_t* never = mdone + 2;                               // fault injection: nothing arrives
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(never + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s = blockIdx.z, xb = blockIdx.x, XB = (n - 1) / kUmN;
   const size_t n2 = (size_t)n * n, L0 = (size_t)blockIdx.y * kUmM;
@@ -829,6 +847,7 @@ __global__ void __launch_bounds__(32 * (SW + 1), 1) k_field_umma(const float4* _
       mbar_init(&bfull[q], 1);
       mbar_init(&mdone[q], 1);
     }
+    mbar_init(never, 1);
     mbar_fence_init();
   }
   if (warp == 0) umma::alloc(tslot, kUmCols);
@@ -907,7 +926,10 @@ __global__ void __launch_bounds__(32 * (SW + 1), 1) k_field_umma(const float4* _
              &bfull[cc & 1]);
     last_copy = cc;
   };
-  if (tid == issuer) issue_copy(0);
+  if (tid == issuer) {
+    issue_copy(0);
+    if (inject) wait(never, 0, budget);  // injected failure: runs out after the budget
+  }
   for (int c = 0; c < nchunks; ++c) {
     const int b = c & 1;
     const int ks0 = c * kUmKC, kn = min(kUmKC, KS - ks0);
@@ -1017,7 +1039,7 @@ __global__ void __launch_bounds__(32 * (SW + 1), 1) k_field_umma(const float4* _
 }
 
 template <typename TOut>
-int field_umma_launch(const float4* xsplit, const unsigned char* XU, const float* e2tab, int* err, int M, int n,
+int field_umma_launch(const float4* xsplit, const unsigned char* XU, const float* e2tab, int M, int n,
                       int KS, int B, double scale, void* kout, double bytes, double flops, cudaStream_t st,
                       double share) {
   // one fold (up to 256 features): 16 staging warps at 120 registers; more: 8, which also hold
@@ -1030,14 +1052,28 @@ int field_umma_launch(const float4* xsplit, const unsigned char* XU, const float
   MLMC_CUDA_TRY(attr2);
   const dim3 grid((unsigned)((n - 1) / kUmN), (unsigned)(((size_t)n * n + kUmM - 1) / kUmM), (unsigned)B);
   const long long budget = wait_budget_clocks();
+  int inject = 0;
+  for (int left = g_inject_wait.load(); left > 0; left = g_inject_wait.load())
+    if (g_inject_wait.compare_exchange_weak(left, left - 1)) {
+      inject = 1;
+      break;
+    }
+  static int* const err = [] {
+    void* p = nullptr;
+    return cudaGetSymbolAddress(&p, g_field_wait_err) == cudaSuccess ? (int*)p : nullptr;
+  }();
+  if (!err) {
+    set_error("field: no address for the wait-error flag");
+    return MLMC_ERR_CUDA;
+  }
   if (M > kTcFold)
     MLMC_LAUNCH("field_tc", bytes * share, flops * share, st,
                 (k_field_umma<TOut, true, 8><<<grid, 32 * 9, kUmSmem, st>>>(xsplit, XU, e2tab, M, n, KS, scale, budget,
-                                                                             err, (TOut*)kout)));
+                                                                             inject, err, (TOut*)kout)));
   else
     MLMC_LAUNCH("field_tc", bytes * share, flops * share, st,
                 (k_field_umma<TOut, false, 16><<<grid, 32 * 17, kUmSmem, st>>>(xsplit, XU, e2tab, M, n, KS, scale,
-                                                                                budget, err, (TOut*)kout)));
+                                                                                budget, inject, err, (TOut*)kout)));
   return MLMC_OK;
 }
 
@@ -1045,8 +1081,7 @@ int field_umma_launch(const float4* xsplit, const unsigned char* XU, const float
 // x < n - 1 (tcgen05 from n = 65 unless warp_mma, warp-level mma.sync otherwise), the face
 // x = n - 1 (y < n - 1), the edge x = y = n - 1.
 template <typename TOut>
-int field_tc_all(const double2* tab, const float4* xsplit, float4* pt, uint4* Xf, unsigned char* XU, int* err,
-                 float* e2tab, int M, int n, int B, double scale, void* kout, double bytes, double flops,
+int field_tc_all(const double2* tab, const float4* xsplit, float4* pt, uint4* Xf, unsigned char* XU, float* e2tab, int M, int n, int B, double scale, void* kout, double bytes, double flops,
                  cudaStream_t st, bool warp_mma) {
   const int KS = (M + 7) / 8;
   const size_t nxs = (size_t)B * ((n - 1) / 16) * KS * 32;
@@ -1064,7 +1099,7 @@ int field_tc_all(const double2* tab, const float4* xsplit, float4* pt, uint4* Xf
     const size_t nux = (size_t)B * ((n - 1) / kUmN) * KS * kUmN * 8;
     MLMC_LAUNCH("xslices", (double)nux * 28.0, (double)nux * 250.0, st,
                 (k_uxslices<<<blocks_for(nux, 256), 256, 0, st>>>(xsplit, B, M, n, KS, XU)));
-    MLMC_TRY(field_umma_launch<TOut>(xsplit, XU, e2tab, err, M, n, KS, B, scale, kout, bytes, flops, st, vshare));
+    MLMC_TRY(field_umma_launch<TOut>(xsplit, XU, e2tab, M, n, KS, B, scale, kout, bytes, flops, st, vshare));
   } else {
     MLMC_TRY((field_tc_dispatch<TOut, false>(xsplit, pt, Xf, e2tab, M, n, KS, B, scale, kout, bytes, flops, st,
                                              vshare)));
@@ -1084,7 +1119,7 @@ size_t field_scratch_bytes(int B, int M, int n) {
   return a256((size_t)B * M * 3 * sizeof(double)) + a256((size_t)B * M * sizeof(double)) +
          a256((size_t)B * 3 * M * n * sizeof(double2)) + a256((size_t)B * 3 * M * n * sizeof(float4)) +
          (tc_applies(n) ? a256(2 * tc_xslice_bytes(B, M, n)) + a256(64 * sizeof(float)) +
-                              a256((size_t)B * M * n * sizeof(float4)) + a256(tc_uxslice_bytes(B, M, n)) + 256
+                              a256((size_t)B * M * n * sizeof(float4)) + a256(tc_uxslice_bytes(B, M, n))
                         : 0);
 }
 
@@ -1114,7 +1149,6 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
   float* e2tab = tc_applies(n) ? (float*)carve(64 * sizeof(float)) : nullptr;
   float4* pt = tc_applies(n) ? (float4*)carve((size_t)B * cfg.M * n * sizeof(float4)) : nullptr;
   unsigned char* XU = tc_applies(n) ? (unsigned char*)carve(tc_uxslice_bytes(B, cfg.M, n)) : nullptr;
-  int* err = tc_applies(n) ? (int*)carve(256) : nullptr;
   const size_t nf = (size_t)B * cfg.M;
   MLMC_LAUNCH("features", nf * 40.0, nf * 200.0, st,
               (k_features<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(ids_dev, B, cfg.M, cfg.run_seed,
@@ -1151,10 +1185,10 @@ int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, in
     if ((arith == kFieldTC || arith == kFieldTCWarp) && tc_applies(n)) {
       const bool warp_mma = arith == kFieldTCWarp;
       if (dtype == MLMC_F64)
-        MLMC_TRY(field_tc_all<double>(tab, xsplit, pt, Xf, XU, err, e2tab, cfg.M, n, B, scale, kout, bytes, flops, st,
+        MLMC_TRY(field_tc_all<double>(tab, xsplit, pt, Xf, XU, e2tab, cfg.M, n, B, scale, kout, bytes, flops, st,
                                       warp_mma));
       else
-        MLMC_TRY(field_tc_all<float>(tab, xsplit, pt, Xf, XU, err, e2tab, cfg.M, n, B, scale, kout, bytes, flops, st,
+        MLMC_TRY(field_tc_all<float>(tab, xsplit, pt, Xf, XU, e2tab, cfg.M, n, B, scale, kout, bytes, flops, st,
                                      warp_mma));
     } else {
       // x < n - 1 in tiles of 8 (of 4 on the 5-node grid), then x = n - 1

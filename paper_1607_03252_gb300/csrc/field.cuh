@@ -21,6 +21,14 @@ enum { kFieldDF32Line = 0, kFieldFP64 = 1, kFieldDF32 = 2, kFieldTC = 3, kFieldT
 // variable MLMC_FIELD_ARITH (0..4) read once.
 int field_arith_default();
 
+// 1 if a bounded wait of a tensor-core field block has run out since the last call (the
+// block's nodes hold NaN); clears the flag. Synchronises with the device.
+int field_wait_error_take();
+
+// The next `launches` launches of the tcgen05 field kernel also wait on an mbarrier that
+// nothing arrives on (host-side fault injection, mlmc_inject_wait_failure).
+void field_inject_wait_failure(int launches);
+
 // k_out[s][z][y][x] = exp(log k) at the n^3 nodes for the B ids in ids_dev (device).
 // dtype MLMC_F64 or MLMC_F32. scratch: field_scratch_bytes(B, M, n) bytes, 256-aligned.
 int field_eval_dev(const mlmc_field_cfg& cfg, const uint64_t* ids_dev, int B, int n, int dtype, void* k_out,

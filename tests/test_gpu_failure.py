@@ -8,7 +8,10 @@
   - a device allocation that fails: injected on the host (mlmc_inject_alloc_failure),
     reported as MLMC_ERR_OOM by the level call and by the service's batch, with the
     partially allocated batch released; afterwards everything runs again;
-  - a request withdrawn from the service queue (mlmc_cancel) and a wait that must time out.
+  - a request withdrawn from the service queue (mlmc_cancel) and a wait that must time out;
+  - a wait of the tcgen05 field kernel on an mbarrier that nothing arrives on (injected on the
+    host, mlmc_inject_wait_failure): NaN in the blocks' nodes, MLMC_ERR_TIMEOUT, and the
+    context usable afterwards.
 """
 import time
 
@@ -29,6 +32,7 @@ def restore_controls():
     yield
     mg.set_wait_budget(2_000_000_000)
     mg.inject_alloc_failure(-1)
+    mg.inject_wait_failure(0)
 
 
 def _solve(k, f, smoother, cycles=3):
@@ -127,3 +131,29 @@ def test_service_wait_times_out_behind_a_pending_batch():
         assert st == mg.MLMC_ERR_TIMEOUT and r.status == mg.MLMC_PENDING
         st, r = svc.wait(t)
         assert st == mg.MLMC_OK and r.status == mg.MLMC_OK
+
+
+def test_expired_field_wait_reports_timeout_and_context_survives(restore_controls):
+    """The tensor-core field (tcgen05 from 65^3) bounds its mbarrier waits. With the failure
+    injected on the host (its issuing thread also waits on an mbarrier nothing arrives on) and
+    a short budget, the wait runs out: the blocks drain their copies and products, write NaN,
+    free their tensor memory, and mlmc_field_eval reports MLMC_ERR_TIMEOUT. The injection is
+    used up; the same context then gives the field again, bit for bit."""
+    n, B = 65, 2
+    fc = mg.field_cfg(**FIELD)
+    ids = sample_ids(2, 11, B)
+    ref = torch.empty((B, n, n, n), dtype=torch.float64, device="cuda")
+    mg.mlmc_field_eval(fc, ids, ref)
+    prev = mg.set_wait_budget(100_000)
+    mg.inject_wait_failure(1)
+    k = torch.zeros_like(ref)
+    with pytest.raises(mg.MlmcError) as e:
+        mg.mlmc_field_eval(fc, ids, k)
+    assert e.value.status == mg.MLMC_ERR_TIMEOUT
+    assert torch.isnan(k[..., : n - 1]).all()  # the tcgen05 volume; the face x = n - 1 is another kernel's
+    mg.set_wait_budget(prev)
+    k2 = torch.empty_like(ref)
+    mg.mlmc_field_eval(fc, ids, k2)
+    assert torch.equal(k2, ref)
+    with pytest.raises(mg.MlmcError):
+        mg.inject_wait_failure(-1)
