@@ -327,7 +327,7 @@ struct LevelBatch {
   int read_record(LevelRecord* r, cudaStream_t st) {
     MLMC_CUDA_TRY(cudaMemcpyAsync(r, rec.get(), sizeof(LevelRecord), cudaMemcpyDeviceToHost, st));
     MLMC_CUDA_TRY(cudaStreamSynchronize(st));
-    if (field_wait_error_take()) {
+    if (field_wait_error_take(st)) {
       set_error("level batch: a bounded wait of the tensor-core field ran out (budget %lld SM clocks)",
                 wait_budget_clocks());
       return MLMC_ERR_TIMEOUT;
@@ -493,7 +493,7 @@ static int field_eval_impl(const mlmc_field_cfg* cfg, const uint64_t* sample_ids
     MLMC_TRY(field_eval_dev(*cfg, ids.as<uint64_t>(), batch, n, dtype, k_out, scratch.get(), st));
   // the host ids may be reused by the caller as soon as this returns
   MLMC_CUDA_TRY(cudaStreamSynchronize(st));
-  if (!spde && field_wait_error_take()) {
+  if (!spde && field_wait_error_take(st)) {
     set_error("mlmc_field_eval: a bounded wait of the tensor-core field ran out (budget %lld SM clocks); the "
               "nodes of the blocks concerned hold NaN",
               wait_budget_clocks());

@@ -767,12 +767,15 @@ __device__ int g_field_wait_err = 0;
 static std::atomic<int> g_inject_wait{0};
 void field_inject_wait_failure(int launches) { g_inject_wait.store(launches); }
 
-int field_wait_error_take() {
+int field_wait_error_take(cudaStream_t st) {
   int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_field_wait_err, sizeof(int)) != cudaSuccess) return 0;
+  if (cudaMemcpyFromSymbolAsync(&v, g_field_wait_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return 0;
   if (v) {
-    const int zero = 0;
-    cudaMemcpyToSymbol(g_field_wait_err, &zero, sizeof(int));
+    static const int zero = 0;
+    cudaMemcpyToSymbolAsync(g_field_wait_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
   }
   return v;
 }

@@ -22,8 +22,8 @@ enum { kFieldDF32Line = 0, kFieldFP64 = 1, kFieldDF32 = 2, kFieldTC = 3, kFieldT
 int field_arith_default();
 
 // 1 if a bounded wait of a tensor-core field block has run out since the last call (the
-// block's nodes hold NaN); clears the flag. Synchronises with the device.
-int field_wait_error_take();
+// block's nodes hold NaN); clears the flag. Reads it on stream st and synchronises st.
+int field_wait_error_take(cudaStream_t st);
 
 // The next `launches` launches of the tcgen05 field kernel also wait on an mbarrier that
 // nothing arrives on (host-side fault injection, mlmc_inject_wait_failure).
