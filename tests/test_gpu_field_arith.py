@@ -5,8 +5,8 @@ warp-level mma.sync below; 4: mma.sync everywhere). Each must give the oracle's 
 1e-12 relative, and its FP32 output must be its FP64 output rounded. The tensor-core form
 also runs every block shape (16 to 128 x-values per block, 17^3 to 257^3), a feature count
 that is not a multiple of the 8 features of a k-step, the fold of its group sums every 256
-features (M = 1024, both forms), the exponential covariance, and a batch whose samples
-differ."""
+features (M = 1024, both forms), a last chunk of one k-step on tcgen05 (M = 100), the
+exponential covariance, and a batch whose samples differ."""
 import os
 import subprocess
 import sys
@@ -29,7 +29,7 @@ worst = 0.0
 cases = [(33, 3, 256, 0.3, 0), (17, 2, 100, 0.1, 0)]
 if len(sys.argv) > 1:
     cases = [(65, 2, 256, 0.3, 0), (129, 1, 256, 0.15, 1), (33, 2, 1024, 0.3, 0), (65, 1, 1024, 0.3, 0),
-             (257, 1, 64, 0.2, 0), (17, 40, 256, 0.3, 1)]
+             (65, 1, 100, 0.2, 0), (257, 1, 64, 0.2, 0), (17, 40, 256, 0.3, 1)]
 for n, B, M, ell, cov in cases:
     ids = sample_ids(2, 7, B)
     fc = mg.field_cfg(RUN_SEED, 1.0, ell, M, cov)
