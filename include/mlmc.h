@@ -200,10 +200,14 @@ typedef struct {
  * (the coefficient of one realisation in Algorithm 1) at the n^3 nodes of
  * one grid. Writes k = exp(log k) into k_out (device, batch * n^3 elements of type
  * `dtype`: MLMC_F64, or MLMC_F32 = the FP64 value rounded to FP32). The phase is
- * always evaluated in FP64. sample_ids_host is host memory, read before return.
+ * always evaluated in FP64; the sum over the M features runs as exact products of bf16
+ * slices of the phasors on the tensor cores (tcgen05 from n = 65, the warp-level MMA
+ * below; grids with n - 1 a multiple of 16, others in double-float), within ~1e-13 of the
+ * FP64 sum relative in k. sample_ids_host is host memory, read before return.
  * Errors: MLMC_ERR_INVALID for n not 2^p+1 (5 <= n <= 4097), batch < 1, M < 1,
- * ell <= 0, sigma2 < 0, unknown cov or dtype, or NULL pointers; MLMC_ERR_OOM / _CUDA.
- * Enqueued on `stream`; the library's scratch is released stream-ordered.
+ * ell <= 0, sigma2 < 0, unknown cov or dtype, or NULL pointers; MLMC_ERR_OOM / _CUDA;
+ * MLMC_ERR_TIMEOUT if a bounded wait of the tensor-core kernel ran out (its nodes hold NaN;
+ * see mlmc_set_wait_budget). Returns after the stream has drained.
  */
 int mlmc_field_eval(const mlmc_field_cfg* cfg, const uint64_t* sample_ids_host, int batch, int n, int dtype,
                     void* k_out, void* stream);
