@@ -5,7 +5,8 @@
 // PTX fragment layout (A: rows g, g + 8 and k pairs 2c, 2c + 8; B: column g and the same k;
 // D: rows g, g + 8, columns 2c, 2c + 1; the lower half of a register holds the even k) in
 // exact double arithmetic, one sum per slice group. Writes, for every sample, line (y, z) and
-// x < n - 1, the sum over the groups, i.e. log k / scale.
+// x < n - 1, the sum over the groups, i.e. log k / scale, then the same on the face x = n - 1
+// for every z and y < n - 1 (the face factors by k_face_factors).
 //   tc_emu seed M n ell cov out.bin id0 id1 ...
 #define _GNU_SOURCE 1
 #include <algorithm>
@@ -62,13 +63,14 @@ static float bf(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 static double lo16(unsigned r) { return (double)bf((uint16_t)(r & 0xffffu)); }
 static double hi16(unsigned r) { return (double)bf((uint16_t)(r >> 16)); }
 
-// The volume x < n - 1 with RX row tiles per block: every block's line slots as the kernel
-// fills them, the staged chunks by tc_stage, the products of every warp emulated.
-template <int RX>
-static void run_volume(int B, int M, int n, const float4* xs, const uint4* Xf, double* S) {
+// The volume x < n - 1 (rows x, lines (y, z)) or the face x = n - 1 (rows y < n - 1, lines z;
+// FACE) with RX row tiles per block: every block's line slots as the kernel fills them, the
+// staged chunks by tc_stage, the products of every warp emulated. S[s][line][row].
+template <int RX, bool FACE>
+static void run_volume(int B, int M, int n, const float4* xs, const float4* pt, const uint4* Xf, double* S) {
   using Sh = TcShape<RX>;
   const int KS = (M + 7) / 8, RT = (n - 1) / 16;
-  const size_t nl = (size_t)n * n;
+  const size_t nl = FACE ? (size_t)n : (size_t)n * n;
   const int lgps = (int)((nl + 31) / 32);
   const int gy = (B * lgps + 8 / RX - 1) / (8 / RX);
   std::vector<int4> sline(Sh::LQ);
@@ -80,13 +82,13 @@ static void run_volume(int B, int M, int n, const float4* xs, const uint4* Xf, d
       for (int t = 0; t < Sh::LQ; ++t) {
         const int lg = by * (8 / RX) + t / 32, ls = lg / lgps, line = (lg % lgps) * 32 + t % 32;
         const bool ok = ls < B && (size_t)line < nl;
-        sline[t] = int4{ls, line % n, line / n, ok ? 1 : 0};
+        sline[t] = FACE ? int4{ls, line, 0, ok ? 1 : 0} : int4{ls, line % n, line / n, ok ? 1 : 0};
       }
       std::fill(acc.begin(), acc.end(), 0.0);
       for (int m0 = 0; m0 < M; m0 += Sh::KCF) {
         std::fill(sq.begin(), sq.end(), uint2{0x7fc07fc0u, 0x7fc07fc0u});  // NaN if read unstaged
         for (int it = 0; it < Sh::LQ * Sh::KCF; ++it)
-          tc_stage<RX, false>(it, m0, M, n, xs, nullptr, sline.data(), sq.data());
+          tc_stage<RX, FACE>(it, m0, M, n, xs, pt, sline.data(), sq.data());
         const int ksn = std::min(RX, KS - m0 / 8);
         for (int warp = 0; warp < 8; ++warp) {
           const int rt = bx * RX + warp % RX, ct0 = (warp / RX) * 4;
@@ -169,18 +171,27 @@ int main(int argc, char** argv) {
   std::vector<uint4> Xf(2 * tc_xslice_bytes(B, M, n) / sizeof(uint4));
   std::vector<float> e2(64);
   k_xslices(xs.data(), B, M, n, KS, 0, Xf.data(), e2.data());
-  std::vector<double> S((size_t)B * n * n * (n - 1), NAN);
-  if (RT % 8 == 0)
-    run_volume<8>(B, M, n, xs.data(), Xf.data(), S.data());
-  else if (RT % 4 == 0)
-    run_volume<4>(B, M, n, xs.data(), Xf.data(), S.data());
-  else if (RT % 2 == 0)
-    run_volume<2>(B, M, n, xs.data(), Xf.data(), S.data());
-  else
-    run_volume<1>(B, M, n, xs.data(), Xf.data(), S.data());
+  std::vector<float4> pt((size_t)B * M * n);
+  k_face_factors(xs.data(), B, M, n, pt.data());
+  const uint4* Xy = Xf.data() + Xf.size() / 2;  // the y-phasor fragments (axis 1)
+  std::vector<double> S((size_t)B * n * n * (n - 1), NAN), Sf((size_t)B * n * (n - 1), NAN);
+  if (RT % 8 == 0) {
+    run_volume<8, false>(B, M, n, xs.data(), pt.data(), Xf.data(), S.data());
+    run_volume<8, true>(B, M, n, xs.data(), pt.data(), Xy, Sf.data());
+  } else if (RT % 4 == 0) {
+    run_volume<4, false>(B, M, n, xs.data(), pt.data(), Xf.data(), S.data());
+    run_volume<4, true>(B, M, n, xs.data(), pt.data(), Xy, Sf.data());
+  } else if (RT % 2 == 0) {
+    run_volume<2, false>(B, M, n, xs.data(), pt.data(), Xf.data(), S.data());
+    run_volume<2, true>(B, M, n, xs.data(), pt.data(), Xy, Sf.data());
+  } else {
+    run_volume<1, false>(B, M, n, xs.data(), pt.data(), Xf.data(), S.data());
+    run_volume<1, true>(B, M, n, xs.data(), pt.data(), Xy, Sf.data());
+  }
   FILE* f = std::fopen(outp, "wb");
   if (!f) return 3;
   std::fwrite(S.data(), sizeof(double), S.size(), f);
+  std::fwrite(Sf.data(), sizeof(double), Sf.size(), f);
   std::fclose(f);
   return 0;
 }

@@ -1,12 +1,13 @@
 """Host run (no GPU) of the warp-level tensor-core field's data path: the kernels' own text
-for the feature draw, the phasor tables, the x-phasor slice fragments (k_xslices) and the
-staging of the line factors' slices (tc_stage), built with g++ and launched as loops, with
-the mma.sync products emulated from the PTX fragment layout in exact arithmetic. The slice
-group sums must give the oracle's log k / scale at every node x < n - 1 (1e-11 absolute,
+for the feature draw, the phasor tables, the x- and y-phasor slice fragments (k_xslices), the
+face factors (k_face_factors) and the staging of the line factors' slices (tc_stage, volume
+and face), built with g++ and launched as loops, with the mma.sync products emulated from the
+PTX fragment layout in exact arithmetic. The slice group sums must give the oracle's
+log k / scale at every node x < n - 1 and on the face x = n - 1, y < n - 1 (1e-11 absolute,
 plus the phase-rounding bound for Cauchy frequencies), with every staged slot written (the
 staging buffer is NaN-filled first). This pins the fragment orders of both operands, the
-block and warp tiling (every block shape: 16 to 128 x-values per block) and the packing of
-samples into line groups on the CPU."""
+block and warp tiling (16 to 64 x-values per block here) and the packing of samples into line
+groups on the CPU."""
 import os
 import shutil
 import subprocess
@@ -53,7 +54,7 @@ def emu(tmp_path_factory):
         _cut(widen, "__device__ __forceinline__ double widen(float f) {", "}  // namespace mlmc"),
         _cut(field, "__device__ __forceinline__ double u53(", "constexpr int kFieldThreads = 256;"),
         _cut(field, "constexpr int kTcSlices = 7;", "__device__ __forceinline__ void mma_bf16_16816("),
-        _cut(field, "size_t tc_xslice_bytes(int B, int M, int n) {", "// The line factors of the x = n - 1 face"),
+        _cut(field, "size_t tc_xslice_bytes(int B, int M, int n) {", "// The edge x = y = n - 1 in FP64"),
         _cut(field, "template <int RX>\nstruct TcShape {",
              "template <typename TOut, int RX, bool FACE>\n__global__ void __launch_bounds__(kTcThreads, 1) k_field_tc("),
     ]
@@ -75,8 +76,10 @@ def test_tensor_core_data_path_matches_oracle(emu, tmp_path, n, B, M, ell, cov):
     res = subprocess.run([emu, str(RUN_SEED), str(M), str(n), repr(ell), str(cov), str(out)] + [str(int(i)) for i in ids],
                          capture_output=True, text=True, timeout=600)
     assert res.returncode == 0, res.stdout + res.stderr
-    S = np.fromfile(out, dtype=np.float64).reshape(B, n, n, n - 1)  # [s][z][y][x < n - 1]
-    assert np.all(np.isfinite(S))
+    raw = np.fromfile(out, dtype=np.float64)
+    S = raw[: B * n * n * (n - 1)].reshape(B, n, n, n - 1)  # [s][z][y][x < n - 1]
+    Sf = raw[B * n * n * (n - 1):].reshape(B, n, n - 1)      # [s][z][y < n - 1] at x = n - 1
+    assert np.all(np.isfinite(S)) and np.all(np.isfinite(Sf))
     x = np.arange(n) / (n - 1)
     for s in range(B):
         w, b = orc.features(RUN_SEED, int(ids[s]), M, ell, cov)
@@ -84,7 +87,11 @@ def test_tensor_core_data_path_matches_oracle(emu, tmp_path, n, B, M, ell, cov):
         ph = (w[:, 0, None, None, None] * x[None, None, None, : n - 1] + w[:, 1, None, None, None] * x[None, None, :, None]
               + w[:, 2, None, None, None] * x[None, :, None, None] + b[:, None, None, None])
         So = np.cos(ph).sum(axis=0)
+        phf = (w[:, 0, None, None] * 1.0 + w[:, 1, None, None] * x[None, None, : n - 1]
+               + w[:, 2, None, None] * x[None, :, None] + b[:, None, None])
+        Sfo = np.cos(phf).sum(axis=0)
         tol = 1e-11 + np.sum(4.0 * np.finfo(np.float64).eps * (np.abs(w).sum(axis=1) + 2.0 * np.pi))
         err = float(np.max(np.abs(S[s] - So)))
-        print("n %d M %d sample %d: max |S - S_oracle| %.3e (tol %.3e)" % (n, M, s, err, tol))
-        assert err <= tol
+        errf = float(np.max(np.abs(Sf[s] - Sfo)))
+        print("n %d M %d sample %d: max |S - S_oracle| %.3e, face %.3e (tol %.3e)" % (n, M, s, err, errf, tol))
+        assert err <= tol and errf <= tol
